@@ -1,0 +1,542 @@
+/*
+ * CPU oracle walker for the Monte Carlo exp(tA)v estimator.
+ *
+ * TEST INFRASTRUCTURE ONLY: called by the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark.  It shares no code with the CUDA library;
+ * it is a plain, sequential statement of the paper's method:
+ *
+ *   - A = D - L (Sec. 2): the potential delta_i is the full row sum of A, the
+ *     jump rate lambda_i = sum_{j != i} a_ij is L_ii, and -L is the generator
+ *     of the continuous-time Markov chain (Lemma 1).
+ *   - Path sampler (Sec. 3, Eq. paths): exponential holding times with rate
+ *     lambda_j, jumps with probability k_ij = a_ij / lambda_j, stop at the
+ *     horizon t.
+ *   - Multiplicative functional (Theorem 1; Algorithm 1): the weight
+ *     W = exp(logW) with logW = integral of delta along the path (EXACT), or
+ *     its Lie / Strang quadratures on the grid k*dt, dt = t/N (Eqs. deff and
+ *     eq_general1).  The estimate of entry i is the sample mean of W v_{X_t}.
+ *   - Forward form (Lemma 2, Theorem 2; Algorithm 2): start j ~ v/V, deposit
+ *     V W at the end state.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fno-fast-math -fopenmp -shared -fPIC.
+ * Every floating-point operation below is a single IEEE operation or an
+ * explicit fma, so the result does not depend on the compiler's contraction
+ * choices.
+ *
+ * Draw schedule (fixed so that another implementation can reproduce every
+ * path exactly): one Philox4x32-10 call per walker event, key = seed,
+ * counter = {event k, entry i, path lo32, path hi32}.  Word 0 (and word 1 in
+ * FP64) gives the holding-time uniform, word 2 the slot in the row, word 3 the
+ * alias acceptance.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define O_EXACT 0
+#define O_STRANG 1
+#define O_LIE 2
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as   */
+/* easy as 1, 2, 3", SC'11.  Ten rounds of two 32x32->64 multiplies; the key */
+/* is bumped by the Weyl constants between rounds.                           */
+/* ------------------------------------------------------------------------ */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)p1;
+        uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)p0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static void draw(uint64_t seed, uint32_t event, uint32_t stream, uint64_t path, uint32_t w[4])
+{
+    uint32_t ctr[4] = {event, stream, (uint32_t)path, (uint32_t)(path >> 32)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    oracle_philox4x32_10(ctr, key, w);
+}
+
+/* Uniforms in (0, 1]: never zero, so the logarithm below is always finite. */
+static float unif_f32(uint32_t w0) { return (float)(16777216u - (w0 >> 8)) * 0x1p-24f; }
+static double unif_f64(uint32_t w0, uint32_t w1)
+{
+    uint64_t m = ((uint64_t)w0 << 21) | (uint64_t)(w1 >> 11);
+    return (double)(9007199254740992ull - m) * 0x1p-53;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Natural logarithm by range reduction x = 2^e m, m in [1/sqrt2, sqrt2], and */
+/* the series ln m = 2 artanh(s) = 2 (s + s^3/3 + s^5/5 + ...), s = (m-1)/(m+1) */
+/* (Abramowitz & Stegun 4.1.27).  Valid for positive normal finite x.          */
+/* ------------------------------------------------------------------------ */
+float oracle_logf(float x)
+{
+    uint32_t b;
+    memcpy(&b, &x, 4);
+    int e = (int)((b >> 23) & 0xffu) - 127;
+    uint32_t mb = (b & 0x007fffffu) | 0x3f800000u;
+    float m;
+    memcpy(&m, &mb, 4);
+    if (m > 1.41421356f) {
+        m = m * 0.5f;
+        e = e + 1;
+    }
+    float s = (m - 1.0f) / (m + 1.0f);
+    float z = s * s;
+    float q = 1.0f / 11.0f;
+    q = fmaf(q, z, 1.0f / 9.0f);
+    q = fmaf(q, z, 1.0f / 7.0f);
+    q = fmaf(q, z, 1.0f / 5.0f);
+    q = fmaf(q, z, 1.0f / 3.0f);
+    float s2 = s + s;
+    float lnm = fmaf(s2 * z, q, s2);
+    return fmaf((float)e, 0.693147181f, lnm);
+}
+
+double oracle_log(double x)
+{
+    uint64_t b;
+    memcpy(&b, &x, 8);
+    int e = (int)((b >> 52) & 0x7ffu) - 1023;
+    uint64_t mb = (b & 0x000fffffffffffffull) | 0x3ff0000000000000ull;
+    double m;
+    memcpy(&m, &mb, 8);
+    if (m > 1.4142135623730951) {
+        m = m * 0.5;
+        e = e + 1;
+    }
+    double s = (m - 1.0) / (m + 1.0);
+    double z = s * s;
+    double q = 1.0 / 25.0;
+    q = fma(q, z, 1.0 / 23.0);
+    q = fma(q, z, 1.0 / 21.0);
+    q = fma(q, z, 1.0 / 19.0);
+    q = fma(q, z, 1.0 / 17.0);
+    q = fma(q, z, 1.0 / 15.0);
+    q = fma(q, z, 1.0 / 13.0);
+    q = fma(q, z, 1.0 / 11.0);
+    q = fma(q, z, 1.0 / 9.0);
+    q = fma(q, z, 1.0 / 7.0);
+    q = fma(q, z, 1.0 / 5.0);
+    q = fma(q, z, 1.0 / 3.0);
+    double s2 = s + s;
+    double lnm = fma(s2 * z, q, s2);
+    return fma((double)e, 0.6931471805599453, lnm);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Preparation: the decomposition A = D - L of Sec. 2 and the jump tables.   */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n;
+    int64_t nnz_off;
+    int32_t *deg;        /* kept off-diagonal entries (a_ij > 0, j != i) */
+    int64_t *row_start;  /* exclusive prefix sum of deg */
+    uint8_t *weighted;   /* 1 if the kept entries are not all bit-equal */
+    float *inv_rate32;   /* (float)(1/lambda_i) */
+    float *delta32;      /* (float)delta_i */
+    double *inv_rate64;  /* 1/lambda_i */
+    double *delta64;     /* delta_i = a_ii + lambda_i */
+    int32_t *edge_col;   /* kept columns, CSR order */
+    int32_t *alias_col;  /* weighted rows: alias column of each slot */
+    uint32_t *thresh;    /* weighted rows: keep the slot's own column iff word3 < thresh */
+} oracle_graph;
+
+/* Status codes (mirroring the library's meaning, defined independently). */
+#define O_OK 0
+#define O_E_INVALID -1
+#define O_E_NEG_OFFDIAG -2
+#define O_E_NONFINITE -3
+
+/* Canonical Vose alias construction for one row of weights a[0..d-1] with
+ * sum lam.  Scaled weights q_k = (a_k d)/lam; indices with q < 1 go to the
+ * "small" list and the rest to "large", both in index order; pairs are popped
+ * from the back; the large entry keeps (q_l + q_s) - 1.  Leftovers get
+ * probability 1 and alias themselves.  The probability is stored as the
+ * 32-bit threshold floor(q * 2^32). */
+static void vose_row(int d, const double *a, double lam, const int32_t *cols,
+                     int32_t *alias_out, uint32_t *thresh_out, double *q, int *small, int *large)
+{
+    int ns = 0, nl = 0;
+    for (int k = 0; k < d; ++k) {
+        q[k] = (a[k] * (double)d) / lam;
+        if (q[k] < 1.0) small[ns++] = k;
+        else large[nl++] = k;
+    }
+    for (int k = 0; k < d; ++k) {
+        alias_out[k] = cols[k];
+        thresh_out[k] = 0xFFFFFFFFu;
+    }
+    while (ns > 0 && nl > 0) {
+        int s = small[--ns];
+        int l = large[--nl];
+        thresh_out[s] = (uint32_t)(q[s] * 4294967296.0);
+        alias_out[s] = cols[l];
+        q[l] = (q[l] + q[s]) - 1.0;
+        if (q[l] < 1.0) small[ns++] = l;
+        else large[nl++] = l;
+    }
+}
+
+int oracle_prep(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                oracle_graph *g)
+{
+    /* validation: CSR structure, sorted unique columns, finite values, a_ij >= 0 off the diagonal */
+    if (n < 0 || row_ptr[0] != 0) return O_E_INVALID;
+    for (int64_t i = 0; i < n; ++i) {
+        if (row_ptr[i + 1] < row_ptr[i]) return O_E_INVALID;
+        for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+            if (col[p] < 0 || col[p] >= n) return O_E_INVALID;
+            if (p > row_ptr[i] && col[p] <= col[p - 1]) return O_E_INVALID;
+            if (!isfinite(val[p])) return O_E_NONFINITE;
+            if (col[p] != i && val[p] < 0.0) return O_E_NEG_OFFDIAG;
+        }
+    }
+    int64_t off = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double lam = 0.0, diag = 0.0;
+        int d = 0, uniform = 1;
+        double first = 0.0;
+        for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+            if (col[p] == i) {
+                diag = val[p];
+            } else if (val[p] > 0.0) {
+                if (d == 0) first = val[p];
+                else if (memcmp(&first, &val[p], 8) != 0) uniform = 0;
+                lam += val[p];
+                ++d;
+            }
+        }
+        g->deg[i] = d;
+        g->row_start[i] = off;
+        g->weighted[i] = (uint8_t)(d > 1 && !uniform);
+        g->delta64[i] = diag + lam;
+        g->delta32[i] = (float)(diag + lam);
+        g->inv_rate64[i] = d > 0 ? 1.0 / lam : 0.0;
+        g->inv_rate32[i] = (float)g->inv_rate64[i];
+        off += d;
+    }
+    g->nnz_off = off;
+    int maxd = 0;
+    for (int64_t i = 0; i < n; ++i)
+        if (g->deg[i] > maxd) maxd = g->deg[i];
+    double *a = (double *)malloc(sizeof(double) * (size_t)(maxd + 1));
+    double *q = (double *)malloc(sizeof(double) * (size_t)(maxd + 1));
+    int *sm = (int *)malloc(sizeof(int) * (size_t)(maxd + 1));
+    int *lg = (int *)malloc(sizeof(int) * (size_t)(maxd + 1));
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t o = g->row_start[i];
+        int d = 0;
+        double lam = 0.0;
+        for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+            if (col[p] != i && val[p] > 0.0) {
+                g->edge_col[o + d] = col[p];
+                a[d] = val[p];
+                lam += val[p];
+                ++d;
+            }
+        }
+        if (g->weighted[i]) {
+            vose_row(d, a, lam, g->edge_col + o, g->alias_col + o, g->thresh + o, q, sm, lg);
+        } else {
+            for (int k = 0; k < d; ++k) {
+                g->alias_col[o + k] = g->edge_col[o + k];
+                g->thresh[o + k] = 0xFFFFFFFFu;
+            }
+        }
+    }
+    free(a); free(q); free(sm); free(lg);
+    return O_OK;
+}
+
+/* Number of edges kept by oracle_prep (to size its output arrays). */
+int64_t oracle_count_offdiag(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val)
+{
+    int64_t c = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
+            if (col[p] != i && val[p] > 0.0) ++c;
+    return c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One backward path (Algorithm 1 / Theorem 1, continuous-path reading).     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t end;
+    uint32_t njumps;
+    uint64_t hash;   /* FNV-1a 64 over the visited indices, start included */
+    double logw;     /* log of the multiplicative functional */
+} path_out;
+
+#define FNV_OFFSET 14695981039346656037ull
+#define FNV_PRIME 1099511628211ull
+
+static int32_t pick_next(const oracle_graph *g, int32_t j, uint32_t w2, uint32_t w3)
+{
+    int64_t o = g->row_start[j];
+    uint32_t slot = (uint32_t)(((uint64_t)w2 * (uint64_t)(uint32_t)g->deg[j]) >> 32);
+    if (g->weighted[j] && !(w3 < g->thresh[o + slot])) return g->alias_col[o + slot];
+    return g->edge_col[o + slot];
+}
+
+/* Grid points m*dt (m = 0..N-1) with m*dt <= rho, counted in the path's
+ * remaining-time coordinate rho = t - time.  Single precision. */
+static int grid_count_f32(float rho, float invdt, int N)
+{
+    if (rho < 0.0f) return 0;
+    float f = floorf(rho * invdt);
+    int c = (int)f + 1;
+    return c < N ? c : N;
+}
+
+static int grid_count_f64(double rho, double invdt, int N)
+{
+    if (rho < 0.0) return 0;
+    double f = floor(rho * invdt);
+    int c = (int)f + 1;
+    return c < N ? c : N;
+}
+
+static path_out path_f32(const oracle_graph *g, int32_t i, uint32_t stream, double t, int mode, int N, uint64_t seed, uint64_t p)
+{
+    path_out o;
+    int32_t j = i;
+    float r = (float)t;
+    float acc = 0.0f;
+    float dt = (float)(t / (double)N);
+    float invdt = (float)((double)N / t);
+    uint32_t k = 0;
+    uint64_t h = (FNV_OFFSET ^ (uint64_t)(uint32_t)i) * FNV_PRIME;
+    for (;;) {
+        float dl = g->delta32[j];
+        if (g->deg[j] == 0) {
+            if (mode == O_EXACT) acc = fmaf(dl, r, acc);
+            else acc = fmaf(dl, (float)grid_count_f32(r, invdt, N), acc);
+            break;
+        }
+        uint32_t w[4];
+        draw(seed, k, stream, p, w);
+        float S = -oracle_logf(unif_f32(w[0])) * g->inv_rate32[j];
+        if (S >= r) {
+            if (mode == O_EXACT) acc = fmaf(dl, r, acc);
+            else acc = fmaf(dl, (float)grid_count_f32(r, invdt, N), acc);
+            break;
+        }
+        float rn = r - S;
+        if (mode == O_EXACT) acc = fmaf(dl, S, acc);
+        else acc = fmaf(dl, (float)(grid_count_f32(r, invdt, N) - grid_count_f32(rn, invdt, N)), acc);
+        r = rn;
+        j = pick_next(g, j, w[2], w[3]);
+        h = (h ^ (uint64_t)(uint32_t)j) * FNV_PRIME;
+        ++k;
+    }
+    float logw;
+    if (mode == O_EXACT) {
+        logw = acc;
+    } else if (mode == O_LIE) {
+        logw = acc * dt;
+    } else {
+        float a = fmaf(0.5f, g->delta32[i], acc);
+        a = fmaf(-0.5f, g->delta32[j], a);
+        logw = a * dt;
+    }
+    o.end = j; o.njumps = k; o.hash = h; o.logw = (double)logw;
+    return o;
+}
+
+static path_out path_f64(const oracle_graph *g, int32_t i, uint32_t stream, double t, int mode, int N, uint64_t seed, uint64_t p)
+{
+    path_out o;
+    int32_t j = i;
+    double r = t;
+    double acc = 0.0;
+    double dt = t / (double)N;
+    double invdt = (double)N / t;
+    uint32_t k = 0;
+    uint64_t h = (FNV_OFFSET ^ (uint64_t)(uint32_t)i) * FNV_PRIME;
+    for (;;) {
+        double dl = g->delta64[j];
+        if (g->deg[j] == 0) {
+            if (mode == O_EXACT) acc = fma(dl, r, acc);
+            else acc = fma(dl, (double)grid_count_f64(r, invdt, N), acc);
+            break;
+        }
+        uint32_t w[4];
+        draw(seed, k, stream, p, w);
+        double S = -oracle_log(unif_f64(w[0], w[1])) * g->inv_rate64[j];
+        if (S >= r) {
+            if (mode == O_EXACT) acc = fma(dl, r, acc);
+            else acc = fma(dl, (double)grid_count_f64(r, invdt, N), acc);
+            break;
+        }
+        double rn = r - S;
+        if (mode == O_EXACT) acc = fma(dl, S, acc);
+        else acc = fma(dl, (double)(grid_count_f64(r, invdt, N) - grid_count_f64(rn, invdt, N)), acc);
+        r = rn;
+        j = pick_next(g, j, w[2], w[3]);
+        h = (h ^ (uint64_t)(uint32_t)j) * FNV_PRIME;
+        ++k;
+    }
+    double logw;
+    if (mode == O_EXACT) {
+        logw = acc;
+    } else if (mode == O_LIE) {
+        logw = acc * dt;
+    } else {
+        double a = fma(0.5, g->delta64[i], acc);
+        a = fma(-0.5, g->delta64[j], a);
+        logw = a * dt;
+    }
+    o.end = j; o.njumps = k; o.hash = h; o.logw = logw;
+    return o;
+}
+
+static path_out one_path_stream(const oracle_graph *g, int32_t i, uint32_t stream, double t, int mode,
+                                int N, int prec, uint64_t seed, uint64_t p)
+{
+    if (t == 0.0) {  /* exp(0 A) v = v: no holding time, no weight */
+        path_out o = {i, 0, (FNV_OFFSET ^ (uint64_t)(uint32_t)i) * FNV_PRIME, 0.0};
+        return o;
+    }
+    return prec == 0 ? path_f32(g, i, stream, t, mode, N, seed, p) : path_f64(g, i, stream, t, mode, N, seed, p);
+}
+
+/* Backward paths of entry i draw from stream word i. */
+static path_out one_path(const oracle_graph *g, int32_t i, double t, int mode, int N, int prec,
+                         uint64_t seed, uint64_t p)
+{
+    return one_path_stream(g, i, (uint32_t)i, t, mode, N, prec, seed, p);
+}
+
+/* Per-path trace for parity checks: paths first_path .. first_path+count-1 of entry i. */
+void oracle_trace(const oracle_graph *g, double t, int mode, int N, int prec, int32_t entry,
+                  uint64_t seed, uint64_t first_path, uint32_t count,
+                  int32_t *end, uint32_t *njumps, uint64_t *hash, double *logw)
+{
+    for (uint32_t q = 0; q < count; ++q) {
+        path_out o = one_path(g, entry, t, mode, N, prec, seed, first_path + q);
+        end[q] = o.end; njumps[q] = o.njumps; hash[q] = o.hash; logw[q] = o.logw;
+    }
+}
+
+/* Sample mean of W v_{X_t} over paths path_offset .. path_offset+M-1 for each
+ * requested entry (Algorithm 1 with the mean divided by M), with the standard
+ * error sqrt(s^2 / M) where s^2 is the unbiased sample variance (Welford's
+ * recurrence).  The mean itself is the plain sequential FP64 sum over paths
+ * divided by M.  Entries run in parallel (OpenMP); each entry is sequential. */
+int oracle_estimate(const oracle_graph *g, const double *v, double t, int mode, int N, int prec,
+                    uint64_t M, const int32_t *entries, int64_t n_entries, uint64_t seed,
+                    uint64_t path_offset, double *mean, double *sem, uint64_t *jumps_out)
+{
+    uint64_t jumps = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : jumps)
+    for (int64_t q = 0; q < n_entries; ++q) {
+        int32_t i = entries ? entries[q] : (int32_t)q;
+        double sum = 0.0, wm = 0.0, wss = 0.0;
+        for (uint64_t p = 0; p < M; ++p) {
+            path_out o = one_path(g, i, t, mode, N, prec, seed, path_offset + p);
+            double w = exp(o.logw) * v[o.end];
+            sum += w;
+            double d = w - wm;
+            wm += d / (double)(p + 1);
+            wss += d * (w - wm);
+            jumps += o.njumps;
+        }
+        mean[q] = M ? sum / (double)M : 0.0;
+        sem[q] = M > 1 ? sqrt(wss / (double)(M - 1) / (double)M) : 0.0;
+    }
+    if (jumps_out) *jumps_out = jumps;
+    return O_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward form (Lemma 2, Theorem 2; Algorithm 2), on the graph of B = A^T:  */
+/* start j ~ v/V from a canonical Vose table over v, walk B's rows with B's  */
+/* potential, deposit V W at the end state.  The start draw uses counter     */
+/* {0, 0xFFFFFFFF, path}; walk events use {k, 0xFFFFFFFE, path}.             */
+/* ------------------------------------------------------------------------ */
+int oracle_start_table(int64_t n, const double *v, int32_t *alias_out, uint32_t *thresh_out, double *vsum_out)
+{
+    double V = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!(v[i] >= 0.0) || !isfinite(v[i])) return O_E_INVALID;
+        V += v[i];
+    }
+    *vsum_out = V;
+    if (!(V > 0.0)) return O_E_INVALID;
+    int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    double *q = (double *)malloc(sizeof(double) * (size_t)n);
+    int *sm = (int *)malloc(sizeof(int) * (size_t)n);
+    int *lg = (int *)malloc(sizeof(int) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) ids[i] = (int32_t)i;
+    vose_row((int)n, v, V, ids, alias_out, thresh_out, q, sm, lg);
+    free(ids); free(q); free(sm); free(lg);
+    return O_OK;
+}
+
+static int32_t forward_start(int64_t n, const int32_t *start_alias, const uint32_t *start_thresh,
+                             uint64_t seed, uint64_t path)
+{
+    uint32_t w[4];
+    draw(seed, 0u, 0xFFFFFFFFu, path, w);
+    uint32_t slot = (uint32_t)(((uint64_t)w[2] * (uint64_t)n) >> 32);
+    return (w[3] < start_thresh[slot]) ? (int32_t)slot : start_alias[slot];
+}
+
+/* Per-state sums over paths path_offset .. path_offset+M-1 of Y = V W 1{X_t = i}
+ * (sum1) and Y^2 (sum2).  Then x_i = sum1_i / M. */
+void oracle_forward(const oracle_graph *g, int64_t n, const int32_t *start_alias, const uint32_t *start_thresh,
+                    double V, double t, int mode, int N, int prec, uint64_t M, uint64_t seed,
+                    uint64_t path_offset, double *sum1, double *sum2, uint64_t *jumps_out)
+{
+    uint64_t jumps = 0;
+    for (uint64_t p = 0; p < M; ++p) {
+        uint64_t path = path_offset + p;
+        int32_t j0 = forward_start(n, start_alias, start_thresh, seed, path);
+        path_out o = one_path_stream(g, j0, 0xFFFFFFFEu, t, mode, N, prec, seed, path);
+        double w = V * exp(o.logw);
+        sum1[o.end] += w;
+        sum2[o.end] += w * w;
+        jumps += o.njumps;
+    }
+    if (jumps_out) *jumps_out = jumps;
+}
+
+void oracle_forward_trace(const oracle_graph *g, int64_t n, const int32_t *start_alias, const uint32_t *start_thresh,
+                          double t, int mode, int N, int prec, uint64_t seed, uint64_t first_path, uint32_t count,
+                          int32_t *start, int32_t *end, uint32_t *njumps, uint64_t *hash, double *logw)
+{
+    for (uint32_t q = 0; q < count; ++q) {
+        uint64_t path = first_path + q;
+        int32_t j0 = forward_start(n, start_alias, start_thresh, seed, path);
+        path_out o = one_path_stream(g, j0, 0xFFFFFFFEu, t, mode, N, prec, seed, path);
+        start[q] = j0; end[q] = o.end; njumps[q] = o.njumps; hash[q] = o.hash; logw[q] = o.logw;
+    }
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
