@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Benchmark of the Monte Carlo exp(tA)v hot path on one GB300 (or N, weak scaling).
+
+Workload (network total communicability, Sec. 6 of the paper): A is the
+symmetric 0/1 adjacency of an Erdos-Renyi graph with n = 10^6 nodes and mean
+degree 10 (seed 0, CSR, int32 columns); beta = 1/lambda_max by power
+iteration; v = 1; the full vector exp(beta A) 1 is estimated with 1000
+backward paths per node (10^9 paths per step), FP32 path weights with
+per-path log scaling, FP64 accumulation.
+
+One step is the whole hot path over that input, with the CSR already
+resident in HBM: plan creation (validation, rates/potentials, jump tables),
+power iteration for lambda_max, the walkers and the per-entry reduction.
+Metric: walker paths per second (whole job).  Between timed steps a 512 MiB
+buffer is written to flush L2 (outside the timed events).
+
+Under torchrun each rank runs the same step on its own GPU with a disjoint
+path range (path_offset = rank * paths), i.e. weak scaling with no data-path
+collective; rank 0 prints the JSON line.
+
+`--impl reference` times the CPU oracle (oracle/walker.c, OpenMP over
+entries) on the host cores, each step a bounded sample of entries of the same
+workload, and prints the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_NODES = 10 ** 6
+MEAN_DEGREE = 10
+PATHS = 1000
+SEED = 0
+BYTES_PER_JUMP = 64  # one 32-B sector for the column, one for the node record
+METRIC = "walker paths/s"
+WORKLOAD = "erdos_renyi_total_communicability"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mcx", choices=["mcx", "reference"])
+    ap.add_argument("--n", type=int, default=N_NODES)
+    ap.add_argument("--paths", type=int, default=PATHS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle CPU time for cpu_baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def _config(args, world):
+    return {"workload": WORKLOAD, "n": args.n, "mean_degree": MEAN_DEGREE, "paths_per_entry": args.paths,
+            "entries": "all", "beta": "1/lambda_max (power iteration, tol 1e-10)", "v": "ones",
+            "functional": "exact", "precision": "fp32 paths, fp64 accumulation", "graph_seed": SEED,
+            "l2": "512 MiB buffer written between timed steps", "parallelism": f"dp{world} (disjoint path ranges)"}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.th.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def _oracle_rate(csr, t, paths, target_s, seed=SEED):
+    """Time the CPU oracle walker on a bounded sample of entries; returns (paths/s, sample, threads, seconds)."""
+    import numpy as np
+
+    from oracle import walker as OW
+
+    g = OW.Graph(csr)
+    v = np.ones(csr.n)
+    k = min(csr.n, 2000)
+    ent = np.arange(k, dtype=np.int32)
+    t0 = time.perf_counter()
+    g.estimate(v, t, paths, entries=ent, seed=seed)
+    dt = time.perf_counter() - t0
+    k2 = int(min(csr.n, max(k, k * target_s / max(dt, 1e-3))))
+    ent = np.arange(k2, dtype=np.int32)
+    t0 = time.perf_counter()
+    g.estimate(v, t, paths, entries=ent, seed=seed)
+    dt = time.perf_counter() - t0
+    return k2 * paths / dt, f"entries 0..{k2 - 1} x {paths} paths ({k2 * paths:.3g} paths)", OW.num_threads(), dt
+
+
+def _beta_cpu(csr):
+    from oracle import dense as OD
+
+    return 1.0 / OD.power_iteration(csr.to_scipy(), iters=1000, tol=1e-10)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+
+    import workloads as W
+    from oracle import walker as OW
+
+    csr = W.erdos_renyi(args.n, MEAN_DEGREE, SEED)
+    t = _beta_cpu(csr)
+    g = OW.Graph(csr)
+    v = np.ones(csr.n)
+    # size one step to ~ (few minutes / steps) of CPU time
+    k = min(csr.n, 2000)
+    t0 = time.perf_counter()
+    g.estimate(v, t, args.paths, entries=np.arange(k, dtype=np.int32), seed=SEED)
+    dt = time.perf_counter() - t0
+    per_step_s = min(20.0, 120.0 / max(1, args.steps + args.warmup))
+    k = int(min(csr.n, max(k, k * per_step_s / max(dt, 1e-3))))
+    ent = np.arange(k, dtype=np.int32)
+    for _ in range(args.warmup):
+        g.estimate(v, t, args.paths, entries=ent[: min(k, 2000)], seed=SEED)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        g.estimate(v, t, args.paths, entries=ent, seed=SEED + s)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = k * args.paths * args.steps / total
+    sample = f"entries 0..{k - 1} x {args.paths} paths per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 paths, f64 sums",
+            "data": "synthetic", "config": _config(args, 1),
+            "cpu_baseline": {"value": value, "unit": "paths/s", "cores": OW.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "paths/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+
+    from paper_1904_12759_gb300 import build as B
+
+    B.build()
+    import paper_1904_12759_gb300 as P
+    import workloads as W
+
+    csr = W.erdos_renyi(args.n, MEAN_DEGREE, SEED)
+    n, nnz = csr.n, csr.nnz
+    dev = torch.device("cuda", local)
+    rp = torch.as_tensor(csr.row_ptr).to(dev)
+    col = torch.as_tensor(csr.col).to(dev)
+    val = torch.as_tensor(csr.val).to(dev)
+    v = torch.ones(n, dtype=torch.float64, device=dev)
+    work = torch.empty(2 * n + 4096, dtype=torch.float64, device=dev)
+    mean = torch.empty(n, dtype=torch.float64, device=dev)
+    sem = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    M = args.paths
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def step(seed, timing=None):
+        e = [ev() for _ in range(4)] if timing is not None else None
+        if e:
+            e[0].record(stream)
+        plan = P.Plan(rp, col, val)
+        if e:
+            e[1].record(stream)
+        lam, iters = P.power_iteration(rp, col, val, max_iters=1000, tol=1e-10, work=work)
+        if e:
+            e[2].record(stream)
+        plan.estimate(v, 1.0 / lam, M, seed=seed, path_offset=rank * M, out=(mean, sem))
+        if e:
+            e[3].record(stream)
+        st = plan.sync()
+        plan.close()
+        if timing is not None:
+            timing.append((e, st, lam, iters))
+        return lam
+
+    for w in range(args.warmup):
+        step(SEED + 1000 + w)
+    torch.cuda.synchronize()
+
+    step_ms, phases, stats = [], [], []
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.zero_()
+            s0, s1 = ev(), ev()
+            rec = []
+            s0.record(stream)
+            step(SEED + k, rec)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            step_ms.append(s0.elapsed_time(s1))
+            e, st, lam, iters = rec[0]
+            phases.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[2].elapsed_time(e[3])))
+            stats.append((st, lam, iters))
+        torch.cuda.synchronize()
+        barrier()
+    total_ms = sum(step_ms)
+    if world > 1:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    paths_per_step = n * M
+    value = world * paths_per_step * args.steps / (total_ms / 1e3)
+
+    prep_ms = statistics.mean(p[0] for p in phases)
+    power_ms = statistics.mean(p[1] for p in phases)
+    walk_ms = statistics.mean(p[2] for p in phases)
+    jumps = statistics.mean(s[0]["jumps"] for s in stats)
+    lam, iters = stats[-1][1], stats[-1][2]
+    # sanity of the estimate: exp(beta A) 1 >= 1 entrywise, and mean equals the oracle-free bound checks
+    m_host = mean.cpu().numpy()
+    assert np.all(np.isfinite(m_host)) and m_host.min() >= 1.0 - 1e-6
+
+    walk_bytes = jumps * BYTES_PER_JUMP
+    achieved = walk_bytes / (walk_ms / 1e3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    # ---- end to end: host (pinned) CSR and v in, host estimate out, through the one-call API ----
+    e2e = None
+    if not args.no_e2e:
+        pin = dict(pin_memory=True)
+        h_rp = torch.as_tensor(csr.row_ptr).pin_memory()
+        h_col = torch.as_tensor(csr.col).pin_memory()
+        h_val = torch.as_tensor(csr.val).pin_memory()
+        h_v = torch.ones(n, dtype=torch.float64, **pin)
+        P.expm_multiply(h_rp, h_col, h_val, h_v, paths=M, seed=SEED)  # warm
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            hm, hs, _ = P.expm_multiply(h_rp, h_col, h_val, h_v, paths=M, seed=SEED + k)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        bi = 8 * (n + 1) + 4 * nnz + 8 * nnz + 8 * n
+        bo = 16 * n
+        e2e = {"value": world * paths_per_step * args.steps / e2e_s, "unit": "paths/s", "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bo}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        import scipy  # noqa: F401
+
+        rate, sample, cores, secs = _oracle_rate(csr, 1.0 / lam, M, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "paths/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "seconds": round(secs, 2)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(args, world),
+        "phases_ms": {"plan_create": round(prep_ms, 3), "power_iteration": round(power_ms, 3),
+                      "walk_and_reduce": round(walk_ms, 3), "power_iters": iters},
+        "walker": {"paths": paths_per_step, "jumps_per_path": jumps / paths_per_step,
+                   "jumps_per_s": jumps / (walk_ms / 1e3), "lambda_max": lam},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
+                     "kernel": "k_walk (estimate launch)", "bytes_per_jump": BYTES_PER_JUMP},
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": None, "clocks": clk.summary(),
+    }
+    # per step: prep (rows, scan tiles, scan sums, scan add, fill) + power iteration (init, then
+    # spmv/finish/scale in batches of 16) + estimate (pack v, walk); L2 flushes are torch's, not counted
+    batches = -(-iters // 16)
+    line["gpu_launches"] = args.steps * (5 + 1 + 3 * 16 * batches + 2)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

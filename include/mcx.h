@@ -1,0 +1,221 @@
+/*
+ * mcx.h — C-ABI of the GB300 Monte Carlo exp(tA)v library.
+ *
+ * The library estimates x = exp(tA) v (the paper writes beta for t, Sec. 2)
+ * for a sparse A in CSR form by simulating independent continuous-time
+ * Markov-chain walkers over the indices of A (Sec. 3, Eq. paths) and
+ * averaging the multiplicative functional of Theorem 1 (one entry, or any set
+ * of entries: Algorithm 1) or Theorem 2 (the full vector from walkers started
+ * at j ~ v/V: Algorithm 2).
+ *
+ * Decomposition (Sec. 2, A = D - L).  For row i:
+ *   lambda_i = sum_{j != i} a_ij     the jump rate (L_ii; needs a_ij >= 0, j != i)
+ *   delta_i  = sum_j a_ij            the potential (D_ii = a_ii + lambda_i)
+ *   k_ij     = a_ij / lambda_i       the jump probabilities of Eq. paths
+ * The paper's d_i denotes both lambda_i and delta_i; they coincide for 0/1
+ * adjacency matrices.  A need not be symmetric for the backward calls; the
+ * forward call walks the rows of the matrix the plan was built from, which
+ * must be A^T (A itself when A is symmetric, as Theorem 2 assumes).
+ *
+ * Conventions shared by every call:
+ *   - Pointers are device pointers unless a flag says otherwise; the caller
+ *     owns every array it passes and allocates every output.  A plan owns the
+ *     device buffers it creates and frees them in mcx_plan_destroy.
+ *   - Calls are asynchronous on the CUDA stream passed as `stream`
+ *     (a cudaStream_t; NULL means the legacy default stream).  Argument
+ *     errors are returned at call time; errors found on the device (result
+ *     overflow) are latched in the plan and returned by mcx_sync.
+ *   - Nothing traps on the device and no C++ exception crosses this ABI.
+ *   - Indices are 0-based; column indices are int32, row pointers int64.
+ *   - Results are a deterministic function of (inputs, seed, path_offset)
+ *     and of the launch configuration the library picks for the sizes given.
+ *
+ * Draw schedule (fixed, so that an independent implementation reproduces
+ * every path bit for bit): one Philox4x32-10 call (Salmon et al., SC'11) per
+ * walker event k = 0, 1, ..., key = {seed lo32, seed hi32}, counter =
+ * {k, i, path lo32, path hi32} for a backward path of entry i.  The holding
+ * time in state j is S = -ln(u) * inv_rate_j with u = (2^24 - (w0 >> 8)) 2^-24
+ * (FP32) or u = (2^53 - ((w0 << 21) | (w1 >> 11))) 2^-53 (FP64), the
+ * logarithm being the library's own (range reduction to [1/sqrt2, sqrt2] and
+ * the artanh series, fused multiply-adds in a fixed order).  If S >= r (the
+ * remaining time) the path stops; otherwise the slot (w2 * deg_j) >> 32 of
+ * row j is taken, and for an alias-table row its own column is kept iff
+ * w3 < threshold, else its alias column.
+ */
+#ifndef MCX_H
+#define MCX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MCX_OK = 0,
+    MCX_E_INVALID = -1,      /* bad argument or malformed CSR (unsorted/duplicate/out-of-range columns) */
+    MCX_E_NEG_OFFDIAG = -2,  /* a_ij < 0 for some j != i: -L is then not a generator (Sec. 2) */
+    MCX_E_NONFINITE = -3,    /* NaN or Inf in A or v */
+    MCX_E_NEG_V = -4,        /* forward form needs v >= 0 with a positive sum (Lemma 2) */
+    MCX_E_CUDA = -5,         /* a CUDA runtime call failed */
+    MCX_E_OOM = -6,          /* device allocation failed */
+    MCX_E_TIMEOUT = -7,      /* a bounded device wait gave up */
+    MCX_E_UNSUPPORTED = -8,  /* valid request outside what this build implements */
+    MCX_E_OVERFLOW = -9      /* an estimate or its standard error overflowed FP64 */
+} mcx_status;
+
+/* The multiplicative functional carried along each path.
+ *   MCX_EXACT : logW = integral_0^t delta(X_s) ds — the limit dt -> 0; unbiased for exp(tA)v.
+ *   MCX_STRANG: logW = dt [delta(X_0)/2 + sum_{k=1}^{N-1} delta(X_{k dt}) + delta(X_t)/2];
+ *               unbiased for the Strang product (Eq. eq_general1, Theorem 1).
+ *   MCX_LIE   : logW = dt sum_{k=1}^{N} delta(X_{k dt}); unbiased for the Lie product (Eq. deff).
+ * with dt = t/N, N = nsteps.  X is one continuous path in every mode, so the
+ * visited indices do not depend on the mode. */
+typedef enum { MCX_EXACT = 0, MCX_STRANG = 1, MCX_LIE = 2 } mcx_functional;
+
+/* MCX_FP32: holding times, remaining time and logW in FP32 (per-path log
+ *           scaling); weights accumulated with compensated FP32 sums per lane
+ *           and FP64 across lanes.  The production path.
+ * MCX_FP64: every per-path quantity in FP64.  The reference path version. */
+typedef enum { MCX_FP32 = 0, MCX_FP64 = 1 } mcx_precision;
+
+/* mcx_plan_create flags */
+#define MCX_PLAN_HOST_INPUT 0x1u /* row_ptr, col, val are host pointers (copied to the device) */
+
+typedef struct mcx_plan mcx_plan;
+
+typedef struct {
+    int64_t n;               /* rows */
+    int64_t nnz;             /* stored entries of A */
+    int64_t nnz_off;         /* kept off-diagonal entries (a_ij > 0, j != i) */
+    int64_t weighted_rows;   /* rows whose kept entries are not all equal (alias-table rows) */
+    int32_t max_deg;         /* max kept entries in a row */
+    int32_t reserved;
+    int64_t device_bytes;    /* device memory the plan holds */
+} mcx_plan_info;
+
+typedef struct {
+    uint64_t paths;          /* walker paths simulated by mcx_estimate since the last mcx_sync */
+    uint64_t jumps;          /* jumps taken by those paths */
+    uint32_t status_bits;    /* latched device status (bit 0: overflow, bit 4: bad entry) */
+    uint32_t reserved;
+} mcx_stats;
+
+/*
+ * Build a plan for A (Sec. 2: A = D - L) from CSR arrays.
+ *   n        rows (= columns), 0 <= n < 2^31
+ *   nnz      stored entries, row_ptr[n] == nnz
+ *   row_ptr  int64 [n+1], non-decreasing, row_ptr[0] = 0
+ *   col      int32 [nnz], strictly increasing within each row, in [0, n)
+ *   val      float64 [nnz], finite, >= 0 off the diagonal; each row's rate
+ *            lambda_i and potential delta_i must be finite with a nonzero
+ *            FP32 reciprocal rate (else MCX_E_NONFINITE)
+ *   flags    MCX_PLAN_HOST_INPUT if the three arrays are host memory
+ *   stream   CUDA stream; the call synchronises it before returning so that
+ *            validation errors come back as its status
+ *   out      receives the plan (NULL on error)
+ * Entries with a_ij = 0 off the diagonal are dropped.  Each row keeps its
+ * off-diagonal columns in CSR order plus, if its values differ, a Vose alias
+ * table (built in FP64, stored as int32 alias column + uint32 threshold) so
+ * that a jump costs O(1) (Sec. 4 notes the uniform-row O(1) case; the table
+ * extends it to weighted rows).
+ * Errors: MCX_E_INVALID, MCX_E_NEG_OFFDIAG, MCX_E_NONFINITE, MCX_E_OOM, MCX_E_CUDA.
+ */
+mcx_status mcx_plan_create(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col,
+                           const double *val, uint32_t flags, void *stream, mcx_plan **out);
+
+/* Fill *info (host pointer) with the plan's sizes.  Errors: MCX_E_INVALID. */
+mcx_status mcx_plan_get_info(const mcx_plan *plan, mcx_plan_info *info);
+
+/*
+ * Backward estimate (Theorem 1, Algorithm 1) of x_i = (exp(tA) v)_i for each
+ * requested entry: the sample mean of W v_{X_t} over paths_per_entry
+ * independent paths started at i, and its standard error.
+ *   v                float64 [n]; any sign (Theorem 1 does not need v >= 0)
+ *   t                horizon, t >= 0 and finite; t = 0 returns v exactly
+ *   functional       mcx_functional; nsteps = N >= 1 for STRANG/LIE (ignored for EXACT)
+ *   paths_per_entry  M >= 1 (M >= 2 for a standard error)
+ *   entries          int32 [n_entries] row indices in [0, n), or NULL for all
+ *                    rows (then n_entries must equal n); an index outside
+ *                    [0, n) yields NaN outputs and MCX_E_INVALID at mcx_sync
+ *   seed, path_offset  paths path_offset .. path_offset+M-1 of each entry are
+ *                    simulated, so disjoint offsets give independent samples
+ *                    that can be merged (checkpoint / sharding)
+ *   precision        mcx_precision
+ *   mean             float64 [n_entries] output
+ *   sem              float64 [n_entries] output, or NULL: sqrt(s^2/M) with s^2
+ *                    the unbiased sample variance of W v_{X_t}
+ * The plan's copy of v is overwritten, so two estimates with different v on
+ * one plan must not overlap in time (use one stream per plan).
+ * Errors: MCX_E_INVALID, MCX_E_CUDA, MCX_E_OOM.
+ */
+mcx_status mcx_estimate(mcx_plan *plan, const double *v, double t, int functional, int32_t nsteps,
+                        uint64_t paths_per_entry, const int32_t *entries, int64_t n_entries,
+                        uint64_t seed, uint64_t path_offset, int precision, double *mean, double *sem,
+                        void *stream);
+
+/*
+ * Per-path record of `count` backward paths of one entry (for parity checks
+ * against an independent implementation of the same draw schedule):
+ *   end     int32  [count]  X_t
+ *   njumps  uint32 [count]  number of jumps
+ *   hash    uint64 [count]  FNV-1a 64 over the visited indices, start included
+ *   logw    float64[count]  log of the multiplicative functional (FP32 paths
+ *                           are widened exactly)
+ * Paths first_path .. first_path+count-1 of `entry` with the same arguments as
+ * mcx_estimate.  Errors: MCX_E_INVALID, MCX_E_CUDA.
+ */
+mcx_status mcx_trace_paths(mcx_plan *plan, double t, int functional, int32_t nsteps, int32_t entry,
+                           uint64_t seed, uint64_t first_path, uint32_t count, int precision,
+                           int32_t *end, uint32_t *njumps, uint64_t *hash, double *logw, void *stream);
+
+/*
+ * Largest eigenvalue of a symmetric A >= 0 by the power method (Sec. 6 picks
+ * beta = 1/lambda_max): x <- A x / ||A x||_2 from x = 1/sqrt(n), Rayleigh
+ * quotient x^T A x, stopped when two successive quotients agree to `tol`
+ * relative or after max_iters.  Works on the caller's CSR (device pointers,
+ * same layout as mcx_plan_create, which must be valid: this call does not
+ * re-validate it) with `work` a caller-owned device buffer of at least
+ * 2n+4096 float64.  *lambda_out and *iters_out (either may be NULL)
+ * are host outputs; the call synchronises the stream.
+ * Errors: MCX_E_INVALID, MCX_E_CUDA.
+ */
+mcx_status mcx_power_iteration(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                               int32_t max_iters, double tol, double *work, double *lambda_out,
+                               int32_t *iters_out, void *stream);
+
+/*
+ * Copy the plan's preparation results (Sec. 2 decomposition, Sec. 4 jump
+ * tables) into caller-owned device arrays, for parity checks against an
+ * independent preparation.  Per row [n]: deg (int32), row_start (int64),
+ * weighted (uint8, 1 for alias-table rows), inv_rate32 = (float)(1/lambda),
+ * delta32 = (float)delta, inv_rate64, delta64 (float64).  Per kept entry
+ * [nnz_off] (mcx_plan_info): edge_col (int32, CSR order), alias_col (int32),
+ * thresh (uint32); for uniform rows alias_col = edge_col and thresh =
+ * 0xFFFFFFFF.  Any output may be NULL.  Errors: MCX_E_INVALID, MCX_E_CUDA.
+ */
+mcx_status mcx_plan_export(const mcx_plan *plan, int32_t *deg, int64_t *row_start, uint8_t *weighted,
+                           float *inv_rate32, float *delta32, double *inv_rate64, double *delta64,
+                           int32_t *edge_col, int32_t *alias_col, uint32_t *thresh, void *stream);
+
+/* Synchronise `stream`, return and clear the plan's latched device status and
+ * counters.  stats (host pointer) may be NULL.  Errors: MCX_E_INVALID (an
+ * estimate was given an entry outside [0, n); its outputs are NaN),
+ * MCX_E_OVERFLOW (a result overflowed FP64, or a path reached the cap of 2^30
+ * events), MCX_E_CUDA. */
+mcx_status mcx_sync(mcx_plan *plan, void *stream, mcx_stats *stats);
+
+/* Free the plan's device memory (synchronises the device first).  NULL is accepted. */
+void mcx_plan_destroy(mcx_plan *plan);
+
+/* Static string for a status code. */
+const char *mcx_status_string(int status);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int mcx_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCX_H */

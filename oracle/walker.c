@@ -224,6 +224,9 @@ int oracle_prep(int64_t n, const int64_t *row_ptr, const int32_t *col, const dou
                 ++d;
             }
         }
+        if (!isfinite(lam) || !isfinite(diag + lam) || !isfinite((float)(diag + lam)) ||
+            (d > 0 && (float)(1.0 / lam) == 0.0f))
+            return O_E_NONFINITE; /* rates/potentials must be finite with a nonzero FP32 reciprocal rate */
         g->deg[i] = d;
         g->row_start[i] = off;
         g->weighted[i] = (uint8_t)(d > 1 && !uniform);

@@ -1,0 +1,21 @@
+"""GB300-native Monte Carlo estimator of x = exp(tA) v (Acebron, arXiv 1904.12759).
+
+Continuous-time Markov-chain walkers over the indices of a sparse A (Sec. 3)
+carry the multiplicative functional of Theorems 1-2; the CUDA library behind
+include/mcx.h runs preparation, walkers and reductions on the GPU.  This
+package is the thin Python binding (ctypes) used by the tests and benchmark.
+"""
+from . import _lib
+from ._lib import EXPORTS, MCXError, load
+
+__all__ = ["EXPORTS", "MCXError", "load", "Plan", "power_iteration", "expm_multiply"]
+
+
+def __getattr__(name):
+    # the torch-facing API is imported lazily so that loading the C library
+    # (and checking its exports) does not require a GPU
+    if name in ("Plan", "power_iteration", "expm_multiply"):
+        from . import api
+
+        return getattr(api, name)
+    raise AttributeError(name)

@@ -1,0 +1,99 @@
+"""ctypes declarations of the C-ABI in include/mcx.h.
+
+Loading never falls back to anything: if the compiled library is missing the
+import fails with an error that says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmcx.so")
+
+# Every symbol declared in include/mcx.h; the library must export all of them.
+EXPORTS = (
+    "mcx_plan_create",
+    "mcx_plan_get_info",
+    "mcx_estimate",
+    "mcx_trace_paths",
+    "mcx_power_iteration",
+    "mcx_plan_export",
+    "mcx_sync",
+    "mcx_plan_destroy",
+    "mcx_status_string",
+    "mcx_version",
+)
+
+MCX_OK = 0
+STATUS_NAMES = {
+    0: "MCX_OK", -1: "MCX_E_INVALID", -2: "MCX_E_NEG_OFFDIAG", -3: "MCX_E_NONFINITE", -4: "MCX_E_NEG_V",
+    -5: "MCX_E_CUDA", -6: "MCX_E_OOM", -7: "MCX_E_TIMEOUT", -8: "MCX_E_UNSUPPORTED", -9: "MCX_E_OVERFLOW",
+}
+FUNCTIONALS = {"exact": 0, "strang": 1, "lie": 2}
+PRECISIONS = {"fp32": 0, "fp64": 1}
+PLAN_HOST_INPUT = 0x1
+
+
+class PlanInfo(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_off", C.c_int64), ("weighted_rows", C.c_int64),
+                ("max_deg", C.c_int32), ("reserved", C.c_int32), ("device_bytes", C.c_int64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("paths", C.c_uint64), ("jumps", C.c_uint64), ("status_bits", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
+class MCXError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)} ({status_string(code)})")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmcx.so (raises ImportError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"mcx CUDA library not built: {path} is missing "
+                          "(run `python -m paper_1904_12759_gb300.build` or __graft_entry__.build())")
+    L = C.CDLL(path)
+    vp, i64, u64, i32, u32, dbl, st = C.c_void_p, C.c_int64, C.c_uint64, C.c_int32, C.c_uint32, C.c_double, C.c_int
+    L.mcx_plan_create.argtypes = [i64, i64, vp, vp, vp, u32, vp, C.POINTER(vp)]
+    L.mcx_plan_create.restype = st
+    L.mcx_plan_get_info.argtypes = [vp, C.POINTER(PlanInfo)]
+    L.mcx_plan_get_info.restype = st
+    L.mcx_estimate.argtypes = [vp, vp, dbl, C.c_int, i32, u64, vp, i64, u64, u64, C.c_int, vp, vp, vp]
+    L.mcx_estimate.restype = st
+    L.mcx_trace_paths.argtypes = [vp, dbl, C.c_int, i32, i32, u64, u64, u32, C.c_int, vp, vp, vp, vp, vp]
+    L.mcx_trace_paths.restype = st
+    L.mcx_power_iteration.argtypes = [i64, vp, vp, vp, i32, dbl, vp, C.POINTER(dbl), C.POINTER(i32), vp]
+    L.mcx_power_iteration.restype = st
+    L.mcx_plan_export.argtypes = [vp] + [vp] * 10 + [vp]
+    L.mcx_plan_export.restype = st
+    L.mcx_sync.argtypes = [vp, vp, C.POINTER(Stats)]
+    L.mcx_sync.restype = st
+    L.mcx_plan_destroy.argtypes = [vp]
+    L.mcx_plan_destroy.restype = None
+    L.mcx_status_string.argtypes = [C.c_int]
+    L.mcx_status_string.restype = C.c_char_p
+    L.mcx_version.restype = C.c_int
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    try:
+        return load().mcx_status_string(int(code)).decode()
+    except ImportError:
+        return STATUS_NAMES.get(code, str(code))
+
+
+def check(code: int, where: str) -> None:
+    if code != MCX_OK:
+        raise MCXError(code, where)

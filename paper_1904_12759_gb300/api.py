@@ -1,0 +1,217 @@
+"""Python front end of the mcx library: argument marshalling only.
+
+Every step of the computation runs in the CUDA kernels behind the C-ABI;
+this module turns torch tensors into device pointers and the current torch
+stream into the stream argument.  PyTorch supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib
+from ._lib import FUNCTIONALS, PRECISIONS, check
+
+
+def _stream(stream=None) -> C.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev(t: torch.Tensor, dtype: torch.dtype, name: str) -> int:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _host(t: torch.Tensor, dtype: torch.dtype, name: str) -> int:
+    if t.dtype != dtype or t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous host tensor of {dtype}")
+    return t.data_ptr()
+
+
+class Plan:
+    """A prepared matrix A (Sec. 2: A = D - L) on the current CUDA device.
+
+    ``Plan(row_ptr, col, val)`` with int64 / int32 / float64 tensors in CSR
+    form, all on the GPU, or all on the host (they are then copied by the
+    library inside the call).
+    """
+
+    def __init__(self, row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, stream=None):
+        L = _lib.load()
+        n = row_ptr.numel() - 1
+        nnz = col.numel()
+        host = not row_ptr.is_cuda
+        conv = _host if host else _dev
+        p_rp = conv(row_ptr, torch.int64, "row_ptr")
+        p_col = conv(col, torch.int32, "col") if nnz else 0
+        p_val = conv(val, torch.float64, "val") if nnz else 0
+        out = C.c_void_p()
+        check(L.mcx_plan_create(n, nnz, C.c_void_p(p_rp), C.c_void_p(p_col), C.c_void_p(p_val),
+                                _lib.PLAN_HOST_INPUT if host else 0, _stream(stream), C.byref(out)),
+              "mcx_plan_create")
+        self._h = out
+        self.n = n
+        self.nnz = nnz
+
+    @classmethod
+    def from_csr(cls, csr, device="cuda", stream=None) -> "Plan":
+        """Build from any object with numpy row_ptr / col / val (e.g. workloads.CSR)."""
+        rp = torch.as_tensor(csr.row_ptr, dtype=torch.int64)
+        col = torch.as_tensor(csr.col, dtype=torch.int32)
+        val = torch.as_tensor(csr.val, dtype=torch.float64)
+        if device is not None and device != "cpu":
+            rp, col, val = rp.to(device), col.to(device), val.to(device)
+        return cls(rp, col, val, stream=stream)
+
+    def info(self) -> dict:
+        inf = _lib.PlanInfo()
+        check(_lib.load().mcx_plan_get_info(self._h, C.byref(inf)), "mcx_plan_get_info")
+        return {k: getattr(inf, k) for k, _ in inf._fields_ if k != "reserved"}
+
+    def estimate(self, v: torch.Tensor, t: float, paths: int, entries: torch.Tensor | None = None, seed: int = 0,
+                 path_offset: int = 0, mode: str = "exact", nsteps: int = 1, prec: str = "fp32",
+                 out: tuple | None = None, stream=None):
+        """Backward estimate of (exp(tA)v)_i for each entry (Theorem 1, Algorithm 1).
+
+        Returns (mean, sem) float64 CUDA tensors of length len(entries) (or n).
+        """
+        L = _lib.load()
+        p_v = _dev(v, torch.float64, "v")
+        if v.numel() != self.n:
+            raise ValueError("v must have n entries")
+        if entries is None:
+            ne, p_e = self.n, 0
+        else:
+            ne, p_e = entries.numel(), _dev(entries, torch.int32, "entries")
+        if out is None:
+            mean = torch.empty(ne, dtype=torch.float64, device=v.device)
+            sem = torch.empty(ne, dtype=torch.float64, device=v.device)
+        else:
+            mean, sem = out
+        p_sem = _dev(sem, torch.float64, "sem") if sem is not None else 0
+        check(L.mcx_estimate(self._h, C.c_void_p(p_v), float(t), FUNCTIONALS[mode], int(nsteps), int(paths),
+                             C.c_void_p(p_e), int(ne), int(seed), int(path_offset), PRECISIONS[prec],
+                             C.c_void_p(_dev(mean, torch.float64, "mean")), C.c_void_p(p_sem), _stream(stream)),
+              "mcx_estimate")
+        return mean, sem
+
+    def trace(self, t: float, entry: int, seed: int, first_path: int, count: int, mode: str = "exact",
+              nsteps: int = 1, prec: str = "fp32", device="cuda", stream=None) -> dict:
+        """Per-path end index, jump count, index hash and log-weight (for parity checks)."""
+        L = _lib.load()
+        out = {
+            "end": torch.empty(count, dtype=torch.int32, device=device),
+            "njumps": torch.empty(count, dtype=torch.int32, device=device),  # uint32 on the C side
+            "hash": torch.empty(count, dtype=torch.int64, device=device),  # uint64 on the C side
+            "logw": torch.empty(count, dtype=torch.float64, device=device),
+        }
+        check(L.mcx_trace_paths(self._h, float(t), FUNCTIONALS[mode], int(nsteps), int(entry), int(seed),
+                                int(first_path), int(count), PRECISIONS[prec],
+                                *[C.c_void_p(out[k].data_ptr()) for k in ("end", "njumps", "hash", "logw")],
+                                _stream(stream)), "mcx_trace_paths")
+        return out
+
+    def export(self, stream=None) -> dict:
+        """Copy the plan's preparation results (rates, potentials, jump tables) to new CUDA tensors."""
+        inf = self.info()
+        n, m = self.n, max(inf["nnz_off"], 1)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        out = {
+            "deg": torch.empty(n, dtype=torch.int32, device=dev),
+            "row_start": torch.empty(n, dtype=torch.int64, device=dev),
+            "weighted": torch.empty(n, dtype=torch.uint8, device=dev),
+            "inv_rate32": torch.empty(n, dtype=torch.float32, device=dev),
+            "delta32": torch.empty(n, dtype=torch.float32, device=dev),
+            "inv_rate64": torch.empty(n, dtype=torch.float64, device=dev),
+            "delta64": torch.empty(n, dtype=torch.float64, device=dev),
+            "edge_col": torch.empty(m, dtype=torch.int32, device=dev),
+            "alias_col": torch.empty(m, dtype=torch.int32, device=dev),
+            "thresh": torch.empty(m, dtype=torch.int32, device=dev),  # uint32 on the C side
+        }
+        keys = ("deg", "row_start", "weighted", "inv_rate32", "delta32", "inv_rate64", "delta64", "edge_col",
+                "alias_col", "thresh")
+        check(_lib.load().mcx_plan_export(self._h, *[C.c_void_p(out[k].data_ptr()) for k in keys], _stream(stream)),
+              "mcx_plan_export")
+        return out
+
+    def sync(self, stream=None) -> dict:
+        st = _lib.Stats()
+        check(_lib.load().mcx_sync(self._h, _stream(stream), C.byref(st)), "mcx_sync")
+        return {"paths": st.paths, "jumps": st.jumps, "status_bits": st.status_bits}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib.load().mcx_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover - interpreter shutdown ordering
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def power_iteration(row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, max_iters: int = 1000,
+                    tol: float = 1e-12, work: torch.Tensor | None = None, stream=None):
+    """lambda_max of a symmetric A >= 0 by the power method on the GPU (Sec. 6: beta = 1/lambda_max).
+
+    Returns (lambda, iterations)."""
+    n = row_ptr.numel() - 1
+    if work is None:
+        work = torch.empty(2 * n + 4096, dtype=torch.float64, device=row_ptr.device)
+    lam = C.c_double()
+    it = C.c_int32()
+    check(_lib.load().mcx_power_iteration(n, C.c_void_p(_dev(row_ptr, torch.int64, "row_ptr")),
+                                          C.c_void_p(_dev(col, torch.int32, "col")),
+                                          C.c_void_p(_dev(val, torch.float64, "val")), int(max_iters), float(tol),
+                                          C.c_void_p(_dev(work, torch.float64, "work")), C.byref(lam), C.byref(it),
+                                          _stream(stream)), "mcx_power_iteration")
+    return lam.value, it.value
+
+
+def expm_multiply(row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, v: torch.Tensor,
+                  t: float | None = None, beta_scale: float = 1.0, paths: int = 1000,
+                  entries: torch.Tensor | None = None, seed: int = 0, mode: str = "exact", nsteps: int = 1,
+                  prec: str = "fp32", power_tol: float = 1e-10, power_iters: int = 1000, stream=None):
+    """x ~ exp(tA) v in one call: plan, optional beta setup, backward estimate.
+
+    With t=None the horizon is beta_scale / lambda_max(A) (Sec. 6 uses
+    beta = 1/lambda_max), lambda_max by the GPU power method.  Host tensors
+    (pinned for asynchronous copies) are copied to the current device inside
+    the call and the results come back as host tensors; device tensors stay
+    on the device.  Returns (mean, sem, t).
+    """
+    host = not row_ptr.is_cuda
+    dev = torch.device("cuda", torch.cuda.current_device())
+    if host:
+        row_ptr, col, val, v = (x.to(dev, non_blocking=True) for x in (row_ptr, col, val, v))
+        if entries is not None:
+            entries = entries.to(dev, non_blocking=True)
+    if t is None:
+        lam, _ = power_iteration(row_ptr, col, val, max_iters=power_iters, tol=power_tol, stream=stream)
+        t = beta_scale / lam
+    plan = Plan(row_ptr, col, val, stream=stream)
+    try:
+        mean, sem = plan.estimate(v, t, paths, entries=entries, seed=seed, mode=mode, nsteps=nsteps, prec=prec,
+                                  stream=stream)
+        plan.sync(stream=stream)
+    finally:
+        plan.close()
+    if host:
+        pin = torch.cuda.is_available()
+        hm = torch.empty(mean.shape, dtype=mean.dtype, pin_memory=pin)
+        hs = torch.empty(sem.shape, dtype=sem.dtype, pin_memory=pin)
+        hm.copy_(mean, non_blocking=True)
+        hs.copy_(sem, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        mean, sem = hm, hs
+    return mean, sem, t

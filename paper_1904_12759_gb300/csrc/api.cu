@@ -1,0 +1,223 @@
+// C-ABI entry points (include/mcx.h): argument checks, plan ownership and
+// status handling around the kernels of prep.cu, walk.cu and spmv.cu.
+#include <math.h>
+#include <stdlib.h>
+
+#include <new>
+
+#include "mcx_internal.cuh"
+
+using namespace mcx;
+
+namespace {
+
+mcx_status from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return MCX_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();  // clear the sticky-free allocation error
+        return MCX_E_OOM;
+    }
+    return MCX_E_CUDA;
+}
+
+void free_plan(mcx_plan *p) {
+    if (!p) return;
+    cudaFree(p->node);
+    cudaFree(p->node64);
+    cudaFree(p->edge_col);
+    cudaFree(p->alias);
+    cudaFree(p->status);
+    cudaFree(p->scratch);
+    delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mcx_version(void) { return 100; }
+
+const char *mcx_status_string(int s) {
+    switch (s) {
+        case MCX_OK: return "ok";
+        case MCX_E_INVALID: return "invalid argument or malformed CSR";
+        case MCX_E_NEG_OFFDIAG: return "negative off-diagonal entry: -L is not a generator";
+        case MCX_E_NONFINITE: return "non-finite value in A or v";
+        case MCX_E_NEG_V: return "forward form needs v >= 0 with a positive sum";
+        case MCX_E_CUDA: return "CUDA runtime error";
+        case MCX_E_OOM: return "device allocation failed";
+        case MCX_E_TIMEOUT: return "bounded device wait gave up";
+        case MCX_E_UNSUPPORTED: return "unsupported request";
+        case MCX_E_OVERFLOW: return "estimate overflowed FP64";
+        default: return "unknown status";
+    }
+}
+
+mcx_status mcx_plan_create(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col, const double *val,
+                           uint32_t flags, void *stream, mcx_plan **out) {
+    if (!out) return MCX_E_INVALID;
+    *out = nullptr;
+    if (n < 0 || n >= (int64_t)0x7fffffff || nnz < 0 || !row_ptr || (nnz > 0 && (!col || !val)))
+        return MCX_E_INVALID;
+    if (flags & ~MCX_PLAN_HOST_INPUT) return MCX_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    mcx_plan *p = new (std::nothrow) mcx_plan();
+    if (!p) return MCX_E_OOM;
+    p->n = n;
+    p->nnz = nnz;
+    cudaGetDevice(&p->device);
+    int64_t *d_rp = nullptr;
+    int32_t *d_col = nullptr;
+    double *d_val = nullptr;
+    const bool host = (flags & MCX_PLAN_HOST_INPUT) != 0;
+    mcx_status rc = MCX_OK;
+    uint32_t dev_status = 0;
+    do {
+        cudaError_t e;
+        const size_t nn = (size_t)(n > 0 ? n : 1);
+        if ((e = cudaMalloc(&p->node, sizeof(NodeRec) * nn)) != cudaSuccess) { rc = from_cuda(e); break; }
+        if ((e = cudaMalloc(&p->node64, sizeof(NodeRec64) * nn)) != cudaSuccess) { rc = from_cuda(e); break; }
+        if ((e = cudaMalloc(&p->status, 32)) != cudaSuccess) { rc = from_cuda(e); break; }
+        if ((e = cudaMemsetAsync(p->status, 0, 32, st)) != cudaSuccess) { rc = from_cuda(e); break; }
+        p->device_bytes = (int64_t)((sizeof(NodeRec) + sizeof(NodeRec64)) * nn + 16);
+        const int64_t *rp = row_ptr;
+        const int32_t *cc = col;
+        const double *vv = val;
+        if (host) {
+            if ((e = cudaMalloc(&d_rp, sizeof(int64_t) * (size_t)(n + 1))) != cudaSuccess) { rc = from_cuda(e); break; }
+            if ((e = cudaMalloc(&d_col, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) { rc = from_cuda(e); break; }
+            if ((e = cudaMalloc(&d_val, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) { rc = from_cuda(e); break; }
+            if ((e = cudaMemcpyAsync(d_rp, row_ptr, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess) { rc = from_cuda(e); break; }
+            if (nnz > 0) {
+                if ((e = cudaMemcpyAsync(d_col, col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, st)) != cudaSuccess) { rc = from_cuda(e); break; }
+                if ((e = cudaMemcpyAsync(d_val, val, sizeof(double) * (size_t)nnz, cudaMemcpyHostToDevice, st)) != cudaSuccess) { rc = from_cuda(e); break; }
+            }
+            rp = d_rp; cc = d_col; vv = d_val;
+        }
+        if ((e = launch_prep(p, rp, cc, vv, st, &dev_status)) != cudaSuccess) { rc = from_cuda(e); break; }
+        if (dev_status & ST_BAD_STRUCT) rc = MCX_E_INVALID;
+        else if (dev_status & ST_NONFINITE) rc = MCX_E_NONFINITE;
+        else if (dev_status & ST_NEG_OFFDIAG) rc = MCX_E_NEG_OFFDIAG;
+    } while (0);
+    if (host) {
+        cudaStreamSynchronize(st);
+        cudaFree(d_rp);
+        cudaFree(d_col);
+        cudaFree(d_val);
+    }
+    if (rc != MCX_OK) {
+        cudaStreamSynchronize(st);
+        free_plan(p);
+        return rc;
+    }
+    *out = p;
+    return MCX_OK;
+}
+
+mcx_status mcx_plan_get_info(const mcx_plan *p, mcx_plan_info *info) {
+    if (!p || !info) return MCX_E_INVALID;
+    info->n = p->n;
+    info->nnz = p->nnz;
+    info->nnz_off = p->nnz_off;
+    info->weighted_rows = p->weighted_rows;
+    info->max_deg = p->max_deg;
+    info->reserved = 0;
+    info->device_bytes = p->device_bytes + (int64_t)p->scratch_bytes;
+    return MCX_OK;
+}
+
+static mcx_status check_common(const mcx_plan *p, double t, int functional, int32_t nsteps, int precision) {
+    if (!p) return MCX_E_INVALID;
+    if (!(t >= 0.0) || !isfinite(t)) return MCX_E_INVALID;
+    if (functional != MCX_EXACT && functional != MCX_STRANG && functional != MCX_LIE) return MCX_E_INVALID;
+    if (functional != MCX_EXACT && (nsteps < 1 || nsteps > (1 << 24))) return MCX_E_INVALID;
+    if (precision != MCX_FP32 && precision != MCX_FP64) return MCX_E_INVALID;
+    return MCX_OK;
+}
+
+mcx_status mcx_estimate(mcx_plan *p, const double *v, double t, int functional, int32_t nsteps,
+                        uint64_t paths_per_entry, const int32_t *entries, int64_t n_entries, uint64_t seed,
+                        uint64_t path_offset, int precision, double *mean, double *sem, void *stream) {
+    mcx_status rc = check_common(p, t, functional, nsteps, precision);
+    if (rc != MCX_OK) return rc;
+    if (n_entries == 0) return MCX_OK;  // nothing requested (an empty entry list may be NULL)
+    if (!v || n_entries < 0 || paths_per_entry < 1 || !mean) return MCX_E_INVALID;
+    if (!entries && n_entries != p->n) return MCX_E_INVALID;
+    if (paths_per_entry > (1ull << 53)) return MCX_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_pack_v(p, v, st);
+    if (e != cudaSuccess) return from_cuda(e);
+    EstimateArgs a{};
+    a.entries = entries;
+    a.n_entries = n_entries;
+    a.paths = paths_per_entry;
+    a.t = t;
+    a.mode = functional;
+    a.nsteps = nsteps;
+    a.precision = precision;
+    a.seed = seed;
+    a.path_offset = path_offset;
+    a.mean = mean;
+    a.sem = sem;
+    return from_cuda(launch_estimate(p, a, st));
+}
+
+mcx_status mcx_trace_paths(mcx_plan *p, double t, int functional, int32_t nsteps, int32_t entry, uint64_t seed,
+                           uint64_t first_path, uint32_t count, int precision, int32_t *end, uint32_t *njumps,
+                           uint64_t *hash, double *logw, void *stream) {
+    mcx_status rc = check_common(p, t, functional, nsteps, precision);
+    if (rc != MCX_OK) return rc;
+    if (entry < 0 || entry >= p->n || !end || !njumps || !hash || !logw) return MCX_E_INVALID;
+    return from_cuda(launch_trace(p, t, functional, nsteps, entry, seed, first_path, count, precision, end, njumps,
+                                  hash, logw, static_cast<cudaStream_t>(stream)));
+}
+
+mcx_status mcx_power_iteration(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                               int32_t max_iters, double tol, double *work, double *lambda_out, int32_t *iters_out,
+                               void *stream) {
+    if (n <= 0 || !row_ptr || !col || !val || !work || max_iters < 1 || !(tol >= 0.0)) return MCX_E_INVALID;
+    double lam = 0.0;
+    int32_t it = 0;
+    cudaError_t e = run_power_iteration(n, row_ptr, col, val, max_iters, tol, work, &lam, &it,
+                                        static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return from_cuda(e);
+    if (lambda_out) *lambda_out = lam;
+    if (iters_out) *iters_out = it;
+    return MCX_OK;
+}
+
+mcx_status mcx_plan_export(const mcx_plan *p, int32_t *deg, int64_t *row_start, uint8_t *weighted,
+                           float *inv_rate32, float *delta32, double *inv_rate64, double *delta64, int32_t *edge_col,
+                           int32_t *alias_col, uint32_t *thresh, void *stream) {
+    if (!p) return MCX_E_INVALID;
+    return from_cuda(launch_export(p, deg, row_start, weighted, inv_rate32, delta32, inv_rate64, delta64, edge_col,
+                                   alias_col, thresh, static_cast<cudaStream_t>(stream)));
+}
+
+mcx_status mcx_sync(mcx_plan *p, void *stream, mcx_stats *stats) {
+    if (!p) return MCX_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(hs, p->status, 32, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return from_cuda(e);
+    e = cudaMemsetAsync(p->status, 0, 32, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (stats) {
+        stats->paths = ((uint64_t)hs[3] << 32) | hs[2];
+        stats->jumps = ((uint64_t)hs[5] << 32) | hs[4];
+        stats->status_bits = hs[0];
+        stats->reserved = 0;
+    }
+    if (hs[0] & ST_BAD_ENTRY) return MCX_E_INVALID;
+    return (hs[0] & ST_OVERFLOW) ? MCX_E_OVERFLOW : MCX_OK;
+}
+
+void mcx_plan_destroy(mcx_plan *p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    free_plan(p);
+}
+
+}  // extern "C"

@@ -1,0 +1,206 @@
+// Internal definitions of the mcx library: the plan, the packed node and edge
+// records the walkers gather, and the device primitives of the draw schedule
+// (Philox4x32-10, uniform maps, logarithms).
+//
+// Every floating-point step that decides a path (holding time, remaining
+// time, grid counts, log-weight) is written with explicit round-to-nearest
+// intrinsics (__fadd_rn, __fmul_rn, __fmaf_rn, __fdiv_rn, and the double
+// versions), and the library is compiled with --fmad=false, so no
+// contraction or reassociation can change a path.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mcx.h"
+
+namespace mcx {
+
+// ---------------------------------------------------------------------------
+// Packed records.
+//
+// One 32-byte node record per row (one DRAM/L2 sector per gather): the CSR
+// offset of the row's kept off-diagonal entries, their count, the FP32 rate
+// reciprocal and potential, and the row's v value (written per estimate so
+// that the end-of-path read of v costs nothing extra).
+// ---------------------------------------------------------------------------
+struct __align__(32) NodeRec {
+    int64_t row_start;  // offset into the edge arrays
+    int32_t deg;        // kept off-diagonal entries (a_ij > 0, j != i)
+    uint32_t flags;     // bit 0: alias-table (weighted) row
+    float inv_rate;     // (float)(1 / lambda_i), lambda_i = sum_{j != i} a_ij
+    float delta;        // (float)(a_ii + lambda_i), the potential D_ii
+    double v;           // v_i of the current estimate
+};
+static_assert(sizeof(NodeRec) == 32, "node record must be one 32-byte sector");
+
+// FP64 path version: exact-precision rate reciprocal and potential.
+struct __align__(16) NodeRec64 {
+    double inv_rate;
+    double delta;
+};
+
+constexpr uint32_t NODE_WEIGHTED = 1u;
+
+// Alias entry of a weighted row: slot k keeps its own column iff w3 < thresh,
+// otherwise it jumps to alias_col.
+struct __align__(8) AliasEnt {
+    int32_t alias_col;
+    uint32_t thresh;
+};
+
+// Device status bits latched in the plan.
+constexpr uint32_t ST_OVERFLOW = 1u;
+constexpr uint32_t ST_BAD_STRUCT = 2u;
+constexpr uint32_t ST_NEG_OFFDIAG = 4u;
+constexpr uint32_t ST_NONFINITE = 8u;
+constexpr uint32_t ST_BAD_ENTRY = 16u;
+
+}  // namespace mcx
+
+struct mcx_plan {
+    int64_t n = 0;
+    int64_t nnz = 0;
+    int64_t nnz_off = 0;
+    int64_t weighted_rows = 0;
+    int32_t max_deg = 0;
+    int device = 0;
+    mcx::NodeRec *node = nullptr;      // [n]
+    mcx::NodeRec64 *node64 = nullptr;  // [n]
+    int32_t *edge_col = nullptr;       // [nnz_off]
+    mcx::AliasEnt *alias = nullptr;    // [nnz_off] if weighted_rows > 0
+    uint32_t *status = nullptr;        // device words: [0] status bits, [2..3] paths (u64), [4..5] jumps (u64)
+    void *scratch = nullptr;           // grow-only scratch for chunk partials
+    size_t scratch_bytes = 0;
+    int64_t device_bytes = 0;
+};
+
+namespace mcx {
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds; each round
+// multiplies counter words 0 and 2 by the two Philox constants, and mixes the
+// high halves with words 1 and 3 and the round key; the key is advanced by
+// the two Weyl increments between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Uniform in (0, 1] from the top 24 bits (exact in FP32, never 0).
+__device__ __forceinline__ float unif24(uint32_t w0) {
+    return __fmul_rn(__uint2float_rn(16777216u - (w0 >> 8)), 5.9604644775390625e-8f /* 2^-24 */);
+}
+
+// Uniform in (0, 1] from 53 bits of (w0, w1) (exact in FP64, never 0).
+__device__ __forceinline__ double unif53(uint32_t w0, uint32_t w1) {
+    const unsigned long long m = ((unsigned long long)w0 << 21) | (unsigned long long)(w1 >> 11);
+    return __dmul_rn(__ull2double_rn(9007199254740992ull - m), 1.1102230246251565e-16 /* 2^-53 */);
+}
+
+// Natural logarithm of a positive normal float: x = 2^e m with m in
+// [1/sqrt2, sqrt2]; ln m = 2 artanh(s) with s = (m-1)/(m+1), summed as
+// 2s + 2s z (1/3 + z/5 + z^2/7 + z^3/9 + z^4/11), z = s^2 (Abramowitz &
+// Stegun 4.1.27); ln x = e ln2 + ln m.
+__device__ __forceinline__ float ln_f32(float x) {
+    const uint32_t b = __float_as_uint(x);
+    int e = (int)((b >> 23) & 0xffu) - 127;
+    float m = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
+    if (m > 1.41421356f) {
+        m = __fmul_rn(m, 0.5f);
+        e = e + 1;
+    }
+    const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float z = __fmul_rn(s, s);
+    float q = 1.0f / 11.0f;
+    q = __fmaf_rn(q, z, 1.0f / 9.0f);
+    q = __fmaf_rn(q, z, 1.0f / 7.0f);
+    q = __fmaf_rn(q, z, 1.0f / 5.0f);
+    q = __fmaf_rn(q, z, 1.0f / 3.0f);
+    const float s2 = __fadd_rn(s, s);
+    const float lnm = __fmaf_rn(__fmul_rn(s2, z), q, s2);
+    return __fmaf_rn(__int2float_rn(e), 0.693147181f, lnm);
+}
+
+// Same construction in FP64 with the series carried to z^11/25.
+__device__ __forceinline__ double ln_f64(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    int e = (int)((b >> 52) & 0x7ffull) - 1023;
+    double m = __longlong_as_double((long long)((b & 0x000fffffffffffffull) | 0x3ff0000000000000ull));
+    if (m > 1.4142135623730951) {
+        m = __dmul_rn(m, 0.5);
+        e = e + 1;
+    }
+    const double s = __ddiv_rn(__dsub_rn(m, 1.0), __dadd_rn(m, 1.0));
+    const double z = __dmul_rn(s, s);
+    double q = 1.0 / 25.0;
+    q = __fma_rn(q, z, 1.0 / 23.0);
+    q = __fma_rn(q, z, 1.0 / 21.0);
+    q = __fma_rn(q, z, 1.0 / 19.0);
+    q = __fma_rn(q, z, 1.0 / 17.0);
+    q = __fma_rn(q, z, 1.0 / 15.0);
+    q = __fma_rn(q, z, 1.0 / 13.0);
+    q = __fma_rn(q, z, 1.0 / 11.0);
+    q = __fma_rn(q, z, 1.0 / 9.0);
+    q = __fma_rn(q, z, 1.0 / 7.0);
+    q = __fma_rn(q, z, 1.0 / 5.0);
+    q = __fma_rn(q, z, 1.0 / 3.0);
+    const double s2 = __dadd_rn(s, s);
+    const double lnm = __fma_rn(__dmul_rn(s2, z), q, s2);
+    return __fma_rn(__int2double_rn(e), 0.6931471805599453, lnm);
+}
+
+__device__ __forceinline__ NodeRec load_node(const NodeRec *__restrict__ node, int32_t j) {
+    const int4 *p = reinterpret_cast<const int4 *>(node + j);
+    const int4 a = __ldg(p);
+    const int4 b = __ldg(p + 1);
+    NodeRec r;
+    r.row_start = ((int64_t)(uint32_t)a.y << 32) | (uint32_t)a.x;
+    r.deg = a.z;
+    r.flags = (uint32_t)a.w;
+    r.inv_rate = __int_as_float(b.x);
+    r.delta = __int_as_float(b.y);
+    r.v = __hiloint2double(b.w, b.z);
+    return r;
+}
+
+// Host-side launch helpers (defined in the .cu files).
+cudaError_t launch_prep(mcx_plan *plan, const int64_t *row_ptr, const int32_t *col, const double *val,
+                        cudaStream_t st, uint32_t *host_status);
+cudaError_t launch_export(const mcx_plan *plan, int32_t *deg, int64_t *row_start, uint8_t *weighted, float *ir32,
+                          float *d32, double *ir64, double *d64, int32_t *ecol, int32_t *acol, uint32_t *thr,
+                          cudaStream_t st);
+cudaError_t launch_pack_v(mcx_plan *plan, const double *v, cudaStream_t st);
+
+struct EstimateArgs {
+    const int32_t *entries;
+    int64_t n_entries;
+    uint64_t paths;
+    double t;
+    int mode;
+    int nsteps;
+    int precision;
+    uint64_t seed;
+    uint64_t path_offset;
+    double *mean;
+    double *sem;
+};
+cudaError_t launch_estimate(mcx_plan *plan, const EstimateArgs &a, cudaStream_t st);
+cudaError_t launch_trace(mcx_plan *plan, double t, int mode, int nsteps, int32_t entry, uint64_t seed,
+                         uint64_t first_path, uint32_t count, int precision, int32_t *end, uint32_t *njumps,
+                         uint64_t *hash, double *logw, cudaStream_t st);
+cudaError_t run_power_iteration(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                                int32_t max_iters, double tol, double *work, double *lambda, int32_t *iters,
+                                cudaStream_t st);
+
+}  // namespace mcx

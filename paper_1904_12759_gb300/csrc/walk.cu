@@ -1,0 +1,536 @@
+// Backward walkers (Theorem 1, Algorithm 1) and the segmented per-entry
+// reduction.
+//
+// Work decomposition: the paths of each requested entry are split into
+// chunks of `chunk_len` consecutive path indices; one warp owns one
+// (entry, chunk).  Each lane runs paths p = chunk_begin + lane, +32, ... one
+// after another in a single flat event loop: every iteration draws one
+// Philox block and either finishes the lane's current path (folding its
+// weight into the lane's accumulators and starting the next path from the
+// entry) or takes one jump.  Lanes therefore refill independently and the
+// warp stays busy until its last path ends.  A jump is two dependent random
+// gathers: the column (4 B) and the new node's 32-byte record.
+//
+// Path arithmetic (every op a single IEEE operation or an explicit fma):
+//   S = (-ln u) * inv_rate_j          holding time in state j
+//   S >= r  -> stop;  else r <- r - S, jump
+//   EXACT : logW += delta_j * hold         (hold = S, or r for the last hold)
+//   grid  : acc  += delta_j * (#grid points m*dt, m = 0..N-1, inside the hold,
+//                              counted in remaining time); LIE logW = acc*dt;
+//           STRANG logW = (acc + delta_start/2 - delta_end/2)*dt
+// Weights: FP32 paths accumulate w = e^{logW - m} v (m a per-lane running
+// shift) with compensated FP32 sums of w and w^2; lanes merge in FP64 by
+// log-sum-exp; chunks merge in FP64 in chunk order (k_reduce_chunks).
+// FP64 paths do all of this in FP64.
+#include <math.h>
+
+#include <type_traits>
+
+#include "mcx_internal.cuh"
+
+namespace mcx {
+namespace {
+
+constexpr int WALK_THREADS = 256;
+constexpr int WARPS_PER_BLOCK = WALK_THREADS / 32;
+constexpr uint64_t FNV_OFFSET = 14695981039346656037ull;
+constexpr uint64_t FNV_PRIME = 1099511628211ull;
+
+struct Partial {
+    double s1;  // sum of e^{logW - m} v
+    double s2;  // sum of (e^{logW - m} v)^2
+    double m;   // shift
+};
+
+struct WalkParams {
+    const NodeRec *node;
+    const NodeRec64 *node64;
+    const int32_t *edge_col;
+    const AliasEnt *alias;
+    const int32_t *entries;
+    int64_t n_entries;
+    uint64_t paths;       // per entry
+    uint64_t chunk_len;   // paths per warp
+    uint32_t chunks_per_entry;
+    int nsteps;
+    int64_t n;            // rows: entries outside [0, n) are rejected
+    uint32_t max_events;  // per-path event cap (guarantees termination)
+    double t64, dt64, invdt64;
+    float t32, dt32, invdt32;
+    uint32_t key0, key1;
+    uint64_t path_offset;
+    double *mean;
+    double *sem;
+    Partial *partials;    // [n_entries * chunks_per_entry] when chunks_per_entry > 1
+    uint32_t *status;
+};
+
+// ---------------------------------------------------------------------------
+// Precision traits: the same path code in FP32 and FP64.
+// ---------------------------------------------------------------------------
+template <bool F64>
+struct P;
+
+template <>
+struct P<false> {
+    using T = float;
+    static __device__ __forceinline__ T unif(uint4 w) { return unif24(w.x); }
+    static __device__ __forceinline__ T neg_ln(T u) { return -ln_f32(u); }
+    static __device__ __forceinline__ T mul(T a, T b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ T sub(T a, T b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ T fma(T a, T b, T c) { return __fmaf_rn(a, b, c); }
+    static __device__ __forceinline__ T from_int(int c) { return __int2float_rn(c); }
+    static __device__ __forceinline__ int grid(T rho, T invdt, int N) {
+        if (rho < 0.0f) return 0;
+        const T f = floorf(__fmul_rn(rho, invdt));
+        const int c = (int)f + 1;
+        return c < N ? c : N;
+    }
+    static __device__ __forceinline__ T rate(const NodeRec &r, const NodeRec64 *, int32_t) { return r.inv_rate; }
+    static __device__ __forceinline__ T pot(const NodeRec &r, const NodeRec64 *, int32_t) { return r.delta; }
+};
+
+template <>
+struct P<true> {
+    using T = double;
+    static __device__ __forceinline__ T unif(uint4 w) { return unif53(w.x, w.y); }
+    static __device__ __forceinline__ T neg_ln(T u) { return -ln_f64(u); }
+    static __device__ __forceinline__ T mul(T a, T b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ T sub(T a, T b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ T fma(T a, T b, T c) { return __fma_rn(a, b, c); }
+    static __device__ __forceinline__ T from_int(int c) { return __int2double_rn(c); }
+    static __device__ __forceinline__ int grid(T rho, T invdt, int N) {
+        if (rho < 0.0) return 0;
+        const T f = floor(__dmul_rn(rho, invdt));
+        const int c = (int)f + 1;
+        return c < N ? c : N;
+    }
+    static __device__ __forceinline__ T rate(const NodeRec &, const NodeRec64 *n64, int32_t j) {
+        return __ldg(&n64[j].inv_rate);
+    }
+    static __device__ __forceinline__ T pot(const NodeRec &, const NodeRec64 *n64, int32_t j) {
+        return __ldg(&n64[j].delta);
+    }
+};
+
+// One walker between events.
+template <bool F64>
+struct Walker {
+    using T = typename P<F64>::T;
+    NodeRec rec;  // record of the current state j
+    int32_t j;
+    T r;          // remaining time
+    T acc;        // EXACT: running logW; grid modes: sum delta * grid count
+    T delta;      // potential of the current state
+    uint32_t k;   // event counter
+};
+
+// Advance one event.  Returns true when the path has ended (then w.acc holds
+// the final accumulated value with the last hold included).
+template <int MODE, bool WEIGHTED, bool F64>
+__device__ __forceinline__ bool advance(Walker<F64> &w, const WalkParams &a, uint32_t stream, uint64_t path) {
+    using Q = P<F64>;
+    using T = typename Q::T;
+    const T invdt = F64 ? (T)a.invdt64 : (T)a.invdt32;
+    const int N = a.nsteps;
+    if (w.rec.deg == 0 || w.k >= a.max_events) {
+        if (w.rec.deg != 0) atomicOr(a.status, ST_OVERFLOW);  // event cap reached: result flagged
+        w.acc = MODE == MCX_EXACT ? Q::fma(w.delta, w.r, w.acc) : Q::fma(w.delta, Q::from_int(Q::grid(w.r, invdt, N)), w.acc);
+        return true;
+    }
+    const uint4 rnd = philox4x32_10(make_uint4(w.k, stream, (uint32_t)path, (uint32_t)(path >> 32)), a.key0, a.key1);
+    const T S = Q::mul(Q::neg_ln(Q::unif(rnd)), Q::rate(w.rec, a.node64, w.j));
+    if (S >= w.r) {
+        w.acc = MODE == MCX_EXACT ? Q::fma(w.delta, w.r, w.acc) : Q::fma(w.delta, Q::from_int(Q::grid(w.r, invdt, N)), w.acc);
+        return true;
+    }
+    const T rn = Q::sub(w.r, S);
+    if (MODE == MCX_EXACT) {
+        w.acc = Q::fma(w.delta, S, w.acc);
+    } else {
+        w.acc = Q::fma(w.delta, Q::from_int(Q::grid(w.r, invdt, N) - Q::grid(rn, invdt, N)), w.acc);
+    }
+    w.r = rn;
+    const uint32_t slot = __umulhi(rnd.z, (uint32_t)w.rec.deg);
+    const int64_t e = w.rec.row_start + slot;
+    int32_t c = __ldg(a.edge_col + e);
+    if (WEIGHTED && (w.rec.flags & NODE_WEIGHTED)) {
+        const int2 al = __ldg(reinterpret_cast<const int2 *>(a.alias + e));
+        if (!(rnd.w < (uint32_t)al.y)) c = al.x;
+    }
+    w.j = c;
+    w.rec = load_node(a.node, c);
+    w.delta = Q::pot(w.rec, a.node64, c);
+    ++w.k;
+    return false;
+}
+
+template <int MODE, bool F64>
+__device__ __forceinline__ typename P<F64>::T final_logw(const Walker<F64> &w, typename P<F64>::T delta_start,
+                                                         const WalkParams &a) {
+    using Q = P<F64>;
+    using T = typename Q::T;
+    const T dt = F64 ? (T)a.dt64 : (T)a.dt32;
+    if (MODE == MCX_EXACT) return w.acc;
+    if (MODE == MCX_LIE) return Q::mul(w.acc, dt);
+    T s = Q::fma((T)0.5, delta_start, w.acc);
+    s = Q::fma((T)-0.5, w.delta, s);
+    return Q::mul(s, dt);
+}
+
+// ---------------------------------------------------------------------------
+// Lane accumulators.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+struct Acc32 {
+    float m = -INFINITY, s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+    __device__ __forceinline__ void add(float L, double v) {
+        if (!(L <= m + 8.0f)) {  // first path, a new larger weight, or a non-finite one
+            const float sc = (m == -INFINITY) ? 0.0f : expf(m - L);
+            const float sc2 = sc * sc;
+            s1 *= sc; c1 *= sc; s2 *= sc2; c2 *= sc2;
+            m = L;
+        }
+        const float wv = __fmul_rn(expf(__fsub_rn(L, m)), __double2float_rn(v));
+        kahan_add(s1, c1, wv);
+        kahan_add(s2, c2, __fmul_rn(wv, wv));
+    }
+    __device__ __forceinline__ double shift() const { return (double)m; }
+    __device__ __forceinline__ double sum1() const { return (double)s1 - (double)c1; }
+    __device__ __forceinline__ double sum2() const { return (double)s2 - (double)c2; }
+};
+
+struct Acc64 {
+    double m = -INFINITY, s1 = 0.0, s2 = 0.0;
+    __device__ __forceinline__ void add(double L, double v) {
+        if (!(L <= m + 64.0)) {
+            const double sc = (m == -INFINITY) ? 0.0 : exp(m - L);
+            s1 *= sc; s2 *= sc * sc;
+            m = L;
+        }
+        const double wv = __dmul_rn(exp(__dsub_rn(L, m)), v);
+        s1 = __dadd_rn(s1, wv);
+        s2 = __fma_rn(wv, wv, s2);
+    }
+    __device__ __forceinline__ double shift() const { return m; }
+    __device__ __forceinline__ double sum1() const { return s1; }
+    __device__ __forceinline__ double sum2() const { return s2; }
+};
+
+__device__ __forceinline__ double warp_max(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// mean and standard error from shifted sums over M paths
+__device__ __forceinline__ void finish_entry(double s1, double s2, double m, double M, double *mean, double *sem,
+                                             uint32_t *status) {
+    const double scale = exp(m);
+    const double mu = s1 / M;
+    double var = M > 1.0 ? (s2 - s1 * mu) / (M - 1.0) : 0.0;
+    if (var < 0.0) var = 0.0;
+    const double mv = scale * mu;
+    const double se = scale * sqrt(var / M);
+    *mean = mv;
+    if (sem) *sem = se;
+    if (!isfinite(mv) || !isfinite(se)) atomicOr(status, ST_OVERFLOW);
+}
+
+// ---------------------------------------------------------------------------
+// Estimate kernel: one warp per (entry, chunk).
+// ---------------------------------------------------------------------------
+template <int MODE, bool WEIGHTED, bool F64>
+__global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkParams a) {
+    using Q = P<F64>;
+    using T = typename Q::T;
+    using Acc = typename std::conditional<F64, Acc64, Acc32>::type;
+    const int lane = threadIdx.x & 31;
+    const uint64_t wid = ((uint64_t)blockIdx.x * WALK_THREADS + threadIdx.x) >> 5;
+    const uint64_t n_chunks = (uint64_t)a.n_entries * a.chunks_per_entry;
+    if (wid >= n_chunks) return;  // uniform across the warp
+    const uint64_t e_idx = wid / a.chunks_per_entry;
+    const uint64_t chunk = wid - e_idx * a.chunks_per_entry;
+    const int32_t i = a.entries ? __ldg(a.entries + e_idx) : (int32_t)e_idx;
+    if (i < 0 || (int64_t)i >= a.n) {  // invalid entry: latch the error, write NaN, touch nothing else
+        if (lane == 0) {
+            atomicOr(a.status, ST_BAD_ENTRY);
+            if (a.chunks_per_entry == 1) {
+                a.mean[e_idx] = __longlong_as_double(0x7ff8000000000000ll);
+                if (a.sem) a.sem[e_idx] = __longlong_as_double(0x7ff8000000000000ll);
+            } else {
+                a.partials[wid] = Partial{__longlong_as_double(0x7ff8000000000000ll), 0.0, 0.0};
+            }
+        }
+        return;
+    }
+    const uint64_t p_begin = chunk * a.chunk_len;
+    const uint64_t p_end = min(a.paths, p_begin + a.chunk_len);
+
+    const NodeRec start = load_node(a.node, i);
+    const T delta_start = Q::pot(start, a.node64, i);
+    const T t0 = F64 ? (T)a.t64 : (T)a.t32;
+
+    Walker<F64> w;
+    w.rec = start; w.j = i; w.r = t0; w.acc = (T)0; w.delta = delta_start; w.k = 0;
+    uint64_t p = p_begin + lane;
+    bool active = p < p_end;
+    Acc acc;
+    uint32_t jumps = 0;
+    while (__any_sync(0xffffffffu, active)) {
+        if (active) {
+            if (advance<MODE, WEIGHTED, F64>(w, a, (uint32_t)i, a.path_offset + p)) {
+                const T L = final_logw<MODE, F64>(w, delta_start, a);
+                acc.add(L, w.rec.v);
+                jumps += w.k;
+                p += 32;
+                active = p < p_end;
+                w.rec = start; w.j = i; w.r = t0; w.acc = (T)0; w.delta = delta_start; w.k = 0;
+            }
+        }
+    }
+    // walker statistics: paths and jumps of this warp, one atomic per warp
+    {
+        unsigned long long jl = jumps;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) jl += __shfl_xor_sync(0xffffffffu, jl, o);
+        if (lane == 0) {
+            unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.status + 2);
+            atomicAdd(ctr, (unsigned long long)(p_end - p_begin));
+            atomicAdd(ctr + 1, jl);
+        }
+    }
+    // merge lanes (log-sum-exp on the shifts), fixed shuffle tree
+    const double m_lane = acc.shift();
+    const double m_w = warp_max(m_lane);
+    const double sc = (m_lane == -INFINITY) ? 0.0 : exp(m_lane - m_w);
+    const double s1 = warp_sum(sc * acc.sum1());
+    const double s2 = warp_sum(sc * sc * acc.sum2());
+    if (lane == 0) {
+        if (a.chunks_per_entry == 1) {
+            finish_entry(s1, s2, m_w, (double)a.paths, a.mean + e_idx, a.sem ? a.sem + e_idx : nullptr, a.status);
+        } else {
+            a.partials[wid] = Partial{s1, s2, m_w};
+        }
+    }
+}
+
+// One warp per entry: merge its chunk partials in chunk order.
+__global__ void __launch_bounds__(WALK_THREADS) k_reduce_chunks(const Partial *__restrict__ part, int64_t n_entries,
+                                                               uint32_t cpe, double M, double *mean, double *sem,
+                                                               uint32_t *status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t e = ((int64_t)blockIdx.x * WALK_THREADS + threadIdx.x) >> 5;
+    if (e >= n_entries) return;
+    const Partial *pp = part + (uint64_t)e * cpe;
+    double m = -INFINITY;
+    for (uint32_t c = lane; c < cpe; c += 32) m = fmax(m, pp[c].m);
+    m = warp_max(m);
+    double s1 = 0.0, s2 = 0.0;
+    for (uint32_t c = lane; c < cpe; c += 32) {
+        const Partial q = pp[c];
+        const double sc = (q.m == -INFINITY) ? 0.0 : exp(q.m - m);
+        s1 += sc * q.s1;
+        s2 += sc * sc * q.s2;
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (lane == 0) finish_entry(s1, s2, m, M, mean + e, sem ? sem + e : nullptr, status);
+}
+
+// ---------------------------------------------------------------------------
+// Trace kernel: one thread per path, same stepping code, plus the index hash.
+// ---------------------------------------------------------------------------
+template <int MODE, bool WEIGHTED, bool F64>
+__global__ void __launch_bounds__(WALK_THREADS) k_trace(const WalkParams a, int32_t i, uint64_t first_path,
+                                                       uint32_t count, int32_t *end, uint32_t *njumps,
+                                                       uint64_t *hash, double *logw) {
+    using Q = P<F64>;
+    using T = typename Q::T;
+    const uint32_t q = blockIdx.x * WALK_THREADS + threadIdx.x;
+    if (q >= count) return;
+    const uint64_t path = first_path + q;
+    const NodeRec start = load_node(a.node, i);
+    const T delta_start = Q::pot(start, a.node64, i);
+    Walker<F64> w;
+    w.rec = start; w.j = i; w.r = F64 ? (T)a.t64 : (T)a.t32; w.acc = (T)0; w.delta = delta_start; w.k = 0;
+    uint64_t h = (FNV_OFFSET ^ (uint64_t)(uint32_t)i) * FNV_PRIME;
+    for (;;) {
+        const uint32_t k_before = w.k;
+        if (advance<MODE, WEIGHTED, F64>(w, a, (uint32_t)i, path)) break;
+        if (w.k != k_before) h = (h ^ (uint64_t)(uint32_t)w.j) * FNV_PRIME;
+    }
+    end[q] = w.j;
+    njumps[q] = w.k;
+    hash[q] = h;
+    logw[q] = (double)final_logw<MODE, F64>(w, delta_start, a);
+}
+
+__global__ void k_trace_t0(int32_t i, uint32_t count, int32_t *end, uint32_t *njumps, uint64_t *hash, double *logw) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= count) return;
+    end[q] = i;
+    njumps[q] = 0;
+    hash[q] = (FNV_OFFSET ^ (uint64_t)(uint32_t)i) * FNV_PRIME;
+    logw[q] = 0.0;
+}
+
+__global__ void k_pack_v(int64_t n, const double *__restrict__ v, NodeRec *__restrict__ node) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) node[i].v = v[i];
+}
+
+// t = 0: exp(0 A) v = v.
+__global__ void k_copy_v(const int32_t *__restrict__ entries, int64_t n_entries, int64_t n,
+                         const NodeRec *__restrict__ node, double *mean, double *sem, uint32_t *status) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_entries) return;
+    const int64_t i = entries ? entries[e] : e;
+    if (i < 0 || i >= n) {
+        atomicOr(status, ST_BAD_ENTRY);
+        mean[e] = __longlong_as_double(0x7ff8000000000000ll);
+        if (sem) sem[e] = mean[e];
+        return;
+    }
+    mean[e] = node[i].v;
+    if (sem) sem[e] = 0.0;
+}
+
+template <bool F64, bool WEIGHTED>
+cudaError_t launch_walk_mode(int mode, unsigned grid, const WalkParams &p, cudaStream_t st) {
+    switch (mode) {
+        case MCX_EXACT: k_walk<MCX_EXACT, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p); break;
+        case MCX_STRANG: k_walk<MCX_STRANG, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p); break;
+        default: k_walk<MCX_LIE, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+
+template <bool F64, bool WEIGHTED>
+cudaError_t launch_trace_mode(int mode, unsigned grid, const WalkParams &p, int32_t i, uint64_t first,
+                              uint32_t count, int32_t *end, uint32_t *nj, uint64_t *h, double *lw, cudaStream_t st) {
+    switch (mode) {
+        case MCX_EXACT: k_trace<MCX_EXACT, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p, i, first, count, end, nj, h, lw); break;
+        case MCX_STRANG: k_trace<MCX_STRANG, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p, i, first, count, end, nj, h, lw); break;
+        default: k_trace<MCX_LIE, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p, i, first, count, end, nj, h, lw); break;
+    }
+    return cudaGetLastError();
+}
+
+WalkParams make_params(mcx_plan *plan, double t, int nsteps, uint64_t seed) {
+    WalkParams p{};
+    p.node = plan->node;
+    p.node64 = plan->node64;
+    p.edge_col = plan->edge_col;
+    p.alias = plan->alias;
+    p.nsteps = nsteps;
+    p.t64 = t;
+    p.dt64 = t / (double)nsteps;
+    p.invdt64 = (double)nsteps / t;
+    p.t32 = (float)t;
+    p.dt32 = (float)p.dt64;
+    p.invdt32 = (float)p.invdt64;
+    p.n = plan->n;
+    p.max_events = 1u << 30;
+    p.key0 = (uint32_t)seed;
+    p.key1 = (uint32_t)(seed >> 32);
+    p.status = plan->status;
+    return p;
+}
+
+}  // namespace
+
+cudaError_t launch_pack_v(mcx_plan *plan, const double *v, cudaStream_t st) {
+    if (plan->n == 0) return cudaSuccess;
+    k_pack_v<<<(unsigned)((plan->n + 255) / 256), 256, 0, st>>>(plan->n, v, plan->node);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_estimate(mcx_plan *plan, const EstimateArgs &a, cudaStream_t st) {
+    if (a.n_entries == 0) return cudaSuccess;
+    if (a.t == 0.0) {
+        k_copy_v<<<(unsigned)((a.n_entries + 255) / 256), 256, 0, st>>>(a.entries, a.n_entries, plan->n,
+                                                                          plan->node, a.mean, a.sem, plan->status);
+        return cudaGetLastError();
+    }
+    WalkParams p = make_params(plan, a.t, a.mode == MCX_EXACT ? 1 : a.nsteps, a.seed);
+    p.entries = a.entries;
+    p.n_entries = a.n_entries;
+    p.paths = a.paths;
+    p.path_offset = a.path_offset;
+    p.mean = a.mean;
+    p.sem = a.sem;
+    // Chunking: at least 1024 paths per warp, and enough warps to fill the GPU
+    // several times over (152 SMs x 64 resident warps x 8 waves).
+    const uint64_t target_warps = 152ull * 64ull * 8ull;
+    uint64_t cpe = (target_warps + (uint64_t)a.n_entries - 1) / (uint64_t)a.n_entries;
+    const uint64_t max_cpe = (a.paths + 1023) / 1024;
+    if (cpe > max_cpe) cpe = max_cpe;
+    if (cpe < 1) cpe = 1;
+    uint64_t chunk = (a.paths + cpe - 1) / cpe;
+    chunk = (chunk + 31) / 32 * 32;
+    cpe = (a.paths + chunk - 1) / chunk;
+    p.chunk_len = chunk;
+    p.chunks_per_entry = (uint32_t)cpe;
+    const uint64_t n_chunks = (uint64_t)a.n_entries * cpe;
+    if (cpe > 1) {
+        const size_t need = sizeof(Partial) * (size_t)n_chunks;
+        if (plan->scratch_bytes < need) {
+            cudaFree(plan->scratch);
+            plan->scratch = nullptr;
+            plan->scratch_bytes = 0;
+            cudaError_t e = cudaMalloc(&plan->scratch, need);
+            if (e != cudaSuccess) return e;
+            plan->scratch_bytes = need;
+        }
+        p.partials = static_cast<Partial *>(plan->scratch);
+    }
+    const unsigned grid = (unsigned)((n_chunks + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+    const bool weighted = plan->weighted_rows > 0;
+    cudaError_t e;
+    if (a.precision == MCX_FP64) {
+        e = weighted ? launch_walk_mode<true, true>(a.mode, grid, p, st) : launch_walk_mode<true, false>(a.mode, grid, p, st);
+    } else {
+        e = weighted ? launch_walk_mode<false, true>(a.mode, grid, p, st) : launch_walk_mode<false, false>(a.mode, grid, p, st);
+    }
+    if (e != cudaSuccess) return e;
+    if (cpe > 1) {
+        const unsigned g2 = (unsigned)((a.n_entries + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+        k_reduce_chunks<<<g2, WALK_THREADS, 0, st>>>(p.partials, a.n_entries, (uint32_t)cpe, (double)a.paths, a.mean,
+                                                    a.sem, plan->status);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+cudaError_t launch_trace(mcx_plan *plan, double t, int mode, int nsteps, int32_t entry, uint64_t seed,
+                         uint64_t first_path, uint32_t count, int precision, int32_t *end, uint32_t *njumps,
+                         uint64_t *hash, double *logw, cudaStream_t st) {
+    if (count == 0) return cudaSuccess;
+    const unsigned grid = (count + WALK_THREADS - 1) / WALK_THREADS;
+    if (t == 0.0) {
+        k_trace_t0<<<grid, WALK_THREADS, 0, st>>>(entry, count, end, njumps, hash, logw);
+        return cudaGetLastError();
+    }
+    WalkParams p = make_params(plan, t, mode == MCX_EXACT ? 1 : nsteps, seed);
+    const bool weighted = plan->weighted_rows > 0;
+    if (precision == MCX_FP64) {
+        return weighted ? launch_trace_mode<true, true>(mode, grid, p, entry, first_path, count, end, njumps, hash, logw, st)
+                        : launch_trace_mode<true, false>(mode, grid, p, entry, first_path, count, end, njumps, hash, logw, st);
+    }
+    return weighted ? launch_trace_mode<false, true>(mode, grid, p, entry, first_path, count, end, njumps, hash, logw, st)
+                    : launch_trace_mode<false, false>(mode, grid, p, entry, first_path, count, end, njumps, hash, logw, st);
+}
+
+}  // namespace mcx

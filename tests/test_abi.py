@@ -1,0 +1,63 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every call that
+include/mcx.h declares (no compute calls: this runs without a GPU)."""
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "mcx.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mcx_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("no nvcc")
+    from paper_1904_12759_gb300 import build as B
+
+    B.build()
+    from paper_1904_12759_gb300 import _lib
+
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    d = _declared()
+    for name in ("mcx_plan_create", "mcx_estimate", "mcx_trace_paths", "mcx_power_iteration", "mcx_sync",
+                 "mcx_plan_destroy", "mcx_status_string"):
+        assert name in d
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1904_12759_gb300 import _lib
+
+    declared = _declared()
+    assert sorted(_lib.EXPORTS) == declared
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_version(lib):
+    assert lib.mcx_version() >= 100
+    for code in range(0, -10, -1):
+        s = lib.mcx_status_string(code).decode()
+        assert s and s != "unknown status"
+    assert lib.mcx_status_string(-99).decode() == "unknown status"
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_1904_12759_gb300 import _lib
+
+    saved = _lib._lib
+    try:
+        _lib._lib = None
+        with pytest.raises(ImportError):
+            _lib.load(str(tmp_path / "nope.so"))
+    finally:
+        _lib._lib = saved
