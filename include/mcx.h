@@ -155,6 +155,37 @@ mcx_status mcx_estimate(mcx_plan *plan, const double *v, double t, int functiona
                         void *stream);
 
 /*
+ * mcx_estimate without any device allocation.  The paper has no counterpart:
+ * this exists for callers that cannot call cudaMalloc once they are running,
+ * e.g. a service that reserves all of its device memory at start-up and must
+ * keep its footprint fixed afterwards, or a host framework whose own pool
+ * allocator owns the device memory and forbids outside allocations.
+ * mcx_estimate may grow plan scratch with cudaMalloc (and cudaFree the old
+ * block, which can synchronise the device); this call never does.
+ *
+ * Arguments, outputs and results are those of mcx_estimate (same kernels,
+ * same chunking, same numbers).  The per-chunk partial sums live in a
+ * fixed device array compiled into the library, of 131072 partials of 24
+ * bytes (3 MiB), which every GPU that loads the library holds until the
+ * process exits.  A request needs n_entries x chunks partials when its paths
+ * are split into more than one chunk per entry (chunks ~ 77824 / n_entries,
+ * at least 1024 paths each); a request beyond 131072 is rejected with
+ * MCX_E_UNSUPPORTED before anything is enqueued.
+ *
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it; make that first call before any stream
+ * capture.  All calls share the array and it keeps the previous call's
+ * contents (each call writes every slot it later reads, so nothing needs
+ * clearing); calls that overlap on the GPU race on it, so serialise them
+ * (one stream, or events between streams).
+ * Errors: those of mcx_estimate, plus MCX_E_UNSUPPORTED for oversized requests.
+ */
+mcx_status mcx_estimate_noalloc(mcx_plan *plan, const double *v, double t, int functional, int32_t nsteps,
+                                uint64_t paths_per_entry, const int32_t *entries, int64_t n_entries,
+                                uint64_t seed, uint64_t path_offset, int precision, double *mean, double *sem,
+                                void *stream);
+
+/*
  * Per-path record of `count` backward paths of one entry (for parity checks
  * against an independent implementation of the same draw schedule):
  *   end     int32  [count]  X_t

@@ -162,6 +162,33 @@ mcx_status mcx_estimate(mcx_plan *p, const double *v, double t, int functional, 
     return from_cuda(launch_estimate(p, a, st));
 }
 
+mcx_status mcx_estimate_noalloc(mcx_plan *p, const double *v, double t, int functional, int32_t nsteps,
+                                uint64_t paths_per_entry, const int32_t *entries, int64_t n_entries, uint64_t seed,
+                                uint64_t path_offset, int precision, double *mean, double *sem, void *stream) {
+    mcx_status rc = check_common(p, t, functional, nsteps, precision);
+    if (rc != MCX_OK) return rc;
+    if (n_entries == 0) return MCX_OK;
+    if (!v || n_entries < 0 || paths_per_entry < 1 || !mean) return MCX_E_INVALID;
+    if (!entries && n_entries != p->n) return MCX_E_INVALID;
+    if (paths_per_entry > (1ull << 53)) return MCX_E_INVALID;
+    EstimateArgs a{};
+    a.entries = entries;
+    a.n_entries = n_entries;
+    a.paths = paths_per_entry;
+    a.t = t;
+    a.mode = functional;
+    a.nsteps = nsteps;
+    a.precision = precision;
+    a.seed = seed;
+    a.path_offset = path_offset;
+    a.mean = mean;
+    a.sem = sem;
+    bool too_large = false;
+    cudaError_t e = launch_estimate_noalloc(p, v, a, static_cast<cudaStream_t>(stream), &too_large);
+    if (too_large) return MCX_E_UNSUPPORTED;
+    return from_cuda(e);
+}
+
 mcx_status mcx_trace_paths(mcx_plan *p, double t, int functional, int32_t nsteps, int32_t entry, uint64_t seed,
                            uint64_t first_path, uint32_t count, int precision, int32_t *end, uint32_t *njumps,
                            uint64_t *hash, double *logw, void *stream) {

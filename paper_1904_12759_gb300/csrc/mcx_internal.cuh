@@ -196,6 +196,9 @@ struct EstimateArgs {
     double *sem;
 };
 cudaError_t launch_estimate(mcx_plan *plan, const EstimateArgs &a, cudaStream_t st);
+cudaError_t launch_estimate_noalloc(mcx_plan *plan, const double *v, const EstimateArgs &a, cudaStream_t st,
+                                    bool *too_large);
+uint64_t noalloc_max_partials();
 cudaError_t launch_trace(mcx_plan *plan, double t, int mode, int nsteps, int32_t entry, uint64_t seed,
                          uint64_t first_path, uint32_t count, int precision, int32_t *end, uint32_t *njumps,
                          uint64_t *hash, double *logw, cudaStream_t st);

@@ -24,6 +24,7 @@
 // FP64 paths do all of this in FP64.
 #include <math.h>
 
+#include <mutex>
 #include <type_traits>
 
 #include "mcx_internal.cuh"
@@ -531,6 +532,105 @@ cudaError_t launch_trace(mcx_plan *plan, double t, int mode, int nsteps, int32_t
     }
     return weighted ? launch_trace_mode<false, true>(mode, grid, p, entry, first_path, count, end, njumps, hash, logw, st)
                     : launch_trace_mode<false, false>(mode, grid, p, entry, first_path, count, end, njumps, hash, logw, st);
+}
+
+// ---------------------------------------------------------------------------
+// Estimate that allocates nothing (mcx_estimate_noalloc).
+//
+// mcx_estimate keeps its per-chunk partial sums in plan scratch that it grows
+// with cudaMalloc on demand.  This variant runs the same kernels but keeps the
+// partials in the fixed array below, compiled into the library: every GPU that
+// loads the library holds NOALLOC_MAX_PARTIALS * 24 bytes (3 MiB) of it until
+// the process exits.  All calls share the array and it keeps the last call's
+// contents; nothing in it needs to start at zero, because each call writes
+// every slot it reads (k_walk writes one partial per chunk before
+// k_reduce_chunks reads it).  Two calls that overlap on the GPU (different
+// streams, or different threads without ordering) race on the array.
+// ---------------------------------------------------------------------------
+constexpr uint64_t NOALLOC_MAX_PARTIALS = 1ull << 17;
+static __device__ __align__(256) Partial g_noalloc_partials[NOALLOC_MAX_PARTIALS];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::once_flag g_noalloc_once[NOALLOC_MAX_DEVICES];
+Partial *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+cudaError_t g_noalloc_err[NOALLOC_MAX_DEVICES];
+
+// Device address of g_noalloc_partials on the current device.  In host code the
+// array's name only stands for it, so the address is looked up once per device
+// (with that device current) and cached.
+cudaError_t noalloc_partials(Partial **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::call_once(g_noalloc_once[dev], [dev]() {
+        void *ptr = nullptr;
+        g_noalloc_err[dev] = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
+        g_noalloc_ptr[dev] = static_cast<Partial *>(ptr);
+    });
+    if (g_noalloc_err[dev] != cudaSuccess) return g_noalloc_err[dev];
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+uint64_t noalloc_max_partials() { return NOALLOC_MAX_PARTIALS; }
+
+cudaError_t launch_estimate_noalloc(mcx_plan *plan, const double *v, const EstimateArgs &a, cudaStream_t st,
+                                    bool *too_large) {
+    *too_large = false;
+    if (a.n_entries == 0) return cudaSuccess;
+    // same chunking as launch_estimate
+    const uint64_t target_warps = 152ull * 64ull * 8ull;
+    uint64_t cpe = (target_warps + (uint64_t)a.n_entries - 1) / (uint64_t)a.n_entries;
+    const uint64_t max_cpe = (a.paths + 1023) / 1024;
+    if (cpe > max_cpe) cpe = max_cpe;
+    if (cpe < 1) cpe = 1;
+    uint64_t chunk = (a.paths + cpe - 1) / cpe;
+    chunk = (chunk + 31) / 32 * 32;
+    cpe = (a.paths + chunk - 1) / chunk;
+    const uint64_t n_chunks = (uint64_t)a.n_entries * cpe;
+    if (a.t != 0.0 && cpe > 1 && n_chunks > NOALLOC_MAX_PARTIALS) {
+        *too_large = true;  // rejected before anything is enqueued
+        return cudaSuccess;
+    }
+    Partial *partials = nullptr;
+    cudaError_t e = noalloc_partials(&partials);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_pack_v(plan, v, st)) != cudaSuccess) return e;
+    if (a.t == 0.0) {
+        k_copy_v<<<(unsigned)((a.n_entries + 255) / 256), 256, 0, st>>>(a.entries, a.n_entries, plan->n,
+                                                                          plan->node, a.mean, a.sem, plan->status);
+        return cudaGetLastError();
+    }
+    WalkParams p = make_params(plan, a.t, a.mode == MCX_EXACT ? 1 : a.nsteps, a.seed);
+    p.entries = a.entries;
+    p.n_entries = a.n_entries;
+    p.paths = a.paths;
+    p.path_offset = a.path_offset;
+    p.mean = a.mean;
+    p.sem = a.sem;
+    p.chunk_len = chunk;
+    p.chunks_per_entry = (uint32_t)cpe;
+    p.partials = partials;
+    const unsigned grid = (unsigned)((n_chunks + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+    const bool weighted = plan->weighted_rows > 0;
+    if (a.precision == MCX_FP64) {
+        e = weighted ? launch_walk_mode<true, true>(a.mode, grid, p, st) : launch_walk_mode<true, false>(a.mode, grid, p, st);
+    } else {
+        e = weighted ? launch_walk_mode<false, true>(a.mode, grid, p, st) : launch_walk_mode<false, false>(a.mode, grid, p, st);
+    }
+    if (e != cudaSuccess) return e;
+    if (cpe > 1) {
+        const unsigned g2 = (unsigned)((a.n_entries + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+        k_reduce_chunks<<<g2, WALK_THREADS, 0, st>>>(partials, a.n_entries, (uint32_t)cpe, (double)a.paths, a.mean,
+                                                    a.sem, plan->status);
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 }  // namespace mcx
