@@ -360,10 +360,11 @@ def main():
                      "kernel": "k_walk (estimate launch)", "bytes_per_jump": BYTES_PER_JUMP},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": None, "clocks": clk.summary(),
     }
-    # per step: prep (rows, scan tiles, scan sums, scan add, fill) + power iteration (init, then
-    # spmv/finish/scale in batches of 16) + estimate (pack v, walk); L2 flushes are torch's, not counted
-    batches = -(-iters // 16)
-    line["gpu_launches"] = args.steps * (5 + 1 + 3 * 16 * batches + 2)
+    # per step: prep (rows, scan tiles, scan sums, scan add, fill) + power iteration (init, then one
+    # fused step per iteration, launched in batches of 8) + estimate (pack v, walk); L2 flushes are
+    # torch's, not counted
+    batches = -(-iters // 8)
+    line["gpu_launches"] = args.steps * (5 + 1 + 8 * batches + 2)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

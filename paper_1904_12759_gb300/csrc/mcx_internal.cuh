@@ -21,8 +21,8 @@ namespace mcx {
 //
 // One 32-byte node record per row (one DRAM/L2 sector per gather): the CSR
 // offset of the row's kept off-diagonal entries, their count, the FP32 rate
-// reciprocal and potential, and the row's v value (written per estimate so
-// that the end-of-path read of v costs nothing extra).
+// reciprocal and potential, and the row's v value in FP32 (written per
+// estimate so that the end-of-path read of v costs nothing extra).
 // ---------------------------------------------------------------------------
 struct __align__(32) NodeRec {
     int64_t row_start;  // offset into the edge arrays
@@ -30,15 +30,19 @@ struct __align__(32) NodeRec {
     uint32_t flags;     // bit 0: alias-table (weighted) row
     float inv_rate;     // (float)(1 / lambda_i), lambda_i = sum_{j != i} a_ij
     float delta;        // (float)(a_ii + lambda_i), the potential D_ii
-    double v;           // v_i of the current estimate
+    float v;            // (float)v_i of the current estimate
+    uint32_t pad;
 };
 static_assert(sizeof(NodeRec) == 32, "node record must be one 32-byte sector");
 
-// FP64 path version: exact-precision rate reciprocal and potential.
-struct __align__(16) NodeRec64 {
+// FP64 path version: exact-precision rate reciprocal, potential and v.
+struct __align__(32) NodeRec64 {
     double inv_rate;
     double delta;
+    double v;
+    double pad;
 };
+static_assert(sizeof(NodeRec64) == 32, "FP64 node record must be one 32-byte sector");
 
 constexpr uint32_t NODE_WEIGHTED = 1u;
 
@@ -170,7 +174,8 @@ __device__ __forceinline__ NodeRec load_node(const NodeRec *__restrict__ node, i
     r.flags = (uint32_t)a.w;
     r.inv_rate = __int_as_float(b.x);
     r.delta = __int_as_float(b.y);
-    r.v = __hiloint2double(b.w, b.z);
+    r.v = __int_as_float(b.z);
+    r.pad = (uint32_t)b.w;
     return r;
 }
 

@@ -98,9 +98,10 @@ __global__ void k_prep_rows(int64_t n, int64_t nnz, const int64_t *__restrict__ 
     r.flags = (d > 1 && !uniform) ? NODE_WEIGHTED : 0u;
     r.inv_rate = __double2float_rn(inv);
     r.delta = __double2float_rn(delta);
-    r.v = 0.0;
+    r.v = 0.0f;
+    r.pad = 0u;
     node[i] = r;
-    node64[i] = NodeRec64{inv, delta};
+    node64[i] = NodeRec64{inv, delta, 0.0, 0.0};
 }
 
 // Tile scan: exclusive prefix of deg within each SCAN_TILE rows; tile totals to tile_sum.

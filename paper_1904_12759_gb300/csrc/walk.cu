@@ -7,9 +7,14 @@
 // after another in a single flat event loop: every iteration draws one
 // Philox block and either finishes the lane's current path (folding its
 // weight into the lane's accumulators and starting the next path from the
-// entry) or takes one jump.  Lanes therefore refill independently and the
-// warp stays busy until its last path ends.  A jump is two dependent random
+// entry) or takes one jump.  A lane whose path ends takes the next unassigned
+// path of the chunk, so the lanes stay busy until the chunk is exhausted.  A jump is two dependent random
 // gathers: the column (4 B) and the new node's 32-byte record.
+//
+// Hot-row staging: every path of a warp starts at the same entry, so the
+// entry's row (its kept columns, their node records and alias slots, up to
+// STAGE entries) is staged in shared memory once per warp; jumps out of the
+// entry state read shared memory instead of two dependent global gathers.
 //
 // Path arithmetic (every op a single IEEE operation or an explicit fma):
 //   S = (-ln u) * inv_rate_j          holding time in state j
@@ -19,9 +24,12 @@
 //                              counted in remaining time); LIE logW = acc*dt;
 //           STRANG logW = (acc + delta_start/2 - delta_end/2)*dt
 // Weights: FP32 paths accumulate w = e^{logW - m} v (m a per-lane running
-// shift) with compensated FP32 sums of w and w^2; lanes merge in FP64 by
-// log-sum-exp; chunks merge in FP64 in chunk order (k_reduce_chunks).
-// FP64 paths do all of this in FP64.
+// shift) with compensated FP32 sums of w and w^2; lanes merge with
+// compensated FP32 pairs after log-sum-exp rescaling, so the FP64 pipe (slow
+// on this GPU) is used only per warp and per entry; each block then finishes
+// its entries (mean, standard error) with one lane per entry.  Entries split
+// into several chunks merge their chunk partials in FP64 in chunk order
+// (k_reduce_chunks).  FP64 paths do all of this in FP64.
 #include <math.h>
 
 #include <mutex>
@@ -34,6 +42,14 @@ namespace {
 
 constexpr int WALK_THREADS = 256;
 constexpr int WARPS_PER_BLOCK = WALK_THREADS / 32;
+constexpr int STAGE = 32;  // max staged entry-row length
+#ifndef MCX_WALK_MIN_BLOCKS
+#define MCX_WALK_MIN_BLOCKS 6
+#endif
+// resident blocks per SM requested from the compiler: FP32 walkers 6 (48 warps,
+// <= 42 registers); the FP64 path version keeps more registers
+constexpr int WALK_MIN_BLOCKS_F32 = MCX_WALK_MIN_BLOCKS;
+constexpr int WALK_MIN_BLOCKS_F64 = 4;
 constexpr uint64_t FNV_OFFSET = 14695981039346656037ull;
 constexpr uint64_t FNV_PRIME = 1099511628211ull;
 
@@ -58,13 +74,35 @@ struct WalkParams {
     uint32_t max_events;  // per-path event cap (guarantees termination)
     double t64, dt64, invdt64;
     float t32, dt32, invdt32;
-    uint32_t key0, key1;
+    uint32_t rk0[10], rk1[10];  // Philox round keys: seed + r * (Weyl increments)
     uint64_t path_offset;
     double *mean;
     double *sem;
     Partial *partials;    // [n_entries * chunks_per_entry] when chunks_per_entry > 1
     uint32_t *status;
 };
+
+// The entry row of one warp, staged in shared memory.
+struct StageWarp {
+    NodeRec start;               // the entry's own record
+    NodeRec rec[STAGE];          // records of its kept columns
+    int32_t col[STAGE];          // kept columns (CSR order)
+    int32_t aslot[STAGE];        // alias rows: slot of the alias column
+    uint32_t thresh[STAGE];      // alias rows: keep-own-column threshold
+};
+
+// Philox4x32-10 with the ten round keys precomputed on the host.
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const WalkParams &a) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ a.rk0[r], lo1, hi0 ^ c.w ^ a.rk1[r], lo0);
+    }
+    return c;
+}
 
 // ---------------------------------------------------------------------------
 // Precision traits: the same path code in FP32 and FP64.
@@ -127,9 +165,11 @@ struct Walker {
 };
 
 // Advance one event.  Returns true when the path has ended (then w.acc holds
-// the final accumulated value with the last hold included).
+// the final accumulated value with the last hold included).  With `sw` set,
+// jumps out of state `i0` read the staged row.
 template <int MODE, bool WEIGHTED, bool F64>
-__device__ __forceinline__ bool advance(Walker<F64> &w, const WalkParams &a, uint32_t stream, uint64_t path) {
+__device__ __forceinline__ bool advance(Walker<F64> &w, const WalkParams &a, uint32_t stream, uint64_t path,
+                                        const StageWarp *sw, int32_t i0) {
     using Q = P<F64>;
     using T = typename Q::T;
     const T invdt = F64 ? (T)a.invdt64 : (T)a.invdt32;
@@ -139,7 +179,7 @@ __device__ __forceinline__ bool advance(Walker<F64> &w, const WalkParams &a, uin
         w.acc = MODE == MCX_EXACT ? Q::fma(w.delta, w.r, w.acc) : Q::fma(w.delta, Q::from_int(Q::grid(w.r, invdt, N)), w.acc);
         return true;
     }
-    const uint4 rnd = philox4x32_10(make_uint4(w.k, stream, (uint32_t)path, (uint32_t)(path >> 32)), a.key0, a.key1);
+    const uint4 rnd = philox_rk(make_uint4(w.k, stream, (uint32_t)path, (uint32_t)(path >> 32)), a);
     const T S = Q::mul(Q::neg_ln(Q::unif(rnd)), Q::rate(w.rec, a.node64, w.j));
     if (S >= w.r) {
         w.acc = MODE == MCX_EXACT ? Q::fma(w.delta, w.r, w.acc) : Q::fma(w.delta, Q::from_int(Q::grid(w.r, invdt, N)), w.acc);
@@ -153,14 +193,22 @@ __device__ __forceinline__ bool advance(Walker<F64> &w, const WalkParams &a, uin
     }
     w.r = rn;
     const uint32_t slot = __umulhi(rnd.z, (uint32_t)w.rec.deg);
-    const int64_t e = w.rec.row_start + slot;
-    int32_t c = __ldg(a.edge_col + e);
-    if (WEIGHTED && (w.rec.flags & NODE_WEIGHTED)) {
-        const int2 al = __ldg(reinterpret_cast<const int2 *>(a.alias + e));
-        if (!(rnd.w < (uint32_t)al.y)) c = al.x;
+    int32_t c;
+    if (sw != nullptr && w.j == i0) {
+        uint32_t s2 = slot;
+        if (WEIGHTED && (w.rec.flags & NODE_WEIGHTED) && !(rnd.w < sw->thresh[slot])) s2 = (uint32_t)sw->aslot[slot];
+        c = sw->col[s2];
+        w.rec = sw->rec[s2];
+    } else {
+        const int64_t e = w.rec.row_start + slot;
+        c = __ldg(a.edge_col + e);
+        if (WEIGHTED && (w.rec.flags & NODE_WEIGHTED)) {
+            const int2 al = __ldg(reinterpret_cast<const int2 *>(a.alias + e));
+            if (!(rnd.w < (uint32_t)al.y)) c = al.x;
+        }
+        w.rec = load_node(a.node, c);
     }
     w.j = c;
-    w.rec = load_node(a.node, c);
     w.delta = Q::pot(w.rec, a.node64, c);
     ++w.k;
     return false;
@@ -180,7 +228,7 @@ __device__ __forceinline__ typename P<F64>::T final_logw(const Walker<F64> &w, t
 }
 
 // ---------------------------------------------------------------------------
-// Lane accumulators.
+// Lane accumulators and their warp merges (result in lane 0).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
     const float y = __fsub_rn(x, c);
@@ -189,23 +237,59 @@ __device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
     s = t;
 }
 
+// (h, l) += (h2, l2) for unevaluated float pairs: TwoSum of the high parts, then renormalise.
+__device__ __forceinline__ void pair_add(float &h, float &l, float h2, float l2) {
+    const float s = __fadd_rn(h, h2);
+    const float bp = __fsub_rn(s, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(h2, bp));
+    const float lo = __fadd_rn(__fadd_rn(l, l2), e);
+    h = __fadd_rn(s, lo);
+    l = __fsub_rn(lo, __fsub_rn(h, s));
+}
+
+// Sum of w: compensated (it is the estimate).  Sum of w^2: plain FP32 fma
+// (it only feeds the standard error; ~31 terms per lane keep it within 1e-5).
 struct Acc32 {
     float m = -INFINITY, s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
-    __device__ __forceinline__ void add(float L, double v) {
+    __device__ __forceinline__ void add(float L, float v) {
         if (!(L <= m + 8.0f)) {  // first path, a new larger weight, or a non-finite one
             const float sc = (m == -INFINITY) ? 0.0f : expf(m - L);
-            const float sc2 = sc * sc;
-            s1 *= sc; c1 *= sc; s2 *= sc2; c2 *= sc2;
+            s1 *= sc; c1 *= sc; s2 *= sc * sc;
             m = L;
         }
-        const float wv = __fmul_rn(expf(__fsub_rn(L, m)), __double2float_rn(v));
+        const float wv = __fmul_rn(expf(__fsub_rn(L, m)), v);
         kahan_add(s1, c1, wv);
-        kahan_add(s2, c2, __fmul_rn(wv, wv));
+        s2 = __fmaf_rn(wv, wv, s2);
     }
-    __device__ __forceinline__ double shift() const { return (double)m; }
-    __device__ __forceinline__ double sum1() const { return (double)s1 - (double)c1; }
-    __device__ __forceinline__ double sum2() const { return (double)s2 - (double)c2; }
+    __device__ __forceinline__ void warp_merge(double &S1, double &S2, double &Mw) const {
+        float mw = m;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+        const float sc = (m == -INFINITY) ? 0.0f : expf(__fsub_rn(m, mw));
+        const float sc2 = __fmul_rn(sc, sc);
+        float h1 = __fmul_rn(s1, sc), l1 = __fmul_rn(-c1, sc);
+        float h2 = __fmul_rn(s2, sc2), l2 = __fmul_rn(-c2, sc2);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            pair_add(h1, l1, __shfl_xor_sync(0xffffffffu, h1, o), __shfl_xor_sync(0xffffffffu, l1, o));
+            pair_add(h2, l2, __shfl_xor_sync(0xffffffffu, h2, o), __shfl_xor_sync(0xffffffffu, l2, o));
+        }
+        S1 = (double)h1 + (double)l1;
+        S2 = (double)h2 + (double)l2;
+        Mw = (double)mw;
+    }
 };
+
+__device__ __forceinline__ double warp_max(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
 
 struct Acc64 {
     double m = -INFINITY, s1 = 0.0, s2 = 0.0;
@@ -219,21 +303,14 @@ struct Acc64 {
         s1 = __dadd_rn(s1, wv);
         s2 = __fma_rn(wv, wv, s2);
     }
-    __device__ __forceinline__ double shift() const { return m; }
-    __device__ __forceinline__ double sum1() const { return s1; }
-    __device__ __forceinline__ double sum2() const { return s2; }
+    __device__ __forceinline__ void warp_merge(double &S1, double &S2, double &Mw) const {
+        const double mw = warp_max(m);
+        const double sc = (m == -INFINITY) ? 0.0 : exp(m - mw);
+        S1 = warp_sum(sc * s1);
+        S2 = warp_sum(sc * sc * s2);
+        Mw = mw;
+    }
 };
-
-__device__ __forceinline__ double warp_max(double x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-    return x;
-}
-__device__ __forceinline__ double warp_sum(double x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
 
 // mean and standard error from shifted sums over M paths
 __device__ __forceinline__ void finish_entry(double s1, double s2, double m, double M, double *mean, double *sem,
@@ -249,60 +326,102 @@ __device__ __forceinline__ void finish_entry(double s1, double s2, double m, dou
     if (!isfinite(mv) || !isfinite(se)) atomicOr(status, ST_OVERFLOW);
 }
 
+constexpr double QNAN = __builtin_nan("");
+
 // ---------------------------------------------------------------------------
-// Estimate kernel: one warp per (entry, chunk).
+// Estimate kernel: one warp per (entry, chunk); a block finishes its entries.
 // ---------------------------------------------------------------------------
 template <int MODE, bool WEIGHTED, bool F64>
-__global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkParams a) {
+__global__ void __launch_bounds__(WALK_THREADS, F64 ? WALK_MIN_BLOCKS_F64 : WALK_MIN_BLOCKS_F32)
+    k_walk(const __grid_constant__ WalkParams a) {
     using Q = P<F64>;
     using T = typename Q::T;
     using Acc = typename std::conditional<F64, Acc64, Acc32>::type;
+    __shared__ StageWarp s_stage[WARPS_PER_BLOCK];
+    __shared__ double s_fin[WARPS_PER_BLOCK][3];
+    __shared__ unsigned int s_done;
+    if (threadIdx.x == 0) s_done = 0u;
+    __syncthreads();  // before any warp can arrive at the finish ticket
     const int lane = threadIdx.x & 31;
-    const uint64_t wid = ((uint64_t)blockIdx.x * WALK_THREADS + threadIdx.x) >> 5;
+    const int warp = threadIdx.x >> 5;
+    const uint64_t wid = (uint64_t)blockIdx.x * WARPS_PER_BLOCK + warp;
     const uint64_t n_chunks = (uint64_t)a.n_entries * a.chunks_per_entry;
-    if (wid >= n_chunks) return;  // uniform across the warp
-    const uint64_t e_idx = wid / a.chunks_per_entry;
-    const uint64_t chunk = wid - e_idx * a.chunks_per_entry;
-    const int32_t i = a.entries ? __ldg(a.entries + e_idx) : (int32_t)e_idx;
-    if (i < 0 || (int64_t)i >= a.n) {  // invalid entry: latch the error, write NaN, touch nothing else
-        if (lane == 0) {
-            atomicOr(a.status, ST_BAD_ENTRY);
-            if (a.chunks_per_entry == 1) {
-                a.mean[e_idx] = __longlong_as_double(0x7ff8000000000000ll);
-                if (a.sem) a.sem[e_idx] = __longlong_as_double(0x7ff8000000000000ll);
-            } else {
-                a.partials[wid] = Partial{__longlong_as_double(0x7ff8000000000000ll), 0.0, 0.0};
+    const bool valid = wid < n_chunks;  // uniform across the warp
+    uint64_t e_idx = 0, chunk = 0;
+    int32_t i = 0;
+    bool bad = false;
+    if (valid) {
+        e_idx = wid / a.chunks_per_entry;
+        chunk = wid - e_idx * a.chunks_per_entry;
+        i = a.entries ? __ldg(a.entries + e_idx) : (int32_t)e_idx;
+        bad = i < 0 || (int64_t)i >= a.n;  // invalid entry: flagged, outputs NaN, nothing read
+    }
+    double S1 = 0.0, S2 = 0.0, Mw = QNAN;
+    if (valid && !bad) {
+        const uint64_t p_begin = chunk * a.chunk_len;
+        const uint64_t p_end = min(a.paths, p_begin + a.chunk_len);
+        StageWarp &sw = s_stage[warp];
+        const NodeRec start = load_node(a.node, i);
+        // stage the entry row (FP32 paths only; the FP64 path version reads global memory)
+        const bool staged = !F64 && start.deg <= STAGE;
+        if (lane == 0) sw.start = start;  // every path restarts from this copy
+        if (staged) {
+            for (int k = lane; k < start.deg; k += 32) {
+                const int32_t c = __ldg(a.edge_col + start.row_start + k);
+                sw.col[k] = c;
+                sw.rec[k] = load_node(a.node, c);
+            }
+            __syncwarp();
+            if (WEIGHTED && (start.flags & NODE_WEIGHTED)) {
+                for (int k = lane; k < start.deg; k += 32) {
+                    const AliasEnt al = a.alias[start.row_start + k];
+                    int32_t s2 = k;
+                    for (int q = 0; q < start.deg; ++q)
+                        if (sw.col[q] == al.alias_col) s2 = q;
+                    sw.aslot[k] = s2;
+                    sw.thresh[k] = al.thresh;
+                }
             }
         }
-        return;
-    }
-    const uint64_t p_begin = chunk * a.chunk_len;
-    const uint64_t p_end = min(a.paths, p_begin + a.chunk_len);
+        __syncwarp();
+        const StageWarp *swp = staged ? &sw : nullptr;
+        const T delta_start = Q::pot(start, a.node64, i);
+        const T t0 = F64 ? (T)a.t64 : (T)a.t32;
 
-    const NodeRec start = load_node(a.node, i);
-    const T delta_start = Q::pot(start, a.node64, i);
-    const T t0 = F64 ? (T)a.t64 : (T)a.t32;
-
-    Walker<F64> w;
-    w.rec = start; w.j = i; w.r = t0; w.acc = (T)0; w.delta = delta_start; w.k = 0;
-    uint64_t p = p_begin + lane;
-    bool active = p < p_end;
-    Acc acc;
-    uint32_t jumps = 0;
-    while (__any_sync(0xffffffffu, active)) {
-        if (active) {
-            if (advance<MODE, WEIGHTED, F64>(w, a, (uint32_t)i, a.path_offset + p)) {
+        Walker<F64> w;
+        w.rec = start; w.j = i; w.r = t0; w.acc = (T)0; w.delta = delta_start; w.k = 0;
+        // lane refill: a lane whose path ends takes the next unassigned path of the
+        // chunk (ranked among the lanes finishing in the same iteration), so all
+        // lanes run until the chunk is exhausted and finish within about one path
+        const uint64_t base = a.path_offset + p_begin;
+        const uint32_t len = (uint32_t)(p_end - p_begin);  // chunks are shorter than 2^31 paths
+        uint32_t next = 32;                                // warp-uniform
+        uint32_t p = (uint32_t)lane;
+        bool active = p < len;
+        Acc acc;
+        uint32_t jumps = 0;
+        const unsigned lt_mask = (1u << lane) - 1u;
+        while (__any_sync(0xffffffffu, active)) {
+            bool fin = false;
+            if (active && advance<MODE, WEIGHTED, F64>(w, a, (uint32_t)i, base + p, swp, i)) {
+                fin = true;
                 const T L = final_logw<MODE, F64>(w, delta_start, a);
-                acc.add(L, w.rec.v);
+                if (F64) acc.add(L, __ldg(&a.node64[w.j].v));
+                else acc.add(L, w.rec.v);
                 jumps += w.k;
-                p += 32;
-                active = p < p_end;
-                w.rec = start; w.j = i; w.r = t0; w.acc = (T)0; w.delta = delta_start; w.k = 0;
+            }
+            const unsigned fm = __ballot_sync(0xffffffffu, fin);
+            if (fm) {
+                if (fin) {
+                    p = next + (uint32_t)__popc(fm & lt_mask);
+                    active = p < len;
+                    w.rec = sw.start;
+                    w.j = i; w.r = t0; w.acc = (T)0; w.delta = delta_start; w.k = 0;
+                }
+                next += (uint32_t)__popc(fm);
             }
         }
-    }
-    // walker statistics: paths and jumps of this warp, one atomic per warp
-    {
+        // walker statistics: paths and jumps of this warp, one atomic per warp
         unsigned long long jl = jumps;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) jl += __shfl_xor_sync(0xffffffffu, jl, o);
@@ -311,19 +430,38 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk(const WalkParams a) {
             atomicAdd(ctr, (unsigned long long)(p_end - p_begin));
             atomicAdd(ctr + 1, jl);
         }
+        acc.warp_merge(S1, S2, Mw);
     }
-    // merge lanes (log-sum-exp on the shifts), fixed shuffle tree
-    const double m_lane = acc.shift();
-    const double m_w = warp_max(m_lane);
-    const double sc = (m_lane == -INFINITY) ? 0.0 : exp(m_lane - m_w);
-    const double s1 = warp_sum(sc * acc.sum1());
-    const double s2 = warp_sum(sc * sc * acc.sum2());
-    if (lane == 0) {
-        if (a.chunks_per_entry == 1) {
-            finish_entry(s1, s2, m_w, (double)a.paths, a.mean + e_idx, a.sem ? a.sem + e_idx : nullptr, a.status);
-        } else {
-            a.partials[wid] = Partial{s1, s2, m_w};
+    if (a.chunks_per_entry == 1) {
+        // each warp leaves its sums in shared memory; the last warp of the block
+        // to arrive finishes all of them, one lane per entry (no block barrier)
+        unsigned int ticket = 0;
+        if (lane == 0) {
+            s_fin[warp][0] = S1;
+            s_fin[warp][1] = S2;
+            s_fin[warp][2] = Mw;
+            __threadfence_block();
+            ticket = atomicAdd(&s_done, 1u);
         }
+        ticket = __shfl_sync(0xffffffffu, ticket, 0);
+        if (ticket == WARPS_PER_BLOCK - 1) {
+            __threadfence_block();
+            const uint64_t e = (uint64_t)blockIdx.x * WARPS_PER_BLOCK + lane;
+            if (lane < WARPS_PER_BLOCK && e < n_chunks) {
+                const double m = ((volatile double *)s_fin[lane])[2];
+                if (isnan(m)) {  // invalid entry
+                    atomicOr(a.status, ST_BAD_ENTRY);
+                    a.mean[e] = QNAN;
+                    if (a.sem) a.sem[e] = QNAN;
+                } else {
+                    finish_entry(((volatile double *)s_fin[lane])[0], ((volatile double *)s_fin[lane])[1], m,
+                                 (double)a.paths, a.mean + e, a.sem ? a.sem + e : nullptr, a.status);
+                }
+            }
+        }
+    } else if (valid && lane == 0) {
+        if (bad) atomicOr(a.status, ST_BAD_ENTRY);
+        a.partials[wid] = Partial{bad ? QNAN : S1, S2, bad ? 0.0 : Mw};
     }
 }
 
@@ -351,12 +489,13 @@ __global__ void __launch_bounds__(WALK_THREADS) k_reduce_chunks(const Partial *_
 }
 
 // ---------------------------------------------------------------------------
-// Trace kernel: one thread per path, same stepping code, plus the index hash.
+// Trace kernel: one thread per path, same stepping code (no staging), plus the
+// index hash.
 // ---------------------------------------------------------------------------
 template <int MODE, bool WEIGHTED, bool F64>
-__global__ void __launch_bounds__(WALK_THREADS) k_trace(const WalkParams a, int32_t i, uint64_t first_path,
-                                                       uint32_t count, int32_t *end, uint32_t *njumps,
-                                                       uint64_t *hash, double *logw) {
+__global__ void __launch_bounds__(WALK_THREADS) k_trace(const __grid_constant__ WalkParams a, int32_t i,
+                                                       uint64_t first_path, uint32_t count, int32_t *end,
+                                                       uint32_t *njumps, uint64_t *hash, double *logw) {
     using Q = P<F64>;
     using T = typename Q::T;
     const uint32_t q = blockIdx.x * WALK_THREADS + threadIdx.x;
@@ -367,11 +506,8 @@ __global__ void __launch_bounds__(WALK_THREADS) k_trace(const WalkParams a, int3
     Walker<F64> w;
     w.rec = start; w.j = i; w.r = F64 ? (T)a.t64 : (T)a.t32; w.acc = (T)0; w.delta = delta_start; w.k = 0;
     uint64_t h = (FNV_OFFSET ^ (uint64_t)(uint32_t)i) * FNV_PRIME;
-    for (;;) {
-        const uint32_t k_before = w.k;
-        if (advance<MODE, WEIGHTED, F64>(w, a, (uint32_t)i, path)) break;
-        if (w.k != k_before) h = (h ^ (uint64_t)(uint32_t)w.j) * FNV_PRIME;
-    }
+    while (!advance<MODE, WEIGHTED, F64>(w, a, (uint32_t)i, path, nullptr, i))
+        h = (h ^ (uint64_t)(uint32_t)w.j) * FNV_PRIME;
     end[q] = w.j;
     njumps[q] = w.k;
     hash[q] = h;
@@ -387,24 +523,28 @@ __global__ void k_trace_t0(int32_t i, uint32_t count, int32_t *end, uint32_t *nj
     logw[q] = 0.0;
 }
 
-__global__ void k_pack_v(int64_t n, const double *__restrict__ v, NodeRec *__restrict__ node) {
+__global__ void k_pack_v(int64_t n, const double *__restrict__ v, NodeRec *__restrict__ node,
+                         NodeRec64 *__restrict__ node64) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) node[i].v = v[i];
+    if (i >= n) return;
+    const double x = v[i];
+    node[i].v = __double2float_rn(x);
+    node64[i].v = x;
 }
 
 // t = 0: exp(0 A) v = v.
 __global__ void k_copy_v(const int32_t *__restrict__ entries, int64_t n_entries, int64_t n,
-                         const NodeRec *__restrict__ node, double *mean, double *sem, uint32_t *status) {
+                         const NodeRec64 *__restrict__ node64, double *mean, double *sem, uint32_t *status) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_entries) return;
     const int64_t i = entries ? entries[e] : e;
     if (i < 0 || i >= n) {
         atomicOr(status, ST_BAD_ENTRY);
-        mean[e] = __longlong_as_double(0x7ff8000000000000ll);
-        if (sem) sem[e] = mean[e];
+        mean[e] = QNAN;
+        if (sem) sem[e] = QNAN;
         return;
     }
-    mean[e] = node[i].v;
+    mean[e] = node64[i].v;
     if (sem) sem[e] = 0.0;
 }
 
@@ -444,8 +584,13 @@ WalkParams make_params(mcx_plan *plan, double t, int nsteps, uint64_t seed) {
     p.invdt32 = (float)p.invdt64;
     p.n = plan->n;
     p.max_events = 1u << 30;
-    p.key0 = (uint32_t)seed;
-    p.key1 = (uint32_t)(seed >> 32);
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        p.rk0[r] = k0;
+        p.rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
     p.status = plan->status;
     return p;
 }
@@ -454,7 +599,7 @@ WalkParams make_params(mcx_plan *plan, double t, int nsteps, uint64_t seed) {
 
 cudaError_t launch_pack_v(mcx_plan *plan, const double *v, cudaStream_t st) {
     if (plan->n == 0) return cudaSuccess;
-    k_pack_v<<<(unsigned)((plan->n + 255) / 256), 256, 0, st>>>(plan->n, v, plan->node);
+    k_pack_v<<<(unsigned)((plan->n + 255) / 256), 256, 0, st>>>(plan->n, v, plan->node, plan->node64);
     return cudaGetLastError();
 }
 
@@ -462,7 +607,7 @@ cudaError_t launch_estimate(mcx_plan *plan, const EstimateArgs &a, cudaStream_t 
     if (a.n_entries == 0) return cudaSuccess;
     if (a.t == 0.0) {
         k_copy_v<<<(unsigned)((a.n_entries + 255) / 256), 256, 0, st>>>(a.entries, a.n_entries, plan->n,
-                                                                          plan->node, a.mean, a.sem, plan->status);
+                                                                          plan->node64, a.mean, a.sem, plan->status);
         return cudaGetLastError();
     }
     WalkParams p = make_params(plan, a.t, a.mode == MCX_EXACT ? 1 : a.nsteps, a.seed);
@@ -479,6 +624,7 @@ cudaError_t launch_estimate(mcx_plan *plan, const EstimateArgs &a, cudaStream_t 
     const uint64_t max_cpe = (a.paths + 1023) / 1024;
     if (cpe > max_cpe) cpe = max_cpe;
     if (cpe < 1) cpe = 1;
+    if ((a.paths + cpe - 1) / cpe > (1ull << 30)) cpe = (a.paths + (1ull << 30) - 1) >> 30;  // 32-bit chunk offsets
     uint64_t chunk = (a.paths + cpe - 1) / cpe;
     chunk = (chunk + 31) / 32 * 32;
     cpe = (a.paths + chunk - 1) / chunk;
@@ -589,6 +735,7 @@ cudaError_t launch_estimate_noalloc(mcx_plan *plan, const double *v, const Estim
     const uint64_t max_cpe = (a.paths + 1023) / 1024;
     if (cpe > max_cpe) cpe = max_cpe;
     if (cpe < 1) cpe = 1;
+    if ((a.paths + cpe - 1) / cpe > (1ull << 30)) cpe = (a.paths + (1ull << 30) - 1) >> 30;  // 32-bit chunk offsets
     uint64_t chunk = (a.paths + cpe - 1) / cpe;
     chunk = (chunk + 31) / 32 * 32;
     cpe = (a.paths + chunk - 1) / chunk;
@@ -603,7 +750,7 @@ cudaError_t launch_estimate_noalloc(mcx_plan *plan, const double *v, const Estim
     if ((e = launch_pack_v(plan, v, st)) != cudaSuccess) return e;
     if (a.t == 0.0) {
         k_copy_v<<<(unsigned)((a.n_entries + 255) / 256), 256, 0, st>>>(a.entries, a.n_entries, plan->n,
-                                                                          plan->node, a.mean, a.sem, plan->status);
+                                                                          plan->node64, a.mean, a.sem, plan->status);
         return cudaGetLastError();
     }
     WalkParams p = make_params(plan, a.t, a.mode == MCX_EXACT ? 1 : a.nsteps, a.seed);
