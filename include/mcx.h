@@ -155,6 +155,44 @@ mcx_status mcx_estimate(mcx_plan *plan, const double *v, double t, int functiona
                         void *stream);
 
 /*
+ * Forward estimate (Lemma 2, Theorem 2, Algorithm 2) of the full vector
+ * x = exp(tA) v: total_paths walkers start at j ~ v_j / V (V = sum of v),
+ * walk the rows of the matrix the plan was built from, which must be
+ * B = A^T (A itself when A is symmetric), carry B's multiplicative
+ * functional, and deposit V W at their end state: x_i = (1/M) sum V W 1{X_t = i}.
+ *   v            float64 [n], v >= 0, finite, V > 0 (else NaN outputs and
+ *                MCX_E_NEG_V at mcx_sync)
+ *   t, functional, nsteps, precision, seed as in mcx_estimate; t = 0 returns v
+ *   total_paths  M >= 1; paths path_offset .. path_offset+M-1
+ *   x, sem       float64 [n] outputs (sem may be NULL); sem is the standard
+ *                error of the per-state mean of V W 1{X_t = i}
+ * The start draw is a two-level alias over v: groups of 1024 indices with
+ * sums S_g (summed in index order), V = sum of the S_g (group order), a Vose
+ * table over the groups and one inside each group; one Philox call with
+ * counter {0, 0xFFFFFFFF, path lo32, path hi32} (words 0-1 pick the group,
+ * words 2-3 the member); walk events use counter {k, 0xFFFFFFFE, path}.
+ * When every potential of the plan is exactly zero (B a CTMC generator, so
+ * W = 1) the deposits are exact integer counts, so sum_i x_i = V up to one
+ * rounding per entry; otherwise they are FP64 atomic sums (summation order,
+ * and so the last bits, vary between runs).  The plan allocates its forward
+ * scratch (about 36 n bytes) on first use.
+ * Errors: MCX_E_INVALID, MCX_E_CUDA, MCX_E_OOM.
+ */
+mcx_status mcx_estimate_forward(mcx_plan *plan, const double *v, double t, int functional, int32_t nsteps,
+                                uint64_t total_paths, uint64_t seed, uint64_t path_offset, int precision,
+                                double *x, double *sem, void *stream);
+
+/*
+ * Per-path record of forward paths first_path .. first_path+count-1 (same
+ * arguments as mcx_estimate_forward): start (int32), end (int32), njumps
+ * (uint32), hash (uint64, FNV-1a over the visited indices from the start),
+ * logw (float64).  Errors: MCX_E_INVALID, MCX_E_CUDA.
+ */
+mcx_status mcx_trace_forward(mcx_plan *plan, const double *v, double t, int functional, int32_t nsteps,
+                             uint64_t seed, uint64_t first_path, uint32_t count, int precision, int32_t *start,
+                             int32_t *end, uint32_t *njumps, uint64_t *hash, double *logw, void *stream);
+
+/*
  * mcx_estimate without any device allocation.  The paper has no counterpart:
  * this exists for callers that cannot call cudaMalloc once they are running,
  * e.g. a service that reserves all of its device memory at start-up and must
@@ -232,6 +270,8 @@ mcx_status mcx_plan_export(const mcx_plan *plan, int32_t *deg, int64_t *row_star
 /* Synchronise `stream`, return and clear the plan's latched device status and
  * counters.  stats (host pointer) may be NULL.  Errors: MCX_E_INVALID (an
  * estimate was given an entry outside [0, n); its outputs are NaN),
+ * MCX_E_NEG_V (a forward call got v with a negative or non-finite entry or a
+ * zero sum; its outputs are NaN),
  * MCX_E_OVERFLOW (a result overflowed FP64, or a path reached the cap of 2^30
  * events), MCX_E_CUDA. */
 mcx_status mcx_sync(mcx_plan *plan, void *stream, mcx_stats *stats);

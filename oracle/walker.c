@@ -472,48 +472,89 @@ int oracle_estimate(const oracle_graph *g, const double *v, double t, int mode, 
 
 /* ------------------------------------------------------------------------ */
 /* Forward form (Lemma 2, Theorem 2; Algorithm 2), on the graph of B = A^T:  */
-/* start j ~ v/V from a canonical Vose table over v, walk B's rows with B's  */
-/* potential, deposit V W at the end state.  The start draw uses counter     */
-/* {0, 0xFFFFFFFF, path}; walk events use {k, 0xFFFFFFFE, path}.             */
+/* start j ~ v_j / V, walk B's rows with B's potential, deposit V W at the   */
+/* end state.                                                                */
+/*                                                                           */
+/* The start draw is a two-level alias: the indices are cut into groups of   */
+/* 1024 (the last one ragged); group g has sum S_g (sequential, index order) */
+/* and V = sum of the S_g (sequential, group order).  A canonical Vose table */
+/* over the S_g picks the group, a canonical Vose table over the group's v_j */
+/* picks the member: P(j) = (S_g / V)(v_j / S_g) = v_j / V.  One Philox call */
+/* {0, 0xFFFFFFFF, path}: w0/w1 pick the group, w2/w3 the member.  Walk      */
+/* events use counter {k, 0xFFFFFFFE, path}.                                 */
 /* ------------------------------------------------------------------------ */
-int oracle_start_table(int64_t n, const double *v, int32_t *alias_out, uint32_t *thresh_out, double *vsum_out)
+#define START_GROUP 1024
+
+int oracle_start_table(int64_t n, const double *v, int32_t *top_alias, uint32_t *top_thresh,
+                       int32_t *in_alias, uint32_t *in_thresh, double *vsum_out)
 {
-    double V = 0.0;
-    for (int64_t i = 0; i < n; ++i) {
+    for (int64_t i = 0; i < n; ++i)
         if (!(v[i] >= 0.0) || !isfinite(v[i])) return O_E_INVALID;
-        V += v[i];
+    int64_t G = (n + START_GROUP - 1) / START_GROUP;
+    double *S = (double *)malloc(sizeof(double) * (size_t)(G + 1));
+    double V = 0.0;
+    for (int64_t g = 0; g < G; ++g) {
+        double s = 0.0;
+        int64_t hi = (g + 1) * START_GROUP < n ? (g + 1) * START_GROUP : n;
+        for (int64_t i = g * START_GROUP; i < hi; ++i) s += v[i];
+        S[g] = s;
+        V += s;
     }
     *vsum_out = V;
-    if (!(V > 0.0)) return O_E_INVALID;
-    int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
-    double *q = (double *)malloc(sizeof(double) * (size_t)n);
-    int *sm = (int *)malloc(sizeof(int) * (size_t)n);
-    int *lg = (int *)malloc(sizeof(int) * (size_t)n);
-    for (int64_t i = 0; i < n; ++i) ids[i] = (int32_t)i;
-    vose_row((int)n, v, V, ids, alias_out, thresh_out, q, sm, lg);
-    free(ids); free(q); free(sm); free(lg);
+    if (!(V > 0.0)) {
+        free(S);
+        return O_E_INVALID;
+    }
+    int64_t m = G > START_GROUP ? G : START_GROUP;
+    int32_t *ids = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+    double *q = (double *)malloc(sizeof(double) * (size_t)m);
+    int *sm = (int *)malloc(sizeof(int) * (size_t)m);
+    int *lg = (int *)malloc(sizeof(int) * (size_t)m);
+    for (int64_t g = 0; g < G; ++g) ids[g] = (int32_t)g;
+    vose_row((int)G, S, V, ids, top_alias, top_thresh, q, sm, lg);
+    for (int64_t g = 0; g < G; ++g) {
+        int64_t lo = g * START_GROUP;
+        int d = (int)(((g + 1) * START_GROUP < n ? (g + 1) * START_GROUP : n) - lo);
+        for (int k = 0; k < d; ++k) ids[k] = (int32_t)(lo + k);
+        if (S[g] > 0.0) {
+            vose_row(d, v + lo, S[g], ids, in_alias + lo, in_thresh + lo, q, sm, lg);
+        } else {
+            for (int k = 0; k < d; ++k) {
+                in_alias[lo + k] = (int32_t)(lo + k);
+                in_thresh[lo + k] = 0xFFFFFFFFu;
+            }
+        }
+    }
+    free(S); free(ids); free(q); free(sm); free(lg);
     return O_OK;
 }
 
-static int32_t forward_start(int64_t n, const int32_t *start_alias, const uint32_t *start_thresh,
-                             uint64_t seed, uint64_t path)
+static int32_t forward_start(int64_t n, const int32_t *top_alias, const uint32_t *top_thresh,
+                             const int32_t *in_alias, const uint32_t *in_thresh, uint64_t seed, uint64_t path)
 {
     uint32_t w[4];
     draw(seed, 0u, 0xFFFFFFFFu, path, w);
-    uint32_t slot = (uint32_t)(((uint64_t)w[2] * (uint64_t)n) >> 32);
-    return (w[3] < start_thresh[slot]) ? (int32_t)slot : start_alias[slot];
+    uint64_t G = (uint64_t)((n + START_GROUP - 1) / START_GROUP);
+    int64_t g = (int64_t)(((uint64_t)w[0] * G) >> 32);
+    if (!(w[1] < top_thresh[g])) g = top_alias[g];
+    int64_t lo = g * START_GROUP;
+    uint64_t d = (uint64_t)(((g + 1) * START_GROUP < n ? (g + 1) * START_GROUP : n) - lo);
+    int64_t j = lo + (int64_t)(((uint64_t)w[2] * d) >> 32);
+    if (!(w[3] < in_thresh[j])) j = in_alias[j];
+    return (int32_t)j;
 }
 
 /* Per-state sums over paths path_offset .. path_offset+M-1 of Y = V W 1{X_t = i}
  * (sum1) and Y^2 (sum2).  Then x_i = sum1_i / M. */
-void oracle_forward(const oracle_graph *g, int64_t n, const int32_t *start_alias, const uint32_t *start_thresh,
-                    double V, double t, int mode, int N, int prec, uint64_t M, uint64_t seed,
-                    uint64_t path_offset, double *sum1, double *sum2, uint64_t *jumps_out)
+void oracle_forward(const oracle_graph *g, int64_t n, const int32_t *top_alias, const uint32_t *top_thresh,
+                    const int32_t *in_alias, const uint32_t *in_thresh, double V, double t, int mode, int N,
+                    int prec, uint64_t M, uint64_t seed, uint64_t path_offset, double *sum1, double *sum2,
+                    uint64_t *jumps_out)
 {
     uint64_t jumps = 0;
     for (uint64_t p = 0; p < M; ++p) {
         uint64_t path = path_offset + p;
-        int32_t j0 = forward_start(n, start_alias, start_thresh, seed, path);
+        int32_t j0 = forward_start(n, top_alias, top_thresh, in_alias, in_thresh, seed, path);
         path_out o = one_path_stream(g, j0, 0xFFFFFFFEu, t, mode, N, prec, seed, path);
         double w = V * exp(o.logw);
         sum1[o.end] += w;
@@ -523,13 +564,14 @@ void oracle_forward(const oracle_graph *g, int64_t n, const int32_t *start_alias
     if (jumps_out) *jumps_out = jumps;
 }
 
-void oracle_forward_trace(const oracle_graph *g, int64_t n, const int32_t *start_alias, const uint32_t *start_thresh,
-                          double t, int mode, int N, int prec, uint64_t seed, uint64_t first_path, uint32_t count,
-                          int32_t *start, int32_t *end, uint32_t *njumps, uint64_t *hash, double *logw)
+void oracle_forward_trace(const oracle_graph *g, int64_t n, const int32_t *top_alias, const uint32_t *top_thresh,
+                          const int32_t *in_alias, const uint32_t *in_thresh, double t, int mode, int N, int prec,
+                          uint64_t seed, uint64_t first_path, uint32_t count, int32_t *start, int32_t *end,
+                          uint32_t *njumps, uint64_t *hash, double *logw)
 {
     for (uint32_t q = 0; q < count; ++q) {
         uint64_t path = first_path + q;
-        int32_t j0 = forward_start(n, start_alias, start_thresh, seed, path);
+        int32_t j0 = forward_start(n, top_alias, top_thresh, in_alias, in_thresh, seed, path);
         path_out o = one_path_stream(g, j0, 0xFFFFFFFEu, t, mode, N, prec, seed, path);
         start[q] = j0; end[q] = o.end; njumps[q] = o.njumps; hash[q] = o.hash; logw[q] = o.logw;
     }

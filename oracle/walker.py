@@ -21,6 +21,7 @@ _lock = threading.Lock()
 _lib = None
 
 MODES = {"exact": 0, "strang": 1, "lie": 2}
+START_GROUP = 1024  # group size of the two-level start table (walker.c)
 PRECS = {"fp32": 0, "fp64": 1}
 
 
@@ -70,12 +71,12 @@ def lib():
             L.oracle_estimate.argtypes = [C.POINTER(_Graph), vp, dbl, C.c_int, C.c_int, C.c_int, u64, vp, i64,
                                           u64, u64, vp, vp, vp]
             L.oracle_estimate.restype = C.c_int
-            L.oracle_start_table.argtypes = [i64, vp, vp, vp, vp]
+            L.oracle_start_table.argtypes = [i64, vp, vp, vp, vp, vp, vp]
             L.oracle_start_table.restype = C.c_int
-            L.oracle_forward.argtypes = [C.POINTER(_Graph), i64, vp, vp, dbl, dbl, C.c_int, C.c_int, C.c_int,
-                                         u64, u64, u64, vp, vp, vp]
-            L.oracle_forward_trace.argtypes = [C.POINTER(_Graph), i64, vp, vp, dbl, C.c_int, C.c_int, C.c_int,
-                                               u64, u64, u32, vp, vp, vp, vp, vp]
+            L.oracle_forward.argtypes = [C.POINTER(_Graph), i64, vp, vp, vp, vp, dbl, dbl, C.c_int, C.c_int,
+                                         C.c_int, u64, u64, u64, vp, vp, vp]
+            L.oracle_forward_trace.argtypes = [C.POINTER(_Graph), i64, vp, vp, vp, vp, dbl, C.c_int, C.c_int,
+                                               C.c_int, u64, u64, u32, vp, vp, vp, vp, vp]
             L.oracle_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -157,39 +158,44 @@ class Graph:
 
     # -- forward form (Theorem 2, Algorithm 2); this graph must be that of A^T --
     def start_table(self, v):
+        """Two-level alias tables for the start draw j ~ v/V (Lemma 2)."""
         v = np.ascontiguousarray(v, dtype=np.float64)
-        alias = np.zeros(self.n, np.int32)
-        thresh = np.zeros(self.n, np.uint32)
+        G = (self.n + START_GROUP - 1) // START_GROUP
+        t = {"top_alias": np.zeros(max(G, 1), np.int32), "top_thresh": np.zeros(max(G, 1), np.uint32),
+             "in_alias": np.zeros(self.n, np.int32), "in_thresh": np.zeros(self.n, np.uint32)}
         vs = np.zeros(1)
-        st = int(lib().oracle_start_table(self.n, _p(v), _p(alias), _p(thresh), _p(vs)))
-        return st, alias, thresh, float(vs[0])
+        st = int(lib().oracle_start_table(self.n, _p(v), _p(t["top_alias"]), _p(t["top_thresh"]),
+                                          _p(t["in_alias"]), _p(t["in_thresh"]), _p(vs)))
+        t["V"] = float(vs[0])
+        return st, t
+
+    def _tables(self, v):
+        st, t = self.start_table(v)
+        if st != 0:
+            raise ValueError("forward form needs v >= 0 with a positive sum")
+        return t, [_p(t[k]) for k in ("top_alias", "top_thresh", "in_alias", "in_thresh")]
 
     def forward(self, v, t, total_paths, seed=0, path_offset=0, mode="exact", nsteps=1, prec="fp32"):
         """Full-vector estimate x_i = V E[W 1{X_t=i}] with its standard error."""
-        st, alias, thresh, V = self.start_table(v)
-        if st != 0:
-            raise ValueError("forward form needs v >= 0 with a positive sum")
+        tab, ptrs = self._tables(v)
         s1 = np.zeros(self.n)
         s2 = np.zeros(self.n)
         jumps = np.zeros(1, np.uint64)
-        lib().oracle_forward(C.byref(self._g), self.n, _p(alias), _p(thresh), V, float(t), MODES[mode],
-                             int(nsteps), PRECS[prec], int(total_paths), int(seed), int(path_offset),
-                             _p(s1), _p(s2), _p(jumps))
+        lib().oracle_forward(C.byref(self._g), self.n, *ptrs, tab["V"], float(t), MODES[mode], int(nsteps),
+                             PRECS[prec], int(total_paths), int(seed), int(path_offset), _p(s1), _p(s2),
+                             _p(jumps))
         M = float(total_paths)
         x = s1 / M
         var = np.maximum(s2 / M - x * x, 0.0) * (M / max(M - 1.0, 1.0))
         return x, np.sqrt(var / M), int(jumps[0])
 
     def forward_trace(self, v, t, seed, first_path, count, mode="exact", nsteps=1, prec="fp32"):
-        st, alias, thresh, _ = self.start_table(v)
-        if st != 0:
-            raise ValueError("forward form needs v >= 0 with a positive sum")
+        tab, ptrs = self._tables(v)
         out = {k: np.zeros(count, dt) for k, dt in (("start", np.int32), ("end", np.int32), ("njumps", np.uint32),
                                                     ("hash", np.uint64), ("logw", np.float64))}
-        lib().oracle_forward_trace(C.byref(self._g), self.n, _p(alias), _p(thresh), float(t), MODES[mode],
-                                   int(nsteps), PRECS[prec], int(seed), int(first_path), int(count),
-                                   _p(out["start"]), _p(out["end"]), _p(out["njumps"]), _p(out["hash"]),
-                                   _p(out["logw"]))
+        lib().oracle_forward_trace(C.byref(self._g), self.n, *ptrs, float(t), MODES[mode], int(nsteps),
+                                   PRECS[prec], int(seed), int(first_path), int(count), _p(out["start"]),
+                                   _p(out["end"]), _p(out["njumps"]), _p(out["hash"]), _p(out["logw"]))
         return out
 
 

@@ -17,6 +17,8 @@ EXPORTS = (
     "mcx_plan_get_info",
     "mcx_estimate",
     "mcx_estimate_noalloc",
+    "mcx_estimate_forward",
+    "mcx_trace_forward",
     "mcx_trace_paths",
     "mcx_power_iteration",
     "mcx_plan_export",
@@ -73,6 +75,10 @@ def load(path: str = LIB_PATH):
     L.mcx_estimate.restype = st
     L.mcx_estimate_noalloc.argtypes = [vp, vp, dbl, C.c_int, i32, u64, vp, i64, u64, u64, C.c_int, vp, vp, vp]
     L.mcx_estimate_noalloc.restype = st
+    L.mcx_estimate_forward.argtypes = [vp, vp, dbl, C.c_int, i32, u64, u64, u64, C.c_int, vp, vp, vp]
+    L.mcx_estimate_forward.restype = st
+    L.mcx_trace_forward.argtypes = [vp, vp, dbl, C.c_int, i32, u64, u64, u32, C.c_int, vp, vp, vp, vp, vp, vp]
+    L.mcx_trace_forward.restype = st
     L.mcx_trace_paths.argtypes = [vp, dbl, C.c_int, i32, i32, u64, u64, u32, C.c_int, vp, vp, vp, vp, vp]
     L.mcx_trace_paths.restype = st
     L.mcx_power_iteration.argtypes = [i64, vp, vp, vp, i32, dbl, vp, C.POINTER(dbl), C.POINTER(i32), vp]

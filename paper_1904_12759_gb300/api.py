@@ -120,6 +120,44 @@ class Plan:
                                 _stream(stream)), "mcx_trace_paths")
         return out
 
+    def forward(self, v: torch.Tensor, t: float, paths: int, seed: int = 0, path_offset: int = 0,
+                mode: str = "exact", nsteps: int = 1, prec: str = "fp32", out: tuple | None = None, stream=None):
+        """Forward full-vector estimate (Theorem 2, Algorithm 2); this plan must be built from A^T.
+
+        Returns (x, sem) float64 CUDA tensors of length n."""
+        p_v = _dev(v, torch.float64, "v")
+        if v.numel() != self.n:
+            raise ValueError("v must have n entries")
+        if out is None:
+            x = torch.empty(self.n, dtype=torch.float64, device=v.device)
+            sem = torch.empty(self.n, dtype=torch.float64, device=v.device)
+        else:
+            x, sem = out
+        p_sem = _dev(sem, torch.float64, "sem") if sem is not None else 0
+        check(_lib.load().mcx_estimate_forward(self._h, C.c_void_p(p_v), float(t), FUNCTIONALS[mode], int(nsteps),
+                                               int(paths), int(seed), int(path_offset), PRECISIONS[prec],
+                                               C.c_void_p(_dev(x, torch.float64, "x")), C.c_void_p(p_sem),
+                                               _stream(stream)), "mcx_estimate_forward")
+        return x, sem
+
+    def trace_forward(self, v: torch.Tensor, t: float, seed: int, first_path: int, count: int, mode: str = "exact",
+                      nsteps: int = 1, prec: str = "fp32", stream=None) -> dict:
+        dev = v.device
+        out = {
+            "start": torch.empty(count, dtype=torch.int32, device=dev),
+            "end": torch.empty(count, dtype=torch.int32, device=dev),
+            "njumps": torch.empty(count, dtype=torch.int32, device=dev),
+            "hash": torch.empty(count, dtype=torch.int64, device=dev),
+            "logw": torch.empty(count, dtype=torch.float64, device=dev),
+        }
+        check(_lib.load().mcx_trace_forward(self._h, C.c_void_p(_dev(v, torch.float64, "v")), float(t),
+                                            FUNCTIONALS[mode], int(nsteps), int(seed), int(first_path), int(count),
+                                            PRECISIONS[prec],
+                                            *[C.c_void_p(out[k].data_ptr()) for k in ("start", "end", "njumps",
+                                                                                      "hash", "logw")],
+                                            _stream(stream)), "mcx_trace_forward")
+        return out
+
     def export(self, stream=None) -> dict:
         """Copy the plan's preparation results (rates, potentials, jump tables) to new CUDA tensors."""
         inf = self.info()

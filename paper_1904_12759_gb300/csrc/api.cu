@@ -28,6 +28,7 @@ void free_plan(mcx_plan *p) {
     cudaFree(p->alias);
     cudaFree(p->status);
     cudaFree(p->scratch);
+    cudaFree(p->fwd);
     delete p;
 }
 
@@ -122,7 +123,7 @@ mcx_status mcx_plan_get_info(const mcx_plan *p, mcx_plan_info *info) {
     info->weighted_rows = p->weighted_rows;
     info->max_deg = p->max_deg;
     info->reserved = 0;
-    info->device_bytes = p->device_bytes + (int64_t)p->scratch_bytes;
+    info->device_bytes = p->device_bytes + (int64_t)p->scratch_bytes + (int64_t)p->fwd_bytes;
     return MCX_OK;
 }
 
@@ -189,6 +190,33 @@ mcx_status mcx_estimate_noalloc(mcx_plan *p, const double *v, double t, int func
     return from_cuda(e);
 }
 
+mcx_status mcx_estimate_forward(mcx_plan *p, const double *v, double t, int functional, int32_t nsteps,
+                                uint64_t total_paths, uint64_t seed, uint64_t path_offset, int precision, double *x,
+                                double *sem, void *stream) {
+    mcx_status rc = check_common(p, t, functional, nsteps, precision);
+    if (rc != MCX_OK) return rc;
+    if (p->n == 0) return MCX_OK;
+    if (!v || !x || total_paths < 1 || total_paths > (1ull << 53)) return MCX_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (t == 0.0) {  // exp(0 A) v = v
+        cudaError_t e = cudaMemcpyAsync(x, v, sizeof(double) * (size_t)p->n, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && sem) e = cudaMemsetAsync(sem, 0, sizeof(double) * (size_t)p->n, st);
+        return from_cuda(e);
+    }
+    return from_cuda(launch_estimate_forward(p, v, t, functional, nsteps, total_paths, seed, path_offset, precision,
+                                             x, sem, st));
+}
+
+mcx_status mcx_trace_forward(mcx_plan *p, const double *v, double t, int functional, int32_t nsteps, uint64_t seed,
+                             uint64_t first_path, uint32_t count, int precision, int32_t *start, int32_t *end,
+                             uint32_t *njumps, uint64_t *hash, double *logw, void *stream) {
+    mcx_status rc = check_common(p, t, functional, nsteps, precision);
+    if (rc != MCX_OK) return rc;
+    if (!v || !start || !end || !njumps || !hash || !logw) return MCX_E_INVALID;
+    return from_cuda(launch_trace_forward(p, v, t, functional, nsteps, seed, first_path, count, precision, start, end,
+                                          njumps, hash, logw, static_cast<cudaStream_t>(stream)));
+}
+
 mcx_status mcx_trace_paths(mcx_plan *p, double t, int functional, int32_t nsteps, int32_t entry, uint64_t seed,
                            uint64_t first_path, uint32_t count, int precision, int32_t *end, uint32_t *njumps,
                            uint64_t *hash, double *logw, void *stream) {
@@ -238,6 +266,7 @@ mcx_status mcx_sync(mcx_plan *p, void *stream, mcx_stats *stats) {
         stats->reserved = 0;
     }
     if (hs[0] & ST_BAD_ENTRY) return MCX_E_INVALID;
+    if (hs[0] & ST_BAD_V) return MCX_E_NEG_V;
     return (hs[0] & ST_OVERFLOW) ? MCX_E_OVERFLOW : MCX_OK;
 }
 

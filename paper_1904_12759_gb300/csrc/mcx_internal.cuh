@@ -59,6 +59,7 @@ constexpr uint32_t ST_BAD_STRUCT = 2u;
 constexpr uint32_t ST_NEG_OFFDIAG = 4u;
 constexpr uint32_t ST_NONFINITE = 8u;
 constexpr uint32_t ST_BAD_ENTRY = 16u;
+constexpr uint32_t ST_BAD_V = 32u;
 
 }  // namespace mcx
 
@@ -76,6 +77,9 @@ struct mcx_plan {
     uint32_t *status = nullptr;        // device words: [0] status bits, [2..3] paths (u64), [4..5] jumps (u64)
     void *scratch = nullptr;           // grow-only scratch for chunk partials
     size_t scratch_bytes = 0;
+    void *fwd = nullptr;               // forward-form scratch (start tables, deposits), made on first use
+    size_t fwd_bytes = 0;
+    bool zero_potential = false;       // every delta_i == 0 exactly (forward weights are 1)
     int64_t device_bytes = 0;
 };
 
@@ -179,6 +183,36 @@ __device__ __forceinline__ NodeRec load_node(const NodeRec *__restrict__ node, i
     return r;
 }
 
+// Canonical Vose alias construction for d weights w[0..d) with sum lam (one
+// thread, FP64): scaled weights q_k = (w_k d) / lam; indices with q < 1 go to
+// the "small" list, the rest to "large", both in index order; pairs are popped
+// from the back; the large entry keeps (q_l + q_s) - 1; leftovers alias
+// themselves.  out[k] = {id(alias slot), floor(q_k 2^32)}; keep-own-slot iff a
+// uniform word is below the threshold.  q and stack are d-element scratch.
+template <typename IdF>
+__device__ void vose_build(int32_t d, const double *__restrict__ w, double lam, IdF id, AliasEnt *__restrict__ out,
+                           double *__restrict__ q, int32_t *__restrict__ stack) {
+    // two stacks in d slots: "small" grows up from the bottom, "large" down from the top
+    int32_t ns = 0, nl = 0;
+    for (int32_t k = 0; k < d; ++k) {
+        const double s = __ddiv_rn(__dmul_rn(w[k], (double)d), lam);
+        q[k] = s;
+        out[k] = AliasEnt{id(k), 0xFFFFFFFFu};
+        if (s < 1.0) stack[ns++] = k;
+        else stack[d - 1 - nl++] = k;
+    }
+    while (ns > 0 && nl > 0) {
+        const int32_t sm = stack[--ns];
+        const int32_t lg = stack[d - 1 - (--nl)];
+        const double qs = q[sm];
+        out[sm] = AliasEnt{id(lg), (uint32_t)__double2ull_rz(__dmul_rn(qs, 4294967296.0))};
+        const double ql = __dsub_rn(__dadd_rn(q[lg], qs), 1.0);
+        q[lg] = ql;
+        if (ql < 1.0) stack[ns++] = lg;
+        else stack[d - 1 - nl++] = lg;
+    }
+}
+
 // Host-side launch helpers (defined in the .cu files).
 cudaError_t launch_prep(mcx_plan *plan, const int64_t *row_ptr, const int32_t *col, const double *val,
                         cudaStream_t st, uint32_t *host_status);
@@ -204,6 +238,12 @@ cudaError_t launch_estimate(mcx_plan *plan, const EstimateArgs &a, cudaStream_t 
 cudaError_t launch_estimate_noalloc(mcx_plan *plan, const double *v, const EstimateArgs &a, cudaStream_t st,
                                     bool *too_large);
 uint64_t noalloc_max_partials();
+cudaError_t launch_estimate_forward(mcx_plan *plan, const double *v, double t, int mode, int nsteps, uint64_t paths,
+                                    uint64_t seed, uint64_t path_offset, int precision, double *x, double *sem,
+                                    cudaStream_t st);
+cudaError_t launch_trace_forward(mcx_plan *plan, const double *v, double t, int mode, int nsteps, uint64_t seed,
+                                 uint64_t first_path, uint32_t count, int precision, int32_t *start, int32_t *end,
+                                 uint32_t *njumps, uint64_t *hash, double *logw, cudaStream_t st);
 cudaError_t launch_trace(mcx_plan *plan, double t, int mode, int nsteps, int32_t entry, uint64_t seed,
                          uint64_t first_path, uint32_t count, int precision, int32_t *end, uint32_t *njumps,
                          uint64_t *hash, double *logw, cudaStream_t st);

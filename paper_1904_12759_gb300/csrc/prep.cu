@@ -35,6 +35,8 @@ struct PrepTotals {
     unsigned long long weighted_rows;
     int max_deg;
     uint32_t status;
+    uint32_t nonzero_potential;
+    uint32_t pad;
 };
 
 __global__ void k_prep_rows(int64_t n, int64_t nnz, const int64_t *__restrict__ row_ptr,
@@ -92,6 +94,7 @@ __global__ void k_prep_rows(int64_t n, int64_t nnz, const int64_t *__restrict__ 
         d = 0;
     }
     deg_out[i] = d;
+    if (delta != 0.0) atomicOr(&tot->nonzero_potential, 1u);
     NodeRec r;
     r.row_start = 0;  // filled by the scan
     r.deg = d;
@@ -225,28 +228,8 @@ __global__ void k_prep_fill(int64_t n, const int64_t *__restrict__ row_ptr, cons
         }
     }
     if (!(r.flags & NODE_WEIGHTED)) return;
-    // Two stacks in the row's d slots of `stack`: "small" grows up from the bottom,
-    // "large" grows down from the top; the lists are disjoint subsets of the d
-    // slots, so they never meet.  Both are filled in index order.
-    int32_t *const base = stack + o;
-    int32_t ns = 0, nl = 0;
-    for (int32_t q = 0; q < d; ++q) {
-        const double s = __ddiv_rn(__dmul_rn(qbuf[o + q], (double)d), lam);
-        qbuf[o + q] = s;
-        alias[o + q] = AliasEnt{edge_col[o + q], 0xFFFFFFFFu};
-        if (s < 1.0) base[ns++] = q;
-        else base[d - 1 - nl++] = q;
-    }
-    while (ns > 0 && nl > 0) {
-        const int32_t s = base[--ns];
-        const int32_t l = base[d - 1 - (--nl)];
-        const double qs = qbuf[o + s];
-        alias[o + s] = AliasEnt{edge_col[o + l], (uint32_t)__double2ull_rz(__dmul_rn(qs, 4294967296.0))};
-        const double ql = __dsub_rn(__dadd_rn(qbuf[o + l], qs), 1.0);
-        qbuf[o + l] = ql;
-        if (ql < 1.0) base[ns++] = l;
-        else base[d - 1 - nl++] = l;
-    }
+    const int32_t *cols = edge_col + o;
+    vose_build(d, qbuf + o, lam, [cols](int32_t k) { return cols[k]; }, alias + o, qbuf + o, stack + o);
 }
 
 __global__ void k_export_rows(int64_t n, const NodeRec *__restrict__ node, const NodeRec64 *__restrict__ node64,
@@ -326,6 +309,7 @@ cudaError_t launch_prep(mcx_plan *plan, const int64_t *row_ptr, const int32_t *c
         plan->nnz_off = (int64_t)tot.nnz_off;
         plan->max_deg = tot.max_deg;
         plan->weighted_rows = (int64_t)tot.weighted_rows;
+        plan->zero_potential = tot.nonzero_potential == 0;
         const size_t m = (size_t)(plan->nnz_off > 0 ? plan->nnz_off : 1);
         if ((err = cudaMalloc(&plan->edge_col, sizeof(int32_t) * m)) != cudaSuccess) break;
         plan->device_bytes += (int64_t)(sizeof(int32_t) * m);

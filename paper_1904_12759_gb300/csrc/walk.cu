@@ -548,6 +548,221 @@ __global__ void k_copy_v(const int32_t *__restrict__ entries, int64_t n_entries,
     if (sem) sem[e] = 0.0;
 }
 
+// ---------------------------------------------------------------------------
+// Forward form (Lemma 2, Theorem 2, Algorithm 2) on the plan of B = A^T.
+//
+// Start draw j ~ v_j / V by a two-level alias: groups of START_GROUP indices
+// (the last one ragged) with sums S_g summed in index order, V = sum of the
+// S_g in group order; a canonical Vose table over the S_g picks the group and
+// one over the group's v_j picks the member.  One Philox block per start,
+// counter {0, 0xFFFFFFFF, path}: words 0/1 pick the group, words 2/3 the
+// member.  Walk events use counter {k, 0xFFFFFFFE, path}.  Each path deposits
+// V W at its end state: exact integer counts when every potential is zero
+// (W = 1, e.g. a CTMC generator), FP64 atomic sums of V W and (V W)^2
+// otherwise.
+// ---------------------------------------------------------------------------
+constexpr int64_t START_GROUP = 1024;
+constexpr uint32_t FWD_START_STREAM = 0xFFFFFFFFu;
+constexpr uint32_t FWD_WALK_STREAM = 0xFFFFFFFEu;
+
+struct FwdTables {
+    const AliasEnt *top;  // [G]
+    const AliasEnt *in;   // [n]
+    int64_t n;
+    uint64_t G;
+    const double *V;      // device scalar
+    const uint32_t *bad;  // device flag: v invalid
+};
+
+// Group sums in index order; flags negative / non-finite entries.
+__global__ void k_group_sums(int64_t n, const double *__restrict__ v, double *__restrict__ S, uint32_t *bad) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t G = (n + START_GROUP - 1) / START_GROUP;
+    if (g >= G) return;
+    const int64_t lo = g * START_GROUP, hi = min(n, lo + START_GROUP);
+    double s = 0.0;
+    bool b = false;
+    for (int64_t i = lo; i < hi; ++i) {
+        const double x = v[i];
+        if (!(x >= 0.0) || !isfinite(x)) b = true;
+        s = __dadd_rn(s, x);
+    }
+    S[g] = s;
+    if (b) atomicOr(bad, 1u);
+}
+
+// V = sum of the group sums (group order) and the top-level table (one thread).
+__global__ void k_top_table(int64_t G, const double *__restrict__ S, AliasEnt *top, double *q, int32_t *stack,
+                            double *V, uint32_t *bad) {
+    double s = 0.0;
+    for (int64_t g = 0; g < G; ++g) s = __dadd_rn(s, S[g]);
+    *V = s;
+    if (!(s > 0.0) || !isfinite(s) || *bad) {
+        atomicOr(bad, 1u);
+        for (int64_t g = 0; g < G; ++g) top[g] = AliasEnt{(int32_t)g, 0xFFFFFFFFu};
+        return;
+    }
+    vose_build((int32_t)G, S, s, [](int32_t k) { return k; }, top, q, stack);
+}
+
+// Member tables, one thread per group (all-zero groups are never drawn).
+__global__ void k_inner_tables(int64_t n, const double *__restrict__ v, const double *__restrict__ S, AliasEnt *in,
+                               double *q, int32_t *stack) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t G = (n + START_GROUP - 1) / START_GROUP;
+    if (g >= G) return;
+    const int64_t lo = g * START_GROUP;
+    const int32_t d = (int32_t)(min(n, lo + START_GROUP) - lo);
+    if (S[g] > 0.0) {
+        vose_build(d, v + lo, S[g], [lo](int32_t k) { return (int32_t)(lo + k); }, in + lo, q + lo, stack + lo);
+    } else {
+        for (int32_t k = 0; k < d; ++k) in[lo + k] = AliasEnt{(int32_t)(lo + k), 0xFFFFFFFFu};
+    }
+}
+
+__device__ __forceinline__ int32_t forward_start(const FwdTables &f, const WalkParams &a, uint64_t path) {
+    const uint4 w = philox_rk(make_uint4(0u, FWD_START_STREAM, (uint32_t)path, (uint32_t)(path >> 32)), a);
+    int64_t g = (int64_t)(((unsigned long long)w.x * f.G) >> 32);
+    const AliasEnt tg = f.top[g];
+    if (!(w.y < tg.thresh)) g = tg.alias_col;
+    const int64_t lo = g * START_GROUP;
+    const uint32_t d = (uint32_t)(min(f.n, lo + START_GROUP) - lo);
+    int64_t j = lo + __umulhi(w.z, d);
+    const AliasEnt tj = f.in[j];
+    if (!(w.w < tj.thresh)) j = tj.alias_col;
+    return (int32_t)j;
+}
+
+struct FwdOut {
+    unsigned long long *count;  // [n], zero-potential plans
+    double *sum1;               // [n] sum of V W
+    double *sum2;               // [n] sum of (V W)^2
+};
+
+template <int MODE, bool WEIGHTED, bool F64, bool COUNT>
+__global__ void __launch_bounds__(WALK_THREADS, F64 ? WALK_MIN_BLOCKS_F64 : WALK_MIN_BLOCKS_F32)
+    k_walk_forward(const __grid_constant__ WalkParams a, const __grid_constant__ FwdTables f, FwdOut o) {
+    using Q = P<F64>;
+    using T = typename Q::T;
+    const int lane = threadIdx.x & 31;
+    const uint64_t wid = ((uint64_t)blockIdx.x * WALK_THREADS + threadIdx.x) >> 5;
+    const uint64_t p_begin = wid * a.chunk_len;
+    if (p_begin >= a.paths || *f.bad) return;  // uniform across the warp
+    const uint32_t len = (uint32_t)(min(a.paths, p_begin + a.chunk_len) - p_begin);
+    const uint64_t base = a.path_offset + p_begin;
+    const T t0 = F64 ? (T)a.t64 : (T)a.t32;
+    const double V = *f.V;
+    uint32_t next = 32;
+    uint32_t p = (uint32_t)lane;
+    bool active = p < len;
+    int32_t i0 = 0;
+    T delta_start = (T)0;
+    Walker<F64> w;
+    auto start_path = [&]() {
+        i0 = forward_start(f, a, base + p);
+        w.rec = load_node(a.node, i0);
+        w.j = i0; w.r = t0; w.acc = (T)0; w.k = 0;
+        delta_start = Q::pot(w.rec, a.node64, i0);
+        w.delta = delta_start;
+    };
+    if (active) start_path();
+    uint32_t jumps = 0;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    while (__any_sync(0xffffffffu, active)) {
+        bool fin = false;
+        if (active && advance<MODE, WEIGHTED, F64>(w, a, FWD_WALK_STREAM, base + p, nullptr, -1)) {
+            fin = true;
+            jumps += w.k;
+            if (COUNT) {
+                atomicAdd(o.count + w.j, 1ull);
+            } else {
+                const T L = final_logw<MODE, F64>(w, delta_start, a);
+                const double y = V * (F64 ? exp((double)L) : (double)expf((float)L));
+                atomicAdd(o.sum1 + w.j, y);
+                atomicAdd(o.sum2 + w.j, y * y);
+            }
+        }
+        const unsigned fm = __ballot_sync(0xffffffffu, fin);
+        if (fm) {
+            if (fin) {
+                p = next + (uint32_t)__popc(fm & lt_mask);
+                active = p < len;
+                if (active) start_path();
+            }
+            next += (uint32_t)__popc(fm);
+        }
+    }
+    unsigned long long jl = jumps;
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) jl += __shfl_xor_sync(0xffffffffu, jl, sh);
+    if (lane == 0) {
+        unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.status + 2);
+        atomicAdd(ctr, (unsigned long long)len);
+        atomicAdd(ctr + 1, jl);
+    }
+}
+
+// x_i = (sum of V W 1{end = i}) / M and its standard error.
+__global__ void k_forward_finish(int64_t n, FwdOut o, const double *Vp, const uint32_t *bad, double M, double *x,
+                                 double *sem, uint32_t *status) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (*bad) {
+        x[i] = QNAN;
+        if (sem) sem[i] = QNAN;
+        if (i == 0) atomicOr(status, ST_BAD_V);
+        return;
+    }
+    double s1, s2;
+    if (o.count) {
+        const double c = (double)o.count[i];
+        const double V = *Vp;
+        s1 = V * c;
+        s2 = V * V * c;
+    } else {
+        s1 = o.sum1[i];
+        s2 = o.sum2[i];
+    }
+    const double mu = s1 / M;
+    double var = M > 1.0 ? (s2 - s1 * mu) / (M - 1.0) : 0.0;
+    if (var < 0.0) var = 0.0;
+    x[i] = mu;
+    if (sem) sem[i] = sqrt(var / M);
+    if (!isfinite(mu)) atomicOr(status, ST_OVERFLOW);
+}
+
+template <int MODE, bool WEIGHTED, bool F64>
+__global__ void __launch_bounds__(WALK_THREADS) k_trace_forward(const __grid_constant__ WalkParams a,
+                                                               const __grid_constant__ FwdTables f,
+                                                               uint64_t first_path, uint32_t count, int32_t *start,
+                                                               int32_t *end, uint32_t *njumps, uint64_t *hash,
+                                                               double *logw) {
+    using Q = P<F64>;
+    using T = typename Q::T;
+    const uint32_t q = blockIdx.x * WALK_THREADS + threadIdx.x;
+    if (q >= count) return;
+    if (*f.bad) {
+        if (q == 0) atomicOr(a.status, ST_BAD_V);
+        return;
+    }
+    const uint64_t path = first_path + q;
+    const int32_t i = forward_start(f, a, path);
+    Walker<F64> w;
+    w.rec = load_node(a.node, i);
+    const T delta_start = Q::pot(w.rec, a.node64, i);
+    w.j = i; w.r = F64 ? (T)a.t64 : (T)a.t32; w.acc = (T)0; w.delta = delta_start; w.k = 0;
+    uint64_t h = (FNV_OFFSET ^ (uint64_t)(uint32_t)i) * FNV_PRIME;
+    if (a.t64 != 0.0) {
+        while (!advance<MODE, WEIGHTED, F64>(w, a, FWD_WALK_STREAM, path, nullptr, -1))
+            h = (h ^ (uint64_t)(uint32_t)w.j) * FNV_PRIME;
+    }
+    start[q] = i;
+    end[q] = w.j;
+    njumps[q] = w.k;
+    hash[q] = h;
+    logw[q] = a.t64 != 0.0 ? (double)final_logw<MODE, F64>(w, delta_start, a) : 0.0;
+}
+
 template <bool F64, bool WEIGHTED>
 cudaError_t launch_walk_mode(int mode, unsigned grid, const WalkParams &p, cudaStream_t st) {
     switch (mode) {
@@ -659,6 +874,160 @@ cudaError_t launch_estimate(mcx_plan *plan, const EstimateArgs &a, cudaStream_t 
         e = cudaGetLastError();
     }
     return e;
+}
+
+namespace {
+
+// Forward scratch: S[G], top[G], in[n], q[max(n,G)], stack[max(n,G)], V, bad, deposits[2n].
+struct FwdScratch {
+    double *S;
+    AliasEnt *top;
+    AliasEnt *in;
+    double *q;
+    int32_t *stack;
+    double *V;
+    uint32_t *bad;
+    double *dep;  // 2n doubles (sum1, sum2) or n u64 counts
+};
+
+cudaError_t fwd_scratch(mcx_plan *plan, FwdScratch *fs) {
+    const int64_t n = plan->n;
+    const int64_t G = (n + START_GROUP - 1) / START_GROUP;
+    const int64_t m = n > G ? n : G;
+    const size_t need = 8 * (size_t)G * 2 + 8 * (size_t)n + 8 * (size_t)m + 4 * (size_t)m + 64 + 16 * (size_t)n + 256;
+    if (plan->fwd_bytes < need) {
+        cudaFree(plan->fwd);
+        plan->fwd = nullptr;
+        plan->fwd_bytes = 0;
+        cudaError_t e = cudaMalloc(&plan->fwd, need);
+        if (e != cudaSuccess) return e;
+        plan->fwd_bytes = need;
+    }
+    char *b = static_cast<char *>(plan->fwd);
+    auto take = [&b](size_t bytes) {
+        char *r = b;
+        b += (bytes + 255) / 256 * 256;
+        return r;
+    };
+    fs->dep = reinterpret_cast<double *>(take(16 * (size_t)n));
+    fs->S = reinterpret_cast<double *>(take(8 * (size_t)G));
+    fs->top = reinterpret_cast<AliasEnt *>(take(8 * (size_t)G));
+    fs->in = reinterpret_cast<AliasEnt *>(take(8 * (size_t)n));
+    fs->q = reinterpret_cast<double *>(take(8 * (size_t)m));
+    fs->stack = reinterpret_cast<int32_t *>(take(4 * (size_t)m));
+    fs->V = reinterpret_cast<double *>(take(8));
+    fs->bad = reinterpret_cast<uint32_t *>(take(8));
+    return cudaSuccess;
+}
+
+// Build the two-level start tables on `st`; fills the FwdTables view.
+cudaError_t build_start_tables(mcx_plan *plan, const double *v, const FwdScratch &fs, FwdTables *f, cudaStream_t st) {
+    const int64_t n = plan->n;
+    const int64_t G = (n + START_GROUP - 1) / START_GROUP;
+    cudaError_t e = cudaMemsetAsync(fs.bad, 0, 4, st);
+    if (e != cudaSuccess) return e;
+    const unsigned gb = (unsigned)((G + 127) / 128);
+    k_group_sums<<<gb, 128, 0, st>>>(n, v, fs.S, fs.bad);
+    k_top_table<<<1, 1, 0, st>>>(G, fs.S, fs.top, fs.q, fs.stack, fs.V, fs.bad);
+    k_inner_tables<<<gb, 128, 0, st>>>(n, v, fs.S, fs.in, fs.q, fs.stack);
+    f->top = fs.top;
+    f->in = fs.in;
+    f->n = n;
+    f->G = (uint64_t)G;
+    f->V = fs.V;
+    f->bad = fs.bad;
+    return cudaGetLastError();
+}
+
+template <bool F64, bool WEIGHTED, bool COUNT>
+void launch_fwd(int mode, unsigned grid, const WalkParams &p, const FwdTables &f, const FwdOut &o, cudaStream_t st) {
+    switch (mode) {
+        case MCX_EXACT: k_walk_forward<MCX_EXACT, WEIGHTED, F64, COUNT><<<grid, WALK_THREADS, 0, st>>>(p, f, o); break;
+        case MCX_STRANG: k_walk_forward<MCX_STRANG, WEIGHTED, F64, COUNT><<<grid, WALK_THREADS, 0, st>>>(p, f, o); break;
+        default: k_walk_forward<MCX_LIE, WEIGHTED, F64, COUNT><<<grid, WALK_THREADS, 0, st>>>(p, f, o); break;
+    }
+}
+
+template <bool F64, bool WEIGHTED>
+void launch_fwd_trace(int mode, unsigned grid, const WalkParams &p, const FwdTables &f, uint64_t first, uint32_t count,
+                      int32_t *start, int32_t *end, uint32_t *nj, uint64_t *h, double *lw, cudaStream_t st) {
+    switch (mode) {
+        case MCX_EXACT: k_trace_forward<MCX_EXACT, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p, f, first, count, start, end, nj, h, lw); break;
+        case MCX_STRANG: k_trace_forward<MCX_STRANG, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p, f, first, count, start, end, nj, h, lw); break;
+        default: k_trace_forward<MCX_LIE, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p, f, first, count, start, end, nj, h, lw); break;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_estimate_forward(mcx_plan *plan, const double *v, double t, int mode, int nsteps, uint64_t paths,
+                                    uint64_t seed, uint64_t path_offset, int precision, double *x, double *sem,
+                                    cudaStream_t st) {
+    const int64_t n = plan->n;
+    if (n == 0) return cudaSuccess;
+    FwdScratch fs;
+    cudaError_t e = fwd_scratch(plan, &fs);
+    if (e != cudaSuccess) return e;
+    FwdTables f;
+    if ((e = build_start_tables(plan, v, fs, &f, st)) != cudaSuccess) return e;
+    WalkParams p = make_params(plan, t, mode == MCX_EXACT ? 1 : nsteps, seed);
+    p.paths = paths;
+    p.path_offset = path_offset;
+    const uint64_t target_warps = 152ull * 64ull * 8ull;
+    uint64_t chunk = (paths + target_warps - 1) / target_warps;
+    if (chunk < 256) chunk = 256;
+    if (chunk > (1ull << 30)) chunk = 1ull << 30;
+    chunk = (chunk + 31) / 32 * 32;
+    p.chunk_len = chunk;
+    const uint64_t n_warps = (paths + chunk - 1) / chunk;
+    const unsigned grid = (unsigned)((n_warps + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+    const bool count = plan->zero_potential;
+    FwdOut o{};
+    if (count) {
+        o.count = reinterpret_cast<unsigned long long *>(fs.dep);
+        e = cudaMemsetAsync(fs.dep, 0, 8 * (size_t)n, st);
+    } else {
+        o.sum1 = fs.dep;
+        o.sum2 = fs.dep + n;
+        e = cudaMemsetAsync(fs.dep, 0, 16 * (size_t)n, st);
+    }
+    if (e != cudaSuccess) return e;
+    const bool wgt = plan->weighted_rows > 0;
+    if (paths > 0) {
+        if (precision == MCX_FP64) {
+            if (count) { if (wgt) launch_fwd<true, true, true>(mode, grid, p, f, o, st); else launch_fwd<true, false, true>(mode, grid, p, f, o, st); }
+            else { if (wgt) launch_fwd<true, true, false>(mode, grid, p, f, o, st); else launch_fwd<true, false, false>(mode, grid, p, f, o, st); }
+        } else {
+            if (count) { if (wgt) launch_fwd<false, true, true>(mode, grid, p, f, o, st); else launch_fwd<false, false, true>(mode, grid, p, f, o, st); }
+            else { if (wgt) launch_fwd<false, true, false>(mode, grid, p, f, o, st); else launch_fwd<false, false, false>(mode, grid, p, f, o, st); }
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_forward_finish<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, o, fs.V, fs.bad, (double)paths, x, sem,
+                                                                   plan->status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_forward(mcx_plan *plan, const double *v, double t, int mode, int nsteps, uint64_t seed,
+                                 uint64_t first_path, uint32_t count, int precision, int32_t *start, int32_t *end,
+                                 uint32_t *njumps, uint64_t *hash, double *logw, cudaStream_t st) {
+    if (count == 0 || plan->n == 0) return cudaSuccess;
+    FwdScratch fs;
+    cudaError_t e = fwd_scratch(plan, &fs);
+    if (e != cudaSuccess) return e;
+    FwdTables f;
+    if ((e = build_start_tables(plan, v, fs, &f, st)) != cudaSuccess) return e;
+    WalkParams p = make_params(plan, t, mode == MCX_EXACT ? 1 : nsteps, seed);
+    const unsigned grid = (count + WALK_THREADS - 1) / WALK_THREADS;
+    const bool wgt = plan->weighted_rows > 0;
+    if (precision == MCX_FP64) {
+        if (wgt) launch_fwd_trace<true, true>(mode, grid, p, f, first_path, count, start, end, njumps, hash, logw, st);
+        else launch_fwd_trace<true, false>(mode, grid, p, f, first_path, count, start, end, njumps, hash, logw, st);
+    } else {
+        if (wgt) launch_fwd_trace<false, true>(mode, grid, p, f, first_path, count, start, end, njumps, hash, logw, st);
+        else launch_fwd_trace<false, false>(mode, grid, p, f, first_path, count, start, end, njumps, hash, logw, st);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_trace(mcx_plan *plan, double t, int mode, int nsteps, int32_t entry, uint64_t seed,

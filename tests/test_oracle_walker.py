@@ -379,3 +379,39 @@ def test_path_offset_splits_compose():
     m_a, _, _ = g.estimate(v, 0.5, 100, entries=ent, seed=8, path_offset=0)
     m_b, _, _ = g.estimate(v, 0.5, 200, entries=ent, seed=8, path_offset=100)
     assert np.allclose((100 * m_a + 200 * m_b) / 300, m_all, rtol=1e-13, atol=0)
+
+
+def test_forward_start_tables_reproduce_v():
+    """The two-level start table (group of 1024, then member) implies P(j) = v_j / V
+    (Lemma 2) up to the 2^-32 threshold quantisation; zero entries are never drawn."""
+    n, GS = 2500, OW.START_GROUP
+    rng = np.random.default_rng(3)
+    v = rng.exponential(1.0, n)
+    v[rng.random(n) < 0.2] = 0.0
+    v[1024:2048] = 0.0  # an all-zero group
+    g = OW.Graph(W.dense_to_csr(np.eye(n)))
+    st, t = g.start_table(v)
+    assert st == 0
+    G = (n + GS - 1) // GS
+
+    def implied(alias, thresh, d):
+        p = np.zeros(d)
+        for k in range(d):
+            keep = 1.0 if thresh[k] == 0xFFFFFFFF else thresh[k] / 2.0 ** 32
+            p[k] += keep / d
+            p[alias[k]] += (1.0 - keep) / d
+        return p
+
+    pg = implied(t["top_alias"], t["top_thresh"], G)
+    P = np.zeros(n)
+    for gi in range(G):
+        lo, hi = gi * GS, min(n, (gi + 1) * GS)
+        if pg[gi] == 0:
+            continue
+        pin = implied(t["in_alias"][lo:hi] - lo, t["in_thresh"][lo:hi], hi - lo)
+        P[lo:hi] = pg[gi] * pin
+    assert abs(t["V"] - v.sum()) <= 1e-12 * v.sum()
+    assert np.abs(P - v / v.sum()).max() <= (G + GS) * 2.0 ** -32
+    assert np.all(P[v == 0] == 0)
+    tr = g.forward_trace(v, 0.0, 5, 0, 20000)
+    assert np.all(v[tr["start"]] > 0)

@@ -273,10 +273,17 @@ def random_generator(n: int, seed: int, kmin: int = 8, kmax: int = 32) -> CSR:
     rows = np.concatenate(rows_l)
     cols = np.concatenate(cols_l)
     rates = np.exp(rng.standard_normal(rows.size))
-    diag = -np.bincount(rows, weights=rates, minlength=n)
-    rows = np.concatenate([rows, np.arange(n)])
-    cols = np.concatenate([cols, np.arange(n)])
-    vals = np.concatenate([rates, diag])
+    off = _csr_from_sorted_rows(n, rows, cols, rates)
+    # diagonal = -(row sum of the off-diagonal rates, summed left to right in column
+    # order), so that every row of Q sums to exactly 0 in floating point too
+    deg = np.diff(off.row_ptr)
+    acc = np.zeros(n)
+    for k in range(int(deg.max()) if n else 0):
+        has = deg > k
+        acc[has] += off.val[off.row_ptr[:-1][has] + k]
+    rows = np.concatenate([np.repeat(np.arange(n), deg), np.arange(n)])
+    cols = np.concatenate([off.col.astype(np.int64), np.arange(n)])
+    vals = np.concatenate([off.val, -acc])
     return _csr_from_sorted_rows(n, rows, cols, vals)
 
 
