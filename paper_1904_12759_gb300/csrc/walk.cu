@@ -894,7 +894,9 @@ cudaError_t fwd_scratch(mcx_plan *plan, FwdScratch *fs) {
     const int64_t n = plan->n;
     const int64_t G = (n + START_GROUP - 1) / START_GROUP;
     const int64_t m = n > G ? n : G;
-    const size_t need = 8 * (size_t)G * 2 + 8 * (size_t)n + 8 * (size_t)m + 4 * (size_t)m + 64 + 16 * (size_t)n + 256;
+    auto seg = [](size_t bytes) { return (bytes + 255) / 256 * 256; };
+    const size_t need = seg(16 * (size_t)n) + seg(8 * (size_t)G) + seg(8 * (size_t)G) + seg(8 * (size_t)n) +
+                        seg(8 * (size_t)m) + seg(4 * (size_t)m) + seg(8) + seg(8);
     if (plan->fwd_bytes < need) {
         cudaFree(plan->fwd);
         plan->fwd = nullptr;
