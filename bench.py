@@ -123,6 +123,27 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _walk_traffic(args):
+    """DRAM bytes per walker launch from the committed ncu record, or None when the
+    walker sources changed since the capture (or the workload differs)."""
+    import hashlib
+
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "k_walk_traffic.json")))
+    except Exception:
+        return None
+    csrc = os.path.join(ROOT, "paper_1904_12759_gb300", "csrc")
+    for name, sha in rec.get("source_sha1", {}).items():
+        try:
+            if hashlib.sha1(open(os.path.join(csrc, name), "rb").read()).hexdigest() != sha:
+                return None
+        except OSError:
+            return None
+    if args.n != N_NODES or args.paths != PATHS:
+        return None
+    return float(rec["dram_bytes_per_launch"])
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
@@ -307,6 +328,7 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    traffic = _walk_traffic(args)
 
     # ---- end to end: host (pinned) CSR and v in, host estimate out, through the one-call API ----
     e2e = None
@@ -356,8 +378,9 @@ def main():
         "walker": {"paths": paths_per_step, "jumps_per_path": jumps / paths_per_step,
                    "jumps_per_s": jumps / (walk_ms / 1e3), "lambda_max": lam},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None, "peak_source": peak_src,
-                     "kernel": "k_walk (estimate launch)", "bytes_per_jump": BYTES_PER_JUMP},
+                     "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_src,
+                     "kernel": "k_walk (estimate launch)", "bytes_per_jump": BYTES_PER_JUMP,
+                     "algorithmic_bytes": walk_bytes},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": None, "clocks": clk.summary(),
     }
     # per step: prep (rows, scan tiles, scan sums, scan add, fill) + power iteration (init, then one
