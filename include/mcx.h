@@ -267,6 +267,80 @@ mcx_status mcx_plan_export(const mcx_plan *plan, int32_t *deg, int64_t *row_star
                            float *inv_rate32, float *delta32, double *inv_rate64, double *delta64,
                            int32_t *edge_col, int32_t *alias_col, uint32_t *thresh, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batching: many forward problems in one persistent launch.                */
+/* ------------------------------------------------------------------------ */
+typedef struct mcx_batch mcx_batch;
+
+/* One forward problem (host memory): the plan matrix B = A^T in CSR form (as
+ * for mcx_plan_create), v >= 0 [n], n_times horizons t > 0, and `paths`
+ * forward paths for each horizon. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int64_t *row_ptr;
+    const int32_t *col;
+    const double *val;
+    const double *v;
+    int32_t n_times;
+    const double *times;
+    uint64_t paths;
+} mcx_problem;
+
+typedef struct {
+    int32_t problems;        /* problems in the batch */
+    int32_t pairs;           /* (problem, time) pairs */
+    int64_t states;          /* states of the block-diagonal plan, blocks padded to multiples of 1024 */
+    uint64_t total_paths;    /* paths per run */
+    uint32_t work_items;     /* work items per run */
+    uint32_t chunk;          /* paths per work item (autotuned) */
+    int32_t blocks_per_sm;   /* resident blocks of 256 threads per SM (autotuned) */
+    int32_t grid;            /* persistent grid size */
+    int32_t count_deposits;  /* 1: every potential is zero, deposits are exact counts */
+    int32_t reserved;
+    double tuned_ms;         /* the autotuner's best sampled run (0 if read from the cache) */
+} mcx_batch_info;
+
+/*
+ * Build a batch of forward problems (Theorem 2, Algorithm 2) for one
+ * persistent launch.  The matrices are placed on the diagonal of one plan
+ * (blocks padded to multiples of 1024 states), per-problem two-level start
+ * tables are built over each v, and the (problem, time) pairs are cut into
+ * work items ordered by estimated cost (largest first: cost ~ paths x
+ * (1 + t x mean jump rate)).  The schedule (paths per work item, resident
+ * blocks per SM) is read from `tune_cache` (a file of JSON lines keyed by GPU
+ * name and problem-set sizes; NULL: no cache) or autotuned by timing sampled
+ * runs, then appended to the cache.  The reset + walk + finish sequence is
+ * captured into a CUDA graph.  Pair k of the batch uses path indices
+ * k * 2^40 + p (pairs numbered problem by problem, time by time), so its
+ * paths are those of mcx_estimate_forward on that problem alone with
+ * path_offset = k * 2^40.  EXACT functional, FP32 paths.  Synchronises
+ * `stream`.
+ * Errors: MCX_E_INVALID (bad description or CSR), MCX_E_NEG_OFFDIAG,
+ * MCX_E_NONFINITE, MCX_E_NEG_V (some v invalid), MCX_E_OOM, MCX_E_CUDA.
+ */
+mcx_status mcx_batch_create(int32_t count, const mcx_problem *problems, const char *tune_cache, void *stream,
+                            mcx_batch **out);
+
+/* One run of the whole batch (one graph launch) with the given seed; results
+ * replace the previous run's.  Asynchronous on `stream`. */
+mcx_status mcx_batch_run(mcx_batch *batch, uint64_t seed, void *stream);
+
+/* Copy the last run's estimate of problem `problem` at horizon `time_index`
+ * into caller-owned device arrays x [n] and sem [n] (sem may be NULL).
+ * Errors: MCX_E_INVALID, MCX_E_CUDA. */
+mcx_status mcx_batch_result(const mcx_batch *batch, int32_t problem, int32_t time_index, double *x, double *sem,
+                            void *stream);
+
+/* Fill *info (host) with the batch's layout and schedule. */
+mcx_status mcx_batch_get_info(const mcx_batch *batch, mcx_batch_info *info);
+
+/* mcx_sync for the batch's plan (latched status, path and jump counters). */
+mcx_status mcx_batch_sync(mcx_batch *batch, void *stream, mcx_stats *stats);
+
+/* Free the batch (synchronises the device first).  NULL is accepted. */
+void mcx_batch_destroy(mcx_batch *batch);
+
 /* Synchronise `stream`, return and clear the plan's latched device status and
  * counters.  stats (host pointer) may be NULL.  Errors: MCX_E_INVALID (an
  * estimate was given an entry outside [0, n); its outputs are NaN),

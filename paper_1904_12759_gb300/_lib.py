@@ -26,6 +26,12 @@ EXPORTS = (
     "mcx_plan_destroy",
     "mcx_status_string",
     "mcx_version",
+    "mcx_batch_create",
+    "mcx_batch_run",
+    "mcx_batch_result",
+    "mcx_batch_get_info",
+    "mcx_batch_sync",
+    "mcx_batch_destroy",
 )
 
 MCX_OK = 0
@@ -41,6 +47,19 @@ PLAN_HOST_INPUT = 0x1
 class PlanInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("nnz_off", C.c_int64), ("weighted_rows", C.c_int64),
                 ("max_deg", C.c_int32), ("reserved", C.c_int32), ("device_bytes", C.c_int64)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p), ("v", C.c_void_p), ("n_times", C.c_int32), ("times", C.c_void_p),
+                ("paths", C.c_uint64)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("problems", C.c_int32), ("pairs", C.c_int32), ("states", C.c_int64), ("total_paths", C.c_uint64),
+                ("work_items", C.c_uint32), ("chunk", C.c_uint32), ("blocks_per_sm", C.c_int32),
+                ("grid", C.c_int32), ("count_deposits", C.c_int32), ("reserved", C.c_int32),
+                ("tuned_ms", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -89,6 +108,18 @@ def load(path: str = LIB_PATH):
     L.mcx_sync.restype = st
     L.mcx_plan_destroy.argtypes = [vp]
     L.mcx_plan_destroy.restype = None
+    L.mcx_batch_create.argtypes = [i32, C.POINTER(Problem), C.c_char_p, vp, C.POINTER(vp)]
+    L.mcx_batch_create.restype = st
+    L.mcx_batch_run.argtypes = [vp, u64, vp]
+    L.mcx_batch_run.restype = st
+    L.mcx_batch_result.argtypes = [vp, i32, i32, vp, vp, vp]
+    L.mcx_batch_result.restype = st
+    L.mcx_batch_get_info.argtypes = [vp, C.POINTER(BatchInfo)]
+    L.mcx_batch_get_info.restype = st
+    L.mcx_batch_sync.argtypes = [vp, vp, C.POINTER(Stats)]
+    L.mcx_batch_sync.restype = st
+    L.mcx_batch_destroy.argtypes = [vp]
+    L.mcx_batch_destroy.restype = None
     L.mcx_status_string.argtypes = [C.c_int]
     L.mcx_status_string.restype = C.c_char_p
     L.mcx_version.restype = C.c_int

@@ -253,3 +253,68 @@ def expm_multiply(row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, v
         torch.cuda.current_stream().synchronize()
         mean, sem = hm, hs
     return mean, sem, t
+
+
+class Batch:
+    """Many forward problems (Theorem 2) in one persistent, graph-captured launch.
+
+    ``problems``: list of dicts with numpy/torch host arrays ``row_ptr``, ``col``,
+    ``val`` (the plan matrix B = A^T), ``v`` (>= 0), ``times`` and ``paths``
+    (forward paths per time).  ``tune_cache``: path of the schedule cache file.
+    """
+
+    def __init__(self, problems, tune_cache: str | None = None, stream=None):
+        import numpy as np
+
+        L = _lib.load()
+        self._keep = []
+        arr = (_lib.Problem * len(problems))()
+        self.sizes = []
+        for k, p in enumerate(problems):
+            rp = np.ascontiguousarray(p["row_ptr"], dtype=np.int64)
+            col = np.ascontiguousarray(p["col"], dtype=np.int32)
+            val = np.ascontiguousarray(p["val"], dtype=np.float64)
+            v = np.ascontiguousarray(p["v"], dtype=np.float64)
+            times = np.ascontiguousarray(p["times"], dtype=np.float64)
+            self._keep += [rp, col, val, v, times]
+            arr[k] = _lib.Problem(rp.size - 1, col.size, rp.ctypes.data, col.ctypes.data, val.ctypes.data,
+                                  v.ctypes.data, times.size, times.ctypes.data, int(p["paths"]))
+            self.sizes.append((rp.size - 1, times.size))
+        out = C.c_void_p()
+        check(L.mcx_batch_create(len(problems), arr, tune_cache.encode() if tune_cache else None,
+                                 _stream(stream), C.byref(out)), "mcx_batch_create")
+        self._keep = None
+        self._h = out
+
+    def info(self) -> dict:
+        inf = _lib.BatchInfo()
+        check(_lib.load().mcx_batch_get_info(self._h, C.byref(inf)), "mcx_batch_get_info")
+        return {k: getattr(inf, k) for k, _ in inf._fields_ if k != "reserved"}
+
+    def run(self, seed: int, stream=None) -> None:
+        check(_lib.load().mcx_batch_run(self._h, int(seed), _stream(stream)), "mcx_batch_run")
+
+    def result(self, problem: int, time_index: int, stream=None):
+        n = self.sizes[problem][0]
+        dev = torch.device("cuda", torch.cuda.current_device())
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+        sem = torch.empty(n, dtype=torch.float64, device=dev)
+        check(_lib.load().mcx_batch_result(self._h, int(problem), int(time_index), C.c_void_p(x.data_ptr()),
+                                           C.c_void_p(sem.data_ptr()), _stream(stream)), "mcx_batch_result")
+        return x, sem
+
+    def sync(self, stream=None) -> dict:
+        st = _lib.Stats()
+        check(_lib.load().mcx_batch_sync(self._h, _stream(stream), C.byref(st)), "mcx_batch_sync")
+        return {"paths": st.paths, "jumps": st.jumps, "status_bits": st.status_bits}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib.load().mcx_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

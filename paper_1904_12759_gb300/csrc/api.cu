@@ -25,7 +25,7 @@ void free_plan(mcx_plan *p) {
     cudaFree(p->node);
     cudaFree(p->node64);
     cudaFree(p->edge_col);
-    cudaFree(p->alias);
+    cudaFree(p->edge16);
     cudaFree(p->status);
     cudaFree(p->scratch);
     cudaFree(p->fwd);

@@ -53,6 +53,16 @@ struct __align__(8) AliasEnt {
     uint32_t thresh;
 };
 
+// Packed edge record of a weighted plan (one 16-byte load per jump): the
+// slot's own column, its alias column and the keep-own threshold.  Rows whose
+// kept entries are all equal alias themselves (threshold 0xFFFFFFFF).
+struct __align__(16) Edge16 {
+    int32_t col;
+    int32_t alias_col;
+    uint32_t thresh;
+    uint32_t pad;
+};
+
 // Device status bits latched in the plan.
 constexpr uint32_t ST_OVERFLOW = 1u;
 constexpr uint32_t ST_BAD_STRUCT = 2u;
@@ -73,7 +83,7 @@ struct mcx_plan {
     mcx::NodeRec *node = nullptr;      // [n]
     mcx::NodeRec64 *node64 = nullptr;  // [n]
     int32_t *edge_col = nullptr;       // [nnz_off]
-    mcx::AliasEnt *alias = nullptr;    // [nnz_off] if weighted_rows > 0
+    mcx::Edge16 *edge16 = nullptr;     // [nnz_off] if weighted_rows > 0 (packed column + alias table)
     uint32_t *status = nullptr;        // device words: [0] status bits, [2..3] paths (u64), [4..5] jumps (u64)
     void *scratch = nullptr;           // grow-only scratch for chunk partials
     size_t scratch_bytes = 0;

@@ -232,6 +232,20 @@ __global__ void k_prep_fill(int64_t n, const int64_t *__restrict__ row_ptr, cons
     vose_build(d, qbuf + o, lam, [cols](int32_t k) { return cols[k]; }, alias + o, qbuf + o, stack + o);
 }
 
+// Pack columns and alias entries into 16-byte edge records (weighted plans).
+__global__ void k_pack_edges(int64_t n, const NodeRec *__restrict__ node, const int32_t *__restrict__ edge_col,
+                             const AliasEnt *__restrict__ alias, Edge16 *__restrict__ e16) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const NodeRec r = node[i];
+    const bool w = (r.flags & NODE_WEIGHTED) != 0;
+    for (int32_t k = 0; k < r.deg; ++k) {
+        const int64_t e = r.row_start + k;
+        const int32_t c = edge_col[e];
+        e16[e] = w ? Edge16{c, alias[e].alias_col, alias[e].thresh, 0u} : Edge16{c, c, 0xFFFFFFFFu, 0u};
+    }
+}
+
 __global__ void k_export_rows(int64_t n, const NodeRec *__restrict__ node, const NodeRec64 *__restrict__ node64,
                               int32_t *deg, int64_t *row_start, uint8_t *weighted, float *ir32, float *d32,
                               double *ir64, double *d64) {
@@ -248,7 +262,7 @@ __global__ void k_export_rows(int64_t n, const NodeRec *__restrict__ node, const
 }
 
 __global__ void k_export_edges(int64_t n, const NodeRec *__restrict__ node, const int32_t *__restrict__ edge_col,
-                               const AliasEnt *__restrict__ alias, int32_t *ecol, int32_t *acol, uint32_t *thr) {
+                               const Edge16 *__restrict__ e16, int32_t *ecol, int32_t *acol, uint32_t *thr) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const NodeRec r = node[i];
@@ -256,9 +270,8 @@ __global__ void k_export_edges(int64_t n, const NodeRec *__restrict__ node, cons
         const int64_t e = r.row_start + k;
         const int32_t c = edge_col[e];
         if (ecol) ecol[e] = c;
-        const bool w = (r.flags & NODE_WEIGHTED) != 0;
-        if (acol) acol[e] = w ? alias[e].alias_col : c;
-        if (thr) thr[e] = w ? alias[e].thresh : 0xFFFFFFFFu;
+        if (acol) acol[e] = e16 ? e16[e].alias_col : c;
+        if (thr) thr[e] = e16 ? e16[e].thresh : 0xFFFFFFFFu;
     }
 }
 
@@ -280,9 +293,11 @@ cudaError_t launch_prep(mcx_plan *plan, const int64_t *row_ptr, const int32_t *c
     PrepTotals *tot_d = nullptr;
     double *qbuf = nullptr;
     int32_t *stack = nullptr;
+    AliasEnt *alias = nullptr;
     cudaError_t err = cudaSuccess;
     auto cleanup = [&]() {
         cudaFree(deg); cudaFree(excl); cudaFree(tile_sum); cudaFree(tot_d); cudaFree(qbuf); cudaFree(stack);
+        cudaFree(alias);
     };
     PrepTotals tot{};
     do {
@@ -314,14 +329,18 @@ cudaError_t launch_prep(mcx_plan *plan, const int64_t *row_ptr, const int32_t *c
         if ((err = cudaMalloc(&plan->edge_col, sizeof(int32_t) * m)) != cudaSuccess) break;
         plan->device_bytes += (int64_t)(sizeof(int32_t) * m);
         if (plan->weighted_rows > 0) {
-            if ((err = cudaMalloc(&plan->alias, sizeof(AliasEnt) * m)) != cudaSuccess) break;
-            plan->device_bytes += (int64_t)(sizeof(AliasEnt) * m);
+            if ((err = cudaMalloc(&alias, sizeof(AliasEnt) * m)) != cudaSuccess) break;
+            if ((err = cudaMalloc(&plan->edge16, sizeof(Edge16) * m)) != cudaSuccess) break;
+            plan->device_bytes += (int64_t)(sizeof(Edge16) * m);
             if ((err = cudaMalloc(&qbuf, sizeof(double) * m)) != cudaSuccess) break;
             if ((err = cudaMalloc(&stack, sizeof(int32_t) * m)) != cudaSuccess) break;
         }
         if (n > 0) {
             k_prep_fill<<<(unsigned)nb, PREP_THREADS, 0, st>>>(n, row_ptr, col, val, plan->node, plan->edge_col,
-                                                              plan->alias, qbuf, stack);
+                                                              alias, qbuf, stack);
+            if (plan->weighted_rows > 0)
+                k_pack_edges<<<(unsigned)nb, PREP_THREADS, 0, st>>>(n, plan->node, plan->edge_col, alias,
+                                                                   plan->edge16);
         }
         if ((err = cudaGetLastError()) != cudaSuccess) break;
         if ((err = cudaStreamSynchronize(st)) != cudaSuccess) break;
@@ -338,7 +357,7 @@ cudaError_t launch_export(const mcx_plan *plan, int32_t *deg, int64_t *row_start
     k_export_rows<<<nb, PREP_THREADS, 0, st>>>(plan->n, plan->node, plan->node64, deg, row_start, weighted, ir32, d32,
                                                ir64, d64);
     if (ecol || acol || thr)
-        k_export_edges<<<nb, PREP_THREADS, 0, st>>>(plan->n, plan->node, plan->edge_col, plan->alias, ecol, acol, thr);
+        k_export_edges<<<nb, PREP_THREADS, 0, st>>>(plan->n, plan->node, plan->edge_col, plan->edge16, ecol, acol, thr);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,91 @@
+"""GPU parity of batching (many forward problems in one persistent, graph-captured launch).
+
+Pair k of a batch (problems in order, horizons in order) uses path indices
+k * 2^40 + p, so it must reproduce, count for count, the oracle's
+single-problem forward run with path_offset = k * 2^40; CTMC generators have
+zero potential, so every pair also conserves probability exactly.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import dense as OD
+from oracle import walker as OW
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mcx():
+    import paper_1904_12759_gb300 as P
+
+    P.load()
+    return P
+
+
+def test_batch_matches_single_problem_oracle(mcx, tmp_path):
+    probs = W.ctmc_batch(10, 7, n_min=300, n_max=2500, paths_per_state=8)
+    cache = str(tmp_path / "tune.jsonl")
+    b = mcx.Batch(probs, tune_cache=cache)
+    info = b.info()
+    assert info["problems"] == 10 and info["pairs"] == 30 and info["count_deposits"] == 1
+    assert info["total_paths"] == sum(3 * p["paths"] for p in probs)
+    assert os.path.exists(cache)
+    b.run(seed=21)
+    torch.cuda.synchronize()
+    st = b.sync()
+    assert st["paths"] == info["total_paths"]
+    k = 0
+    for i, p in enumerate(probs):
+        og = OW.Graph(p["csr"])
+        for ti, t in enumerate(p["times"]):
+            x, sem = b.result(i, ti)
+            x = x.cpu().numpy()
+            ox, osem, _ = og.forward(p["v"], t, p["paths"], seed=21, path_offset=k << 40)
+            V = og.start_table(p["v"])[1]["V"]
+            assert np.allclose(x, ox, rtol=1e-12, atol=1e-15), (i, ti)
+            assert np.allclose(sem.cpu().numpy(), osem, rtol=1e-9, atol=1e-15)
+            assert abs(x.sum() - V) <= 1e-12 * V  # conservation of total probability
+            k += 1
+    # the schedule is read back from the cache the second time
+    b2 = mcx.Batch(probs, tune_cache=cache)
+    i2 = b2.info()
+    assert (i2["chunk"], i2["blocks_per_sm"]) == (info["chunk"], info["blocks_per_sm"]) and i2["tuned_ms"] == 0.0
+    b2.run(seed=21)
+    x2, _ = b2.result(3, 2)
+    x1, _ = b.result(3, 2)
+    assert torch.equal(x1, x2)  # deterministic, schedule-independent counts
+    b.close()
+    b2.close()
+
+
+def test_batch_transients_vs_uniformization(mcx):
+    probs = W.ctmc_batch(4, 3, n_min=1000, n_max=4000, paths_per_state=400)
+    b = mcx.Batch(probs)
+    b.run(seed=5)
+    for i, p in enumerate(probs):
+        q = p["csr"].to_scipy()
+        for ti, t in enumerate(p["times"]):
+            x, sem = b.result(i, ti)
+            x, sem = x.cpu().numpy(), sem.cpu().numpy()
+            want = OD.uniformization_expmv(q.T.tocsr(), t, p["v"])
+            ok = sem > 0
+            z = (x[ok] - want[ok]) / sem[ok]
+            assert abs(z.mean()) < 5 / math.sqrt(ok.sum()) + 0.05, (i, t)
+            assert 0.7 < z.var() < 1.3, (i, t, z.var())
+    b.sync()
+    b.close()
+
+
+def test_batch_rejects_bad_vectors(mcx):
+    probs = W.ctmc_batch(2, 1, n_min=300, n_max=600, paths_per_state=2)
+    probs[1]["v"] = probs[1]["v"].copy()
+    probs[1]["v"][3] = -0.1
+    with pytest.raises(mcx.MCXError) as e:
+        mcx.Batch(probs)
+    assert e.value.code == -4

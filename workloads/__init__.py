@@ -318,3 +318,21 @@ def dirichlet_probability(n: int, seed: int) -> np.ndarray:
 def random_entries(n: int, k: int, seed: int) -> np.ndarray:
     """k distinct entry indices drawn uniformly from 0..n-1 (int32, sorted)."""
     return np.sort(_rng(seed).choice(n, size=k, replace=False)).astype(np.int32)
+
+
+def ctmc_batch(count: int, seed: int, n_min: int = 1000, n_max: int = 100000, times=(0.1, 1.0, 10.0),
+               paths_per_state: int = 64):
+    """Batched CTMC transients: `count` random generators with sizes drawn
+    log-uniformly in [n_min, n_max], each with a flat-Dirichlet start vector,
+    the given horizons and paths_per_state * n forward paths per horizon.
+
+    Returns a list of dicts (row_ptr, col, val, v, times, paths, csr)."""
+    rng = _rng(seed)
+    sizes = np.rint(10.0 ** rng.uniform(np.log10(n_min), np.log10(n_max), size=count)).astype(np.int64)
+    out = []
+    for b, n in enumerate(sizes):
+        q = random_generator(int(n), seed * 100003 + 2 * b)
+        p0 = dirichlet_probability(int(n), seed * 100003 + 2 * b + 1)
+        out.append({"row_ptr": q.row_ptr, "col": q.col, "val": q.val, "v": p0,
+                    "times": np.asarray(times, dtype=np.float64), "paths": int(paths_per_state * n), "csr": q})
+    return out
