@@ -56,6 +56,9 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle CPU time for cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="erdos_renyi", choices=["erdos_renyi", "ctmc_batch", "heat3d"],
+                    help="erdos_renyi: the default line; ctmc_batch / heat3d: the batched CTMC transients and "
+                         "the 3D heat equation (own JSON lines)")
     return ap.parse_args()
 
 
@@ -218,10 +221,174 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def run_ctmc_batch(args):
+    """Batched CTMC transients: 256 generators (n log-uniform in 1e3..1e5, 8-32 lognormal
+    rates per row), flat-Dirichlet p0, t in {0.1, 1, 10}, 64 forward paths per state per
+    (Q, t), one persistent graph launch per step.  Metric: walker jumps/s."""
+    import numpy as np
+    import torch
+
+    import paper_1904_12759_gb300 as P
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    probs = W.ctmc_batch(256, SEED)
+    t0 = time.perf_counter()
+    b = P.Batch(probs)
+    create_s = time.perf_counter() - t0
+    info = b.info()
+    for w in range(args.warmup):
+        b.run(1000 + w)
+    torch.cuda.synchronize()
+    b.sync()
+    ms = []
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.run(SEED + k)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    st = b.sync()
+    jumps, paths = st["jumps"] / args.steps, st["paths"] / args.steps
+    worst = 0.0
+    for i, p in enumerate(probs):
+        for ti in range(len(p["times"])):
+            x, _ = b.result(i, ti)
+            worst = max(worst, abs(x.sum().item() - float(np.sum(p["v"]))))
+    step_s = sum(ms) / 1e3 / args.steps
+    achieved = BYTES_PER_JUMP * jumps / step_s / 1e9
+    peak = float(_peaks().get("hbm_gbs", 6800.0))
+    # CPU oracle on the smallest instances (forward form, sequential) for ~10 s
+    from oracle import walker as OW
+
+    order = sorted(range(len(probs)), key=lambda i: probs[i]["csr"].n)
+    cpu_paths, cpu_s, used = 0, 0.0, 0
+    for i in order:
+        p = probs[i]
+        g = OW.Graph(p["csr"])
+        t1 = time.perf_counter()
+        for t in p["times"]:
+            g.forward(p["v"], t, p["paths"], seed=SEED)
+        cpu_s += time.perf_counter() - t1
+        cpu_paths += 3 * p["paths"]
+        used += 1
+        if cpu_s > 10.0:
+            break
+    line = {"metric": "walker jumps/s", "value": jumps / step_s, "unit": "jumps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "ctmc_batch", "generators": 256, "states": info["states"],
+                       "times": [0.1, 1.0, 10.0], "paths_per_state": 64, "functional": "exact, forward form",
+                       "schedule": {k: info[k] for k in ("chunk", "blocks_per_sm", "grid", "work_items")},
+                       "l2": "inputs (2 GB of edge records) larger than L2"},
+            "walker": {"paths": paths, "jumps": jumps, "paths_per_s": paths / step_s,
+                       "max_conservation_error": worst, "batch_create_s": create_s},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "k_batch_walk", "bytes_per_jump": BYTES_PER_JUMP},
+            "cpu_baseline": {"value": cpu_paths / cpu_s, "unit": "paths/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{used} smallest generators x 3 horizons, forward form, sequential"},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
+def run_heat3d(args):
+    """3D heat equation: 7-point Dirichlet Laplacian on 128^3, t = 20/(6*129^2) (about 20 jumps
+    per path), v a Gaussian bump + 1e-3 noise, 4096 random entries x 1e6 backward paths.
+    FP32 paths timed; the FP64 path version on 64 of the entries gives the precision split."""
+    import numpy as np
+    import torch
+
+    import paper_1904_12759_gb300 as P
+    import workloads as W
+    from oracle import dense as OD
+
+    torch.cuda.set_device(0)
+    m = 128
+    csr = W.grid_laplacian_3d(m)
+    t = 20.0 / (6.0 * (m + 1) ** 2)
+    v = W.gaussian_bump_3d(m, SEED)
+    ent = W.random_entries(csr.n, 4096, SEED)
+    plan = P.Plan.from_csr(csr)
+    vd = torch.as_tensor(v).cuda()
+    ed = torch.as_tensor(ent).cuda()
+    M = 10 ** 6
+    for w in range(args.warmup):
+        plan.estimate(vd, t, M // 10, entries=ed, seed=1000 + w)
+    torch.cuda.synchronize()
+    plan.sync()
+    ms = []
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            mean, sem = plan.estimate(vd, t, M, entries=ed, seed=SEED + k)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    st = plan.sync()
+    step_s = sum(ms) / 1e3 / args.steps
+    jumps = st["jumps"] / args.steps
+    x = OD.grid3d_expmv(m, t, v)[ent]
+    z = (mean.cpu().numpy() - x) / sem.cpu().numpy()
+    # precision split on 64 entries: same seed, FP32 vs FP64 path versions
+    sub = ed[:64]
+    m32, _ = plan.estimate(vd, t, M, entries=sub, seed=SEED)
+    m64, s64 = plan.estimate(vd, t, M, entries=sub, seed=SEED, prec="fp64")
+    rel = (m32 - m64).abs() / m64.abs()
+    div = []
+    for e in ent[:8]:
+        a = plan.trace(t, int(e), SEED, 0, 100000, prec="fp32")
+        b = plan.trace(t, int(e), SEED, 0, 100000, prec="fp64")
+        div.append(float((a["hash"] != b["hash"]).double().mean().item()))
+    achieved = BYTES_PER_JUMP * jumps / step_s / 1e9
+    peak = float(_peaks().get("hbm_gbs", 6800.0))
+    from oracle import walker as OW
+
+    g = OW.Graph(csr)
+    t1 = time.perf_counter()
+    g.estimate(v, t, M, entries=ent[:16], seed=SEED)
+    cpu_s = time.perf_counter() - t1
+    line = {"metric": "walker paths/s", "value": 4096 * M / step_s, "unit": "paths/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "heat3d", "grid": "128^3", "t": t, "entries": 4096, "paths_per_entry": M,
+                       "v": "gaussian bump (width 0.1) + 1e-3 U[0,1)", "functional": "exact"},
+            "walker": {"jumps_per_path": jumps / (4096 * M), "jumps_per_s": jumps / step_s,
+                       "z_vs_closed_form": {"mean": float(z.mean()), "var": float(z.var()),
+                                            "frac_abs_gt_3": float((np.abs(z) > 3).mean())}},
+            "precision_split": {"entries": 64, "max_rel_diff_fp32_vs_fp64": float(rel.max().item()),
+                                "mean_rel_diff": float(rel.mean().item()),
+                                "fp64_sem_rel": float((s64 / m64.abs()).mean().item()),
+                                "diverged_path_fraction": float(np.mean(div)), "traced_paths": 8 * 100000},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "k_walk", "bytes_per_jump": BYTES_PER_JUMP},
+            "cpu_baseline": {"value": 16 * M / cpu_s, "unit": "paths/s", "cores": OW.num_threads(), "kind": "oracle",
+                             "sample": "16 entries x 1e6 paths"},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "ctmc_batch":
+        run_ctmc_batch(args)
+        return
+    if args.workload == "heat3d":
+        run_heat3d(args)
         return
     import numpy as np
     import torch
