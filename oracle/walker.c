@@ -577,6 +577,102 @@ void oracle_forward_trace(const oracle_graph *g, int64_t n, const int32_t *top_a
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* Control-variate estimator (variance reduction, Sec. 5).  For any h with    */
+/* h(0) = v, Duhamel's formula with the Feynman-Kac representation of        */
+/* exp(sA) gives x_i = h(t, i) + E_i[ int_0^t W_s R(t - s, X_s) ds ] with    */
+/* R = A h - dh/dtau.  For h(tau) = v + tau Av + tau^2 A^2v/2 + tau^3 c3,     */
+/* R(tau, j) = a_j tau^2 + b_j tau^3 (a = A^3v/2 - 3 c3, b = A c3).  Over a   */
+/* hold of length D in state j that starts with remaining time r and log     */
+/* weight L, the integral is exactly                                         */
+/*   e^L sum_k c_k D^{k+1} phi_k(delta_j D),  phi_k(z) = int_0^1 e^{zs} s^k ds */
+/* with R(r - u) = c0 + c1 u + c2 u^2 + c3' u^3.  The path is the FP32 path  */
+/* of the backward walker (same draws); the integral is evaluated in FP64.   */
+/* ------------------------------------------------------------------------ */
+double oracle_phi(int k, double z)
+{
+    if (fabs(z) <= 2.0) {
+        /* series: sum_n z^n / (n! (n + k + 1)) */
+        double term = 1.0, sum = 0.0;
+        for (int n = 0; n < 40; ++n) {
+            sum += term / (double)(n + k + 1);
+            term *= z / (double)(n + 1);
+        }
+        return sum;
+    }
+    double ez = exp(z);
+    double p = (ez - 1.0) / z;
+    for (int m = 1; m <= k; ++m) p = (ez - (double)m * p) / z;
+    return p;
+}
+
+static double hold_integral(double a, double b, double delta, double r, double D)
+{
+    double c0 = a * r * r + b * r * r * r;
+    double c1 = -2.0 * a * r - 3.0 * b * r * r;
+    double c2 = a + 3.0 * b * r;
+    double c3 = -b;
+    double z = delta * D;
+    return c0 * D * oracle_phi(0, z) + c1 * D * D * oracle_phi(1, z) + c2 * D * D * D * oracle_phi(2, z) +
+           c3 * D * D * D * D * oracle_phi(3, z);
+}
+
+/* Residual part of one path's control-variate estimate (FP32 path, EXACT functional). */
+static double cv_path(const oracle_graph *g, int32_t i, double t, const double *ca, const double *cb, uint64_t seed,
+                      uint64_t p, uint32_t *njumps)
+{
+    int32_t j = i;
+    float r = (float)t;
+    float L = 0.0f;
+    double y = 0.0;
+    uint32_t k = 0;
+    for (;;) {
+        float dl = g->delta32[j];
+        if (g->deg[j] == 0) {
+            y += exp((double)L) * hold_integral(ca[j], cb[j], (double)dl, (double)r, (double)r);
+            break;
+        }
+        uint32_t w[4];
+        draw(seed, k, (uint32_t)i, p, w);
+        float S = -oracle_logf(unif_f32(w[0])) * g->inv_rate32[j];
+        if (S >= r) {
+            y += exp((double)L) * hold_integral(ca[j], cb[j], (double)dl, (double)r, (double)r);
+            break;
+        }
+        y += exp((double)L) * hold_integral(ca[j], cb[j], (double)dl, (double)r, (double)S);
+        L = fmaf(dl, S, L);
+        r = r - S;
+        j = pick_next(g, j, w[2], w[3]);
+        ++k;
+    }
+    *njumps = k;
+    return y;
+}
+
+/* Per-entry control-variate estimate: mean = h_i + mean of the residual
+ * integrals, sem from the residual integrals' sample variance (Welford). */
+int oracle_estimate_cv(const oracle_graph *g, const double *ca, const double *cb, const double *h, double t,
+                       uint64_t M, const int32_t *entries, int64_t n_entries, uint64_t seed, uint64_t path_offset,
+                       double *mean, double *sem)
+{
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < n_entries; ++q) {
+        int32_t i = entries ? entries[q] : (int32_t)q;
+        double sum = 0.0, wm = 0.0, wss = 0.0;
+        for (uint64_t p = 0; p < M; ++p) {
+            uint32_t nj;
+            double y = t == 0.0 ? 0.0 : cv_path(g, i, t, ca, cb, seed, path_offset + p, &nj);
+            sum += y;
+            double d = y - wm;
+            wm += d / (double)(p + 1);
+            wss += d * (y - wm);
+        }
+        mean[q] = h[i] + (M ? sum / (double)M : 0.0);
+        sem[q] = M > 1 ? sqrt(wss / (double)(M - 1) / (double)M) : 0.0;
+    }
+    return O_OK;
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP

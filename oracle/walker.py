@@ -77,6 +77,10 @@ def lib():
                                          C.c_int, u64, u64, u64, vp, vp, vp]
             L.oracle_forward_trace.argtypes = [C.POINTER(_Graph), i64, vp, vp, vp, vp, dbl, C.c_int, C.c_int,
                                                C.c_int, u64, u64, u32, vp, vp, vp, vp, vp]
+            L.oracle_phi.argtypes = [C.c_int, dbl]
+            L.oracle_phi.restype = dbl
+            L.oracle_estimate_cv.argtypes = [C.POINTER(_Graph), vp, vp, vp, dbl, u64, vp, i64, u64, u64, vp, vp]
+            L.oracle_estimate_cv.restype = C.c_int
             L.oracle_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -156,6 +160,22 @@ class Graph:
                               _p(jumps))
         return mean, sem, int(jumps[0])
 
+    def estimate_cv(self, a, b, h, t, paths, entries=None, seed=0, path_offset=0):
+        """Control-variate estimate h_i + mean residual integral (FP32 paths, EXACT)."""
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        if entries is None:
+            ne, ent_p = self.n, None
+        else:
+            entries = np.ascontiguousarray(entries, dtype=np.int32)
+            ne, ent_p = entries.size, _p(entries)
+        mean = np.zeros(ne)
+        sem = np.zeros(ne)
+        lib().oracle_estimate_cv(C.byref(self._g), _p(a), _p(b), _p(h), float(t), int(paths), ent_p, int(ne),
+                                 int(seed), int(path_offset), _p(mean), _p(sem))
+        return mean, sem
+
     # -- forward form (Theorem 2, Algorithm 2); this graph must be that of A^T --
     def start_table(self, v):
         """Two-level alias tables for the start draw j ~ v/V (Lemma 2)."""
@@ -197,6 +217,11 @@ class Graph:
                                    PRECS[prec], int(seed), int(first_path), int(count), _p(out["start"]),
                                    _p(out["end"]), _p(out["njumps"]), _p(out["hash"]), _p(out["logw"]))
         return out
+
+
+def phi(k: int, z: float) -> float:
+    """int_0^1 e^{zs} s^k ds (the oracle's evaluation)."""
+    return float(lib().oracle_phi(int(k), float(z)))
 
 
 def num_threads() -> int:

@@ -1,0 +1,127 @@
+"""Pins for the control-variate oracle (oracle/cv.py and the CV estimator in walker.c).
+
+* phi_k(z) = int_0^1 e^{zs} s^k ds against SciPy quadrature and closed forms.
+* Zero variance when h is exact: for a 3-node directed path A^3 = 0, so
+  exp(tA)v = v + tAv + t^2A^2v/2 and with c3 = 0 the residual R vanishes.
+* Unbiasedness for an arbitrary (random) h: z-test against expm.
+* The Taylor-only h already cuts the variance for short horizons.
+* MLP gradients against central finite differences; BF16 rounding rule.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import cv as CV
+from oracle import dense as OD
+from oracle import walker as OW
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+@pytest.mark.parametrize("z", [-40.0, -3.0, -2.0, -0.7, -1e-4, 0.0, 1e-4, 0.9, 2.0, 2.5, 12.0, 40.0])
+def test_phi_against_quadrature(k, z):
+    quad = pytest.importorskip("scipy.integrate").quad
+    want, err = quad(lambda s: math.exp(z * s) * s ** k, 0.0, 1.0, epsabs=1e-300, epsrel=2e-14, limit=200)
+    assert abs(OW.phi(k, z) - want) <= 1e-13 * abs(want) + 1e-300
+
+
+def test_phi_closed_forms():
+    assert OW.phi(0, 0.0) == 1.0 and abs(OW.phi(3, 0.0) - 0.25) < 1e-16
+    for z in (-5.0, 0.5, 3.0):
+        assert abs(OW.phi(0, z) - math.expm1(z) / z) < 1e-14 * abs(math.expm1(z) / z)
+
+
+def test_exact_h_gives_zero_variance():
+    a = np.zeros((3, 3))
+    a[0, 1] = 1.3
+    a[1, 2] = 0.7  # strictly upper triangular: A^3 = 0
+    csr = W.dense_to_csr(a)
+    v = np.array([0.2, -1.0, 2.0])
+    t = 0.9
+    T = CV.taylor_terms(csr, v)
+    assert np.allclose(np.linalg.matrix_power(a, 3), 0)
+    exact = OD.expmv_dense(a, t, v)
+    T2 = T[0] + t * T[1] + t * t * T[2] / 2
+    assert np.allclose(T2, exact, rtol=1e-13)
+    c3, ca, cb = CV.cv_coefficients(csr, T, t, T2)
+    assert np.allclose(c3, 0) and np.allclose(ca, 0) and np.allclose(cb, 0)
+    g = OW.Graph(csr)
+    mean, sem = g.estimate_cv(ca, cb, T2, t, 5000, seed=1)
+    assert np.allclose(mean, exact, rtol=1e-13) and np.all(sem == 0)
+
+
+def _conditioned(n, seed, rate=1.5, dsd=1.0):
+    rng = np.random.default_rng(seed)
+    a = np.where(rng.random((n, n)) < 0.3, rng.lognormal(0, 1, (n, n)), 0.0)
+    np.fill_diagonal(a, 0.0)
+    a *= rate / a.sum(axis=1).mean()
+    np.fill_diagonal(a, rng.normal(0, dsd, n) - a.sum(axis=1) + rng.normal(0, dsd, n))
+    return a
+
+
+def test_cv_unbiased_for_random_h():
+    a = _conditioned(40, 21)
+    csr = W.dense_to_csr(a)
+    v = W.uniform_vector(40, 2, -1.0, 1.0)
+    t = 0.8
+    T = CV.taylor_terms(csr, v)
+    xhat = np.random.default_rng(5).normal(0, 2.0, 40)  # an arbitrary (bad) prediction
+    c3, ca, cb = CV.cv_coefficients(csr, T, t, xhat)
+    g = OW.Graph(csr)
+    mean, sem = g.estimate_cv(ca, cb, xhat, t, 20000, seed=3)
+    z = (mean - OD.expmv_dense(a, t, v)) / sem
+    assert abs(z.mean()) < 5 / math.sqrt(40) and 0.5 < z.var() < 1.6 and np.abs(z).max() < 4.5
+
+
+def test_taylor_only_h_reduces_variance():
+    csr = W.erdos_renyi(400, 6, 2)
+    v = W.uniform_vector(400, 1)
+    lam = OD.power_iteration(csr.to_scipy())
+    t = 0.5 / lam
+    T = CV.taylor_terms(csr, v)
+    T2 = T[0] + t * T[1] + t * t * T[2] / 2
+    c3, ca, cb = CV.cv_coefficients(csr, T, t, T2)
+    g = OW.Graph(csr)
+    m_cv, s_cv = g.estimate_cv(ca, cb, T2, t, 2000, seed=4)
+    m_pl, s_pl, _ = g.estimate(v, t, 2000, seed=4)
+    x = OD.taylor_expmv(csr.to_scipy(), t, v)
+    z = (m_cv - x) / s_cv
+    assert abs(z.mean()) < 5 / math.sqrt(400) and 0.7 < z.var() < 1.4
+    assert np.median(s_pl / s_cv) > 10.0  # variance reduction by > 100x
+
+
+def test_mlp_gradient_finite_differences():
+    rng = np.random.default_rng(0)
+    p = CV.init_params(3)
+    X = rng.normal(size=(50, CV.N_FEATURES))
+    tgt = rng.normal(size=50)
+    loss, g = CV.loss_and_grad(p, X, tgt, round_weights=False)
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        q = {k: v.astype(np.float64) for k, v in p.items()}
+        idx = tuple(rng.integers(0, s) for s in q[name].shape)
+        h = 1e-6
+        q[name][idx] += h
+        lp, _ = CV.loss_and_grad(q, X, tgt, round_weights=False)
+        q[name][idx] -= 2 * h
+        lm, _ = CV.loss_and_grad(q, X, tgt, round_weights=False)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[name][idx]) <= 1e-6 * max(1.0, abs(fd)), name
+
+
+def test_bf16_rounding():
+    x = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -2.5, 3.1415926], dtype=np.float32)
+    y = CV.bf16(x)
+    assert y[0] == 1.0 and y[1] == 1.0  # tie to even
+    assert y[2] == np.float32(1.0 + 2 ** -7)
+    assert y[3] == -2.5 and abs(y[4] - 3.140625) < 1e-7
+
+
+def test_features_shapes_and_values():
+    csr = W.erdos_renyi(300, 5, 1)
+    v = W.uniform_vector(300, 3)
+    F, T2, T = CV.features(csr, v, 0.05)
+    assert F.shape == (300, 5) and np.all(np.isfinite(F))
+    deg = np.diff(csr.row_ptr)
+    assert np.allclose(F[:, 0], np.log1p(deg))
+    assert np.allclose(T2, v + 0.05 * T[1] + 0.05 ** 2 * T[2] / 2)
