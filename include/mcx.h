@@ -341,6 +341,93 @@ mcx_status mcx_batch_sync(mcx_batch *batch, void *stream, mcx_stats *stats);
 /* Free the batch (synchronises the device first).  NULL is accepted. */
 void mcx_batch_destroy(mcx_batch *batch);
 
+/* ------------------------------------------------------------------------ */
+/* Learned control variate (variance reduction, Sec. 5).                    */
+/*                                                                          */
+/* For any h with h(0) = v, x_i = h(t, i) + E_i[int_0^t W_s R(t - s, X_s) ds] */
+/* with R = A h - dh/dtau (Duhamel's formula with the Feynman-Kac form of    */
+/* exp(sA), Theorem 1): unbiased whatever h is.  The library uses            */
+/* h(tau) = v + tau Av + tau^2 A^2 v/2 + tau^3 c3 with c3 chosen so that       */
+/* h(t, i) = xhat_i, a prediction of x_i by a small network; then            */
+/* R(tau) = a tau^2 + b tau^3, a = A^3 v/2 - 3 c3, b = A c3, and the walker    */
+/* integrates e^{logW} R exactly over every holding interval.  A good        */
+/* prediction leaves only a small residual to estimate.                     */
+/* ------------------------------------------------------------------------ */
+typedef struct mcx_mlp mcx_mlp;
+
+/*
+ * Taylor terms and node features of (A, v, t); all pointers are device memory.
+ *   taylor   float64 [4n] out: v, Av, A^2 v, A^3 v (A with its diagonal)
+ *   features float32 [5n] out, node-major: log1p(lambda_i), log1p(mean of the
+ *            neighbours' lambda), log1p(their standard deviation),
+ *            t(Av)_i/T2_i, t^2(A^2v)_i/(2 T2_i), T2 = v + tAv + t^2A^2v/2
+ *   work     float64 [n] scratch
+ * Errors: MCX_E_INVALID, MCX_E_CUDA.
+ */
+mcx_status mcx_cv_prepare(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                          const double *v, double t, double *work, double *taylor, float *features, void *stream);
+
+/* Training targets y_i = log(max(x_i / T2_i, 1e-6)) from estimates x (float64 [n])
+ * and the Taylor terms; y float32 [n] out (device). */
+mcx_status mcx_cv_targets(int64_t n, const double *x, const double *taylor, double t, float *y, void *stream);
+
+/* A 5-64-64-1 ReLU network predicting y = log(x / T2) from the features
+ * (standardised with the training set's mean and deviation).  FP32 master
+ * weights on the device; every use rounds the weights to BF16 (round to
+ * nearest even) and accumulates in FP32.  Initialised from `seed`. */
+mcx_status mcx_mlp_create(uint64_t seed, mcx_mlp **out);
+
+/* Host copies of the parameters (4609 floats: W1 [5][64] in-major, b1 [64],
+ * W2 [64][64], b2 [64], W3 [64], b3) and the feature mean / deviation [5];
+ * any pointer may be NULL. */
+mcx_status mcx_mlp_set(mcx_mlp *model, const float *params, const float *mu, const float *sd);
+mcx_status mcx_mlp_get(const mcx_mlp *model, float *params, float *mu, float *sd);
+
+/* y [n] = network(features [5n]) (device). */
+mcx_status mcx_mlp_predict(const mcx_mlp *model, int64_t n, const float *features, float *y, void *stream);
+
+/* Gradient of the mean squared error (1/n) sum (net(f_i) - y_i)^2 with respect
+ * to the parameters as used (BF16-rounded weights): grad float32 [4609]
+ * (device) and the loss (host, may be NULL; the call then synchronises).
+ * Deterministic: block partial sums are added in a fixed order. */
+mcx_status mcx_mlp_gradient(mcx_mlp *model, int64_t n, const float *features, const float *targets,
+                            float *grad, float *loss, void *stream);
+
+/* Adam (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on minibatches of
+ * `batch` rows, `epochs` passes over a permutation drawn from `seed`; first
+ * sets the feature standardisation from these features.  epoch_loss (host,
+ * [epochs], may be NULL) receives the mean minibatch loss of each epoch.
+ * Synchronises `stream`. */
+mcx_status mcx_mlp_fit(mcx_mlp *model, int64_t n, const float *features, const float *targets, int32_t epochs,
+                       int32_t batch, float lr, uint64_t seed, float *epoch_loss, void *stream);
+
+void mcx_mlp_destroy(mcx_mlp *model);
+
+/*
+ * Control-variate coefficients from the Taylor terms and the network output
+ * y (float32 [n], device; NULL means y = 0, i.e. xhat = T2, the Taylor-only
+ * control variate): coef float64 [3n] out = [(a_i, b_i) pairs (2n) | h (n)]
+ * with h_i = xhat_i = T2_i e^{y_i}, c3 = (xhat - T2)/t^3, a = A^3 v/2 - 3 c3,
+ * b = A c3; coef must be 16-byte aligned (the pairs are read as 16-byte
+ * vectors).  work: float64 [2n] scratch.  Errors: MCX_E_INVALID, MCX_E_CUDA.
+ */
+mcx_status mcx_cv_coefficients(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                               const double *taylor, const float *y, double t, double *work, double *coef,
+                               void *stream);
+
+/*
+ * Control-variate backward estimate of x_i = (exp(tA) v)_i for the requested
+ * entries: mean = h_i + the sample mean of the residual integrals over
+ * `paths` paths (the FP32 paths of mcx_estimate with the same seed, EXACT
+ * functional), sem = the residuals' standard error.  precision: MCX_FP32
+ * (residual integrals in FP32 with per-path scaling) or MCX_FP64 (in FP64).
+ * coef from mcx_cv_coefficients for the same (A, v, t); entries, outputs and
+ * errors as in mcx_estimate.
+ */
+mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_t paths, const int32_t *entries,
+                           int64_t n_entries, uint64_t seed, uint64_t path_offset, int precision, double *mean,
+                           double *sem, void *stream);
+
 /* Synchronise `stream`, return and clear the plan's latched device status and
  * counters.  stats (host pointer) may be NULL.  Errors: MCX_E_INVALID (an
  * estimate was given an entry outside [0, n); its outputs are NaN),

@@ -8,13 +8,13 @@ package is the thin Python binding (ctypes) used by the tests and benchmark.
 from . import _lib
 from ._lib import EXPORTS, MCXError, load
 
-__all__ = ["EXPORTS", "MCXError", "load", "Plan", "power_iteration", "expm_multiply", "Batch"]
+__all__ = ["EXPORTS", "MCXError", "load", "Plan", "power_iteration", "expm_multiply", "Batch", "MLP", "cv_prepare", "cv_targets", "cv_coefficients"]
 
 
 def __getattr__(name):
     # the torch-facing API is imported lazily so that loading the C library
     # (and checking its exports) does not require a GPU
-    if name in ("Plan", "power_iteration", "expm_multiply", "Batch"):
+    if name in ("Plan", "power_iteration", "expm_multiply", "Batch", "MLP", "cv_prepare", "cv_targets", "cv_coefficients"):
         from . import api
 
         return getattr(api, name)

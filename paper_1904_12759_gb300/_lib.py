@@ -32,6 +32,17 @@ EXPORTS = (
     "mcx_batch_get_info",
     "mcx_batch_sync",
     "mcx_batch_destroy",
+    "mcx_cv_prepare",
+    "mcx_cv_targets",
+    "mcx_mlp_create",
+    "mcx_mlp_set",
+    "mcx_mlp_get",
+    "mcx_mlp_predict",
+    "mcx_mlp_gradient",
+    "mcx_mlp_fit",
+    "mcx_mlp_destroy",
+    "mcx_cv_coefficients",
+    "mcx_estimate_cv",
 )
 
 MCX_OK = 0
@@ -120,6 +131,28 @@ def load(path: str = LIB_PATH):
     L.mcx_batch_sync.restype = st
     L.mcx_batch_destroy.argtypes = [vp]
     L.mcx_batch_destroy.restype = None
+    L.mcx_cv_prepare.argtypes = [i64, vp, vp, vp, vp, dbl, vp, vp, vp, vp]
+    L.mcx_cv_prepare.restype = st
+    L.mcx_cv_targets.argtypes = [i64, vp, vp, dbl, vp, vp]
+    L.mcx_cv_targets.restype = st
+    L.mcx_mlp_create.argtypes = [u64, C.POINTER(vp)]
+    L.mcx_mlp_create.restype = st
+    L.mcx_mlp_set.argtypes = [vp, vp, vp, vp]
+    L.mcx_mlp_set.restype = st
+    L.mcx_mlp_get.argtypes = [vp, vp, vp, vp]
+    L.mcx_mlp_get.restype = st
+    L.mcx_mlp_predict.argtypes = [vp, i64, vp, vp, vp]
+    L.mcx_mlp_predict.restype = st
+    L.mcx_mlp_gradient.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+    L.mcx_mlp_gradient.restype = st
+    L.mcx_mlp_fit.argtypes = [vp, i64, vp, vp, i32, i32, C.c_float, u64, vp, vp]
+    L.mcx_mlp_fit.restype = st
+    L.mcx_mlp_destroy.argtypes = [vp]
+    L.mcx_mlp_destroy.restype = None
+    L.mcx_cv_coefficients.argtypes = [i64, vp, vp, vp, vp, vp, dbl, vp, vp, vp]
+    L.mcx_cv_coefficients.restype = st
+    L.mcx_estimate_cv.argtypes = [vp, vp, dbl, u64, vp, i64, u64, u64, C.c_int, vp, vp, vp]
+    L.mcx_estimate_cv.restype = st
     L.mcx_status_string.argtypes = [C.c_int]
     L.mcx_status_string.restype = C.c_char_p
     L.mcx_version.restype = C.c_int

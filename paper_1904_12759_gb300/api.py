@@ -158,6 +158,25 @@ class Plan:
                                             _stream(stream)), "mcx_trace_forward")
         return out
 
+    def estimate_cv(self, coef: torch.Tensor, t: float, paths: int, entries: torch.Tensor | None = None,
+                    seed: int = 0, path_offset: int = 0, prec: str = "fp32", out: tuple | None = None, stream=None):
+        """Control-variate backward estimate (see cv_coefficients); returns (mean, sem)."""
+        if entries is None:
+            ne, p_e = self.n, 0
+        else:
+            ne, p_e = entries.numel(), _dev(entries, torch.int32, "entries")
+        if out is None:
+            mean = torch.empty(ne, dtype=torch.float64, device=coef.device)
+            sem = torch.empty(ne, dtype=torch.float64, device=coef.device)
+        else:
+            mean, sem = out
+        check(_lib.load().mcx_estimate_cv(self._h, C.c_void_p(_dev(coef, torch.float64, "coef")), float(t), int(paths),
+                                          C.c_void_p(p_e), int(ne), int(seed), int(path_offset), PRECISIONS[prec],
+                                          C.c_void_p(_dev(mean, torch.float64, "mean")),
+                                          C.c_void_p(_dev(sem, torch.float64, "sem")), _stream(stream)),
+              "mcx_estimate_cv")
+        return mean, sem
+
     def export(self, stream=None) -> dict:
         """Copy the plan's preparation results (rates, potentials, jump tables) to new CUDA tensors."""
         inf = self.info()
@@ -311,6 +330,115 @@ class Batch:
     def close(self) -> None:
         if getattr(self, "_h", None):
             _lib.load().mcx_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# Learned control variate
+# ---------------------------------------------------------------------------
+def cv_prepare(row_ptr, col, val, v, t: float, stream=None):
+    """Taylor terms [4, n] (v, Av, A^2v, A^3v) and node features [n, 5] of (A, v, t)."""
+    n = row_ptr.numel() - 1
+    dev = row_ptr.device
+    work = torch.empty(n, dtype=torch.float64, device=dev)
+    taylor = torch.empty(4 * n, dtype=torch.float64, device=dev)
+    feat = torch.empty(5 * n, dtype=torch.float32, device=dev)
+    check(_lib.load().mcx_cv_prepare(n, C.c_void_p(_dev(row_ptr, torch.int64, "row_ptr")),
+                                     C.c_void_p(_dev(col, torch.int32, "col")),
+                                     C.c_void_p(_dev(val, torch.float64, "val")),
+                                     C.c_void_p(_dev(v, torch.float64, "v")), float(t), C.c_void_p(work.data_ptr()),
+                                     C.c_void_p(taylor.data_ptr()), C.c_void_p(feat.data_ptr()), _stream(stream)),
+          "mcx_cv_prepare")
+    return taylor.view(4, n), feat.view(n, 5)
+
+
+def cv_targets(x, taylor, t: float, stream=None):
+    n = x.numel()
+    y = torch.empty(n, dtype=torch.float32, device=x.device)
+    check(_lib.load().mcx_cv_targets(n, C.c_void_p(_dev(x, torch.float64, "x")),
+                                     C.c_void_p(_dev(taylor.contiguous(), torch.float64, "taylor")), float(t),
+                                     C.c_void_p(y.data_ptr()), _stream(stream)), "mcx_cv_targets")
+    return y
+
+
+def cv_coefficients(row_ptr, col, val, taylor, y, t: float, stream=None):
+    """coef [3n] = [(a, b) pairs | xhat] for mcx_estimate_cv (y None: Taylor-only)."""
+    n = row_ptr.numel() - 1
+    dev = row_ptr.device
+    work = torch.empty(2 * n, dtype=torch.float64, device=dev)
+    coef = torch.empty(3 * n, dtype=torch.float64, device=dev)
+    p_y = _dev(y, torch.float32, "y") if y is not None else 0
+    check(_lib.load().mcx_cv_coefficients(n, C.c_void_p(_dev(row_ptr, torch.int64, "row_ptr")),
+                                          C.c_void_p(_dev(col, torch.int32, "col")),
+                                          C.c_void_p(_dev(val, torch.float64, "val")),
+                                          C.c_void_p(_dev(taylor.contiguous(), torch.float64, "taylor")),
+                                          C.c_void_p(p_y), float(t), C.c_void_p(work.data_ptr()),
+                                          C.c_void_p(coef.data_ptr()), _stream(stream)), "mcx_cv_coefficients")
+    return coef
+
+
+class MLP:
+    """The 5-64-64-1 control-variate network (BF16 weights in use, FP32 master)."""
+
+    NPARAM = 4609
+
+    def __init__(self, seed: int = 0):
+        out = C.c_void_p()
+        check(_lib.load().mcx_mlp_create(int(seed), C.byref(out)), "mcx_mlp_create")
+        self._h = out
+
+    def get(self):
+        import numpy as np
+
+        p = np.zeros(self.NPARAM, np.float32)
+        mu = np.zeros(5, np.float32)
+        sd = np.zeros(5, np.float32)
+        check(_lib.load().mcx_mlp_get(self._h, p.ctypes.data, mu.ctypes.data, sd.ctypes.data), "mcx_mlp_get")
+        return p, mu, sd
+
+    def set(self, params=None, mu=None, sd=None):
+        import numpy as np
+
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in (params, mu, sd)]
+        check(_lib.load().mcx_mlp_set(self._h, *[None if a is None else a.ctypes.data for a in arrs]),
+              "mcx_mlp_set")
+
+    def predict(self, features, stream=None):
+        n = features.shape[0]
+        y = torch.empty(n, dtype=torch.float32, device=features.device)
+        check(_lib.load().mcx_mlp_predict(self._h, n, C.c_void_p(_dev(features.contiguous(), torch.float32, "f")),
+                                          C.c_void_p(y.data_ptr()), _stream(stream)), "mcx_mlp_predict")
+        return y
+
+    def gradient(self, features, targets, stream=None):
+        g = torch.empty(self.NPARAM, dtype=torch.float32, device=features.device)
+        loss = C.c_float()
+        check(_lib.load().mcx_mlp_gradient(self._h, features.shape[0],
+                                           C.c_void_p(_dev(features.contiguous(), torch.float32, "f")),
+                                           C.c_void_p(_dev(targets, torch.float32, "targets")),
+                                           C.c_void_p(g.data_ptr()), C.byref(loss), _stream(stream)),
+              "mcx_mlp_gradient")
+        return g, loss.value
+
+    def fit(self, features, targets, epochs=20, batch=4096, lr=1e-3, seed=0, stream=None):
+        import numpy as np
+
+        losses = np.zeros(max(epochs, 1), np.float32)
+        check(_lib.load().mcx_mlp_fit(self._h, features.shape[0],
+                                      C.c_void_p(_dev(features.contiguous(), torch.float32, "f")),
+                                      C.c_void_p(_dev(targets, torch.float32, "targets")), int(epochs), int(batch),
+                                      float(lr), int(seed), losses.ctypes.data, _stream(stream)), "mcx_mlp_fit")
+        return losses[:epochs]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.load().mcx_mlp_destroy(self._h)
             self._h = None
 
     def __del__(self):  # pragma: no cover

@@ -1,0 +1,837 @@
+// Learned control variate (variance reduction, Sec. 5).
+//
+// Estimator: for any h with h(0) = v, x_i = h(t, i) + E_i[int_0^t W_s R(t - s, X_s) ds]
+// with R = A h - dh/dtau (Duhamel's formula with the Feynman-Kac form of
+// exp(sA)).  We take h(tau) = v + tau Av + tau^2 A^2v/2 + tau^3 c3 with c3 set so
+// that h(t) = xhat, the network's prediction: c3 = (xhat - T2)/t^3,
+// T2 = v + t Av + t^2 A^2 v/2, hence R(tau, j) = a_j tau^2 + b_j tau^3 with
+// a = A^3 v/2 - 3 c3 and b = A c3.  Over a hold of length D in state j starting
+// with remaining time r and log-weight L the residual integral is exactly
+//   e^L sum_k c_k D^{k+1} phi_k(delta_j D),   phi_k(z) = int_0^1 e^{zs} s^k ds,
+// where R(r - u) = c0 + c1 u + c2 u^2 + c3' u^3.  phi_k: series for |z| <= 1
+// (FP32) or 2 (FP64), the recursion phi_k = (e^z - k phi_{k-1})/z otherwise.
+//
+// Kernels: FP64 SpMV for the Taylor terms; node features; a 5-64-64-1 ReLU MLP
+// (weights rounded to BF16 on load, FP32 accumulation) for prediction,
+// full-batch gradients and Adam training (block partial gradients reduced in a
+// fixed order: deterministic); the coefficient builder; and the CV walker (the
+// FP32 path of the backward walker, with the residual integral in FP32 or FP64).
+#include <math.h>
+
+#include <algorithm>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "walker.cuh"
+
+namespace mcx {
+namespace {
+
+constexpr int NF = 5;    // features
+constexpr int HID = 64;  // hidden width
+constexpr int P_W1 = 0;
+constexpr int P_B1 = P_W1 + NF * HID;
+constexpr int P_W2 = P_B1 + HID;
+constexpr int P_B2 = P_W2 + HID * HID;
+constexpr int P_W3 = P_B2 + HID;
+constexpr int P_B3 = P_W3 + HID;
+constexpr int NPARAM = P_B3 + 1;  // 4609
+constexpr int FWD_THREADS = 128;
+constexpr int GRAD_SAMPLES = 64;  // samples per gradient block (one per thread)
+
+// ---------------------------------------------------------------------------
+// Taylor terms and features
+// ---------------------------------------------------------------------------
+__global__ void k_spmv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                       const double *__restrict__ val, const double *__restrict__ x, double *__restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) acc = __fma_rn(val[p], x[col[p]], acc);
+        y[i] = acc;
+    }
+}
+
+// rate lambda_i (sum of positive off-diagonal entries, CSR order) into lam
+__global__ void k_rates(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                        const double *__restrict__ val, double *__restrict__ lam) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+            if (col[p] != i && val[p] > 0.0) s = __dadd_rn(s, val[p]);
+        lam[i] = s;
+    }
+}
+
+__global__ void k_features(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                           const double *__restrict__ val, const double *__restrict__ lam,
+                           const double *__restrict__ T, double t, float *__restrict__ F) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s1 = 0.0, s2 = 0.0;
+        int64_t d = 0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+            const int32_t c = col[p];
+            if (c != i && val[p] > 0.0) {
+                const double l = lam[c];
+                s1 += l;
+                s2 += l * l;
+                ++d;
+            }
+        }
+        const double mean = d > 0 ? s1 / (double)d : 0.0;
+        double var = d > 0 ? s2 / (double)d - mean * mean : 0.0;
+        if (var < 0.0) var = 0.0;
+        const double T2 = T[i] + t * T[n + i] + t * t * T[2 * n + i] / 2.0;
+        const double T2s = T2 != 0.0 ? T2 : 1.0;
+        float *f = F + i * NF;
+        f[0] = (float)log1p(lam[i]);
+        f[1] = (float)log1p(mean);
+        f[2] = (float)log1p(sqrt(var));
+        f[3] = (float)(t * T[n + i] / T2s);
+        f[4] = (float)(t * t * T[2 * n + i] / (2.0 * T2s));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// MLP
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float bf16_round(float x) {
+    uint32_t u = __float_as_uint(x);
+    u = (u + 0x7FFFu + ((u >> 16) & 1u)) & 0xFFFF0000u;
+    return __uint_as_float(u);
+}
+
+struct MLPView {
+    const float *params;  // FP32 master (weights rounded to BF16 when loaded)
+    const float *mu;      // [NF] feature means
+    const float *sd;      // [NF] feature standard deviations
+};
+
+// weights to shared memory: W rounded to BF16, biases as they are
+__device__ void load_params(const float *__restrict__ p, float *s) {
+    for (int k = threadIdx.x; k < NPARAM; k += blockDim.x) {
+        const bool is_w = (k < P_B1) || (k >= P_W2 && k < P_B2) || (k >= P_W3 && k < P_B3);
+        s[k] = is_w ? bf16_round(p[k]) : p[k];
+    }
+}
+
+__device__ __forceinline__ void standardise(const float *__restrict__ f, const MLPView &m, float x[NF]) {
+#pragma unroll
+    for (int q = 0; q < NF; ++q) x[q] = (f[q] - m.mu[q]) / m.sd[q];
+}
+
+// y = W3 . relu(W2^T relu(W1^T x + b1) + b2) + b3, FP32 accumulation
+__device__ float mlp_eval(const float x[NF], const float *__restrict__ s) {
+    float h1[HID];
+#pragma unroll
+    for (int j = 0; j < HID; ++j) {
+        float a = s[P_B1 + j];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) a = fmaf(x[q], s[P_W1 + q * HID + j], a);
+        h1[j] = fmaxf(a, 0.0f);
+    }
+    float y = s[P_B3];
+#pragma unroll
+    for (int kc = 0; kc < HID; kc += 16) {
+        float acc[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc[k] = s[P_B2 + kc + k];
+#pragma unroll
+        for (int j = 0; j < HID; ++j) {
+            const float hj = h1[j];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) acc[k] = fmaf(hj, s[P_W2 + j * HID + kc + k], acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) y = fmaf(fmaxf(acc[k], 0.0f), s[P_W3 + kc + k], y);
+    }
+    return y;
+}
+
+__global__ void __launch_bounds__(FWD_THREADS) k_mlp_predict(int64_t n, const float *__restrict__ F, MLPView m,
+                                                              float *__restrict__ y) {
+    __shared__ float s[NPARAM];
+    load_params(m.params, s);
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        float x[NF];
+        standardise(F + i * NF, m, x);
+        y[i] = mlp_eval(x, s);
+    }
+}
+
+// Gradient of the mean squared error over samples [0, n) with respect to the
+// weights as used (BF16-rounded).  Block b takes samples [b*64, b*64+64), one
+// per thread, and writes its partial gradient (and loss) to part[b]; the
+// per-sample activations and deltas go through shared memory for the
+// reductions over the block's samples.
+__global__ void __launch_bounds__(GRAD_SAMPLES) k_mlp_grad(int64_t n, const float *__restrict__ F,
+                                                          const float *__restrict__ tgt, const int64_t *__restrict__ idx,
+                                                          MLPView m, float inv_batch, float *__restrict__ part) {
+    extern __shared__ float sm[];
+    float *s = sm;                          // NPARAM weights (+3 pad)
+    float *X = s + NPARAM + 3;              // [64][NF] standardised inputs
+    float *H1 = X + GRAD_SAMPLES * NF;      // [64][HID]
+    float *H2 = H1 + GRAD_SAMPLES * HID;    // [64][HID]
+    float *D2 = H2 + GRAD_SAMPLES * HID;    // [64][HID]
+    float *D1 = D2 + GRAD_SAMPLES * HID;    // [64][HID]
+    float *DY = D1 + GRAD_SAMPLES * HID;    // [64]
+    float *LS = DY + GRAD_SAMPLES;          // [64] squared residuals
+    load_params(m.params, s);
+    const int tid = threadIdx.x;
+    const int64_t smp = (int64_t)blockIdx.x * GRAD_SAMPLES + tid;
+    const bool valid = smp < n;
+    float x[NF] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float target = 0.0f;
+    if (valid) {
+        const int64_t row = idx ? idx[smp] : smp;
+        standardise(F + row * NF, m, x);
+        target = tgt[row];
+    }
+#pragma unroll
+    for (int q = 0; q < NF; ++q) X[tid * NF + q] = x[q];
+    __syncthreads();
+    // forward (one sample per thread)
+    for (int j = 0; j < HID; ++j) {
+        float a = s[P_B1 + j];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) a = fmaf(x[q], s[P_W1 + q * HID + j], a);
+        H1[tid * HID + j] = fmaxf(a, 0.0f);
+    }
+    float y = s[P_B3];
+    for (int kc = 0; kc < HID; kc += 16) {
+        float acc[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc[k] = s[P_B2 + kc + k];
+        for (int j = 0; j < HID; ++j) {
+            const float hj = H1[tid * HID + j];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) acc[k] = fmaf(hj, s[P_W2 + j * HID + kc + k], acc[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            H2[tid * HID + kc + k] = fmaxf(acc[k], 0.0f);
+            D2[tid * HID + kc + k] = acc[k] > 0.0f ? 1.0f : 0.0f;  // mask, scaled below
+            y = fmaf(fmaxf(acc[k], 0.0f), s[P_W3 + kc + k], y);
+        }
+    }
+    const float r = valid ? y - target : 0.0f;
+    const float dy = 2.0f * r * inv_batch;
+    DY[tid] = dy;
+    LS[tid] = r * r;
+    for (int k = 0; k < HID; ++k) D2[tid * HID + k] *= dy * s[P_W3 + k];
+    // d1 = (W2 d2) masked by h1 > 0
+    for (int j = 0; j < HID; ++j) {
+        float a = 0.0f;
+#pragma unroll 8
+        for (int k = 0; k < HID; ++k) a = fmaf(s[P_W2 + j * HID + k], D2[tid * HID + k], a);
+        D1[tid * HID + j] = H1[tid * HID + j] > 0.0f ? a : 0.0f;
+    }
+    __syncthreads();
+    float *out = part + (int64_t)blockIdx.x * (NPARAM + 1);
+    for (int e = tid; e < HID * HID; e += GRAD_SAMPLES) {  // W2[j][k] = sum_s h1[s][j] d2[s][k]
+        const int j = e / HID, k = e % HID;
+        float a = 0.0f;
+        for (int q = 0; q < GRAD_SAMPLES; ++q) a = fmaf(H1[q * HID + j], D2[q * HID + k], a);
+        out[P_W2 + e] = a;
+    }
+    {
+        const int k = tid;  // one hidden unit per thread
+        float gb2 = 0.0f, gb1 = 0.0f, gw3 = 0.0f;
+        for (int q = 0; q < GRAD_SAMPLES; ++q) {
+            gb2 += D2[q * HID + k];
+            gb1 += D1[q * HID + k];
+            gw3 = fmaf(H2[q * HID + k], DY[q], gw3);
+        }
+        out[P_B2 + k] = gb2;
+        out[P_B1 + k] = gb1;
+        out[P_W3 + k] = gw3;
+        for (int f = 0; f < NF; ++f) {
+            float a = 0.0f;
+            for (int q = 0; q < GRAD_SAMPLES; ++q) a = fmaf(X[q * NF + f], D1[q * HID + k], a);
+            out[P_W1 + f * HID + k] = a;
+        }
+    }
+    if (tid == 0) {
+        float gb3 = 0.0f, loss = 0.0f;
+        for (int q = 0; q < GRAD_SAMPLES; ++q) {
+            gb3 += DY[q];
+            loss += LS[q];
+        }
+        out[P_B3] = gb3;
+        out[NPARAM] = loss * inv_batch;
+    }
+}
+
+// Sum the block partials in block order (deterministic); optionally apply Adam.
+__global__ void k_grad_reduce(int nblocks, const float *__restrict__ part, float *__restrict__ grad,
+                              float *__restrict__ params, float *__restrict__ m1, float *__restrict__ m2, float lr,
+                              float b1c, float b2c, int adam) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > NPARAM) return;
+    float g = 0.0f;
+    for (int b = 0; b < nblocks; ++b) g += part[(int64_t)b * (NPARAM + 1) + k];
+    grad[k] = g;
+    if (!adam || k == NPARAM) return;
+    const float a = 0.9f * m1[k] + 0.1f * g;
+    const float v = 0.999f * m2[k] + 0.001f * g * g;
+    m1[k] = a;
+    m2[k] = v;
+    params[k] -= lr * (a / b1c) / (sqrtf(v / b2c) + 1e-8f);
+}
+
+// feature mean / standard deviation over n samples (one block per feature, fixed order)
+__global__ void k_feature_stats(int64_t n, const float *__restrict__ F, float *mu, float *sd) {
+    __shared__ double sh[256][2];
+    const int f = blockIdx.x;
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double x = F[i * NF + f];
+        s1 += x;
+        s2 += x * x;
+    }
+    sh[threadIdx.x][0] = s1;
+    sh[threadIdx.x][1] = s2;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            sh[threadIdx.x][0] += sh[threadIdx.x + o][0];
+            sh[threadIdx.x][1] += sh[threadIdx.x + o][1];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double m = sh[0][0] / (double)n;
+        const double v = sh[0][1] / (double)n - m * m;
+        mu[f] = (float)m;
+        sd[f] = (float)(v > 1e-12 ? sqrt(v) : 1.0);
+    }
+}
+
+// xhat = T2 e^y; c3 = (xhat - T2)/t^3 -> coef: h [n], then (a, b) pairs [n]; c3 staged in b's slot
+__global__ void k_cv_xhat(int64_t n, const double *__restrict__ T, const float *__restrict__ y, double t,
+                          double *__restrict__ h, double *__restrict__ c3) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double T2 = T[i] + t * T[n + i] + t * t * T[2 * n + i] / 2.0;
+        const double xh = T2 * exp((double)(y ? y[i] : 0.0f));
+        h[i] = xh;
+        c3[i] = (xh - T2) / (t * t * t);
+    }
+}
+
+__global__ void k_cv_targets(int64_t n, const double *__restrict__ x, const double *__restrict__ T, double t,
+                             float *__restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double T2 = T[i] + t * T[n + i] + t * t * T[2 * n + i] / 2.0;
+        const double q = T2 != 0.0 ? x[i] / T2 : 1.0;
+        y[i] = (float)log(q > 1e-6 ? q : 1e-6);
+    }
+}
+
+__global__ void k_cv_ab(int64_t n, const double *__restrict__ T, const double *__restrict__ c3,
+                        const double *__restrict__ Ac3, double2 *__restrict__ ab) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        ab[i] = make_double2(T[3 * n + i] / 2.0 - 3.0 * c3[i], Ac3[i]);
+}
+
+// ---------------------------------------------------------------------------
+// CV walker
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void phis(R z, R ph[4]) {
+    const R lim = sizeof(R) == 8 ? (R)2.0 : (R)1.0;
+    if (fabs(z) <= lim) {
+        const int terms = sizeof(R) == 8 ? 40 : 14;
+        R term = (R)1, s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        for (int n = 0; n < terms; ++n) {
+            s0 += term / (R)(n + 1);
+            s1 += term / (R)(n + 2);
+            s2 += term / (R)(n + 3);
+            s3 += term / (R)(n + 4);
+            term *= z / (R)(n + 1);
+        }
+        ph[0] = s0; ph[1] = s1; ph[2] = s2; ph[3] = s3;
+    } else {
+        const R ez = sizeof(R) == 8 ? (R)exp((double)z) : (R)expf((float)z);
+        ph[0] = (ez - (R)1) / z;
+        ph[1] = (ez - (R)1 * ph[0]) / z;
+        ph[2] = (ez - (R)2 * ph[1]) / z;
+        ph[3] = (ez - (R)3 * ph[2]) / z;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ R hold_integral(R a, R b, R delta, R r, R D) {
+    const R c0 = a * r * r + b * r * r * r;
+    const R c1 = (R)-2 * a * r - (R)3 * b * r * r;
+    const R c2 = a + (R)3 * b * r;
+    const R c3 = -b;
+    R ph[4];
+    phis<R>(delta * D, ph);
+    return c0 * D * ph[0] + c1 * D * D * ph[1] + c2 * D * D * D * ph[2] + c3 * D * D * D * D * ph[3];
+}
+
+struct CVArgs {
+    const double *h;    // [n] h(t, i) = xhat_i
+    const double2 *ab;  // [n] (a, b)
+};
+
+// Residual accumulators: FP64 plain sums, or FP32 per-path scaled sums.
+template <bool F64I, bool WEIGHTED>
+__global__ void __launch_bounds__(WALK_THREADS) k_walk_cv(const __grid_constant__ WalkParams a, CVArgs cv) {
+    using R = typename std::conditional<F64I, double, float>::type;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const uint64_t wid = (uint64_t)blockIdx.x * WARPS_PER_BLOCK + warp;
+    const uint64_t n_chunks = (uint64_t)a.n_entries * a.chunks_per_entry;
+    if (wid >= n_chunks) return;
+    const uint64_t e_idx = wid / a.chunks_per_entry;
+    const uint64_t chunk = wid - e_idx * a.chunks_per_entry;
+    const int32_t i = a.entries ? __ldg(a.entries + e_idx) : (int32_t)e_idx;
+    if (i < 0 || (int64_t)i >= a.n) {
+        if (lane == 0) {
+            atomicOr(a.status, ST_BAD_ENTRY);
+            a.partials[wid] = Partial{QNAN, 0.0, 0.0};
+        }
+        return;
+    }
+    const uint64_t p_begin = chunk * a.chunk_len;
+    const uint32_t len = (uint32_t)(min(a.paths, p_begin + a.chunk_len) - p_begin);
+    const uint64_t base = a.path_offset + p_begin;
+    const NodeRec start = load_node(a.node, i);
+    Walker<false> w;
+    w.rec = start; w.j = i; w.r = a.t32; w.acc = 0.0f; w.delta = start.delta; w.k = 0;
+    // per-path residual: y = e^{Ls} ys (FP32) or y (FP64)
+    R ys = (R)0;
+    float Ls = 0.0f;
+    double s1 = 0.0, s2 = 0.0;        // FP64 sums over finished paths (FP64 integral)
+    float m = -INFINITY, f1 = 0.f, c1 = 0.f, f2 = 0.f;  // FP32: shifted compensated sums
+    uint32_t next = 32, p = (uint32_t)lane;
+    bool active = p < len;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    while (__any_sync(0xffffffffu, active)) {
+        bool fin = false;
+        if (active) {
+            const int32_t j = w.j;
+            const float r0 = w.r, L0 = w.acc, dl = w.delta;
+            float D;  // the hold just simulated: S (jump) or r0 (end)
+            fin = advance<MCX_EXACT, WEIGHTED, false>(w, a, (uint32_t)i, base + p, nullptr, -1, &D);
+            const double2 c = __ldg(cv.ab + j);
+            const R J = hold_integral<R>((R)c.x, (R)c.y, (R)dl, (R)r0, (R)D);
+            if (F64I) {
+                ys += (R)exp((double)L0) * J;
+            } else {
+                if (L0 > Ls + 40.0f) {  // keep e^{L - Ls} in range
+                    ys *= (R)expf(Ls - L0);
+                    Ls = L0;
+                }
+                ys += (R)expf(L0 - Ls) * J;
+            }
+            if (fin) {
+                if (F64I) {
+                    s1 += (double)ys;
+                    s2 += (double)ys * (double)ys;
+                } else {
+                    // fold e^{Ls} ys into the lane's shifted compensated sums
+                    const float Lp = Ls;
+                    if (!(Lp <= m + 8.0f)) {
+                        const float sc = (m == -INFINITY) ? 0.0f : expf(m - Lp);
+                        f1 *= sc; c1 *= sc; f2 *= sc * sc;
+                        m = Lp;
+                    }
+                    const float wv = __fmul_rn(expf(__fsub_rn(Lp, m)), (float)ys);
+                    const float yk = __fsub_rn(wv, c1);
+                    const float tk = __fadd_rn(f1, yk);
+                    c1 = __fsub_rn(__fsub_rn(tk, f1), yk);
+                    f1 = tk;
+                    f2 = __fmaf_rn(wv, wv, f2);
+                }
+            }
+        }
+        const unsigned fm = __ballot_sync(0xffffffffu, fin);
+        if (fm) {
+            if (fin) {
+                p = next + (uint32_t)__popc(fm & lt_mask);
+                active = p < len;
+                w.rec = start; w.j = i; w.r = a.t32; w.acc = 0.0f; w.delta = start.delta; w.k = 0;
+                ys = (R)0;
+                Ls = 0.0f;
+            }
+            next += (uint32_t)__popc(fm);
+        }
+    }
+    double S1, S2, Mw;
+    if (F64I) {
+        S1 = s1;
+        S2 = s2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+            S2 += __shfl_xor_sync(0xffffffffu, S2, o);
+        }
+        Mw = 0.0;
+    } else {
+        float mw = m;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+        const double sc = (m == -INFINITY) ? 0.0 : exp((double)m - (double)mw);
+        S1 = sc * ((double)f1 - (double)c1);
+        S2 = sc * sc * (double)f2;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            S1 += __shfl_xor_sync(0xffffffffu, S1, o);
+            S2 += __shfl_xor_sync(0xffffffffu, S2, o);
+        }
+        Mw = (double)mw;
+    }
+    if (lane == 0) a.partials[wid] = Partial{S1, S2, Mw};
+}
+
+// mean = h_i + (e^m sum y)/M over the entry's chunks; sem from the residual variance
+__global__ void k_cv_finish(const Partial *__restrict__ part, int64_t n_entries, uint32_t cpe, double M,
+                            const int32_t *__restrict__ entries, const double *__restrict__ h, double *mean,
+                            double *sem, uint32_t *status) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_entries) return;
+    const Partial *pp = part + (uint64_t)e * cpe;
+    double mx = -INFINITY;
+    for (uint32_t c = 0; c < cpe; ++c) mx = fmax(mx, pp[c].m);
+    double s1 = 0.0, s2 = 0.0;
+    bool bad = false;
+    for (uint32_t c = 0; c < cpe; ++c) {
+        const Partial q = pp[c];
+        if (isnan(q.s1)) bad = true;
+        const double sc = q.m == -INFINITY ? 0.0 : exp(q.m - mx);
+        s1 += sc * q.s1;
+        s2 += sc * sc * q.s2;
+    }
+    const int64_t i = entries ? entries[e] : e;
+    if (bad) {
+        mean[e] = QNAN;
+        if (sem) sem[e] = QNAN;
+        return;
+    }
+    const double scale = mx == -INFINITY ? 0.0 : exp(mx);
+    const double mu = s1 / M;
+    double var = M > 1.0 ? (s2 - s1 * mu) / (M - 1.0) : 0.0;
+    if (var < 0.0) var = 0.0;
+    mean[e] = h[i] + scale * mu;
+    if (sem) sem[e] = scale * sqrt(var / M);
+    if (!isfinite(mean[e])) atomicOr(status, ST_OVERFLOW);
+}
+
+unsigned blocks_for(int64_t n, int threads) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 152 * 32));
+}
+
+}  // namespace
+}  // namespace mcx
+
+using namespace mcx;
+
+struct mcx_mlp {
+    float *params = nullptr;  // [NPARAM + 1] (last: unused)
+    float *m1 = nullptr, *m2 = nullptr;
+    float *stats = nullptr;   // mu [NF], sd [NF]
+    float *grad = nullptr;    // [NPARAM + 1] (last: loss)
+    float *part = nullptr;
+    int64_t part_blocks = 0;
+    int64_t *idx = nullptr;   // minibatch permutation
+    int64_t idx_n = 0;
+    int64_t step = 0;
+};
+
+namespace {
+
+mcx_status stat(cudaError_t e) {
+    if (e == cudaSuccess) return MCX_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return MCX_E_OOM;
+    }
+    return MCX_E_CUDA;
+}
+
+MLPView view(const mcx_mlp *m) { return MLPView{m->params, m->stats, m->stats + NF}; }
+
+cudaError_t ensure_part(mcx_mlp *m, int64_t blocks) {
+    if (m->part_blocks >= blocks) return cudaSuccess;
+    cudaFree(m->part);
+    m->part = nullptr;
+    m->part_blocks = 0;
+    cudaError_t e = cudaMalloc(&m->part, sizeof(float) * (NPARAM + 1) * (size_t)blocks);
+    if (e == cudaSuccess) m->part_blocks = blocks;
+    return e;
+}
+
+size_t grad_smem() { return sizeof(float) * (NPARAM + 3 + GRAD_SAMPLES * NF + 4 * GRAD_SAMPLES * HID + 2 * GRAD_SAMPLES); }
+
+}  // namespace
+
+extern "C" {
+
+mcx_status mcx_cv_prepare(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val, const double *v,
+                          double t, double *work, double *taylor, float *features, void *stream) {
+    if (n < 1 || !row_ptr || !col || !val || !v || !work || !taylor || !features || !(t > 0.0)) return MCX_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned nb = blocks_for(n, 256);
+    cudaError_t e = cudaMemcpyAsync(taylor, v, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return stat(e);
+    for (int k = 1; k <= 3; ++k)
+        k_spmv<<<nb, 256, 0, st>>>(n, row_ptr, col, val, taylor + (k - 1) * n, taylor + k * n);
+    k_rates<<<nb, 256, 0, st>>>(n, row_ptr, col, val, work);
+    k_features<<<nb, 256, 0, st>>>(n, row_ptr, col, val, work, taylor, t, features);
+    return stat(cudaGetLastError());
+}
+
+mcx_status mcx_cv_targets(int64_t n, const double *x, const double *taylor, double t, float *y, void *stream) {
+    if (n < 1 || !x || !taylor || !y || !(t > 0.0)) return MCX_E_INVALID;
+    k_cv_targets<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, x, taylor, t, y);
+    return stat(cudaGetLastError());
+}
+
+mcx_status mcx_mlp_create(uint64_t seed, mcx_mlp **out) {
+    if (!out) return MCX_E_INVALID;
+    *out = nullptr;
+    mcx_mlp *m = new (std::nothrow) mcx_mlp();
+    if (!m) return MCX_E_OOM;
+    // He-uniform weights from a counter-based stream (host), small uniform biases
+    std::vector<float> p(NPARAM + 1, 0.0f);
+    uint64_t s = seed * 0x9E3779B97F4A7C15ull + 0x2545F4914F6CDD1Dull;
+    auto unif = [&s]() {  // splitmix64
+        s += 0x9E3779B97F4A7C15ull;
+        uint64_t z = s;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * 0x1p-53;
+    };
+    auto fill = [&](int off, int count, double lim) {
+        for (int k = 0; k < count; ++k) p[off + k] = (float)((2.0 * unif() - 1.0) * lim);
+    };
+    fill(P_W1, NF * HID, sqrt(6.0 / NF));
+    fill(P_B1, HID, 0.1);
+    fill(P_W2, HID * HID, sqrt(6.0 / HID));
+    fill(P_B2, HID, 0.1);
+    fill(P_W3, HID, sqrt(6.0 / HID) * 0.1);
+    p[P_B3] = 0.0f;
+    std::vector<float> stats(2 * NF, 0.0f);
+    for (int f = 0; f < NF; ++f) stats[NF + f] = 1.0f;
+    cudaError_t e;
+    do {
+        if ((e = cudaMalloc(&m->params, sizeof(float) * (NPARAM + 1))) != cudaSuccess) break;
+        if ((e = cudaMalloc(&m->m1, sizeof(float) * (NPARAM + 1))) != cudaSuccess) break;
+        if ((e = cudaMalloc(&m->m2, sizeof(float) * (NPARAM + 1))) != cudaSuccess) break;
+        if ((e = cudaMalloc(&m->grad, sizeof(float) * (NPARAM + 1))) != cudaSuccess) break;
+        if ((e = cudaMalloc(&m->stats, sizeof(float) * 2 * NF)) != cudaSuccess) break;
+        cudaMemcpy(m->params, p.data(), sizeof(float) * (NPARAM + 1), cudaMemcpyHostToDevice);
+        cudaMemcpy(m->stats, stats.data(), sizeof(float) * 2 * NF, cudaMemcpyHostToDevice);
+        cudaMemset(m->m1, 0, sizeof(float) * (NPARAM + 1));
+        e = cudaMemset(m->m2, 0, sizeof(float) * (NPARAM + 1));
+    } while (0);
+    if (e != cudaSuccess) {
+        mcx_mlp_destroy(m);
+        return stat(e);
+    }
+    *out = m;
+    return MCX_OK;
+}
+
+mcx_status mcx_mlp_set(mcx_mlp *m, const float *params, const float *mu, const float *sd) {
+    if (!m) return MCX_E_INVALID;
+    cudaError_t e = cudaSuccess;
+    if (params) e = cudaMemcpy(m->params, params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && mu) e = cudaMemcpy(m->stats, mu, sizeof(float) * NF, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && sd) e = cudaMemcpy(m->stats + NF, sd, sizeof(float) * NF, cudaMemcpyHostToDevice);
+    return stat(e);
+}
+
+mcx_status mcx_mlp_get(const mcx_mlp *m, float *params, float *mu, float *sd) {
+    if (!m) return MCX_E_INVALID;
+    cudaError_t e = cudaSuccess;
+    if (params) e = cudaMemcpy(params, m->params, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && mu) e = cudaMemcpy(mu, m->stats, sizeof(float) * NF, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && sd) e = cudaMemcpy(sd, m->stats + NF, sizeof(float) * NF, cudaMemcpyDeviceToHost);
+    return stat(e);
+}
+
+mcx_status mcx_mlp_predict(const mcx_mlp *m, int64_t n, const float *features, float *y, void *stream) {
+    if (!m || n < 0 || (n > 0 && (!features || !y))) return MCX_E_INVALID;
+    if (n == 0) return MCX_OK;
+    k_mlp_predict<<<blocks_for(n, FWD_THREADS), FWD_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(n, features,
+                                                                                                   view(m), y);
+    return stat(cudaGetLastError());
+}
+
+mcx_status mcx_mlp_gradient(mcx_mlp *m, int64_t n, const float *features, const float *targets, float *grad,
+                            float *loss, void *stream) {
+    if (!m || n < 1 || !features || !targets || !grad) return MCX_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t blocks = (n + GRAD_SAMPLES - 1) / GRAD_SAMPLES;
+    cudaError_t e = ensure_part(m, blocks);
+    if (e != cudaSuccess) return stat(e);
+    cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem());
+    k_mlp_grad<<<(unsigned)blocks, GRAD_SAMPLES, grad_smem(), st>>>(n, features, targets, nullptr, view(m),
+                                                                     1.0f / (float)n, m->part);
+    k_grad_reduce<<<(NPARAM + 256) / 256, 256, 0, st>>>((int)blocks, m->part, m->grad, nullptr, nullptr, nullptr,
+                                                         0.f, 1.f, 1.f, 0);
+    e = cudaMemcpyAsync(grad, m->grad, sizeof(float) * NPARAM, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && loss) {
+        e = cudaMemcpyAsync(loss, m->grad + NPARAM, sizeof(float), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    return stat(e == cudaSuccess ? cudaGetLastError() : e);
+}
+
+mcx_status mcx_mlp_fit(mcx_mlp *m, int64_t n, const float *features, const float *targets, int32_t epochs,
+                       int32_t batch, float lr, uint64_t seed, float *epoch_loss, void *stream) {
+    if (!m || n < 1 || !features || !targets || epochs < 0 || batch < 1 || !(lr > 0.0f)) return MCX_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // feature standardisation from this training set
+    k_feature_stats<<<NF, 256, 0, st>>>(n, features, m->stats, m->stats + NF);
+    const int64_t bblocks = (batch + GRAD_SAMPLES - 1) / GRAD_SAMPLES;
+    cudaError_t e = ensure_part(m, bblocks);
+    if (e != cudaSuccess) return stat(e);
+    if (m->idx_n < n) {
+        cudaFree(m->idx);
+        m->idx = nullptr;
+        if ((e = cudaMalloc(&m->idx, sizeof(int64_t) * (size_t)n)) != cudaSuccess) return stat(e);
+        m->idx_n = n;
+    }
+    cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem());
+    std::vector<int64_t> perm(n);
+    uint64_t s = seed * 0xD1B54A32D192ED03ull + 1;
+    for (int32_t ep = 0; ep < epochs; ++ep) {
+        for (int64_t i = 0; i < n; ++i) perm[i] = i;
+        for (int64_t i = n - 1; i > 0; --i) {  // Fisher-Yates with splitmix64
+            s += 0x9E3779B97F4A7C15ull;
+            uint64_t z = s;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            std::swap(perm[i], perm[(int64_t)(z % (uint64_t)(i + 1))]);
+        }
+        cudaMemcpyAsync(m->idx, perm.data(), sizeof(int64_t) * (size_t)n, cudaMemcpyHostToDevice, st);
+        double eloss = 0.0;
+        int64_t nb = 0;
+        for (int64_t b0 = 0; b0 < n; b0 += batch) {
+            const int64_t bn = std::min<int64_t>(batch, n - b0);
+            const int64_t blocks = (bn + GRAD_SAMPLES - 1) / GRAD_SAMPLES;
+            ++m->step;
+            const float b1c = 1.0f - powf(0.9f, (float)m->step);
+            const float b2c = 1.0f - powf(0.999f, (float)m->step);
+            k_mlp_grad<<<(unsigned)blocks, GRAD_SAMPLES, grad_smem(), st>>>(bn, features, targets, m->idx + b0,
+                                                                             view(m), 1.0f / (float)bn, m->part);
+            k_grad_reduce<<<(NPARAM + 256) / 256, 256, 0, st>>>((int)blocks, m->part, m->grad, m->params, m->m1,
+                                                                 m->m2, lr, b1c, b2c, 1);
+            if (epoch_loss) {
+                float l = 0.0f;
+                cudaMemcpyAsync(&l, m->grad + NPARAM, sizeof(float), cudaMemcpyDeviceToHost, st);
+                cudaStreamSynchronize(st);
+                eloss += l;
+                ++nb;
+            }
+        }
+        if (epoch_loss) epoch_loss[ep] = (float)(eloss / (double)std::max<int64_t>(nb, 1));
+        if ((e = cudaGetLastError()) != cudaSuccess) return stat(e);
+    }
+    return stat(cudaStreamSynchronize(st));
+}
+
+void mcx_mlp_destroy(mcx_mlp *m) {
+    if (!m) return;
+    cudaFree(m->params);
+    cudaFree(m->m1);
+    cudaFree(m->m2);
+    cudaFree(m->stats);
+    cudaFree(m->grad);
+    cudaFree(m->part);
+    cudaFree(m->idx);
+    delete m;
+}
+
+mcx_status mcx_cv_coefficients(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                               const double *taylor, const float *y, double t, double *work, double *coef,
+                               void *stream) {
+    if (n < 1 || !row_ptr || !col || !val || !taylor || !work || !coef || !(t > 0.0)) return MCX_E_INVALID;
+    if (reinterpret_cast<uintptr_t>(coef) % 16 != 0) return MCX_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const unsigned nb = blocks_for(n, 256);
+    // layout: (a, b) pairs at offset 0 (16-byte aligned with the buffer), then h
+    double *c3 = work, *Ac3 = work + n;
+    k_cv_xhat<<<nb, 256, 0, st>>>(n, taylor, y, t, coef + 2 * n, c3);
+    k_spmv<<<nb, 256, 0, st>>>(n, row_ptr, col, val, c3, Ac3);
+    k_cv_ab<<<nb, 256, 0, st>>>(n, taylor, c3, Ac3, reinterpret_cast<double2 *>(coef));
+    return stat(cudaGetLastError());
+}
+
+mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_t paths, const int32_t *entries,
+                           int64_t n_entries, uint64_t seed, uint64_t path_offset, int precision, double *mean,
+                           double *sem, void *stream) {
+    if (!plan || !coef || !(t > 0.0) || !isfinite(t) || paths < 1 || paths > (1ull << 53)) return MCX_E_INVALID;
+    if (precision != MCX_FP32 && precision != MCX_FP64) return MCX_E_INVALID;
+    if (n_entries == 0) return MCX_OK;
+    if (n_entries < 0 || !mean || (!entries && n_entries != plan->n)) return MCX_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    WalkParams p{};
+    p.node = plan->node;
+    p.node64 = plan->node64;
+    p.edge_col = plan->edge_col;
+    p.edge16 = plan->edge16;
+    p.entries = entries;
+    p.n_entries = n_entries;
+    p.paths = paths;
+    p.nsteps = 1;
+    p.n = plan->n;
+    p.max_events = 1u << 30;
+    p.t64 = t;
+    p.t32 = (float)t;
+    p.path_offset = path_offset;
+    p.status = plan->status;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        p.rk0[r] = k0;
+        p.rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    const uint64_t target_warps = 152ull * 64ull * 8ull;
+    uint64_t cpe = (target_warps + (uint64_t)n_entries - 1) / (uint64_t)n_entries;
+    const uint64_t max_cpe = (paths + 1023) / 1024;
+    if (cpe > max_cpe) cpe = max_cpe;
+    if (cpe < 1) cpe = 1;
+    if ((paths + cpe - 1) / cpe > (1ull << 30)) cpe = (paths + (1ull << 30) - 1) >> 30;
+    uint64_t chunk = (paths + cpe - 1) / cpe;
+    chunk = (chunk + 31) / 32 * 32;
+    cpe = (paths + chunk - 1) / chunk;
+    p.chunk_len = chunk;
+    p.chunks_per_entry = (uint32_t)cpe;
+    const uint64_t n_chunks = (uint64_t)n_entries * cpe;
+    const size_t need = sizeof(Partial) * (size_t)n_chunks;
+    if (plan->scratch_bytes < need) {
+        cudaFree(plan->scratch);
+        plan->scratch = nullptr;
+        plan->scratch_bytes = 0;
+        cudaError_t e = cudaMalloc(&plan->scratch, need);
+        if (e != cudaSuccess) return stat(e);
+        plan->scratch_bytes = need;
+    }
+    p.partials = static_cast<Partial *>(plan->scratch);
+    if (reinterpret_cast<uintptr_t>(coef) % 16 != 0) return MCX_E_INVALID;  // (a, b) pairs are read as double2
+    CVArgs cv{coef + 2 * plan->n, reinterpret_cast<const double2 *>(coef)};
+    const unsigned grid = (unsigned)((n_chunks + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+    const bool wgt = plan->weighted_rows > 0;
+    if (precision == MCX_FP64) {
+        if (wgt) k_walk_cv<true, true><<<grid, WALK_THREADS, 0, st>>>(p, cv);
+        else k_walk_cv<true, false><<<grid, WALK_THREADS, 0, st>>>(p, cv);
+    } else {
+        if (wgt) k_walk_cv<false, true><<<grid, WALK_THREADS, 0, st>>>(p, cv);
+        else k_walk_cv<false, false><<<grid, WALK_THREADS, 0, st>>>(p, cv);
+    }
+    k_cv_finish<<<(unsigned)((n_entries + 255) / 256), 256, 0, st>>>(p.partials, n_entries, (uint32_t)cpe,
+                                                                       (double)paths, entries, coef + 2 * plan->n,
+                                                                       mean, sem, plan->status);
+    return stat(cudaGetLastError());
+}
+
+}  // extern "C"

@@ -143,7 +143,8 @@ struct Walker {
 // jumps out of state `i0` read the staged row.
 template <int MODE, bool WEIGHTED, bool F64>
 __device__ __forceinline__ bool advance(Walker<F64> &w, const WalkParams &a, uint32_t stream, uint64_t path,
-                                        const StageWarp *sw, int32_t i0) {
+                                        const StageWarp *sw, int32_t i0,
+                                        typename P<F64>::T *hold = nullptr) {
     using Q = P<F64>;
     using T = typename Q::T;
     const T invdt = F64 ? (T)a.invdt64 : (T)a.invdt32;
@@ -151,14 +152,17 @@ __device__ __forceinline__ bool advance(Walker<F64> &w, const WalkParams &a, uin
     if (w.rec.deg == 0 || w.k >= a.max_events) {
         if (w.rec.deg != 0) atomicOr(a.status, ST_OVERFLOW);  // event cap reached: result flagged
         w.acc = MODE == MCX_EXACT ? Q::fma(w.delta, w.r, w.acc) : Q::fma(w.delta, Q::from_int(Q::grid(w.r, invdt, N)), w.acc);
+        if (hold) *hold = w.r;
         return true;
     }
     const uint4 rnd = philox_rk(make_uint4(w.k, stream, (uint32_t)path, (uint32_t)(path >> 32)), a);
     const T S = Q::mul(Q::neg_ln(Q::unif(rnd)), Q::rate(w.rec, a.node64, w.j));
     if (S >= w.r) {
         w.acc = MODE == MCX_EXACT ? Q::fma(w.delta, w.r, w.acc) : Q::fma(w.delta, Q::from_int(Q::grid(w.r, invdt, N)), w.acc);
+        if (hold) *hold = w.r;
         return true;
     }
+    if (hold) *hold = S;
     const T rn = Q::sub(w.r, S);
     if (MODE == MCX_EXACT) {
         w.acc = Q::fma(w.delta, S, w.acc);

@@ -1,0 +1,191 @@
+"""GPU parity of the learned control variate (Sec. 5: variance reduction).
+
+* Taylor terms and node features against oracle/cv.py.
+* The network: predictions and full-batch gradients against the FP64 oracle
+  with the same BF16-rounded weights (the GPU accumulates in FP32), and Adam
+  training that drives the loss down.
+* The CV walker on the same paths as the oracle's CV estimator: FP64 residual
+  integrals within 1e-12, FP32 within 1e-5 of the entry's scale.
+* Unbiasedness for an arbitrary prediction (z-test against expm), zero
+  variance when h is exact, and the gain of the trained network over plain
+  MC and over the Taylor-only control variate at equal paths.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import cv as CV
+from oracle import dense as OD
+from oracle import walker as OW
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def mcx():
+    import paper_1904_12759_gb300 as P
+
+    P.load()
+    return P
+
+
+def _dev(csr):
+    return (torch.as_tensor(csr.row_ptr).cuda(), torch.as_tensor(csr.col).cuda(), torch.as_tensor(csr.val).cuda())
+
+
+def _conditioned(n, seed, rate=1.5, dsd=1.0):
+    rng = np.random.default_rng(seed)
+    a = np.where(rng.random((n, n)) < 0.3, rng.lognormal(0, 1, (n, n)), 0.0)
+    np.fill_diagonal(a, 0.0)
+    a *= rate / a.sum(axis=1).mean()
+    np.fill_diagonal(a, rng.normal(0, dsd, n) - a.sum(axis=1) + rng.normal(0, dsd, n))
+    return a
+
+
+def test_prepare_matches_oracle(mcx):
+    csr = W.barabasi_albert(3000, 5, 4)
+    v = W.uniform_vector(3000, 1)
+    t = 0.03
+    rp, col, val = _dev(csr)
+    T, F = mcx.cv_prepare(rp, col, val, torch.as_tensor(v).cuda(), t)
+    oF, oT2, oT = CV.features(csr, v, t)
+    assert np.allclose(T.cpu().numpy(), oT, rtol=1e-13, atol=1e-300)
+    assert np.allclose(F.cpu().numpy(), oF.astype(np.float32), rtol=2e-6, atol=1e-6)
+
+
+def test_network_forward_and_gradient_match_oracle(mcx):
+    rng = np.random.default_rng(2)
+    X = rng.normal(size=(777, 5)).astype(np.float32)  # ragged: not a multiple of 64
+    tgt = rng.normal(size=777).astype(np.float32)
+    net = mcx.MLP(seed=5)
+    p = CV.init_params(9)
+    flat = np.concatenate([p["W1"].ravel(), p["b1"], p["W2"].ravel(), p["b2"], p["W3"].ravel(), p["b3"]])
+    net.set(flat, np.zeros(5), np.ones(5))
+    y = net.predict(torch.as_tensor(X).cuda()).cpu().numpy()
+    oy, _ = CV.forward(p, X.astype(np.float64), round_weights=True)
+    assert np.allclose(y, oy, rtol=1e-5, atol=1e-5)
+    g, loss = net.gradient(torch.as_tensor(X).cuda(), torch.as_tensor(tgt).cuda())
+    g = g.cpu().numpy()
+    oloss, og = CV.loss_and_grad(p, X.astype(np.float64), tgt.astype(np.float64), round_weights=True)
+    assert abs(loss - oloss) <= 1e-5 * oloss
+    ogf = np.concatenate([og["W1"].ravel(), og["b1"], og["W2"].ravel(), og["b2"], og["W3"].ravel(), og["b3"]])
+    assert np.linalg.norm(g - ogf) <= 1e-4 * np.linalg.norm(ogf)
+    for a, b in ((0, 320), (320, 384), (384, 4480), (4480, 4544), (4544, 4608)):  # per tensor
+        assert np.linalg.norm(g[a:b] - ogf[a:b]) <= 1e-4 * np.linalg.norm(ogf[a:b]) + 1e-9
+    net.close()
+
+
+def test_training_reduces_loss(mcx):
+    rng = np.random.default_rng(0)
+    X = rng.normal(size=(20000, 5)).astype(np.float32)
+    tgt = (np.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2] - 0.3 * X[:, 3] ** 2).astype(np.float32)
+    net = mcx.MLP(seed=1)
+    losses = net.fit(torch.as_tensor(X).cuda(), torch.as_tensor(tgt).cuda(), epochs=15, batch=1024, lr=3e-3, seed=2)
+    assert losses[-1] < 0.2 * losses[0], losses
+    net.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cv_estimates_match_oracle_same_paths(mcx, prec):
+    a = _conditioned(80, 21)
+    csr = W.dense_to_csr(a)
+    v = W.uniform_vector(80, 2, -1.0, 1.0)
+    t = 0.8
+    rp, col, val = _dev(csr)
+    T, F = mcx.cv_prepare(rp, col, val, torch.as_tensor(v).cuda(), t)
+    yrand = torch.as_tensor(np.random.default_rng(3).normal(0, 0.5, 80).astype(np.float32)).cuda()
+    coef = mcx.cv_coefficients(rp, col, val, T, yrand, t)
+    # oracle coefficients from the same prediction
+    oT = CV.taylor_terms(csr, v)
+    T2 = oT[0] + t * oT[1] + t * t * oT[2] / 2
+    xhat = T2 * np.exp(yrand.cpu().numpy().astype(np.float64))
+    c3, ca, cb = CV.cv_coefficients(csr, oT, t, xhat)
+    cg = coef.cpu().numpy()
+    assert np.allclose(cg[160:], xhat, rtol=1e-13)
+    assert np.allclose(cg[:160].reshape(80, 2), np.stack([ca, cb], 1), rtol=1e-11, atol=1e-12 * np.abs(ca).max())
+    plan = mcx.Plan.from_csr(csr)
+    M = 3000
+    gm, gs = plan.estimate_cv(coef, t, M, seed=7, prec=prec)
+    om, os_ = OW.Graph(csr).estimate_cv(ca, cb, xhat, t, M, seed=7)
+    gm, gs = gm.cpu().numpy(), gs.cpu().numpy()
+    scale = np.abs(xhat) + os_ * math.sqrt(M)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert np.all(np.abs(gm - om) <= tol * scale), np.max(np.abs(gm - om) / scale)
+    assert np.allclose(gs, os_, rtol=1e-9 if prec == "fp64" else 1e-3)
+    # unbiased for this arbitrary prediction
+    z = (gm - OD.expmv_dense(a, t, v)) / gs
+    assert abs(z.mean()) < 5 / math.sqrt(80) + 0.1 and 0.5 < z.var() < 1.7
+    plan.close()
+
+
+def test_cv_exact_h_zero_variance(mcx):
+    a = np.zeros((3, 3))
+    a[0, 1] = 1.3
+    a[1, 2] = 0.7
+    csr = W.dense_to_csr(a)
+    v = np.array([0.2, 1.0, 2.0])
+    rp, col, val = _dev(csr)
+    T, _ = mcx.cv_prepare(rp, col, val, torch.as_tensor(v).cuda(), 0.9)
+    coef = mcx.cv_coefficients(rp, col, val, T, None, 0.9)
+    plan = mcx.Plan.from_csr(csr)
+    m, s = plan.estimate_cv(coef, 0.9, 4096, prec="fp64")
+    assert np.allclose(m.cpu().numpy(), OD.expmv_dense(a, 0.9, v), rtol=1e-13)
+    assert torch.all(s == 0)
+    plan.close()
+
+
+def test_learned_cv_gain_over_plain_and_taylor(mcx):
+    """Train on labels from the Taylor-only control-variate estimator on two small BA
+    graphs (the method's own estimates), then on a third graph compare, at equal
+    paths, the relative L2 error of plain MC, the Taylor-only CV and the learned CV
+    against the FP64 Taylor oracle; unbiasedness is checked with many paths on a
+    subset (per-path weights are skewed, so z-scores need large samples)."""
+    def setup(seed, n=20000):
+        csr = W.barabasi_albert(n, 5, seed)
+        v = W.uniform_vector(n, seed + 100)
+        lam = OD.power_iteration(csr.to_scipy(), iters=2000, tol=1e-10)
+        return csr, v, 0.5 / lam
+
+    feats, tgts = [], []
+    for seed in (1, 2):
+        csr, v, t = setup(seed)
+        rp, col, val = _dev(csr)
+        vd = torch.as_tensor(v).cuda()
+        plan = mcx.Plan.from_csr(csr)
+        T, F = mcx.cv_prepare(rp, col, val, vd, t)
+        x, _ = plan.estimate_cv(mcx.cv_coefficients(rp, col, val, T, None, t), t, 256, seed=seed)
+        feats.append(F)
+        tgts.append(mcx.cv_targets(x, T, t))
+        plan.close()
+    net = mcx.MLP(seed=3)
+    losses = net.fit(torch.cat(feats), torch.cat(tgts), epochs=30, batch=2048, lr=2e-3, seed=4)
+    assert losses[-1] < 0.5 * losses[0]
+    csr, v, t = setup(7)
+    rp, col, val = _dev(csr)
+    vd = torch.as_tensor(v).cuda()
+    plan = mcx.Plan.from_csr(csr)
+    T, F = mcx.cv_prepare(rp, col, val, vd, t)
+    x = OD.taylor_expmv(csr.to_scipy(), t, v)
+    M = 64
+    m_pl, s_pl = plan.estimate(vd, t, M, seed=9)
+    coef_tay = mcx.cv_coefficients(rp, col, val, T, None, t)
+    coef_cv = mcx.cv_coefficients(rp, col, val, T, net.predict(F), t)
+    m_tay, s_tay = plan.estimate_cv(coef_tay, t, M, seed=9)
+    m_cv, s_cv = plan.estimate_cv(coef_cv, t, M, seed=9)
+    err = lambda m: float(np.linalg.norm(m.cpu().numpy() - x) / np.linalg.norm(x))  # noqa: E731
+    rms = lambda s: float(np.sqrt(np.mean(s.cpu().numpy() ** 2)))  # noqa: E731
+    print(f"rel L2 error at M={M}: plain {err(m_pl):.3e} taylor-cv {err(m_tay):.3e} learned-cv {err(m_cv):.3e}; "
+          f"rms SE plain {rms(s_pl):.3e} taylor {rms(s_tay):.3e} learned {rms(s_cv):.3e}")
+    assert err(m_cv) < err(m_pl) / 10
+    assert rms(s_cv) < rms(s_tay)  # the network helps beyond the Taylor-only control variate
+    # unbiasedness with many paths on a subset
+    ent = torch.as_tensor(W.random_entries(csr.n, 300, 5)).cuda()
+    m, s = plan.estimate_cv(coef_cv, t, 20000, entries=ent, seed=11)
+    z = (m.cpu().numpy() - x[ent.cpu().numpy()]) / s.cpu().numpy()
+    assert abs(z.mean()) < 0.3 and float((np.abs(z) > 4).mean()) < 0.02, (z.mean(), z.var())
+    plan.close()
+    net.close()
