@@ -56,9 +56,10 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle CPU time for cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="erdos_renyi", choices=["erdos_renyi", "ctmc_batch", "heat3d"],
-                    help="erdos_renyi: the default line; ctmc_batch / heat3d: the batched CTMC transients and "
-                         "the 3D heat equation (own JSON lines)")
+    ap.add_argument("--workload", default="erdos_renyi", choices=["erdos_renyi", "ctmc_batch", "heat3d", "ba_cv"],
+                    help="erdos_renyi: the default line; ctmc_batch / heat3d / ba_cv: the batched CTMC "
+                         "transients, the 3D heat equation and the learned control variate's time to 1e-2 "
+                         "error (own JSON lines)")
     return ap.parse_args()
 
 
@@ -379,6 +380,105 @@ def run_heat3d(args):
     plan.close()
 
 
+def run_ba_cv(args):
+    """Learned control variate vs plain MC: time to 1e-2 relative L2 error on the full
+    vector exp(beta A) v, A the adjacency of a Barabasi-Albert graph (n = 4e6, m = 5),
+    beta = 0.5/lambda_max, v ~ U[0,1).  The network is trained first (reported
+    separately) on 8 BA(1e5, 5) graphs labelled by the Taylor-only control-variate
+    estimator with 256 paths per node.  GPU time per method includes every kernel the
+    method needs: features and Taylor terms, network, coefficients, walk, reduction."""
+    import numpy as np
+    import torch
+
+    import paper_1904_12759_gb300 as P
+    import workloads as W
+    from oracle import dense as OD
+
+    torch.cuda.set_device(0)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def dev(c):
+        return (torch.as_tensor(c.row_ptr).cuda(), torch.as_tensor(c.col).cuda(), torch.as_tensor(c.val).cuda())
+
+    # ---- training (once) ----
+    t_train0 = time.perf_counter()
+    e0 = ev()
+    e0.record()
+    feats, tgts = [], []
+    for seed in range(1, 9):
+        csr = W.barabasi_albert(10 ** 5, 5, seed)
+        rp, col, val = dev(csr)
+        vd = torch.as_tensor(W.uniform_vector(csr.n, seed + 100)).cuda()
+        lam, _ = P.power_iteration(rp, col, val, max_iters=20000, tol=1e-9)
+        t = 0.5 / lam
+        plan = P.Plan(rp, col, val)
+        T, F = P.cv_prepare(rp, col, val, vd, t)
+        x, _ = plan.estimate_cv(P.cv_coefficients(rp, col, val, T, None, t), t, 256, seed=seed)
+        feats.append(F)
+        tgts.append(P.cv_targets(x, T, t))
+        plan.close()
+    net = P.MLP(seed=0)
+    losses = net.fit(torch.cat(feats), torch.cat(tgts), epochs=30, batch=4096, lr=2e-3, seed=1)
+    e1 = ev()
+    e1.record()
+    torch.cuda.synchronize()
+    train = {"graphs": 8, "n": 10 ** 5, "label_paths": 256, "epochs": 30, "gpu_ms": e0.elapsed_time(e1),
+             "wall_s": time.perf_counter() - t_train0, "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
+    # ---- target graph ----
+    csr = W.barabasi_albert(4 * 10 ** 6, 5, SEED)
+    v = W.uniform_vector(csr.n, SEED)
+    rp, col, val = dev(csr)
+    vd = torch.as_tensor(v).cuda()
+    lam, iters = P.power_iteration(rp, col, val, max_iters=20000, tol=1e-9)
+    t = 0.5 / lam
+    x_ref = OD.taylor_expmv(csr.to_scipy(), t, v, norm_bound=lam)  # A, v >= 0: one sub-step, positive terms
+    xn = float(np.linalg.norm(x_ref))
+    plan = P.Plan(rp, col, val)
+    out = (torch.empty(csr.n, dtype=torch.float64, device="cuda"), torch.empty(csr.n, dtype=torch.float64, device="cuda"))
+
+    def run(method, M, seed):
+        a, b = ev(), ev()
+        a.record()
+        if method == "plain":
+            m, _ = plan.estimate(vd, t, M, seed=seed, out=out)
+        else:
+            T, F = P.cv_prepare(rp, col, val, vd, t)
+            y = net.predict(F) if method == "learned_cv" else None
+            m, _ = plan.estimate_cv(P.cv_coefficients(rp, col, val, T, y, t), t, M, seed=seed, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        err = float(np.linalg.norm(m.cpu().numpy() - x_ref)) / xn
+        return a.elapsed_time(b), err
+
+    for mth in ("plain", "taylor_cv", "learned_cv"):  # warm
+        run(mth, 1, 999)
+    results = {}
+    with ClockSampler(0) as clk:
+        for mth, mmax in (("plain", 1 << 15), ("taylor_cv", 1 << 12), ("learned_cv", 1 << 12)):
+            sweep = []
+            M = 1
+            while M <= mmax:
+                ms, err = run(mth, M, SEED + M)
+                sweep.append({"M": M, "ms": round(ms, 3), "rel_l2": err})
+                if err <= 1e-2:
+                    break
+                M *= 2
+            hit = next((r for r in sweep if r["rel_l2"] <= 1e-2), None)
+            results[mth] = {"time_to_1e-2_ms": hit["ms"] if hit else None, "M": hit["M"] if hit else None,
+                            "sweep": sweep}
+    tp = results["plain"]["time_to_1e-2_ms"]
+    tl = results["learned_cv"]["time_to_1e-2_ms"]
+    line = {"metric": "GPU time to 1e-2 relative L2 error, learned CV", "value": tl, "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32 paths, f64 accumulation", "data": "synthetic",
+            "config": {"workload": "ba_cv", "n": csr.n, "m": 5, "beta": "0.5/lambda_max", "lambda_max": lam,
+                       "power_iters": iters, "v": "U[0,1)", "target": "relative L2 error 1e-2 vs FP64 Taylor oracle"},
+            "speedup_vs_plain": (tp / tl) if (tp and tl) else None,
+            "results": results, "training": train, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    plan.close()
+    net.close()
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -389,6 +489,9 @@ def main():
         return
     if args.workload == "heat3d":
         run_heat3d(args)
+        return
+    if args.workload == "ba_cv":
+        run_ba_cv(args)
         return
     import numpy as np
     import torch
