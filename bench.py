@@ -518,7 +518,7 @@ def main():
     col = torch.as_tensor(csr.col).to(dev)
     val = torch.as_tensor(csr.val).to(dev)
     v = torch.ones(n, dtype=torch.float64, device=dev)
-    work = torch.empty(2 * n + 4096, dtype=torch.float64, device=dev)
+    work = torch.empty(3 * n + 4096, dtype=torch.float64, device=dev)
     mean = torch.empty(n, dtype=torch.float64, device=dev)
     sem = torch.empty(n, dtype=torch.float64, device=dev)
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device=dev)

@@ -245,7 +245,8 @@ mcx_status mcx_trace_paths(mcx_plan *plan, double t, int functional, int32_t nst
  * relative or after max_iters.  Works on the caller's CSR (device pointers,
  * same layout as mcx_plan_create, which must be valid: this call does not
  * re-validate it) with `work` a caller-owned device buffer of at least
- * 2n+4096 float64.  *lambda_out and *iters_out (either may be NULL)
+ * 3n+4096 float64.  Rows longer than 32 entries (hubs) are handled one warp
+ * per row.  *lambda_out and *iters_out (either may be NULL)
  * are host outputs; the call synchronises the stream.
  * Errors: MCX_E_INVALID, MCX_E_CUDA.
  */
@@ -361,7 +362,8 @@ typedef struct mcx_mlp mcx_mlp;
  *   features float32 [5n] out, node-major: log1p(lambda_i), log1p(mean of the
  *            neighbours' lambda), log1p(their standard deviation),
  *            t(Av)_i/T2_i, t^2(A^2v)_i/(2 T2_i), T2 = v + tAv + t^2A^2v/2
- *   work     float64 [n] scratch
+ *   work     float64 [2n + 64] scratch
+ * Rows longer than 32 entries (hubs) are handled one warp per row.
  * Errors: MCX_E_INVALID, MCX_E_CUDA.
  */
 mcx_status mcx_cv_prepare(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
@@ -409,7 +411,7 @@ void mcx_mlp_destroy(mcx_mlp *model);
  * control variate): coef float64 [3n] out = [(a_i, b_i) pairs (2n) | h (n)]
  * with h_i = xhat_i = T2_i e^{y_i}, c3 = (xhat - T2)/t^3, a = A^3 v/2 - 3 c3,
  * b = A c3; coef must be 16-byte aligned (the pairs are read as 16-byte
- * vectors).  work: float64 [2n] scratch.  Errors: MCX_E_INVALID, MCX_E_CUDA.
+ * vectors).  work: float64 [3n + 64] scratch.  Errors: MCX_E_INVALID, MCX_E_CUDA.
  */
 mcx_status mcx_cv_coefficients(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
                                const double *taylor, const float *y, double t, double *work, double *coef,

@@ -224,7 +224,7 @@ def power_iteration(row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
     Returns (lambda, iterations)."""
     n = row_ptr.numel() - 1
     if work is None:
-        work = torch.empty(2 * n + 4096, dtype=torch.float64, device=row_ptr.device)
+        work = torch.empty(3 * n + 4096, dtype=torch.float64, device=row_ptr.device)
     lam = C.c_double()
     it = C.c_int32()
     check(_lib.load().mcx_power_iteration(n, C.c_void_p(_dev(row_ptr, torch.int64, "row_ptr")),
@@ -346,7 +346,7 @@ def cv_prepare(row_ptr, col, val, v, t: float, stream=None):
     """Taylor terms [4, n] (v, Av, A^2v, A^3v) and node features [n, 5] of (A, v, t)."""
     n = row_ptr.numel() - 1
     dev = row_ptr.device
-    work = torch.empty(n, dtype=torch.float64, device=dev)
+    work = torch.empty(2 * n + 64, dtype=torch.float64, device=dev)
     taylor = torch.empty(4 * n, dtype=torch.float64, device=dev)
     feat = torch.empty(5 * n, dtype=torch.float32, device=dev)
     check(_lib.load().mcx_cv_prepare(n, C.c_void_p(_dev(row_ptr, torch.int64, "row_ptr")),
@@ -371,7 +371,7 @@ def cv_coefficients(row_ptr, col, val, taylor, y, t: float, stream=None):
     """coef [3n] = [(a, b) pairs | xhat] for mcx_estimate_cv (y None: Taylor-only)."""
     n = row_ptr.numel() - 1
     dev = row_ptr.device
-    work = torch.empty(2 * n, dtype=torch.float64, device=dev)
+    work = torch.empty(3 * n + 64, dtype=torch.float64, device=dev)
     coef = torch.empty(3 * n, dtype=torch.float64, device=dev)
     p_y = _dev(y, torch.float32, "y") if y is not None else 0
     check(_lib.load().mcx_cv_coefficients(n, C.c_void_p(_dev(row_ptr, torch.int64, "row_ptr")),

@@ -23,6 +23,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "rows.cuh"
 #include "walker.cuh"
 
 namespace mcx {
@@ -43,19 +44,11 @@ constexpr int GRAD_SAMPLES = 64;  // samples per gradient block (one per thread)
 // ---------------------------------------------------------------------------
 // Taylor terms and features
 // ---------------------------------------------------------------------------
-__global__ void k_spmv(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                       const double *__restrict__ val, const double *__restrict__ x, double *__restrict__ y) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) acc = __fma_rn(val[p], x[col[p]], acc);
-        y[i] = acc;
-    }
-}
-
-// rate lambda_i (sum of positive off-diagonal entries, CSR order) into lam
+// rate lambda_i (sum of positive off-diagonal entries) for rows of at most LONG_ROW entries
 __global__ void k_rates(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                         const double *__restrict__ val, double *__restrict__ lam) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (rp[i + 1] - rp[i] > LONG_ROW) continue;
         double s = 0.0;
         for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
             if (col[p] != i && val[p] > 0.0) s = __dadd_rn(s, val[p]);
@@ -63,32 +56,85 @@ __global__ void k_rates(int64_t n, const int64_t *__restrict__ rp, const int32_t
     }
 }
 
+// the same for the queued long rows, one warp per row
+__global__ void k_rates_long(const int32_t *__restrict__ queue, const unsigned int *qn,
+                             const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                             const double *__restrict__ val, double *__restrict__ lam) {
+    const int lane = threadIdx.x & 31;
+    const unsigned int nq = *qn;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
+        const int32_t i = queue[q];
+        double s = 0.0;
+        for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32)
+            if (col[p] != i && val[p] > 0.0) s += val[p];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) lam[i] = s;
+    }
+}
+
+__device__ __forceinline__ void write_features(int64_t n, int64_t i, double s1, double s2, double d,
+                                               const double *__restrict__ lam, const double *__restrict__ T,
+                                               double t, float *__restrict__ F) {
+    const double mean = d > 0 ? s1 / d : 0.0;
+    double var = d > 0 ? s2 / d - mean * mean : 0.0;
+    if (var < 0.0) var = 0.0;
+    const double T2 = T[i] + t * T[n + i] + t * t * T[2 * n + i] / 2.0;
+    const double T2s = T2 != 0.0 ? T2 : 1.0;
+    float *f = F + i * NF;
+    f[0] = (float)log1p(lam[i]);
+    f[1] = (float)log1p(mean);
+    f[2] = (float)log1p(sqrt(var));
+    f[3] = (float)(t * T[n + i] / T2s);
+    f[4] = (float)(t * t * T[2 * n + i] / (2.0 * T2s));
+}
+
 __global__ void k_features(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                            const double *__restrict__ val, const double *__restrict__ lam,
                            const double *__restrict__ T, double t, float *__restrict__ F) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double s1 = 0.0, s2 = 0.0;
-        int64_t d = 0;
+        if (rp[i + 1] - rp[i] > LONG_ROW) continue;
+        double s1 = 0.0, s2 = 0.0, d = 0.0;
         for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
             const int32_t c = col[p];
             if (c != i && val[p] > 0.0) {
                 const double l = lam[c];
                 s1 += l;
                 s2 += l * l;
-                ++d;
+                d += 1.0;
             }
         }
-        const double mean = d > 0 ? s1 / (double)d : 0.0;
-        double var = d > 0 ? s2 / (double)d - mean * mean : 0.0;
-        if (var < 0.0) var = 0.0;
-        const double T2 = T[i] + t * T[n + i] + t * t * T[2 * n + i] / 2.0;
-        const double T2s = T2 != 0.0 ? T2 : 1.0;
-        float *f = F + i * NF;
-        f[0] = (float)log1p(lam[i]);
-        f[1] = (float)log1p(mean);
-        f[2] = (float)log1p(sqrt(var));
-        f[3] = (float)(t * T[n + i] / T2s);
-        f[4] = (float)(t * t * T[2 * n + i] / (2.0 * T2s));
+        write_features(n, i, s1, s2, d, lam, T, t, F);
+    }
+}
+
+__global__ void k_features_long(int64_t n, const int32_t *__restrict__ queue, const unsigned int *qn,
+                                const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                const double *__restrict__ val, const double *__restrict__ lam,
+                                const double *__restrict__ T, double t, float *__restrict__ F) {
+    const int lane = threadIdx.x & 31;
+    const unsigned int nq = *qn;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
+        const int32_t i = queue[q];
+        double s1 = 0.0, s2 = 0.0, d = 0.0;
+        for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
+            const int32_t c = col[p];
+            if (c != i && val[p] > 0.0) {
+                const double l = lam[c];
+                s1 += l;
+                s2 += l * l;
+                d += 1.0;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            d += __shfl_xor_sync(0xffffffffu, d, o);
+        }
+        if (lane == 0) write_features(n, i, s1, s2, d, lam, T, t, F);
     }
 }
 
@@ -487,6 +533,97 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_cv(const __grid_constant_
     if (lane == 0) a.partials[wid] = Partial{S1, S2, Mw};
 }
 
+// Few paths per entry: one lane per entry, paths in path order, the lane writes
+// the entry's result (no partials).
+template <bool F64I, bool WEIGHTED>
+__global__ void __launch_bounds__(WALK_THREADS) k_walk_cv_lanes(const __grid_constant__ WalkParams a, CVArgs cv) {
+    using R = typename std::conditional<F64I, double, float>::type;
+    const int64_t e = (int64_t)blockIdx.x * WALK_THREADS + threadIdx.x;
+    const bool valid = e < a.n_entries;
+    unsigned long long jumps = 0, npaths = 0;
+    if (valid) {
+        const int32_t i = a.entries ? __ldg(a.entries + e) : (int32_t)e;
+        if (i < 0 || (int64_t)i >= a.n) {
+            atomicOr(a.status, ST_BAD_ENTRY);
+            a.mean[e] = QNAN;
+            if (a.sem) a.sem[e] = QNAN;
+        } else {
+            const NodeRec start = load_node(a.node, i);
+            double s1 = 0.0, s2 = 0.0;                           // FP64 residual sums
+            float m = -INFINITY, f1 = 0.f, c1 = 0.f, f2 = 0.f;  // FP32 shifted sums
+            for (uint64_t p = 0; p < a.paths; ++p) {
+                Walker<false> w;
+                w.rec = start; w.j = i; w.r = a.t32; w.acc = 0.0f; w.delta = start.delta; w.k = 0;
+                R ys = (R)0;
+                float Ls = 0.0f;
+                bool fin = false;
+                while (!fin) {
+                    const int32_t j = w.j;
+                    const float r0 = w.r, L0 = w.acc, dl = w.delta;
+                    float D;
+                    fin = advance<MCX_EXACT, WEIGHTED, false>(w, a, (uint32_t)i, a.path_offset + p, nullptr, -1, &D);
+                    const double2 c = __ldg(cv.ab + j);
+                    const R J = hold_integral<R>((R)c.x, (R)c.y, (R)dl, (R)r0, (R)D);
+                    if (F64I) {
+                        ys += (R)exp((double)L0) * J;
+                    } else {
+                        if (L0 > Ls + 40.0f) {
+                            ys *= (R)expf(Ls - L0);
+                            Ls = L0;
+                        }
+                        ys += (R)expf(L0 - Ls) * J;
+                    }
+                }
+                jumps += w.k;
+                if (F64I) {
+                    s1 += (double)ys;
+                    s2 += (double)ys * (double)ys;
+                } else {
+                    if (!(Ls <= m + 8.0f)) {
+                        const float sc = (m == -INFINITY) ? 0.0f : expf(m - Ls);
+                        f1 *= sc; c1 *= sc; f2 *= sc * sc;
+                        m = Ls;
+                    }
+                    const float wv = __fmul_rn(expf(__fsub_rn(Ls, m)), (float)ys);
+                    const float yk = __fsub_rn(wv, c1);
+                    const float tk = __fadd_rn(f1, yk);
+                    c1 = __fsub_rn(__fsub_rn(tk, f1), yk);
+                    f1 = tk;
+                    f2 = __fmaf_rn(wv, wv, f2);
+                }
+            }
+            npaths = a.paths;
+            double S1, S2, scale;
+            if (F64I) {
+                S1 = s1;
+                S2 = s2;
+                scale = 1.0;
+            } else {
+                S1 = (double)f1 - (double)c1;
+                S2 = (double)f2;
+                scale = m == -INFINITY ? 0.0 : exp((double)m);
+            }
+            const double M = (double)a.paths;
+            const double mu = S1 / M;
+            double var = M > 1.0 ? (S2 - S1 * mu) / (M - 1.0) : 0.0;
+            if (var < 0.0) var = 0.0;
+            a.mean[e] = cv.h[i] + scale * mu;
+            if (a.sem) a.sem[e] = scale * sqrt(var / M);
+            if (!isfinite(a.mean[e])) atomicOr(a.status, ST_OVERFLOW);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        jumps += __shfl_xor_sync(0xffffffffu, jumps, o);
+        npaths += __shfl_xor_sync(0xffffffffu, npaths, o);
+    }
+    if ((threadIdx.x & 31) == 0 && npaths) {
+        unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.status + 2);
+        atomicAdd(ctr, npaths);
+        atomicAdd(ctr + 1, jumps);
+    }
+}
+
 // mean = h_i + (e^m sum y)/M over the entry's chunks; sem from the residual variance
 __global__ void k_cv_finish(const Partial *__restrict__ part, int64_t n_entries, uint32_t cpe, double M,
                             const int32_t *__restrict__ entries, const double *__restrict__ h, double *mean,
@@ -575,12 +712,22 @@ mcx_status mcx_cv_prepare(int64_t n, const int64_t *row_ptr, const int32_t *col,
     if (n < 1 || !row_ptr || !col || !val || !v || !work || !taylor || !features || !(t > 0.0)) return MCX_E_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const unsigned nb = blocks_for(n, 256);
+    double *lam = work;
+    int32_t *queue = reinterpret_cast<int32_t *>(work + n);  // n int32
+    unsigned int *qn = reinterpret_cast<unsigned int *>(work + 2 * n);
     cudaError_t e = cudaMemcpyAsync(taylor, v, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(qn, 0, sizeof(unsigned int), st);
     if (e != cudaSuccess) return stat(e);
-    for (int k = 1; k <= 3; ++k)
-        k_spmv<<<nb, 256, 0, st>>>(n, row_ptr, col, val, taylor + (k - 1) * n, taylor + k * n);
-    k_rates<<<nb, 256, 0, st>>>(n, row_ptr, col, val, work);
-    k_features<<<nb, 256, 0, st>>>(n, row_ptr, col, val, work, taylor, t, features);
+    k_find_long_rows<<<nb, 256, 0, st>>>(n, row_ptr, queue, qn);
+    for (int k = 1; k <= 3; ++k) {
+        k_spmv_short<<<nb, 256, 0, st>>>(n, row_ptr, col, val, taylor + (k - 1) * n, nullptr, taylor + k * n, nullptr);
+        k_spmv_long<<<152 * 8, 256, 0, st>>>(queue, qn, row_ptr, col, val, taylor + (k - 1) * n, nullptr,
+                                               taylor + k * n, nullptr);
+    }
+    k_rates<<<nb, 256, 0, st>>>(n, row_ptr, col, val, lam);
+    k_rates_long<<<152 * 8, 256, 0, st>>>(queue, qn, row_ptr, col, val, lam);
+    k_features<<<nb, 256, 0, st>>>(n, row_ptr, col, val, lam, taylor, t, features);
+    k_features_long<<<152 * 8, 256, 0, st>>>(n, queue, qn, row_ptr, col, val, lam, taylor, t, features);
     return stat(cudaGetLastError());
 }
 
@@ -760,7 +907,9 @@ mcx_status mcx_cv_coefficients(int64_t n, const int64_t *row_ptr, const int32_t 
     // layout: (a, b) pairs at offset 0 (16-byte aligned with the buffer), then h
     double *c3 = work, *Ac3 = work + n;
     k_cv_xhat<<<nb, 256, 0, st>>>(n, taylor, y, t, coef + 2 * n, c3);
-    k_spmv<<<nb, 256, 0, st>>>(n, row_ptr, col, val, c3, Ac3);
+    cudaError_t e = spmv_hybrid(n, row_ptr, col, val, c3, Ac3, reinterpret_cast<int32_t *>(work + 2 * n),
+                                reinterpret_cast<unsigned int *>(work + 3 * n), st);
+    if (e != cudaSuccess) return stat(e);
     k_cv_ab<<<nb, 256, 0, st>>>(n, taylor, c3, Ac3, reinterpret_cast<double2 *>(coef));
     return stat(cudaGetLastError());
 }
@@ -795,6 +944,22 @@ mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
+    if (reinterpret_cast<uintptr_t>(coef) % 16 != 0) return MCX_E_INVALID;  // (a, b) pairs are read as double2
+    const bool wgt = plan->weighted_rows > 0;
+    if (paths <= LANE_MODE_MAX_PATHS) {  // few paths per entry: one lane per entry
+        p.mean = mean;
+        p.sem = sem;
+        CVArgs cvl{coef + 2 * plan->n, reinterpret_cast<const double2 *>(coef)};
+        const unsigned grid = (unsigned)((n_entries + WALK_THREADS - 1) / WALK_THREADS);
+        if (precision == MCX_FP64) {
+            if (wgt) k_walk_cv_lanes<true, true><<<grid, WALK_THREADS, 0, st>>>(p, cvl);
+            else k_walk_cv_lanes<true, false><<<grid, WALK_THREADS, 0, st>>>(p, cvl);
+        } else {
+            if (wgt) k_walk_cv_lanes<false, true><<<grid, WALK_THREADS, 0, st>>>(p, cvl);
+            else k_walk_cv_lanes<false, false><<<grid, WALK_THREADS, 0, st>>>(p, cvl);
+        }
+        return stat(cudaGetLastError());
+    }
     const uint64_t target_warps = 152ull * 64ull * 8ull;
     uint64_t cpe = (target_warps + (uint64_t)n_entries - 1) / (uint64_t)n_entries;
     const uint64_t max_cpe = (paths + 1023) / 1024;
@@ -817,10 +982,8 @@ mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_
         plan->scratch_bytes = need;
     }
     p.partials = static_cast<Partial *>(plan->scratch);
-    if (reinterpret_cast<uintptr_t>(coef) % 16 != 0) return MCX_E_INVALID;  // (a, b) pairs are read as double2
     CVArgs cv{coef + 2 * plan->n, reinterpret_cast<const double2 *>(coef)};
     const unsigned grid = (unsigned)((n_chunks + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
-    const bool wgt = plan->weighted_rows > 0;
     if (precision == MCX_FP64) {
         if (wgt) k_walk_cv<true, true><<<grid, WALK_THREADS, 0, st>>>(p, cv);
         else k_walk_cv<true, false><<<grid, WALK_THREADS, 0, st>>>(p, cv);

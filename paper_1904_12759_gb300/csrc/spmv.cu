@@ -1,24 +1,75 @@
-// Power iteration for lambda_max of a symmetric A >= 0 (Sec. 6 sets
+// Sparse products on the caller's CSR arrays: the hybrid SpMV of rows.cuh, and
+// power iteration for lambda_max of a symmetric A >= 0 (Sec. 6 sets
 // beta = 1/lambda_max; the paper notes finding it is costly for large
-// networks, so it runs here on the GPU over the caller's CSR arrays).
+// networks, so it runs here on the GPU).
 //
-// x_0 = 1 with scale s_0 = 1/sqrt(n); iteration k computes y = A (s_k x_k)
-// (x_k unnormalised, s_k = 1/||x_k||), the Rayleigh quotient
-// lambda_k = (s_k x_k) . y and s_{k+1} = 1/||y||, then x_{k+1} = y: one
-// fused kernel per iteration, ping-pong buffers, no separate scaling pass.
-// One thread per row, so each stored entry costs one FP64 fma slot.
-// Each block writes its two partial dot products; the last block to finish
-// (atomic ticket after a fence) reduces all partials in a fixed tree order,
-// so the result does not depend on block scheduling.  Iterations stop when
+// Power iteration: x_0 = 1 with scale s_0 = 1/sqrt(n); iteration k computes
+// y = A (s_k x_k) (x_k unnormalised, s_k = 1/||x_k||), the Rayleigh quotient
+// lambda_k = (s_k x_k) . y and s_{k+1} = 1/||y||, then x_{k+1} = y (ping-pong
+// buffers).  Per iteration: the short-row SpMV, the long-row SpMV (hubs, one
+// warp per row; the long rows are listed once per call), and a dot-product
+// pass whose block partials the last block to finish reduces in a fixed order,
+// so the result does not depend on scheduling.  Iterations stop when
 // |lambda_k - lambda_{k-1}| <= tol |lambda_k|; the host checks every CHECK
-// launches and launches after convergence return at once.
+// iterations and launches after convergence return at once.
 #include <math.h>
 
 #include <algorithm>
 
-#include "mcx_internal.cuh"
+#include "rows.cuh"
 
 namespace mcx {
+
+__global__ void k_find_long_rows(int64_t n, const int64_t *__restrict__ rp, int32_t *__restrict__ queue,
+                                 unsigned int *qn) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (rp[i + 1] - rp[i] > LONG_ROW) queue[atomicAdd(qn, 1u)] = (int32_t)i;
+}
+
+__global__ void k_spmv_short(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                             const double *__restrict__ val, const double *__restrict__ x, const double *scale,
+                             double *__restrict__ y, const int32_t *done) {
+    if (done && *(volatile const int32_t *)done) return;
+    const double s = scale ? *scale : 1.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p0 = rp[i], p1 = rp[i + 1];
+        if (p1 - p0 > LONG_ROW) continue;
+        double acc = 0.0;
+        for (int64_t p = p0; p < p1; ++p) acc = __fma_rn(val[p], x[col[p]], acc);
+        y[i] = __dmul_rn(acc, s);
+    }
+}
+
+__global__ void k_spmv_long(const int32_t *__restrict__ queue, const unsigned int *qn,
+                            const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                            const double *__restrict__ val, const double *__restrict__ x, const double *scale,
+                            double *__restrict__ y, const int32_t *done) {
+    if (done && *(volatile const int32_t *)done) return;
+    const double s = scale ? *scale : 1.0;
+    const int lane = threadIdx.x & 31;
+    const unsigned int nq = *qn;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
+        const int32_t i = queue[q];
+        double acc = 0.0;
+        for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) acc = __fma_rn(val[p], x[col[p]], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) y[i] = __dmul_rn(acc, s);
+    }
+}
+
+cudaError_t spmv_hybrid(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *x,
+                        double *y, int32_t *queue, unsigned int *qn, cudaStream_t st) {
+    const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
+    cudaError_t e = cudaMemsetAsync(qn, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    k_find_long_rows<<<nb, 256, 0, st>>>(n, rp, queue, qn);
+    k_spmv_short<<<nb, 256, 0, st>>>(n, rp, col, val, x, nullptr, y, nullptr);
+    k_spmv_long<<<152 * 8, 256, 0, st>>>(queue, qn, rp, col, val, x, nullptr, y, nullptr);
+    return cudaGetLastError();
+}
+
 namespace {
 
 constexpr int PI_THREADS = 256;
@@ -32,7 +83,7 @@ struct PowerScalars {
     int32_t done;
     int32_t iters;
     uint32_t ticket;
-    uint32_t pad;
+    uint32_t qn;  // long rows
 };
 
 __global__ void k_init(int64_t n, double *x, PowerScalars *s) {
@@ -45,6 +96,7 @@ __global__ void k_init(int64_t n, double *x, PowerScalars *s) {
         s->done = 0;
         s->iters = 0;
         s->ticket = 0;
+        s->qn = 0;
     }
 }
 
@@ -72,26 +124,20 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double (*sh)[2]
     }
 }
 
-__global__ void __launch_bounds__(PI_THREADS) k_power_step(int64_t n, const int64_t *__restrict__ rp,
-                                                           const int32_t *__restrict__ col,
-                                                           const double *__restrict__ val,
-                                                           const double *__restrict__ x, double *__restrict__ y,
-                                                           double *__restrict__ part, PowerScalars *sc, double tol) {
+// (s x) . y and y . y by blocks in a fixed grid-stride order; the last block
+// reduces the block partials in block order and updates the scalars.
+__global__ void __launch_bounds__(PI_THREADS) k_power_dots(int64_t n, const double *__restrict__ x,
+                                                           const double *__restrict__ y, double *__restrict__ part,
+                                                           PowerScalars *sc, double tol) {
     __shared__ double sh[PI_THREADS / 32][2];
     __shared__ bool last;
     if (*(volatile int32_t *)&sc->done) return;  // uniform over the grid
     const double s = sc->inv_norm;
-    // one thread per row: each stored entry costs exactly one FP64 fma slot (the
-    // FP64 pipe, not memory, bounds this kernel on this GPU)
     double xy = 0.0, yy = 0.0;
-    for (int64_t row = (int64_t)blockIdx.x * PI_THREADS + threadIdx.x; row < n; row += (int64_t)gridDim.x * PI_THREADS) {
-        double acc = 0.0;
-        const int64_t p1 = rp[row + 1];
-        for (int64_t p = rp[row]; p < p1; ++p) acc = __fma_rn(val[p], x[col[p]], acc);
-        acc = __dmul_rn(acc, s);
-        y[row] = acc;
-        xy = __fma_rn(__dmul_rn(s, x[row]), acc, xy);
-        yy = __fma_rn(acc, acc, yy);
+    for (int64_t i = (int64_t)blockIdx.x * PI_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * PI_THREADS) {
+        const double yi = y[i];
+        xy = __fma_rn(__dmul_rn(s, x[i]), yi, xy);
+        yy = __fma_rn(yi, yi, yy);
     }
     block_sum2(xy, yy, sh);
     if (threadIdx.x == 0) {
@@ -102,7 +148,6 @@ __global__ void __launch_bounds__(PI_THREADS) k_power_step(int64_t n, const int6
     }
     __syncthreads();
     if (!last) return;
-    // last block: fixed-order reduction of all block partials
     __threadfence();
     double a = 0.0, b = 0.0;
     for (int k = threadIdx.x; k < (int)gridDim.x; k += PI_THREADS) {
@@ -130,18 +175,25 @@ cudaError_t run_power_iteration(int64_t n, const int64_t *row_ptr, const int32_t
     double *buf[2] = {work, work + n};
     double *part = work + 2 * n;
     PowerScalars *s = reinterpret_cast<PowerScalars *>(work + 2 * n + 2 * PI_MAX_BLOCKS);
+    int32_t *queue = reinterpret_cast<int32_t *>(work + 2 * n + 2 * PI_MAX_BLOCKS + 8);
     const int64_t want = (n + PI_THREADS - 1) / PI_THREADS;
     const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(PI_MAX_BLOCKS, want));
+    const unsigned nrow = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 32));
     k_init<<<nb, PI_THREADS, 0, st>>>(n, buf[0], s);
+    k_find_long_rows<<<nrow, 256, 0, st>>>(n, row_ptr, queue, &s->qn);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     PowerScalars hs{};
     int32_t launched = 0;
     while (launched < max_iters) {
         const int32_t batch = std::min<int32_t>(CHECK, max_iters - launched);
-        for (int32_t b = 0; b < batch; ++b, ++launched)
-            k_power_step<<<nb, PI_THREADS, 0, st>>>(n, row_ptr, col, val, buf[launched & 1], buf[(launched + 1) & 1],
-                                                    part, s, tol);
+        for (int32_t b = 0; b < batch; ++b, ++launched) {
+            const double *x = buf[launched & 1];
+            double *y = buf[(launched + 1) & 1];
+            k_spmv_short<<<nrow, 256, 0, st>>>(n, row_ptr, col, val, x, &s->inv_norm, y, &s->done);
+            k_spmv_long<<<152 * 8, 256, 0, st>>>(queue, &s->qn, row_ptr, col, val, x, &s->inv_norm, y, &s->done);
+            k_power_dots<<<nb, PI_THREADS, 0, st>>>(n, x, y, part, s, tol);
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(&hs, s, sizeof(hs), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;

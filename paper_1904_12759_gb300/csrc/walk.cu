@@ -74,6 +74,11 @@ struct Acc32 {
         kahan_add(s1, c1, wv);
         s2 = __fmaf_rn(wv, wv, s2);
     }
+    __device__ __forceinline__ void lane_result(double &S1, double &S2, double &Mw) const {
+        S1 = (double)s1 - (double)c1;
+        S2 = (double)s2;
+        Mw = (double)m;
+    }
     __device__ __forceinline__ void warp_merge(double &S1, double &S2, double &Mw) const {
         float mw = m;
 #pragma unroll
@@ -115,6 +120,11 @@ struct Acc64 {
         const double wv = __dmul_rn(exp(__dsub_rn(L, m)), v);
         s1 = __dadd_rn(s1, wv);
         s2 = __fma_rn(wv, wv, s2);
+    }
+    __device__ __forceinline__ void lane_result(double &S1, double &S2, double &Mw) const {
+        S1 = s1;
+        S2 = s2;
+        Mw = m;
     }
     __device__ __forceinline__ void warp_merge(double &S1, double &S2, double &Mw) const {
         const double mw = warp_max(m);
@@ -298,6 +308,58 @@ __global__ void __launch_bounds__(WALK_THREADS) k_reduce_chunks(const Partial *_
     s1 = warp_sum(s1);
     s2 = warp_sum(s2);
     if (lane == 0) finish_entry(s1, s2, m, M, mean + e, sem ? sem + e : nullptr, status);
+}
+
+// ---------------------------------------------------------------------------
+// Few paths per entry (M <= LANE_MODE_MAX_PATHS): one lane per entry.  The
+// lane runs the entry's paths in path order, keeps its own accumulators and
+// writes the entry's mean and standard error; no partials, no scratch.
+// ---------------------------------------------------------------------------
+template <int MODE, bool WEIGHTED, bool F64>
+__global__ void __launch_bounds__(WALK_THREADS) k_walk_lanes(const __grid_constant__ WalkParams a) {
+    using Q = P<F64>;
+    using T = typename Q::T;
+    using Acc = typename std::conditional<F64, Acc64, Acc32>::type;
+    const int64_t e = (int64_t)blockIdx.x * WALK_THREADS + threadIdx.x;
+    const bool valid = e < a.n_entries;  // lanes past the end stay for the warp reduction below
+    unsigned long long jumps = 0, paths = 0;
+    if (valid) {
+        const int32_t i = a.entries ? __ldg(a.entries + e) : (int32_t)e;
+        if (i < 0 || (int64_t)i >= a.n) {
+            atomicOr(a.status, ST_BAD_ENTRY);
+            a.mean[e] = QNAN;
+            if (a.sem) a.sem[e] = QNAN;
+        } else {
+            const NodeRec start = load_node(a.node, i);
+            const T delta_start = Q::pot(start, a.node64, i);
+            const T t0 = F64 ? (T)a.t64 : (T)a.t32;
+            Acc acc;
+            for (uint64_t p = 0; p < a.paths; ++p) {
+                Walker<F64> w;
+                w.rec = start; w.j = i; w.r = t0; w.acc = (T)0; w.delta = delta_start; w.k = 0;
+                while (!advance<MODE, WEIGHTED, F64>(w, a, (uint32_t)i, a.path_offset + p, nullptr, i)) {
+                }
+                const T L = final_logw<MODE, F64>(w, delta_start, a);
+                if (F64) acc.add(L, __ldg(&a.node64[w.j].v));
+                else acc.add(L, w.rec.v);
+                jumps += w.k;
+            }
+            paths = a.paths;
+            double S1, S2, M;
+            acc.lane_result(S1, S2, M);
+            finish_entry(S1, S2, M, (double)a.paths, a.mean + e, a.sem ? a.sem + e : nullptr, a.status);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        jumps += __shfl_xor_sync(0xffffffffu, jumps, o);
+        paths += __shfl_xor_sync(0xffffffffu, paths, o);
+    }
+    if ((threadIdx.x & 31) == 0 && paths) {
+        unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.status + 2);
+        atomicAdd(ctr, paths);
+        atomicAdd(ctr + 1, jumps);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -576,6 +638,16 @@ __global__ void __launch_bounds__(WALK_THREADS) k_trace_forward(const __grid_con
 }
 
 template <bool F64, bool WEIGHTED>
+cudaError_t launch_lanes_mode(int mode, unsigned grid, const WalkParams &p, cudaStream_t st) {
+    switch (mode) {
+        case MCX_EXACT: k_walk_lanes<MCX_EXACT, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p); break;
+        case MCX_STRANG: k_walk_lanes<MCX_STRANG, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p); break;
+        default: k_walk_lanes<MCX_LIE, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p); break;
+    }
+    return cudaGetLastError();
+}
+
+template <bool F64, bool WEIGHTED>
 cudaError_t launch_walk_mode(int mode, unsigned grid, const WalkParams &p, cudaStream_t st) {
     switch (mode) {
         case MCX_EXACT: k_walk<MCX_EXACT, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p); break;
@@ -644,6 +716,15 @@ cudaError_t launch_estimate(mcx_plan *plan, const EstimateArgs &a, cudaStream_t 
     p.path_offset = a.path_offset;
     p.mean = a.mean;
     p.sem = a.sem;
+    if (a.paths <= LANE_MODE_MAX_PATHS) {  // few paths per entry: one lane per entry
+        const unsigned grid = (unsigned)((a.n_entries + WALK_THREADS - 1) / WALK_THREADS);
+        const bool weighted = plan->weighted_rows > 0;
+        if (a.precision == MCX_FP64)
+            return weighted ? launch_lanes_mode<true, true>(a.mode, grid, p, st)
+                            : launch_lanes_mode<true, false>(a.mode, grid, p, st);
+        return weighted ? launch_lanes_mode<false, true>(a.mode, grid, p, st)
+                        : launch_lanes_mode<false, false>(a.mode, grid, p, st);
+    }
     // Chunking: at least 1024 paths per warp, and enough warps to fill the GPU
     // several times over (152 SMs x 64 resident warps x 8 waves).
     const uint64_t target_warps = 152ull * 64ull * 8ull;
@@ -931,6 +1012,7 @@ cudaError_t launch_estimate_noalloc(mcx_plan *plan, const double *v, const Estim
     cudaError_t e = noalloc_partials(&partials);
     if (e != cudaSuccess) return e;
     if ((e = launch_pack_v(plan, v, st)) != cudaSuccess) return e;
+    if (a.t != 0.0 && a.paths <= LANE_MODE_MAX_PATHS) return launch_estimate(plan, a, st);  // lane layout: no scratch
     if (a.t == 0.0) {
         k_copy_v<<<(unsigned)((a.n_entries + 255) / 256), 256, 0, st>>>(a.entries, a.n_entries, plan->n,
                                                                           plan->node64, a.mean, a.sem, plan->status);

@@ -16,6 +16,7 @@ namespace {
 constexpr int WALK_THREADS = 256;
 constexpr int WARPS_PER_BLOCK = WALK_THREADS / 32;
 constexpr int STAGE = 32;  // max staged entry-row length
+constexpr uint64_t LANE_MODE_MAX_PATHS = 64;  // at most this many paths per entry: one lane per entry
 #ifndef MCX_WALK_MIN_BLOCKS
 #define MCX_WALK_MIN_BLOCKS 6
 #endif

@@ -89,8 +89,9 @@ def test_training_reduces_loss(mcx):
     net.close()
 
 
+@pytest.mark.parametrize("M", [3000, 40])  # warp-per-entry and lane-per-entry layouts
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_cv_estimates_match_oracle_same_paths(mcx, prec):
+def test_cv_estimates_match_oracle_same_paths(mcx, prec, M):
     a = _conditioned(80, 21)
     csr = W.dense_to_csr(a)
     v = W.uniform_vector(80, 2, -1.0, 1.0)
@@ -108,7 +109,6 @@ def test_cv_estimates_match_oracle_same_paths(mcx, prec):
     assert np.allclose(cg[160:], xhat, rtol=1e-13)
     assert np.allclose(cg[:160].reshape(80, 2), np.stack([ca, cb], 1), rtol=1e-11, atol=1e-12 * np.abs(ca).max())
     plan = mcx.Plan.from_csr(csr)
-    M = 3000
     gm, gs = plan.estimate_cv(coef, t, M, seed=7, prec=prec)
     om, os_ = OW.Graph(csr).estimate_cv(ca, cb, xhat, t, M, seed=7)
     gm, gs = gm.cpu().numpy(), gs.cpu().numpy()
@@ -116,9 +116,9 @@ def test_cv_estimates_match_oracle_same_paths(mcx, prec):
     tol = 1e-12 if prec == "fp64" else 1e-5
     assert np.all(np.abs(gm - om) <= tol * scale), np.max(np.abs(gm - om) / scale)
     assert np.allclose(gs, os_, rtol=1e-9 if prec == "fp64" else 1e-3)
-    # unbiased for this arbitrary prediction
-    z = (gm - OD.expmv_dense(a, t, v)) / gs
-    assert abs(z.mean()) < 5 / math.sqrt(80) + 0.1 and 0.5 < z.var() < 1.7
+    if M >= 1000:  # unbiased for this arbitrary prediction
+        z = (gm - OD.expmv_dense(a, t, v)) / gs
+        assert abs(z.mean()) < 5 / math.sqrt(80) + 0.1 and 0.5 < z.var() < 1.7
     plan.close()
 
 

@@ -273,3 +273,24 @@ def test_deterministic_and_offsets_compose(mcx):
     al, _ = plan.estimate(v, 0.1, 500, seed=5, prec="fp64")
     assert torch.allclose((200 * lo + 300 * hi) / 500, al, rtol=1e-12, atol=0)
     plan.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_lane_layout_matches_oracle(mcx, prec):
+    """At most 64 paths per entry the walker runs one lane per entry: same paths,
+    same accumulators, results against the oracle on 1000 ragged entries."""
+    csr = W.erdos_renyi(5000, 10, 8)
+    plan = mcx.Plan.from_csr(csr)
+    og = OW.Graph(csr)
+    v = W.uniform_vector(5000, 3, -1.0, 1.0)
+    ent = np.sort(np.random.default_rng(1).choice(5000, 1000, replace=False)).astype(np.int32)
+    for M in (1, 17, 64):
+        gm, gs, om, os_ = _estimate_both(plan, og, v, 0.1, M, ent, prec=prec, seed=M)
+        scale, _, _ = og.estimate(np.abs(v), 0.1, M, entries=ent, seed=M, prec=prec)
+        tol = 1e-12 if prec == "fp64" else 2e-6
+        assert np.all(np.abs(gm - om) <= tol * scale), (M, np.max(np.abs(gm - om) / scale))
+        if M > 1:
+            assert np.allclose(gs, os_, rtol=1e-3 if prec == "fp32" else 1e-9, atol=1e-6 * scale.max())
+    st = plan.sync()
+    assert st["paths"] == 1000 * (1 + 17 + 64)
+    plan.close()
