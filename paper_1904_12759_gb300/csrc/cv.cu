@@ -11,7 +11,10 @@
 // where R(r - u) = c0 + c1 u + c2 u^2 + c3' u^3.  phi_k: series for |z| <= 1
 // (FP32) or 2 (FP64), the recursion phi_k = (e^z - k phi_{k-1})/z otherwise.
 //
-// Kernels: FP64 SpMV for the Taylor terms; node features; a 5-64-64-1 ReLU MLP
+// Kernels: FP64 SpMV for the Taylor terms; node rates and features
+// (double-float sums on the FP32 pipe, FP64 only for rows with values outside
+// the double-float range; feature maps in FP32, the network's input
+// precision); a 5-64-64-1 ReLU MLP
 // (weights rounded to BF16 on load, FP32 accumulation) for prediction,
 // full-batch gradients and Adam training (block partial gradients reduced in a
 // fixed order: deterministic); the coefficient builder; and the CV walker (the
@@ -23,6 +26,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "rows.cuh"
 #include "walker.cuh"
 
@@ -44,19 +48,55 @@ constexpr int GRAD_SAMPLES = 64;  // samples per gradient block (one per thread)
 // ---------------------------------------------------------------------------
 // Taylor terms and features
 // ---------------------------------------------------------------------------
-// rate lambda_i (sum of positive off-diagonal entries) for rows of at most LONG_ROW entries
+// Sums over the kept (positive off-diagonal) entries of row i of the double-float
+// values f(p, c): one thread per row for rows of at most LONG_ROW entries, one
+// warp per queued long row.  `bad` flags values outside the double-float range.
+struct RowSums {
+    df s1, s2;
+    int d;
+    bool bad;
+};
+
+__device__ __forceinline__ void row_add(RowSums &r, df x) {
+    r.s1 = df_add(r.s1, x);
+    r.s2 = df_add(r.s2, df_mul(x, x));
+    r.d += 1;
+}
+
+__device__ __forceinline__ RowSums warp_rowsums(RowSums r) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        r.s1 = df_add(r.s1, df_shfl_xor(r.s1, o));
+        r.s2 = df_add(r.s2, df_shfl_xor(r.s2, o));
+        r.d += __shfl_xor_sync(0xffffffffu, r.d, o);
+    }
+    r.bad = __any_sync(0xffffffffu, r.bad);
+    return r;
+}
+
+// rate lambda_i = sum of the positive off-diagonal entries (FP64 if a value is
+// outside the double-float range)
+__device__ __forceinline__ double rate_fp64(int64_t i, int64_t p0, int64_t p1, int64_t step,
+                                            const int32_t *__restrict__ col, const double *__restrict__ val) {
+    double s = 0.0;
+    for (int64_t p = p0; p < p1; p += step)
+        if (col[p] != i && val[p] > 0.0) s = __dadd_rn(s, val[p]);
+    return s;
+}
+
 __global__ void k_rates(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                         const double *__restrict__ val, double *__restrict__ lam) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (rp[i + 1] - rp[i] > LONG_ROW) continue;
-        double s = 0.0;
-        for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
-            if (col[p] != i && val[p] > 0.0) s = __dadd_rn(s, val[p]);
-        lam[i] = s;
+        const int64_t p0 = rp[i], p1 = rp[i + 1];
+        if (p1 - p0 > LONG_ROW) continue;
+        df s{0.0f, 0.0f};
+        bool bad = false;
+        for (int64_t p = p0; p < p1; ++p)
+            if (col[p] != i && val[p] > 0.0) s = df_add(s, df_split(val[p], bad));
+        lam[i] = bad ? rate_fp64(i, p0, p1, 1, col, val) : df_to_double(df_norm(s));
     }
 }
 
-// the same for the queued long rows, one warp per row
 __global__ void k_rates_long(const int32_t *__restrict__ queue, const unsigned int *qn,
                              const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                              const double *__restrict__ val, double *__restrict__ lam) {
@@ -65,29 +105,73 @@ __global__ void k_rates_long(const int32_t *__restrict__ queue, const unsigned i
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
         const int32_t i = queue[q];
-        double s = 0.0;
+        df s{0.0f, 0.0f};
+        bool bad = false;
         for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32)
-            if (col[p] != i && val[p] > 0.0) s += val[p];
+            if (col[p] != i && val[p] > 0.0) s = df_add(s, df_split(val[p], bad));
+        if (__any_sync(0xffffffffu, bad)) {
+            double r = rate_fp64(i, rp[i] + lane, rp[i + 1], 32, col, val);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) lam[i] = s;
+            for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+            if (lane == 0) lam[i] = r;
+        } else {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s = df_add(s, df_shfl_xor(s, o));
+            if (lane == 0) lam[i] = df_to_double(df_norm(s));
+        }
     }
 }
 
-__device__ __forceinline__ void write_features(int64_t n, int64_t i, double s1, double s2, double d,
+// Features of node i from the neighbour sums (double-float) and the Taylor
+// terms (FP64), mapped to FP32: log1p(lambda), log1p(mean and standard
+// deviation of the neighbours' lambda), t Av / T2, t^2 A^2 v / (2 T2).
+// Neighbour mean and standard deviation of lambda in FP64 (rows where a
+// neighbour's lambda is outside the double-float range).
+__device__ __forceinline__ void neighbour_stats_fp64(int64_t i, const int64_t *__restrict__ rp,
+                                                     const int32_t *__restrict__ col, const double *__restrict__ val,
+                                                     const double *__restrict__ lam, float &mean, float &sd) {
+    double s1 = 0.0, s2 = 0.0, d = 0.0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        const int32_t c = col[p];
+        if (c != i && val[p] > 0.0) {
+            s1 += lam[c];
+            s2 += lam[c] * lam[c];
+            d += 1.0;
+        }
+    }
+    const double m = d > 0.0 ? s1 / d : 0.0;
+    const double var = d > 0.0 ? s2 / d - m * m : 0.0;
+    mean = (float)m;
+    sd = var > 0.0 ? (float)sqrt(var) : 0.0f;
+}
+
+__device__ __forceinline__ void write_features(int64_t n, int64_t i, RowSums r, const int64_t *__restrict__ rp,
+                                               const int32_t *__restrict__ col, const double *__restrict__ val,
                                                const double *__restrict__ lam, const double *__restrict__ T,
                                                double t, float *__restrict__ F) {
-    const double mean = d > 0 ? s1 / d : 0.0;
-    double var = d > 0 ? s2 / d - mean * mean : 0.0;
-    if (var < 0.0) var = 0.0;
+    float mean = 0.0f, sd = 0.0f;
+    if (r.bad) {
+        neighbour_stats_fp64(i, rp, col, val, lam, mean, sd);
+    } else if (r.d > 0) {
+        const float d = (float)r.d;  // exact: rows have fewer than 2^24 entries
+        // mean = s1/d and var = s2/d - mean^2 in double-float (one correction step per quotient)
+        const float m1 = __fdiv_rn(r.s1.h, d);
+        const df mu = df{m1, __fdiv_rn(__fadd_rn(__fmaf_rn(-m1, d, r.s1.h), r.s1.l), d)};
+        const float m2 = __fdiv_rn(r.s2.h, d);
+        const df q2 = df{m2, __fdiv_rn(__fadd_rn(__fmaf_rn(-m2, d, r.s2.h), r.s2.l), d)};
+        const df mm = df_mul(mu, mu);
+        const df var = df_norm(df_add(q2, df{-mm.h, -mm.l}));
+        mean = __fadd_rn(mu.h, mu.l);
+        sd = var.h > 0.0f ? sqrtf(var.h) : 0.0f;
+    }
     const double T2 = T[i] + t * T[n + i] + t * t * T[2 * n + i] / 2.0;
-    const double T2s = T2 != 0.0 ? T2 : 1.0;
+    const float T2s = T2 != 0.0 ? (float)T2 : 1.0f;
     float *f = F + i * NF;
-    f[0] = (float)log1p(lam[i]);
-    f[1] = (float)log1p(mean);
-    f[2] = (float)log1p(sqrt(var));
-    f[3] = (float)(t * T[n + i] / T2s);
-    f[4] = (float)(t * t * T[2 * n + i] / (2.0 * T2s));
+    f[0] = log1pf((float)lam[i]);
+    f[1] = log1pf(mean);
+    f[2] = log1pf(sd);
+    f[3] = __fdiv_rn((float)(t * T[n + i]), T2s);
+    f[4] = __fdiv_rn((float)(t * t * T[2 * n + i]), __fmul_rn(2.0f, T2s));
 }
 
 __global__ void k_features(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
@@ -95,17 +179,12 @@ __global__ void k_features(int64_t n, const int64_t *__restrict__ rp, const int3
                            const double *__restrict__ T, double t, float *__restrict__ F) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (rp[i + 1] - rp[i] > LONG_ROW) continue;
-        double s1 = 0.0, s2 = 0.0, d = 0.0;
+        RowSums r{{0.0f, 0.0f}, {0.0f, 0.0f}, 0, false};
         for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
             const int32_t c = col[p];
-            if (c != i && val[p] > 0.0) {
-                const double l = lam[c];
-                s1 += l;
-                s2 += l * l;
-                d += 1.0;
-            }
+            if (c != i && val[p] > 0.0) row_add(r, df_split(lam[c], r.bad));
         }
-        write_features(n, i, s1, s2, d, lam, T, t, F);
+        write_features(n, i, r, rp, col, val, lam, T, t, F);
     }
 }
 
@@ -118,23 +197,13 @@ __global__ void k_features_long(int64_t n, const int32_t *__restrict__ queue, co
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
         const int32_t i = queue[q];
-        double s1 = 0.0, s2 = 0.0, d = 0.0;
+        RowSums r{{0.0f, 0.0f}, {0.0f, 0.0f}, 0, false};
         for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
             const int32_t c = col[p];
-            if (c != i && val[p] > 0.0) {
-                const double l = lam[c];
-                s1 += l;
-                s2 += l * l;
-                d += 1.0;
-            }
+            if (c != i && val[p] > 0.0) row_add(r, df_split(lam[c], r.bad));
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-            d += __shfl_xor_sync(0xffffffffu, d, o);
-        }
-        if (lane == 0) write_features(n, i, s1, s2, d, lam, T, t, F);
+        r = warp_rowsums(r);
+        if (lane == 0) write_features(n, i, r, rp, col, val, lam, T, t, F);
     }
 }
 

@@ -46,15 +46,33 @@ def _conditioned(n, seed, rate=1.5, dsd=1.0):
     return a
 
 
-def test_prepare_matches_oracle(mcx):
-    csr = W.barabasi_albert(3000, 5, 4)
+def _fp64_bound(csr, v):
+    """Error bound of the Taylor terms A^k v on either side (FP64 row sums in
+    different orders: each of the k chained row sums is exact to
+    (row length + 1) 2^-53 of its absolute sum, so |T_k - A^k v| <=
+    2 * 3 (maxdeg + 1) 2^-52 (|A|^k |v|) between the two), as [4, n]."""
+    a = abs(csr.to_scipy())
+    S = [np.abs(np.asarray(v, dtype=np.float64))]
+    for _ in range(3):
+        S.append(a @ S[-1])
+    return 6 * (np.diff(csr.row_ptr).max() + 1) * 2.0 ** -52 * np.stack(S)
+
+
+@pytest.mark.parametrize("scale", [1.0, 3e-26])  # 3e-26: rates below 2^-74, the FP64 feature sums
+def test_prepare_matches_oracle(mcx, scale):
+    import dataclasses
+
+    csr = W.barabasi_albert(3000, 5, 4)  # hub rows take the warp-per-row kernels
+    assert np.diff(csr.row_ptr).max() > 32
+    csr = dataclasses.replace(csr, val=csr.val * scale)
     v = W.uniform_vector(3000, 1)
     t = 0.03
     rp, col, val = _dev(csr)
     T, F = mcx.cv_prepare(rp, col, val, torch.as_tensor(v).cuda(), t)
     oF, oT2, oT = CV.features(csr, v, t)
-    assert np.allclose(T.cpu().numpy(), oT, rtol=1e-13, atol=1e-300)
-    assert np.allclose(F.cpu().numpy(), oF.astype(np.float32), rtol=2e-6, atol=1e-6)
+    assert np.all(np.abs(T.cpu().numpy() - oT) <= _fp64_bound(csr, v))
+    assert np.array_equal(T.cpu().numpy()[0], v)
+    assert np.allclose(F.cpu().numpy(), oF.astype(np.float32), rtol=2e-6, atol=1e-6 * scale)
 
 
 def test_network_forward_and_gradient_match_oracle(mcx):
@@ -106,11 +124,16 @@ def test_cv_estimates_match_oracle_same_paths(mcx, prec, M):
     xhat = T2 * np.exp(yrand.cpu().numpy().astype(np.float64))
     c3, ca, cb = CV.cv_coefficients(csr, oT, t, xhat)
     cg = coef.cpu().numpy()
-    assert np.allclose(cg[160:], xhat, rtol=1e-13)
+    # xhat = T2 e^y inherits the Taylor terms' bound
+    B = _fp64_bound(csr, v)
+    ey = np.exp(yrand.cpu().numpy().astype(np.float64))
+    assert np.all(np.abs(cg[160:] - xhat) <= 1e-15 * np.abs(xhat) + ey * (t * B[1] + t * t * B[2] / 2))
     assert np.allclose(cg[:160].reshape(80, 2), np.stack([ca, cb], 1), rtol=1e-11, atol=1e-12 * np.abs(ca).max())
     plan = mcx.Plan.from_csr(csr)
     gm, gs = plan.estimate_cv(coef, t, M, seed=7, prec=prec)
-    om, os_ = OW.Graph(csr).estimate_cv(ca, cb, xhat, t, M, seed=7)
+    # the walker is compared on the GPU's own coefficients (checked above)
+    gab = cg[:160].reshape(80, 2)
+    om, os_ = OW.Graph(csr).estimate_cv(gab[:, 0].copy(), gab[:, 1].copy(), cg[160:].copy(), t, M, seed=7)
     gm, gs = gm.cpu().numpy(), gs.cpu().numpy()
     scale = np.abs(xhat) + os_ * math.sqrt(M)
     tol = 1e-12 if prec == "fp64" else 1e-5
