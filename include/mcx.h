@@ -385,8 +385,18 @@ mcx_status mcx_mlp_create(uint64_t seed, mcx_mlp **out);
 mcx_status mcx_mlp_set(mcx_mlp *model, const float *params, const float *mu, const float *sd);
 mcx_status mcx_mlp_get(const mcx_mlp *model, float *params, float *mu, float *sd);
 
-/* y [n] = network(features [5n]) (device). */
+/* y [n] = network(features [5n]) (device), on the tensor cores: tiles of 128
+ * nodes; the first hidden layer (FP32, BF16 weights) is rounded to BF16 (round
+ * to nearest even) and multiplied by W2 (BF16) with FP32 accumulation in
+ * tensor memory (tcgen05 MMAs); bias, ReLU and the output layer in FP32.
+ * Asynchronous; a device-side failure of an MMA completion wait is latched and
+ * returned by mcx_mlp_sync. */
 mcx_status mcx_mlp_predict(const mcx_mlp *model, int64_t n, const float *features, float *y, void *stream);
+
+/* Synchronise `stream`; return and clear the model's latched inference status:
+ * MCX_OK, or MCX_E_TIMEOUT if an MMA completion wait gave up (that call's
+ * outputs are unspecified).  Errors: MCX_E_INVALID, MCX_E_CUDA. */
+mcx_status mcx_mlp_sync(mcx_mlp *model, void *stream);
 
 /* Gradient of the mean squared error (1/n) sum (net(f_i) - y_i)^2 with respect
  * to the parameters as used (BF16-rounded weights): grad float32 [4609]

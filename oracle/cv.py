@@ -11,7 +11,9 @@ so that R(tau) = a tau^2 + b tau^3, a = A^3 v / 2 - 3 c3, b = A c3.
 
 The network: 5 node features -> 64 ReLU -> 64 ReLU -> 1, predicting
 y = log(x / T2); xhat = T2 exp(y).  Weights are used rounded to BF16 (round to
-nearest even), biases in full precision; everything else here is FP64.
+nearest even), biases in full precision; everything else here is FP64, except
+that `forward(..., bf16_hidden=True)` takes the first hidden layer as the
+tensor-core inference does (FP32 multiply-adds, then BF16).
 """
 from __future__ import annotations
 
@@ -84,11 +86,31 @@ def init_params(seed: int = 0):
     return p
 
 
-def forward(p, X, round_weights=True):
-    """MLP forward in FP64 (weights rounded to BF16 when round_weights); X standardised."""
+def _fma_chain_f32(X, W1, b1):
+    """z1 = b1 + x_0 W1[0] + ... + x_4 W1[4] as FP32 fused multiply-adds in that
+    order (the inference kernel's precision and order).  Each FMA is emulated in
+    FP64: the product of two FP32 numbers is exact there, the sum is rounded to
+    FP64 and then to FP32 (the two roundings differ from one only when the FP64
+    result lands exactly on an FP32 tie)."""
+    a = np.broadcast_to(np.asarray(b1, np.float32), (X.shape[0], W1.shape[1])).copy()
+    Xf = np.asarray(X, np.float32).astype(np.float64)
+    for q in range(W1.shape[0]):
+        a = (Xf[:, q:q + 1] * W1[q].astype(np.float64) + a.astype(np.float64)).astype(np.float32)
+    return a
+
+
+def forward(p, X, round_weights=True, bf16_hidden=False):
+    """MLP forward in FP64 (weights rounded to BF16 when round_weights); X standardised.
+    bf16_hidden: the first hidden layer as the tensor-core inference computes it,
+    FP32 multiply-adds then ReLU and rounding to BF16; the rest in FP64."""
     W = {k: (bf16(v) if (round_weights and k[0] == "W") else v).astype(np.float64) for k, v in p.items()}
-    z1 = X @ W["W1"] + W["b1"]
-    h1 = np.maximum(z1, 0.0)
+    if bf16_hidden:
+        Wf = bf16(p["W1"]) if round_weights else np.asarray(p["W1"], np.float32)
+        z1 = _fma_chain_f32(X, Wf, p["b1"]).astype(np.float64)
+        h1 = bf16(np.maximum(z1, 0.0).astype(np.float32)).astype(np.float64)
+    else:
+        z1 = X @ W["W1"] + W["b1"]
+        h1 = np.maximum(z1, 0.0)
     z2 = h1 @ W["W2"] + W["b2"]
     h2 = np.maximum(z2, 0.0)
     y = (h2 @ W["W3"] + W["b3"])[:, 0]

@@ -38,6 +38,7 @@ EXPORTS = (
     "mcx_mlp_set",
     "mcx_mlp_get",
     "mcx_mlp_predict",
+    "mcx_mlp_sync",
     "mcx_mlp_gradient",
     "mcx_mlp_fit",
     "mcx_mlp_destroy",
@@ -143,6 +144,8 @@ def load(path: str = LIB_PATH):
     L.mcx_mlp_get.restype = st
     L.mcx_mlp_predict.argtypes = [vp, i64, vp, vp, vp]
     L.mcx_mlp_predict.restype = st
+    L.mcx_mlp_sync.argtypes = [vp, vp]
+    L.mcx_mlp_sync.restype = st
     L.mcx_mlp_gradient.argtypes = [vp, i64, vp, vp, vp, vp, vp]
     L.mcx_mlp_gradient.restype = st
     L.mcx_mlp_fit.argtypes = [vp, i64, vp, vp, i32, i32, C.c_float, u64, vp, vp]

@@ -384,7 +384,8 @@ def cv_coefficients(row_ptr, col, val, taylor, y, t: float, stream=None):
 
 
 class MLP:
-    """The 5-64-64-1 control-variate network (BF16 weights in use, FP32 master)."""
+    """The 5-64-64-1 control-variate network (BF16 weights in use, FP32 master;
+    inference on the tensor cores with the first hidden layer rounded to BF16)."""
 
     NPARAM = 4609
 
@@ -415,6 +416,10 @@ class MLP:
         check(_lib.load().mcx_mlp_predict(self._h, n, C.c_void_p(_dev(features.contiguous(), torch.float32, "f")),
                                           C.c_void_p(y.data_ptr()), _stream(stream)), "mcx_mlp_predict")
         return y
+
+    def sync(self, stream=None):
+        """Synchronise and raise if an inference call latched a device error."""
+        check(_lib.load().mcx_mlp_sync(self._h, _stream(stream)), "mcx_mlp_sync")
 
     def gradient(self, features, targets, stream=None):
         g = torch.empty(self.NPARAM, dtype=torch.float32, device=features.device)

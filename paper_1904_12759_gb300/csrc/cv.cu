@@ -28,6 +28,7 @@
 
 #include "dfloat.cuh"
 #include "rows.cuh"
+#include "tc.cuh"
 #include "walker.cuh"
 
 namespace mcx {
@@ -42,7 +43,6 @@ constexpr int P_B2 = P_W2 + HID * HID;
 constexpr int P_W3 = P_B2 + HID;
 constexpr int P_B3 = P_W3 + HID;
 constexpr int NPARAM = P_B3 + 1;  // 4609
-constexpr int FWD_THREADS = 128;
 constexpr int GRAD_SAMPLES = 64;  // samples per gradient block (one per thread)
 
 // ---------------------------------------------------------------------------
@@ -235,44 +235,118 @@ __device__ __forceinline__ void standardise(const float *__restrict__ f, const M
     for (int q = 0; q < NF; ++q) x[q] = (f[q] - m.mu[q]) / m.sd[q];
 }
 
-// y = W3 . relu(W2^T relu(W1^T x + b1) + b2) + b3, FP32 accumulation
-__device__ float mlp_eval(const float x[NF], const float *__restrict__ s) {
-    float h1[HID];
-#pragma unroll
-    for (int j = 0; j < HID; ++j) {
-        float a = s[P_B1 + j];
-#pragma unroll
-        for (int q = 0; q < NF; ++q) a = fmaf(x[q], s[P_W1 + q * HID + j], a);
-        h1[j] = fmaxf(a, 0.0f);
-    }
-    float y = s[P_B3];
-#pragma unroll
-    for (int kc = 0; kc < HID; kc += 16) {
-        float acc[16];
-#pragma unroll
-        for (int k = 0; k < 16; ++k) acc[k] = s[P_B2 + kc + k];
-#pragma unroll
-        for (int j = 0; j < HID; ++j) {
-            const float hj = h1[j];
-#pragma unroll
-            for (int k = 0; k < 16; ++k) acc[k] = fmaf(hj, s[P_W2 + j * HID + kc + k], acc[k]);
-        }
-#pragma unroll
-        for (int k = 0; k < 16; ++k) y = fmaf(fmaxf(acc[k], 0.0f), s[P_W3 + kc + k], y);
-    }
-    return y;
+// ---------------------------------------------------------------------------
+// Inference on the tensor cores.  A CTA of 4 warps takes tiles of 128 nodes:
+// each thread computes its node's first hidden layer (5 -> 64, FP32 CUDA
+// cores, BF16 weights) and writes it, rounded to BF16, as row `tid` of the MMA
+// operand A (128 x 64, K-major core-matrix layout in shared memory); one
+// thread issues four 128 x 64 x 16 BF16 MMAs against W2 (resident in shared
+// memory as the K-major operand B = W2^T) into 64 TMEM columns of FP32
+// accumulators, committed to an mbarrier; each warp then reads its 32 TMEM
+// lanes (= its 32 nodes) and finishes bias, ReLU and the 64 -> 1 output layer.
+// ---------------------------------------------------------------------------
+constexpr int TC_ROWS = 128;        // nodes per tile (MMA M)
+constexpr uint32_t TC_COLS = 64;    // TMEM columns (MMA N, FP32 accumulators)
+constexpr uint32_t TC_WAIT = 1u << 22;  // mbarrier polls before giving up
+
+// byte offset of element (r, k) in a K-major no-swizzle operand with 64 K
+// elements per row: 8-row groups 1024 B apart, K-adjacent core matrices 128 B apart
+__device__ __forceinline__ uint32_t tc_off(uint32_t r, uint32_t k) {
+    return (r >> 3) * 1024u + (k >> 3) * 128u + (r & 7u) * 16u + (k & 7u) * 2u;
 }
 
-__global__ void __launch_bounds__(FWD_THREADS) k_mlp_predict(int64_t n, const float *__restrict__ F, MLPView m,
-                                                              float *__restrict__ y) {
-    __shared__ float s[NPARAM];
-    load_params(m.params, s);
-    __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        float x[NF];
-        standardise(F + i * NF, m, x);
-        y[i] = mlp_eval(x, s);
+__device__ __forceinline__ uint32_t bf16_bits(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+
+__global__ void __launch_bounds__(TC_ROWS, 4) k_mlp_predict_tc(int64_t n, const float *__restrict__ F, MLPView m,
+                                                               float *__restrict__ y, uint32_t *err) {
+    __shared__ __align__(1024) uint8_t sA[TC_ROWS * HID * 2];  // 16 KB
+    __shared__ __align__(1024) uint8_t sB[HID * HID * 2];      // 8 KB
+    __shared__ float sW1[NF * HID], sb1[HID], sb2[HID], sw3[HID];
+    __shared__ float sb3;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int k = tid; k < HID * HID; k += TC_ROWS) {  // B[n][j] = W2[j][n]
+        const int j = k / HID, nn = k % HID;
+        *reinterpret_cast<uint16_t *>(sB + tc_off(nn, j)) = (uint16_t)bf16_bits(m.params[P_W2 + k]);
     }
+    for (int k = tid; k < NF * HID; k += TC_ROWS) sW1[k] = bf16_round(m.params[P_W1 + k]);
+    if (tid < HID) {
+        sb1[tid] = m.params[P_B1 + tid];
+        sb2[tid] = m.params[P_B2 + tid];
+        sw3[tid] = bf16_round(m.params[P_W3 + tid]);
+    }
+    if (tid == 0) {
+        sb3 = m.params[P_B3];
+        tc::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, TC_COLS);
+    tc::fence_proxy_async_smem();  // B written by this thread's generic stores
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    const uint32_t a_addr = tc::smem_addr(sA), b_addr = tc::smem_addr(sB);
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(TC_ROWS, TC_COLS);
+    uint32_t phase = 0;
+    for (int64_t tile = blockIdx.x; tile * TC_ROWS < n; tile += gridDim.x) {
+        const int64_t i = tile * TC_ROWS + tid;
+        float x[NF] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (i < n) standardise(F + i * NF, m, x);
+        // first hidden layer, BF16, 16 bytes (8 K elements) per store
+#pragma unroll
+        for (int kc = 0; kc < HID; kc += 8) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+                float a0 = sb1[kc + q], a1 = sb1[kc + q + 1];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) {
+                    a0 = fmaf(x[f], sW1[f * HID + kc + q], a0);
+                    a1 = fmaf(x[f], sW1[f * HID + kc + q + 1], a1);
+                }
+                pk[q >> 1] = bf16_bits(fmaxf(a0, 0.0f)) | (bf16_bits(fmaxf(a1, 0.0f)) << 16);
+            }
+            *reinterpret_cast<uint4 *>(sA + tc_off((uint32_t)tid, (uint32_t)kc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+#pragma unroll
+            for (uint32_t kk = 0; kk < HID / 16; ++kk)
+                tc::mma_bf16(tmem, tc::smem_desc(a_addr + kk * 256u, 128u, 1024u),
+                             tc::smem_desc(b_addr + kk * 256u, 128u, 1024u), idesc, kk > 0);
+            tc::mma_commit(&bar);
+        }
+        const bool got = tc::mbar_wait(&bar, phase, TC_WAIT);
+        if (__syncthreads_or(!got)) {  // the MMAs did not complete: flag, wait once more, stop
+            if (tid == 0) atomicOr(err, 1u);
+            tc::mbar_wait(&bar, phase, TC_WAIT);
+            break;
+        }
+        phase ^= 1u;
+        tc::fence_after_sync();
+        float yv = sb3;
+#pragma unroll
+        for (uint32_t c = 0; c < TC_COLS; c += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int k = 0; k < 16; ++k) yv = fmaf(fmaxf(v[k] + sb2[c + k], 0.0f), sw3[c + k], yv);
+        }
+        if (i < n) y[i] = yv;
+        tc::fence_before_sync();
+        __syncthreads();  // TMEM read and A consumed before the next tile overwrites them
+    }
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, TC_COLS);
 }
 
 // Gradient of the mean squared error over samples [0, n) with respect to the
@@ -745,6 +819,7 @@ struct mcx_mlp {
     int64_t *idx = nullptr;   // minibatch permutation
     int64_t idx_n = 0;
     int64_t step = 0;
+    uint32_t *err = nullptr;  // latched device status of inference (bit 0: an MMA wait gave up)
 };
 
 namespace {
@@ -840,6 +915,8 @@ mcx_status mcx_mlp_create(uint64_t seed, mcx_mlp **out) {
         if ((e = cudaMalloc(&m->m2, sizeof(float) * (NPARAM + 1))) != cudaSuccess) break;
         if ((e = cudaMalloc(&m->grad, sizeof(float) * (NPARAM + 1))) != cudaSuccess) break;
         if ((e = cudaMalloc(&m->stats, sizeof(float) * 2 * NF)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&m->err, sizeof(uint32_t))) != cudaSuccess) break;
+        cudaMemset(m->err, 0, sizeof(uint32_t));
         cudaMemcpy(m->params, p.data(), sizeof(float) * (NPARAM + 1), cudaMemcpyHostToDevice);
         cudaMemcpy(m->stats, stats.data(), sizeof(float) * 2 * NF, cudaMemcpyHostToDevice);
         cudaMemset(m->m1, 0, sizeof(float) * (NPARAM + 1));
@@ -874,9 +951,21 @@ mcx_status mcx_mlp_get(const mcx_mlp *m, float *params, float *mu, float *sd) {
 mcx_status mcx_mlp_predict(const mcx_mlp *m, int64_t n, const float *features, float *y, void *stream) {
     if (!m || n < 0 || (n > 0 && (!features || !y))) return MCX_E_INVALID;
     if (n == 0) return MCX_OK;
-    k_mlp_predict<<<blocks_for(n, FWD_THREADS), FWD_THREADS, 0, static_cast<cudaStream_t>(stream)>>>(n, features,
-                                                                                                   view(m), y);
+    const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, 152 * 4);
+    k_mlp_predict_tc<<<grid, TC_ROWS, 0, static_cast<cudaStream_t>(stream)>>>(n, features, view(m), y, m->err);
     return stat(cudaGetLastError());
+}
+
+mcx_status mcx_mlp_sync(mcx_mlp *m, void *stream) {
+    if (!m) return MCX_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, m->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && h) e = cudaMemsetAsync(m->err, 0, sizeof(uint32_t), st);
+    if (e != cudaSuccess) return stat(e);
+    return h ? MCX_E_TIMEOUT : MCX_OK;
 }
 
 mcx_status mcx_mlp_gradient(mcx_mlp *m, int64_t n, const float *features, const float *targets, float *grad,
@@ -963,6 +1052,7 @@ void mcx_mlp_destroy(mcx_mlp *m) {
     cudaFree(m->grad);
     cudaFree(m->part);
     cudaFree(m->idx);
+    cudaFree(m->err);
     delete m;
 }
 

@@ -150,14 +150,18 @@ __device__ __forceinline__ bool advance(Walker<F64> &w, const WalkParams &a, uin
     using T = typename Q::T;
     const T invdt = F64 ? (T)a.invdt64 : (T)a.invdt32;
     const int N = a.nsteps;
+    // the event's draw and -ln(u) do not depend on the state, so they are computed
+    // before the state's record (often still in flight from the last jump) is used;
+    // a state without jumps simply ignores them
+    const uint4 rnd = philox_rk(make_uint4(w.k, stream, (uint32_t)path, (uint32_t)(path >> 32)), a);
+    const T e = Q::neg_ln(Q::unif(rnd));
     if (w.rec.deg == 0 || w.k >= a.max_events) {
         if (w.rec.deg != 0) atomicOr(a.status, ST_OVERFLOW);  // event cap reached: result flagged
         w.acc = MODE == MCX_EXACT ? Q::fma(w.delta, w.r, w.acc) : Q::fma(w.delta, Q::from_int(Q::grid(w.r, invdt, N)), w.acc);
         if (hold) *hold = w.r;
         return true;
     }
-    const uint4 rnd = philox_rk(make_uint4(w.k, stream, (uint32_t)path, (uint32_t)(path >> 32)), a);
-    const T S = Q::mul(Q::neg_ln(Q::unif(rnd)), Q::rate(w.rec, a.node64, w.j));
+    const T S = Q::mul(e, Q::rate(w.rec, a.node64, w.j));
     if (S >= w.r) {
         w.acc = MODE == MCX_EXACT ? Q::fma(w.delta, w.r, w.acc) : Q::fma(w.delta, Q::from_int(Q::grid(w.r, invdt, N)), w.acc);
         if (hold) *hold = w.r;

@@ -84,8 +84,12 @@ def test_network_forward_and_gradient_match_oracle(mcx):
     flat = np.concatenate([p["W1"].ravel(), p["b1"], p["W2"].ravel(), p["b2"], p["W3"].ravel(), p["b3"]])
     net.set(flat, np.zeros(5), np.ones(5))
     y = net.predict(torch.as_tensor(X).cuda()).cpu().numpy()
-    oy, _ = CV.forward(p, X.astype(np.float64), round_weights=True)
-    assert np.allclose(y, oy, rtol=1e-5, atol=1e-5)
+    net.sync()
+    # tensor-core inference: first hidden layer rounded to BF16 as in the oracle's bf16_hidden
+    # form; the remaining difference is FP32 accumulation (64 terms in tensor memory, 64 in
+    # the output layer), below 1e-4 (1 + |y|)
+    oy, _ = CV.forward(p, X.astype(np.float64), round_weights=True, bf16_hidden=True)
+    assert np.all(np.abs(y - oy) <= 1e-4 * (1 + np.abs(oy))), np.max(np.abs(y - oy))
     g, loss = net.gradient(torch.as_tensor(X).cuda(), torch.as_tensor(tgt).cuda())
     g = g.cpu().numpy()
     oloss, og = CV.loss_and_grad(p, X.astype(np.float64), tgt.astype(np.float64), round_weights=True)

@@ -125,3 +125,25 @@ def test_features_shapes_and_values():
     deg = np.diff(csr.row_ptr)
     assert np.allclose(F[:, 0], np.log1p(deg))
     assert np.allclose(T2, v + 0.05 * T[1] + 0.05 ** 2 * T[2] / 2)
+
+
+def test_bf16_hidden_forward_exact_cases():
+    """With inputs, weights and biases on a coarse binary grid every FP32 multiply-add
+    and the BF16 rounding of the first layer are exact, so the tensor-core form of the
+    forward pass equals the plain one; off the grid it differs by BF16 rounding only."""
+    rng = np.random.default_rng(4)
+    p = CV.init_params(2)
+    # W1 and b1 on multiples of 1/4, X on multiples of 1/2 in [-3, 3]: |z1| < 20 on
+    # multiples of 1/8, at most 8 significant bits, so BF16 holds it exactly
+    q = {k: (np.round(v * 4) / 4).astype(np.float32) for k, v in p.items()}
+    X = np.clip(np.round(rng.normal(size=(40, CV.N_FEATURES)) * 2) / 2, -3, 3)
+    assert np.abs(q["W1"]).max() <= 1.25
+    y0, _ = CV.forward(q, X, round_weights=True)
+    y1, _ = CV.forward(q, X, round_weights=True, bf16_hidden=True)
+    assert np.array_equal(y0, y1)
+    X = rng.normal(size=(300, CV.N_FEATURES)).astype(np.float32).astype(np.float64)
+    y0, (_, z1, h1, _, _, W) = CV.forward(p, X, round_weights=True)
+    y1, _ = CV.forward(p, X, round_weights=True, bf16_hidden=True)
+    # one BF16 rounding of every hidden activation: |dy| <= 2^-9 |h1| |W2| |W3| (row sums)
+    bound = 2.0 ** -9 * (np.abs(h1) @ np.abs(W["W2"]) @ np.abs(W["W3"]))[:, 0] + 1e-12
+    assert np.all(np.abs(y1 - y0) <= bound) and np.any(y1 != y0)
