@@ -122,6 +122,47 @@ __global__ void k_rates_long(const int32_t *__restrict__ queue, const unsigned i
     }
 }
 
+// Fixed-shape double-float sum over a block of ROW_BLOCK threads; valid in thread 0.
+__device__ __forceinline__ df block_sum_df(df v, df *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    df r{0.0f, 0.0f};
+    if (warp == 0) {
+        if (lane < ROW_BLOCK / 32) r = sh[lane];
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) r = df_add(r, df_shfl_xor(r, o));
+    }
+    __syncthreads();
+    return r;
+}
+
+// rates of the queued rows above HUGE_ROW entries, one block per row
+__global__ void __launch_bounds__(ROW_BLOCK) k_rates_huge(int64_t n, const int32_t *__restrict__ queue,
+                                                          const unsigned int *qn, const int64_t *__restrict__ rp,
+                                                          const int32_t *__restrict__ col,
+                                                          const double *__restrict__ val, double *__restrict__ lam) {
+    __shared__ df shd[ROW_BLOCK / 32];
+    __shared__ double sh[ROW_BLOCK / 32];
+    const unsigned int nq = qn[1];
+    for (unsigned int b = blockIdx.x; b < nq; b += gridDim.x) {
+        const int32_t i = queue[n - 1 - (int64_t)b];
+        df s{0.0f, 0.0f};
+        bool bad = false;
+        for (int64_t p = rp[i] + threadIdx.x; p < rp[i + 1]; p += ROW_BLOCK)
+            if (col[p] != i && val[p] > 0.0) s = df_add(s, df_split(val[p], bad));
+        if (__syncthreads_or(bad)) {
+            const double r = block_sum_row(rate_fp64(i, rp[i] + threadIdx.x, rp[i + 1], ROW_BLOCK, col, val), sh);
+            if (threadIdx.x == 0) lam[i] = r;
+        } else {
+            s = block_sum_df(s, shd);
+            if (threadIdx.x == 0) lam[i] = df_to_double(df_norm(s));
+        }
+    }
+}
+
 // Features of node i from the neighbour sums (double-float) and the Taylor
 // terms (FP64), mapped to FP32: log1p(lambda), log1p(mean and standard
 // deviation of the neighbours' lambda), t Av / T2, t^2 A^2 v / (2 T2).
@@ -207,6 +248,32 @@ __global__ void k_features_long(int64_t n, const int32_t *__restrict__ queue, co
     }
 }
 
+// features of the queued rows above HUGE_ROW entries, one block per row
+__global__ void __launch_bounds__(ROW_BLOCK) k_features_huge(int64_t n, const int32_t *__restrict__ queue,
+                                                             const unsigned int *qn, const int64_t *__restrict__ rp,
+                                                             const int32_t *__restrict__ col,
+                                                             const double *__restrict__ val,
+                                                             const double *__restrict__ lam,
+                                                             const double *__restrict__ T, double t,
+                                                             float *__restrict__ F) {
+    __shared__ df shd[ROW_BLOCK / 32];
+    __shared__ double sh[ROW_BLOCK / 32];
+    const unsigned int nq = qn[1];
+    for (unsigned int b = blockIdx.x; b < nq; b += gridDim.x) {
+        const int32_t i = queue[n - 1 - (int64_t)b];
+        RowSums r{{0.0f, 0.0f}, {0.0f, 0.0f}, 0, false};
+        for (int64_t p = rp[i] + threadIdx.x; p < rp[i + 1]; p += ROW_BLOCK) {
+            const int32_t c = col[p];
+            if (c != i && val[p] > 0.0) row_add(r, df_split(lam[c], r.bad));
+        }
+        r.bad = __syncthreads_or(r.bad);
+        r.s1 = block_sum_df(r.s1, shd);
+        r.s2 = block_sum_df(r.s2, shd);
+        r.d = (int)block_sum_row((double)r.d, sh);
+        if (threadIdx.x == 0) write_features(n, i, r, rp, col, val, lam, T, t, F);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // MLP
 // ---------------------------------------------------------------------------
@@ -260,7 +327,7 @@ __device__ __forceinline__ uint32_t bf16_bits(float x) {
     return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
 }
 
-__global__ void __launch_bounds__(TC_ROWS, 4) k_mlp_predict_tc(int64_t n, const float *__restrict__ F, MLPView m,
+__global__ void __launch_bounds__(TC_ROWS, 7) k_mlp_predict_tc(int64_t n, const float *__restrict__ F, MLPView m,
                                                                float *__restrict__ y, uint32_t *err) {
     __shared__ __align__(1024) uint8_t sA[TC_ROWS * HID * 2];  // 16 KB
     __shared__ __align__(1024) uint8_t sB[HID * HID * 2];      // 8 KB
@@ -860,18 +927,22 @@ mcx_status mcx_cv_prepare(int64_t n, const int64_t *row_ptr, const int32_t *col,
     int32_t *queue = reinterpret_cast<int32_t *>(work + n);  // n int32
     unsigned int *qn = reinterpret_cast<unsigned int *>(work + 2 * n);
     cudaError_t e = cudaMemcpyAsync(taylor, v, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(qn, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(qn, 0, 2 * sizeof(unsigned int), st);
     if (e != cudaSuccess) return stat(e);
     k_find_long_rows<<<nb, 256, 0, st>>>(n, row_ptr, queue, qn);
     for (int k = 1; k <= 3; ++k) {
-        k_spmv_short<<<nb, 256, 0, st>>>(n, row_ptr, col, val, taylor + (k - 1) * n, nullptr, taylor + k * n, nullptr);
-        k_spmv_long<<<152 * 8, 256, 0, st>>>(queue, qn, row_ptr, col, val, taylor + (k - 1) * n, nullptr,
-                                               taylor + k * n, nullptr);
+        const double *x = taylor + (k - 1) * n;
+        double *y = taylor + k * n;
+        k_spmv_short<<<nb, 256, 0, st>>>(n, row_ptr, col, val, x, nullptr, y, nullptr);
+        k_spmv_long<<<152 * 8, 256, 0, st>>>(queue, qn, row_ptr, col, val, x, nullptr, y, nullptr);
+        k_spmv_huge<<<152 * 2, ROW_BLOCK, 0, st>>>(n, queue, qn, row_ptr, col, val, x, nullptr, y, nullptr);
     }
     k_rates<<<nb, 256, 0, st>>>(n, row_ptr, col, val, lam);
     k_rates_long<<<152 * 8, 256, 0, st>>>(queue, qn, row_ptr, col, val, lam);
+    k_rates_huge<<<152 * 2, ROW_BLOCK, 0, st>>>(n, queue, qn, row_ptr, col, val, lam);
     k_features<<<nb, 256, 0, st>>>(n, row_ptr, col, val, lam, taylor, t, features);
     k_features_long<<<152 * 8, 256, 0, st>>>(n, queue, qn, row_ptr, col, val, lam, taylor, t, features);
+    k_features_huge<<<152 * 2, ROW_BLOCK, 0, st>>>(n, queue, qn, row_ptr, col, val, lam, taylor, t, features);
     return stat(cudaGetLastError());
 }
 
@@ -952,7 +1023,8 @@ mcx_status mcx_mlp_predict(const mcx_mlp *m, int64_t n, const float *features, f
     if (!m || n < 0 || (n > 0 && (!features || !y))) return MCX_E_INVALID;
     if (n == 0) return MCX_OK;
     const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
-    const unsigned grid = (unsigned)std::min<int64_t>(tiles, 152 * 4);
+    // 7 resident CTAs per SM (registers and shared memory allow 7; 7 x 64 of the 512 TMEM columns)
+    const unsigned grid = (unsigned)std::min<int64_t>(tiles, 152 * 7);
     k_mlp_predict_tc<<<grid, TC_ROWS, 0, static_cast<cudaStream_t>(stream)>>>(n, features, view(m), y, m->err);
     return stat(cudaGetLastError());
 }

@@ -6,8 +6,9 @@
 // Power iteration: x_0 = 1 with scale s_0 = 1/sqrt(n); iteration k computes
 // y = A (s_k x_k) (x_k unnormalised, s_k = 1/||x_k||), the Rayleigh quotient
 // lambda_k = (s_k x_k) . y and s_{k+1} = 1/||y||, then x_{k+1} = y (ping-pong
-// buffers).  Per iteration: the short-row SpMV, the long-row SpMV (hubs, one
-// warp per row; the long rows are listed once per call), and a dot-product
+// buffers).  Per iteration: the short-row SpMV, the long-row SpMVs (hubs, one
+// warp or one block per row; the long rows are listed once per call and their
+// kernels launched only if the graph has such rows), and a dot-product
 // pass whose block partials the last block to finish reduces in a fixed order,
 // so the result does not depend on scheduling.  Iterations stop when
 // |lambda_k - lambda_{k-1}| <= tol |lambda_k|; the host checks every CHECK
@@ -22,8 +23,11 @@ namespace mcx {
 
 __global__ void k_find_long_rows(int64_t n, const int64_t *__restrict__ rp, int32_t *__restrict__ queue,
                                  unsigned int *qn) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        if (rp[i + 1] - rp[i] > LONG_ROW) queue[atomicAdd(qn, 1u)] = (int32_t)i;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t len = rp[i + 1] - rp[i];
+        if (len > HUGE_ROW) queue[n - 1 - (int64_t)atomicAdd(qn + 1, 1u)] = (int32_t)i;
+        else if (len > LONG_ROW) queue[atomicAdd(qn, 1u)] = (int32_t)i;
+    }
 }
 
 __global__ void k_spmv_short(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
@@ -59,14 +63,34 @@ __global__ void k_spmv_long(const int32_t *__restrict__ queue, const unsigned in
     }
 }
 
+__global__ void __launch_bounds__(ROW_BLOCK) k_spmv_huge(int64_t n, const int32_t *__restrict__ queue,
+                                                         const unsigned int *qn, const int64_t *__restrict__ rp,
+                                                         const int32_t *__restrict__ col,
+                                                         const double *__restrict__ val,
+                                                         const double *__restrict__ x, const double *scale,
+                                                         double *__restrict__ y, const int32_t *done) {
+    __shared__ double sh[ROW_BLOCK / 32];
+    if (done && *(volatile const int32_t *)done) return;  // uniform over the grid
+    const double s = scale ? *scale : 1.0;
+    const unsigned int nq = qn[1];
+    for (unsigned int b = blockIdx.x; b < nq; b += gridDim.x) {
+        const int32_t i = queue[n - 1 - (int64_t)b];
+        double acc = 0.0;
+        for (int64_t p = rp[i] + threadIdx.x; p < rp[i + 1]; p += ROW_BLOCK) acc = __fma_rn(val[p], x[col[p]], acc);
+        acc = block_sum_row(acc, sh);
+        if (threadIdx.x == 0) y[i] = __dmul_rn(acc, s);
+    }
+}
+
 cudaError_t spmv_hybrid(int64_t n, const int64_t *rp, const int32_t *col, const double *val, const double *x,
                         double *y, int32_t *queue, unsigned int *qn, cudaStream_t st) {
     const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
-    cudaError_t e = cudaMemsetAsync(qn, 0, sizeof(unsigned int), st);
+    cudaError_t e = cudaMemsetAsync(qn, 0, 2 * sizeof(unsigned int), st);
     if (e != cudaSuccess) return e;
     k_find_long_rows<<<nb, 256, 0, st>>>(n, rp, queue, qn);
     k_spmv_short<<<nb, 256, 0, st>>>(n, rp, col, val, x, nullptr, y, nullptr);
     k_spmv_long<<<152 * 8, 256, 0, st>>>(queue, qn, rp, col, val, x, nullptr, y, nullptr);
+    k_spmv_huge<<<152 * 2, ROW_BLOCK, 0, st>>>(n, queue, qn, rp, col, val, x, nullptr, y, nullptr);
     return cudaGetLastError();
 }
 
@@ -83,7 +107,7 @@ struct PowerScalars {
     int32_t done;
     int32_t iters;
     uint32_t ticket;
-    uint32_t qn;  // long rows
+    uint32_t qn[2];  // long rows, huge rows
 };
 
 __global__ void k_init(int64_t n, double *x, PowerScalars *s) {
@@ -96,7 +120,8 @@ __global__ void k_init(int64_t n, double *x, PowerScalars *s) {
         s->done = 0;
         s->iters = 0;
         s->ticket = 0;
-        s->qn = 0;
+        s->qn[0] = 0;
+        s->qn[1] = 0;
     }
 }
 
@@ -180,10 +205,14 @@ cudaError_t run_power_iteration(int64_t n, const int64_t *row_ptr, const int32_t
     const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(PI_MAX_BLOCKS, want));
     const unsigned nrow = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 152 * 32));
     k_init<<<nb, PI_THREADS, 0, st>>>(n, buf[0], s);
-    k_find_long_rows<<<nrow, 256, 0, st>>>(n, row_ptr, queue, &s->qn);
+    k_find_long_rows<<<nrow, 256, 0, st>>>(n, row_ptr, queue, s->qn);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     PowerScalars hs{};
+    // the queue sizes decide which row kernels each iteration needs
+    if ((e = cudaMemcpyAsync(&hs, s, sizeof(hs), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    const bool any_long = hs.qn[0] > 0, any_huge = hs.qn[1] > 0;
     int32_t launched = 0;
     while (launched < max_iters) {
         const int32_t batch = std::min<int32_t>(CHECK, max_iters - launched);
@@ -191,7 +220,11 @@ cudaError_t run_power_iteration(int64_t n, const int64_t *row_ptr, const int32_t
             const double *x = buf[launched & 1];
             double *y = buf[(launched + 1) & 1];
             k_spmv_short<<<nrow, 256, 0, st>>>(n, row_ptr, col, val, x, &s->inv_norm, y, &s->done);
-            k_spmv_long<<<152 * 8, 256, 0, st>>>(queue, &s->qn, row_ptr, col, val, x, &s->inv_norm, y, &s->done);
+            if (any_long)
+                k_spmv_long<<<152 * 8, 256, 0, st>>>(queue, s->qn, row_ptr, col, val, x, &s->inv_norm, y, &s->done);
+            if (any_huge)
+                k_spmv_huge<<<152 * 2, ROW_BLOCK, 0, st>>>(n, queue, s->qn, row_ptr, col, val, x, &s->inv_norm, y,
+                                                          &s->done);
             k_power_dots<<<nb, PI_THREADS, 0, st>>>(n, x, y, part, s, tol);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -58,12 +58,28 @@ def _fp64_bound(csr, v):
     return 6 * (np.diff(csr.row_ptr).max() + 1) * 2.0 ** -52 * np.stack(S)
 
 
+def _with_hub(csr):
+    """The graph plus one node joined to every other node (a row of n - 1 entries)."""
+    import scipy.sparse as sp
+
+    n = csr.n
+    a = csr.to_scipy().tolil()
+    a.resize((n + 1, n + 1))
+    a[n, :n] = 1.0
+    a[:n, n] = 1.0
+    m = sp.csr_matrix(a)
+    m.sort_indices()
+    return W.CSR(n + 1, m.indptr.astype(np.int64), m.indices.astype(np.int32), m.data.astype(np.float64))
+
+
 @pytest.mark.parametrize("scale", [1.0, 3e-26])  # 3e-26: rates below 2^-74, the FP64 feature sums
 def test_prepare_matches_oracle(mcx, scale):
     import dataclasses
 
-    csr = W.barabasi_albert(3000, 5, 4)  # hub rows take the warp-per-row kernels
-    assert np.diff(csr.row_ptr).max() > 32
+    # rows of 33..1024 entries take the warp-per-row kernels, the added hub (2999) the block-per-row ones
+    csr = _with_hub(W.barabasi_albert(2999, 5, 4))
+    deg = np.diff(csr.row_ptr)
+    assert deg.max() > 1024 and np.any((deg > 32) & (deg <= 1024))
     csr = dataclasses.replace(csr, val=csr.val * scale)
     v = W.uniform_vector(3000, 1)
     t = 0.03

@@ -182,8 +182,17 @@ def test_power_iteration_hub_rows_and_fp64_fallback(mcx, scale):
     above 2^127 are outside the double-float range and take the FP64 kernels."""
     import dataclasses
 
-    csr = W.barabasi_albert(6000, 5, 2)
-    assert np.diff(csr.row_ptr).max() > 32
+    import scipy.sparse as sp
+
+    a = W.barabasi_albert(6000, 5, 2).to_scipy().tolil()
+    a.resize((6001, 6001))
+    a[6000, :6000] = 1.0  # a hub row of 6000 entries: the block-per-row kernel
+    a[:6000, 6000] = 1.0
+    m = sp.csr_matrix(a)
+    m.sort_indices()
+    csr = W.CSR(6001, m.indptr.astype(np.int64), m.indices.astype(np.int32), m.data.astype(np.float64))
+    deg = np.diff(csr.row_ptr)
+    assert deg.max() > 1024 and np.any((deg > 32) & (deg <= 1024))
     csr = dataclasses.replace(csr, val=csr.val * scale)
     lam, it = mcx.power_iteration(_cuda(csr.row_ptr, torch.int64), _cuda(csr.col, torch.int32),
                                   _cuda(csr.val, torch.float64), max_iters=20000, tol=1e-13)
