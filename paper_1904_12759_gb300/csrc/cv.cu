@@ -593,13 +593,47 @@ __global__ void k_cv_ab(int64_t n, const double *__restrict__ T, const double *_
 // ---------------------------------------------------------------------------
 // CV walker
 // ---------------------------------------------------------------------------
+// phi_k(z) = sum_n z^n / (n! (n + k + 1)): Horner coefficients 1/(n! (n+k+1)).
+struct PhiSeries {
+    float c[4][11];  // FP32: 11 terms for |z| <= 1 (remainder below 2e-9)
+};
+__host__ __device__ constexpr PhiSeries phi_series() {
+    PhiSeries s{};
+    for (int k = 0; k < 4; ++k) {
+        double f = 1.0;  // n!
+        for (int n = 0; n < 11; ++n) {
+            if (n > 0) f *= n;
+            s.c[k][n] = (float)(1.0 / (f * (n + k + 1)));
+        }
+    }
+    return s;
+}
+__constant__ PhiSeries c_phi = phi_series();
+
 template <typename R>
 __device__ __forceinline__ void phis(R z, R ph[4]) {
-    const R lim = sizeof(R) == 8 ? (R)2.0 : (R)1.0;
-    if (fabs(z) <= lim) {
-        const int terms = sizeof(R) == 8 ? 40 : 14;
+    if (sizeof(R) == 4) {
+        if (fabsf((float)z) <= 1.0f) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                float p = c_phi.c[k][10];
+#pragma unroll
+                for (int n = 9; n >= 0; --n) p = fmaf(p, (float)z, c_phi.c[k][n]);
+                ph[k] = (R)p;
+            }
+        } else {
+            const float ez = expf((float)z), iz = 1.0f / (float)z;
+            ph[0] = (R)((ez - 1.0f) * iz);
+            ph[1] = (R)((ez - (float)ph[0]) * iz);
+            ph[2] = (R)((ez - 2.0f * (float)ph[1]) * iz);
+            ph[3] = (R)((ez - 3.0f * (float)ph[2]) * iz);
+        }
+        return;
+    }
+    // FP64: series to 40 terms for |z| <= 2, else the recursion
+    if (fabs((double)z) <= 2.0) {
         R term = (R)1, s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-        for (int n = 0; n < terms; ++n) {
+        for (int n = 0; n < 40; ++n) {
             s0 += term / (R)(n + 1);
             s1 += term / (R)(n + 2);
             s2 += term / (R)(n + 3);
@@ -608,7 +642,7 @@ __device__ __forceinline__ void phis(R z, R ph[4]) {
         }
         ph[0] = s0; ph[1] = s1; ph[2] = s2; ph[3] = s3;
     } else {
-        const R ez = sizeof(R) == 8 ? (R)exp((double)z) : (R)expf((float)z);
+        const R ez = (R)exp((double)z);
         ph[0] = (ez - (R)1) / z;
         ph[1] = (ez - (R)1 * ph[0]) / z;
         ph[2] = (ez - (R)2 * ph[1]) / z;
@@ -803,22 +837,35 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_cv_lanes(const __grid_con
                 }
             }
             npaths = a.paths;
-            double S1, S2, scale;
-            if (F64I) {
-                S1 = s1;
-                S2 = s2;
-                scale = 1.0;
+            if (!F64I && m <= 80.0f) {
+                // the residual is a correction to h: its mean and standard error in FP32
+                // (M <= 64 here, exact), added to h in FP64
+                const float M = (float)a.paths;
+                const float S1 = __fsub_rn(f1, c1);
+                const float sc = expf(m);
+                const float mu = __fdiv_rn(S1, M);
+                float var = M > 1.0f ? __fdiv_rn(__fsub_rn(f2, __fmul_rn(S1, mu)), M - 1.0f) : 0.0f;
+                if (var < 0.0f) var = 0.0f;
+                a.mean[e] = cv.h[i] + (double)__fmul_rn(sc, mu);
+                if (a.sem) a.sem[e] = (double)__fmul_rn(sc, sqrtf(__fdiv_rn(var, M)));
             } else {
-                S1 = (double)f1 - (double)c1;
-                S2 = (double)f2;
-                scale = m == -INFINITY ? 0.0 : exp((double)m);
+                double S1, S2, scale;
+                if (F64I) {
+                    S1 = s1;
+                    S2 = s2;
+                    scale = 1.0;
+                } else {
+                    S1 = (double)f1 - (double)c1;
+                    S2 = (double)f2;
+                    scale = exp((double)m);
+                }
+                const double M = (double)a.paths;
+                const double mu = S1 / M;
+                double var = M > 1.0 ? (S2 - S1 * mu) / (M - 1.0) : 0.0;
+                if (var < 0.0) var = 0.0;
+                a.mean[e] = cv.h[i] + scale * mu;
+                if (a.sem) a.sem[e] = scale * sqrt(var / M);
             }
-            const double M = (double)a.paths;
-            const double mu = S1 / M;
-            double var = M > 1.0 ? (S2 - S1 * mu) / (M - 1.0) : 0.0;
-            if (var < 0.0) var = 0.0;
-            a.mean[e] = cv.h[i] + scale * mu;
-            if (a.sem) a.sem[e] = scale * sqrt(var / M);
             if (!isfinite(a.mean[e])) atomicOr(a.status, ST_OVERFLOW);
         }
     }
