@@ -56,10 +56,11 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle CPU time for cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="erdos_renyi", choices=["erdos_renyi", "ctmc_batch", "heat3d", "ba_cv"],
-                    help="erdos_renyi: the default line; ctmc_batch / heat3d / ba_cv: the batched CTMC "
-                         "transients, the 3D heat equation and the learned control variate's time to 1e-2 "
-                         "error (own JSON lines)")
+    ap.add_argument("--workload", default="erdos_renyi",
+                    choices=["erdos_renyi", "ctmc_batch", "heat3d", "ba_cv", "tc"],
+                    help="erdos_renyi: the default line; ctmc_batch / heat3d / ba_cv / tc: the batched CTMC "
+                         "transients, the 3D heat equation, the learned control variate's time to 1e-2 "
+                         "error and the total communicability at the paper's settings (own JSON lines)")
     return ap.parse_args()
 
 
@@ -491,6 +492,76 @@ def run_ba_cv(args):
     net.close()
 
 
+# the paper's single-core timings for TC at M = 1e6 paths, dt = 0.03125 (derived paths/s = M / time)
+PAPER_TC_PATHS_PER_S = {"small_world": 1e6 / 0.95, "scale_free": 1e6 / 0.71}
+
+
+def run_tc(args):
+    """Total communicability TC = 1^T exp(A) 1 (beta = 1) by Algorithm 2 with v = 1 at the
+    paper's settings: M = 1e6 paths, dt = 1/32 (STRANG, N = 32), on a small-world graph
+    (ring lattice k = 1 + shortcuts p = 0.2, mean degree 2.4) and a scale-free graph (BA,
+    m = 2), n = 1e6.  Each step is one whole call (start tables, walk, reduction).  Also
+    reported: EXACT and LIE at the same M, the throughput at M = 1e9, and the estimate
+    against the FP64 Taylor oracle."""
+    import numpy as np
+    import torch
+
+    import paper_1904_12759_gb300 as P
+    import workloads as W
+    from oracle import dense as OD
+
+    torch.cuda.set_device(0)
+    n = 10 ** 6
+    M = 10 ** 6
+    N = 32
+    flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    graphs = {"small_world": W.small_world(n, 1, 0.2, SEED), "scale_free": W.barabasi_albert(n, 2, SEED)}
+    res = {}
+    with ClockSampler(0) as clk:
+        for name, csr in graphs.items():
+            plan = P.Plan.from_csr(csr)
+            dev = [torch.as_tensor(a).cuda() for a in (csr.row_ptr, csr.col, csr.val)]
+            lam, _ = P.power_iteration(*dev, max_iters=20000, tol=1e-9)  # symmetric A: ||A||_2 = lambda_max
+            exact = float(OD.taylor_expmv(csr.to_scipy(), 1.0, np.ones(n), norm_bound=lam).sum())
+            out = (torch.empty(1, dtype=torch.float64, device="cuda"), torch.empty(1, dtype=torch.float64, device="cuda"))
+            r = {"n": n, "nnz": csr.nnz, "lambda_max": lam, "tc_exact_oracle": exact}
+            for mode, nsteps, paths in (("strang", N, M), ("lie", N, M), ("exact", 1, M), ("exact", 1, 10 ** 9)):
+                for w in range(args.warmup):
+                    plan.total_communicability(1.0, paths, mode=mode, nsteps=nsteps, seed=SEED + 1000 + w, out=out)
+                ts, vals = [], []
+                for k in range(args.steps if paths == M else 3):
+                    flush.zero_()
+                    a, b = ev(), ev()
+                    a.record()
+                    tc, se = plan.total_communicability(1.0, paths, mode=mode, nsteps=nsteps, seed=SEED + k, out=out)
+                    b.record()
+                    torch.cuda.synchronize()
+                    ts.append(a.elapsed_time(b))
+                    vals.append((tc.item(), se.item()))
+                st = plan.sync()
+                ms = statistics.median(ts)
+                tcv, sev = vals[-1]
+                key = f"{mode}" + (f"_N{nsteps}" if mode != "exact" else "") + f"_M{paths:.0e}".replace("+0", "")
+                r[key] = {"ms_per_call": ms, "paths_per_s": paths / (ms / 1e3), "tc": tcv, "sem": sev,
+                          "rel_sem": sev / tcv, "rel_err_vs_exact": (tcv - exact) / exact,
+                          "jumps_per_path": st["jumps"] / max(st["paths"], 1)}
+            plan.close()
+            res[name] = r
+    head = res["small_world"]["strang_N32_M1e6"]
+    line = {"metric": "total communicability paths/s (Algorithm 2, v = 1)", "value": head["paths_per_s"],
+            "unit": "paths/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": head["ms_per_call"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": head["paths_per_s"] / PAPER_TC_PATHS_PER_S["small_world"],
+            "vs_baseline_note": "paper: one Xeon E5620 core, Fortran, small-world n=1e6, M=1e6, dt=0.03125: 0.95 s",
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "tc_small_world_n1e6", "beta": 1.0, "paths": M, "functional": "strang",
+                       "nsteps": N, "graph": "ring lattice k=1 + shortcuts p=0.2 (mean degree 2.4)",
+                       "l2": "512 MiB buffer written between timed calls"},
+            "results": res, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -504,6 +575,9 @@ def main():
         return
     if args.workload == "ba_cv":
         run_ba_cv(args)
+        return
+    if args.workload == "tc":
+        run_tc(args)
         return
     import numpy as np
     import torch

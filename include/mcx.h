@@ -183,6 +183,26 @@ mcx_status mcx_estimate_forward(mcx_plan *plan, const double *v, double t, int f
                                 double *x, double *sem, void *stream);
 
 /*
+ * Total communicability TC(t) = 1^T exp(tA) 1 = sum_ij (exp(tA))_ij (Sec. 6,
+ * with t = beta) from the forward form with v = 1 (Theorem 2, Algorithm 2):
+ * the same paths as mcx_estimate_forward with v = 1 (start uniform over the
+ * n states through the same two-level table and draw schedule), but instead of
+ * a histogram only the mean path weight is kept: TC = n E[W].  The plan must be
+ * built from A^T (A itself when A is symmetric).
+ *   t, functional, nsteps, precision, seed, path_offset as in mcx_estimate_forward
+ *   total_paths  M >= 2
+ *   tc, sem      float64 [1] device outputs: the estimate and its standard
+ *                error (sem may be NULL); t = 0 gives n exactly (synchronising)
+ * Per-warp partial sums of W (log-sum-exp shifted, compensated within lanes)
+ * are merged in warp order, so the result is deterministic.  Uses the plan's
+ * forward scratch and grows its partial-sum scratch as needed.
+ * Errors: MCX_E_INVALID, MCX_E_CUDA, MCX_E_OOM; MCX_E_OVERFLOW at mcx_sync.
+ */
+mcx_status mcx_total_communicability(mcx_plan *plan, double t, int functional, int32_t nsteps,
+                                     uint64_t total_paths, uint64_t seed, uint64_t path_offset, int precision,
+                                     double *tc, double *sem, void *stream);
+
+/*
  * Per-path record of forward paths first_path .. first_path+count-1 (same
  * arguments as mcx_estimate_forward): start (int32), end (int32), njumps
  * (uint32), hash (uint64, FNV-1a over the visited indices from the start),

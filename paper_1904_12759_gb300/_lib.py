@@ -19,6 +19,7 @@ EXPORTS = (
     "mcx_estimate_noalloc",
     "mcx_estimate_forward",
     "mcx_trace_forward",
+    "mcx_total_communicability",
     "mcx_trace_paths",
     "mcx_power_iteration",
     "mcx_plan_export",
@@ -110,6 +111,8 @@ def load(path: str = LIB_PATH):
     L.mcx_estimate_forward.restype = st
     L.mcx_trace_forward.argtypes = [vp, vp, dbl, C.c_int, i32, u64, u64, u32, C.c_int, vp, vp, vp, vp, vp, vp]
     L.mcx_trace_forward.restype = st
+    L.mcx_total_communicability.argtypes = [vp, dbl, C.c_int, i32, u64, u64, u64, C.c_int, vp, vp, vp]
+    L.mcx_total_communicability.restype = st
     L.mcx_trace_paths.argtypes = [vp, dbl, C.c_int, i32, i32, u64, u64, u32, C.c_int, vp, vp, vp, vp, vp]
     L.mcx_trace_paths.restype = st
     L.mcx_power_iteration.argtypes = [i64, vp, vp, vp, i32, dbl, vp, C.POINTER(dbl), C.POINTER(i32), vp]

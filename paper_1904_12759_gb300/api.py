@@ -140,6 +140,22 @@ class Plan:
                                                _stream(stream)), "mcx_estimate_forward")
         return x, sem
 
+    def total_communicability(self, t: float, paths: int, mode: str = "exact", nsteps: int = 1, seed: int = 0,
+                              path_offset: int = 0, prec: str = "fp32", out: tuple | None = None, stream=None):
+        """TC(t) = 1^T exp(tA) 1 from the forward paths of v = 1 (plan of A^T); returns
+        (tc, sem) as one-element device tensors."""
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if out is None:
+            tc = torch.empty(1, dtype=torch.float64, device=dev)
+            sem = torch.empty(1, dtype=torch.float64, device=dev)
+        else:
+            tc, sem = out
+        check(_lib.load().mcx_total_communicability(self._h, float(t), FUNCTIONALS[mode], int(nsteps), int(paths),
+                                                    int(seed), int(path_offset), PRECISIONS[prec],
+                                                    C.c_void_p(tc.data_ptr()), C.c_void_p(sem.data_ptr()),
+                                                    _stream(stream)), "mcx_total_communicability")
+        return tc, sem
+
     def trace_forward(self, v: torch.Tensor, t: float, seed: int, first_path: int, count: int, mode: str = "exact",
                       nsteps: int = 1, prec: str = "fp32", stream=None) -> dict:
         dev = v.device

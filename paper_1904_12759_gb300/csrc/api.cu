@@ -207,6 +207,24 @@ mcx_status mcx_estimate_forward(mcx_plan *p, const double *v, double t, int func
                                              x, sem, st));
 }
 
+mcx_status mcx_total_communicability(mcx_plan *p, double t, int functional, int32_t nsteps, uint64_t total_paths,
+                                     uint64_t seed, uint64_t path_offset, int precision, double *tc, double *sem,
+                                     void *stream) {
+    mcx_status rc = check_common(p, t, functional, nsteps, precision);
+    if (rc != MCX_OK) return rc;
+    if (p->n == 0 || !tc || total_paths < 2 || total_paths > (1ull << 53)) return MCX_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (t == 0.0) {  // 1^T 1 = n exactly
+        const double nn = (double)p->n;
+        cudaError_t e = cudaMemcpyAsync(tc, &nn, sizeof(double), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && sem) e = cudaMemsetAsync(sem, 0, sizeof(double), st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // nn lives on this stack frame
+        return from_cuda(e);
+    }
+    return from_cuda(launch_total_communicability(p, t, functional, nsteps, total_paths, seed, path_offset,
+                                                  precision, tc, sem, st));
+}
+
 mcx_status mcx_trace_forward(mcx_plan *p, const double *v, double t, int functional, int32_t nsteps, uint64_t seed,
                              uint64_t first_path, uint32_t count, int precision, int32_t *start, int32_t *end,
                              uint32_t *njumps, uint64_t *hash, double *logw, void *stream) {

@@ -251,6 +251,9 @@ uint64_t noalloc_max_partials();
 cudaError_t launch_estimate_forward(mcx_plan *plan, const double *v, double t, int mode, int nsteps, uint64_t paths,
                                     uint64_t seed, uint64_t path_offset, int precision, double *x, double *sem,
                                     cudaStream_t st);
+cudaError_t launch_total_communicability(mcx_plan *plan, double t, int mode, int nsteps, uint64_t paths,
+                                         uint64_t seed, uint64_t path_offset, int precision, double *tc, double *sem,
+                                         cudaStream_t st);
 cudaError_t launch_trace_forward(mcx_plan *plan, const double *v, double t, int mode, int nsteps, uint64_t seed,
                                  uint64_t first_path, uint32_t count, int precision, int32_t *start, int32_t *end,
                                  uint32_t *njumps, uint64_t *hash, double *logw, cudaStream_t st);

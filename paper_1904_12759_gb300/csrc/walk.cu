@@ -576,6 +576,82 @@ __global__ void __launch_bounds__(WALK_THREADS, F64 ? WALK_MIN_BLOCKS_F64 : WALK
     }
 }
 
+// Total communicability TC(t) = 1^T exp(tA) 1 (Sec. 6): the forward paths of
+// v = 1 (Theorem 2; V = n, start uniform through the same two-level table) with
+// no deposit: TC = V E[W].  Each warp leaves one partial (shifted sums of W)
+// for the chunk reduction.
+template <int MODE, bool WEIGHTED, bool F64>
+__global__ void __launch_bounds__(WALK_THREADS, F64 ? WALK_MIN_BLOCKS_F64 : WALK_MIN_BLOCKS_F32)
+    k_walk_tc(const __grid_constant__ WalkParams a, const __grid_constant__ FwdTables f) {
+    using Q = P<F64>;
+    using T = typename Q::T;
+    using Acc = typename std::conditional<F64, Acc64, Acc32>::type;
+    const int lane = threadIdx.x & 31;
+    const uint64_t wid = ((uint64_t)blockIdx.x * WALK_THREADS + threadIdx.x) >> 5;
+    const uint64_t p_begin = wid * a.chunk_len;
+    if (p_begin >= a.paths) return;  // uniform across the warp
+    const uint32_t len = (uint32_t)(min(a.paths, p_begin + a.chunk_len) - p_begin);
+    const uint64_t base = a.path_offset + p_begin;
+    const T t0 = F64 ? (T)a.t64 : (T)a.t32;
+    uint32_t next = 32;
+    uint32_t p = (uint32_t)lane;
+    bool active = p < len;
+    int32_t i0 = 0;
+    T delta_start = (T)0;
+    Walker<F64> w;
+    auto start_path = [&]() {
+        i0 = forward_start(f, a, base + p);
+        w.rec = load_node(a.node, i0);
+        w.j = i0; w.r = t0; w.acc = (T)0; w.k = 0;
+        delta_start = Q::pot(w.rec, a.node64, i0);
+        w.delta = delta_start;
+    };
+    if (active) start_path();
+    Acc acc;
+    uint32_t jumps = 0;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    while (__any_sync(0xffffffffu, active)) {
+        bool fin = false;
+        if (active && advance<MODE, WEIGHTED, F64>(w, a, FWD_WALK_STREAM, base + p, nullptr, -1)) {
+            fin = true;
+            jumps += w.k;
+            acc.add(final_logw<MODE, F64>(w, delta_start, a), (T)1);
+        }
+        const unsigned fm = __ballot_sync(0xffffffffu, fin);
+        if (fm) {
+            if (fin) {
+                p = next + (uint32_t)__popc(fm & lt_mask);
+                active = p < len;
+                if (active) start_path();
+            }
+            next += (uint32_t)__popc(fm);
+        }
+    }
+    unsigned long long jl = jumps;
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) jl += __shfl_xor_sync(0xffffffffu, jl, sh);
+    double S1, S2, Mw;
+    acc.warp_merge(S1, S2, Mw);
+    if (lane == 0) {
+        unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.status + 2);
+        atomicAdd(ctr, (unsigned long long)len);
+        atomicAdd(ctr + 1, jl);
+        a.partials[wid] = Partial{S1, S2, Mw};
+    }
+}
+
+__global__ void k_fill(int64_t n, double *x, double value) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = value;
+}
+
+// (mean, SE) of W -> (V mean, V SE)
+__global__ void k_scale_tc(const double *Vp, double *tc, double *sem) {
+    const double V = *Vp;
+    *tc *= V;
+    if (sem) *sem *= V;
+}
+
 // x_i = (sum of V W 1{end = i}) / M and its standard error.
 __global__ void k_forward_finish(int64_t n, FwdOut o, const double *Vp, const uint32_t *bad, double M, double *x,
                                  double *sem, uint32_t *status) {
@@ -900,6 +976,60 @@ cudaError_t launch_estimate_forward(mcx_plan *plan, const double *v, double t, i
     }
     k_forward_finish<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, o, fs.V, fs.bad, (double)paths, x, sem,
                                                                    plan->status);
+    return cudaGetLastError();
+}
+
+template <bool F64, bool WEIGHTED>
+void launch_tc_kernel(int mode, unsigned grid, const WalkParams &p, const FwdTables &f, cudaStream_t st) {
+    switch (mode) {
+        case MCX_EXACT: k_walk_tc<MCX_EXACT, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p, f); break;
+        case MCX_STRANG: k_walk_tc<MCX_STRANG, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p, f); break;
+        default: k_walk_tc<MCX_LIE, WEIGHTED, F64><<<grid, WALK_THREADS, 0, st>>>(p, f); break;
+    }
+}
+
+cudaError_t launch_total_communicability(mcx_plan *plan, double t, int mode, int nsteps, uint64_t paths,
+                                         uint64_t seed, uint64_t path_offset, int precision, double *tc, double *sem,
+                                         cudaStream_t st) {
+    const int64_t n = plan->n;
+    FwdScratch fs;
+    cudaError_t e = fwd_scratch(plan, &fs);
+    if (e != cudaSuccess) return e;
+    double *ones = fs.dep;  // the deposit area is free in this mode
+    k_fill<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32), 256, 0, st>>>(n, ones, 1.0);
+    FwdTables f;
+    if ((e = build_start_tables(plan, ones, fs, &f, st)) != cudaSuccess) return e;
+    WalkParams p = make_params(plan, t, mode == MCX_EXACT ? 1 : nsteps, seed);
+    p.paths = paths;
+    p.path_offset = path_offset;
+    const uint64_t target_warps = 152ull * 64ull * 8ull;
+    uint64_t chunk = (paths + target_warps - 1) / target_warps;
+    if (chunk < 256) chunk = 256;
+    if (chunk > (1ull << 30)) chunk = 1ull << 30;
+    chunk = (chunk + 31) / 32 * 32;
+    p.chunk_len = chunk;
+    const uint64_t n_warps = (paths + chunk - 1) / chunk;
+    const size_t need = sizeof(Partial) * (size_t)n_warps;
+    if (plan->scratch_bytes < need) {
+        cudaFree(plan->scratch);
+        plan->scratch = nullptr;
+        plan->scratch_bytes = 0;
+        if ((e = cudaMalloc(&plan->scratch, need)) != cudaSuccess) return e;
+        plan->scratch_bytes = need;
+    }
+    p.partials = static_cast<Partial *>(plan->scratch);
+    const unsigned grid = (unsigned)((n_warps + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+    const bool wgt = plan->weighted_rows > 0;
+    if (precision == MCX_FP64) {
+        if (wgt) launch_tc_kernel<true, true>(mode, grid, p, f, st); else launch_tc_kernel<true, false>(mode, grid, p, f, st);
+    } else {
+        if (wgt) launch_tc_kernel<false, true>(mode, grid, p, f, st); else launch_tc_kernel<false, false>(mode, grid, p, f, st);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // all warp partials in chunk order, as one entry
+    k_reduce_chunks<<<1, WALK_THREADS, 0, st>>>(p.partials, 1, (uint32_t)n_warps, (double)paths, tc, sem,
+                                                 plan->status);
+    k_scale_tc<<<1, 1, 0, st>>>(fs.V, tc, sem);
     return cudaGetLastError();
 }
 

@@ -415,3 +415,20 @@ def test_forward_start_tables_reproduce_v():
     assert np.all(P[v == 0] == 0)
     tr = g.forward_trace(v, 0.0, 5, 0, 20000)
     assert np.all(v[tr["start"]] > 0)
+
+
+def test_total_communicability_from_forward_paths():
+    """TC(t) = 1^T exp(tA) 1 = n E[W] over the forward paths of v = 1 (Theorem 2 with
+    v = 1, Sec. 6), for EXACT and the split products (1^T S 1 for S the Strang or
+    Lie product: the scalar is the same for S and its transpose)."""
+    csr = W.erdos_renyi(200, 5, 2)
+    a = csr.to_scipy().toarray()
+    g = OW.Graph(csr)
+    t, N, M = 0.3, 2, 200000
+    for mode in ("exact", "strang", "lie"):
+        x = OD.expmv_dense(a, t, np.ones(200)) if mode == "exact" else OD.split_expmv(a, t, N, np.ones(200), mode)
+        want = float(x.sum())
+        tr = g.forward_trace(np.ones(200), t, 7, 0, M, mode=mode, nsteps=N, prec="fp64")
+        w = np.exp(tr["logw"])
+        z = (200 * w.mean() - want) / (200 * w.std(ddof=1) / np.sqrt(M))
+        assert abs(z) < 4, (mode, z)

@@ -166,6 +166,30 @@ def erdos_renyi(n: int, mean_degree: float, seed: int) -> CSR:
     return _symmetric_adjacency(n, keys // n, keys % n)
 
 
+def small_world(n: int, k: int, p: float, seed: int) -> CSR:
+    """Symmetric 0/1 adjacency of a small-world graph in the style of the
+    Watts-Strogatz model without rewiring: the ring lattice joining each node to
+    its k nearest neighbours on each side, plus, for each node with
+    probability p, one shortcut to a node drawn uniformly among the others
+    (duplicates of existing edges are dropped).  Mean degree about 2k + 2p.
+    """
+    rng = _rng(seed)
+    i = np.arange(n, dtype=np.int64)
+    lo_l, hi_l = [], []
+    for j in range(1, k + 1):
+        u, v = i, (i + j) % n
+        lo_l.append(np.minimum(u, v))
+        hi_l.append(np.maximum(u, v))
+    has = rng.random(n) < p
+    src = i[has]
+    dst = rng.integers(0, n - 1, size=src.size, dtype=np.int64)
+    dst = dst + (dst >= src)  # uniform over the other nodes
+    lo_l.append(np.minimum(src, dst))
+    hi_l.append(np.maximum(src, dst))
+    keys = np.unique(np.concatenate(lo_l) * n + np.concatenate(hi_l))
+    return _symmetric_adjacency(n, keys // n, keys % n)
+
+
 def barabasi_albert(n: int, m: int, seed: int) -> CSR:
     """Symmetric 0/1 adjacency of a Barabasi-Albert graph.
 
