@@ -57,10 +57,11 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle CPU time for cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="erdos_renyi",
-                    choices=["erdos_renyi", "ctmc_batch", "heat3d", "ba_cv", "tc"],
+                    choices=["erdos_renyi", "ctmc_batch", "heat3d", "ba_cv", "tc", "splitting", "ranking"],
                     help="erdos_renyi: the default line; ctmc_batch / heat3d / ba_cv / tc: the batched CTMC "
                          "transients, the 3D heat equation, the learned control variate's time to 1e-2 "
-                         "error and the total communicability at the paper's settings (own JSON lines)")
+                         "error and the total communicability at the paper's settings; splitting / ranking: "
+                         "the splitting-error and sample-size study and the ranking similarities (own JSON lines)")
     return ap.parse_args()
 
 
@@ -497,12 +498,13 @@ PAPER_TC_PATHS_PER_S = {"small_world": 1e6 / 0.95, "scale_free": 1e6 / 0.71}
 
 
 def run_tc(args):
-    """Total communicability TC = 1^T exp(A) 1 (beta = 1) by Algorithm 2 with v = 1 at the
-    paper's settings: M = 1e6 paths, dt = 1/32 (STRANG, N = 32), on a small-world graph
-    (ring lattice k = 1 + shortcuts p = 0.2, mean degree 2.4) and a scale-free graph (BA,
-    m = 2), n = 1e6.  Each step is one whole call (start tables, walk, reduction).  Also
-    reported: EXACT and LIE at the same M, the throughput at M = 1e9, and the estimate
-    against the FP64 Taylor oracle."""
+    """Total communicability TC = 1^T exp(beta A) 1 by Algorithm 2 with v = 1 at the paper's
+    settings: M = 1e6 paths, dt = beta/32 (STRANG, N = 32), on a small-world graph (ring
+    lattice k = 1 + shortcuts p = 0.2, mean degree 2.4; beta = 1) and a scale-free graph
+    (BA, m = 2; beta = 1/d_max), n = 1e6.  Each timed step is one whole call (walk and
+    reduction; the plan keeps the start tables of v = 1 after the first call, whose time
+    is reported apart).  Also reported: EXACT and LIE at the same M, the throughput at
+    M = 1e9, and the estimate against the FP64 Taylor oracle."""
     import numpy as np
     import torch
 
@@ -516,25 +518,36 @@ def run_tc(args):
     N = 32
     flush = torch.empty(512 * 2 ** 20 // 4, dtype=torch.float32, device="cuda")
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    # small-world: beta = 1; scale-free: beta = 1/d_max and TC_n = TC/n, as the paper does for
+    # graphs with hubs (dt = beta/32 in both)
     graphs = {"small_world": W.small_world(n, 1, 0.2, SEED), "scale_free": W.barabasi_albert(n, 2, SEED)}
     res = {}
     with ClockSampler(0) as clk:
         for name, csr in graphs.items():
+            t_cold0 = time.perf_counter()
             plan = P.Plan.from_csr(csr)
             dev = [torch.as_tensor(a).cuda() for a in (csr.row_ptr, csr.col, csr.val)]
             lam, _ = P.power_iteration(*dev, max_iters=20000, tol=1e-9)  # symmetric A: ||A||_2 = lambda_max
-            exact = float(OD.taylor_expmv(csr.to_scipy(), 1.0, np.ones(n), norm_bound=lam).sum())
+            dmax = int(np.diff(csr.row_ptr).max())
+            beta = 1.0 if name == "small_world" else 1.0 / dmax
+            exact = float(OD.taylor_expmv(csr.to_scipy(), beta, np.ones(n), norm_bound=lam * beta).sum())
             out = (torch.empty(1, dtype=torch.float64, device="cuda"), torch.empty(1, dtype=torch.float64, device="cuda"))
-            r = {"n": n, "nnz": csr.nnz, "lambda_max": lam, "tc_exact_oracle": exact}
+            a0, b0 = ev(), ev()
+            a0.record()
+            plan.total_communicability(beta, M, mode="strang", nsteps=N, seed=SEED + 999, out=out)  # builds tables
+            b0.record()
+            torch.cuda.synchronize()
+            r = {"n": n, "nnz": csr.nnz, "lambda_max": lam, "d_max": dmax, "beta": beta, "tc_exact_oracle": exact,
+                 "tc_n_exact_oracle": exact / n, "first_call_ms_with_start_tables": a0.elapsed_time(b0)}
             for mode, nsteps, paths in (("strang", N, M), ("lie", N, M), ("exact", 1, M), ("exact", 1, 10 ** 9)):
                 for w in range(args.warmup):
-                    plan.total_communicability(1.0, paths, mode=mode, nsteps=nsteps, seed=SEED + 1000 + w, out=out)
+                    plan.total_communicability(beta, paths, mode=mode, nsteps=nsteps, seed=SEED + 1000 + w, out=out)
                 ts, vals = [], []
                 for k in range(args.steps if paths == M else 3):
                     flush.zero_()
                     a, b = ev(), ev()
                     a.record()
-                    tc, se = plan.total_communicability(1.0, paths, mode=mode, nsteps=nsteps, seed=SEED + k, out=out)
+                    tc, se = plan.total_communicability(beta, paths, mode=mode, nsteps=nsteps, seed=SEED + k, out=out)
                     b.record()
                     torch.cuda.synchronize()
                     ts.append(a.elapsed_time(b))
@@ -562,6 +575,129 @@ def run_tc(args):
     print(json.dumps(line), flush=True)
 
 
+def _slope(xs, ys):
+    import numpy as np
+
+    xs, ys = np.log(np.asarray(xs, float)), np.log(np.asarray(ys, float))
+    return float(np.polyfit(xs, ys, 1)[0])
+
+
+def run_splitting(args):
+    """Splitting error and statistical error of the method (Sec. 5; Figs. 2-4): on a
+    small-world graph of 1000 nodes at beta = 1, TC = 1^T exp(A) 1 and the communicability
+    of node 0 by LIE and STRANG for dt = 1/2 ... 1/64, each against the exact value, with
+    the pure splitting error from the dense split products beside them, and the error of
+    EXACT-mode TC against the sample size M.  Slopes of log-log fits are reported."""
+    import numpy as np
+    import torch
+
+    import paper_1904_12759_gb300 as P
+    import workloads as W
+    from oracle import dense as OD
+
+    torch.cuda.set_device(0)
+    n = 1000
+    csr = W.small_world(n, 1, 0.2, SEED)
+    a = csr.to_scipy().toarray()
+    ones = np.ones(n)
+    x_exact = OD.expmv_dense(a, 1.0, ones)
+    tc_exact = float(x_exact.sum())
+    plan = P.Plan.from_csr(csr)
+    one = torch.ones(n, dtype=torch.float64, device="cuda")
+    ent = torch.zeros(1, dtype=torch.int32, device="cuda")
+    t0 = time.perf_counter()
+    rows = []
+    with ClockSampler(0) as clk:
+        for N in (2, 4, 8, 16, 32, 64):
+            row = {"dt": 1.0 / N}
+            for mode in ("lie", "strang"):
+                xs = OD.split_expmv(a, 1.0, N, ones, mode)
+                tc, se = plan.total_communicability(1.0, 4 * 10 ** 8, mode=mode, nsteps=N, seed=SEED + N,
+                                                    prec="fp32")
+                m0, s0 = plan.estimate(one, 1.0, 10 ** 8, entries=ent, mode=mode, nsteps=N, seed=SEED + N)
+                row[mode] = {"tc_split_err": abs(float(xs.sum()) - tc_exact) / tc_exact,
+                             "tc_mc_err": abs(tc.item() - tc_exact) / tc_exact, "tc_mc_rel_se": se.item() / tc.item(),
+                             "node0_split_err": abs(xs[0] - x_exact[0]) / x_exact[0],
+                             "node0_mc_err": abs(m0.item() - x_exact[0]) / x_exact[0],
+                             "node0_mc_rel_se": s0.item() / m0.item()}
+            rows.append(row)
+        mrows = []
+        for M in (10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7, 10 ** 8):
+            errs = []
+            for k in range(8):
+                tc, se = plan.total_communicability(1.0, M, seed=SEED + 97 * k + M % 89, prec="fp32")
+                errs.append(abs(tc.item() - tc_exact) / tc_exact)
+            mrows.append({"M": M, "rms_rel_err": float(np.sqrt(np.mean(np.square(errs))))})
+    plan.close()
+    dts = [r["dt"] for r in rows]
+    slopes = {f"{mode}_{q}": _slope(dts, [r[mode][q] for r in rows])
+              for mode in ("lie", "strang") for q in ("tc_split_err", "node0_split_err")}
+    slopes["mc_err_vs_M"] = _slope([r["M"] for r in mrows], [r["rms_rel_err"] for r in mrows])
+    line = {"metric": "splitting and statistical error study (Sec. 5, Figs. 2-4)", "value": slopes["mc_err_vs_M"],
+            "unit": "log-log slope of TC error vs M", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "splitting_small_world_n1000", "beta": 1.0, "tc_exact": tc_exact,
+                       "paths_tc": 4e8, "paths_node0": 1e8},
+            "slopes": slopes, "dt_sweep": rows, "m_sweep": mrows, "wall_s": time.perf_counter() - t0,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def run_ranking(args):
+    """Ranking similarity (Sec. 6, Tables 1 and 3).  Table 1: small-world graphs of 1e3 and
+    1e4 nodes, beta = 1; node communicabilities exp(A) 1 by the forward form (Algorithm 2,
+    STRANG, dt = 1/32) with M = 1e5, 1e6, 1e7 paths against the exact vector: isim over all
+    nodes and over the top 10%.  Table 3: scale-free (BA, m = 2) graphs of 1e3 and 1e4
+    nodes: exact exp(beta A) 1 for beta = 1, 0.5, 0.125, 1/lambda_max, 1/d_max ranked
+    against beta = 1, and the same with the forward estimate at M = 1e7."""
+    import numpy as np
+    import torch
+
+    import paper_1904_12759_gb300 as P
+    import workloads as W
+    from oracle import dense as OD
+    from paper_1904_12759_gb300 import metrics
+
+    torch.cuda.set_device(0)
+    t1, t3 = [], []
+    with ClockSampler(0) as clk:
+        for n in (1000, 10000):
+            csr = W.small_world(n, 1, 0.2, SEED)
+            lam = float(OD.power_iteration(csr.to_scipy(), iters=100000, tol=1e-13))
+            exact = OD.taylor_expmv(csr.to_scipy(), 1.0, np.ones(n), norm_bound=lam)
+            plan = P.Plan.from_csr(csr)
+            one = torch.ones(n, dtype=torch.float64, device="cuda")
+            for M in (10 ** 5, 10 ** 6, 10 ** 7):
+                x, _ = plan.forward(one, 1.0, M, mode="strang", nsteps=32, seed=SEED + M % 101)
+                xe = x.cpu().numpy()
+                t1.append({"n": n, "M": M, "isim_100": metrics.isim(xe, exact),
+                           "isim_10": metrics.isim(xe, exact, n // 10)})
+            plan.close()
+        for n in (1000, 10000):
+            csr = W.barabasi_albert(n, 2, SEED)
+            sp = csr.to_scipy()
+            lam = float(OD.power_iteration(sp, iters=100000, tol=1e-13))
+            dmax = float(np.diff(csr.row_ptr).max())
+            ref = OD.taylor_expmv(sp, 1.0, np.ones(n), norm_bound=lam)
+            plan = P.Plan.from_csr(csr)
+            one = torch.ones(n, dtype=torch.float64, device="cuda")
+            for name, beta in (("1", 1.0), ("0.5", 0.5), ("0.125", 0.125), ("1/lambda_max", 1 / lam),
+                               ("1/d_max", 1 / dmax)):
+                xb = OD.taylor_expmv(sp, beta, np.ones(n), norm_bound=lam * beta)
+                x, _ = plan.forward(one, beta, 10 ** 7, mode="strang", nsteps=32, seed=SEED + 7)
+                xm = x.cpu().numpy()
+                t3.append({"n": n, "lambda_max": lam, "d_max": dmax, "beta": name,
+                           "exact_isim_100": metrics.isim(xb, ref), "exact_isim_10": metrics.isim(xb, ref, n // 10),
+                           "mc_isim_100": metrics.isim(xm, ref), "mc_isim_10": metrics.isim(xm, ref, n // 10)})
+            plan.close()
+    head = next(r for r in t1 if r["n"] == 10000 and r["M"] == 10 ** 7)
+    line = {"metric": "ranking intersection similarity isim (Sec. 6, Tables 1 and 3)", "value": head["isim_100"],
+            "unit": "isim over all nodes, small-world n=1e4, M=1e7", "higher_is_better": False, "n_gpus": 1,
+            "data": "synthetic", "config": {"workload": "ranking_small_world_scale_free", "dt": 1 / 32,
+                                            "functional": "strang"},
+            "table1": t1, "table3": t3, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -578,6 +714,12 @@ def main():
         return
     if args.workload == "tc":
         run_tc(args)
+        return
+    if args.workload == "splitting":
+        run_splitting(args)
+        return
+    if args.workload == "ranking":
+        run_ranking(args)
         return
     import numpy as np
     import torch

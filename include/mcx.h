@@ -195,7 +195,9 @@ mcx_status mcx_estimate_forward(mcx_plan *plan, const double *v, double t, int f
  *                error (sem may be NULL); t = 0 gives n exactly (synchronising)
  * Per-warp partial sums of W (log-sum-exp shifted, compensated within lanes)
  * are merged in warp order, so the result is deterministic.  Uses the plan's
- * forward scratch and grows its partial-sum scratch as needed.
+ * forward scratch (the start tables of v = 1 are built on the first call and
+ * kept until a forward call with another v replaces them) and grows its
+ * partial-sum scratch as needed.
  * Errors: MCX_E_INVALID, MCX_E_CUDA, MCX_E_OOM; MCX_E_OVERFLOW at mcx_sync.
  */
 mcx_status mcx_total_communicability(mcx_plan *plan, double t, int functional, int32_t nsteps,

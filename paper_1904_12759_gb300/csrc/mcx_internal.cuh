@@ -90,6 +90,7 @@ struct mcx_plan {
     void *fwd = nullptr;               // forward-form scratch (start tables, deposits), made on first use
     size_t fwd_bytes = 0;
     bool zero_potential = false;       // every delta_i == 0 exactly (forward weights are 1)
+    bool fwd_ones = false;             // the forward start tables currently hold v = 1
     int64_t device_bytes = 0;
 };
 

@@ -870,6 +870,7 @@ cudaError_t fwd_scratch(mcx_plan *plan, FwdScratch *fs) {
         cudaFree(plan->fwd);
         plan->fwd = nullptr;
         plan->fwd_bytes = 0;
+        plan->fwd_ones = false;
         cudaError_t e = cudaMalloc(&plan->fwd, need);
         if (e != cudaSuccess) return e;
         plan->fwd_bytes = need;
@@ -892,21 +893,29 @@ cudaError_t fwd_scratch(mcx_plan *plan, FwdScratch *fs) {
 }
 
 // Build the two-level start tables on `st`; fills the FwdTables view.
+// the tables in the forward scratch as the walkers see them
+FwdTables start_view(const mcx_plan *plan, const FwdScratch &fs) {
+    FwdTables f;
+    f.top = fs.top;
+    f.in = fs.in;
+    f.n = plan->n;
+    f.G = (uint64_t)((plan->n + START_GROUP - 1) / START_GROUP);
+    f.V = fs.V;
+    f.bad = fs.bad;
+    return f;
+}
+
 cudaError_t build_start_tables(mcx_plan *plan, const double *v, const FwdScratch &fs, FwdTables *f, cudaStream_t st) {
     const int64_t n = plan->n;
     const int64_t G = (n + START_GROUP - 1) / START_GROUP;
+    plan->fwd_ones = false;
     cudaError_t e = cudaMemsetAsync(fs.bad, 0, 4, st);
     if (e != cudaSuccess) return e;
     const unsigned gb = (unsigned)((G + 127) / 128);
     k_group_sums<<<gb, 128, 0, st>>>(n, v, fs.S, fs.bad);
     k_top_table<<<1, 1, 0, st>>>(G, fs.S, fs.top, fs.q, fs.stack, fs.V, fs.bad);
     k_inner_tables<<<gb, 128, 0, st>>>(n, v, fs.S, fs.in, fs.q, fs.stack);
-    f->top = fs.top;
-    f->in = fs.in;
-    f->n = n;
-    f->G = (uint64_t)G;
-    f->V = fs.V;
-    f->bad = fs.bad;
+    *f = start_view(plan, fs);
     return cudaGetLastError();
 }
 
@@ -995,10 +1004,14 @@ cudaError_t launch_total_communicability(mcx_plan *plan, double t, int mode, int
     FwdScratch fs;
     cudaError_t e = fwd_scratch(plan, &fs);
     if (e != cudaSuccess) return e;
-    double *ones = fs.dep;  // the deposit area is free in this mode
-    k_fill<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32), 256, 0, st>>>(n, ones, 1.0);
-    FwdTables f;
-    if ((e = build_start_tables(plan, ones, fs, &f, st)) != cudaSuccess) return e;
+    // the start tables of v = 1 are built once and kept until another forward call replaces them
+    FwdTables f = start_view(plan, fs);
+    if (!plan->fwd_ones) {
+        double *ones = fs.dep;  // the deposit area is free in this mode
+        k_fill<<<(unsigned)std::min<int64_t>((n + 255) / 256, 152 * 32), 256, 0, st>>>(n, ones, 1.0);
+        if ((e = build_start_tables(plan, ones, fs, &f, st)) != cudaSuccess) return e;
+        plan->fwd_ones = true;
+    }
     WalkParams p = make_params(plan, t, mode == MCX_EXACT ? 1 : nsteps, seed);
     p.paths = paths;
     p.path_offset = path_offset;

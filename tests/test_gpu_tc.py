@@ -103,3 +103,20 @@ def test_tc_offset_composes_and_edge_cases(mcx):
     with pytest.raises(Exception):
         plan.total_communicability(t, 1)
     plan.close()
+
+
+def test_tc_start_tables_survive_and_refresh(mcx):
+    """The plan keeps the start tables of v = 1 between TC calls; a forward call with
+    another v replaces them, and the next TC call rebuilds them (same result)."""
+    csr = W.erdos_renyi(3000, 5, 8)
+    plan = mcx.Plan.from_csr(csr)
+    t = 0.25
+    a, _ = plan.total_communicability(t, 50000, seed=21, prec="fp64")
+    b, _ = plan.total_communicability(t, 50000, seed=21, prec="fp64")
+    v = torch.as_tensor(W.uniform_vector(3000, 4)).cuda()
+    plan.forward(v, t, 20000, seed=5)
+    c, _ = plan.total_communicability(t, 50000, seed=21, prec="fp64")
+    assert a.item() == b.item() == c.item()
+    otc, _ = _oracle_tc(csr, t, 50000, 21, prec="fp64")
+    assert abs(a.item() - otc) <= 1e-12 * otc
+    plan.close()
