@@ -239,6 +239,29 @@ def test_diagonal_and_isolated_nodes_exact(mcx):
     plan.close()
 
 
+@pytest.mark.parametrize("a00", [0.0, -1.25, 0.7])
+def test_single_state(mcx, a00):
+    """n = 1: no jumps, exp(t a) v exactly for the backward form (any M, both layouts,
+    both precisions), the forward form and the total communicability."""
+    rp = np.array([0, 1], np.int64) if a00 != 0.0 else np.array([0, 0], np.int64)
+    col = np.array([0], np.int32)[: rp[1]]
+    val = np.array([a00])[: rp[1]]
+    plan = mcx.Plan(_cuda(rp, torch.int64), _cuda(col, torch.int32), _cuda(val, torch.float64))
+    t, v = 0.8, np.array([1.5])
+    want = math.exp(t * a00) * 1.5
+    for M in (1, 40, 5000):
+        for prec, tol in (("fp32", 1e-6), ("fp64", 1e-15)):
+            gm, gs = plan.estimate(_cuda(v, torch.float64), t, M, prec=prec)
+            assert abs(gm.item() - want) <= tol * want and gs.item() == 0.0
+    # forward and TC sum 1000 equal FP64 terms: within 1000 * 2^-53 of the value
+    x, _ = plan.forward(_cuda(v, torch.float64), t, 1000, prec="fp64")
+    assert abs(x.item() - want) <= 2e-13 * want
+    tc, se = plan.total_communicability(t, 1000, prec="fp64")
+    assert abs(tc.item() - math.exp(t * a00)) <= 2e-13 * math.exp(t * a00) and se.item() == 0.0
+    assert plan.sync()["status_bits"] == 0
+    plan.close()
+
+
 def test_zero_potential_gives_one(mcx):
     q = W.random_generator(2000, 7)
     plan = mcx.Plan.from_csr(q)
