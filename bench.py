@@ -886,11 +886,10 @@ def main():
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": None, "clocks": clk.summary(),
     }
     # per step: prep (rows, scan tiles, scan sums, scan add, fill) + power iteration (init, long-row
-    # list, then per iteration the short-row SpMV and the dot products, launched in batches of 8; this
-    # graph has no row above 32 entries, so no long-row kernel is launched) + estimate (pack v, walk);
-    # L2 flushes are torch's, not counted
+    # list, then one fused SpMV + dot-product kernel per iteration, launched in batches of 8: this
+    # graph has no row above 32 entries) + estimate (pack v, walk); L2 flushes are torch's, not counted
     batches = -(-iters // 8)
-    line["gpu_launches"] = args.steps * (5 + 2 + 2 * 8 * batches + 2)
+    line["gpu_launches"] = args.steps * (5 + 2 + 8 * batches + 2)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

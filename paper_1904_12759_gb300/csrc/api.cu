@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdlib.h>
 
+#include <mutex>
 #include <new>
 
 #include "mcx_internal.cuh"
@@ -20,19 +21,56 @@ mcx_status from_cuda(cudaError_t e) {
     return MCX_E_CUDA;
 }
 
+// The plan's own arrays come from the memory pool; its grow-only scratch from cudaMalloc.
+// Called with no work of the plan in flight.
 void free_plan(mcx_plan *p) {
     if (!p) return;
-    cudaFree(p->node);
-    cudaFree(p->node64);
-    cudaFree(p->edge_col);
-    cudaFree(p->edge16);
-    cudaFree(p->status);
+    pool_free(p->node, 0);
+    pool_free(p->node64, 0);
+    pool_free(p->edge_col, 0);
+    pool_free(p->edge16, 0);
+    pool_free(p->status, 0);
     cudaFree(p->scratch);
     cudaFree(p->fwd);
     delete p;
 }
 
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[64];
+bool g_pool_ready[64] = {};
+
 }  // namespace
+
+namespace mcx {
+
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        if (!g_pool_ready[dev]) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            if ((e = cudaMemPoolCreate(&g_pools[dev], &props)) != cudaSuccess) return e;
+            uint64_t keep = ~0ull;  // never trim: freed blocks serve the next plan
+            cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+            g_pool_ready[dev] = true;
+        }
+        pool = g_pools[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes ? bytes : 1, pool, st);
+}
+
+void pool_free(void *p, cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+}
+
+}  // namespace mcx
 
 extern "C" {
 
@@ -76,18 +114,18 @@ mcx_status mcx_plan_create(int64_t n, int64_t nnz, const int64_t *row_ptr, const
     do {
         cudaError_t e;
         const size_t nn = (size_t)(n > 0 ? n : 1);
-        if ((e = cudaMalloc(&p->node, sizeof(NodeRec) * nn)) != cudaSuccess) { rc = from_cuda(e); break; }
-        if ((e = cudaMalloc(&p->node64, sizeof(NodeRec64) * nn)) != cudaSuccess) { rc = from_cuda(e); break; }
-        if ((e = cudaMalloc(&p->status, 32)) != cudaSuccess) { rc = from_cuda(e); break; }
+        if ((e = pool_alloc(reinterpret_cast<void **>(&p->node), sizeof(NodeRec) * nn, st)) != cudaSuccess) { rc = from_cuda(e); break; }
+        if ((e = pool_alloc(reinterpret_cast<void **>(&p->node64), sizeof(NodeRec64) * nn, st)) != cudaSuccess) { rc = from_cuda(e); break; }
+        if ((e = pool_alloc(reinterpret_cast<void **>(&p->status), 32, st)) != cudaSuccess) { rc = from_cuda(e); break; }
         if ((e = cudaMemsetAsync(p->status, 0, 32, st)) != cudaSuccess) { rc = from_cuda(e); break; }
         p->device_bytes = (int64_t)((sizeof(NodeRec) + sizeof(NodeRec64)) * nn + 16);
         const int64_t *rp = row_ptr;
         const int32_t *cc = col;
         const double *vv = val;
         if (host) {
-            if ((e = cudaMalloc(&d_rp, sizeof(int64_t) * (size_t)(n + 1))) != cudaSuccess) { rc = from_cuda(e); break; }
-            if ((e = cudaMalloc(&d_col, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) { rc = from_cuda(e); break; }
-            if ((e = cudaMalloc(&d_val, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1))) != cudaSuccess) { rc = from_cuda(e); break; }
+            if ((e = pool_alloc(reinterpret_cast<void **>(&d_rp), sizeof(int64_t) * (size_t)(n + 1), st)) != cudaSuccess) { rc = from_cuda(e); break; }
+            if ((e = pool_alloc(reinterpret_cast<void **>(&d_col), sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1), st)) != cudaSuccess) { rc = from_cuda(e); break; }
+            if ((e = pool_alloc(reinterpret_cast<void **>(&d_val), sizeof(double) * (size_t)(nnz > 0 ? nnz : 1), st)) != cudaSuccess) { rc = from_cuda(e); break; }
             if ((e = cudaMemcpyAsync(d_rp, row_ptr, sizeof(int64_t) * (size_t)(n + 1), cudaMemcpyHostToDevice, st)) != cudaSuccess) { rc = from_cuda(e); break; }
             if (nnz > 0) {
                 if ((e = cudaMemcpyAsync(d_col, col, sizeof(int32_t) * (size_t)nnz, cudaMemcpyHostToDevice, st)) != cudaSuccess) { rc = from_cuda(e); break; }
@@ -100,11 +138,10 @@ mcx_status mcx_plan_create(int64_t n, int64_t nnz, const int64_t *row_ptr, const
         else if (dev_status & ST_NONFINITE) rc = MCX_E_NONFINITE;
         else if (dev_status & ST_NEG_OFFDIAG) rc = MCX_E_NEG_OFFDIAG;
     } while (0);
-    if (host) {
-        cudaStreamSynchronize(st);
-        cudaFree(d_rp);
-        cudaFree(d_col);
-        cudaFree(d_val);
+    if (host) {  // stream-ordered: freed after the preparation that reads them
+        pool_free(d_rp, st);
+        pool_free(d_col, st);
+        pool_free(d_val, st);
     }
     if (rc != MCX_OK) {
         cudaStreamSynchronize(st);

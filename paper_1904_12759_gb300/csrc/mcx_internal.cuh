@@ -252,6 +252,12 @@ uint64_t noalloc_max_partials();
 cudaError_t launch_estimate_forward(mcx_plan *plan, const double *v, double t, int mode, int nsteps, uint64_t paths,
                                     uint64_t seed, uint64_t path_offset, int precision, double *x, double *sem,
                                     cudaStream_t st);
+// Stream-ordered allocation from the library's memory pool of the current
+// device (created on first use; memory freed to it stays reserved for the next
+// plan instead of going back to the driver, so plans are created and destroyed
+// without device-wide synchronisation).
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st);
+void pool_free(void *p, cudaStream_t st);
 cudaError_t launch_total_communicability(mcx_plan *plan, double t, int mode, int nsteps, uint64_t paths,
                                          uint64_t seed, uint64_t path_offset, int precision, double *tc, double *sem,
                                          cudaStream_t st);

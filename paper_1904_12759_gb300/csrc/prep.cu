@@ -295,16 +295,16 @@ cudaError_t launch_prep(mcx_plan *plan, const int64_t *row_ptr, const int32_t *c
     int32_t *stack = nullptr;
     AliasEnt *alias = nullptr;
     cudaError_t err = cudaSuccess;
-    auto cleanup = [&]() {
-        cudaFree(deg); cudaFree(excl); cudaFree(tile_sum); cudaFree(tot_d); cudaFree(qbuf); cudaFree(stack);
-        cudaFree(alias);
+    auto cleanup = [&]() {  // stream-ordered frees to the library pool
+        pool_free(deg, st); pool_free(excl, st); pool_free(tile_sum, st); pool_free(tot_d, st);
+        pool_free(qbuf, st); pool_free(stack, st); pool_free(alias, st);
     };
     PrepTotals tot{};
     do {
-        if ((err = cudaMalloc(&deg, sizeof(int32_t) * (size_t)(n + 1))) != cudaSuccess) break;
-        if ((err = cudaMalloc(&excl, sizeof(int64_t) * (size_t)(n + 1))) != cudaSuccess) break;
-        if ((err = cudaMalloc(&tile_sum, sizeof(int64_t) * (size_t)(ntiles + 1))) != cudaSuccess) break;
-        if ((err = cudaMalloc(&tot_d, sizeof(PrepTotals))) != cudaSuccess) break;
+        if ((err = pool_alloc(reinterpret_cast<void **>(&deg), sizeof(int32_t) * (size_t)(n + 1), st)) != cudaSuccess) break;
+        if ((err = pool_alloc(reinterpret_cast<void **>(&excl), sizeof(int64_t) * (size_t)(n + 1), st)) != cudaSuccess) break;
+        if ((err = pool_alloc(reinterpret_cast<void **>(&tile_sum), sizeof(int64_t) * (size_t)(ntiles + 1), st)) != cudaSuccess) break;
+        if ((err = pool_alloc(reinterpret_cast<void **>(&tot_d), sizeof(PrepTotals), st)) != cudaSuccess) break;
         if ((err = cudaMemsetAsync(tot_d, 0, sizeof(PrepTotals), st)) != cudaSuccess) break;
         const int64_t nb = (n + PREP_THREADS - 1) / PREP_THREADS;
         if (n > 0) {
@@ -326,14 +326,14 @@ cudaError_t launch_prep(mcx_plan *plan, const int64_t *row_ptr, const int32_t *c
         plan->weighted_rows = (int64_t)tot.weighted_rows;
         plan->zero_potential = tot.nonzero_potential == 0;
         const size_t m = (size_t)(plan->nnz_off > 0 ? plan->nnz_off : 1);
-        if ((err = cudaMalloc(&plan->edge_col, sizeof(int32_t) * m)) != cudaSuccess) break;
+        if ((err = pool_alloc(reinterpret_cast<void **>(&plan->edge_col), sizeof(int32_t) * m, st)) != cudaSuccess) break;
         plan->device_bytes += (int64_t)(sizeof(int32_t) * m);
         if (plan->weighted_rows > 0) {
-            if ((err = cudaMalloc(&alias, sizeof(AliasEnt) * m)) != cudaSuccess) break;
-            if ((err = cudaMalloc(&plan->edge16, sizeof(Edge16) * m)) != cudaSuccess) break;
+            if ((err = pool_alloc(reinterpret_cast<void **>(&alias), sizeof(AliasEnt) * m, st)) != cudaSuccess) break;
+            if ((err = pool_alloc(reinterpret_cast<void **>(&plan->edge16), sizeof(Edge16) * m, st)) != cudaSuccess) break;
             plan->device_bytes += (int64_t)(sizeof(Edge16) * m);
-            if ((err = cudaMalloc(&qbuf, sizeof(double) * m)) != cudaSuccess) break;
-            if ((err = cudaMalloc(&stack, sizeof(int32_t) * m)) != cudaSuccess) break;
+            if ((err = pool_alloc(reinterpret_cast<void **>(&qbuf), sizeof(double) * m, st)) != cudaSuccess) break;
+            if ((err = pool_alloc(reinterpret_cast<void **>(&stack), sizeof(int32_t) * m, st)) != cudaSuccess) break;
         }
         if (n > 0) {
             k_prep_fill<<<(unsigned)nb, PREP_THREADS, 0, st>>>(n, row_ptr, col, val, plan->node, plan->edge_col,

@@ -8,7 +8,8 @@
 // lambda_k = (s_k x_k) . y and s_{k+1} = 1/||y||, then x_{k+1} = y (ping-pong
 // buffers).  Per iteration: the short-row SpMV, the long-row SpMVs (hubs, one
 // warp or one block per row; the long rows are listed once per call and their
-// kernels launched only if the graph has such rows), and a dot-product
+// kernels launched only if the graph has such rows; without them the SpMV and
+// the dot products run as one kernel), and a dot-product
 // pass whose block partials the last block to finish reduces in a fixed order,
 // so the result does not depend on scheduling.  Iterations stop when
 // |lambda_k - lambda_{k-1}| <= tol |lambda_k|; the host checks every CHECK
@@ -149,6 +150,28 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double (*sh)[2]
     }
 }
 
+// The last block of a dot pass: the block partials in block order, then the
+// Rayleigh quotient lambda = (s x) . y, the next scale 1/||y|| and the test.
+__device__ __forceinline__ void power_finish(PowerScalars *sc, const double *part, double tol, double (*sh)[2]) {
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += PI_THREADS) {
+        a += ((volatile const double *)part)[2 * k];
+        b += ((volatile const double *)part)[2 * k + 1];
+    }
+    __syncthreads();
+    block_sum2(a, b, sh);
+    if (threadIdx.x == 0) {
+        const int32_t it = sc->iters + 1;
+        sc->lambda_prev = sc->lambda;
+        sc->lambda = a;
+        sc->iters = it;
+        sc->inv_norm = b > 0.0 ? 1.0 / sqrt(b) : 0.0;
+        sc->ticket = 0;
+        if (b == 0.0 || (it > 1 && fabs(a - sc->lambda_prev) <= tol * fabs(a))) sc->done = 1;
+    }
+}
+
 // (s x) . y and y . y by blocks in a fixed grid-stride order; the last block
 // reduces the block partials in block order and updates the scalars.
 __global__ void __launch_bounds__(PI_THREADS) k_power_dots(int64_t n, const double *__restrict__ x,
@@ -172,24 +195,41 @@ __global__ void __launch_bounds__(PI_THREADS) k_power_dots(int64_t n, const doub
         last = atomicAdd(&sc->ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!last) return;
-    __threadfence();
-    double a = 0.0, b = 0.0;
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += PI_THREADS) {
-        a += ((volatile double *)part)[2 * k];
-        b += ((volatile double *)part)[2 * k + 1];
+    if (last) power_finish(sc, part, tol, sh);
+}
+
+// One whole iteration for matrices without rows above LONG_ROW entries: y = A (s x)
+// one thread per row, and the dot products x . y, y . y in the same pass (per-thread
+// sums in grid-stride order, fixed block tree, the last block reduces the block
+// partials in block order).  The grid must not exceed PI_MAX_BLOCKS blocks.
+__global__ void __launch_bounds__(PI_THREADS) k_power_fused(int64_t n, const int64_t *__restrict__ rp,
+                                                            const int32_t *__restrict__ col,
+                                                            const double *__restrict__ val,
+                                                            const double *__restrict__ x, double *__restrict__ y,
+                                                            double *__restrict__ part, PowerScalars *sc,
+                                                            double tol) {
+    __shared__ double sh[PI_THREADS / 32][2];
+    __shared__ bool last;
+    if (*(volatile int32_t *)&sc->done) return;  // uniform over the grid
+    const double s = sc->inv_norm;
+    double xy = 0.0, yy = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * PI_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * PI_THREADS) {
+        double acc = 0.0;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) acc = __fma_rn(val[p], x[col[p]], acc);
+        const double yi = __dmul_rn(acc, s);
+        y[i] = yi;
+        xy = __fma_rn(__dmul_rn(s, x[i]), yi, xy);
+        yy = __fma_rn(yi, yi, yy);
+    }
+    block_sum2(xy, yy, sh);
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = xy;
+        part[2 * blockIdx.x + 1] = yy;
+        __threadfence();
+        last = atomicAdd(&sc->ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    block_sum2(a, b, sh);
-    if (threadIdx.x == 0) {
-        const int32_t it = sc->iters + 1;
-        sc->lambda_prev = sc->lambda;
-        sc->lambda = a;
-        sc->iters = it;
-        sc->inv_norm = b > 0.0 ? 1.0 / sqrt(b) : 0.0;
-        sc->ticket = 0;
-        if (b == 0.0 || (it > 1 && fabs(a - sc->lambda_prev) <= tol * fabs(a))) sc->done = 1;
-    }
+    if (last) power_finish(sc, part, tol, sh);
 }
 
 }  // namespace
@@ -219,6 +259,10 @@ cudaError_t run_power_iteration(int64_t n, const int64_t *row_ptr, const int32_t
         for (int32_t b = 0; b < batch; ++b, ++launched) {
             const double *x = buf[launched & 1];
             double *y = buf[(launched + 1) & 1];
+            if (!any_long && !any_huge) {
+                k_power_fused<<<nb, PI_THREADS, 0, st>>>(n, row_ptr, col, val, x, y, part, s, tol);
+                continue;
+            }
             k_spmv_short<<<nrow, 256, 0, st>>>(n, row_ptr, col, val, x, &s->inv_norm, y, &s->done);
             if (any_long)
                 k_spmv_long<<<152 * 8, 256, 0, st>>>(queue, s->qn, row_ptr, col, val, x, &s->inv_norm, y, &s->done);
