@@ -60,7 +60,7 @@ typedef enum {
     MCX_E_CUDA = -5,         /* a CUDA runtime call failed */
     MCX_E_OOM = -6,          /* device allocation failed */
     MCX_E_TIMEOUT = -7,      /* a bounded device wait gave up */
-    MCX_E_UNSUPPORTED = -8,  /* valid request outside what this build implements */
+    MCX_E_UNSUPPORTED = -8,  /* valid request outside what this library implements */
     MCX_E_OVERFLOW = -9      /* an estimate or its standard error overflowed FP64 */
 } mcx_status;
 

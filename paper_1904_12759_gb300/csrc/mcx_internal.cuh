@@ -254,7 +254,7 @@ cudaError_t launch_estimate_forward(mcx_plan *plan, const double *v, double t, i
                                     cudaStream_t st);
 // Stream-ordered allocation from the library's memory pool of the current
 // device (created on first use; memory freed to it stays reserved for the next
-// plan instead of going back to the driver, so plans are created and destroyed
+// plan instead of being released to the system, so plans are created and destroyed
 // without device-wide synchronisation).
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st);
 void pool_free(void *p, cudaStream_t st);
