@@ -10,6 +10,8 @@ full-size run):
   1 path (the control-variate benchmark at M = 1): 64 sampled entries.
 * Total communicability on the small-world graph n = 1e6 at M = 1e6, STRANG
   N = 32: the whole sum over the same paths.
+* The 256-generator CTMC batch in one persistent graph launch: the 6 pairs of
+  the two smallest generators, exact counts.
 
 FP32 paths: means within 2e-6 of each entry's absolute scale (the path
 log-weights are bit-exact; see the parity bar of the small cases), control-variate
@@ -110,3 +112,25 @@ def test_total_communicability_paper_setting(mcx):
     assert abs(tc.item() - otc) <= 2e-6 * otc, (tc.item(), otc)
     assert abs(se.item() - csr.n * w.std(ddof=1) / math.sqrt(M)) <= 1e-3 * se.item()
     plan.close()
+
+
+def test_ctmc_batch_benchmark_sampled(mcx):
+    """The 256-generator batch of the CTMC benchmark in its persistent graph launch: the
+    pairs of the two smallest generators at every horizon against the oracle's
+    single-problem forward runs (path indices k * 2^40 + p), count for count."""
+    probs = W.ctmc_batch(256, 0)
+    b = mcx.Batch(probs)
+    b.run(seed=41)
+    torch.cuda.synchronize()
+    st = b.sync()
+    assert st["status_bits"] == 0
+    order = sorted(range(len(probs)), key=lambda i: probs[i]["csr"].n)[:2]
+    for i in order:
+        p = probs[i]
+        og = OW.Graph(p["csr"])
+        for ti, t in enumerate(p["times"]):
+            k = sum(len(q["times"]) for q in probs[:i]) + ti  # pairs numbered problem by problem
+            x, _ = b.result(i, ti)
+            ox, _, _ = og.forward(p["v"], t, p["paths"], seed=41, path_offset=k << 40)
+            assert np.allclose(x.cpu().numpy(), ox, rtol=1e-12, atol=1e-15), (i, ti)
+    b.close()
