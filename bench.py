@@ -56,6 +56,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle CPU time for cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--generators", type=int, default=256, help="ctmc_batch: number of generators")
+    ap.add_argument("--tune-cache", default=None, help="ctmc_batch: schedule cache file (JSON lines)")
     ap.add_argument("--workload", default="erdos_renyi",
                     choices=["erdos_renyi", "ctmc_batch", "heat3d", "ba_cv", "tc", "splitting", "ranking"],
                     help="erdos_renyi: the default line; ctmc_batch / heat3d / ba_cv / tc: the batched CTMC "
@@ -129,13 +131,15 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def _walk_traffic(args):
-    """DRAM bytes per walker launch from the committed ncu record, or None when the
-    walker sources changed since the capture (or the workload differs)."""
+def _traffic(workload):
+    """DRAM bytes per launch of the workload's dominant kernel from the committed ncu
+    record (profiles/traffic.json), or None when the kernel's sources changed since the
+    capture.  Records of captures on a smaller case hold the bytes scaled to a full
+    launch by the units processed (the record says so)."""
     import hashlib
 
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "k_walk_traffic.json")))
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[workload]
     except Exception:
         return None
     csrc = os.path.join(ROOT, "paper_1904_12759_gb300", "csrc")
@@ -145,9 +149,14 @@ def _walk_traffic(args):
                 return None
         except OSError:
             return None
+    return float(rec["dram_bytes_per_launch"])
+
+
+def _walk_traffic(args):
+    """The default workload's record (only for its default sizes)."""
     if args.n != N_NODES or args.paths != PATHS:
         return None
-    return float(rec["dram_bytes_per_launch"])
+    return _traffic("erdos_renyi")
 
 
 # ---------------------------------------------------------------------------
@@ -242,9 +251,9 @@ def run_ctmc_batch(args):
     import workloads as W
 
     torch.cuda.set_device(0)
-    probs = W.ctmc_batch(256, SEED)
+    probs = W.ctmc_batch(args.generators, SEED)
     t0 = time.perf_counter()
-    b = P.Batch(probs)
+    b = P.Batch(probs, tune_cache=args.tune_cache)
     create_s = time.perf_counter() - t0
     info = b.info()
     for w in range(args.warmup):
@@ -275,7 +284,7 @@ def run_ctmc_batch(args):
 
     order = sorted(range(len(probs)), key=lambda i: probs[i]["csr"].n)
     cpu_paths, cpu_s, used = 0, 0.0, 0
-    for i in order:
+    for i in ([] if args.no_cpu_baseline else order):
         p = probs[i]
         g = OW.Graph(p["csr"])
         t1 = time.perf_counter()
@@ -289,16 +298,18 @@ def run_ctmc_batch(args):
     line = {"metric": "walker jumps/s", "value": jumps / step_s, "unit": "jumps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "ctmc_batch", "generators": 256, "states": info["states"],
+            "config": {"workload": "ctmc_batch", "generators": args.generators, "states": info["states"],
                        "times": [0.1, 1.0, 10.0], "paths_per_state": 64, "functional": "exact, forward form",
                        "schedule": {k: info[k] for k in ("chunk", "blocks_per_sm", "grid", "work_items")},
                        "l2": "inputs (2 GB of edge records) larger than L2"},
             "walker": {"paths": paths, "jumps": jumps, "paths_per_s": paths / step_s,
                        "max_conservation_error": worst, "batch_create_s": create_s},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": "k_batch_walk", "bytes_per_jump": BYTES_PER_JUMP},
-            "cpu_baseline": {"value": cpu_paths / cpu_s, "unit": "paths/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{used} smallest generators x 3 horizons, forward form, sequential"},
+                         "traffic": _traffic("ctmc_batch") if args.generators == 256 else None,
+                         "kernel": "k_batch_walk", "bytes_per_jump": BYTES_PER_JUMP},
+            "cpu_baseline": None if not used else {
+                "value": cpu_paths / cpu_s, "unit": "paths/s", "cores": 1, "kind": "oracle",
+                "sample": f"{used} smallest generators x 3 horizons, forward form, sequential"},
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     b.close()
@@ -374,7 +385,7 @@ def run_heat3d(args):
                                 "fp64_sem_rel": float((s64 / m64.abs()).mean().item()),
                                 "diverged_path_fraction": float(np.mean(div)), "traced_paths": 8 * 100000},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": "k_walk", "bytes_per_jump": BYTES_PER_JUMP},
+                         "traffic": _traffic("heat3d"), "kernel": "k_walk", "bytes_per_jump": BYTES_PER_JUMP},
             "cpu_baseline": {"value": 16 * M / cpu_s, "unit": "paths/s", "cores": OW.num_threads(), "kind": "oracle",
                              "sample": "16 entries x 1e6 paths"},
             "clocks": clk.summary()}
@@ -562,12 +573,18 @@ def run_tc(args):
             plan.close()
             res[name] = r
     head = res["small_world"]["strang_N32_M1e6"]
+    thr = res["small_world"]["exact_M1e9"]  # the throughput launch: the walk dominates
+    achieved = BYTES_PER_JUMP * thr["jumps_per_path"] * thr["paths_per_s"] / 1e9
+    peak = float(_peaks().get("hbm_gbs", 6800.0))
     line = {"metric": "total communicability paths/s (Algorithm 2, v = 1)", "value": head["paths_per_s"],
             "unit": "paths/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": head["ms_per_call"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": head["paths_per_s"] / PAPER_TC_PATHS_PER_S["small_world"],
             "vs_baseline_note": "paper: one Xeon E5620 core, Fortran, small-world n=1e6, M=1e6, dt=0.03125: 0.95 s",
             "dtype": "f32", "data": "synthetic",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": _traffic("tc"), "kernel": "k_walk_tc (M = 1e9 call, EXACT)",
+                         "bytes_per_jump": BYTES_PER_JUMP},
             "config": {"workload": "tc_small_world_n1e6", "beta": 1.0, "paths": M, "functional": "strang",
                        "nsteps": N, "graph": "ring lattice k=1 + shortcuts p=0.2 (mean degree 2.4)",
                        "l2": "512 MiB buffer written between timed calls"},
