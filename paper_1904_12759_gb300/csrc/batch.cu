@@ -143,7 +143,7 @@ __device__ __forceinline__ int32_t batch_start(const BatchArgs &b, const BatchPT
 }
 
 template <bool WEIGHTED, bool COUNT>
-__global__ void __launch_bounds__(WALK_THREADS, 4) k_batch_walk(const __grid_constant__ WalkParams a,
+__global__ void __launch_bounds__(WALK_THREADS, 5) k_batch_walk(const __grid_constant__ WalkParams a,
                                                                const __grid_constant__ BatchArgs b) {
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -622,8 +622,8 @@ mcx_status mcx_batch_create(int32_t count, const mcx_problem *pr, const char *tu
             if ((e = make_items(b, L, st)) != cudaSuccess) break;
             if ((e = capture(b, st)) != cudaSuccess) break;
         } else {
-            const uint32_t Ls[] = {1024, 4096};
-            const int bpss[] = {3, 4};
+            const uint32_t Ls[] = {512, 1024, 2048, 4096};
+            const int bpss[] = {2, 3, 4, 5};  // 49 registers: at most 5 resident blocks of 256
             double best = 1e300;
             uint32_t bestL = 4096;
             int bestb = 4;
