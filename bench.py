@@ -131,11 +131,30 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _prefix_through(text, marker):
+    """The text from the start of a source file through the closing brace of the
+    first function whose signature contains `marker` (the kernel and everything it
+    can use above it), or None."""
+    i = text.find(marker)
+    if i < 0:
+        return None
+    j = text.find("{", i)
+    depth = 0
+    for k in range(j, len(text)):
+        if text[k] == "{":
+            depth += 1
+        elif text[k] == "}":
+            depth -= 1
+            if depth == 0:
+                return text[: k + 1]
+    return None
+
+
 def _traffic(workload):
     """DRAM bytes per launch of the workload's dominant kernel from the committed ncu
     record (profiles/traffic.json), or None when the kernel's sources changed since the
-    capture.  Records of captures on a smaller case hold the bytes scaled to a full
-    launch by the units processed (the record says so)."""
+    capture: whole headers, and each kernel file from its start through the end of the
+    captured kernel."""
     import hashlib
 
     try:
@@ -143,12 +162,16 @@ def _traffic(workload):
     except Exception:
         return None
     csrc = os.path.join(ROOT, "paper_1904_12759_gb300", "csrc")
-    for name, sha in rec.get("source_sha1", {}).items():
-        try:
+    try:
+        for name, sha in rec.get("source_sha1", {}).items():
             if hashlib.sha1(open(os.path.join(csrc, name), "rb").read()).hexdigest() != sha:
                 return None
-        except OSError:
-            return None
+        for name, (marker, sha) in rec.get("kernel_sha1", {}).items():
+            part = _prefix_through(open(os.path.join(csrc, name)).read(), marker)
+            if part is None or hashlib.sha1(part.encode()).hexdigest() != sha:
+                return None
+    except OSError:
+        return None
     return float(rec["dram_bytes_per_launch"])
 
 

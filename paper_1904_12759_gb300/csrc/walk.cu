@@ -645,11 +645,48 @@ __global__ void k_fill(int64_t n, double *x, double value) {
         x[i] = value;
 }
 
-// (mean, SE) of W -> (V mean, V SE)
-__global__ void k_scale_tc(const double *Vp, double *tc, double *sem) {
-    const double V = *Vp;
-    *tc *= V;
-    if (sem) *sem *= V;
+// All warp partials of a TC call merged by one block: the common shift (max),
+// then the rescaled sums in a fixed thread-strided order and tree; the result
+// (V mean, V SE) with V = *Vp.
+__global__ void __launch_bounds__(WALK_THREADS) k_reduce_tc(const Partial *__restrict__ part, uint32_t np, double M,
+                                                            const double *Vp, double *tc, double *sem,
+                                                            uint32_t *status) {
+    __shared__ double sh[WARPS_PER_BLOCK][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double m = -INFINITY;
+    for (uint32_t c = threadIdx.x; c < np; c += WALK_THREADS) m = fmax(m, part[c].m);
+    m = warp_max(m);
+    if (lane == 0) sh[warp][0] = m;
+    __syncthreads();
+    m = -INFINITY;
+    for (int w = 0; w < WARPS_PER_BLOCK; ++w) m = fmax(m, sh[w][0]);
+    __syncthreads();
+    double s1 = 0.0, s2 = 0.0;
+    for (uint32_t c = threadIdx.x; c < np; c += WALK_THREADS) {
+        const Partial q = part[c];
+        const double sc = q.m == -INFINITY ? 0.0 : exp(q.m - m);
+        s1 += sc * q.s1;
+        s2 += sc * sc * q.s2;
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if (lane == 0) {
+        sh[warp][0] = s1;
+        sh[warp][1] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < WARPS_PER_BLOCK; ++w) {
+            a += sh[w][0];
+            b += sh[w][1];
+        }
+        double mean, se;
+        finish_entry(a, b, m, M, &mean, &se, status);
+        const double V = *Vp;
+        *tc = V * mean;
+        if (sem) *sem = V * se;
+    }
 }
 
 // x_i = (sum of V W 1{end = i}) / M and its standard error.
@@ -1039,10 +1076,8 @@ cudaError_t launch_total_communicability(mcx_plan *plan, double t, int mode, int
         if (wgt) launch_tc_kernel<false, true>(mode, grid, p, f, st); else launch_tc_kernel<false, false>(mode, grid, p, f, st);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // all warp partials in chunk order, as one entry
-    k_reduce_chunks<<<1, WALK_THREADS, 0, st>>>(p.partials, 1, (uint32_t)n_warps, (double)paths, tc, sem,
-                                                 plan->status);
-    k_scale_tc<<<1, 1, 0, st>>>(fs.V, tc, sem);
+    k_reduce_tc<<<1, WALK_THREADS, 0, st>>>(p.partials, (uint32_t)n_warps, (double)paths, fs.V, tc, sem,
+                                             plan->status);
     return cudaGetLastError();
 }
 
