@@ -930,6 +930,8 @@ struct mcx_mlp {
     float *grad = nullptr;    // [NPARAM + 1] (last: loss)
     float *part = nullptr;
     int64_t part_blocks = 0;
+    float *losses = nullptr;  // per-minibatch losses of one epoch (device)
+    int64_t losses_n = 0;
     int64_t *idx = nullptr;   // minibatch permutation
     int64_t idx_n = 0;
     int64_t step = 0;
@@ -1122,8 +1124,16 @@ mcx_status mcx_mlp_fit(mcx_mlp *m, int64_t n, const float *features, const float
         if ((e = cudaMalloc(&m->idx, sizeof(int64_t) * (size_t)n)) != cudaSuccess) return stat(e);
         m->idx_n = n;
     }
+    const int64_t steps = (n + batch - 1) / batch;  // minibatches per epoch
+    if (epoch_loss && m->losses_n < steps) {
+        cudaFree(m->losses);
+        m->losses = nullptr;
+        if ((e = cudaMalloc(&m->losses, sizeof(float) * (size_t)steps)) != cudaSuccess) return stat(e);
+        m->losses_n = steps;
+    }
     cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem());
     std::vector<int64_t> perm(n);
+    std::vector<float> hl(epoch_loss ? (size_t)steps : 0);
     uint64_t s = seed * 0xD1B54A32D192ED03ull + 1;
     for (int32_t ep = 0; ep < epochs; ++ep) {
         for (int64_t i = 0; i < n; ++i) perm[i] = i;
@@ -1148,15 +1158,18 @@ mcx_status mcx_mlp_fit(mcx_mlp *m, int64_t n, const float *features, const float
                                                                              view(m), 1.0f / (float)bn, m->part);
             k_grad_reduce<<<(NPARAM + 256) / 256, 256, 0, st>>>((int)blocks, m->part, m->grad, m->params, m->m1,
                                                                  m->m2, lr, b1c, b2c, 1);
-            if (epoch_loss) {
-                float l = 0.0f;
-                cudaMemcpyAsync(&l, m->grad + NPARAM, sizeof(float), cudaMemcpyDeviceToHost, st);
-                cudaStreamSynchronize(st);
-                eloss += l;
-                ++nb;
-            }
+            if (epoch_loss)  // kept on the device; read once per epoch
+                cudaMemcpyAsync(m->losses + nb, m->grad + NPARAM, sizeof(float), cudaMemcpyDeviceToDevice, st);
+            ++nb;
         }
-        if (epoch_loss) epoch_loss[ep] = (float)(eloss / (double)std::max<int64_t>(nb, 1));
+        if (epoch_loss) {
+            if ((e = cudaMemcpyAsync(hl.data(), m->losses, sizeof(float) * (size_t)nb, cudaMemcpyDeviceToHost, st)) !=
+                    cudaSuccess ||
+                (e = cudaStreamSynchronize(st)) != cudaSuccess)
+                return stat(e);
+            for (int64_t k = 0; k < nb; ++k) eloss += hl[k];
+            epoch_loss[ep] = (float)(eloss / (double)std::max<int64_t>(nb, 1));
+        }
         if ((e = cudaGetLastError()) != cudaSuccess) return stat(e);
     }
     return stat(cudaStreamSynchronize(st));
@@ -1172,6 +1185,7 @@ void mcx_mlp_destroy(mcx_mlp *m) {
     cudaFree(m->part);
     cudaFree(m->idx);
     cudaFree(m->err);
+    cudaFree(m->losses);
     delete m;
 }
 
