@@ -147,3 +147,68 @@ def test_bf16_hidden_forward_exact_cases():
     # one BF16 rounding of every hidden activation: |dy| <= 2^-9 |h1| |W2| |W3| (row sums)
     bound = 2.0 ** -9 * (np.abs(h1) @ np.abs(W["W2"]) @ np.abs(W["W3"]))[:, 0] + 1e-12
     assert np.all(np.abs(y1 - y0) <= bound) and np.any(y1 != y0)
+
+
+def test_features_and_taylor_terms_brute_force():
+    """Every feature column, the rates and the Taylor terms against per-node loops over
+    explicit neighbour lists and dense matrix powers on a small weighted graph with a
+    diagonal, a node without off-diagonal entries and a zero T2 (features divide by 1 there)."""
+    rng = np.random.default_rng(11)
+    n = 40
+    a = np.where(rng.random((n, n)) < 0.15, rng.lognormal(0, 0.7, (n, n)), 0.0)
+    a[5, :] = 0.0  # no positive off-diagonal entry: rate 0, no neighbours
+    np.fill_diagonal(a, rng.normal(0, 1, n))
+    csr = W.dense_to_csr(a)
+    v = rng.uniform(-1, 1, n)
+    v[5] = 0.0  # row 5 holds only its diagonal, so T2[5] = 0 exactly
+    t = 0.37
+    F, T2, T = CV.features(csr, v, t)
+    for k in range(4):
+        assert np.allclose(T[k], np.linalg.matrix_power(a, k) @ v, rtol=1e-12, atol=1e-13)
+    lam = np.array([sum(a[i, j] for j in range(n) if j != i and a[i, j] > 0) for i in range(n)])
+    assert np.allclose(CV.rates(csr)[0], lam, rtol=1e-14, atol=0)
+    for i in range(n):
+        nb = [lam[j] for j in range(n) if j != i and a[i, j] > 0]
+        mean = float(np.mean(nb)) if nb else 0.0
+        sd = float(np.sqrt(max(np.mean(np.square(nb)) - mean * mean, 0.0))) if nb else 0.0
+        t2 = v[i] + t * T[1][i] + t * t * T[2][i] / 2
+        t2s = t2 if t2 != 0 else 1.0
+        want = [math.log1p(lam[i]), math.log1p(mean), math.log1p(sd), t * T[1][i] / t2s, t * t * T[2][i] / (2 * t2s)]
+        assert np.allclose(F[i], want, rtol=1e-12, atol=1e-14), i
+        assert abs(T2[i] - t2) <= 1e-14 * (abs(t2) + 1)
+    assert T2[5] == 0.0 and np.all(F[5] == 0.0)
+
+
+def test_training_targets():
+    x = np.array([2.0, 1.0, -3.0, 1e-9, 5.0])
+    T2 = np.array([1.0, 4.0, 1.0, 1.0, 5.0])
+    y = CV.targets(x, T2)
+    assert np.allclose(y[[0, 1, 4]], [math.log(2.0), math.log(0.25), 0.0], rtol=1e-15)
+    assert y[2] == y[3] == math.log(1e-6)  # ratios clamped below at 1e-6
+
+
+def test_cv_coefficients_are_the_residual_of_h():
+    """For h(tau) = v + tau Av + tau^2 A^2 v/2 + c3 tau^3 with h(t) = xhat, the residual
+    A h(tau) - h'(tau) is a tau^2 + b tau^3 (the source term of the control variate),
+    checked with dense matrix powers and a central difference for h'."""
+    rng = np.random.default_rng(4)
+    n = 30
+    a = np.where(rng.random((n, n)) < 0.2, rng.uniform(0.1, 1.0, (n, n)), 0.0)
+    np.fill_diagonal(a, rng.normal(0, 0.5, n))
+    csr = W.dense_to_csr(a)
+    v = rng.uniform(0, 1, n)
+    t = 0.6
+    T = CV.taylor_terms(csr, v)
+    xhat = rng.uniform(0.5, 2.0, n)
+    c3, ca, cb = CV.cv_coefficients(csr, T, t, xhat)
+    P = [np.linalg.matrix_power(a, k) @ v for k in range(3)]
+
+    def h(tau):
+        return P[0] + tau * P[1] + tau * tau * P[2] / 2 + c3 * tau ** 3
+
+    assert np.allclose(h(t), xhat, rtol=1e-12)
+    for tau in (0.1, 0.35, 0.6):
+        eps = 1e-5
+        dh = (h(tau + eps) - h(tau - eps)) / (2 * eps)
+        r = a @ h(tau) - dh
+        assert np.allclose(r, ca * tau ** 2 + cb * tau ** 3, rtol=1e-7, atol=1e-7 * np.abs(r).max())
