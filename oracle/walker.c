@@ -27,7 +27,8 @@
  * path exactly): one Philox4x32-10 call per walker event, key = seed,
  * counter = {event k, entry i, path lo32, path hi32}.  Word 0 (and word 1 in
  * FP64) gives the holding-time uniform, word 2 the slot in the row, word 3 the
- * alias acceptance.
+ * alias acceptance.  The randomised-QMC estimator replaces words 0 and 2 of the
+ * first events by scrambled Sobol' coordinates (see below).
  */
 #include <math.h>
 #include <stdint.h>
@@ -280,6 +281,137 @@ int64_t oracle_count_offdiag(int64_t n, const int64_t *row_ptr, const int32_t *c
 }
 
 /* ------------------------------------------------------------------------ */
+/* Quasi-random draws for the first events of a path (randomised QMC, one of */
+/* the variance-reduction directions of Sec. 5).                             */
+/*                                                                           */
+/* Sobol' points (Sobol' 1967; Bratley & Fox 1988): coordinate d of point q  */
+/* is the XOR of the direction numbers V_d[b] over the set bits b of q.      */
+/* Dimension 0 takes V_0[b] = 2^(31-b) (van der Corput); dimension d >= 1    */
+/* takes a primitive polynomial x^s + a_1 x^(s-1) + ... + a_(s-1) x + 1 over */
+/* GF(2) and initial odd m_1..m_s (m_k < 2^k), continued by                  */
+/*   m_k = 2 a_1 m_(k-1) ^ 4 a_2 m_(k-2) ^ ... ^ 2^s m_(k-s) ^ m_(k-s),       */
+/* and V_d[k-1] = m_k 2^(32-k).  The (s, a, m) below are the first entries   */
+/* of Joe & Kuo's table (ACM TOMS 29, 2003; SIAM J. Sci. Comput. 30, 2008).  */
+/*                                                                           */
+/* Randomisation per replicate r: Matousek's (1998) random linear scramble, a */
+/* lower-triangular binary matrix L_(r,d) with unit diagonal (output bit b,   */
+/* counted from the most significant, depends on input bits 0..b), applied   */
+/* to the direction numbers, followed by a random digital shift e_(i,r,d)    */
+/* (XOR) per entry i.  Both keep the net structure; every point is uniform,  */
+/* so each replicate mean is unbiased and the spread of R independent         */
+/* replicate means gives the standard error.                                 */
+/*                                                                           */
+/* Draw schedule: event k < QMC_EVENTS of point q of replicate r takes its    */
+/* holding-time word (word 0) from dimension 2k and its slot word (word 2)   */
+/* from dimension 2k + 1; words 1 and 3 and all later events come from the   */
+/* path's Philox block, with path index r 2^m + q.  Row b of L_(r,d) is word */
+/* 0 of Philox counter {b, 0xFFFFFFFC, d, r} (bits above b kept, bit b set);  */
+/* e_(i,r,d) is word 0 of counter {d, 0xFFFFFFFD, i, r}.                      */
+/* ------------------------------------------------------------------------ */
+#define QMC_DIMS 16
+#define QMC_EVENTS (QMC_DIMS / 2)
+#define QMC_MAX_LOG2 24
+
+static const struct {
+    int s, a;
+    uint32_t m[6];
+} sobol_par[QMC_DIMS - 1] = {
+    {1, 0, {1}},           {2, 1, {1, 3}},          {3, 1, {1, 3, 1}},         {3, 2, {1, 1, 1}},
+    {4, 1, {1, 1, 3, 3}},  {4, 4, {1, 3, 5, 13}},   {5, 2, {1, 1, 5, 5, 17}},  {5, 4, {1, 1, 5, 5, 5}},
+    {5, 7, {1, 1, 7, 11, 19}}, {5, 11, {1, 1, 5, 1, 1}}, {5, 13, {1, 1, 1, 3, 11}}, {5, 14, {1, 3, 5, 5, 31}},
+    {6, 1, {1, 3, 3, 9, 7, 49}}, {6, 13, {1, 1, 1, 15, 21, 21}}, {6, 16, {1, 3, 1, 13, 27, 49}},
+};
+
+int oracle_qmc_dims(void) { return QMC_DIMS; }
+
+/* Primitive-polynomial parameters of dimension d >= 1 (degree, coefficient bits). */
+void oracle_sobol_poly(int d, int *s, int *a)
+{
+    *s = sobol_par[d - 1].s;
+    *a = sobol_par[d - 1].a;
+}
+
+/* Unscrambled direction numbers V[d][b], d < QMC_DIMS, b < 32. */
+void oracle_sobol_directions(uint32_t V[QMC_DIMS][32])
+{
+    for (int b = 0; b < 32; ++b) V[0][b] = 1u << (31 - b);
+    for (int d = 1; d < QMC_DIMS; ++d) {
+        int s = sobol_par[d - 1].s, a = sobol_par[d - 1].a;
+        uint64_t m[33];
+        for (int k = 1; k <= s; ++k) m[k] = sobol_par[d - 1].m[k - 1];
+        for (int k = s + 1; k <= 32; ++k) {
+            uint64_t x = (m[k - s] << s) ^ m[k - s];
+            for (int c = 1; c < s; ++c)
+                if ((a >> (s - 1 - c)) & 1) x ^= m[k - c] << c;
+            m[k] = x;
+        }
+        for (int k = 1; k <= 32; ++k) V[d][k - 1] = (uint32_t)(m[k] << (32 - k));
+    }
+}
+
+/* Coordinate of point q from 32 direction numbers. */
+uint32_t oracle_sobol_point(const uint32_t *Vd, uint32_t q)
+{
+    uint32_t x = 0;
+    for (int b = 0; q != 0; ++b, q >>= 1)
+        if (q & 1u) x ^= Vd[b];
+    return x;
+}
+
+static uint32_t parity32(uint32_t x)
+{
+    uint32_t p = 0;
+    while (x) {
+        p ^= 1u;
+        x &= x - 1u;
+    }
+    return p;
+}
+
+/* Apply L_(r,d) to a 32-bit word. */
+static uint32_t lms_apply(uint64_t seed, uint32_t r, uint32_t d, uint32_t x)
+{
+    uint32_t y = 0;
+    for (uint32_t b = 0; b < 32; ++b) {
+        uint32_t w[4];
+        draw(seed, b, 0xFFFFFFFCu, ((uint64_t)r << 32) | d, w);
+        uint32_t above = b == 0 ? 0u : (0xFFFFFFFFu << (32 - b));
+        uint32_t row = (w[0] & above) | (1u << (31 - b));
+        y |= parity32(row & x) << (31 - b);
+    }
+    return y;
+}
+
+/* Scrambled direction numbers of replicate r: out[d][b] = L_(r,d) V[d][b], b < 32. */
+void oracle_qmc_scrambled(uint64_t seed, uint32_t r, uint32_t out[QMC_DIMS][32])
+{
+    uint32_t V[QMC_DIMS][32];
+    oracle_sobol_directions(V);
+    for (uint32_t d = 0; d < QMC_DIMS; ++d)
+        for (int b = 0; b < 32; ++b) out[d][b] = lms_apply(seed, r, d, V[d][b]);
+}
+
+uint32_t oracle_qmc_shift(uint64_t seed, int32_t entry, uint32_t r, uint32_t d)
+{
+    uint32_t w[4];
+    draw(seed, d, 0xFFFFFFFDu, ((uint64_t)r << 32) | (uint32_t)entry, w);
+    return w[0];
+}
+
+typedef struct {
+    const uint32_t (*V)[32]; /* scrambled direction numbers of the replicate */
+    uint32_t e[QMC_DIMS];    /* digital shifts of (entry, replicate) */
+    uint32_t q;              /* point index within the replicate */
+} qmc_point;
+
+static void qmc_override(const qmc_point *qp, uint32_t k, uint32_t w[4])
+{
+    if (k >= QMC_EVENTS) return;
+    w[0] = oracle_sobol_point(qp->V[2 * k], qp->q) ^ qp->e[2 * k];
+    w[2] = oracle_sobol_point(qp->V[2 * k + 1], qp->q) ^ qp->e[2 * k + 1];
+}
+
+/* ------------------------------------------------------------------------ */
 /* One backward path (Algorithm 1 / Theorem 1, continuous-path reading).     */
 /* ------------------------------------------------------------------------ */
 typedef struct {
@@ -318,7 +450,8 @@ static int grid_count_f64(double rho, double invdt, int N)
     return c < N ? c : N;
 }
 
-static path_out path_f32(const oracle_graph *g, int32_t i, uint32_t stream, double t, int mode, int N, uint64_t seed, uint64_t p)
+static path_out path_f32(const oracle_graph *g, int32_t i, uint32_t stream, double t, int mode, int N, uint64_t seed, uint64_t p,
+                         const qmc_point *qp)
 {
     path_out o;
     int32_t j = i;
@@ -337,6 +470,7 @@ static path_out path_f32(const oracle_graph *g, int32_t i, uint32_t stream, doub
         }
         uint32_t w[4];
         draw(seed, k, stream, p, w);
+        if (qp) qmc_override(qp, k, w);
         float S = -oracle_logf(unif_f32(w[0])) * g->inv_rate32[j];
         if (S >= r) {
             if (mode == O_EXACT) acc = fmaf(dl, r, acc);
@@ -365,7 +499,8 @@ static path_out path_f32(const oracle_graph *g, int32_t i, uint32_t stream, doub
     return o;
 }
 
-static path_out path_f64(const oracle_graph *g, int32_t i, uint32_t stream, double t, int mode, int N, uint64_t seed, uint64_t p)
+static path_out path_f64(const oracle_graph *g, int32_t i, uint32_t stream, double t, int mode, int N, uint64_t seed, uint64_t p,
+                         const qmc_point *qp)
 {
     path_out o;
     int32_t j = i;
@@ -384,6 +519,7 @@ static path_out path_f64(const oracle_graph *g, int32_t i, uint32_t stream, doub
         }
         uint32_t w[4];
         draw(seed, k, stream, p, w);
+        if (qp) qmc_override(qp, k, w);
         double S = -oracle_log(unif_f64(w[0], w[1])) * g->inv_rate64[j];
         if (S >= r) {
             if (mode == O_EXACT) acc = fma(dl, r, acc);
@@ -419,7 +555,7 @@ static path_out one_path_stream(const oracle_graph *g, int32_t i, uint32_t strea
         path_out o = {i, 0, (FNV_OFFSET ^ (uint64_t)(uint32_t)i) * FNV_PRIME, 0.0};
         return o;
     }
-    return prec == 0 ? path_f32(g, i, stream, t, mode, N, seed, p) : path_f64(g, i, stream, t, mode, N, seed, p);
+    return prec == 0 ? path_f32(g, i, stream, t, mode, N, seed, p, NULL) : path_f64(g, i, stream, t, mode, N, seed, p, NULL);
 }
 
 /* Backward paths of entry i draw from stream word i. */
@@ -468,6 +604,86 @@ int oracle_estimate(const oracle_graph *g, const double *v, double t, int mode, 
     }
     if (jumps_out) *jumps_out = jumps;
     return O_OK;
+}
+
+/* Randomised QMC estimate: for each requested entry, R replicates of the     */
+/* 2^log2q points of the scrambled Sobol' set (quasi-random draws for events */
+/* 0..QMC_EVENTS-1, as described above); replicate mean mu_r = plain          */
+/* sequential FP64 sum of W v_{X_t} over its points / 2^log2q; the estimate  */
+/* is the mean of the mu_r and its standard error sqrt(s^2 / R) with s^2 the */
+/* unbiased sample variance of the mu_r (two passes).  rep_means (nullable)   */
+/* receives the mu_r, entry-major.                                            */
+static void qmc_replicate(uint64_t seed, int32_t i, uint32_t r, uint32_t V[QMC_DIMS][32], qmc_point *qp)
+{
+    oracle_qmc_scrambled(seed, r, V);
+    qp->V = (const uint32_t(*)[32])V;
+    for (uint32_t d = 0; d < QMC_DIMS; ++d) qp->e[d] = oracle_qmc_shift(seed, i, r, d);
+}
+
+static path_out qmc_path(const oracle_graph *g, int32_t i, double t, int mode, int N, int prec, uint64_t seed,
+                         uint32_t log2q, uint32_t r, const qmc_point *qp)
+{
+    uint64_t p = ((uint64_t)r << log2q) | qp->q;
+    if (t == 0.0) {
+        path_out o = {i, 0, (FNV_OFFSET ^ (uint64_t)(uint32_t)i) * FNV_PRIME, 0.0};
+        return o;
+    }
+    return prec == 0 ? path_f32(g, i, (uint32_t)i, t, mode, N, seed, p, qp)
+                     : path_f64(g, i, (uint32_t)i, t, mode, N, seed, p, qp);
+}
+
+int oracle_estimate_rqmc(const oracle_graph *g, const double *v, double t, int mode, int N, int prec,
+                         uint32_t log2q, uint32_t R, const int32_t *entries, int64_t n_entries, uint64_t seed,
+                         double *mean, double *sem, double *rep_means, uint64_t *jumps_out)
+{
+    if (log2q > QMC_MAX_LOG2 || R < 1) return O_E_INVALID;
+    uint64_t jumps = 0;
+    const uint32_t Q = 1u << log2q;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : jumps)
+    for (int64_t e = 0; e < n_entries; ++e) {
+        int32_t i = entries ? entries[e] : (int32_t)e;
+        double *mu = (double *)malloc(sizeof(double) * R);
+        uint32_t V[QMC_DIMS][32];
+        for (uint32_t r = 0; r < R; ++r) {
+            qmc_point qp;
+            qmc_replicate(seed, i, r, V, &qp);
+            double sum = 0.0;
+            for (uint32_t q = 0; q < Q; ++q) {
+                qp.q = q;
+                path_out o = qmc_path(g, i, t, mode, N, prec, seed, log2q, r, &qp);
+                sum += exp(o.logw) * v[o.end];
+                jumps += o.njumps;
+            }
+            mu[r] = sum / (double)Q;
+        }
+        double m = 0.0;
+        for (uint32_t r = 0; r < R; ++r) m += mu[r];
+        m /= (double)R;
+        double ss = 0.0;
+        for (uint32_t r = 0; r < R; ++r) ss += (mu[r] - m) * (mu[r] - m);
+        mean[e] = m;
+        sem[e] = R > 1 ? sqrt(ss / (double)(R - 1) / (double)R) : 0.0;
+        if (rep_means)
+            for (uint32_t r = 0; r < R; ++r) rep_means[(uint64_t)e * R + r] = mu[r];
+        free(mu);
+    }
+    if (jumps_out) *jumps_out = jumps;
+    return O_OK;
+}
+
+/* Per-path trace of points q0 .. q0+count-1 of replicate r of entry i. */
+void oracle_trace_rqmc(const oracle_graph *g, double t, int mode, int N, int prec, int32_t entry, uint64_t seed,
+                       uint32_t log2q, uint32_t r, uint32_t q0, uint32_t count, int32_t *end, uint32_t *njumps,
+                       uint64_t *hash, double *logw)
+{
+    uint32_t V[QMC_DIMS][32];
+    qmc_point qp;
+    qmc_replicate(seed, entry, r, V, &qp);
+    for (uint32_t c = 0; c < count; ++c) {
+        qp.q = q0 + c;
+        path_out o = qmc_path(g, entry, t, mode, N, prec, seed, log2q, r, &qp);
+        end[c] = o.end; njumps[c] = o.njumps; hash[c] = o.hash; logw[c] = o.logw;
+    }
 }
 
 /* ------------------------------------------------------------------------ */

@@ -82,6 +82,19 @@ def lib():
             L.oracle_estimate_cv.argtypes = [C.POINTER(_Graph), vp, vp, vp, dbl, u64, vp, i64, u64, u64, vp, vp]
             L.oracle_estimate_cv.restype = C.c_int
             L.oracle_num_threads.restype = C.c_int
+            L.oracle_qmc_dims.restype = C.c_int
+            L.oracle_sobol_poly.argtypes = [C.c_int, vp, vp]
+            L.oracle_sobol_directions.argtypes = [vp]
+            L.oracle_sobol_point.argtypes = [vp, u32]
+            L.oracle_sobol_point.restype = u32
+            L.oracle_qmc_scrambled.argtypes = [u64, u32, vp]
+            L.oracle_qmc_shift.argtypes = [u64, i32, u32, u32]
+            L.oracle_qmc_shift.restype = u32
+            L.oracle_estimate_rqmc.argtypes = [C.POINTER(_Graph), vp, dbl, C.c_int, C.c_int, C.c_int, u32, u32, vp,
+                                               i64, u64, vp, vp, vp, vp]
+            L.oracle_estimate_rqmc.restype = C.c_int
+            L.oracle_trace_rqmc.argtypes = [C.POINTER(_Graph), dbl, C.c_int, C.c_int, C.c_int, i32, u64, u32, u32,
+                                            u32, u32, vp, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -176,6 +189,37 @@ class Graph:
                                  int(seed), int(path_offset), _p(mean), _p(sem))
         return mean, sem
 
+    def estimate_rqmc(self, v, t, log2q, replicates, entries=None, seed=0, mode="exact", nsteps=1, prec="fp32"):
+        """Randomised-QMC estimate: per entry, the mean of `replicates` replicate means over
+        the 2^log2q scrambled Sobol' points, its standard error from their spread, and the
+        replicate means themselves [entries, replicates]."""
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        if entries is None:
+            ne, ent_p = self.n, None
+        else:
+            entries = np.ascontiguousarray(entries, dtype=np.int32)
+            ne, ent_p = entries.size, _p(entries)
+        mean = np.zeros(ne)
+        sem = np.zeros(ne)
+        reps = np.zeros((ne, int(replicates)))
+        jumps = np.zeros(1, np.uint64)
+        st = lib().oracle_estimate_rqmc(C.byref(self._g), _p(v), float(t), MODES[mode], int(nsteps), PRECS[prec],
+                                        int(log2q), int(replicates), ent_p, int(ne), int(seed), _p(mean), _p(sem),
+                                        _p(reps), _p(jumps))
+        if st != 0:
+            raise ValueError("invalid quasi-random set size")
+        return mean, sem, reps
+
+    def trace_rqmc(self, t, entry, seed, log2q, replicate, first_point, count, mode="exact", nsteps=1, prec="fp32"):
+        end = np.zeros(count, np.int32)
+        nj = np.zeros(count, np.uint32)
+        hs = np.zeros(count, np.uint64)
+        lw = np.zeros(count, np.float64)
+        lib().oracle_trace_rqmc(C.byref(self._g), float(t), MODES[mode], int(nsteps), PRECS[prec], int(entry),
+                                int(seed), int(log2q), int(replicate), int(first_point), int(count), _p(end),
+                                _p(nj), _p(hs), _p(lw))
+        return {"end": end, "njumps": nj, "hash": hs, "logw": lw}
+
     # -- forward form (Theorem 2, Algorithm 2); this graph must be that of A^T --
     def start_table(self, v):
         """Two-level alias tables for the start draw j ~ v/V (Lemma 2)."""
@@ -222,6 +266,48 @@ class Graph:
 def phi(k: int, z: float) -> float:
     """int_0^1 e^{zs} s^k ds (the oracle's evaluation)."""
     return float(lib().oracle_phi(int(k), float(z)))
+
+
+def qmc_dims() -> int:
+    return int(lib().oracle_qmc_dims())
+
+
+def sobol_poly(d: int):
+    """(degree, coefficient bits) of the primitive polynomial of Sobol' dimension d >= 1."""
+    s = np.zeros(1, np.int32)
+    a = np.zeros(1, np.int32)
+    lib().oracle_sobol_poly(int(d), _p(s), _p(a))
+    return int(s[0]), int(a[0])
+
+
+def sobol_directions() -> np.ndarray:
+    """Unscrambled direction numbers [dims, 32] (uint32)."""
+    V = np.zeros((qmc_dims(), 32), np.uint32)
+    lib().oracle_sobol_directions(_p(V))
+    return V
+
+
+def sobol_points(V, count: int) -> np.ndarray:
+    """Points 0..count-1 of every dimension of the direction-number array V: [count, dims] uint32."""
+    V = np.ascontiguousarray(V, dtype=np.uint32)
+    out = np.zeros((count, V.shape[0]), np.uint32)
+    L = lib()
+    for d in range(V.shape[0]):
+        row = np.ascontiguousarray(V[d])
+        for q in range(count):
+            out[q, d] = L.oracle_sobol_point(_p(row), q)
+    return out
+
+
+def qmc_scrambled(seed: int, replicate: int) -> np.ndarray:
+    """Direction numbers of one replicate after the random linear scramble: [dims, 32]."""
+    V = np.zeros((qmc_dims(), 32), np.uint32)
+    lib().oracle_qmc_scrambled(int(seed), int(replicate), _p(V))
+    return V
+
+
+def qmc_shift(seed: int, entry: int, replicate: int, dim: int) -> int:
+    return int(lib().oracle_qmc_shift(int(seed), int(entry), int(replicate), int(dim)))
 
 
 def num_threads() -> int:
