@@ -306,7 +306,7 @@ int64_t oracle_count_offdiag(int64_t n, const int64_t *row_ptr, const int32_t *c
 /* from dimension 2k + 1; words 1 and 3 and all later events come from the   */
 /* path's Philox block, with path index r 2^m + q.  Row b of L_(r,d) is word */
 /* 0 of Philox counter {b, 0xFFFFFFFC, d, r} (bits above b kept, bit b set);  */
-/* e_(i,r,d) is word 0 of counter {d, 0xFFFFFFFD, i, r}.                      */
+/* e_(i,r,d) is word d mod 4 of counter {d / 4, 0xFFFFFFFD, i, r}.            */
 /* ------------------------------------------------------------------------ */
 #define QMC_DIMS 16
 #define QMC_EVENTS (QMC_DIMS / 2)
@@ -394,8 +394,8 @@ void oracle_qmc_scrambled(uint64_t seed, uint32_t r, uint32_t out[QMC_DIMS][32])
 uint32_t oracle_qmc_shift(uint64_t seed, int32_t entry, uint32_t r, uint32_t d)
 {
     uint32_t w[4];
-    draw(seed, d, 0xFFFFFFFDu, ((uint64_t)r << 32) | (uint32_t)entry, w);
-    return w[0];
+    draw(seed, d / 4, 0xFFFFFFFDu, ((uint64_t)r << 32) | (uint32_t)entry, w);
+    return w[d % 4];
 }
 
 typedef struct {
