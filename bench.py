@@ -59,11 +59,12 @@ def _args():
     ap.add_argument("--generators", type=int, default=256, help="ctmc_batch: number of generators")
     ap.add_argument("--tune-cache", default=None, help="ctmc_batch: schedule cache file (JSON lines)")
     ap.add_argument("--workload", default="erdos_renyi",
-                    choices=["erdos_renyi", "ctmc_batch", "heat3d", "ba_cv", "tc", "splitting", "ranking"],
+                    choices=["erdos_renyi", "ctmc_batch", "heat3d", "ba_cv", "tc", "splitting", "ranking", "rqmc"],
                     help="erdos_renyi: the default line; ctmc_batch / heat3d / ba_cv / tc: the batched CTMC "
                          "transients, the 3D heat equation, the learned control variate's time to 1e-2 "
                          "error and the total communicability at the paper's settings; splitting / ranking: "
-                         "the splitting-error and sample-size study and the ranking similarities (own JSON lines)")
+                         "the splitting-error and sample-size study and the ranking similarities; rqmc: "
+                         "randomised quasi-Monte Carlo against plain Monte Carlo (own JSON lines)")
     return ap.parse_args()
 
 
@@ -438,13 +439,13 @@ def run_ba_cv(args):
 
     # ---- training (once) ----
     t_train0 = time.perf_counter()
-    e0 = ev()
+    graphs = [(W.barabasi_albert(10 ** 5, 5, seed), W.uniform_vector(10 ** 5, seed + 100)) for seed in range(1, 9)]
+    e0, e1, e2 = ev(), ev(), ev()
     e0.record()
     feats, tgts = [], []
-    for seed in range(1, 9):
-        csr = W.barabasi_albert(10 ** 5, 5, seed)
+    for seed, (csr, vh) in enumerate(graphs, start=1):
         rp, col, val = dev(csr)
-        vd = torch.as_tensor(W.uniform_vector(csr.n, seed + 100)).cuda()
+        vd = torch.as_tensor(vh).cuda()
         lam, _ = P.power_iteration(rp, col, val, max_iters=20000, tol=1e-9)
         t = 0.5 / lam
         plan = P.Plan(rp, col, val)
@@ -453,12 +454,13 @@ def run_ba_cv(args):
         feats.append(F)
         tgts.append(P.cv_targets(x, T, t))
         plan.close()
+    e1.record()
     net = P.MLP(seed=0)
     losses = net.fit(torch.cat(feats), torch.cat(tgts), epochs=30, batch=4096, lr=2e-3, seed=1)
-    e1 = ev()
-    e1.record()
+    e2.record()
     torch.cuda.synchronize()
-    train = {"graphs": 8, "n": 10 ** 5, "label_paths": 256, "epochs": 30, "gpu_ms": e0.elapsed_time(e1),
+    train = {"graphs": 8, "n": 10 ** 5, "label_paths": 256, "epochs": 30, "batch": 4096,
+             "labels_ms": e0.elapsed_time(e1), "fit_ms": e1.elapsed_time(e2),
              "wall_s": time.perf_counter() - t_train0, "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
     # ---- target graph ----
     csr = W.barabasi_albert(4 * 10 ** 6, 5, SEED)
@@ -525,6 +527,82 @@ def run_ba_cv(args):
     print(json.dumps(line), flush=True)
     plan.close()
     net.close()
+
+
+def run_rqmc(args):
+    """Randomised quasi-Monte Carlo against plain Monte Carlo on the default graph
+    (Erdos-Renyi n = 1e6, mean degree 10, beta = 1/lambda_max, v = 1, every entry):
+    relative L2 error against the FP64 Taylor oracle (computed outside the timed calls)
+    and GPU time per call, swept over M = 16, 32, ... paths per entry until the error
+    reaches 1e-3 (quasi-random: 16 replicates of M/16 scrambled Sobol' points); the
+    error's log-log slope in M and the GPU time to relative L2 errors 1e-2, 3e-3, 1e-3."""
+    import numpy as np
+    import torch
+
+    import paper_1904_12759_gb300 as P
+    import workloads as W
+    from oracle import dense as OD
+
+    torch.cuda.set_device(0)
+    csr = W.erdos_renyi(args.n, MEAN_DEGREE, SEED)
+    rp, col, val = (torch.as_tensor(a).cuda() for a in (csr.row_ptr, csr.col, csr.val))
+    lam, iters = P.power_iteration(rp, col, val, max_iters=1000, tol=1e-10)
+    beta = 1.0 / lam
+    x_ref = OD.taylor_expmv(csr.to_scipy(), beta, np.ones(csr.n), norm_bound=1.0)
+    xn = float(np.linalg.norm(x_ref))
+    plan = P.Plan(rp, col, val)
+    vd = torch.ones(csr.n, dtype=torch.float64, device="cuda")
+    out = (torch.empty(csr.n, dtype=torch.float64, device="cuda"), torch.empty(csr.n, dtype=torch.float64, device="cuda"))
+    R = 16
+
+    def run(method, M, seed):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if method == "plain":
+            m, s = plan.estimate(vd, beta, M, seed=seed, out=out)
+        else:
+            m, s = plan.estimate_rqmc(vd, beta, int(M // R).bit_length() - 1, R, seed=seed, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        mc = m.cpu().numpy()
+        return e0.elapsed_time(e1), float(np.linalg.norm(mc - x_ref)) / xn, float(s.mean().item())
+
+    for mth in ("plain", "rqmc"):
+        for _ in range(3):
+            run(mth, 64, 999)
+    results = {}
+    with ClockSampler(0) as clk:
+        for mth in ("plain", "rqmc"):
+            sweep = []
+            M = 16
+            while M <= (1 << 16):  # until the error reaches 1e-3 (and at least to M = 8192)
+                ms, err, se = run(mth, M, SEED + M)
+                sweep.append({"M": M, "ms": round(ms, 3), "rel_l2": err, "mean_sem": se})
+                if err <= 1e-3 and M >= (1 << 13):
+                    break
+                M *= 2
+            lm = np.log([r["M"] for r in sweep])
+            le = np.log([r["rel_l2"] for r in sweep])
+            res = {"sweep": sweep, "slope_log_err_vs_log_M": float(np.polyfit(lm, le, 1)[0])}
+            for eps in (1e-2, 3e-3, 1e-3):
+                hit = next((r for r in sweep if r["rel_l2"] <= eps), None)
+                res[f"time_to_{eps:g}_ms"] = hit["ms"] if hit else None
+                res[f"M_to_{eps:g}"] = hit["M"] if hit else None
+            results[mth] = res
+    Ms = [r["M"] for r in results["rqmc"]["sweep"]]
+    vr = [(p["rel_l2"] / q["rel_l2"]) ** 2 for p, q in zip(results["plain"]["sweep"], results["rqmc"]["sweep"])]
+    tq = results["rqmc"]["time_to_0.001_ms"]
+    tp = results["plain"]["time_to_0.001_ms"]
+    line = {"metric": "GPU time to 1e-3 relative L2 error, randomised QMC", "value": tq, "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "dtype": "f32 paths, f64 accumulation", "data": "synthetic",
+            "config": {"workload": "rqmc", "n": csr.n, "mean_degree": MEAN_DEGREE, "beta": "1/lambda_max",
+                       "lambda_max": lam, "v": "ones", "entries": "all", "replicates": R,
+                       "quasi_random_events": 8, "target": "relative L2 error vs FP64 Taylor oracle"},
+            "speedup_vs_plain": (tp / tq) if (tp and tq) else None,
+            "error_variance_ratio_plain_over_rqmc": {str(M): round(r, 2) for M, r in zip(Ms, vr)},
+            "results": results, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    plan.close()
 
 
 # the paper's single-core timings for TC at M = 1e6 paths, dt = 0.03125 (derived paths/s = M / time)
@@ -760,6 +838,9 @@ def main():
         return
     if args.workload == "ranking":
         run_ranking(args)
+        return
+    if args.workload == "rqmc":
+        run_rqmc(args)
         return
     import numpy as np
     import torch

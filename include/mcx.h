@@ -245,6 +245,45 @@ mcx_status mcx_estimate_noalloc(mcx_plan *plan, const double *v, double t, int f
                                 uint64_t seed, uint64_t path_offset, int precision, double *mean, double *sem,
                                 void *stream);
 
+/* Largest log2 of the points per replicate of mcx_estimate_rqmc. */
+#define MCX_QMC_MAX_LOG2 24
+/* Sobol' dimensions of mcx_estimate_rqmc: holding time and slot of the first 8 events. */
+#define MCX_QMC_DIMS 16
+
+/*
+ * Randomised quasi-Monte Carlo backward estimate (the walker of mcx_estimate
+ * with quasi-random draws; variance reduction, Sec. 5).  For each requested
+ * entry, `replicates` independent randomisations of the first
+ * 2^log2_points points of a Sobol' sequence drive the paths: event k < 8 of
+ * point q takes its holding-time uniform from Sobol' dimension 2k and its
+ * slot uniform from dimension 2k + 1; later events, the FP64 low bits and
+ * the alias acceptance keep the path's Philox draws (path index
+ * r 2^log2_points + q for replicate r).  Each replicate scrambles the direction
+ * numbers with a random lower-triangular binary matrix (Matousek's linear
+ * scramble, one per replicate and dimension) and XORs a random digital shift
+ * (one per entry, replicate and dimension); the Sobol' parameters are the
+ * first entries of Joe and Kuo's table.  Every path is an exact sample of the
+ * chain, so each replicate mean mu_r of W v_{X_t} is unbiased.
+ *   v, t, functional, nsteps, entries, n_entries, seed, precision
+ *                    as for mcx_estimate
+ *   log2_points      points per replicate 2^log2_points, 0 <= log2_points <=
+ *                    MCX_QMC_MAX_LOG2 (0: one point, a plain Monte Carlo draw)
+ *   replicates       1 <= R <= 2^16 (R >= 2 for a standard error); paths per
+ *                    entry are R 2^log2_points, at most 2^40
+ *   mean             float64 [n_entries] output: the mean of the mu_r
+ *   sem              float64 [n_entries] output, or NULL: sqrt(s^2 / R) with
+ *                    s^2 the unbiased sample variance of the mu_r (0 if R = 1)
+ * Device scratch of R * 16 * ceil(log2_points / 5) * 32 uint32 (digit tables
+ * of the scrambled points) and, when n_entries * R < 77824, n_entries * R *
+ * slices double pairs comes from the library's memory pool, stream-ordered.  The plan's copy of v is overwritten
+ * as in mcx_estimate.  An invalid entry yields NaN and MCX_E_INVALID at
+ * mcx_sync; a non-finite result sets the overflow flag.
+ * Errors: MCX_E_INVALID, MCX_E_CUDA, MCX_E_OOM.
+ */
+mcx_status mcx_estimate_rqmc(mcx_plan *plan, const double *v, double t, int functional, int32_t nsteps,
+                             uint32_t log2_points, uint32_t replicates, const int32_t *entries, int64_t n_entries,
+                             uint64_t seed, int precision, double *mean, double *sem, void *stream);
+
 /*
  * Per-path record of `count` backward paths of one entry (for parity checks
  * against an independent implementation of the same draw schedule):

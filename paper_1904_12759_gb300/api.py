@@ -104,6 +104,35 @@ class Plan:
               "mcx_estimate")
         return mean, sem
 
+    def estimate_rqmc(self, v: torch.Tensor, t: float, log2_points: int, replicates: int,
+                      entries: torch.Tensor | None = None, seed: int = 0, mode: str = "exact", nsteps: int = 1,
+                      prec: str = "fp32", out: tuple | None = None, stream=None):
+        """Randomised quasi-Monte Carlo estimate of (exp(tA)v)_i: `replicates` scrambled
+        Sobol' sets of 2^log2_points points drive the first events of the paths.
+
+        Returns (mean, sem) float64 CUDA tensors; sem comes from the spread of the
+        replicate means.
+        """
+        L = _lib.load()
+        p_v = _dev(v, torch.float64, "v")
+        if v.numel() != self.n:
+            raise ValueError("v must have n entries")
+        if entries is None:
+            ne, p_e = self.n, 0
+        else:
+            ne, p_e = entries.numel(), _dev(entries, torch.int32, "entries")
+        if out is None:
+            mean = torch.empty(ne, dtype=torch.float64, device=v.device)
+            sem = torch.empty(ne, dtype=torch.float64, device=v.device)
+        else:
+            mean, sem = out
+        p_sem = _dev(sem, torch.float64, "sem") if sem is not None else 0
+        check(L.mcx_estimate_rqmc(self._h, C.c_void_p(p_v), float(t), FUNCTIONALS[mode], int(nsteps),
+                                  int(log2_points), int(replicates), C.c_void_p(p_e), int(ne), int(seed),
+                                  PRECISIONS[prec], C.c_void_p(_dev(mean, torch.float64, "mean")),
+                                  C.c_void_p(p_sem), _stream(stream)), "mcx_estimate_rqmc")
+        return mean, sem
+
     def trace(self, t: float, entry: int, seed: int, first_path: int, count: int, mode: str = "exact",
               nsteps: int = 1, prec: str = "fp32", device="cuda", stream=None) -> dict:
         """Per-path end index, jump count, index hash and log-weight (for parity checks)."""

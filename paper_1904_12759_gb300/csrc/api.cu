@@ -200,6 +200,47 @@ mcx_status mcx_estimate(mcx_plan *p, const double *v, double t, int functional, 
     return from_cuda(launch_estimate(p, a, st));
 }
 
+mcx_status mcx_estimate_rqmc(mcx_plan *p, const double *v, double t, int functional, int32_t nsteps,
+                             uint32_t log2_points, uint32_t replicates, const int32_t *entries, int64_t n_entries,
+                             uint64_t seed, int precision, double *mean, double *sem, void *stream) {
+    mcx_status rc = check_common(p, t, functional, nsteps, precision);
+    if (rc != MCX_OK) return rc;
+    if (n_entries == 0) return MCX_OK;
+    if (!v || n_entries < 0 || !mean || replicates < 1 || replicates > (1u << 16) || log2_points > MCX_QMC_MAX_LOG2)
+        return MCX_E_INVALID;
+    if (!entries && n_entries != p->n) return MCX_E_INVALID;
+    if (((uint64_t)replicates << log2_points) > (1ull << 40)) return MCX_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_pack_v(p, v, st);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (t == 0.0) {  // exp(0 A) v = v: the plain estimator's copy path
+        EstimateArgs a{};
+        a.entries = entries;
+        a.n_entries = n_entries;
+        a.paths = 1;
+        a.t = 0.0;
+        a.mode = functional;
+        a.nsteps = nsteps;
+        a.precision = precision;
+        a.mean = mean;
+        a.sem = sem;
+        return from_cuda(launch_estimate(p, a, st));
+    }
+    RqmcArgs a{};
+    a.entries = entries;
+    a.n_entries = n_entries;
+    a.log2q = log2_points;
+    a.replicates = replicates;
+    a.t = t;
+    a.mode = functional;
+    a.nsteps = nsteps;
+    a.precision = precision;
+    a.seed = seed;
+    a.mean = mean;
+    a.sem = sem;
+    return from_cuda(launch_estimate_rqmc(p, a, st));
+}
+
 mcx_status mcx_estimate_noalloc(mcx_plan *p, const double *v, double t, int functional, int32_t nsteps,
                                 uint64_t paths_per_entry, const int32_t *entries, int64_t n_entries, uint64_t seed,
                                 uint64_t path_offset, int precision, double *mean, double *sem, void *stream) {

@@ -385,13 +385,7 @@ cudaError_t capture(mcx_batch *b, cudaStream_t st) {
 }
 
 cudaError_t run_graph(mcx_batch *b, uint64_t seed, cudaStream_t st) {
-    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    for (int r = 0; r < 10; ++r) {
-        b->wp.rk0[r] = k0;
-        b->wp.rk1[r] = k1;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
+    set_round_keys(b->wp, seed);
     void *args[] = {&b->wp, &b->ba};
     cudaKernelNodeParams kp;
     cudaError_t e = cudaGraphKernelNodeGetParams(b->walk_node, &kp);

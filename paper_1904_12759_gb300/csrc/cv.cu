@@ -44,6 +44,9 @@ constexpr int P_W3 = P_B2 + HID;
 constexpr int P_B3 = P_W3 + HID;
 constexpr int NPARAM = P_B3 + 1;  // 4609
 constexpr int GRAD_SAMPLES = 64;  // samples per gradient block (one per thread)
+// Row stride of the per-sample activation arrays in shared memory: one float of
+// padding puts the rows of a warp's samples in distinct banks.
+constexpr int HS = HID + 1;
 
 // ---------------------------------------------------------------------------
 // Taylor terms and features
@@ -427,11 +430,11 @@ __global__ void __launch_bounds__(GRAD_SAMPLES) k_mlp_grad(int64_t n, const floa
     extern __shared__ float sm[];
     float *s = sm;                          // NPARAM weights (+3 pad)
     float *X = s + NPARAM + 3;              // [64][NF] standardised inputs
-    float *H1 = X + GRAD_SAMPLES * NF;      // [64][HID]
-    float *H2 = H1 + GRAD_SAMPLES * HID;    // [64][HID]
-    float *D2 = H2 + GRAD_SAMPLES * HID;    // [64][HID]
-    float *D1 = D2 + GRAD_SAMPLES * HID;    // [64][HID]
-    float *DY = D1 + GRAD_SAMPLES * HID;    // [64]
+    float *H1 = X + GRAD_SAMPLES * NF;      // [64][HS]
+    float *H2 = H1 + GRAD_SAMPLES * HS;     // [64][HS]
+    float *D2 = H2 + GRAD_SAMPLES * HS;     // [64][HS]
+    float *D1 = D2 + GRAD_SAMPLES * HS;     // [64][HS]
+    float *DY = D1 + GRAD_SAMPLES * HS;     // [64]
     float *LS = DY + GRAD_SAMPLES;          // [64] squared residuals
     load_params(m.params, s);
     const int tid = threadIdx.x;
@@ -452,7 +455,7 @@ __global__ void __launch_bounds__(GRAD_SAMPLES) k_mlp_grad(int64_t n, const floa
         float a = s[P_B1 + j];
 #pragma unroll
         for (int q = 0; q < NF; ++q) a = fmaf(x[q], s[P_W1 + q * HID + j], a);
-        H1[tid * HID + j] = fmaxf(a, 0.0f);
+        H1[tid * HS + j] = fmaxf(a, 0.0f);
     }
     float y = s[P_B3];
     for (int kc = 0; kc < HID; kc += 16) {
@@ -460,14 +463,14 @@ __global__ void __launch_bounds__(GRAD_SAMPLES) k_mlp_grad(int64_t n, const floa
 #pragma unroll
         for (int k = 0; k < 16; ++k) acc[k] = s[P_B2 + kc + k];
         for (int j = 0; j < HID; ++j) {
-            const float hj = H1[tid * HID + j];
+            const float hj = H1[tid * HS + j];
 #pragma unroll
             for (int k = 0; k < 16; ++k) acc[k] = fmaf(hj, s[P_W2 + j * HID + kc + k], acc[k]);
         }
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-            H2[tid * HID + kc + k] = fmaxf(acc[k], 0.0f);
-            D2[tid * HID + kc + k] = acc[k] > 0.0f ? 1.0f : 0.0f;  // mask, scaled below
+            H2[tid * HS + kc + k] = fmaxf(acc[k], 0.0f);
+            D2[tid * HS + kc + k] = acc[k] > 0.0f ? 1.0f : 0.0f;  // mask, scaled below
             y = fmaf(fmaxf(acc[k], 0.0f), s[P_W3 + kc + k], y);
         }
     }
@@ -475,36 +478,36 @@ __global__ void __launch_bounds__(GRAD_SAMPLES) k_mlp_grad(int64_t n, const floa
     const float dy = 2.0f * r * inv_batch;
     DY[tid] = dy;
     LS[tid] = r * r;
-    for (int k = 0; k < HID; ++k) D2[tid * HID + k] *= dy * s[P_W3 + k];
+    for (int k = 0; k < HID; ++k) D2[tid * HS + k] *= dy * s[P_W3 + k];
     // d1 = (W2 d2) masked by h1 > 0
     for (int j = 0; j < HID; ++j) {
         float a = 0.0f;
 #pragma unroll 8
-        for (int k = 0; k < HID; ++k) a = fmaf(s[P_W2 + j * HID + k], D2[tid * HID + k], a);
-        D1[tid * HID + j] = H1[tid * HID + j] > 0.0f ? a : 0.0f;
+        for (int k = 0; k < HID; ++k) a = fmaf(s[P_W2 + j * HID + k], D2[tid * HS + k], a);
+        D1[tid * HS + j] = H1[tid * HS + j] > 0.0f ? a : 0.0f;
     }
     __syncthreads();
     float *out = part + (int64_t)blockIdx.x * (NPARAM + 1);
     for (int e = tid; e < HID * HID; e += GRAD_SAMPLES) {  // W2[j][k] = sum_s h1[s][j] d2[s][k]
         const int j = e / HID, k = e % HID;
         float a = 0.0f;
-        for (int q = 0; q < GRAD_SAMPLES; ++q) a = fmaf(H1[q * HID + j], D2[q * HID + k], a);
+        for (int q = 0; q < GRAD_SAMPLES; ++q) a = fmaf(H1[q * HS + j], D2[q * HS + k], a);
         out[P_W2 + e] = a;
     }
     {
         const int k = tid;  // one hidden unit per thread
         float gb2 = 0.0f, gb1 = 0.0f, gw3 = 0.0f;
         for (int q = 0; q < GRAD_SAMPLES; ++q) {
-            gb2 += D2[q * HID + k];
-            gb1 += D1[q * HID + k];
-            gw3 = fmaf(H2[q * HID + k], DY[q], gw3);
+            gb2 += D2[q * HS + k];
+            gb1 += D1[q * HS + k];
+            gw3 = fmaf(H2[q * HS + k], DY[q], gw3);
         }
         out[P_B2 + k] = gb2;
         out[P_B1 + k] = gb1;
         out[P_W3 + k] = gw3;
         for (int f = 0; f < NF; ++f) {
             float a = 0.0f;
-            for (int q = 0; q < GRAD_SAMPLES; ++q) a = fmaf(X[q * NF + f], D1[q * HID + k], a);
+            for (int q = 0; q < GRAD_SAMPLES; ++q) a = fmaf(X[q * NF + f], D1[q * HS + k], a);
             out[P_W1 + f * HID + k] = a;
         }
     }
@@ -961,7 +964,7 @@ cudaError_t ensure_part(mcx_mlp *m, int64_t blocks) {
     return e;
 }
 
-size_t grad_smem() { return sizeof(float) * (NPARAM + 3 + GRAD_SAMPLES * NF + 4 * GRAD_SAMPLES * HID + 2 * GRAD_SAMPLES); }
+size_t grad_smem() { return sizeof(float) * (NPARAM + 3 + GRAD_SAMPLES * NF + 4 * GRAD_SAMPLES * HS + 2 * GRAD_SAMPLES); }
 
 }  // namespace
 
@@ -1229,13 +1232,7 @@ mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_
     p.t32 = (float)t;
     p.path_offset = path_offset;
     p.status = plan->status;
-    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    for (int r = 0; r < 10; ++r) {
-        p.rk0[r] = k0;
-        p.rk1[r] = k1;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
+    set_round_keys(p, seed);
     if (reinterpret_cast<uintptr_t>(coef) % 16 != 0) return MCX_E_INVALID;  // (a, b) pairs are read as double2
     const bool wgt = plan->weighted_rows > 0;
     if (paths <= LANE_MODE_MAX_PATHS) {  // few paths per entry: one lane per entry

@@ -246,6 +246,21 @@ struct EstimateArgs {
     double *sem;
 };
 cudaError_t launch_estimate(mcx_plan *plan, const EstimateArgs &a, cudaStream_t st);
+struct RqmcArgs {
+    const int32_t *entries;
+    int64_t n_entries;
+    uint32_t log2q;
+    uint32_t replicates;
+    double t;
+    int mode;
+    int nsteps;
+    int precision;
+    uint64_t seed;
+    double *mean;
+    double *sem;
+};
+// Randomised-QMC estimate (v already packed into the node records).
+cudaError_t launch_estimate_rqmc(mcx_plan *plan, const RqmcArgs &a, cudaStream_t st);
 cudaError_t launch_estimate_noalloc(mcx_plan *plan, const double *v, const EstimateArgs &a, cudaStream_t st,
                                     bool *too_large);
 uint64_t noalloc_max_partials();

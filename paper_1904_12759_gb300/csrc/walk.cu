@@ -35,120 +35,11 @@
 #include <mutex>
 #include <type_traits>
 
+#include "accum.cuh"
 #include "walker.cuh"
 
 namespace mcx {
 namespace {
-
-// ---------------------------------------------------------------------------
-// Lane accumulators and their warp merges (result in lane 0).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void kahan_add(float &s, float &c, float x) {
-    const float y = __fsub_rn(x, c);
-    const float t = __fadd_rn(s, y);
-    c = __fsub_rn(__fsub_rn(t, s), y);
-    s = t;
-}
-
-// (h, l) += (h2, l2) for unevaluated float pairs: TwoSum of the high parts, then renormalise.
-__device__ __forceinline__ void pair_add(float &h, float &l, float h2, float l2) {
-    const float s = __fadd_rn(h, h2);
-    const float bp = __fsub_rn(s, h);
-    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(h2, bp));
-    const float lo = __fadd_rn(__fadd_rn(l, l2), e);
-    h = __fadd_rn(s, lo);
-    l = __fsub_rn(lo, __fsub_rn(h, s));
-}
-
-// Sum of w: compensated (it is the estimate).  Sum of w^2: plain FP32 fma
-// (it only feeds the standard error; ~31 terms per lane keep it within 1e-5).
-struct Acc32 {
-    float m = -INFINITY, s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
-    __device__ __forceinline__ void add(float L, float v) {
-        if (!(L <= m + 8.0f)) {  // first path, a new larger weight, or a non-finite one
-            const float sc = (m == -INFINITY) ? 0.0f : expf(m - L);
-            s1 *= sc; c1 *= sc; s2 *= sc * sc;
-            m = L;
-        }
-        const float wv = __fmul_rn(expf(__fsub_rn(L, m)), v);
-        kahan_add(s1, c1, wv);
-        s2 = __fmaf_rn(wv, wv, s2);
-    }
-    __device__ __forceinline__ void lane_result(double &S1, double &S2, double &Mw) const {
-        S1 = (double)s1 - (double)c1;
-        S2 = (double)s2;
-        Mw = (double)m;
-    }
-    __device__ __forceinline__ void warp_merge(double &S1, double &S2, double &Mw) const {
-        float mw = m;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
-        const float sc = (m == -INFINITY) ? 0.0f : expf(__fsub_rn(m, mw));
-        const float sc2 = __fmul_rn(sc, sc);
-        float h1 = __fmul_rn(s1, sc), l1 = __fmul_rn(-c1, sc);
-        float h2 = __fmul_rn(s2, sc2), l2 = __fmul_rn(-c2, sc2);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            pair_add(h1, l1, __shfl_xor_sync(0xffffffffu, h1, o), __shfl_xor_sync(0xffffffffu, l1, o));
-            pair_add(h2, l2, __shfl_xor_sync(0xffffffffu, h2, o), __shfl_xor_sync(0xffffffffu, l2, o));
-        }
-        S1 = (double)h1 + (double)l1;
-        S2 = (double)h2 + (double)l2;
-        Mw = (double)mw;
-    }
-};
-
-__device__ __forceinline__ double warp_max(double x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-    return x;
-}
-__device__ __forceinline__ double warp_sum(double x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
-struct Acc64 {
-    double m = -INFINITY, s1 = 0.0, s2 = 0.0;
-    __device__ __forceinline__ void add(double L, double v) {
-        if (!(L <= m + 64.0)) {
-            const double sc = (m == -INFINITY) ? 0.0 : exp(m - L);
-            s1 *= sc; s2 *= sc * sc;
-            m = L;
-        }
-        const double wv = __dmul_rn(exp(__dsub_rn(L, m)), v);
-        s1 = __dadd_rn(s1, wv);
-        s2 = __fma_rn(wv, wv, s2);
-    }
-    __device__ __forceinline__ void lane_result(double &S1, double &S2, double &Mw) const {
-        S1 = s1;
-        S2 = s2;
-        Mw = m;
-    }
-    __device__ __forceinline__ void warp_merge(double &S1, double &S2, double &Mw) const {
-        const double mw = warp_max(m);
-        const double sc = (m == -INFINITY) ? 0.0 : exp(m - mw);
-        S1 = warp_sum(sc * s1);
-        S2 = warp_sum(sc * sc * s2);
-        Mw = mw;
-    }
-};
-
-// mean and standard error from shifted sums over M paths
-__device__ __forceinline__ void finish_entry(double s1, double s2, double m, double M, double *mean, double *sem,
-                                             uint32_t *status) {
-    const double scale = exp(m);
-    const double mu = s1 / M;
-    double var = M > 1.0 ? (s2 - s1 * mu) / (M - 1.0) : 0.0;
-    if (var < 0.0) var = 0.0;
-    const double mv = scale * mu;
-    const double se = scale * sqrt(var / M);
-    *mean = mv;
-    if (sem) *sem = se;
-    if (!isfinite(mv) || !isfinite(se)) atomicOr(status, ST_OVERFLOW);
-}
-
 
 // ---------------------------------------------------------------------------
 // Estimate kernel: one warp per (entry, chunk); a block finishes its entries.
@@ -187,24 +78,7 @@ __global__ void __launch_bounds__(WALK_THREADS, F64 ? WALK_MIN_BLOCKS_F64 : WALK
         // stage the entry row (FP32 paths only; the FP64 path version reads global memory)
         const bool staged = !F64 && start.deg <= STAGE;
         if (lane == 0) sw.start = start;  // every path restarts from this copy
-        if (staged) {
-            for (int k = lane; k < start.deg; k += 32) {
-                const int32_t c = __ldg(a.edge_col + start.row_start + k);
-                sw.col[k] = c;
-                sw.rec[k] = load_node(a.node, c);
-            }
-            __syncwarp();
-            if (WEIGHTED && (start.flags & NODE_WEIGHTED)) {
-                for (int k = lane; k < start.deg; k += 32) {
-                    const Edge16 ed = a.edge16[start.row_start + k];
-                    int32_t s2 = k;
-                    for (int q = 0; q < start.deg; ++q)
-                        if (sw.col[q] == ed.alias_col) s2 = q;
-                    sw.aslot[k] = s2;
-                    sw.thresh[k] = ed.thresh;
-                }
-            }
-        }
+        if (staged) stage_row<WEIGHTED>(sw, a, start, lane);
         __syncwarp();
         const StageWarp *swp = staged ? &sw : nullptr;
         const T delta_start = Q::pot(start, a.node64, i);
@@ -781,31 +655,6 @@ cudaError_t launch_trace_mode(int mode, unsigned grid, const WalkParams &p, int3
     return cudaGetLastError();
 }
 
-WalkParams make_params(mcx_plan *plan, double t, int nsteps, uint64_t seed) {
-    WalkParams p{};
-    p.node = plan->node;
-    p.node64 = plan->node64;
-    p.edge_col = plan->edge_col;
-    p.edge16 = plan->edge16;
-    p.nsteps = nsteps;
-    p.t64 = t;
-    p.dt64 = t / (double)nsteps;
-    p.invdt64 = (double)nsteps / t;
-    p.t32 = (float)t;
-    p.dt32 = (float)p.dt64;
-    p.invdt32 = (float)p.invdt64;
-    p.n = plan->n;
-    p.max_events = 1u << 30;
-    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-    for (int r = 0; r < 10; ++r) {
-        p.rk0[r] = k0;
-        p.rk1[r] = k1;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    p.status = plan->status;
-    return p;
-}
 
 }  // namespace
 

@@ -1,9 +1,11 @@
-// Walker core shared by the estimate, forward and batch kernels: launch
-// parameters, Philox4x32-10 with precomputed round keys, the FP32/FP64
-// precision traits and the one-event step `advance` (Sec. 3, Eq. paths:
-// exponential holding time, stop at the horizon, jump by the row's table),
-// plus the final log-weight of each functional (Theorem 1; Eqs. deff and
-// eq_general1).  See walk.cu for the path arithmetic.
+// Walker core shared by the estimate, forward, quasi-random and batch
+// kernels: launch parameters (and their construction from a plan),
+// Philox4x32-10 with precomputed round keys, the staging of an entry row in
+// shared memory, the FP32/FP64 precision traits and the one-event step
+// `advance` / `advance_drawn` (Sec. 3, Eq. paths: exponential holding time,
+// stop at the horizon, jump by the row's table), plus the final log-weight of
+// each functional (Theorem 1; Eqs. deff and eq_general1).  See walk.cu for the
+// path arithmetic.
 #pragma once
 
 #include <math.h>
@@ -65,6 +67,62 @@ struct StageWarp {
     int32_t aslot[STAGE];        // alias rows: slot of the alias column
     uint32_t thresh[STAGE];      // alias rows: keep-own-column threshold
 };
+
+// Round keys of Philox4x32-10 for key = seed: the key words bumped by the
+// Weyl constants before each round.
+inline void set_round_keys(WalkParams &p, uint64_t seed) {
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        p.rk0[r] = k0;
+        p.rk1[r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// Walk parameters of a plan for horizon t, N grid steps and the given seed.
+inline WalkParams make_params(mcx_plan *plan, double t, int nsteps, uint64_t seed) {
+    WalkParams p{};
+    p.node = plan->node;
+    p.node64 = plan->node64;
+    p.edge_col = plan->edge_col;
+    p.edge16 = plan->edge16;
+    p.nsteps = nsteps;
+    p.t64 = t;
+    p.dt64 = t / (double)nsteps;
+    p.invdt64 = (double)nsteps / t;
+    p.t32 = (float)t;
+    p.dt32 = (float)p.dt64;
+    p.invdt32 = (float)p.invdt64;
+    p.n = plan->n;
+    p.max_events = 1u << 30;
+    set_round_keys(p, seed);
+    p.status = plan->status;
+    return p;
+}
+
+// Stage the row of an entry with record `start` (deg <= STAGE) into sw: its
+// kept columns, their node records and, for weighted rows, the alias slots and
+// thresholds.  Called by the whole warp; sw.start is set by the caller.
+template <bool WEIGHTED>
+__device__ __forceinline__ void stage_row(StageWarp &sw, const WalkParams &a, const NodeRec &start, int lane) {
+    for (int k = lane; k < start.deg; k += 32) {
+        const int32_t c = __ldg(a.edge_col + start.row_start + k);
+        sw.col[k] = c;
+        sw.rec[k] = load_node(a.node, c);
+    }
+    __syncwarp();
+    if (WEIGHTED && (start.flags & NODE_WEIGHTED)) {
+        for (int k = lane; k < start.deg; k += 32) {
+            const Edge16 ed = a.edge16[start.row_start + k];
+            int32_t s2 = k;
+            for (int q = 0; q < start.deg; ++q)
+                if (sw.col[q] == ed.alias_col) s2 = q;
+            sw.aslot[k] = s2;
+            sw.thresh[k] = ed.thresh;
+        }
+    }
+}
 
 // Philox4x32-10 with the ten round keys precomputed on the host.
 __device__ __forceinline__ uint4 philox_rk(uint4 c, const WalkParams &a) {
@@ -139,21 +197,21 @@ struct Walker {
     uint32_t k;   // event counter
 };
 
-// Advance one event.  Returns true when the path has ended (then w.acc holds
-// the final accumulated value with the last hold included).  With `sw` set,
-// jumps out of state `i0` read the staged row.
+// Advance one event with the event's draw `rnd` given (word 0: holding-time
+// uniform, with word 1 in FP64; word 2: slot; word 3: alias acceptance).
+// Returns true when the path has ended (then w.acc holds the final accumulated
+// value with the last hold included).  With `sw` set, jumps out of state `i0`
+// read the staged row.
 template <int MODE, bool WEIGHTED, bool F64>
-__device__ __forceinline__ bool advance(Walker<F64> &w, const WalkParams &a, uint32_t stream, uint64_t path,
-                                        const StageWarp *sw, int32_t i0,
-                                        typename P<F64>::T *hold = nullptr) {
+__device__ __forceinline__ bool advance_drawn(Walker<F64> &w, const WalkParams &a, uint4 rnd, const StageWarp *sw,
+                                              int32_t i0, typename P<F64>::T *hold = nullptr) {
     using Q = P<F64>;
     using T = typename Q::T;
     const T invdt = F64 ? (T)a.invdt64 : (T)a.invdt32;
     const int N = a.nsteps;
-    // the event's draw and -ln(u) do not depend on the state, so they are computed
-    // before the state's record (often still in flight from the last jump) is used;
-    // a state without jumps simply ignores them
-    const uint4 rnd = philox_rk(make_uint4(w.k, stream, (uint32_t)path, (uint32_t)(path >> 32)), a);
+    // -ln(u) does not depend on the state, so it is computed before the state's
+    // record (often still in flight from the last jump) is used; a state without
+    // jumps simply ignores it
     const T e = Q::neg_ln(Q::unif(rnd));
     if (w.rec.deg == 0 || w.k >= a.max_events) {
         if (w.rec.deg != 0) atomicOr(a.status, ST_OVERFLOW);  // event cap reached: result flagged
@@ -196,6 +254,15 @@ __device__ __forceinline__ bool advance(Walker<F64> &w, const WalkParams &a, uin
     w.delta = Q::pot(w.rec, a.node64, c);
     ++w.k;
     return false;
+}
+
+// Advance one event with the path's own Philox block {k, stream, path}.
+template <int MODE, bool WEIGHTED, bool F64>
+__device__ __forceinline__ bool advance(Walker<F64> &w, const WalkParams &a, uint32_t stream, uint64_t path,
+                                        const StageWarp *sw, int32_t i0,
+                                        typename P<F64>::T *hold = nullptr) {
+    const uint4 rnd = philox_rk(make_uint4(w.k, stream, (uint32_t)path, (uint32_t)(path >> 32)), a);
+    return advance_drawn<MODE, WEIGHTED, F64>(w, a, rnd, sw, i0, hold);
 }
 
 template <int MODE, bool F64>

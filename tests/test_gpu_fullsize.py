@@ -4,7 +4,8 @@ sampled outputs the oracle computes one by one (paths are a function of
 full-size run):
 
 * Erdos-Renyi n = 1e6, mean degree 10, beta = 1/lambda_max, v = 1, every entry
-  x 1000 paths (the default benchmark step): 24 sampled entries.
+  x 1000 paths (the default benchmark step): 24 sampled entries; the same graph
+  with 16 quasi-random replicates x 64 points per entry: 24 sampled entries.
 * 3D heat, 128^3 grid, 4096 entries x 1e6 paths: 2 sampled entries.
 * Barabasi-Albert n = 4e6 with the Taylor-only control variate, every entry x
   1 path (the control-variate benchmark at M = 1): 64 sampled entries.
@@ -58,6 +59,25 @@ def test_erdos_renyi_benchmark_step_sampled(mcx):
     scale = np.abs(om) + osem * math.sqrt(M)  # >= sum |W v| / M
     assert np.all(np.abs(gm - om) <= 2e-6 * scale), np.max(np.abs(gm - om) / scale)
     assert np.allclose(gs, osem, rtol=1e-3)
+    plan.close()
+
+
+def test_erdos_renyi_rqmc_sampled(mcx):
+    """The quasi-random study's launch at M = 1024 (16 replicates x 64 points) over
+    every entry: 24 sampled entries against the oracle on the same points."""
+    csr = W.erdos_renyi(10 ** 6, 10, 0)
+    rp, col, val = _dev(csr)
+    lam, _ = mcx.power_iteration(rp, col, val, max_iters=1000, tol=1e-10)
+    plan = mcx.Plan(rp, col, val)
+    v = torch.ones(csr.n, dtype=torch.float64, device="cuda")
+    mean, sem = plan.estimate_rqmc(v, 1.0 / lam, 6, 16, seed=13)
+    st = plan.sync()
+    assert st["status_bits"] == 0 and st["paths"] == csr.n * 1024
+    ent = W.random_entries(csr.n, 24, 5)
+    om, osem, _ = OW.Graph(csr).estimate_rqmc(np.ones(csr.n), 1.0 / lam, 6, 16, entries=ent, seed=13)
+    gm, gs = mean.cpu().numpy()[ent], sem.cpu().numpy()[ent]
+    assert np.all(np.abs(gm - om) <= 2e-6 * np.abs(om)), np.max(np.abs(gm - om) / np.abs(om))
+    assert np.all(np.abs(gs - osem) <= 1e-9 * osem + 4e-6 * np.abs(om))
     plan.close()
 
 
