@@ -93,6 +93,9 @@ def lib():
             L.oracle_estimate_rqmc.argtypes = [C.POINTER(_Graph), vp, dbl, C.c_int, C.c_int, C.c_int, u32, u32, vp,
                                                i64, u64, vp, vp, vp, vp]
             L.oracle_estimate_rqmc.restype = C.c_int
+            L.oracle_estimate_level_difference.argtypes = [C.POINTER(_Graph), vp, dbl, C.c_int, C.c_int, C.c_int,
+                                                           u64, vp, i64, u64, u64, vp, vp]
+            L.oracle_estimate_level_difference.restype = C.c_int
             L.oracle_trace_rqmc.argtypes = [C.POINTER(_Graph), dbl, C.c_int, C.c_int, C.c_int, i32, u64, u32, u32,
                                             u32, u32, vp, vp, vp, vp]
             _lib = L
@@ -209,6 +212,25 @@ class Graph:
         if st != 0:
             raise ValueError("invalid quasi-random set size")
         return mean, sem, reps
+
+    def estimate_level_difference(self, v, t, nsteps, paths, entries=None, seed=0, path_offset=0, mode="strang",
+                                  prec="fp32"):
+        """Multilevel difference: per entry the mean and standard error of
+        v_{X_t} (W_N - W_{N/2}) over the same paths (N = nsteps, even)."""
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        if entries is None:
+            ne, ent_p = self.n, None
+        else:
+            entries = np.ascontiguousarray(entries, dtype=np.int32)
+            ne, ent_p = entries.size, _p(entries)
+        mean = np.zeros(ne)
+        sem = np.zeros(ne)
+        st = lib().oracle_estimate_level_difference(C.byref(self._g), _p(v), float(t), MODES[mode], int(nsteps),
+                                                    PRECS[prec], int(paths), ent_p, int(ne), int(seed),
+                                                    int(path_offset), _p(mean), _p(sem))
+        if st != 0:
+            raise ValueError("level differences need STRANG or LIE with an even step count")
+        return mean, sem
 
     def trace_rqmc(self, t, entry, seed, log2q, replicate, first_point, count, mode="exact", nsteps=1, prec="fp32"):
         end = np.zeros(count, np.int32)
