@@ -59,12 +59,14 @@ def _args():
     ap.add_argument("--generators", type=int, default=256, help="ctmc_batch: number of generators")
     ap.add_argument("--tune-cache", default=None, help="ctmc_batch: schedule cache file (JSON lines)")
     ap.add_argument("--workload", default="erdos_renyi",
-                    choices=["erdos_renyi", "ctmc_batch", "heat3d", "ba_cv", "tc", "splitting", "ranking", "rqmc"],
+                    choices=["erdos_renyi", "ctmc_batch", "heat3d", "ba_cv", "tc", "splitting", "ranking", "rqmc",
+                             "mlmc"],
                     help="erdos_renyi: the default line; ctmc_batch / heat3d / ba_cv / tc: the batched CTMC "
                          "transients, the 3D heat equation, the learned control variate's time to 1e-2 "
                          "error and the total communicability at the paper's settings; splitting / ranking: "
                          "the splitting-error and sample-size study and the ranking similarities; rqmc: "
-                         "randomised quasi-Monte Carlo against plain Monte Carlo (own JSON lines)")
+                         "randomised quasi-Monte Carlo against plain Monte Carlo; mlmc: multilevel Monte Carlo "
+                         "over the time step (own JSON lines)")
     return ap.parse_args()
 
 
@@ -760,6 +762,90 @@ def run_splitting(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mlmc(args):
+    """Multilevel Monte Carlo over the time step (Giles 2008) for the STRANG functional on
+    the splitting study's graph (small-world n = 1000, beta = 1, v = 1, every entry),
+    target N_L = 64 steps from n0 = 2 (5 difference levels): per-level per-path variance
+    V_l and GPU cost C_l from pilot runs, Giles' allocation for a sampling error of 1e-4 of
+    the mean entry, the multilevel run against the dense Strang product, and beside it the
+    single-level STRANG estimate at N = 64 and the EXACT functional with the paths that
+    reach the same sampling error."""
+    import numpy as np
+    import torch
+
+    import paper_1904_12759_gb300 as P
+    import workloads as W
+    from oracle import dense as OD
+    from paper_1904_12759_gb300 import mlmc
+
+    torch.cuda.set_device(0)
+    n = 1000
+    csr = W.small_world(n, 1, 0.2, SEED)
+    a = csr.to_scipy().toarray()
+    ones = np.ones(n)
+    n0, L, t = 2, 5, 1.0
+    target = OD.split_expmv(a, t, n0 << L, ones, "strang")
+    exact = OD.expmv_dense(a, t, ones)
+    plan = P.Plan.from_csr(csr)
+    v = torch.ones(n, dtype=torch.float64, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+
+    def timed(fn):
+        e0, e1 = ev(), ev()
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    def level(lvl, M, seed):
+        if lvl == 0:
+            return plan.estimate(v, t, M, seed=seed, mode="strang", nsteps=n0)
+        return plan.estimate_level_difference(v, t, n0 << lvl, M, seed=seed, path_offset=lvl * mlmc.LEVEL_STRIDE,
+                                              mode="strang")
+
+    for lvl in range(L + 1):  # warm
+        level(lvl, 4096, 1)
+    pilot = 100000
+    V, C = [], []
+    with ClockSampler(0) as clk:
+        for lvl in range(L + 1):
+            (m, s), ms = timed(lambda: level(lvl, pilot, SEED + 11 * lvl))
+            V.append(float((s.cpu().numpy() ** 2).mean()) * pilot)
+            C.append(ms / (n * pilot))
+        eps = 1e-4 * float(np.abs(target).mean())
+        Ms = mlmc.allocation(V, C, eps)
+        (res, ms_ml) = timed(lambda: mlmc.estimate(plan, v, t, n0, L, Ms, seed=SEED + 1))
+        mean, sem, _ = res
+        mean = mean.cpu().numpy()
+        # single level at the finest step count, and EXACT, with the paths for the same sampling error
+        (m1, s1), _ = timed(lambda: plan.estimate(v, t, pilot, seed=SEED + 2, mode="strang", nsteps=n0 << L))
+        v_single = float((s1.cpu().numpy() ** 2).mean()) * pilot
+        M_single = int(np.ceil(v_single / eps ** 2))
+        (ms_out, ms_single) = timed(lambda: plan.estimate(v, t, M_single, seed=SEED + 3, mode="strang",
+                                                          nsteps=n0 << L))
+        (me_out, ms_exact) = timed(lambda: plan.estimate(v, t, M_single, seed=SEED + 4))
+    plan.close()
+    rel = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))  # noqa: E731
+    line = {"metric": "multilevel (STRANG, N = 2..64) GPU time at sampling error 1e-4", "value": ms_ml, "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": "mlmc_small_world_n1000", "beta": t, "n0": n0, "levels": L,
+                       "target_steps": n0 << L, "eps_abs": eps, "pilot_paths": pilot},
+            "levels": [{"level": l, "steps": n0 << l, "V": V[l], "C_ns_per_path": C[l] * 1e6, "M": Ms[l]}
+                       for l in range(L + 1)],
+            "variance_slope_log2": float(np.polyfit(np.arange(1, L + 1), np.log2(V[1:]), 1)[0]),
+            "mlmc": {"ms": ms_ml, "rel_l2_vs_strang64": rel(mean, target), "mean_sem_rel":
+                     float((sem.cpu().numpy() / np.abs(target)).mean())},
+            "single_level_strang64": {"M": M_single, "ms": ms_single,
+                                      "rel_l2_vs_strang64": rel(ms_out[0].cpu().numpy(), target)},
+            "exact_functional": {"M": M_single, "ms": ms_exact,
+                                 "rel_l2_vs_expm": rel(me_out[0].cpu().numpy(), exact)},
+            "strang64_bias_rel_l2": rel(target, exact),
+            "cost_ratio_mlmc_over_single": ms_ml / ms_single,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def run_ranking(args):
     """Ranking similarity (Sec. 6, Tables 1 and 3).  Table 1: small-world graphs of 1e3 and
     1e4 nodes, beta = 1; node communicabilities exp(A) 1 by the forward form (Algorithm 2,
@@ -841,6 +927,9 @@ def main():
         return
     if args.workload == "rqmc":
         run_rqmc(args)
+        return
+    if args.workload == "mlmc":
+        run_mlmc(args)
         return
     import numpy as np
     import torch

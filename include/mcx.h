@@ -245,6 +245,29 @@ mcx_status mcx_estimate_noalloc(mcx_plan *plan, const double *v, double t, int f
                                 uint64_t seed, uint64_t path_offset, int precision, double *mean, double *sem,
                                 void *stream);
 
+/*
+ * Multilevel Monte Carlo level difference (Giles 2008) for the split
+ * functionals (Theorem 1 with Eqs. deff / eq_general1): per requested entry
+ * the mean and standard error of Y = v_{X_t} (W_N - W_{N/2}) over
+ * paths_per_entry paths, where W_N and W_{N/2} are the STRANG or LIE
+ * functionals with N and N/2 steps evaluated on the same path.  The paths are
+ * those of mcx_estimate with the same seed and path_offset (the draw schedule
+ * does not depend on N), so estimate(N_0) + the differences at N_1 .. N_L on
+ * common paths telescope to estimate(N_L); independent levels take disjoint
+ * path_offset ranges.
+ *   functional       MCX_STRANG or MCX_LIE
+ *   nsteps           N, even, >= 2
+ *   other arguments  as for mcx_estimate
+ * Chunk partials (n_entries x chunks x 24 bytes) come from the library's
+ * memory pool, stream-ordered.  An invalid entry yields NaN and MCX_E_INVALID
+ * at mcx_sync.
+ * Errors: MCX_E_INVALID (also for EXACT or an odd N), MCX_E_CUDA, MCX_E_OOM.
+ */
+mcx_status mcx_estimate_level_difference(mcx_plan *plan, const double *v, double t, int functional, int32_t nsteps,
+                                         uint64_t paths_per_entry, const int32_t *entries, int64_t n_entries,
+                                         uint64_t seed, uint64_t path_offset, int precision, double *mean,
+                                         double *sem, void *stream);
+
 /* Largest log2 of the points per replicate of mcx_estimate_rqmc. */
 #define MCX_QMC_MAX_LOG2 24
 /* Sobol' dimensions of mcx_estimate_rqmc: holding time and slot of the first 8 events. */

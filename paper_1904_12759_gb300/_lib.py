@@ -17,6 +17,7 @@ EXPORTS = (
     "mcx_plan_get_info",
     "mcx_estimate",
     "mcx_estimate_rqmc",
+    "mcx_estimate_level_difference",
     "mcx_estimate_noalloc",
     "mcx_estimate_forward",
     "mcx_trace_forward",
@@ -108,6 +109,9 @@ def load(path: str = LIB_PATH):
     L.mcx_estimate.restype = st
     L.mcx_estimate_rqmc.argtypes = [vp, vp, dbl, C.c_int, i32, u32, u32, vp, i64, u64, C.c_int, vp, vp, vp]
     L.mcx_estimate_rqmc.restype = st
+    L.mcx_estimate_level_difference.argtypes = [vp, vp, dbl, C.c_int, i32, u64, vp, i64, u64, u64, C.c_int, vp,
+                                                vp, vp]
+    L.mcx_estimate_level_difference.restype = st
     L.mcx_estimate_noalloc.argtypes = [vp, vp, dbl, C.c_int, i32, u64, vp, i64, u64, u64, C.c_int, vp, vp, vp]
     L.mcx_estimate_noalloc.restype = st
     L.mcx_estimate_forward.argtypes = [vp, vp, dbl, C.c_int, i32, u64, u64, u64, C.c_int, vp, vp, vp]

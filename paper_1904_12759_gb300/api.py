@@ -104,6 +104,32 @@ class Plan:
               "mcx_estimate")
         return mean, sem
 
+    def estimate_level_difference(self, v: torch.Tensor, t: float, nsteps: int, paths: int,
+                                  entries: torch.Tensor | None = None, seed: int = 0, path_offset: int = 0,
+                                  mode: str = "strang", prec: str = "fp32", out: tuple | None = None, stream=None):
+        """Multilevel level difference: per entry the mean and standard error of
+        v_{X_t} (W_N - W_{N/2}) over the paths of `estimate` with the same seed and
+        offset (N = nsteps, even; STRANG or LIE).  Returns (mean, sem)."""
+        L = _lib.load()
+        p_v = _dev(v, torch.float64, "v")
+        if v.numel() != self.n:
+            raise ValueError("v must have n entries")
+        if entries is None:
+            ne, p_e = self.n, 0
+        else:
+            ne, p_e = entries.numel(), _dev(entries, torch.int32, "entries")
+        if out is None:
+            mean = torch.empty(ne, dtype=torch.float64, device=v.device)
+            sem = torch.empty(ne, dtype=torch.float64, device=v.device)
+        else:
+            mean, sem = out
+        p_sem = _dev(sem, torch.float64, "sem") if sem is not None else 0
+        check(L.mcx_estimate_level_difference(self._h, C.c_void_p(p_v), float(t), FUNCTIONALS[mode], int(nsteps),
+                                              int(paths), C.c_void_p(p_e), int(ne), int(seed), int(path_offset),
+                                              PRECISIONS[prec], C.c_void_p(_dev(mean, torch.float64, "mean")),
+                                              C.c_void_p(p_sem), _stream(stream)), "mcx_estimate_level_difference")
+        return mean, sem
+
     def estimate_rqmc(self, v: torch.Tensor, t: float, log2_points: int, replicates: int,
                       entries: torch.Tensor | None = None, seed: int = 0, mode: str = "exact", nsteps: int = 1,
                       prec: str = "fp32", out: tuple | None = None, stream=None):

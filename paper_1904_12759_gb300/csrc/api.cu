@@ -200,6 +200,41 @@ mcx_status mcx_estimate(mcx_plan *p, const double *v, double t, int functional, 
     return from_cuda(launch_estimate(p, a, st));
 }
 
+mcx_status mcx_estimate_level_difference(mcx_plan *p, const double *v, double t, int functional, int32_t nsteps,
+                                         uint64_t paths_per_entry, const int32_t *entries, int64_t n_entries,
+                                         uint64_t seed, uint64_t path_offset, int precision, double *mean,
+                                         double *sem, void *stream) {
+    mcx_status rc = check_common(p, t, functional, nsteps, precision);
+    if (rc != MCX_OK) return rc;
+    if (functional != MCX_STRANG && functional != MCX_LIE) return MCX_E_INVALID;
+    if (nsteps < 2 || (nsteps & 1)) return MCX_E_INVALID;
+    if (n_entries == 0) return MCX_OK;
+    if (!v || n_entries < 0 || paths_per_entry < 1 || !mean) return MCX_E_INVALID;
+    if (!entries && n_entries != p->n) return MCX_E_INVALID;
+    if (paths_per_entry > (1ull << 53)) return MCX_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = launch_pack_v(p, v, st);
+    if (e != cudaSuccess) return from_cuda(e);
+    EstimateArgs a{};
+    a.entries = entries;
+    a.n_entries = n_entries;
+    a.paths = paths_per_entry;
+    a.t = t;
+    a.mode = functional;
+    a.nsteps = nsteps;
+    a.precision = precision;
+    a.seed = seed;
+    a.path_offset = path_offset;
+    a.mean = mean;
+    a.sem = sem;
+    if (t == 0.0) {  // both functionals are 0: every difference is 0
+        e = cudaMemsetAsync(mean, 0, sizeof(double) * (size_t)n_entries, st);
+        if (e == cudaSuccess && sem) e = cudaMemsetAsync(sem, 0, sizeof(double) * (size_t)n_entries, st);
+        return from_cuda(e);
+    }
+    return from_cuda(launch_level_difference(p, a, st));
+}
+
 mcx_status mcx_estimate_rqmc(mcx_plan *p, const double *v, double t, int functional, int32_t nsteps,
                              uint32_t log2_points, uint32_t replicates, const int32_t *entries, int64_t n_entries,
                              uint64_t seed, int precision, double *mean, double *sem, void *stream) {

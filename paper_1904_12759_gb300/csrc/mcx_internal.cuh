@@ -259,6 +259,8 @@ struct RqmcArgs {
     double *mean;
     double *sem;
 };
+// Multilevel level difference N vs N/2 (v already packed into the node records).
+cudaError_t launch_level_difference(mcx_plan *plan, const EstimateArgs &a, cudaStream_t st);
 // Randomised-QMC estimate (v already packed into the node records).
 cudaError_t launch_estimate_rqmc(mcx_plan *plan, const RqmcArgs &a, cudaStream_t st);
 cudaError_t launch_estimate_noalloc(mcx_plan *plan, const double *v, const EstimateArgs &a, cudaStream_t st,
