@@ -293,6 +293,11 @@ mcx_status mcx_estimate_level_difference(mcx_plan *plan, const double *v, double
  *                    MCX_QMC_MAX_LOG2 (0: one point, a plain Monte Carlo draw)
  *   replicates       1 <= R <= 2^16 (R >= 2 for a standard error); paths per
  *                    entry are R 2^log2_points, at most 2^40
+ *   replicate_offset the replicates drawn are replicate_offset ..
+ *                    replicate_offset + R - 1 (their scrambles, shifts and
+ *                    Philox path indices), so disjoint ranges are independent
+ *                    and merge into one estimate (sharding; the sum with R must
+ *                    stay below 2^32)
  *   mean             float64 [n_entries] output: the mean of the mu_r
  *   sem              float64 [n_entries] output, or NULL: sqrt(s^2 / R) with
  *                    s^2 the unbiased sample variance of the mu_r (0 if R = 1)
@@ -304,8 +309,9 @@ mcx_status mcx_estimate_level_difference(mcx_plan *plan, const double *v, double
  * Errors: MCX_E_INVALID, MCX_E_CUDA, MCX_E_OOM.
  */
 mcx_status mcx_estimate_rqmc(mcx_plan *plan, const double *v, double t, int functional, int32_t nsteps,
-                             uint32_t log2_points, uint32_t replicates, const int32_t *entries, int64_t n_entries,
-                             uint64_t seed, int precision, double *mean, double *sem, void *stream);
+                             uint32_t log2_points, uint32_t replicates, uint32_t replicate_offset,
+                             const int32_t *entries, int64_t n_entries, uint64_t seed, int precision, double *mean,
+                             double *sem, void *stream);
 
 /*
  * Per-path record of `count` backward paths of one entry (for parity checks

@@ -606,7 +606,8 @@ int oracle_estimate(const oracle_graph *g, const double *v, double t, int mode, 
     return O_OK;
 }
 
-/* Randomised QMC estimate: for each requested entry, R replicates of the     */
+/* Randomised QMC estimate: for each requested entry, replicates r0 .. r0+R-1 */
+/* (R of them; disjoint ranges are independent and can be merged) of the      */
 /* 2^log2q points of the scrambled Sobol' set (quasi-random draws for events */
 /* 0..QMC_EVENTS-1, as described above); replicate mean mu_r = plain          */
 /* sequential FP64 sum of W v_{X_t} over its points / 2^log2q; the estimate  */
@@ -633,8 +634,8 @@ static path_out qmc_path(const oracle_graph *g, int32_t i, double t, int mode, i
 }
 
 int oracle_estimate_rqmc(const oracle_graph *g, const double *v, double t, int mode, int N, int prec,
-                         uint32_t log2q, uint32_t R, const int32_t *entries, int64_t n_entries, uint64_t seed,
-                         double *mean, double *sem, double *rep_means, uint64_t *jumps_out)
+                         uint32_t log2q, uint32_t R, uint32_t r0, const int32_t *entries, int64_t n_entries,
+                         uint64_t seed, double *mean, double *sem, double *rep_means, uint64_t *jumps_out)
 {
     if (log2q > QMC_MAX_LOG2 || R < 1) return O_E_INVALID;
     uint64_t jumps = 0;
@@ -646,11 +647,11 @@ int oracle_estimate_rqmc(const oracle_graph *g, const double *v, double t, int m
         uint32_t V[QMC_DIMS][32];
         for (uint32_t r = 0; r < R; ++r) {
             qmc_point qp;
-            qmc_replicate(seed, i, r, V, &qp);
+            qmc_replicate(seed, i, r0 + r, V, &qp);
             double sum = 0.0;
             for (uint32_t q = 0; q < Q; ++q) {
                 qp.q = q;
-                path_out o = qmc_path(g, i, t, mode, N, prec, seed, log2q, r, &qp);
+                path_out o = qmc_path(g, i, t, mode, N, prec, seed, log2q, r0 + r, &qp);
                 sum += exp(o.logw) * v[o.end];
                 jumps += o.njumps;
             }

@@ -90,8 +90,8 @@ def lib():
             L.oracle_qmc_scrambled.argtypes = [u64, u32, vp]
             L.oracle_qmc_shift.argtypes = [u64, i32, u32, u32]
             L.oracle_qmc_shift.restype = u32
-            L.oracle_estimate_rqmc.argtypes = [C.POINTER(_Graph), vp, dbl, C.c_int, C.c_int, C.c_int, u32, u32, vp,
-                                               i64, u64, vp, vp, vp, vp]
+            L.oracle_estimate_rqmc.argtypes = [C.POINTER(_Graph), vp, dbl, C.c_int, C.c_int, C.c_int, u32, u32, u32,
+                                               vp, i64, u64, vp, vp, vp, vp]
             L.oracle_estimate_rqmc.restype = C.c_int
             L.oracle_estimate_level_difference.argtypes = [C.POINTER(_Graph), vp, dbl, C.c_int, C.c_int, C.c_int,
                                                            u64, vp, i64, u64, u64, vp, vp]
@@ -192,10 +192,11 @@ class Graph:
                                  int(seed), int(path_offset), _p(mean), _p(sem))
         return mean, sem
 
-    def estimate_rqmc(self, v, t, log2q, replicates, entries=None, seed=0, mode="exact", nsteps=1, prec="fp32"):
-        """Randomised-QMC estimate: per entry, the mean of `replicates` replicate means over
-        the 2^log2q scrambled Sobol' points, its standard error from their spread, and the
-        replicate means themselves [entries, replicates]."""
+    def estimate_rqmc(self, v, t, log2q, replicates, entries=None, seed=0, mode="exact", nsteps=1, prec="fp32",
+                      replicate_offset=0):
+        """Randomised-QMC estimate: per entry, the mean of `replicates` replicate means (replicates
+        replicate_offset ..) over the 2^log2q scrambled Sobol' points, its standard error from
+        their spread, and the replicate means themselves [entries, replicates]."""
         v = np.ascontiguousarray(v, dtype=np.float64)
         if entries is None:
             ne, ent_p = self.n, None
@@ -207,8 +208,8 @@ class Graph:
         reps = np.zeros((ne, int(replicates)))
         jumps = np.zeros(1, np.uint64)
         st = lib().oracle_estimate_rqmc(C.byref(self._g), _p(v), float(t), MODES[mode], int(nsteps), PRECS[prec],
-                                        int(log2q), int(replicates), ent_p, int(ne), int(seed), _p(mean), _p(sem),
-                                        _p(reps), _p(jumps))
+                                        int(log2q), int(replicates), int(replicate_offset), ent_p, int(ne),
+                                        int(seed), _p(mean), _p(sem), _p(reps), _p(jumps))
         if st != 0:
             raise ValueError("invalid quasi-random set size")
         return mean, sem, reps

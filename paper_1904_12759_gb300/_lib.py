@@ -107,7 +107,7 @@ def load(path: str = LIB_PATH):
     L.mcx_plan_get_info.restype = st
     L.mcx_estimate.argtypes = [vp, vp, dbl, C.c_int, i32, u64, vp, i64, u64, u64, C.c_int, vp, vp, vp]
     L.mcx_estimate.restype = st
-    L.mcx_estimate_rqmc.argtypes = [vp, vp, dbl, C.c_int, i32, u32, u32, vp, i64, u64, C.c_int, vp, vp, vp]
+    L.mcx_estimate_rqmc.argtypes = [vp, vp, dbl, C.c_int, i32, u32, u32, u32, vp, i64, u64, C.c_int, vp, vp, vp]
     L.mcx_estimate_rqmc.restype = st
     L.mcx_estimate_level_difference.argtypes = [vp, vp, dbl, C.c_int, i32, u64, vp, i64, u64, u64, C.c_int, vp,
                                                 vp, vp]

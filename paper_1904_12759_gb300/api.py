@@ -132,9 +132,10 @@ class Plan:
 
     def estimate_rqmc(self, v: torch.Tensor, t: float, log2_points: int, replicates: int,
                       entries: torch.Tensor | None = None, seed: int = 0, mode: str = "exact", nsteps: int = 1,
-                      prec: str = "fp32", out: tuple | None = None, stream=None):
+                      prec: str = "fp32", replicate_offset: int = 0, out: tuple | None = None, stream=None):
         """Randomised quasi-Monte Carlo estimate of (exp(tA)v)_i: `replicates` scrambled
-        Sobol' sets of 2^log2_points points drive the first events of the paths.
+        Sobol' sets of 2^log2_points points (replicates replicate_offset ..; disjoint
+        ranges merge with shard.merge) drive the first events of the paths.
 
         Returns (mean, sem) float64 CUDA tensors; sem comes from the spread of the
         replicate means.
@@ -154,7 +155,8 @@ class Plan:
             mean, sem = out
         p_sem = _dev(sem, torch.float64, "sem") if sem is not None else 0
         check(L.mcx_estimate_rqmc(self._h, C.c_void_p(p_v), float(t), FUNCTIONALS[mode], int(nsteps),
-                                  int(log2_points), int(replicates), C.c_void_p(p_e), int(ne), int(seed),
+                                  int(log2_points), int(replicates), int(replicate_offset), C.c_void_p(p_e),
+                                  int(ne), int(seed),
                                   PRECISIONS[prec], C.c_void_p(_dev(mean, torch.float64, "mean")),
                                   C.c_void_p(p_sem), _stream(stream)), "mcx_estimate_rqmc")
         return mean, sem

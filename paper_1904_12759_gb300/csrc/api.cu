@@ -236,8 +236,9 @@ mcx_status mcx_estimate_level_difference(mcx_plan *p, const double *v, double t,
 }
 
 mcx_status mcx_estimate_rqmc(mcx_plan *p, const double *v, double t, int functional, int32_t nsteps,
-                             uint32_t log2_points, uint32_t replicates, const int32_t *entries, int64_t n_entries,
-                             uint64_t seed, int precision, double *mean, double *sem, void *stream) {
+                             uint32_t log2_points, uint32_t replicates, uint32_t replicate_offset,
+                             const int32_t *entries, int64_t n_entries, uint64_t seed, int precision, double *mean,
+                             double *sem, void *stream) {
     mcx_status rc = check_common(p, t, functional, nsteps, precision);
     if (rc != MCX_OK) return rc;
     if (n_entries == 0) return MCX_OK;
@@ -245,6 +246,7 @@ mcx_status mcx_estimate_rqmc(mcx_plan *p, const double *v, double t, int functio
         return MCX_E_INVALID;
     if (!entries && n_entries != p->n) return MCX_E_INVALID;
     if (((uint64_t)replicates << log2_points) > (1ull << 40)) return MCX_E_INVALID;
+    if ((uint64_t)replicate_offset + replicates > 0xFFFFFFFFull) return MCX_E_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = launch_pack_v(p, v, st);
     if (e != cudaSuccess) return from_cuda(e);
@@ -266,6 +268,7 @@ mcx_status mcx_estimate_rqmc(mcx_plan *p, const double *v, double t, int functio
     a.n_entries = n_entries;
     a.log2q = log2_points;
     a.replicates = replicates;
+    a.r0 = replicate_offset;
     a.t = t;
     a.mode = functional;
     a.nsteps = nsteps;

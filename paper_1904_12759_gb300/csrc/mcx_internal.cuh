@@ -251,6 +251,7 @@ struct RqmcArgs {
     int64_t n_entries;
     uint32_t log2q;
     uint32_t replicates;
+    uint32_t r0;  // first replicate index
     double t;
     int mode;
     int nsteps;

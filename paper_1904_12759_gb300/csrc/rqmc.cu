@@ -112,14 +112,14 @@ SobolBase sobol_base() {
 constexpr uint32_t QMC_DIGIT = 5;
 constexpr uint32_t QMC_LEVELS = (MCX_QMC_MAX_LOG2 + QMC_DIGIT - 1) / QMC_DIGIT;
 
-// One thread per (replicate r, dimension d): the scrambled direction numbers
-// L_(r,d) V_d[b], b < bits, then the digit tables
+// One thread per (replicate r0 + r, dimension d): the scrambled direction
+// numbers L_(r0+r,d) V_d[b], b < bits, then the digit tables
 // tabs[((r * QMC_DIMS + d) * nlev + l) * 32 + c].
 __global__ void k_qmc_scramble(const __grid_constant__ WalkParams a, const __grid_constant__ SobolBase base,
-                               uint32_t R, uint32_t bits, uint32_t nlev, uint32_t *__restrict__ tabs) {
+                               uint32_t R, uint32_t r0, uint32_t bits, uint32_t nlev, uint32_t *__restrict__ tabs) {
     const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= R * (uint32_t)QMC_DIMS) return;
-    const uint32_t r = id / QMC_DIMS, d = id % QMC_DIMS;
+    const uint32_t r = r0 + id / QMC_DIMS, d = id % QMC_DIMS;  // r: the replicate's global index
     uint32_t row[32];
 #pragma unroll
     for (uint32_t b = 0; b < 32; ++b) {
@@ -162,6 +162,7 @@ __device__ __forceinline__ uint32_t sobol_coord(const uint32_t *__restrict__ tab
 struct RqmcJob {
     uint32_t log2q;        // points per replicate: 2^log2q
     uint32_t R;            // replicates
+    uint32_t r0;           // global index of replicate 0 (scrambles, shifts, path indices)
     uint32_t G;            // replicates per warp (slices == 1)
     uint32_t groups;       // ceil(R / G)
     uint32_t slices;       // warps per replicate (a power of two <= 2^log2q; G == 1 when > 1)
@@ -341,10 +342,10 @@ __global__ void __launch_bounds__(WALK_THREADS, F64 ? WALK_MIN_BLOCKS_F64 : MCX_
             const unsigned lt_mask = (1u << lane) - 1u;
             for (uint32_t r = r_begin; r < r_end; ++r) {
                 __syncwarp();  // the previous replicate's shifts are no longer read
-                load_shifts(sh, a, i, r, 1, lane);
+                load_shifts(sh, a, i, job.r0 + r, 1, lane);
                 __syncwarp();
                 const uint32_t *tab = job.tabs + (uint64_t)r * tab_words;
-                const uint64_t pbase = ((uint64_t)r << bits) + q0;
+                const uint64_t pbase = ((uint64_t)(job.r0 + r) << bits) + q0;
                 w.rec = sw.start; w.j = i; w.r = t0; w.acc = (T)0; w.delta = delta_start; w.k = 0;
                 uint32_t next = 32;  // warp-uniform
                 uint32_t p = (uint32_t)lane;
@@ -388,12 +389,12 @@ __global__ void __launch_bounds__(WALK_THREADS, F64 ? WALK_MIN_BLOCKS_F64 : MCX_
             for (uint32_t rb = r_begin; rb < r_end; rb += per) {
                 const uint32_t np = min(per, r_end - rb);
                 __syncwarp();
-                load_shifts(sh_all, a, i, rb, np, lane);
+                load_shifts(sh_all, a, i, job.r0 + rb, np, lane);
                 __syncwarp();
                 const bool mine = rl < np;
                 T L = (T)0, vend = (T)0;
                 if (mine) {
-                    const uint64_t path = ((uint64_t)(rb + rl) << bits) + q;
+                    const uint64_t path = ((uint64_t)(job.r0 + rb + rl) << bits) + q;
                     w.rec = sw.start; w.j = i; w.r = t0; w.acc = (T)0; w.delta = delta_start; w.k = 0;
                     const uint32_t *tab = job.tabs + (uint64_t)(rb + rl) * tab_words;
                     while (!advance_drawn<MODE, WEIGHTED, F64>(
@@ -574,6 +575,7 @@ cudaError_t launch_estimate_rqmc(mcx_plan *plan, const RqmcArgs &a, cudaStream_t
     RqmcJob job{};
     job.log2q = a.log2q;
     job.R = a.replicates;
+    job.r0 = a.r0;
     job.G = G;
     job.groups = groups;
     job.slices = slices;
@@ -587,7 +589,7 @@ cudaError_t launch_estimate_rqmc(mcx_plan *plan, const RqmcArgs &a, cudaStream_t
     if (e == cudaSuccess && !job.fused) e = pool_alloc(&part, sizeof(double2) * (size_t)(units * slices), st);
     if (e == cudaSuccess && tab_bytes > 0) {
         const uint32_t threads = a.replicates * (uint32_t)QMC_DIMS;
-        k_qmc_scramble<<<(threads + 127) / 128, 128, 0, st>>>(p, sobol_base(), a.replicates, a.log2q, nlev,
+        k_qmc_scramble<<<(threads + 127) / 128, 128, 0, st>>>(p, sobol_base(), a.replicates, a.r0, a.log2q, nlev,
                                                               static_cast<uint32_t *>(tabs));
         e = cudaGetLastError();
     }

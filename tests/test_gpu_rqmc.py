@@ -154,3 +154,30 @@ def test_rqmc_reduces_variance_on_gpu(mcx):
     zq = (q - x) / qs
     assert np.mean(np.abs(zq) > 3.5) < 0.02 and abs(zq.mean()) < 0.3
     plan.close()
+
+
+def test_rqmc_replicate_ranges_shard(mcx):
+    """Replicates 0..6 and 7..11 as two calls (two ranks) against the oracle with the
+    same offsets, and merged by the shard formula against one call over all 12."""
+    from paper_1904_12759_gb300 import shard
+
+    csr = W.erdos_renyi(2000, 10, 5)
+    plan = mcx.Plan.from_csr(csr)
+    og = OW.Graph(csr)
+    v = W.uniform_vector(csr.n, 2)
+    vd = _cuda(v, torch.float64)
+    ent = np.arange(0, csr.n, 13, dtype=np.int32)
+    ed = _cuda(ent, torch.int32)
+    parts = []
+    for r0, R in ((0, 7), (7, 5)):
+        gm, gs = plan.estimate_rqmc(vd, 0.09, 6, R, entries=ed, seed=8, replicate_offset=r0)
+        om, os_, _ = og.estimate_rqmc(v, 0.09, 6, R, entries=ent, seed=8, replicate_offset=r0)
+        _check(gm.cpu().numpy(), gs.cpu().numpy(), om, os_, np.abs(om), "fp32", r0)
+        parts.append((gm.cpu().numpy(), gs.cpu().numpy(), R))
+    am, asem = plan.estimate_rqmc(vd, 0.09, 6, 12, entries=ed, seed=8)
+    mm, ss = shard.merge(np.stack([p[0] for p in parts]), np.stack([p[1] for p in parts]), np.array([7, 5]))
+    am, asem = am.cpu().numpy(), asem.cpu().numpy()
+    assert np.allclose(mm, am, rtol=4e-6) and np.allclose(ss, asem, rtol=1e-3, atol=1e-6 * np.abs(am).max())
+    with pytest.raises(mcx.MCXError):
+        plan.estimate_rqmc(vd, 0.09, 6, 12, entries=ed, replicate_offset=0xFFFFFFFF - 5)
+    plan.close()

@@ -179,3 +179,22 @@ def test_one_point_replicates_are_plain_monte_carlo():
     mean, sem, reps = OW.Graph(csr).estimate_rqmc(v, t, 0, 256, seed=8)
     assert reps.shape == (csr.n, 256)
     assert np.mean(np.abs((mean - x) / sem) > 3.5) <= 0.05
+
+
+def test_replicate_ranges_merge_like_one_run():
+    """Two disjoint replicate ranges (two ranks) merged by the shard formula give the
+    single run over all replicates: the same replicate means, the same estimate and
+    standard error."""
+    from paper_1904_12759_gb300 import shard
+
+    csr, _ = _small_graph()
+    g = OW.Graph(csr)
+    v = W.uniform_vector(csr.n, 5)
+    m, s, reps = g.estimate_rqmc(v, 0.3, 5, 12, seed=21)
+    m1, s1, r1 = g.estimate_rqmc(v, 0.3, 5, 7, seed=21)
+    m2, s2, r2 = g.estimate_rqmc(v, 0.3, 5, 5, seed=21, replicate_offset=7)
+    assert np.array_equal(np.concatenate([r1, r2], axis=1), reps)
+    mm, ss = shard.merge(np.stack([m1, m2]), np.stack([s1, s2]), np.array([7, 5]))
+    # the merge's one-pass variance leaves ~1e-8 of the mean where the spread is zero
+    assert np.allclose(mm, m, rtol=1e-13, atol=0)
+    assert np.allclose(ss, s, rtol=1e-8, atol=1e-7 * np.abs(m).max())
