@@ -7,6 +7,7 @@
 #include <new>
 
 #include "mcx_internal.cuh"
+#include "launch.h"
 
 using namespace mcx;
 

@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "walker.cuh"
+#include "launch.h"
 
 namespace mcx {
 namespace {

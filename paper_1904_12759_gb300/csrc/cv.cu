@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "dfloat.cuh"
+#include "launch.h"
 #include "rows.cuh"
 #include "tc.cuh"
 #include "walker.cuh"

@@ -224,69 +224,4 @@ __device__ void vose_build(int32_t d, const double *__restrict__ w, double lam, 
     }
 }
 
-// Host-side launch helpers (defined in the .cu files).
-cudaError_t launch_prep(mcx_plan *plan, const int64_t *row_ptr, const int32_t *col, const double *val,
-                        cudaStream_t st, uint32_t *host_status);
-cudaError_t launch_export(const mcx_plan *plan, int32_t *deg, int64_t *row_start, uint8_t *weighted, float *ir32,
-                          float *d32, double *ir64, double *d64, int32_t *ecol, int32_t *acol, uint32_t *thr,
-                          cudaStream_t st);
-cudaError_t launch_pack_v(mcx_plan *plan, const double *v, cudaStream_t st);
-
-struct EstimateArgs {
-    const int32_t *entries;
-    int64_t n_entries;
-    uint64_t paths;
-    double t;
-    int mode;
-    int nsteps;
-    int precision;
-    uint64_t seed;
-    uint64_t path_offset;
-    double *mean;
-    double *sem;
-};
-cudaError_t launch_estimate(mcx_plan *plan, const EstimateArgs &a, cudaStream_t st);
-struct RqmcArgs {
-    const int32_t *entries;
-    int64_t n_entries;
-    uint32_t log2q;
-    uint32_t replicates;
-    uint32_t r0;  // first replicate index
-    double t;
-    int mode;
-    int nsteps;
-    int precision;
-    uint64_t seed;
-    double *mean;
-    double *sem;
-};
-// Multilevel level difference N vs N/2 (v already packed into the node records).
-cudaError_t launch_level_difference(mcx_plan *plan, const EstimateArgs &a, cudaStream_t st);
-// Randomised-QMC estimate (v already packed into the node records).
-cudaError_t launch_estimate_rqmc(mcx_plan *plan, const RqmcArgs &a, cudaStream_t st);
-cudaError_t launch_estimate_noalloc(mcx_plan *plan, const double *v, const EstimateArgs &a, cudaStream_t st,
-                                    bool *too_large);
-uint64_t noalloc_max_partials();
-cudaError_t launch_estimate_forward(mcx_plan *plan, const double *v, double t, int mode, int nsteps, uint64_t paths,
-                                    uint64_t seed, uint64_t path_offset, int precision, double *x, double *sem,
-                                    cudaStream_t st);
-// Stream-ordered allocation from the library's memory pool of the current
-// device (created on first use; memory freed to it stays reserved for the next
-// plan instead of being released to the system, so plans are created and destroyed
-// without device-wide synchronisation).
-cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st);
-void pool_free(void *p, cudaStream_t st);
-cudaError_t launch_total_communicability(mcx_plan *plan, double t, int mode, int nsteps, uint64_t paths,
-                                         uint64_t seed, uint64_t path_offset, int precision, double *tc, double *sem,
-                                         cudaStream_t st);
-cudaError_t launch_trace_forward(mcx_plan *plan, const double *v, double t, int mode, int nsteps, uint64_t seed,
-                                 uint64_t first_path, uint32_t count, int precision, int32_t *start, int32_t *end,
-                                 uint32_t *njumps, uint64_t *hash, double *logw, cudaStream_t st);
-cudaError_t launch_trace(mcx_plan *plan, double t, int mode, int nsteps, int32_t entry, uint64_t seed,
-                         uint64_t first_path, uint32_t count, int precision, int32_t *end, uint32_t *njumps,
-                         uint64_t *hash, double *logw, cudaStream_t st);
-cudaError_t run_power_iteration(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
-                                int32_t max_iters, double tol, double *work, double *lambda, int32_t *iters,
-                                cudaStream_t st);
-
 }  // namespace mcx

@@ -21,6 +21,7 @@
 #include <math.h>
 
 #include "mcx_internal.cuh"
+#include "launch.h"
 
 namespace mcx {
 namespace {

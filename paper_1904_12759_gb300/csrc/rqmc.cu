@@ -41,6 +41,7 @@
 #include <type_traits>
 
 #include "accum.cuh"
+#include "launch.h"
 #include "walker.cuh"
 
 namespace mcx {

@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "rows.cuh"
+#include "launch.h"
 
 namespace mcx {
 

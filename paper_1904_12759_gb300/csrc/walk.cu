@@ -36,6 +36,7 @@
 #include <type_traits>
 
 #include "accum.cuh"
+#include "launch.h"
 #include "walker.cuh"
 
 namespace mcx {
