@@ -326,7 +326,7 @@ def run_ctmc_batch(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "ctmc_batch", "generators": args.generators, "states": info["states"],
                        "times": [0.1, 1.0, 10.0], "paths_per_state": 64, "functional": "exact, forward form",
-                       "schedule": {k: info[k] for k in ("chunk", "blocks_per_sm", "grid", "work_items")},
+                       "schedule": {k: info[k] for k in ("chunk", "blocks_per_sm", "lane_refill", "grid", "work_items")},
                        "l2": "inputs (2 GB of edge records) larger than L2"},
             "walker": {"paths": paths, "jumps": jumps, "paths_per_s": paths / step_s,
                        "max_conservation_error": worst, "batch_create_s": create_s},

@@ -388,7 +388,7 @@ typedef struct {
     int32_t blocks_per_sm;   /* resident blocks of 256 threads per SM (autotuned) */
     int32_t grid;            /* persistent grid size */
     int32_t count_deposits;  /* 1: every potential is zero, deposits are exact counts */
-    int32_t reserved;
+    int32_t lane_refill;     /* 1: lanes take the next path of the item as theirs end (autotuned) */
     double tuned_ms;         /* the autotuner's best sampled run (0 if read from the cache) */
 } mcx_batch_info;
 
@@ -399,7 +399,8 @@ typedef struct {
  * tables are built over each v, and the (problem, time) pairs are cut into
  * work items ordered by estimated cost (largest first: cost ~ paths x
  * (1 + t x mean jump rate)).  The schedule (paths per work item, resident
- * blocks per SM) is read from `tune_cache` (a file of JSON lines keyed by GPU
+ * blocks per SM, lane refill on or off) is read from `tune_cache` (a file of
+ * JSON lines keyed by GPU
  * name and problem-set sizes; NULL: no cache) or autotuned by timing sampled
  * runs, then appended to the cache.  The reset + walk + finish sequence is
  * captured into a CUDA graph.  Pair k of the batch uses path indices

@@ -73,7 +73,7 @@ class Problem(C.Structure):
 class BatchInfo(C.Structure):
     _fields_ = [("problems", C.c_int32), ("pairs", C.c_int32), ("states", C.c_int64), ("total_paths", C.c_uint64),
                 ("work_items", C.c_uint32), ("chunk", C.c_uint32), ("blocks_per_sm", C.c_int32),
-                ("grid", C.c_int32), ("count_deposits", C.c_int32), ("reserved", C.c_int32),
+                ("grid", C.c_int32), ("count_deposits", C.c_int32), ("lane_refill", C.c_int32),
                 ("tuned_ms", C.c_double)]
 
 

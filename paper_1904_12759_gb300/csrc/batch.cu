@@ -16,12 +16,13 @@
 // paths; items are ordered by estimated cost per item, largest first
 // (longest-processing-time order; cost ~ paths x (1 + t x mean jump rate));
 // a persistent grid of warps takes items from an atomic counter.  Each warp
-// runs its item's paths with lane refill and deposits at the end states:
-// exact counts when every potential is zero (W = 1), FP64 sums otherwise.
-// The counter reset, deposit reset, walk and finish are captured once into a
-// CUDA graph; each run only updates the walk node's seed.  The autotuner
-// times a few (chunk, blocks per SM) settings and keeps the fastest, cached
-// by problem-set signature in a small JSON file.
+// runs its item's paths (with lane refill, or a fixed share per lane) and
+// deposits at the end states: exact counts when every potential is zero
+// (W = 1), FP64 sums otherwise.  The counter reset, deposit reset, walk and
+// finish are captured once into a CUDA graph; each run only updates the walk
+// node's seed.  The autotuner times the (lane refill, chunk, blocks per SM)
+// settings on a sample of the items and keeps the fastest, cached by
+// problem-set signature in a small JSON file.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -143,7 +144,10 @@ __device__ __forceinline__ int32_t batch_start(const BatchArgs &b, const BatchPT
     return (int32_t)j;
 }
 
-template <bool WEIGHTED, bool COUNT>
+// REFILL: a lane whose path ends takes the next unassigned path of the item
+// (ballot per event); otherwise each lane runs the fixed paths lane, lane + 32,
+// ... of the item with no per-event bookkeeping (the autotuner picks one).
+template <bool WEIGHTED, bool COUNT, bool REFILL>
 __global__ void __launch_bounds__(WALK_THREADS, 5) k_batch_walk(const __grid_constant__ WalkParams a,
                                                                const __grid_constant__ BatchArgs b) {
     const int lane = threadIdx.x & 31;
@@ -172,21 +176,35 @@ __global__ void __launch_bounds__(WALK_THREADS, 5) k_batch_walk(const __grid_con
             w.j = i0; w.r = t0; w.acc = 0.0f; w.k = 0;
             w.delta = w.rec.delta;
         };
-        if (active) start_path();
         uint32_t jumps = 0;
+        auto deposit = [&]() {
+            jumps += w.k;
+            const int64_t slot = p.dep + (w.j - p.off);
+            if (COUNT) {
+                atomicAdd(b.count + slot, 1ull);
+            } else {
+                const double y = V * (double)expf(w.acc);
+                atomicAdd(b.sum1 + slot, y);
+                atomicAdd(b.sum2 + slot, y * y);
+            }
+        };
+        if (!REFILL) {
+            for (; q < len; q += 32) {
+                start_path();
+                while (!advance<MCX_EXACT, WEIGHTED, false>(w, a, 0xFFFFFFFEu, base + q, nullptr, -1)) {
+                }
+                deposit();
+            }
+            paths_done += len;
+            jumps_done += jumps;
+            continue;
+        }
+        if (active) start_path();
         while (__any_sync(0xffffffffu, active)) {
             bool fin = false;
             if (active && advance<MCX_EXACT, WEIGHTED, false>(w, a, 0xFFFFFFFEu, base + q, nullptr, -1)) {
                 fin = true;
-                jumps += w.k;
-                const int64_t slot = p.dep + (w.j - p.off);
-                if (COUNT) {
-                    atomicAdd(b.count + slot, 1ull);
-                } else {
-                    const double y = V * (double)expf(w.acc);
-                    atomicAdd(b.sum1 + slot, y);
-                    atomicAdd(b.sum2 + slot, y * y);
-                }
+                deposit();
             }
             const unsigned fm = __ballot_sync(0xffffffffu, fin);
             if (fm) {
@@ -274,6 +292,7 @@ struct mcx_batch {
     uint32_t n_items = 0;
     uint32_t chunk = 0;
     int blocks_per_sm = 0;
+    bool refill = true;  // lane refill (autotuned)
     int sms = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -306,10 +325,18 @@ void free_batch(mcx_batch *b) {
     delete b;
 }
 
-void *walk_func(bool weighted, bool count) {
-    if (weighted) return count ? (void *)k_batch_walk<true, true> : (void *)k_batch_walk<true, false>;
-    return count ? (void *)k_batch_walk<false, true> : (void *)k_batch_walk<false, false>;
+template <bool REFILL>
+void *walk_func_r(bool weighted, bool count) {
+    if (weighted) return count ? (void *)k_batch_walk<true, true, REFILL> : (void *)k_batch_walk<true, false, REFILL>;
+    return count ? (void *)k_batch_walk<false, true, REFILL> : (void *)k_batch_walk<false, false, REFILL>;
 }
+
+void *walk_func(bool weighted, bool count, bool refill) {
+    return refill ? walk_func_r<true>(weighted, count) : walk_func_r<false>(weighted, count);
+}
+
+template <bool REFILL>
+void launch_walk(const mcx_batch *b, bool weighted, unsigned grid, cudaStream_t cs);
 
 // Work items for chunk length L, largest estimated item cost first; with
 // stride > 1 only every stride-th item is kept (the autotuner's sample).
@@ -338,6 +365,17 @@ cudaError_t make_items(mcx_batch *b, uint32_t L, cudaStream_t st, uint32_t strid
 }
 
 // Capture reset + walk + finish into a graph for the current schedule.
+template <bool REFILL>
+void launch_walk(const mcx_batch *b, bool weighted, unsigned grid, cudaStream_t cs) {
+    if (weighted) {
+        if (b->count_mode) k_batch_walk<true, true, REFILL><<<grid, WALK_THREADS, 0, cs>>>(b->wp, b->ba);
+        else k_batch_walk<true, false, REFILL><<<grid, WALK_THREADS, 0, cs>>>(b->wp, b->ba);
+    } else {
+        if (b->count_mode) k_batch_walk<false, true, REFILL><<<grid, WALK_THREADS, 0, cs>>>(b->wp, b->ba);
+        else k_batch_walk<false, false, REFILL><<<grid, WALK_THREADS, 0, cs>>>(b->wp, b->ba);
+    }
+}
+
 cudaError_t capture(mcx_batch *b, cudaStream_t st) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
@@ -355,13 +393,8 @@ cudaError_t capture(mcx_batch *b, cudaStream_t st) {
         cudaMemsetAsync(b->next_item, 0, sizeof(unsigned int), cs);
         cudaMemsetAsync(b->dep, 0, (b->count_mode ? 8 : 16) * (size_t)b->slots, cs);
         const unsigned grid = (unsigned)(b->sms * b->blocks_per_sm);
-        if (weighted) {
-            if (b->count_mode) k_batch_walk<true, true><<<grid, WALK_THREADS, 0, cs>>>(b->wp, b->ba);
-            else k_batch_walk<true, false><<<grid, WALK_THREADS, 0, cs>>>(b->wp, b->ba);
-        } else {
-            if (b->count_mode) k_batch_walk<false, true><<<grid, WALK_THREADS, 0, cs>>>(b->wp, b->ba);
-            else k_batch_walk<false, false><<<grid, WALK_THREADS, 0, cs>>>(b->wp, b->ba);
-        }
+        if (b->refill) launch_walk<true>(b, weighted, grid, cs);
+        else launch_walk<false>(b, weighted, grid, cs);
         k_batch_finish<<<b->n_pt, 256, 0, cs>>>(b->pts, b->ba, b->x, b->sem, b->plan->status);
         e = cudaStreamEndCapture(cs, &b->graph);
     }
@@ -374,7 +407,7 @@ cudaError_t capture(mcx_batch *b, cudaStream_t st) {
     cudaGraphGetNodes(b->graph, nullptr, &nn);
     std::vector<cudaGraphNode_t> nodes(nn);
     cudaGraphGetNodes(b->graph, nodes.data(), &nn);
-    const void *wf = walk_func(weighted, b->count_mode);
+    const void *wf = walk_func(weighted, b->count_mode, b->refill);
     for (auto nd : nodes) {
         cudaGraphNodeType ty;
         cudaGraphNodeGetType(nd, &ty);
@@ -410,8 +443,9 @@ std::string signature(const mcx_batch *b) {
     return buf;
 }
 
-// Minimal cache: one JSON object per line {"key": "...", "chunk": L, "blocks_per_sm": k, "ms": t}.
-bool cache_lookup(const char *path, const std::string &key, uint32_t *L, int *bps) {
+// Minimal cache: one JSON object per line
+// {"key": "...", "chunk": L, "blocks_per_sm": k, "refill": r, "ms": t} ("refill" 1 when absent).
+bool cache_lookup(const char *path, const std::string &key, uint32_t *L, int *bps, bool *refill) {
     if (!path) return false;
     FILE *f = fopen(path, "r");
     if (!f) return false;
@@ -422,9 +456,11 @@ bool cache_lookup(const char *path, const std::string &key, uint32_t *L, int *bp
         if (!strstr(line, needle.c_str())) continue;
         const char *c = strstr(line, "\"chunk\": ");
         const char *k = strstr(line, "\"blocks_per_sm\": ");
+        const char *r = strstr(line, "\"refill\": ");
         if (c && k) {
             *L = (uint32_t)strtoul(c + 9, nullptr, 10);
             *bps = (int)strtol(k + 17, nullptr, 10);
+            *refill = r ? strtol(r + 10, nullptr, 10) != 0 : true;
             found = *L > 0 && *bps > 0;
         }
     }
@@ -432,11 +468,12 @@ bool cache_lookup(const char *path, const std::string &key, uint32_t *L, int *bp
     return found;
 }
 
-void cache_store(const char *path, const std::string &key, uint32_t L, int bps, double ms) {
+void cache_store(const char *path, const std::string &key, uint32_t L, int bps, bool refill, double ms) {
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    fprintf(f, "{\"key\": \"%s\", \"chunk\": %u, \"blocks_per_sm\": %d, \"ms\": %.4f}\n", key.c_str(), L, bps, ms);
+    fprintf(f, "{\"key\": \"%s\", \"chunk\": %u, \"blocks_per_sm\": %d, \"refill\": %d, \"ms\": %.4f}\n",
+            key.c_str(), L, bps, refill ? 1 : 0, ms);
     fclose(f);
 }
 
@@ -608,52 +645,70 @@ mcx_status mcx_batch_create(int32_t count, const mcx_problem *pr, const char *tu
             ba.sum1 = static_cast<double *>(b->dep);
             ba.sum2 = static_cast<double *>(b->dep) + slots;
         }
-        // schedule: cached, else autotuned over chunk x blocks-per-SM (one timed run each)
+        // schedule: cached, else autotuned over lane refill x chunk x blocks-per-SM (one timed run each)
         const std::string key = signature(b);
         uint32_t L = 0;
         int bps = 0;
-        if (cache_lookup(tune_cache, key, &L, &bps)) {
+        bool rf = true;
+        if (cache_lookup(tune_cache, key, &L, &bps, &rf)) {
             b->blocks_per_sm = bps;
+            b->refill = rf;
             if ((e = make_items(b, L, st)) != cudaSuccess) break;
             if ((e = capture(b, st)) != cudaSuccess) break;
         } else {
             const uint32_t Ls[] = {512, 1024, 2048, 4096};
             const int bpss[] = {2, 3, 4, 5};  // 49 registers: at most 5 resident blocks of 256
-            double best = 1e300;
-            uint32_t bestL = 4096;
-            int bestb = 4;
+            // lane refill on over the (chunk, blocks per SM) grid, then refill off at
+            // the best of those; refill off is kept only if it wins the sample by more
+            // than 5% (a closer win did not carry over to the full batch)
+            double best_r[2] = {1e300, 1e300};
+            uint32_t bestL_r[2] = {4096, 4096};
+            int bestb_r[2] = {4, 4};
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
+            auto time_setting = [&](uint32_t Lc, int bc, int rc) -> cudaError_t {
+                b->refill = rc != 0;
+                b->blocks_per_sm = bc;
+                cudaError_t er;
+                if ((er = capture(b, st)) != cudaSuccess) return er;
+                if ((er = run_graph(b, 0x5eed, st)) != cudaSuccess) return er;  // warm
+                cudaEventRecord(e0, st);
+                if ((er = run_graph(b, 0x5eed, st)) != cudaSuccess) return er;
+                cudaEventRecord(e1, st);
+                if ((er = cudaEventSynchronize(e1)) != cudaSuccess) return er;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_r[rc]) {
+                    best_r[rc] = ms;
+                    bestL_r[rc] = Lc;
+                    bestb_r[rc] = bc;
+                }
+                return cudaSuccess;
+            };
             for (uint32_t Lc : Ls) {
                 // time each setting on every 8th work item of the cost-ordered list
                 if ((e = make_items(b, Lc, st, 8)) != cudaSuccess) break;
-                for (int bc : bpss) {
-                    b->blocks_per_sm = bc;
-                    if ((e = capture(b, st)) != cudaSuccess) break;
-                    if ((e = run_graph(b, 0x5eed, st)) != cudaSuccess) break;  // warm
-                    cudaEventRecord(e0, st);
-                    if ((e = run_graph(b, 0x5eed, st)) != cudaSuccess) break;
-                    cudaEventRecord(e1, st);
-                    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (ms < best) {
-                        best = ms;
-                        bestL = Lc;
-                        bestb = bc;
-                    }
-                }
+                for (int bc : bpss)
+                    if ((e = time_setting(Lc, bc, 1)) != cudaSuccess) break;
                 if (e != cudaSuccess) break;
             }
+            if (e == cudaSuccess && (e = make_items(b, bestL_r[1], st, 8)) == cudaSuccess)
+                e = time_setting(bestL_r[1], bestb_r[1], 0);
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             if (e != cudaSuccess) break;
+            const int pick = best_r[0] < 0.95 * best_r[1] ? 0 : 1;
+            const double best = best_r[pick];
+            const uint32_t bestL = bestL_r[pick];
+            const int bestb = bestb_r[pick];
+            const bool bestr = pick == 1;
             b->blocks_per_sm = bestb;
+            b->refill = bestr;
             b->tuned_ms = best;
             if ((e = make_items(b, bestL, st)) != cudaSuccess) break;
             if ((e = capture(b, st)) != cudaSuccess) break;
-            cache_store(tune_cache, key, bestL, bestb, best);
+            cache_store(tune_cache, key, bestL, bestb, bestr, best);
         }
         // clear the tuning runs' statistics
         cudaMemsetAsync(b->plan->status, 0, 32, st);
@@ -696,6 +751,7 @@ mcx_status mcx_batch_get_info(const mcx_batch *b, mcx_batch_info *info) {
     info->chunk = b->chunk;
     info->blocks_per_sm = b->blocks_per_sm;
     info->grid = b->sms * b->blocks_per_sm;
+    info->lane_refill = b->refill ? 1 : 0;
     info->count_deposits = b->count_mode ? 1 : 0;
     info->tuned_ms = b->tuned_ms;
     return MCX_OK;

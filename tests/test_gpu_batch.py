@@ -5,6 +5,7 @@ k * 2^40 + p, so it must reproduce, count for count, the oracle's
 single-problem forward run with path_offset = k * 2^40; CTMC generators have
 zero potential, so every pair also conserves probability exactly.
 """
+import json
 import math
 import os
 
@@ -55,13 +56,29 @@ def test_batch_matches_single_problem_oracle(mcx, tmp_path):
     # the schedule is read back from the cache the second time
     b2 = mcx.Batch(probs, tune_cache=cache)
     i2 = b2.info()
-    assert (i2["chunk"], i2["blocks_per_sm"]) == (info["chunk"], info["blocks_per_sm"]) and i2["tuned_ms"] == 0.0
+    assert (i2["chunk"], i2["blocks_per_sm"], i2["lane_refill"]) == (info["chunk"], info["blocks_per_sm"],
+                                                                      info["lane_refill"]) and i2["tuned_ms"] == 0.0
     b2.run(seed=21)
     x2, _ = b2.result(3, 2)
     x1, _ = b.result(3, 2)
     assert torch.equal(x1, x2)  # deterministic, schedule-independent counts
+    # the other lane-refill setting (forced through a cache entry) gives the same counts
+    line = json.loads(open(cache).readline())
+    line["refill"] = 1 - info["lane_refill"]
+    line["chunk"] = 512
+    forced = str(tmp_path / "forced.jsonl")
+    with open(forced, "w") as f:
+        f.write(json.dumps(line) + "\n")
+    b3 = mcx.Batch(probs, tune_cache=forced)
+    i3 = b3.info()
+    assert i3["lane_refill"] == 1 - info["lane_refill"] and i3["chunk"] == 512 and i3["tuned_ms"] == 0.0
+    b3.run(seed=21)
+    for i in range(len(probs)):
+        for ti in range(3):
+            assert torch.equal(b3.result(i, ti)[0], b.result(i, ti)[0]), (i, ti)
     b.close()
     b2.close()
+    b3.close()
 
 
 def test_batch_transients_vs_uniformization(mcx):
