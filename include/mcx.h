@@ -302,9 +302,10 @@ mcx_status mcx_estimate_level_difference(mcx_plan *plan, const double *v, double
  *   sem              float64 [n_entries] output, or NULL: sqrt(s^2 / R) with
  *                    s^2 the unbiased sample variance of the mu_r (0 if R = 1)
  * Device scratch of R * 16 * ceil(log2_points / 5) * 32 uint32 (digit tables
- * of the scrambled points) and, when n_entries * R < 77824, n_entries * R *
- * slices double pairs comes from the library's memory pool, stream-ordered.  The plan's copy of v is overwritten
- * as in mcx_estimate.  An invalid entry yields NaN and MCX_E_INVALID at
+ * of the scrambled points) and, when n_entries < 77824 (then a warp holds
+ * fewer than all replicates of its entry), n_entries * R * slices double
+ * pairs comes from the library's memory pool, stream-ordered.  The plan's copy
+ * of v is overwritten as in mcx_estimate.  An invalid entry yields NaN and MCX_E_INVALID at
  * mcx_sync; a non-finite result sets the overflow flag.
  * Errors: MCX_E_INVALID, MCX_E_CUDA, MCX_E_OOM.
  */
