@@ -25,3 +25,43 @@ def test_allocation_rejects_bad_input():
         mlmc.allocation([1.0], [1.0], 0.0)
     with pytest.raises(ValueError):
         mlmc.allocation([1.0, 2.0], [1.0], 0.1)
+
+
+class _FakePlan:
+    """Records the calls the driver makes and returns fixed per-level results."""
+
+    def __init__(self):
+        self.calls = []
+
+    def estimate(self, v, t, paths, entries=None, seed=0, path_offset=0, mode="exact", nsteps=1, prec="fp32"):
+        import torch
+
+        self.calls.append(("plain", nsteps, paths, path_offset, mode, seed))
+        return torch.tensor([10.0, 20.0]), torch.tensor([0.3, 0.4])
+
+    def estimate_level_difference(self, v, t, nsteps, paths, entries=None, seed=0, path_offset=0, mode="strang",
+                                  prec="fp32"):
+        import torch
+
+        self.calls.append(("diff", nsteps, paths, path_offset, mode, seed))
+        return torch.tensor([0.1 * nsteps, -0.01 * nsteps]), torch.tensor([0.01, 0.02])
+
+
+def test_driver_levels_offsets_and_combination():
+    torch = pytest.importorskip("torch")
+    plan = _FakePlan()
+    mean, sem, levels = mlmc.estimate(plan, None, 0.5, 4, 3, [1000, 500, 250, 125], seed=7, mode="lie")
+    assert plan.calls == [("plain", 4, 1000, 0, "lie", 7), ("diff", 8, 500, mlmc.LEVEL_STRIDE, "lie", 7),
+                          ("diff", 16, 250, 2 * mlmc.LEVEL_STRIDE, "lie", 7),
+                          ("diff", 32, 125, 3 * mlmc.LEVEL_STRIDE, "lie", 7)]
+    assert torch.allclose(mean, torch.tensor([10.0 + 0.1 * (8 + 16 + 32), 20.0 - 0.01 * (8 + 16 + 32)]))
+    assert torch.allclose(sem, torch.tensor([math.sqrt(0.09 + 3e-4), math.sqrt(0.16 + 3 * 4e-4)]))
+    assert len(levels) == 4
+
+
+def test_driver_rejects_exact_and_bad_sizes():
+    pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        mlmc.estimate(_FakePlan(), None, 0.5, 4, 1, [10, 10], mode="exact")
+    with pytest.raises(ValueError):
+        mlmc.estimate(_FakePlan(), None, 0.5, 4, 2, [10, 10])
