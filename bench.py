@@ -1081,6 +1081,22 @@ def main():
         cpu = {"value": rate, "unit": "paths/s", "cores": cores, "kind": "oracle", "sample": sample,
                "seconds": round(secs, 2)}
 
+    # measured random-gather ceiling (32-byte sectors): a buffer of the graph's working set
+    # (node records + columns, L2-resident here) and one far larger than L2, with dependent
+    # chains as the walkers' jumps are and with independent loads; outside the timed region
+    gather = None
+    try:
+        ws = 32 * n + 4 * nnz
+        rates = {}
+        for tag, nbytes in (("working_set", ws), ("hbm", 8 << 30)):
+            for dep in (True, False):
+                rates[f"{tag}_{'dependent' if dep else 'independent'}_gbs"] = \
+                    P.gather_rate(nbytes, dependent=dep, loads=1 << 31) * 32 / 1e9
+        gather = {"working_set_mb": round(ws / 2 ** 20, 1), **{k: round(v, 1) for k, v in rates.items()},
+                  "frac_of_working_set_dependent": achieved / rates["working_set_dependent_gbs"]}
+    except Exception as exc:  # the ceiling is context; its failure must not lose the line
+        gather = {"error": str(exc)[:200]}
+
     line = {
         "metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -1092,7 +1108,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic, "peak_source": peak_src,
                      "kernel": "k_walk (estimate launch)", "bytes_per_jump": BYTES_PER_JUMP,
-                     "algorithmic_bytes": walk_bytes},
+                     "algorithmic_bytes": walk_bytes, "gather_ceiling": gather},
         "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": None, "clocks": clk.summary(),
     }
     # per step: prep (rows, scan tiles, scan sums, scan add, fill) + power iteration (init, long-row

@@ -268,6 +268,23 @@ mcx_status mcx_estimate_level_difference(mcx_plan *plan, const double *v, double
                                          uint64_t seed, uint64_t path_offset, int precision, double *mean,
                                          double *sem, void *stream);
 
+/*
+ * Random-gather ceiling (a measurement for the walkers' roofline: every jump of
+ * Sec. 3's path sampler is two gathers, the drawn column and the new state's
+ * record, each a random 32-byte sector).  Returns in *sectors_per_second the
+ * rate at which this GPU serves `loads` loads of random sectors from a device
+ * buffer of `buffer_bytes` (allocated from the library's pool, filled and
+ * freed inside the call; 1 MiB <= buffer_bytes <= 128 GiB and fewer than 2^32
+ * sectors).  dependent = 1: each thread's next sector depends on the word it
+ * loaded (chains of dependent loads, as a walker's jumps are); dependent = 0:
+ * independent loads.  One warm-up launch, then one launch timed with CUDA
+ * events on `stream`; synchronises the stream.  A buffer that fits in L2
+ * measures L2, one far larger than L2 measures HBM.
+ * Errors: MCX_E_INVALID, MCX_E_OOM, MCX_E_CUDA.
+ */
+mcx_status mcx_gather_rate(uint64_t buffer_bytes, int dependent, uint64_t loads, double *sectors_per_second,
+                           void *stream);
+
 /* Largest log2 of the points per replicate of mcx_estimate_rqmc. */
 #define MCX_QMC_MAX_LOG2 24
 /* Sobol' dimensions of mcx_estimate_rqmc: holding time and slot of the first 8 events. */

@@ -8,13 +8,14 @@ package is the thin Python binding (ctypes) used by the tests and benchmark.
 from . import _lib
 from ._lib import EXPORTS, MCXError, load
 
-__all__ = ["EXPORTS", "MCXError", "load", "Plan", "power_iteration", "expm_multiply", "Batch", "MLP", "cv_prepare", "cv_targets", "cv_coefficients"]
+__all__ = ["EXPORTS", "MCXError", "load", "Plan", "power_iteration", "expm_multiply", "Batch", "MLP", "cv_prepare", "cv_targets", "cv_coefficients", "gather_rate"]
 
 
 def __getattr__(name):
     # the torch-facing API is imported lazily so that loading the C library
     # (and checking its exports) does not require a GPU
-    if name in ("Plan", "power_iteration", "expm_multiply", "Batch", "MLP", "cv_prepare", "cv_targets", "cv_coefficients"):
+    if name in ("Plan", "power_iteration", "expm_multiply", "Batch", "MLP", "cv_prepare", "cv_targets", "cv_coefficients",
+                "gather_rate"):
         from . import api
 
         return getattr(api, name)

@@ -290,6 +290,16 @@ class Plan:
             pass
 
 
+def gather_rate(buffer_bytes: int, dependent: bool = True, loads: int = 1 << 31, stream=None) -> float:
+    """Random 32-byte-sector gathers per second from a device buffer of `buffer_bytes`
+    (dependent chains as in the walkers, or independent loads): the measured
+    gather roofline, from L2 for a buffer that fits in it, from HBM otherwise."""
+    out = C.c_double(0.0)
+    check(_lib.load().mcx_gather_rate(int(buffer_bytes), 1 if dependent else 0, int(loads), C.byref(out),
+                                      _stream(stream)), "mcx_gather_rate")
+    return out.value
+
+
 def power_iteration(row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, max_iters: int = 1000,
                     tol: float = 1e-12, work: torch.Tensor | None = None, stream=None):
     """lambda_max of a symmetric A >= 0 by the power method on the GPU (Sec. 6: beta = 1/lambda_max).
