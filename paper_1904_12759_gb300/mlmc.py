@@ -52,3 +52,36 @@ def estimate(plan, v, t: float, n0: int, levels: int, paths, entries=None, seed:
     mean = torch.stack([m for m, _ in per_level]).sum(dim=0)
     sem = torch.stack([s * s for _, s in per_level]).sum(dim=0).sqrt()
     return mean, sem, per_level
+
+
+PILOT_OFFSET = 1 << 39  # pilot samples of level l use paths l 2^40 + 2^39 + p (disjoint from the run's)
+
+
+def adaptive(plan, v, t: float, n0: int, levels: int, eps: float, pilot_paths: int = 10000, costs=None,
+             entries=None, seed: int = 0, mode: str = "strang", prec: str = "fp32"):
+    """Giles' multilevel method with a pilot: per level, `pilot_paths` samples give the
+    per-sample variance V_l (mean over the entries of M SE^2); the allocation for a
+    sampling error eps (per entry, root mean square over entries) uses the costs
+    C_l (default: equal, since a walker's cost does not depend on the step count);
+    then the multilevel estimate with those sample sizes on fresh paths.
+    Returns (mean, sem, per_level, sizes)."""
+    if mode not in ("strang", "lie"):
+        raise ValueError("multilevel estimates need the STRANG or LIE functional")
+    if pilot_paths < 2:
+        raise ValueError("the pilot needs at least two samples per level")
+    V = []
+    for lvl in range(levels + 1):
+        off = lvl * LEVEL_STRIDE + PILOT_OFFSET
+        if lvl == 0:
+            _, s = plan.estimate(v, t, int(pilot_paths), entries=entries, seed=seed, path_offset=off, mode=mode,
+                                 nsteps=n0, prec=prec)
+        else:
+            _, s = plan.estimate_level_difference(v, t, n0 << lvl, int(pilot_paths), entries=entries, seed=seed,
+                                                  path_offset=off, mode=mode, prec=prec)
+        V.append(float((s * s).mean()) * pilot_paths)
+    C = list(costs) if costs is not None else [1.0] * (levels + 1)
+    sizes = allocation(V, C, eps)
+    if max(sizes) > PILOT_OFFSET:
+        raise ValueError("the allocation exceeds 2^39 samples on a level")
+    mean, sem, per_level = estimate(plan, v, t, n0, levels, sizes, entries=entries, seed=seed, mode=mode, prec=prec)
+    return mean, sem, per_level, sizes

@@ -65,3 +65,20 @@ def test_driver_rejects_exact_and_bad_sizes():
         mlmc.estimate(_FakePlan(), None, 0.5, 4, 1, [10, 10], mode="exact")
     with pytest.raises(ValueError):
         mlmc.estimate(_FakePlan(), None, 0.5, 4, 2, [10, 10])
+
+
+def test_adaptive_pilot_then_allocation():
+    torch = pytest.importorskip("torch")
+    plan = _FakePlan()
+    mean, sem, levels, sizes = mlmc.adaptive(plan, None, 0.5, 2, 2, eps=0.01, pilot_paths=100, seed=3)
+    pilot, run = plan.calls[:3], plan.calls[3:]
+    assert [c[0] for c in pilot] == ["plain", "diff", "diff"] and [c[1] for c in pilot] == [2, 4, 8]
+    assert all(c[2] == 100 for c in pilot)
+    assert [c[3] for c in pilot] == [mlmc.PILOT_OFFSET, mlmc.LEVEL_STRIDE + mlmc.PILOT_OFFSET,
+                                     2 * mlmc.LEVEL_STRIDE + mlmc.PILOT_OFFSET]
+    # pilot variances: mean SE^2 x 100 -> level 0: (0.09 + 0.16)/2 x 100, levels 1, 2: (1e-4 + 4e-4)/2 x 100
+    V = [12.5, 0.025, 0.025]
+    assert sizes == mlmc.allocation(V, [1.0, 1.0, 1.0], 0.01)
+    assert [c[2] for c in run] == sizes and [c[3] for c in run] == [0, mlmc.LEVEL_STRIDE, 2 * mlmc.LEVEL_STRIDE]
+    with pytest.raises(ValueError):
+        mlmc.adaptive(plan, None, 0.5, 2, 2, eps=0.01, pilot_paths=1)
