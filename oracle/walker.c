@@ -28,7 +28,8 @@
  * counter = {event k, entry i, path lo32, path hi32}.  Word 0 (and word 1 in
  * FP64) gives the holding-time uniform, word 2 the slot in the row, word 3 the
  * alias acceptance.  The randomised-QMC estimator replaces words 0 and 2 of the
- * first events by scrambled Sobol' coordinates (see below).
+ * first events by scrambled Sobol' coordinates (see below); the multilevel
+ * level difference runs each path twice, at N and N/2 steps, on the same draws.
  */
 #include <math.h>
 #include <stdint.h>
