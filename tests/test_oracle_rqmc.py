@@ -219,3 +219,28 @@ def test_rqmc_unbiased_on_weighted_rows():
     assert np.mean(np.abs(z) > 3.5) <= 0.06 and abs(z.mean()) < 0.5
     _, sem_mc, _ = g.estimate(v, t, 16 << 6, seed=12)
     assert np.mean(sem ** 2) < np.mean(sem_mc ** 2)
+
+
+def test_first_event_jointly_stratified_on_a_star():
+    """Entry 0 of a star with four absorbing leaves (rate 4, t = ln 2 / 4): a path
+    jumps iff its first holding word falls in the half [0, 1/2) of dimension 0, and
+    its leaf is the quarter of dimension 1 its slot word falls in.  Dimensions 0 and
+    1 form a (0, m, 2)-net (kept by the scramble and the shift), so each box
+    [0, 1/2) x [k/4, (k+1)/4) holds exactly 2^m / 8 of a replicate's points: half
+    the paths jump and each leaf receives exactly an eighth, with no sampling noise."""
+    a = np.zeros((5, 5))
+    a[0, 1:] = 1.0
+    csr = W.dense_to_csr(a)
+    g = OW.Graph(csr)
+    t = math.log(2.0) / 4.0
+    m = 8
+    for r in range(4):
+        tr = g.trace_rqmc(t, 0, 31, m, r, 0, 1 << m)
+        jumped = tr["njumps"] == 1
+        assert int(jumped.sum()) == (1 << m) // 2, r
+        counts = np.bincount(tr["end"][jumped], minlength=5)[1:]
+        assert np.all(counts == (1 << m) // 8), (r, counts)
+    # the same number of plain Monte Carlo paths is not stratified (sensitivity of the check)
+    tp = g.trace(t, 0, 31, 0, 1 << m)
+    plain = np.bincount(tp["end"][tp["njumps"] == 1], minlength=5)[1:]
+    assert not np.all(plain == (1 << m) // 8)
