@@ -11,9 +11,13 @@ so that R(tau) = a tau^2 + b tau^3, a = A^3 v / 2 - 3 c3, b = A c3.
 
 The network: 5 node features -> 64 ReLU -> 64 ReLU -> 1, predicting
 y = log(x / T2); xhat = T2 exp(y).  Weights are used rounded to BF16 (round to
-nearest even), biases in full precision; everything else here is FP64, except
-that `forward(..., bf16_hidden=True)` takes the first hidden layer as the
-tensor-core inference does (FP32 multiply-adds, then BF16).
+nearest even), biases in full precision; everything else here is FP64.
+`forward_error_bound` states how far an implementation of the same network
+may land from this FP64 forward pass when it rounds each first-layer
+activation to BF16 once and accumulates in FP32 (a bound from the arithmetic,
+not a restatement of any implementation's operation order), and
+`forward_rounding_sigma` the typical size of that difference when the
+roundings are to nearest (independent errors, uniform over half an ulp).
 """
 from __future__ import annotations
 
@@ -86,35 +90,52 @@ def init_params(seed: int = 0):
     return p
 
 
-def _fma_chain_f32(X, W1, b1):
-    """z1 = b1 + x_0 W1[0] + ... + x_4 W1[4] as FP32 fused multiply-adds in that
-    order (the inference kernel's precision and order).  Each FMA is emulated in
-    FP64: the product of two FP32 numbers is exact there, the sum is rounded to
-    FP64 and then to FP32 (the two roundings differ from one only when the FP64
-    result lands exactly on an FP32 tie)."""
-    a = np.broadcast_to(np.asarray(b1, np.float32), (X.shape[0], W1.shape[1])).copy()
-    Xf = np.asarray(X, np.float32).astype(np.float64)
-    for q in range(W1.shape[0]):
-        a = (Xf[:, q:q + 1] * W1[q].astype(np.float64) + a.astype(np.float64)).astype(np.float32)
-    return a
-
-
-def forward(p, X, round_weights=True, bf16_hidden=False):
-    """MLP forward in FP64 (weights rounded to BF16 when round_weights); X standardised.
-    bf16_hidden: the first hidden layer as the tensor-core inference computes it,
-    FP32 multiply-adds then ReLU and rounding to BF16; the rest in FP64."""
+def forward(p, X, round_weights=True):
+    """MLP forward in FP64 (weights rounded to BF16 when round_weights); X standardised."""
     W = {k: (bf16(v) if (round_weights and k[0] == "W") else v).astype(np.float64) for k, v in p.items()}
-    if bf16_hidden:
-        Wf = bf16(p["W1"]) if round_weights else np.asarray(p["W1"], np.float32)
-        z1 = _fma_chain_f32(X, Wf, p["b1"]).astype(np.float64)
-        h1 = bf16(np.maximum(z1, 0.0).astype(np.float32)).astype(np.float64)
-    else:
-        z1 = X @ W["W1"] + W["b1"]
-        h1 = np.maximum(z1, 0.0)
+    z1 = X @ W["W1"] + W["b1"]
+    h1 = np.maximum(z1, 0.0)
     z2 = h1 @ W["W2"] + W["b2"]
     h2 = np.maximum(z2, 0.0)
     y = (h2 @ W["W3"] + W["b3"])[:, 0]
     return y, (X, z1, h1, z2, h2, W)
+
+
+# unit roundoffs 2^-p of round to nearest: BF16 (p = 8 significand bits) and FP32 (p = 24)
+U_BF16 = 2.0 ** -8
+U_FP32 = 2.0 ** -24
+
+
+def forward_error_bound(p, X):
+    """Per-sample bound on |y' - y| between the FP64 forward pass y (BF16 weights) and
+    any evaluation y' of the same network that
+      - computes the first layer z1 in FP32 (6 terms: |e1| <= 2^-21 (|b1| + |X||W1|)),
+      - rounds each ReLU(z1) to BF16 once (relative error <= 2^-8),
+      - accumulates the 64 -> 64 layer in FP32 in any order, allowing a non-IEEE
+        accumulator (taken as 2^-16 of the sum of magnitudes, 4x the IEEE bound 64 u),
+      - accumulates the 64 -> 1 output layer in FP32 (65 terms: <= 2^-17.9).
+    ReLU is 1-Lipschitz, so errors propagate through |W2| and |W3|.  Standard
+    forward-error analysis (Higham, Accuracy and Stability of Numerical
+    Algorithms, 2nd ed., Sec. 3.1: |fl(sum) - sum| <= gamma_k sum |terms|)."""
+    y, (X, z1, h1, z2, h2, W) = forward(p, X, round_weights=True)
+    A1, A2, A3 = np.abs(W["W1"]), np.abs(W["W2"]), np.abs(W["W3"])
+    e1 = 2.0 ** -21 * (np.abs(W["b1"]) + np.abs(X) @ A1)            # FP32 first layer
+    dh1 = (1.0 + U_BF16) * e1 + U_BF16 * np.abs(h1)                 # + one BF16 rounding
+    dz2 = dh1 @ A2 + 2.0 ** -16 * ((np.abs(h1) + dh1) @ A2 + np.abs(W["b2"]))
+    dy = (dz2 @ A3)[:, 0] + 2.0 ** -17 * (np.abs(W["b3"][0]) + ((np.abs(h2) + dz2) @ A3)[:, 0])
+    return dy + 1e-12
+
+
+def forward_rounding_sigma(p, X):
+    """Standard deviation of the output change when every first-layer activation h1_k is
+    rounded to the nearest BF16 value, the errors taken as independent and uniform over
+    half an ulp (ulp = 2^(floor(log2 h1_k) - 7), variance ulp^2 / 12), to first order:
+    dy = sum_k dh1_k g_k with g_k = dy/dh1_k = sum_j W2_kj [z2_j > 0] W3_j."""
+    y, (X, z1, h1, z2, h2, W) = forward(p, X, round_weights=True)
+    g = (W["W2"][None, :, :] * (z2 > 0)[:, None, :] * W["W3"][:, 0][None, None, :]).sum(-1)
+    pos = h1 > 0
+    ulp = np.where(pos, np.exp2(np.floor(np.log2(np.where(pos, h1, 1.0))) - 7), 0.0)
+    return np.sqrt(((ulp * g) ** 2).sum(1) / 12.0) + 1e-12
 
 
 def loss_and_grad(p, X, target, round_weights=True):

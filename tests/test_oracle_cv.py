@@ -127,26 +127,49 @@ def test_features_shapes_and_values():
     assert np.allclose(T2, v + 0.05 * T[1] + 0.05 ** 2 * T[2] / 2)
 
 
-def test_bf16_hidden_forward_exact_cases():
-    """With inputs, weights and biases on a coarse binary grid every FP32 multiply-add
-    and the BF16 rounding of the first layer are exact, so the tensor-core form of the
-    forward pass equals the plain one; off the grid it differs by BF16 rounding only."""
+def _fp32_bf16_forward(p, X, order=1):
+    """A test-local evaluation inside the model the bound covers: FP32 first layer,
+    one BF16 rounding of each hidden activation, FP32 sums in the given order."""
+    Wb = {k: (CV.bf16(v) if k[0] == "W" else np.asarray(v, np.float32)) for k, v in p.items()}
+    Xf = np.asarray(X, np.float32)
+    z1 = Xf[:, ::order] @ Wb["W1"][::order] + Wb["b1"]
+    h1 = CV.bf16(np.maximum(z1, 0).astype(np.float32))
+    z2 = h1[:, ::order] @ Wb["W2"][::order] + Wb["b2"]
+    h2 = np.maximum(z2, 0).astype(np.float32)
+    return (h2[:, ::order] @ Wb["W3"][::order] + Wb["b3"])[:, 0].astype(np.float64)
+
+
+def test_forward_error_bound_covers_bf16_hidden_and_fp32_sums():
+    """The bound of one BF16 rounding per first-layer activation plus FP32 accumulation
+    holds for FP32/BF16 evaluations in two summation orders, on several networks; the
+    mean square of the difference in units of forward_rounding_sigma is 1 (to sampling
+    error), while rounding toward zero instead of to nearest gives more than 2; a dropped
+    bias, a transposed hidden weight or a missing ReLU exceeds the elementwise bound."""
     rng = np.random.default_rng(4)
-    p = CV.init_params(2)
-    # W1 and b1 on multiples of 1/4, X on multiples of 1/2 in [-3, 3]: |z1| < 20 on
-    # multiples of 1/8, at most 8 significant bits, so BF16 holds it exactly
-    q = {k: (np.round(v * 4) / 4).astype(np.float32) for k, v in p.items()}
-    X = np.clip(np.round(rng.normal(size=(40, CV.N_FEATURES)) * 2) / 2, -3, 3)
-    assert np.abs(q["W1"]).max() <= 1.25
-    y0, _ = CV.forward(q, X, round_weights=True)
-    y1, _ = CV.forward(q, X, round_weights=True, bf16_hidden=True)
-    assert np.array_equal(y0, y1)
-    X = rng.normal(size=(300, CV.N_FEATURES)).astype(np.float32).astype(np.float64)
-    y0, (_, z1, h1, _, _, W) = CV.forward(p, X, round_weights=True)
-    y1, _ = CV.forward(p, X, round_weights=True, bf16_hidden=True)
-    # one BF16 rounding of every hidden activation: |dy| <= 2^-9 |h1| |W2| |W3| (row sums)
-    bound = 2.0 ** -9 * (np.abs(h1) @ np.abs(W["W2"]) @ np.abs(W["W3"]))[:, 0] + 1e-12
-    assert np.all(np.abs(y1 - y0) <= bound) and np.any(y1 != y0)
+    for seed in range(4):
+        p = CV.init_params(seed)
+        X = rng.normal(size=(1000, CV.N_FEATURES)).astype(np.float32).astype(np.float64)
+        y, _ = CV.forward(p, X)
+        bound = CV.forward_error_bound(p, X)
+        sig = CV.forward_rounding_sigma(p, X)
+        for order in (1, -1):
+            d = _fp32_bf16_forward(p, X, order) - y
+            assert np.all(np.abs(d) <= bound)
+            assert 0.8 < np.mean((d / sig) ** 2) < 1.25
+        # the same evaluation with the activations truncated to BF16 (round toward zero)
+        Wb = {k: (CV.bf16(v) if k[0] == "W" else np.asarray(v, np.float32)) for k, v in p.items()}
+        z1 = np.asarray(X, np.float32) @ Wb["W1"] + Wb["b1"]
+        h1 = (np.maximum(z1, 0).astype(np.float32).view(np.uint32) & 0xFFFF0000).view(np.float32)
+        yt = (np.maximum(h1 @ Wb["W2"] + Wb["b2"], 0) @ Wb["W3"] + Wb["b3"])[:, 0]
+        assert np.mean(((yt - y) / sig) ** 2) > 2.0
+        # plausible mistakes are detected
+        q = dict(p, b2=np.zeros_like(p["b2"]))
+        assert np.any(np.abs(_fp32_bf16_forward(q, X) - y) > bound)
+        q = dict(p, W2=np.ascontiguousarray(p["W2"].T))
+        assert np.any(np.abs(_fp32_bf16_forward(q, X) - y) > bound)
+        Wb = {k: CV.bf16(v).astype(np.float64) if k[0] == "W" else v.astype(np.float64) for k, v in p.items()}
+        no_relu = ((X @ Wb["W1"] + Wb["b1"]) @ Wb["W2"] + Wb["b2"]).clip(0) @ Wb["W3"] + Wb["b3"]
+        assert np.any(np.abs(no_relu[:, 0] - y) > bound)
 
 
 def test_features_and_taylor_terms_brute_force():
