@@ -75,7 +75,10 @@ typedef enum { MCX_EXACT = 0, MCX_STRANG = 1, MCX_LIE = 2 } mcx_functional;
 
 /* MCX_FP32: holding times, remaining time and logW in FP32 (per-path log
  *           scaling); weights accumulated with compensated FP32 sums per lane
- *           and FP64 across lanes.  The production path.
+ *           and FP64 across lanes.  v enters as an FP32 copy scaled by the
+ *           power of two 2^-k, k the binary exponent of max |v_i| (exact), and
+ *           results are scaled back by 2^k, so any scale of v within the FP64
+ *           range gives the same relative accuracy.  The production path.
  * MCX_FP64: every per-path quantity in FP64.  The reference path version. */
 typedef enum { MCX_FP32 = 0, MCX_FP64 = 1 } mcx_precision;
 

@@ -106,15 +106,16 @@ struct Acc64 {
     }
 };
 
-// mean and standard error from shifted sums over M paths
-__device__ __forceinline__ void finish_entry(double s1, double s2, double m, double M, double *mean, double *sem,
-                                             uint32_t *status) {
+// mean and standard error from shifted sums over M paths, times vs (the power
+// of two the FP32 copy of v was scaled by, 1 for FP64 paths)
+__device__ __forceinline__ void finish_entry(double s1, double s2, double m, double M, double vs, double *mean,
+                                             double *sem, uint32_t *status) {
     const double scale = exp(m);
     const double mu = s1 / M;
     double var = M > 1.0 ? (s2 - s1 * mu) / (M - 1.0) : 0.0;
     if (var < 0.0) var = 0.0;
-    const double mv = scale * mu;
-    const double se = scale * sqrt(var / M);
+    const double mv = scale * mu * vs;
+    const double se = scale * sqrt(var / M) * vs;
     *mean = mv;
     if (sem) *sem = se;
     if (!isfinite(mv) || !isfinite(se)) atomicOr(status, ST_OVERFLOW);

@@ -117,8 +117,8 @@ mcx_status mcx_plan_create(int64_t n, int64_t nnz, const int64_t *row_ptr, const
         const size_t nn = (size_t)(n > 0 ? n : 1);
         if ((e = pool_alloc(reinterpret_cast<void **>(&p->node), sizeof(NodeRec) * nn, st)) != cudaSuccess) { rc = from_cuda(e); break; }
         if ((e = pool_alloc(reinterpret_cast<void **>(&p->node64), sizeof(NodeRec64) * nn, st)) != cudaSuccess) { rc = from_cuda(e); break; }
-        if ((e = pool_alloc(reinterpret_cast<void **>(&p->status), 32, st)) != cudaSuccess) { rc = from_cuda(e); break; }
-        if ((e = cudaMemsetAsync(p->status, 0, 32, st)) != cudaSuccess) { rc = from_cuda(e); break; }
+        if ((e = pool_alloc(reinterpret_cast<void **>(&p->status), 4 * STATUS_WORDS, st)) != cudaSuccess) { rc = from_cuda(e); break; }
+        if ((e = cudaMemsetAsync(p->status, 0, 4 * STATUS_WORDS, st)) != cudaSuccess) { rc = from_cuda(e); break; }
         p->device_bytes = (int64_t)((sizeof(NodeRec) + sizeof(NodeRec64)) * nn + 16);
         const int64_t *rp = row_ptr;
         const int32_t *cc = col;
@@ -387,11 +387,11 @@ mcx_status mcx_plan_export(const mcx_plan *p, int32_t *deg, int64_t *row_start, 
 mcx_status mcx_sync(mcx_plan *p, void *stream, mcx_stats *stats) {
     if (!p) return MCX_E_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    uint32_t hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    cudaError_t e = cudaMemcpyAsync(hs, p->status, 32, cudaMemcpyDeviceToHost, st);
+    uint32_t hs[STATUS_SYNC_WORDS] = {0, 0, 0, 0, 0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(hs, p->status, 4 * STATUS_SYNC_WORDS, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return from_cuda(e);
-    e = cudaMemsetAsync(p->status, 0, 32, st);
+    e = cudaMemsetAsync(p->status, 0, 4 * STATUS_SYNC_WORDS, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return from_cuda(e);
     if (stats) {

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(WALK_THREADS, 5) k_batch_walk(const __grid_con
             if (COUNT) {
                 atomicAdd(b.count + slot, 1ull);
             } else {
-                const double y = V * (double)expf(w.acc);
+                const double y = V * exp((double)w.acc);
                 atomicAdd(b.sum1 + slot, y);
                 atomicAdd(b.sum2 + slot, y * y);
             }
@@ -255,7 +255,7 @@ __global__ void k_batch_finish(const BatchPT *__restrict__ pts, BatchArgs b, dou
         if (var < 0.0) var = 0.0;
         x[s] = mu;
         sem[s] = sqrt(var / M);
-        if (!isfinite(mu)) atomicOr(status, ST_OVERFLOW);
+        if (!isfinite(mu) || !isfinite(var)) atomicOr(status, ST_OVERFLOW);
     }
     if (*b.bad && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_BAD_V);
 }

@@ -71,6 +71,23 @@ constexpr uint32_t ST_NONFINITE = 8u;
 constexpr uint32_t ST_BAD_ENTRY = 16u;
 constexpr uint32_t ST_BAD_V = 32u;
 
+// Status words: the first STATUS_SYNC_WORDS are read and cleared by mcx_sync.
+constexpr int STATUS_SYNC_WORDS = 8;
+constexpr int STATUS_WORDS = 16;
+constexpr int STATUS_VEXP = 8;
+constexpr uint32_t VEXP_BIAS = 2048u;
+
+// The FP32 node records hold v scaled by a power of two, v * 2^-k with k the
+// binary exponent of the largest finite |v_i| (so |v| < 2 there): the per-path
+// weights and their squares then stay inside the FP32 range whatever the scale
+// of v, and the scaling is exact.  k is kept in status word STATUS_VEXP as
+// k + VEXP_BIAS (0 when v has no nonzero finite entry, k = 0); results of FP32
+// paths are multiplied by 2^k when they are finished.
+__device__ __forceinline__ double v_scale(const uint32_t *status) {
+    const uint32_t e = status[STATUS_VEXP];
+    return e ? ldexp(1.0, (int)e - (int)VEXP_BIAS) : 1.0;
+}
+
 }  // namespace mcx
 
 struct mcx_plan {
@@ -85,6 +102,7 @@ struct mcx_plan {
     int32_t *edge_col = nullptr;       // [nnz_off]
     mcx::Edge16 *edge16 = nullptr;     // [nnz_off] if weighted_rows > 0 (packed column + alias table)
     uint32_t *status = nullptr;        // device words: [0] status bits, [2..3] paths (u64), [4..5] jumps (u64)
+                                       // (cleared by mcx_sync); [8] exponent of the FP32 copy of v (see v_scale)
     void *scratch = nullptr;           // grow-only scratch for chunk partials
     size_t scratch_bytes = 0;
     void *fwd = nullptr;               // forward-form scratch (start tables, deposits), made on first use

@@ -135,8 +135,8 @@ __global__ void __launch_bounds__(WALK_THREADS, F64 ? WALK_MIN_BLOCKS_F64 : WALK
 // One warp per entry: merge its chunk partials in chunk order, then mean and
 // standard error.
 __global__ void __launch_bounds__(WALK_THREADS) k_reduce_diff(const Partial *__restrict__ part, int64_t n_entries,
-                                                             uint32_t cpe, double M, double *mean, double *sem,
-                                                             uint32_t *status) {
+                                                             uint32_t cpe, double M, bool v_scaled, double *mean,
+                                                             double *sem, uint32_t *status) {
     const int lane = threadIdx.x & 31;
     const int64_t e = ((int64_t)blockIdx.x * WALK_THREADS + threadIdx.x) >> 5;
     if (e >= n_entries) return;
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_reduce_diff(const Partial *__r
             mean[e] = QNAN;
             if (sem) sem[e] = QNAN;
         } else {
-            finish_entry(s1, s2, m, M, mean + e, sem ? sem + e : nullptr, status);
+            finish_entry(s1, s2, m, M, v_scaled ? v_scale(status) : 1.0, mean + e, sem ? sem + e : nullptr, status);
         }
     }
 }
@@ -219,8 +219,8 @@ cudaError_t launch_level_difference(mcx_plan *plan, const EstimateArgs &a, cudaS
                      : launch_diff_mode<false, false>(a.mode, grid, p, d, st);
     if (e == cudaSuccess) {
         const unsigned g2 = (unsigned)((a.n_entries + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
-        k_reduce_diff<<<g2, WALK_THREADS, 0, st>>>(d.part, a.n_entries, (uint32_t)cpe, (double)a.paths, a.mean,
-                                                   a.sem, plan->status);
+        k_reduce_diff<<<g2, WALK_THREADS, 0, st>>>(d.part, a.n_entries, (uint32_t)cpe, (double)a.paths,
+                                                   a.precision != MCX_FP64, a.mean, a.sem, plan->status);
         e = cudaGetLastError();
     }
     pool_free(part, st);

@@ -454,7 +454,7 @@ __global__ void __launch_bounds__(WALK_THREADS, F64 ? WALK_MIN_BLOCKS_F64 : MCX_
                 if (a.sem) a.sem[e] = QNAN;
             } else {
                 const double R = f[4], sd = f[2];
-                const double scale = exp(mref);
+                const double scale = exp(mref) * (F64 ? 1.0 : v_scale(a.status));
                 const double mv = scale * (f[1] + sd / R);
                 double var = R > 1.0 ? (f[3] - sd * sd / R) / (R - 1.0) : 0.0;
                 if (var < 0.0) var = 0.0;
@@ -483,7 +483,8 @@ __device__ __forceinline__ void replicate_sum(const double2 *pp, uint32_t slices
 __global__ void __launch_bounds__(WALK_THREADS) k_rqmc_finish(const double2 *__restrict__ part,
                                                              const int32_t *__restrict__ entries, int64_t n,
                                                              int64_t n_entries, uint32_t R, uint32_t slices, double Qn,
-                                                             double *mean, double *sem, uint32_t *status) {
+                                                             bool v_scaled, double *mean, double *sem,
+                                                             uint32_t *status) {
     const int lane = threadIdx.x & 31;
     const int64_t e = ((int64_t)blockIdx.x * WALK_THREADS + threadIdx.x) >> 5;
     if (e >= n_entries) return;
@@ -519,7 +520,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_rqmc_finish(const double2 *__r
     }
     ss = warp_sum(ss);
     if (lane == 0) {
-        const double scale = M == -INFINITY ? 0.0 : exp(M);
+        const double scale = (M == -INFINITY ? 0.0 : exp(M)) * (v_scaled ? v_scale(status) : 1.0);
         const double mv = scale * mu;
         const double se = R > 1 ? scale * sqrt(ss / (double)(R - 1) / (double)R) : 0.0;
         mean[e] = mv;
@@ -609,7 +610,7 @@ cudaError_t launch_estimate_rqmc(mcx_plan *plan, const RqmcArgs &a, cudaStream_t
     if (e == cudaSuccess && !job.fused) {
         const unsigned g2 = (unsigned)((a.n_entries + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
         k_rqmc_finish<<<g2, WALK_THREADS, 0, st>>>(job.part, a.entries, plan->n, a.n_entries, a.replicates, slices,
-                                                   (double)Qn, a.mean, a.sem, plan->status);
+                                                   (double)Qn, a.precision != MCX_FP64, a.mean, a.sem, plan->status);
         e = cudaGetLastError();
     }
     if (tabs) pool_free(tabs, st);

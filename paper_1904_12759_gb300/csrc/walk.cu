@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(WALK_THREADS, F64 ? WALK_MIN_BLOCKS_F64 : WALK
                     if (a.sem) a.sem[e] = QNAN;
                 } else {
                     finish_entry(((volatile double *)s_fin[lane])[0], ((volatile double *)s_fin[lane])[1], m,
-                                 (double)a.paths, a.mean + e, a.sem ? a.sem + e : nullptr, a.status);
+                                 (double)a.paths, F64 ? 1.0 : v_scale(a.status), a.mean + e,
+                                 a.sem ? a.sem + e : nullptr, a.status);
                 }
             }
         }
@@ -162,10 +163,11 @@ __global__ void __launch_bounds__(WALK_THREADS, F64 ? WALK_MIN_BLOCKS_F64 : WALK
     }
 }
 
-// One warp per entry: merge its chunk partials in chunk order.
+// One warp per entry: merge its chunk partials in chunk order (v_scaled: the
+// partials come from FP32 paths over the scaled copy of v).
 __global__ void __launch_bounds__(WALK_THREADS) k_reduce_chunks(const Partial *__restrict__ part, int64_t n_entries,
-                                                               uint32_t cpe, double M, double *mean, double *sem,
-                                                               uint32_t *status) {
+                                                               uint32_t cpe, double M, bool v_scaled, double *mean,
+                                                               double *sem, uint32_t *status) {
     const int lane = threadIdx.x & 31;
     const int64_t e = ((int64_t)blockIdx.x * WALK_THREADS + threadIdx.x) >> 5;
     if (e >= n_entries) return;
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_reduce_chunks(const Partial *_
     }
     s1 = warp_sum(s1);
     s2 = warp_sum(s2);
-    if (lane == 0) finish_entry(s1, s2, m, M, mean + e, sem ? sem + e : nullptr, status);
+    if (lane == 0) finish_entry(s1, s2, m, M, v_scaled ? v_scale(status) : 1.0, mean + e, sem ? sem + e : nullptr, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -222,7 +224,8 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_lanes(const __grid_consta
             paths = a.paths;
             double S1, S2, M;
             acc.lane_result(S1, S2, M);
-            finish_entry(S1, S2, M, (double)a.paths, a.mean + e, a.sem ? a.sem + e : nullptr, a.status);
+            finish_entry(S1, S2, M, (double)a.paths, F64 ? 1.0 : v_scale(a.status), a.mean + e,
+                         a.sem ? a.sem + e : nullptr, a.status);
         }
     }
 #pragma unroll
@@ -272,12 +275,28 @@ __global__ void k_trace_t0(int32_t i, uint32_t count, int32_t *end, uint32_t *nj
     logw[q] = 0.0;
 }
 
+// Exponent of the largest finite |v_i| into status word STATUS_VEXP (biased;
+// the word is cleared before the launch).
+__global__ void k_v_exponent(int64_t n, const double *__restrict__ v, uint32_t *status) {
+    uint32_t e = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = fabs(v[i]);
+        if (x > 0.0 && x <= 1.7976931348623157e308) e = max(e, (uint32_t)(ilogb(x) + (int)VEXP_BIAS));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 31) == 0 && e) atomicMax(status + STATUS_VEXP, e);
+}
+
+// v into the node records: FP64 as given, FP32 scaled by 2^-k (exact; see v_scale).
 __global__ void k_pack_v(int64_t n, const double *__restrict__ v, NodeRec *__restrict__ node,
-                         NodeRec64 *__restrict__ node64) {
+                         NodeRec64 *__restrict__ node64, const uint32_t *status) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    const uint32_t eb = status[STATUS_VEXP];
+    const int k = eb ? (int)eb - (int)VEXP_BIAS : 0;
     const double x = v[i];
-    node[i].v = __double2float_rn(x);
+    node[i].v = __double2float_rn(ldexp(x, -k));
     node64[i].v = x;
 }
 
@@ -426,7 +445,7 @@ __global__ void __launch_bounds__(WALK_THREADS, F64 ? WALK_MIN_BLOCKS_F64 : WALK
                 atomicAdd(o.count + w.j, 1ull);
             } else {
                 const T L = final_logw<MODE, F64>(w, delta_start, a);
-                const double y = V * (F64 ? exp((double)L) : (double)expf((float)L));
+                const double y = V * exp((double)L);  // FP64: finite for any FP32 log-weight below ~709
                 atomicAdd(o.sum1 + w.j, y);
                 atomicAdd(o.sum2 + w.j, y * y);
             }
@@ -557,7 +576,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_reduce_tc(const Partial *__res
             b += sh[w][1];
         }
         double mean, se;
-        finish_entry(a, b, m, M, &mean, &se, status);
+        finish_entry(a, b, m, M, 1.0, &mean, &se, status);
         const double V = *Vp;
         *tc = V * mean;
         if (sem) *sem = V * se;
@@ -590,7 +609,7 @@ __global__ void k_forward_finish(int64_t n, FwdOut o, const double *Vp, const ui
     if (var < 0.0) var = 0.0;
     x[i] = mu;
     if (sem) sem[i] = sqrt(var / M);
-    if (!isfinite(mu)) atomicOr(status, ST_OVERFLOW);
+    if (!isfinite(mu) || !isfinite(var)) atomicOr(status, ST_OVERFLOW);
 }
 
 template <int MODE, bool WEIGHTED, bool F64>
@@ -661,17 +680,42 @@ cudaError_t launch_trace_mode(int mode, unsigned grid, const WalkParams &p, int3
 
 cudaError_t launch_pack_v(mcx_plan *plan, const double *v, cudaStream_t st) {
     if (plan->n == 0) return cudaSuccess;
-    k_pack_v<<<(unsigned)((plan->n + 255) / 256), 256, 0, st>>>(plan->n, v, plan->node, plan->node64);
+    cudaError_t e = cudaMemsetAsync(plan->status + STATUS_VEXP, 0, 4, st);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)std::min<int64_t>((plan->n + 255) / 256, 152 * 8);
+    k_v_exponent<<<blocks, 256, 0, st>>>(plan->n, v, plan->status);
+    k_pack_v<<<(unsigned)((plan->n + 255) / 256), 256, 0, st>>>(plan->n, v, plan->node, plan->node64, plan->status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_estimate(mcx_plan *plan, const EstimateArgs &a, cudaStream_t st) {
-    if (a.n_entries == 0) return cudaSuccess;
-    if (a.t == 0.0) {
-        k_copy_v<<<(unsigned)((a.n_entries + 255) / 256), 256, 0, st>>>(a.entries, a.n_entries, plan->n,
-                                                                          plan->node64, a.mean, a.sem, plan->status);
-        return cudaGetLastError();
-    }
+namespace {
+
+// Chunking of an estimate over warps: at least 1024 paths per warp, and enough
+// warps to fill the GPU several times over (152 SMs x 64 resident warps x 8
+// waves); chunk lengths are multiples of 32 and below 2^30 paths (32-bit chunk
+// offsets).  Shared by mcx_estimate and mcx_estimate_noalloc, whose results
+// are therefore identical.
+struct Chunking {
+    uint64_t chunk;     // paths per warp
+    uint64_t cpe;       // chunks per entry
+    uint64_t n_chunks;  // n_entries * cpe
+};
+
+Chunking estimate_chunking(const EstimateArgs &a) {
+    const uint64_t target_warps = 152ull * 64ull * 8ull;
+    uint64_t cpe = (target_warps + (uint64_t)a.n_entries - 1) / (uint64_t)a.n_entries;
+    const uint64_t max_cpe = (a.paths + 1023) / 1024;
+    if (cpe > max_cpe) cpe = max_cpe;
+    if (cpe < 1) cpe = 1;
+    if ((a.paths + cpe - 1) / cpe > (1ull << 30)) cpe = (a.paths + (1ull << 30) - 1) >> 30;
+    uint64_t chunk = (a.paths + cpe - 1) / cpe;
+    chunk = (chunk + 31) / 32 * 32;
+    cpe = (a.paths + chunk - 1) / chunk;
+    return Chunking{chunk, cpe, (uint64_t)a.n_entries * cpe};
+}
+
+// Walk parameters of an estimate (t > 0).
+WalkParams estimate_params(mcx_plan *plan, const EstimateArgs &a) {
     WalkParams p = make_params(plan, a.t, a.mode == MCX_EXACT ? 1 : a.nsteps, a.seed);
     p.entries = a.entries;
     p.n_entries = a.n_entries;
@@ -679,42 +723,37 @@ cudaError_t launch_estimate(mcx_plan *plan, const EstimateArgs &a, cudaStream_t 
     p.path_offset = a.path_offset;
     p.mean = a.mean;
     p.sem = a.sem;
-    if (a.paths <= LANE_MODE_MAX_PATHS) {  // few paths per entry: one lane per entry
-        const unsigned grid = (unsigned)((a.n_entries + WALK_THREADS - 1) / WALK_THREADS);
-        const bool weighted = plan->weighted_rows > 0;
-        if (a.precision == MCX_FP64)
-            return weighted ? launch_lanes_mode<true, true>(a.mode, grid, p, st)
-                            : launch_lanes_mode<true, false>(a.mode, grid, p, st);
-        return weighted ? launch_lanes_mode<false, true>(a.mode, grid, p, st)
-                        : launch_lanes_mode<false, false>(a.mode, grid, p, st);
-    }
-    // Chunking: at least 1024 paths per warp, and enough warps to fill the GPU
-    // several times over (152 SMs x 64 resident warps x 8 waves).
-    const uint64_t target_warps = 152ull * 64ull * 8ull;
-    uint64_t cpe = (target_warps + (uint64_t)a.n_entries - 1) / (uint64_t)a.n_entries;
-    const uint64_t max_cpe = (a.paths + 1023) / 1024;
-    if (cpe > max_cpe) cpe = max_cpe;
-    if (cpe < 1) cpe = 1;
-    if ((a.paths + cpe - 1) / cpe > (1ull << 30)) cpe = (a.paths + (1ull << 30) - 1) >> 30;  // 32-bit chunk offsets
-    uint64_t chunk = (a.paths + cpe - 1) / cpe;
-    chunk = (chunk + 31) / 32 * 32;
-    cpe = (a.paths + chunk - 1) / chunk;
-    p.chunk_len = chunk;
-    p.chunks_per_entry = (uint32_t)cpe;
-    const uint64_t n_chunks = (uint64_t)a.n_entries * cpe;
-    if (cpe > 1) {
-        const size_t need = sizeof(Partial) * (size_t)n_chunks;
-        if (plan->scratch_bytes < need) {
-            cudaFree(plan->scratch);
-            plan->scratch = nullptr;
-            plan->scratch_bytes = 0;
-            cudaError_t e = cudaMalloc(&plan->scratch, need);
-            if (e != cudaSuccess) return e;
-            plan->scratch_bytes = need;
-        }
-        p.partials = static_cast<Partial *>(plan->scratch);
-    }
-    const unsigned grid = (unsigned)((n_chunks + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
+    return p;
+}
+
+// t = 0: the entries of v.
+cudaError_t launch_copy_v(mcx_plan *plan, const EstimateArgs &a, cudaStream_t st) {
+    k_copy_v<<<(unsigned)((a.n_entries + 255) / 256), 256, 0, st>>>(a.entries, a.n_entries, plan->n, plan->node64,
+                                                                      a.mean, a.sem, plan->status);
+    return cudaGetLastError();
+}
+
+// One lane per entry (at most LANE_MODE_MAX_PATHS paths): no partials.
+cudaError_t launch_lanes(mcx_plan *plan, const EstimateArgs &a, cudaStream_t st) {
+    const WalkParams p = estimate_params(plan, a);
+    const unsigned grid = (unsigned)((a.n_entries + WALK_THREADS - 1) / WALK_THREADS);
+    const bool weighted = plan->weighted_rows > 0;
+    if (a.precision == MCX_FP64)
+        return weighted ? launch_lanes_mode<true, true>(a.mode, grid, p, st)
+                        : launch_lanes_mode<true, false>(a.mode, grid, p, st);
+    return weighted ? launch_lanes_mode<false, true>(a.mode, grid, p, st)
+                    : launch_lanes_mode<false, false>(a.mode, grid, p, st);
+}
+
+// Warp per (entry, chunk) and, when entries span several chunks, the chunk
+// merge over `partials` (c.n_chunks of them).
+cudaError_t launch_chunks(mcx_plan *plan, const EstimateArgs &a, const Chunking &c, Partial *partials,
+                          cudaStream_t st) {
+    WalkParams p = estimate_params(plan, a);
+    p.chunk_len = c.chunk;
+    p.chunks_per_entry = (uint32_t)c.cpe;
+    p.partials = partials;
+    const unsigned grid = (unsigned)((c.n_chunks + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
     const bool weighted = plan->weighted_rows > 0;
     cudaError_t e;
     if (a.precision == MCX_FP64) {
@@ -723,13 +762,34 @@ cudaError_t launch_estimate(mcx_plan *plan, const EstimateArgs &a, cudaStream_t 
         e = weighted ? launch_walk_mode<false, true>(a.mode, grid, p, st) : launch_walk_mode<false, false>(a.mode, grid, p, st);
     }
     if (e != cudaSuccess) return e;
-    if (cpe > 1) {
+    if (c.cpe > 1) {
         const unsigned g2 = (unsigned)((a.n_entries + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
-        k_reduce_chunks<<<g2, WALK_THREADS, 0, st>>>(p.partials, a.n_entries, (uint32_t)cpe, (double)a.paths, a.mean,
-                                                    a.sem, plan->status);
+        k_reduce_chunks<<<g2, WALK_THREADS, 0, st>>>(partials, a.n_entries, (uint32_t)c.cpe, (double)a.paths,
+                                                    a.precision != MCX_FP64, a.mean, a.sem, plan->status);
         e = cudaGetLastError();
     }
     return e;
+}
+
+}  // namespace
+
+cudaError_t launch_estimate(mcx_plan *plan, const EstimateArgs &a, cudaStream_t st) {
+    if (a.n_entries == 0) return cudaSuccess;
+    if (a.t == 0.0) return launch_copy_v(plan, a, st);
+    if (a.paths <= LANE_MODE_MAX_PATHS) return launch_lanes(plan, a, st);
+    const Chunking c = estimate_chunking(a);
+    if (c.cpe > 1) {
+        const size_t need = sizeof(Partial) * (size_t)c.n_chunks;
+        if (plan->scratch_bytes < need) {
+            cudaFree(plan->scratch);
+            plan->scratch = nullptr;
+            plan->scratch_bytes = 0;
+            cudaError_t e = cudaMalloc(&plan->scratch, need);
+            if (e != cudaSuccess) return e;
+            plan->scratch_bytes = need;
+        }
+    }
+    return launch_chunks(plan, a, c, static_cast<Partial *>(plan->scratch), st);
 }
 
 namespace {
@@ -991,24 +1051,25 @@ static __device__ __align__(256) Partial g_noalloc_partials[NOALLOC_MAX_PARTIALS
 namespace {
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
-std::once_flag g_noalloc_once[NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mutex;
 Partial *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
-cudaError_t g_noalloc_err[NOALLOC_MAX_DEVICES];
 
 // Device address of g_noalloc_partials on the current device.  In host code the
-// array's name only stands for it, so the address is looked up once per device
-// (with that device current) and cached.
+// array's name only stands for it, so the address is looked up per device (with
+// that device current) and cached once the lookup has succeeded; a failed
+// lookup is returned and tried again on the next call.
 cudaError_t noalloc_partials(Partial **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::call_once(g_noalloc_once[dev], [dev]() {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (g_noalloc_ptr[dev] == nullptr) {
         void *ptr = nullptr;
-        g_noalloc_err[dev] = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
+        if (e != cudaSuccess) return e;
         g_noalloc_ptr[dev] = static_cast<Partial *>(ptr);
-    });
-    if (g_noalloc_err[dev] != cudaSuccess) return g_noalloc_err[dev];
+    }
     *out = g_noalloc_ptr[dev];
     return cudaSuccess;
 }
@@ -1021,18 +1082,9 @@ cudaError_t launch_estimate_noalloc(mcx_plan *plan, const double *v, const Estim
                                     bool *too_large) {
     *too_large = false;
     if (a.n_entries == 0) return cudaSuccess;
-    // same chunking as launch_estimate
-    const uint64_t target_warps = 152ull * 64ull * 8ull;
-    uint64_t cpe = (target_warps + (uint64_t)a.n_entries - 1) / (uint64_t)a.n_entries;
-    const uint64_t max_cpe = (a.paths + 1023) / 1024;
-    if (cpe > max_cpe) cpe = max_cpe;
-    if (cpe < 1) cpe = 1;
-    if ((a.paths + cpe - 1) / cpe > (1ull << 30)) cpe = (a.paths + (1ull << 30) - 1) >> 30;  // 32-bit chunk offsets
-    uint64_t chunk = (a.paths + cpe - 1) / cpe;
-    chunk = (chunk + 31) / 32 * 32;
-    cpe = (a.paths + chunk - 1) / chunk;
-    const uint64_t n_chunks = (uint64_t)a.n_entries * cpe;
-    if (a.t != 0.0 && cpe > 1 && n_chunks > NOALLOC_MAX_PARTIALS) {
+    const bool walk = a.t != 0.0 && a.paths > LANE_MODE_MAX_PATHS;
+    const Chunking c = estimate_chunking(a);
+    if (walk && c.cpe > 1 && c.n_chunks > NOALLOC_MAX_PARTIALS) {
         *too_large = true;  // rejected before anything is enqueued
         return cudaSuccess;
     }
@@ -1040,37 +1092,9 @@ cudaError_t launch_estimate_noalloc(mcx_plan *plan, const double *v, const Estim
     cudaError_t e = noalloc_partials(&partials);
     if (e != cudaSuccess) return e;
     if ((e = launch_pack_v(plan, v, st)) != cudaSuccess) return e;
-    if (a.t != 0.0 && a.paths <= LANE_MODE_MAX_PATHS) return launch_estimate(plan, a, st);  // lane layout: no scratch
-    if (a.t == 0.0) {
-        k_copy_v<<<(unsigned)((a.n_entries + 255) / 256), 256, 0, st>>>(a.entries, a.n_entries, plan->n,
-                                                                          plan->node64, a.mean, a.sem, plan->status);
-        return cudaGetLastError();
-    }
-    WalkParams p = make_params(plan, a.t, a.mode == MCX_EXACT ? 1 : a.nsteps, a.seed);
-    p.entries = a.entries;
-    p.n_entries = a.n_entries;
-    p.paths = a.paths;
-    p.path_offset = a.path_offset;
-    p.mean = a.mean;
-    p.sem = a.sem;
-    p.chunk_len = chunk;
-    p.chunks_per_entry = (uint32_t)cpe;
-    p.partials = partials;
-    const unsigned grid = (unsigned)((n_chunks + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
-    const bool weighted = plan->weighted_rows > 0;
-    if (a.precision == MCX_FP64) {
-        e = weighted ? launch_walk_mode<true, true>(a.mode, grid, p, st) : launch_walk_mode<true, false>(a.mode, grid, p, st);
-    } else {
-        e = weighted ? launch_walk_mode<false, true>(a.mode, grid, p, st) : launch_walk_mode<false, false>(a.mode, grid, p, st);
-    }
-    if (e != cudaSuccess) return e;
-    if (cpe > 1) {
-        const unsigned g2 = (unsigned)((a.n_entries + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
-        k_reduce_chunks<<<g2, WALK_THREADS, 0, st>>>(partials, a.n_entries, (uint32_t)cpe, (double)a.paths, a.mean,
-                                                    a.sem, plan->status);
-        e = cudaGetLastError();
-    }
-    return e;
+    if (a.t == 0.0) return launch_copy_v(plan, a, st);
+    if (!walk) return launch_lanes(plan, a, st);
+    return launch_chunks(plan, a, c, partials, st);
 }
 
 }  // namespace mcx

@@ -1,8 +1,9 @@
 """mcx_estimate_noalloc: the estimate for callers that cannot allocate device
 memory once they are running (a service that reserves its memory at start-up
 and must keep it fixed, or a host framework whose pool allocator owns the
-device memory).  It must give the same numbers as mcx_estimate, call after
-call, while keeping its scratch in the library's fixed device array.
+device memory).  It must give the same numbers as mcx_estimate, bit for bit,
+call after call, while keeping its scratch in the library's fixed device
+array, and agree with the oracle on the same paths.
 
 Called straight through the C-ABI (ctypes), with torch only providing device
 buffers allocated before the calls.
@@ -13,6 +14,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from oracle import walker as OW
 
 pytestmark = pytest.mark.gpu
 
@@ -36,7 +38,9 @@ def test_noalloc_matches_estimate_two_calls_in_a_row(prec):
     L = P.load()
     csr = W.erdos_renyi(3000, 8, 11)
     plan = P.Plan.from_csr(csr)
-    v = torch.as_tensor(W.uniform_vector(3000, 1, -1.0, 1.0)).cuda()
+    vh = W.uniform_vector(3000, 1, -1.0, 1.0)
+    v = torch.as_tensor(vh).cuda()
+    og = OW.Graph(csr)
     t = 0.12
     tol = 2e-6 if prec == 0 else 1e-12
     # (entries, paths): several chunks per entry, so the fixed scratch array is used;
@@ -55,10 +59,16 @@ def test_noalloc_matches_estimate_two_calls_in_a_row(prec):
             assert _call(L, "mcx_estimate", plan, v, t, M, ent, n_ent, seed, prec, ref_m, ref_s) == 0
             assert _call(L, "mcx_estimate_noalloc", plan, v, t, M, ent, n_ent, seed, prec, got_m, got_s) == 0
             torch.cuda.synchronize()
-            rm, gm = ref_m.cpu().numpy(), got_m.cpu().numpy()
-            scale = np.abs(rm).max()
-            assert np.all(np.abs(gm - rm) <= tol * scale), (M, call, np.abs(gm - rm).max() / scale)
-            assert np.allclose(got_s.cpu().numpy(), ref_s.cpu().numpy(), rtol=tol, atol=tol * scale)
+            # same kernels, same chunking, same reduction order: identical numbers
+            assert torch.equal(got_m, ref_m) and torch.equal(got_s, ref_s), (M, call)
+        # and the oracle's estimate over the same paths (last call's seed)
+        ent_np = np.arange(3000, dtype=np.int32) if ent is None else ent.cpu().numpy()
+        sel = slice(None) if ent_np.size <= 64 else slice(0, None, ent_np.size // 32)
+        om, osd, _ = og.estimate(vh, t, M, entries=ent_np[sel], seed=seed, prec="fp64" if prec else "fp32")
+        gm = got_m.cpu().numpy()[sel]
+        scale = og.estimate(np.abs(vh), t, M, entries=ent_np[sel], seed=seed, prec="fp64" if prec else "fp32")[0]
+        assert np.all(np.abs(gm - om) <= tol * scale), (M, np.max(np.abs(gm - om) / scale))
+        assert np.allclose(got_s.cpu().numpy()[sel], osd, rtol=1e-3)
     plan.sync()
     plan.close()
 
