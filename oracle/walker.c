@@ -84,34 +84,71 @@ static double unif_f64(uint32_t w0, uint32_t w1)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Natural logarithm by range reduction x = 2^e m, m in [1/sqrt2, sqrt2], and */
-/* the series ln m = 2 artanh(s) = 2 (s + s^3/3 + s^5/5 + ...), s = (m-1)/(m+1) */
-/* (Abramowitz & Stegun 4.1.27).  Valid for positive normal finite x.          */
+/* FP32 natural logarithm, table-driven (P. T. P. Tang, "Table-driven         */
+/* implementation of the logarithm function in IEEE floating-point            */
+/* arithmetic", ACM TOMS 16(4), 1990), with no division.  Write x = 2^E M,    */
+/* M in [1, 2).  The breakpoints are c_j = 1 + j/64, j = 0..64; j is the one  */
+/* nearest M (the top six mantissa bits, rounded).  With inv_j = 1/c_j in     */
+/* FP32, r = M inv_j - 1 (one fma; |r| <= 2^-7) and                           */
+/*     ln x = E ln2 + ln(1/inv_j) + ln(1 + r),                                */
+/* ln(1 + r) by its Taylor polynomial r - r^2/2 + r^3/3 - r^4/4.  Rows with   */
+/* c_j > sqrt2 (j >= 27) move one factor 2 into the exponent (E + 1 and       */
+/* ln(1/(2 inv_j))), so the table term stays below ln sqrt2 in size and      */
+/* x near 1 (E = -1, M near 2) loses nothing to cancellation.                 */
 /* ------------------------------------------------------------------------ */
+#define LN_ROWS 65
+#define LN_SPLIT 27
+static float ln_inv[LN_ROWS], ln_row[LN_ROWS];
+
+/* Filled when the library is loaded, before any walker thread runs. */
+__attribute__((constructor)) static void ln_table_init(void)
+{
+    for (int j = 0; j < LN_ROWS; ++j) {
+        float inv = (float)(1.0 / (1.0 + (double)j / 64.0));
+        double a = j >= LN_SPLIT ? 2.0 * (double)inv : (double)inv;
+        ln_inv[j] = inv;
+        ln_row[j] = (float)(0.0 - log(a));
+    }
+}
+
+/* The table as the logarithm uses it (for the tests): inv[j], L[j]. */
+void oracle_ln_table(float *inv, float *L)
+{
+    for (int j = 0; j < LN_ROWS; ++j) {
+        inv[j] = ln_inv[j];
+        L[j] = ln_row[j];
+    }
+}
+
 float oracle_logf(float x)
 {
     uint32_t b;
     memcpy(&b, &x, 4);
-    int e = (int)((b >> 23) & 0xffu) - 127;
-    uint32_t mb = (b & 0x007fffffu) | 0x3f800000u;
+    uint32_t mb = b & 0x007fffffu;
+    int j = (int)((mb + 0x10000u) >> 17);
+    int e = (int)(b >> 23) - 127 + (j >= LN_SPLIT ? 1 : 0);
+    uint32_t mbits = mb | 0x3f800000u;
     float m;
-    memcpy(&m, &mb, 4);
-    if (m > 1.41421356f) {
-        m = m * 0.5f;
-        e = e + 1;
-    }
-    float s = (m - 1.0f) / (m + 1.0f);
-    float z = s * s;
-    float q = 1.0f / 11.0f;
-    q = fmaf(q, z, 1.0f / 9.0f);
-    q = fmaf(q, z, 1.0f / 7.0f);
-    q = fmaf(q, z, 1.0f / 5.0f);
-    q = fmaf(q, z, 1.0f / 3.0f);
-    float s2 = s + s;
-    float lnm = fmaf(s2 * z, q, s2);
-    return fmaf((float)e, 0.693147181f, lnm);
+    memcpy(&m, &mbits, 4);
+    float r = fmaf(m, ln_inv[j], -1.0f);
+    float q = fmaf(r, -0.25f, 1.0f / 3.0f);
+    q = fmaf(q, r, -0.5f);
+    float p = fmaf(r * r, q, r);
+    return fmaf((float)e, 0.693147181f, ln_row[j]) + p;
 }
 
+/* Batch form for the tests: y[k] = oracle_logf(x[k]). */
+void oracle_logf_many(const float *x, float *y, int64_t n)
+{
+    for (int64_t k = 0; k < n; ++k) y[k] = oracle_logf(x[k]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* FP64 natural logarithm by range reduction x = 2^e m, m in [1/sqrt2,      */
+/* sqrt2], and the series ln m = 2 artanh(s) = 2 (s + s^3/3 + s^5/5 + ...),  */
+/* s = (m-1)/(m+1) (Abramowitz & Stegun 4.1.27).  Valid for positive normal  */
+/* finite x.                                                                 */
+/* ------------------------------------------------------------------------ */
 double oracle_log(double x)
 {
     uint64_t b;

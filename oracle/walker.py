@@ -60,6 +60,8 @@ def lib():
             L.oracle_philox4x32_10.argtypes = [vp, vp, vp]
             L.oracle_logf.argtypes = [C.c_float]
             L.oracle_logf.restype = C.c_float
+            L.oracle_logf_many.argtypes = [vp, vp, i64]
+            L.oracle_ln_table.argtypes = [vp, vp]
             L.oracle_log.argtypes = [dbl]
             L.oracle_log.restype = dbl
             L.oracle_count_offdiag.argtypes = [i64, vp, vp, vp]
@@ -116,6 +118,22 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 def logf(x: float) -> float:
     return float(np.float32(lib().oracle_logf(float(x))))
+
+
+def logf_many(x) -> np.ndarray:
+    """The FP32 logarithm of every element of x (float32 array)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.empty_like(x)
+    lib().oracle_logf_many(_p(x), _p(y), int(x.size))
+    return y
+
+
+def ln_table():
+    """The FP32 logarithm's breakpoint table: (1/c_j, L_j) for j = 0..64."""
+    inv = np.empty(65, np.float32)
+    L = np.empty(65, np.float32)
+    lib().oracle_ln_table(_p(inv), _p(L))
+    return inv, L
 
 
 def log(x: float) -> float:

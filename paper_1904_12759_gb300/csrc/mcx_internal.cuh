@@ -4,15 +4,16 @@
 //
 // Every floating-point step that decides a path (holding time, remaining
 // time, grid counts, log-weight) is written with explicit round-to-nearest
-// intrinsics (__fadd_rn, __fmul_rn, __fmaf_rn, __fdiv_rn, and the double
-// versions), and the library is compiled with --fmad=false, so no
-// contraction or reassociation can change a path.
+// intrinsics (__fadd_rn, __fmul_rn, __fmaf_rn, and the double versions), and
+// the library is compiled with --fmad=false, so no contraction or
+// reassociation can change a path.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "../../include/mcx.h"
+#include "ln_table.cuh"
 
 namespace mcx {
 
@@ -145,28 +146,28 @@ __device__ __forceinline__ double unif53(uint32_t w0, uint32_t w1) {
     return __dmul_rn(__ull2double_rn(9007199254740992ull - m), 1.1102230246251565e-16 /* 2^-53 */);
 }
 
-// Natural logarithm of a positive normal float: x = 2^e m with m in
-// [1/sqrt2, sqrt2]; ln m = 2 artanh(s) with s = (m-1)/(m+1), summed as
-// 2s + 2s z (1/3 + z/5 + z^2/7 + z^3/9 + z^4/11), z = s^2 (Abramowitz &
-// Stegun 4.1.27); ln x = e ln2 + ln m.
+// Natural logarithm of a positive normal float, table-driven after Tang
+// ("Table-driven implementation of the logarithm function in IEEE
+// floating-point arithmetic", ACM TOMS 16(4), 1990), without a division:
+//   x = 2^E M, M in [1, 2); j = the breakpoint c_j = 1 + j/64 nearest M
+//   (j = 0..64, from the top mantissa bits rounded);
+//   r = M (1/c_j) - 1 in one fma, |r| <= 2^-7;
+//   ln(1 + r) = r - r^2/2 + r^3/3 - r^4/4 (Taylor, truncation below 2^-37 |r|);
+//   ln x = e ln2 + L_j + ln(1 + r), with L_j = -ln(1/c_j as rounded) and
+//   e = E, or, for j >= 27 (c_j > sqrt2), L_j = -ln(2/c_j as rounded) and
+//   e = E + 1, so that L_j stays within [-ln sqrt2, ln sqrt2] and nothing
+//   cancels near x = 1.  Within 2 ulp of the correctly rounded logarithm.
 __device__ __forceinline__ float ln_f32(float x) {
     const uint32_t b = __float_as_uint(x);
-    int e = (int)((b >> 23) & 0xffu) - 127;
-    float m = __uint_as_float((b & 0x007fffffu) | 0x3f800000u);
-    if (m > 1.41421356f) {
-        m = __fmul_rn(m, 0.5f);
-        e = e + 1;
-    }
-    const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
-    const float z = __fmul_rn(s, s);
-    float q = 1.0f / 11.0f;
-    q = __fmaf_rn(q, z, 1.0f / 9.0f);
-    q = __fmaf_rn(q, z, 1.0f / 7.0f);
-    q = __fmaf_rn(q, z, 1.0f / 5.0f);
-    q = __fmaf_rn(q, z, 1.0f / 3.0f);
-    const float s2 = __fadd_rn(s, s);
-    const float lnm = __fmaf_rn(__fmul_rn(s2, z), q, s2);
-    return __fmaf_rn(__int2float_rn(e), 0.693147181f, lnm);
+    const uint32_t mb = b & 0x007fffffu;
+    const int j = (int)((mb + 0x10000u) >> 17);
+    const int e = (int)(b >> 23) - 127 + (j >= LN_TABLE_BINADE_SPLIT ? 1 : 0);
+    const uint2 row = __ldg(&c_ln_table[j]);
+    const float r = __fmaf_rn(__uint_as_float(mb | 0x3f800000u), __uint_as_float(row.x), -1.0f);
+    float q = __fmaf_rn(r, -0.25f, 1.0f / 3.0f);
+    q = __fmaf_rn(q, r, -0.5f);
+    const float p = __fmaf_rn(__fmul_rn(r, r), q, r);
+    return __fadd_rn(__fmaf_rn(__int2float_rn(e), 0.693147181f, __uint_as_float(row.y)), p);
 }
 
 // Same construction in FP64 with the series carried to z^11/25.

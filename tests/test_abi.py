@@ -61,3 +61,24 @@ def test_missing_library_fails_loudly(tmp_path):
             _lib.load(str(tmp_path / "nope.so"))
     finally:
         _lib._lib = saved
+
+
+def test_walker_log_table_matches_the_oracle_table():
+    """The CUDA library's FP32 logarithm table (ln_table.cuh, written by its generator
+    script) and the oracle's own table (built from libm when the oracle loads) are
+    independent statements of one definition: they must hold the same bits."""
+    import re
+
+    import numpy as np
+
+    from oracle import walker as OW
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    text = open(os.path.join(here, "..", "paper_1904_12759_gb300", "csrc", "ln_table.cuh")).read()
+    rows = re.findall(r"\{0x([0-9a-f]{8})u, 0x([0-9a-f]{8})u\}", text)
+    assert len(rows) == 65
+    inv = np.array([int(a, 16) for a, _ in rows], np.uint32).view(np.float32)
+    L = np.array([int(b, 16) for _, b in rows], np.uint32).view(np.float32)
+    oinv, oL = OW.ln_table()
+    assert np.array_equal(inv.view(np.uint32), oinv.view(np.uint32))
+    assert np.array_equal(L.view(np.uint32), oL.view(np.uint32))

@@ -56,15 +56,48 @@ def test_philox_words_uniform():
 
 def test_own_logf_against_libm():
     rng = np.random.default_rng(1)
-    xs = np.concatenate([rng.uniform(0, 1, 20000), 2.0 ** -rng.uniform(0, 24, 5000), [2.0 ** -24, 0.5, 1.0]])
+    xs = np.concatenate([rng.uniform(0, 1, 20000), 2.0 ** -rng.uniform(0, 24, 5000), [2.0 ** -24, 0.5, 1.0],
+                         rng.uniform(1, 1e6, 5000), 2.0 ** rng.uniform(-126, 127, 5000)])
     xs = xs.astype(np.float32)
     xs = xs[xs > 0]
-    for x in xs[::7]:
-        got = OW.logf(float(x))
-        want = math.log(float(x))
-        ulp = np.spacing(np.float32(abs(want))) if want != 0 else np.float32(1e-45)
-        assert abs(got - want) <= 2 * float(ulp) + 1e-45, (x, got, want)
+    got = OW.logf_many(xs).astype(np.float64)
+    want = np.log(xs.astype(np.float64))
+    ulp = np.where(want != 0, np.spacing(np.abs(want).astype(np.float32)).astype(np.float64), 1e-45)
+    assert np.all(np.abs(got - want) <= 2 * ulp + 1e-45)
     assert OW.logf(1.0) == 0.0
+
+
+def test_own_logf_exhaustive_on_the_walker_uniforms():
+    """Every uniform the FP32 walker can draw, u = K 2^-24 for K = 1 .. 2^24: the
+    logarithm is within 2 ulp of the correctly rounded value (FP64 log rounded), never
+    positive, exactly 0 only at u = 1, and monotone non-decreasing in u (so a larger
+    uniform never gives a longer holding time)."""
+    K = np.arange(1, 2 ** 24 + 1, dtype=np.float64)
+    u = (K * 2.0 ** -24).astype(np.float32)
+    got = OW.logf_many(u).astype(np.float64)
+    want = np.log(u.astype(np.float64))
+    ulp = np.where(want != 0, np.spacing(np.abs(want).astype(np.float32)).astype(np.float64), 1e-45)
+    err = np.abs(got - want) / ulp
+    assert err.max() <= 2.0, (err.max(), u[np.argmax(err)])
+    assert np.all(got <= 0) and got[-1] == 0.0 and np.all(got[:-1] < 0)
+    assert np.all(np.diff(got) >= 0)
+
+
+def test_own_logf_table_against_its_definition():
+    """Row j of the breakpoint table: 1/c_j rounded to FP32 for c_j = 1 + j/64, and
+    -ln(1/c_j) (j <= 26) or -ln(2/c_j) (j >= 27) of that rounded value, rounded to
+    FP32, checked with 40-digit decimal logarithms (so no row sits on a rounding tie
+    of the FP64 logarithm the oracle takes)."""
+    from decimal import Decimal, getcontext
+
+    getcontext().prec = 40
+    inv, L = OW.ln_table()
+    for j in range(65):
+        assert inv[j] == np.float32(1.0 / (1.0 + j / 64.0))
+        a = Decimal(float(inv[j])) * (2 if j >= 27 else 1)
+        assert L[j] == np.float32(float(-a.ln())), j
+    assert inv[0] == 1.0 and L[0] == 0.0 and inv[64] == 0.5 and L[64] == 0.0
+    assert np.all(np.abs(L) <= np.float32(math.log(2) / 2 + 0.01))
 
 
 def test_own_log_against_libm():
