@@ -218,6 +218,35 @@ mcx_status mcx_trace_forward(mcx_plan *plan, const double *v, double t, int func
                              int32_t *end, uint32_t *njumps, uint64_t *hash, double *logw, void *stream);
 
 /*
+ * x ~ exp(tA) v in one call (Theorem 1, Algorithm 1, with the beta setup of
+ * Sec. 6): plan creation, optionally the power iteration for lambda_max, the
+ * backward estimate of the requested entries and the status check.
+ *   n, nnz, row_ptr, col, val   the CSR of A, as for mcx_plan_create
+ *   v                float64 [n]
+ *   t                horizon; t <= 0 asks for t = beta_scale / lambda_max(A)
+ *                    (power iteration to 1e-10 relative, at most 1000 steps)
+ *   beta_scale       used only when t <= 0 (beta = 1/lambda_max: 1)
+ *   functional, nsteps, paths_per_entry, entries, n_entries, seed,
+ *   path_offset, precision    as for mcx_estimate
+ *   flags            MCX_PLAN_HOST_INPUT: every array argument (row_ptr, col,
+ *                    val, v, entries, mean, sem) is host memory; the call
+ *                    copies the inputs to the device and the results back
+ *                    (page-locked host memory makes the copies asynchronous
+ *                    DMA); 0: every array is device memory
+ *   mean, sem        float64 [n_entries] outputs (sem may be NULL)
+ *   t_used           host double, may be NULL: the horizon that was used
+ * Device temporaries come from the library's memory pool and are returned to
+ * it; the call synchronises `stream` and returns the plan's device status.
+ * Errors: those of mcx_plan_create, mcx_power_iteration, mcx_estimate and
+ * mcx_sync.
+ */
+mcx_status mcx_expm_multiply(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col, const double *val,
+                             const double *v, double t, double beta_scale, int functional, int32_t nsteps,
+                             uint64_t paths_per_entry, const int32_t *entries, int64_t n_entries, uint64_t seed,
+                             uint64_t path_offset, int precision, uint32_t flags, double *mean, double *sem,
+                             double *t_used, void *stream);
+
+/*
  * mcx_estimate without any device allocation.  The paper has no counterpart:
  * this exists for callers that cannot call cudaMalloc once they are running,
  * e.g. a service that reserves all of its device memory at start-up and must

@@ -16,6 +16,7 @@ EXPORTS = (
     "mcx_plan_create",
     "mcx_plan_get_info",
     "mcx_estimate",
+    "mcx_expm_multiply",
     "mcx_estimate_rqmc",
     "mcx_estimate_level_difference",
     "mcx_gather_rate",
@@ -108,6 +109,9 @@ def load(path: str = LIB_PATH):
     L.mcx_plan_get_info.restype = st
     L.mcx_estimate.argtypes = [vp, vp, dbl, C.c_int, i32, u64, vp, i64, u64, u64, C.c_int, vp, vp, vp]
     L.mcx_estimate.restype = st
+    L.mcx_expm_multiply.argtypes = [i64, i64, vp, vp, vp, vp, dbl, dbl, C.c_int, i32, u64, vp, i64, u64, u64,
+                                    C.c_int, u32, vp, vp, C.POINTER(dbl), vp]
+    L.mcx_expm_multiply.restype = st
     L.mcx_estimate_rqmc.argtypes = [vp, vp, dbl, C.c_int, i32, u32, u32, u32, vp, i64, u64, C.c_int, vp, vp, vp]
     L.mcx_estimate_rqmc.restype = st
     L.mcx_estimate_level_difference.argtypes = [vp, vp, dbl, C.c_int, i32, u64, vp, i64, u64, u64, C.c_int, vp,

@@ -320,41 +320,45 @@ def power_iteration(row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
 
 def expm_multiply(row_ptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, v: torch.Tensor,
                   t: float | None = None, beta_scale: float = 1.0, paths: int = 1000,
-                  entries: torch.Tensor | None = None, seed: int = 0, mode: str = "exact", nsteps: int = 1,
-                  prec: str = "fp32", power_tol: float = 1e-10, power_iters: int = 1000, stream=None):
-    """x ~ exp(tA) v in one call: plan, optional beta setup, backward estimate.
+                  entries: torch.Tensor | None = None, seed: int = 0, path_offset: int = 0, mode: str = "exact",
+                  nsteps: int = 1, prec: str = "fp32", out: tuple | None = None, stream=None):
+    """x ~ exp(tA) v in one call of mcx_expm_multiply: plan, optional beta setup,
+    backward estimate, status check.
 
     With t=None the horizon is beta_scale / lambda_max(A) (Sec. 6 uses
-    beta = 1/lambda_max), lambda_max by the GPU power method.  Host tensors
-    (pinned for asynchronous copies) are copied to the current device inside
-    the call and the results come back as host tensors; device tensors stay
-    on the device.  Returns (mean, sem, t).
+    beta = 1/lambda_max), lambda_max by the GPU power method.  All tensors on
+    the host (page-locked for asynchronous copies): the library copies the
+    inputs to the current device and the results back inside the call; all on
+    the device: they are used in place.  Returns (mean, sem, t).
     """
     host = not row_ptr.is_cuda
-    dev = torch.device("cuda", torch.cuda.current_device())
-    if host:
-        row_ptr, col, val, v = (x.to(dev, non_blocking=True) for x in (row_ptr, col, val, v))
-        if entries is not None:
-            entries = entries.to(dev, non_blocking=True)
-    if t is None:
-        lam, _ = power_iteration(row_ptr, col, val, max_iters=power_iters, tol=power_tol, stream=stream)
-        t = beta_scale / lam
-    plan = Plan(row_ptr, col, val, stream=stream)
-    try:
-        mean, sem = plan.estimate(v, t, paths, entries=entries, seed=seed, mode=mode, nsteps=nsteps, prec=prec,
-                                  stream=stream)
-        plan.sync(stream=stream)
-    finally:
-        plan.close()
-    if host:
-        pin = torch.cuda.is_available()
-        hm = torch.empty(mean.shape, dtype=mean.dtype, pin_memory=pin)
-        hs = torch.empty(sem.shape, dtype=sem.dtype, pin_memory=pin)
-        hm.copy_(mean, non_blocking=True)
-        hs.copy_(sem, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-        mean, sem = hm, hs
-    return mean, sem, t
+    tensors = [row_ptr, col, val, v] + ([entries] if entries is not None else [])
+    if any(x.is_cuda == host for x in tensors):
+        raise ValueError("expm_multiply: the arrays must be all on the host or all on the device")
+    n = row_ptr.numel() - 1
+    ne = n if entries is None else entries.numel()
+    if out is None:
+        kw = dict(dtype=torch.float64, pin_memory=host and torch.cuda.is_available()) if host else \
+            dict(dtype=torch.float64, device=v.device)
+        mean, sem = torch.empty(ne, **kw), torch.empty(ne, **kw)
+    else:
+        mean, sem = out
+
+    def ptr(x, dt, name):
+        if x.dtype != dt or not x.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {dt} tensor")
+        return C.c_void_p(x.data_ptr())
+
+    t_used = C.c_double(0.0)
+    check(_lib.load().mcx_expm_multiply(
+        n, col.numel(), ptr(row_ptr, torch.int64, "row_ptr"), ptr(col, torch.int32, "col"),
+        ptr(val, torch.float64, "val"), ptr(v, torch.float64, "v"), -1.0 if t is None else float(t),
+        float(beta_scale), FUNCTIONALS[mode], int(nsteps), int(paths),
+        ptr(entries, torch.int32, "entries") if entries is not None else C.c_void_p(0), int(ne), int(seed),
+        int(path_offset), PRECISIONS[prec], _lib.PLAN_HOST_INPUT if host else 0, ptr(mean, torch.float64, "mean"),
+        ptr(sem, torch.float64, "sem") if sem is not None else C.c_void_p(0), C.byref(t_used), _stream(stream)),
+        "mcx_expm_multiply")
+    return mean, sem, t_used.value
 
 
 class Batch:

@@ -376,6 +376,87 @@ mcx_status mcx_power_iteration(int64_t n, const int64_t *row_ptr, const int32_t 
     return MCX_OK;
 }
 
+mcx_status mcx_expm_multiply(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col, const double *val,
+                             const double *v, double t, double beta_scale, int functional, int32_t nsteps,
+                             uint64_t paths_per_entry, const int32_t *entries, int64_t n_entries, uint64_t seed,
+                             uint64_t path_offset, int precision, uint32_t flags, double *mean, double *sem,
+                             double *t_used, void *stream) {
+    if (flags & ~MCX_PLAN_HOST_INPUT) return MCX_E_INVALID;
+    if (n < 1 || nnz < 0 || !row_ptr || (nnz > 0 && (!col || !val)) || !v || !mean) return MCX_E_INVALID;
+    if (!(t <= 0.0) && !(t > 0.0)) return MCX_E_INVALID;  // NaN
+    if (t <= 0.0 && !(beta_scale > 0.0 && isfinite(beta_scale))) return MCX_E_INVALID;
+    if (n_entries < 0 || (!entries && n_entries != n)) return MCX_E_INVALID;
+    const bool host = (flags & MCX_PLAN_HOST_INPUT) != 0;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t ne = entries ? n_entries : n;
+    // device copies of the host arrays (pool); device arrays are used in place
+    int64_t *d_rp = const_cast<int64_t *>(row_ptr);
+    int32_t *d_col = const_cast<int32_t *>(col);
+    double *d_val = const_cast<double *>(val), *d_v = const_cast<double *>(v), *d_mean = mean, *d_sem = sem;
+    int32_t *d_ent = const_cast<int32_t *>(entries);
+    double *work = nullptr;
+    void *owned[8] = {};
+    int n_owned = 0;
+    mcx_plan *plan = nullptr;
+    mcx_status rc = MCX_OK;
+    cudaError_t e = cudaSuccess;
+    auto take = [&](void **p, size_t bytes) {
+        e = pool_alloc(p, bytes, st);
+        if (e == cudaSuccess) owned[n_owned++] = *p;
+        return e == cudaSuccess;
+    };
+    auto h2d = [&](void *dst, const void *src, size_t bytes) {
+        e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+        return e == cudaSuccess;
+    };
+    do {
+        if (host) {
+            const size_t nz = (size_t)(nnz > 0 ? nnz : 1);
+            if (!take(reinterpret_cast<void **>(&d_rp), 8 * (size_t)(n + 1)) ||
+                !take(reinterpret_cast<void **>(&d_col), 4 * nz) || !take(reinterpret_cast<void **>(&d_val), 8 * nz) ||
+                !take(reinterpret_cast<void **>(&d_v), 8 * (size_t)n) ||
+                !take(reinterpret_cast<void **>(&d_mean), 8 * (size_t)(ne > 0 ? ne : 1)))
+                break;
+            if (sem && !take(reinterpret_cast<void **>(&d_sem), 8 * (size_t)(ne > 0 ? ne : 1))) break;
+            if (entries && ne > 0 && !take(reinterpret_cast<void **>(&d_ent), 4 * (size_t)ne)) break;
+            if (!h2d(d_rp, row_ptr, 8 * (size_t)(n + 1)) || (nnz > 0 && !h2d(d_col, col, 4 * (size_t)nnz)) ||
+                (nnz > 0 && !h2d(d_val, val, 8 * (size_t)nnz)) || !h2d(d_v, v, 8 * (size_t)n) ||
+                (entries && ne > 0 && !h2d(d_ent, entries, 4 * (size_t)ne)))
+                break;
+        }
+        if ((rc = mcx_plan_create(n, nnz, d_rp, d_col, d_val, 0, stream, &plan)) != MCX_OK) break;
+        if (t <= 0.0) {
+            if (!take(reinterpret_cast<void **>(&work), 8 * (size_t)(3 * n + 4096))) break;
+            double lam = 0.0;
+            int32_t it = 0;
+            if ((e = run_power_iteration(n, d_rp, d_col, d_val, 1000, 1e-10, work, &lam, &it, st)) != cudaSuccess)
+                break;
+            if (!(lam > 0.0) || !isfinite(lam)) {
+                rc = MCX_E_INVALID;  // no positive dominant eigenvalue: beta = scale / lambda is undefined
+                break;
+            }
+            t = beta_scale / lam;
+        }
+        if (t_used) *t_used = t;
+        if ((rc = mcx_estimate(plan, d_v, t, functional, nsteps, paths_per_entry, entries ? d_ent : nullptr, ne, seed,
+                               path_offset, precision, d_mean, d_sem, stream)) != MCX_OK)
+            break;
+        if (host && ne > 0) {
+            if ((e = cudaMemcpyAsync(mean, d_mean, 8 * (size_t)ne, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
+            if (sem && (e = cudaMemcpyAsync(sem, d_sem, 8 * (size_t)ne, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+                break;
+        }
+        rc = mcx_sync(plan, stream, nullptr);  // synchronises the stream: the host results are complete
+    } while (0);
+    if (rc == MCX_OK && e != cudaSuccess) rc = from_cuda(e);
+    for (int k = 0; k < n_owned; ++k) pool_free(owned[k], st);
+    if (plan) {
+        cudaStreamSynchronize(st);
+        free_plan(plan);
+    }
+    return rc;
+}
+
 mcx_status mcx_plan_export(const mcx_plan *p, int32_t *deg, int64_t *row_start, uint8_t *weighted,
                            float *inv_rate32, float *delta32, double *inv_rate64, double *delta64, int32_t *edge_col,
                            int32_t *alias_col, uint32_t *thresh, void *stream) {

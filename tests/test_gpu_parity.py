@@ -377,3 +377,31 @@ def test_lane_layout_matches_oracle(mcx, prec):
     st = plan.sync()
     assert st["paths"] == 1000 * (1 + 17 + 64)
     plan.close()
+
+
+def test_expm_multiply_host_and_device_buffers(mcx):
+    """The one-call C-ABI entry point mcx_expm_multiply: with host arrays (copied in and
+    out inside the call) and with device arrays it gives, bit for bit, the estimates of
+    a plan's mcx_estimate on the same paths; with t <= 0 it takes beta_scale/lambda_max
+    from the same power iteration as mcx_power_iteration; mixed arrays are refused."""
+    csr = W.erdos_renyi(3000, 8, 2)
+    vh = W.uniform_vector(3000, 4)
+    rp, col, val = (torch.as_tensor(x) for x in (csr.row_ptr, csr.col, csr.val))
+    ent = torch.as_tensor(W.random_entries(3000, 100, 1))
+    v = torch.as_tensor(vh)
+    dev = [x.cuda() for x in (rp, col, val, v, ent)]
+    hm, hs, t1 = mcx.expm_multiply(rp, col, val, v, t=0.1, paths=500, entries=ent, seed=5)
+    dm, ds, _ = mcx.expm_multiply(*dev[:4], t=0.1, paths=500, entries=dev[4], seed=5)
+    plan = mcx.Plan(*dev[:3])
+    pm, ps = plan.estimate(dev[3], 0.1, 500, entries=dev[4], seed=5)
+    assert t1 == 0.1 and not hm.is_cuda and dm.is_cuda
+    assert torch.equal(hm, pm.cpu()) and torch.equal(hs, ps.cpu())
+    assert torch.equal(dm, pm) and torch.equal(ds, ps)
+    lam, _ = mcx.power_iteration(*dev[:3], max_iters=1000, tol=1e-10)
+    hm2, _, t2 = mcx.expm_multiply(rp, col, val, v, t=None, beta_scale=0.5, paths=200, seed=1)
+    assert t2 == 0.5 / lam
+    pm2, _ = plan.estimate(dev[3], t2, 200, seed=1)
+    assert torch.equal(hm2, pm2.cpu())
+    plan.close()
+    with pytest.raises(ValueError):
+        mcx.expm_multiply(dev[0], col, val, v, t=0.1)
