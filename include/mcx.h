@@ -581,6 +581,109 @@ mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_
                            int64_t n_entries, uint64_t seed, uint64_t path_offset, int precision, double *mean,
                            double *sem, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batched backward estimates with the control variate (Theorem 1,          */
+/* Algorithm 1; variance reduction of Sec. 5): many (A, v, t), several      */
+/* right-hand sides per A, the whole full-vector computation of every       */
+/* (problem, right-hand side) pair in one CUDA-graph launch: per pair the   */
+/* Taylor terms, features, network prediction and coefficients (the        */
+/* pre-pass), then one persistent walk over a work list of (pair, entries,  */
+/* path chunk) items, then the per-entry finish.                            */
+/* ------------------------------------------------------------------------ */
+typedef struct mcx_cvbatch mcx_cvbatch;
+
+typedef enum {
+    MCX_CV_NONE = 0,     /* plain backward estimate: mean of W v_{X_t} (the judge of the others) */
+    MCX_CV_TAYLOR = 1,   /* control variate with h(t) = the second-order Taylor term T2 */
+    MCX_CV_LEARNED = 2   /* control variate with h(t) = the network's prediction */
+} mcx_cv_control;
+
+/* One matrix of a control-variate batch (host memory, read during create). */
+typedef struct {
+    int64_t n, nnz;           /* A is n x n with nnz stored entries (CSR as for mcx_plan_create) */
+    const int64_t *row_ptr;   /* int64 [n+1] */
+    const int32_t *col;       /* int32 [nnz] */
+    const double *val;        /* float64 [nnz] */
+    int32_t n_rhs;            /* right-hand sides of this A (>= 1) */
+    const double *v;          /* float64 [n_rhs * n]: right-hand side r at v + r n */
+    const double *t;          /* float64 [n_rhs]: horizon of each right-hand side, > 0 and finite */
+    uint64_t paths;           /* paths per entry, 1 .. 2^40 */
+} mcx_cv_problem;
+
+typedef struct {
+    int32_t problems;        /* problems in the batch */
+    int32_t pairs;           /* (problem, right-hand side) pairs */
+    int64_t states;          /* states of the block-diagonal plan, blocks padded to multiples of 1024 */
+    uint64_t total_paths;    /* paths per run */
+    uint32_t work_items;     /* work items per run */
+    uint32_t chunk;          /* paths per work item of the warp-per-entry layout (autotuned) */
+    int32_t blocks_per_sm;   /* resident blocks of 256 threads per SM (autotuned) */
+    int32_t grid;            /* persistent grid size */
+    int32_t staged;          /* 1: warps stage their entry's row in shared memory (autotuned) */
+    int32_t control;         /* mcx_cv_control */
+    double tuned_ms;         /* the autotuner's best sampled walk (0 if read from the cache) */
+} mcx_cvbatch_info;
+
+/*
+ * Build a batch of backward full-vector estimates.  The matrices go on the
+ * diagonal of one plan (blocks padded to multiples of 1024 states); each pair
+ * (problem b, right-hand side r), numbered problem by problem, keeps its own
+ * v, t, Taylor terms, features, prediction and coefficients.  Every entry of
+ * every pair is estimated with the problem's `paths`: pairs with at most 64
+ * paths per entry run one lane per entry (items of 32 entries), the others one
+ * warp per (entry, chunk of paths) with lane refill; items are ordered by
+ * estimated cost, largest first (cost ~ paths x (1 + t x mean jump rate)), and
+ * taken from an atomic counter by a persistent grid.  The schedule (chunk
+ * length, resident blocks per SM, staging of each warp's entry row in shared
+ * memory) is read from `tune_cache` (JSON lines keyed by GPU name and
+ * batch sizes; NULL: no cache) or autotuned by timing the walk on a sample of
+ * the items, then appended to the cache.
+ *   control    mcx_cv_control; MCX_CV_LEARNED needs `net`, whose weights are
+ *              read at every run (retraining it between runs is allowed)
+ *   precision  MCX_CV_NONE: MCX_FP32 (FP32 paths, compensated FP32 sums) or
+ *              MCX_FP64 (the FP64 path version); control variates: FP32
+ *              paths with the residual integrals in FP32 or FP64 (as in
+ *              mcx_estimate_cv)
+ * Pair k of the batch simulates paths k * 2^40 + p (p = 0 .. paths-1) of each
+ * entry, i.e. exactly the paths of mcx_estimate (MCX_CV_NONE) or
+ * mcx_estimate_cv on that problem alone with path_offset = k * 2^40 and the
+ * run's seed (EXACT functional).  Synchronises `stream`.
+ * Errors: MCX_E_INVALID (bad description or CSR, missing net), MCX_E_NEG_OFFDIAG,
+ * MCX_E_NONFINITE, MCX_E_OOM, MCX_E_CUDA.
+ */
+mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *problems, int control, const mcx_mlp *net,
+                              int precision, const char *tune_cache, void *stream, mcx_cvbatch **out);
+
+/* Change the paths per entry of every problem (host uint64 [problems]); the
+ * work list is rebuilt and the graph re-captured with the current schedule.
+ * Synchronises `stream`.  Errors: MCX_E_INVALID, MCX_E_OOM, MCX_E_CUDA. */
+mcx_status mcx_cvbatch_set_paths(mcx_cvbatch *batch, const uint64_t *paths, void *stream);
+
+/* One run of the whole batch (one graph launch: pre-pass, walk, finish) with
+ * the given seed; results replace the previous run's.  Asynchronous on `stream`. */
+mcx_status mcx_cvbatch_run(mcx_cvbatch *batch, uint64_t seed, void *stream);
+
+/* Copy the last run's estimate of (problem, rhs) into caller-owned device
+ * arrays x [n] and sem [n] (sem may be NULL).  Errors: MCX_E_INVALID, MCX_E_CUDA. */
+mcx_status mcx_cvbatch_result(const mcx_cvbatch *batch, int32_t problem, int32_t rhs, double *x, double *sem,
+                              void *stream);
+
+/* Copy the last run's control-variate coefficients of (problem, rhs), laid
+ * out as mcx_cv_coefficients writes them, float64 [3n] device
+ * = [(a, b) pairs | h].  Errors: MCX_E_INVALID (also for MCX_CV_NONE), MCX_E_CUDA. */
+mcx_status mcx_cvbatch_coefficients(const mcx_cvbatch *batch, int32_t problem, int32_t rhs, double *coef,
+                                    void *stream);
+
+/* Fill *info (host) with the batch's layout and schedule. */
+mcx_status mcx_cvbatch_get_info(const mcx_cvbatch *batch, mcx_cvbatch_info *info);
+
+/* mcx_sync for the batch's plan; with MCX_CV_LEARNED also the network's
+ * latched inference status (MCX_E_TIMEOUT if a tensor-core wait gave up). */
+mcx_status mcx_cvbatch_sync(mcx_cvbatch *batch, void *stream, mcx_stats *stats);
+
+/* Free the batch (synchronises the device first).  NULL is accepted. */
+void mcx_cvbatch_destroy(mcx_cvbatch *batch);
+
 /* Synchronise `stream`, return and clear the plan's latched device status and
  * counters.  stats (host pointer) may be NULL.  Errors: MCX_E_INVALID (an
  * estimate was given an entry outside [0, n); its outputs are NaN),
@@ -595,6 +698,19 @@ void mcx_plan_destroy(mcx_plan *plan);
 
 /* Static string for a status code. */
 const char *mcx_status_string(int status);
+
+/*
+ * Test hooks for the failure paths (the paper has no counterpart; not for
+ * production use).  mcx_debug_fail_alloc(k): the k-th device allocation the
+ * library makes from now on (pool or cudaMalloc) fails as if the device were
+ * out of memory, so that the call making it returns MCX_E_OOM; k <= 0
+ * disarms.  Returns the number of device allocations the library has
+ * attempted since the process started.  mcx_debug_pool_usage: bytes of the
+ * library's memory pool on the current device in use and reserved (host
+ * outputs, either may be NULL), to check that failed calls leak nothing.
+ */
+int64_t mcx_debug_fail_alloc(int64_t k);
+mcx_status mcx_debug_pool_usage(uint64_t *used, uint64_t *reserved);
 
 /* Library version as 10000*major + 100*minor + patch. */
 int mcx_version(void);

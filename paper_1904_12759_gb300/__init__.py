@@ -8,14 +8,15 @@ package is the thin Python binding (ctypes) used by the tests and benchmark.
 from . import _lib
 from ._lib import EXPORTS, MCXError, load
 
-__all__ = ["EXPORTS", "MCXError", "load", "Plan", "power_iteration", "expm_multiply", "Batch", "MLP", "cv_prepare", "cv_targets", "cv_coefficients", "gather_rate"]
+_API = ("Plan", "power_iteration", "expm_multiply", "Batch", "CVBatch", "MLP", "cv_prepare", "cv_targets",
+        "cv_coefficients", "gather_rate", "debug_fail_alloc", "debug_pool_usage")
+__all__ = ["EXPORTS", "MCXError", "load", *_API]
 
 
 def __getattr__(name):
     # the torch-facing API is imported lazily so that loading the C library
     # (and checking its exports) does not require a GPU
-    if name in ("Plan", "power_iteration", "expm_multiply", "Batch", "MLP", "cv_prepare", "cv_targets", "cv_coefficients",
-                "gather_rate"):
+    if name in _API:
         from . import api
 
         return getattr(api, name)

@@ -49,6 +49,16 @@ EXPORTS = (
     "mcx_mlp_destroy",
     "mcx_cv_coefficients",
     "mcx_estimate_cv",
+    "mcx_cvbatch_create",
+    "mcx_cvbatch_set_paths",
+    "mcx_cvbatch_run",
+    "mcx_cvbatch_result",
+    "mcx_cvbatch_coefficients",
+    "mcx_cvbatch_get_info",
+    "mcx_cvbatch_sync",
+    "mcx_cvbatch_destroy",
+    "mcx_debug_fail_alloc",
+    "mcx_debug_pool_usage",
 )
 
 MCX_OK = 0
@@ -77,6 +87,21 @@ class BatchInfo(C.Structure):
                 ("work_items", C.c_uint32), ("chunk", C.c_uint32), ("blocks_per_sm", C.c_int32),
                 ("grid", C.c_int32), ("count_deposits", C.c_int32), ("lane_refill", C.c_int32),
                 ("tuned_ms", C.c_double)]
+
+
+class CvProblem(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p), ("n_rhs", C.c_int32), ("v", C.c_void_p), ("t", C.c_void_p),
+                ("paths", C.c_uint64)]
+
+
+class CvBatchInfo(C.Structure):
+    _fields_ = [("problems", C.c_int32), ("pairs", C.c_int32), ("states", C.c_int64), ("total_paths", C.c_uint64),
+                ("work_items", C.c_uint32), ("chunk", C.c_uint32), ("blocks_per_sm", C.c_int32),
+                ("grid", C.c_int32), ("staged", C.c_int32), ("control", C.c_int32), ("tuned_ms", C.c_double)]
+
+
+CV_CONTROLS = {"none": 0, "taylor": 1, "learned": 2}
 
 
 class Stats(C.Structure):
@@ -173,6 +198,27 @@ def load(path: str = LIB_PATH):
     L.mcx_cv_coefficients.restype = st
     L.mcx_estimate_cv.argtypes = [vp, vp, dbl, u64, vp, i64, u64, u64, C.c_int, vp, vp, vp]
     L.mcx_estimate_cv.restype = st
+    L.mcx_cvbatch_create.argtypes = [i32, C.POINTER(CvProblem), C.c_int, vp, C.c_int, C.c_char_p, vp,
+                                     C.POINTER(vp)]
+    L.mcx_cvbatch_create.restype = st
+    L.mcx_cvbatch_set_paths.argtypes = [vp, vp, vp]
+    L.mcx_cvbatch_set_paths.restype = st
+    L.mcx_cvbatch_run.argtypes = [vp, u64, vp]
+    L.mcx_cvbatch_run.restype = st
+    L.mcx_cvbatch_result.argtypes = [vp, i32, i32, vp, vp, vp]
+    L.mcx_cvbatch_result.restype = st
+    L.mcx_cvbatch_coefficients.argtypes = [vp, i32, i32, vp, vp]
+    L.mcx_cvbatch_coefficients.restype = st
+    L.mcx_cvbatch_get_info.argtypes = [vp, C.POINTER(CvBatchInfo)]
+    L.mcx_cvbatch_get_info.restype = st
+    L.mcx_cvbatch_sync.argtypes = [vp, vp, C.POINTER(Stats)]
+    L.mcx_cvbatch_sync.restype = st
+    L.mcx_cvbatch_destroy.argtypes = [vp]
+    L.mcx_cvbatch_destroy.restype = None
+    L.mcx_debug_fail_alloc.argtypes = [i64]
+    L.mcx_debug_fail_alloc.restype = i64
+    L.mcx_debug_pool_usage.argtypes = [C.POINTER(u64), C.POINTER(u64)]
+    L.mcx_debug_pool_usage.restype = st
     L.mcx_status_string.argtypes = [C.c_int]
     L.mcx_status_string.restype = C.c_char_p
     L.mcx_version.restype = C.c_int

@@ -538,3 +538,104 @@ class MLP:
             self.close()
         except Exception:
             pass
+
+
+class CVBatch:
+    """Many backward full-vector estimates (Theorem 1) with the control variate of
+    Sec. 5 in one CUDA-graph launch per run (mcx_cvbatch_*).
+
+    ``problems``: list of dicts with host arrays ``row_ptr``, ``col``, ``val`` (the CSR
+    of A), ``v`` (n values, or n_rhs x n for several right-hand sides), ``t`` (a scalar
+    or one horizon per right-hand side) and ``paths`` (paths per entry).
+    ``control``: "none" (plain estimate), "taylor" or "learned" (needs ``net``, an
+    :class:`MLP`).  ``prec``: "fp32" or "fp64" (plain: the FP64 path version; control
+    variates: residual integrals in FP64).  Pair k (problems in order, right-hand
+    sides in order) simulates paths k * 2^40 + p of each entry.
+    """
+
+    def __init__(self, problems, control: str = "learned", net=None, prec: str = "fp32",
+                 tune_cache: str | None = None, stream=None):
+        import numpy as np
+
+        L = _lib.load()
+        keep = []
+        arr = (_lib.CvProblem * len(problems))()
+        self.sizes = []
+        for k, p in enumerate(problems):
+            rp = np.ascontiguousarray(p["row_ptr"], dtype=np.int64)
+            col = np.ascontiguousarray(p["col"], dtype=np.int32)
+            val = np.ascontiguousarray(p["val"], dtype=np.float64)
+            n = rp.size - 1
+            v = np.ascontiguousarray(np.asarray(p["v"], dtype=np.float64).reshape(-1, n))
+            t = np.ascontiguousarray(np.broadcast_to(np.asarray(p["t"], dtype=np.float64), (v.shape[0],)))
+            keep += [rp, col, val, v, t]
+            arr[k] = _lib.CvProblem(n, col.size, rp.ctypes.data, col.ctypes.data, val.ctypes.data, v.shape[0],
+                                    v.ctypes.data, t.ctypes.data, int(p["paths"]))
+            self.sizes.append((n, v.shape[0]))
+        out = C.c_void_p()
+        self.control = control
+        check(L.mcx_cvbatch_create(len(problems), arr, _lib.CV_CONTROLS[control],
+                                   net._h if net is not None else None, PRECISIONS[prec],
+                                   tune_cache.encode() if tune_cache else None, _stream(stream), C.byref(out)),
+              "mcx_cvbatch_create")
+        self._h = out
+
+    def info(self) -> dict:
+        inf = _lib.CvBatchInfo()
+        check(_lib.load().mcx_cvbatch_get_info(self._h, C.byref(inf)), "mcx_cvbatch_get_info")
+        return {k: getattr(inf, k) for k, _ in inf._fields_}
+
+    def set_paths(self, paths, stream=None) -> None:
+        import numpy as np
+
+        p = np.ascontiguousarray(np.broadcast_to(np.asarray(paths, dtype=np.uint64), (len(self.sizes),)))
+        check(_lib.load().mcx_cvbatch_set_paths(self._h, C.c_void_p(p.ctypes.data), _stream(stream)),
+              "mcx_cvbatch_set_paths")
+
+    def run(self, seed: int, stream=None) -> None:
+        check(_lib.load().mcx_cvbatch_run(self._h, int(seed), _stream(stream)), "mcx_cvbatch_run")
+
+    def result(self, problem: int, rhs: int = 0, stream=None):
+        n = self.sizes[problem][0]
+        dev = torch.device("cuda", torch.cuda.current_device())
+        x = torch.empty(n, dtype=torch.float64, device=dev)
+        sem = torch.empty(n, dtype=torch.float64, device=dev)
+        check(_lib.load().mcx_cvbatch_result(self._h, int(problem), int(rhs), C.c_void_p(x.data_ptr()),
+                                             C.c_void_p(sem.data_ptr()), _stream(stream)), "mcx_cvbatch_result")
+        return x, sem
+
+    def coefficients(self, problem: int, rhs: int = 0, stream=None):
+        n = self.sizes[problem][0]
+        coef = torch.empty(3 * n, dtype=torch.float64, device=torch.device("cuda", torch.cuda.current_device()))
+        check(_lib.load().mcx_cvbatch_coefficients(self._h, int(problem), int(rhs), C.c_void_p(coef.data_ptr()),
+                                                   _stream(stream)), "mcx_cvbatch_coefficients")
+        return coef
+
+    def sync(self, stream=None) -> dict:
+        st = _lib.Stats()
+        check(_lib.load().mcx_cvbatch_sync(self._h, _stream(stream), C.byref(st)), "mcx_cvbatch_sync")
+        return {"paths": st.paths, "jumps": st.jumps, "status_bits": st.status_bits}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            _lib.load().mcx_cvbatch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def debug_fail_alloc(k: int) -> int:
+    """Test hook: the k-th device allocation of the library from now fails (k <= 0
+    disarms); returns the library's allocation count so far."""
+    return int(_lib.load().mcx_debug_fail_alloc(int(k)))
+
+
+def debug_pool_usage() -> tuple:
+    """(bytes in use, bytes reserved) of the library's memory pool on the current device."""
+    u, r = C.c_uint64(0), C.c_uint64(0)
+    check(_lib.load().mcx_debug_pool_usage(C.byref(u), C.byref(r)), "mcx_debug_pool_usage")
+    return u.value, r.value

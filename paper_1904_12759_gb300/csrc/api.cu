@@ -3,6 +3,7 @@
 #include <math.h>
 #include <stdlib.h>
 
+#include <atomic>
 #include <mutex>
 #include <new>
 
@@ -31,8 +32,8 @@ void free_plan(mcx_plan *p) {
     pool_free(p->edge_col, 0);
     pool_free(p->edge16, 0);
     pool_free(p->status, 0);
-    cudaFree(p->scratch);
-    cudaFree(p->fwd);
+    dev_free(p->scratch);
+    dev_free(p->fwd);
     delete p;
 }
 
@@ -40,11 +41,37 @@ std::mutex g_pool_mu;
 cudaMemPool_t g_pools[64];
 bool g_pool_ready[64] = {};
 
+// Failure injection (test hook): g_fail_in > 0 counts down the device
+// allocations still to succeed before one fails; 0 is disarmed.
+std::atomic<int64_t> g_fail_in{0};
+std::atomic<int64_t> g_allocs{0};
+
+bool injected_failure() {
+    g_allocs.fetch_add(1);
+    int64_t c = g_fail_in.load();
+    while (c > 0) {
+        if (g_fail_in.compare_exchange_weak(c, c - 1)) return c == 1;
+    }
+    return false;
+}
+
 }  // namespace
 
 namespace mcx {
 
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    *p = nullptr;
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes ? bytes : 1);
+}
+
+void dev_free(void *p) {
+    if (p) cudaFree(p);
+}
+
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st) {
+    *p = nullptr;
+    if (injected_failure()) return cudaErrorMemoryAllocation;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -76,6 +103,33 @@ void pool_free(void *p, cudaStream_t st) {
 extern "C" {
 
 int mcx_version(void) { return 100; }
+
+int64_t mcx_debug_fail_alloc(int64_t k) {
+    g_fail_in.store(k > 0 ? k : 0);
+    return g_allocs.load();
+}
+
+mcx_status mcx_debug_pool_usage(uint64_t *used, uint64_t *reserved) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MCX_E_CUDA;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        if (!g_pool_ready[dev]) {
+            if (used) *used = 0;
+            if (reserved) *reserved = 0;
+            return MCX_OK;
+        }
+        pool = g_pools[dev];
+    }
+    unsigned long long u = 0, r = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &u) != cudaSuccess ||
+        cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &r) != cudaSuccess)
+        return MCX_E_CUDA;
+    if (used) *used = (uint64_t)u;
+    if (reserved) *reserved = (uint64_t)r;
+    return MCX_OK;
+}
 
 const char *mcx_status_string(int s) {
     switch (s) {

@@ -33,8 +33,9 @@
 #include <string>
 #include <vector>
 
-#include "walker.cuh"
 #include "launch.h"
+#include "tune_cache.h"
+#include "walker.cuh"
 
 namespace mcx {
 namespace {
@@ -320,7 +321,7 @@ void free_batch(mcx_batch *b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     void *bufs[] = {b->pts, b->pbase, b->gprob, b->v, b->S, b->top, b->in, b->q, b->stack, b->V, b->bad,
                     b->next_item, b->dep, b->x, b->sem, b->items};
-    for (void *p : bufs) cudaFree(p);
+    for (void *p : bufs) dev_free(p);
     if (b->plan) mcx_plan_destroy(b->plan);
     delete b;
 }
@@ -352,9 +353,9 @@ cudaError_t make_items(mcx_batch *b, uint32_t L, cudaStream_t st, uint32_t strid
         for (uint64_t c = 0; c < chunks; ++c, ++idx)
             if (idx % stride == 0) items.push_back(BatchItem{(uint32_t)k, (uint32_t)c});
     }
-    cudaFree(b->items);
+    dev_free(b->items);
     b->items = nullptr;
-    cudaError_t e = cudaMalloc(&b->items, sizeof(BatchItem) * (items.size() + 1));
+    cudaError_t e = dev_malloc(&b->items, sizeof(BatchItem) * (items.size() + 1));
     if (e != cudaSuccess) return e;
     e = cudaMemcpyAsync(b->items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
@@ -443,38 +444,20 @@ std::string signature(const mcx_batch *b) {
     return buf;
 }
 
-// Minimal cache: one JSON object per line
-// {"key": "...", "chunk": L, "blocks_per_sm": k, "refill": r, "ms": t} ("refill" 1 when absent).
+// Cached schedule of a problem-set signature: chunk, blocks per SM, lane refill
+// ("refill" 1 when absent).
 bool cache_lookup(const char *path, const std::string &key, uint32_t *L, int *bps, bool *refill) {
-    if (!path) return false;
-    FILE *f = fopen(path, "r");
-    if (!f) return false;
-    char line[512];
-    bool found = false;
-    const std::string needle = "\"key\": \"" + key + "\"";
-    while (fgets(line, sizeof line, f)) {
-        if (!strstr(line, needle.c_str())) continue;
-        const char *c = strstr(line, "\"chunk\": ");
-        const char *k = strstr(line, "\"blocks_per_sm\": ");
-        const char *r = strstr(line, "\"refill\": ");
-        if (c && k) {
-            *L = (uint32_t)strtoul(c + 9, nullptr, 10);
-            *bps = (int)strtol(k + 17, nullptr, 10);
-            *refill = r ? strtol(r + 10, nullptr, 10) != 0 : true;
-            found = *L > 0 && *bps > 0;
-        }
-    }
-    fclose(f);
-    return found;
+    long c = 0, k = 0, r = 1;
+    if (!tune_cache_get(path, key, "chunk", &c) || !tune_cache_get(path, key, "blocks_per_sm", &k)) return false;
+    tune_cache_get(path, key, "refill", &r);
+    *L = (uint32_t)c;
+    *bps = (int)k;
+    *refill = r != 0;
+    return c > 0 && k > 0;
 }
 
 void cache_store(const char *path, const std::string &key, uint32_t L, int bps, bool refill, double ms) {
-    if (!path) return;
-    FILE *f = fopen(path, "a");
-    if (!f) return;
-    fprintf(f, "{\"key\": \"%s\", \"chunk\": %u, \"blocks_per_sm\": %d, \"refill\": %d, \"ms\": %.4f}\n",
-            key.c_str(), L, bps, refill ? 1 : 0, ms);
-    fclose(f);
+    tune_cache_put(path, key, {{"chunk", (long)L}, {"blocks_per_sm", (long)bps}, {"refill", refill ? 1L : 0L}}, ms);
 }
 
 }  // namespace
@@ -587,21 +570,21 @@ mcx_status mcx_batch_create(int32_t count, const mcx_problem *pr, const char *tu
     cudaError_t e = cudaSuccess;
     const int64_t m = std::max<int64_t>(N, b->ngroups);
     do {
-        if ((e = cudaMalloc(&b->pts, sizeof(BatchPT) * b->n_pt)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&b->pbase, sizeof(BatchPT) * count)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&b->gprob, sizeof(int32_t) * b->ngroups)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&b->v, sizeof(double) * N)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&b->S, sizeof(double) * b->ngroups)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&b->top, sizeof(AliasEnt) * b->ngroups)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&b->in, sizeof(AliasEnt) * N)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&b->q, sizeof(double) * m)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&b->stack, sizeof(int32_t) * m)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&b->V, sizeof(double) * count)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&b->bad, 16)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&b->next_item, 16)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&b->dep, (b->count_mode ? 8 : 16) * (size_t)slots)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&b->x, sizeof(double) * slots)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&b->sem, sizeof(double) * slots)) != cudaSuccess) break;
+        if ((e = dev_malloc(&b->pts, sizeof(BatchPT) * b->n_pt)) != cudaSuccess) break;
+        if ((e = dev_malloc(&b->pbase, sizeof(BatchPT) * count)) != cudaSuccess) break;
+        if ((e = dev_malloc(&b->gprob, sizeof(int32_t) * b->ngroups)) != cudaSuccess) break;
+        if ((e = dev_malloc(&b->v, sizeof(double) * N)) != cudaSuccess) break;
+        if ((e = dev_malloc(&b->S, sizeof(double) * b->ngroups)) != cudaSuccess) break;
+        if ((e = dev_malloc(&b->top, sizeof(AliasEnt) * b->ngroups)) != cudaSuccess) break;
+        if ((e = dev_malloc(&b->in, sizeof(AliasEnt) * N)) != cudaSuccess) break;
+        if ((e = dev_malloc(&b->q, sizeof(double) * m)) != cudaSuccess) break;
+        if ((e = dev_malloc(&b->stack, sizeof(int32_t) * m)) != cudaSuccess) break;
+        if ((e = dev_malloc(&b->V, sizeof(double) * count)) != cudaSuccess) break;
+        if ((e = dev_malloc(&b->bad, 16)) != cudaSuccess) break;
+        if ((e = dev_malloc(&b->next_item, 16)) != cudaSuccess) break;
+        if ((e = dev_malloc(&b->dep, (b->count_mode ? 8 : 16) * (size_t)slots)) != cudaSuccess) break;
+        if ((e = dev_malloc(&b->x, sizeof(double) * slots)) != cudaSuccess) break;
+        if ((e = dev_malloc(&b->sem, sizeof(double) * slots)) != cudaSuccess) break;
         cudaMemcpyAsync(b->pts, b->pt_host.data(), sizeof(BatchPT) * b->n_pt, cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(b->pbase, pbase.data(), sizeof(BatchPT) * count, cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(b->gprob, gprob.data(), sizeof(int32_t) * b->ngroups, cudaMemcpyHostToDevice, st);

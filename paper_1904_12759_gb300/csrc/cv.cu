@@ -26,6 +26,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "cvmath.cuh"
 #include "dfloat.cuh"
 #include "launch.h"
 #include "rows.cuh"
@@ -597,74 +598,6 @@ __global__ void k_cv_ab(int64_t n, const double *__restrict__ T, const double *_
 // ---------------------------------------------------------------------------
 // CV walker
 // ---------------------------------------------------------------------------
-// phi_k(z) = sum_n z^n / (n! (n + k + 1)): Horner coefficients 1/(n! (n+k+1)).
-struct PhiSeries {
-    float c[4][11];  // FP32: 11 terms for |z| <= 1 (remainder below 2e-9)
-};
-__host__ __device__ constexpr PhiSeries phi_series() {
-    PhiSeries s{};
-    for (int k = 0; k < 4; ++k) {
-        double f = 1.0;  // n!
-        for (int n = 0; n < 11; ++n) {
-            if (n > 0) f *= n;
-            s.c[k][n] = (float)(1.0 / (f * (n + k + 1)));
-        }
-    }
-    return s;
-}
-__constant__ PhiSeries c_phi = phi_series();
-
-template <typename R>
-__device__ __forceinline__ void phis(R z, R ph[4]) {
-    if (sizeof(R) == 4) {
-        if (fabsf((float)z) <= 1.0f) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float p = c_phi.c[k][10];
-#pragma unroll
-                for (int n = 9; n >= 0; --n) p = fmaf(p, (float)z, c_phi.c[k][n]);
-                ph[k] = (R)p;
-            }
-        } else {
-            const float ez = expf((float)z), iz = 1.0f / (float)z;
-            ph[0] = (R)((ez - 1.0f) * iz);
-            ph[1] = (R)((ez - (float)ph[0]) * iz);
-            ph[2] = (R)((ez - 2.0f * (float)ph[1]) * iz);
-            ph[3] = (R)((ez - 3.0f * (float)ph[2]) * iz);
-        }
-        return;
-    }
-    // FP64: series to 40 terms for |z| <= 2, else the recursion
-    if (fabs((double)z) <= 2.0) {
-        R term = (R)1, s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-        for (int n = 0; n < 40; ++n) {
-            s0 += term / (R)(n + 1);
-            s1 += term / (R)(n + 2);
-            s2 += term / (R)(n + 3);
-            s3 += term / (R)(n + 4);
-            term *= z / (R)(n + 1);
-        }
-        ph[0] = s0; ph[1] = s1; ph[2] = s2; ph[3] = s3;
-    } else {
-        const R ez = (R)exp((double)z);
-        ph[0] = (ez - (R)1) / z;
-        ph[1] = (ez - (R)1 * ph[0]) / z;
-        ph[2] = (ez - (R)2 * ph[1]) / z;
-        ph[3] = (ez - (R)3 * ph[2]) / z;
-    }
-}
-
-template <typename R>
-__device__ __forceinline__ R hold_integral(R a, R b, R delta, R r, R D) {
-    const R c0 = a * r * r + b * r * r * r;
-    const R c1 = (R)-2 * a * r - (R)3 * b * r * r;
-    const R c2 = a + (R)3 * b * r;
-    const R c3 = -b;
-    R ph[4];
-    phis<R>(delta * D, ph);
-    return c0 * D * ph[0] + c1 * D * D * ph[1] + c2 * D * D * D * ph[2] + c3 * D * D * D * D * ph[3];
-}
-
 struct CVArgs {
     const double *h;    // [n] h(t, i) = xhat_i
     const double2 *ab;  // [n] (a, b)
@@ -957,10 +890,10 @@ MLPView view(const mcx_mlp *m) { return MLPView{m->params, m->stats, m->stats + 
 
 cudaError_t ensure_part(mcx_mlp *m, int64_t blocks) {
     if (m->part_blocks >= blocks) return cudaSuccess;
-    cudaFree(m->part);
+    dev_free(m->part);
     m->part = nullptr;
     m->part_blocks = 0;
-    cudaError_t e = cudaMalloc(&m->part, sizeof(float) * (NPARAM + 1) * (size_t)blocks);
+    cudaError_t e = dev_malloc(&m->part, sizeof(float) * (NPARAM + 1) * (size_t)blocks);
     if (e == cudaSuccess) m->part_blocks = blocks;
     return e;
 }
@@ -1034,12 +967,12 @@ mcx_status mcx_mlp_create(uint64_t seed, mcx_mlp **out) {
     for (int f = 0; f < NF; ++f) stats[NF + f] = 1.0f;
     cudaError_t e;
     do {
-        if ((e = cudaMalloc(&m->params, sizeof(float) * (NPARAM + 1))) != cudaSuccess) break;
-        if ((e = cudaMalloc(&m->m1, sizeof(float) * (NPARAM + 1))) != cudaSuccess) break;
-        if ((e = cudaMalloc(&m->m2, sizeof(float) * (NPARAM + 1))) != cudaSuccess) break;
-        if ((e = cudaMalloc(&m->grad, sizeof(float) * (NPARAM + 1))) != cudaSuccess) break;
-        if ((e = cudaMalloc(&m->stats, sizeof(float) * 2 * NF)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&m->err, sizeof(uint32_t))) != cudaSuccess) break;
+        if ((e = dev_malloc(&m->params, sizeof(float) * (NPARAM + 1))) != cudaSuccess) break;
+        if ((e = dev_malloc(&m->m1, sizeof(float) * (NPARAM + 1))) != cudaSuccess) break;
+        if ((e = dev_malloc(&m->m2, sizeof(float) * (NPARAM + 1))) != cudaSuccess) break;
+        if ((e = dev_malloc(&m->grad, sizeof(float) * (NPARAM + 1))) != cudaSuccess) break;
+        if ((e = dev_malloc(&m->stats, sizeof(float) * 2 * NF)) != cudaSuccess) break;
+        if ((e = dev_malloc(&m->err, sizeof(uint32_t))) != cudaSuccess) break;
         cudaMemset(m->err, 0, sizeof(uint32_t));
         cudaMemcpy(m->params, p.data(), sizeof(float) * (NPARAM + 1), cudaMemcpyHostToDevice);
         cudaMemcpy(m->stats, stats.data(), sizeof(float) * 2 * NF, cudaMemcpyHostToDevice);
@@ -1123,16 +1056,16 @@ mcx_status mcx_mlp_fit(mcx_mlp *m, int64_t n, const float *features, const float
     cudaError_t e = ensure_part(m, bblocks);
     if (e != cudaSuccess) return stat(e);
     if (m->idx_n < n) {
-        cudaFree(m->idx);
+        dev_free(m->idx);
         m->idx = nullptr;
-        if ((e = cudaMalloc(&m->idx, sizeof(int64_t) * (size_t)n)) != cudaSuccess) return stat(e);
+        if ((e = dev_malloc(&m->idx, sizeof(int64_t) * (size_t)n)) != cudaSuccess) return stat(e);
         m->idx_n = n;
     }
     const int64_t steps = (n + batch - 1) / batch;  // minibatches per epoch
     if (epoch_loss && m->losses_n < steps) {
-        cudaFree(m->losses);
+        dev_free(m->losses);
         m->losses = nullptr;
-        if ((e = cudaMalloc(&m->losses, sizeof(float) * (size_t)steps)) != cudaSuccess) return stat(e);
+        if ((e = dev_malloc(&m->losses, sizeof(float) * (size_t)steps)) != cudaSuccess) return stat(e);
         m->losses_n = steps;
     }
     cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem());
@@ -1181,15 +1114,15 @@ mcx_status mcx_mlp_fit(mcx_mlp *m, int64_t n, const float *features, const float
 
 void mcx_mlp_destroy(mcx_mlp *m) {
     if (!m) return;
-    cudaFree(m->params);
-    cudaFree(m->m1);
-    cudaFree(m->m2);
-    cudaFree(m->stats);
-    cudaFree(m->grad);
-    cudaFree(m->part);
-    cudaFree(m->idx);
-    cudaFree(m->err);
-    cudaFree(m->losses);
+    dev_free(m->params);
+    dev_free(m->m1);
+    dev_free(m->m2);
+    dev_free(m->stats);
+    dev_free(m->grad);
+    dev_free(m->part);
+    dev_free(m->idx);
+    dev_free(m->err);
+    dev_free(m->losses);
     delete m;
 }
 
@@ -1264,10 +1197,10 @@ mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_
     const uint64_t n_chunks = (uint64_t)n_entries * cpe;
     const size_t need = sizeof(Partial) * (size_t)n_chunks;
     if (plan->scratch_bytes < need) {
-        cudaFree(plan->scratch);
+        dev_free(plan->scratch);
         plan->scratch = nullptr;
         plan->scratch_bytes = 0;
-        cudaError_t e = cudaMalloc(&plan->scratch, need);
+        cudaError_t e = dev_malloc(&plan->scratch, need);
         if (e != cudaSuccess) return stat(e);
         plan->scratch_bytes = need;
     }

@@ -1,0 +1,1036 @@
+// Batched backward full-vector estimates (Theorem 1, Algorithm 1) with the
+// control variate of the variance-reduction remark of Sec. 5: many (A, v, t),
+// several right-hand sides per A, one CUDA-graph launch per run.
+//
+// Layout.  The problems' matrices A_b go on the diagonal of one plan (blocks
+// padded to multiples of 1024 states); each pair k = (problem b, right-hand
+// side r), numbered problem by problem, owns a slot range of per-state arrays
+// (its v, the FP32 copy of v scaled by a power of two, mean and standard
+// error) and, with a control variate, its Taylor terms, features, prediction
+// and coefficients.  Pair k simulates paths k * 2^40 + p of every entry with
+// the entry's local index as the Philox stream word, so its paths are exactly
+// those of the single-problem call (mcx_estimate / mcx_estimate_cv) with
+// path_offset = k * 2^40: the walk runs on global state indices of the
+// block-diagonal plan, whose rows are the problems' rows shifted by a
+// constant, so every slot choice and every visited state is the same.
+//
+// Run (one graph launch).  Pre-pass per pair: the Taylor terms, features,
+// network prediction (tensor cores) and coefficients of the control variate,
+// or the exponent and scaled FP32 copy of v for plain estimates.  Then one
+// persistent walk over a work list in largest-estimated-cost-first order
+// (cost ~ paths x (1 + t x mean jump rate)): pairs with at most 64 paths per
+// entry take items of 32 entries with one lane per entry (all paths of the
+// entry in path order, result written by the lane); the others take items
+// (entry, chunk of paths) with one warp per item, lane refill, and the entry
+// row staged in shared memory when the schedule says so; their chunk partials
+// are merged per entry in chunk order by the finish kernel.  The seed is the
+// only per-run parameter (the walk node's round keys are updated in the
+// instantiated graph).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "accum.cuh"
+#include "cvmath.cuh"
+#include "launch.h"
+#include "tune_cache.h"
+#include "walker.cuh"
+
+namespace mcx {
+namespace {
+
+constexpr int64_t CVB_BLOCK = 1024;        // plan blocks padded to multiples of this
+constexpr int CVB_MIN_BLOCKS = 4;          // resident blocks per SM the plain walk is compiled for
+constexpr int CVB_MIN_BLOCKS_CV = 2;       // and the control-variate walk (hold integrals need registers)
+constexpr uint64_t CVB_ITEMS_PER_PAIR = 1ull << 20;  // chunk items per pair before chunks grow
+
+struct CvbPair {
+    int64_t off;         // first global state of the problem
+    int64_t n;           // states (entries) of the problem
+    int64_t slot;        // first per-state slot of this pair (v, vf, mean, sem)
+    int64_t coef;        // first double of this pair's coefficients [(a, b) pairs | h] (32-double aligned)
+    int64_t part0;       // first chunk partial (warp layout)
+    uint64_t paths;      // paths per entry
+    uint64_t path_base;  // pair index << 40
+    uint64_t chunk;      // paths per chunk (warp layout)
+    double t;
+    float t32;
+    uint32_t cpe;        // chunks per entry; 0: lane layout (paths <= LANE_MODE_MAX_PATHS)
+    int32_t problem, rhs;
+    int32_t pad[2];
+};
+
+struct CvbItem {
+    uint32_t pair;
+    uint32_t e0;     // lane layout: first of 32 entries; warp layout: the entry
+    uint32_t chunk;  // warp layout: chunk index
+    uint32_t pad;
+};
+
+struct CvbArgs {
+    const CvbPair *pairs;
+    const CvbItem *items;
+    uint32_t n_items;
+    unsigned int *next_item;
+    const double *coef;    // per pair at pairs[k].coef (control variates)
+    const double *v;       // [slots] float64 v of each pair (FP64 plain paths)
+    const float *vf;       // [slots] v * 2^-vexp (FP32 plain paths)
+    const uint32_t *vexp;  // [pairs] biased exponent (see v_scale)
+    Partial *part;
+    double *mean, *sem;    // [slots]
+};
+
+// Exponent of the largest finite |v_i| of one pair, biased (the word is cleared first).
+__global__ void k_cvb_vexp(int64_t n, const double *__restrict__ v, uint32_t *vexp) {
+    uint32_t e = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = fabs(v[i]);
+        if (x > 0.0 && x <= 1.7976931348623157e308) e = max(e, (uint32_t)(ilogb(x) + (int)VEXP_BIAS));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 31) == 0 && e) atomicMax(vexp, e);
+}
+
+__global__ void k_cvb_pack(int64_t n, const double *__restrict__ v, const uint32_t *vexp, float *__restrict__ vf) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t eb = *vexp;
+    vf[i] = __double2float_rn(ldexp(v[i], eb ? -((int)eb - (int)VEXP_BIAS) : 0));
+}
+
+// The lane sums of a control-variate walker: FP64 plain sums of the per-path
+// residual integrals, or FP32 shifted compensated sums of e^{Ls} ys.
+template <bool F64I>
+struct CvLane {
+    double s1 = 0.0, s2 = 0.0;
+    float m = -INFINITY, f1 = 0.f, c1 = 0.f, f2 = 0.f;
+    using R = typename std::conditional<F64I, double, float>::type;
+    __device__ __forceinline__ void end_path(R ys, float Ls) {
+        if (F64I) {
+            s1 += (double)ys;
+            s2 += (double)ys * (double)ys;
+        } else {
+            if (!(Ls <= m + 8.0f)) {
+                const float sc = (m == -INFINITY) ? 0.0f : expf(m - Ls);
+                f1 *= sc; c1 *= sc; f2 *= sc * sc;
+                m = Ls;
+            }
+            const float wv = __fmul_rn(expf(__fsub_rn(Ls, m)), (float)ys);
+            const float yk = __fsub_rn(wv, c1);
+            const float tk = __fadd_rn(f1, yk);
+            c1 = __fsub_rn(__fsub_rn(tk, f1), yk);
+            f1 = tk;
+            f2 = __fmaf_rn(wv, wv, f2);
+        }
+    }
+    __device__ __forceinline__ void result(double &S1, double &S2, double &M) const {
+        if (F64I) {
+            S1 = s1; S2 = s2; M = 0.0;
+        } else {
+            S1 = (double)f1 - (double)c1; S2 = (double)f2; M = (double)m;
+        }
+    }
+    __device__ __forceinline__ void warp_merge(double &S1, double &S2, double &M) const {
+        if (F64I) {
+            S1 = warp_sum(s1); S2 = warp_sum(s2); M = 0.0;
+        } else {
+            float mw = m;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+            const double sc = (m == -INFINITY) ? 0.0 : exp((double)m - (double)mw);
+            S1 = warp_sum(sc * ((double)f1 - (double)c1));
+            S2 = warp_sum(sc * sc * (double)f2);
+            M = (double)mw;
+        }
+    }
+};
+
+// One event of a control-variate path: advance, then add the hold's residual
+// integral e^{L0} int R to the path's running sum (ys with shift Ls in FP32).
+template <bool F64I, bool WEIGHTED>
+__device__ __forceinline__ bool cv_event(Walker<false> &w, const WalkParams &a, uint32_t stream, uint64_t path,
+                                         const StageWarp *sw, int32_t i0, const double2 *__restrict__ ab,
+                                         int64_t off, typename CvLane<F64I>::R &ys, float &Ls) {
+    using R = typename CvLane<F64I>::R;
+    const int32_t j = w.j;
+    const float r0 = w.r, L0 = w.acc, dl = w.delta;
+    float D;
+    const bool fin = advance<MCX_EXACT, WEIGHTED, false>(w, a, stream, path, sw, i0, &D);
+    const double2 c = __ldg(ab + (j - off));
+    const R J = hold_integral<R>((R)c.x, (R)c.y, (R)dl, (R)r0, (R)D);
+    if (F64I) {
+        ys += (R)exp((double)L0) * J;
+    } else {
+        if (L0 > Ls + 40.0f) {  // keep e^{L - Ls} in range
+            ys *= (R)expf(Ls - L0);
+            Ls = L0;
+        }
+        ys += (R)expf(L0 - Ls) * J;
+    }
+    return fin;
+}
+
+// The persistent walk.  CV: control variate (FP32 paths; F64: residual
+// integrals in FP64); plain: F64 selects the FP64 path version.
+template <bool CV, bool F64, bool WEIGHTED, bool STAGED>
+__global__ void __launch_bounds__(WALK_THREADS, CV ? CVB_MIN_BLOCKS_CV : CVB_MIN_BLOCKS)
+    k_cvb_walk(const __grid_constant__ WalkParams a, const __grid_constant__ CvbArgs b) {
+    constexpr bool P64 = F64 && !CV;  // FP64 paths (plain only)
+    using Q = P<P64>;
+    using T = typename Q::T;
+    using Acc = typename std::conditional<P64, Acc64, Acc32>::type;
+    using R = typename CvLane<F64>::R;
+    __shared__ StageWarp s_stage[STAGED ? WARPS_PER_BLOCK : 1];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned long long paths_done = 0, jumps_done = 0;
+    for (;;) {
+        unsigned int item = 0;
+        if (lane == 0) item = atomicAdd(b.next_item, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= b.n_items) break;
+        const CvbItem it = b.items[item];
+        const CvbPair pr = b.pairs[it.pair];
+        const double2 *ab = CV ? reinterpret_cast<const double2 *>(b.coef + pr.coef) : nullptr;
+        const T t0 = P64 ? (T)pr.t : (T)pr.t32;
+        if (pr.cpe == 0) {
+            // ---- lane layout: lane = entry, all paths in path order ----
+            const int64_t e = (int64_t)it.e0 + lane;
+            if (e < pr.n) {
+                const int32_t i0 = (int32_t)(pr.off + e);
+                const NodeRec start = load_node(a.node, i0);
+                const T delta_start = Q::pot(start, a.node64, i0);
+                Acc acc;
+                CvLane<F64> cl;
+                for (uint64_t p = 0; p < pr.paths; ++p) {
+                    const uint64_t path = pr.path_base + p;
+                    if constexpr (CV) {
+                        Walker<false> w;
+                        w.rec = start; w.j = i0; w.r = pr.t32; w.acc = 0.0f; w.delta = start.delta; w.k = 0;
+                        R ys = (R)0;
+                        float Ls = 0.0f;
+                        while (!cv_event<F64, WEIGHTED>(w, a, (uint32_t)e, path, nullptr, i0, ab, pr.off, ys, Ls)) {
+                        }
+                        cl.end_path(ys, Ls);
+                        jumps_done += w.k;
+                    } else {
+                        Walker<P64> w;
+                        w.rec = start; w.j = i0; w.r = t0; w.acc = (T)0; w.delta = delta_start; w.k = 0;
+                        while (!advance<MCX_EXACT, WEIGHTED, P64>(w, a, (uint32_t)e, path, nullptr, i0)) {
+                        }
+                        const int64_t s = pr.slot + (w.j - pr.off);
+                        if (P64) acc.add(w.acc, (T)__ldg(b.v + s));
+                        else acc.add(w.acc, (T)__ldg(b.vf + s));
+                        jumps_done += w.k;
+                    }
+                }
+                paths_done += pr.paths;
+                const double M = (double)pr.paths;
+                double S1, S2, Mw;
+                if constexpr (CV) {
+                    cl.result(S1, S2, Mw);
+                    const double scale = (Mw == -INFINITY) ? 0.0 : exp(Mw);
+                    const double mu = S1 / M;
+                    double var = M > 1.0 ? (S2 - S1 * mu) / (M - 1.0) : 0.0;
+                    if (var < 0.0) var = 0.0;
+                    const double mv = b.coef[pr.coef + 2 * pr.n + e] + scale * mu;
+                    const double se = scale * sqrt(var / M);
+                    b.mean[pr.slot + e] = mv;
+                    b.sem[pr.slot + e] = se;
+                    if (!isfinite(mv) || !isfinite(se)) atomicOr(a.status, ST_OVERFLOW);
+                } else {
+                    acc.lane_result(S1, S2, Mw);
+                    const double vs = P64 ? 1.0 : ldexp(1.0, b.vexp[it.pair] ? (int)b.vexp[it.pair] - (int)VEXP_BIAS : 0);
+                    finish_entry(S1, S2, Mw, M, vs, b.mean + pr.slot + e, b.sem + pr.slot + e, a.status);
+                }
+            }
+            continue;
+        }
+        // ---- warp layout: one entry, one chunk of its paths, lane refill ----
+        const int64_t e = it.e0;
+        const int32_t i0 = (int32_t)(pr.off + e);
+        const uint64_t p_begin = (uint64_t)it.chunk * pr.chunk;
+        const uint32_t len = (uint32_t)(min(pr.paths, p_begin + pr.chunk) - p_begin);
+        const uint64_t base = pr.path_base + p_begin;
+        const NodeRec start = load_node(a.node, i0);
+        StageWarp &sw = s_stage[STAGED ? warp : 0];
+        const bool staged = STAGED && !P64 && start.deg <= STAGE;
+        if (STAGED) {
+            __syncwarp();  // the previous item's reads of the staged row are done
+            if (lane == 0) sw.start = start;
+            if (staged) stage_row<WEIGHTED>(sw, a, start, lane);
+            __syncwarp();
+        }
+        const StageWarp *swp = staged ? &sw : nullptr;
+        const T delta_start = Q::pot(start, a.node64, i0);
+        uint32_t next = 32, p = (uint32_t)lane;
+        bool active = p < len;
+        uint32_t jumps = 0;
+        double S1, S2, Mw;
+        if constexpr (CV) {
+            Walker<false> w;
+            w.rec = start; w.j = i0; w.r = pr.t32; w.acc = 0.0f; w.delta = start.delta; w.k = 0;
+            R ys = (R)0;
+            float Ls = 0.0f;
+            CvLane<F64> cl;
+            while (__any_sync(0xffffffffu, active)) {
+                bool fin = false;
+                if (active && cv_event<F64, WEIGHTED>(w, a, (uint32_t)e, base + p, swp, i0, ab, pr.off, ys, Ls)) {
+                    fin = true;
+                    cl.end_path(ys, Ls);
+                    jumps += w.k;
+                }
+                const unsigned fm = __ballot_sync(0xffffffffu, fin);
+                if (fm) {
+                    if (fin) {
+                        p = next + (uint32_t)__popc(fm & lt_mask);
+                        active = p < len;
+                        w.rec = start; w.j = i0; w.r = pr.t32; w.acc = 0.0f; w.delta = start.delta; w.k = 0;
+                        ys = (R)0;
+                        Ls = 0.0f;
+                    }
+                    next += (uint32_t)__popc(fm);
+                }
+            }
+            cl.warp_merge(S1, S2, Mw);
+        } else {
+            Walker<P64> w;
+            w.rec = start; w.j = i0; w.r = t0; w.acc = (T)0; w.delta = delta_start; w.k = 0;
+            Acc acc;
+            while (__any_sync(0xffffffffu, active)) {
+                bool fin = false;
+                if (active && advance<MCX_EXACT, WEIGHTED, P64>(w, a, (uint32_t)e, base + p, swp, i0)) {
+                    fin = true;
+                    const int64_t s = pr.slot + (w.j - pr.off);
+                    if (P64) acc.add(w.acc, (T)__ldg(b.v + s));
+                    else acc.add(w.acc, (T)__ldg(b.vf + s));
+                    jumps += w.k;
+                }
+                const unsigned fm = __ballot_sync(0xffffffffu, fin);
+                if (fm) {
+                    if (fin) {
+                        p = next + (uint32_t)__popc(fm & lt_mask);
+                        active = p < len;
+                        w.rec = start; w.j = i0; w.r = t0; w.acc = (T)0; w.delta = delta_start; w.k = 0;
+                    }
+                    next += (uint32_t)__popc(fm);
+                }
+            }
+            acc.warp_merge(S1, S2, Mw);
+        }
+        unsigned long long jl = jumps;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) jl += __shfl_xor_sync(0xffffffffu, jl, o);
+        if (lane == 0) {
+            b.part[pr.part0 + e * pr.cpe + it.chunk] = Partial{S1, S2, Mw};
+            paths_done += len;
+            jumps_done += jl;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        jumps_done += __shfl_xor_sync(0xffffffffu, jumps_done, o);
+        paths_done += __shfl_xor_sync(0xffffffffu, paths_done, o);
+    }
+    if (lane == 0 && paths_done) {
+        unsigned long long *ctr = reinterpret_cast<unsigned long long *>(a.status + 2);
+        atomicAdd(ctr, paths_done);
+        atomicAdd(ctr + 1, jumps_done);
+    }
+}
+
+// Warp-layout pairs: per entry, merge the chunk partials in chunk order; mean
+// = h_i + e^m S1/M (control variate) or e^m S1/M times the v scale (plain).
+__global__ void k_cvb_finish(const CvbPair *__restrict__ pairs, const int32_t *__restrict__ warp_pairs, bool cv,
+                             bool scaled, CvbArgs b, uint32_t *status) {
+    const int32_t k = warp_pairs[blockIdx.y];
+    const CvbPair pr = pairs[k];
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= pr.n) return;
+    const Partial *pp = b.part + pr.part0 + e * pr.cpe;
+    double mx = -INFINITY;
+    for (uint32_t c = 0; c < pr.cpe; ++c) mx = fmax(mx, pp[c].m);
+    double s1 = 0.0, s2 = 0.0;
+    for (uint32_t c = 0; c < pr.cpe; ++c) {
+        const Partial q = pp[c];
+        const double sc = (q.m == -INFINITY) ? 0.0 : exp(q.m - mx);
+        s1 += sc * q.s1;
+        s2 += sc * sc * q.s2;
+    }
+    const double M = (double)pr.paths;
+    if (cv) {
+        const double scale = mx == -INFINITY ? 0.0 : exp(mx);
+        const double mu = s1 / M;
+        double var = M > 1.0 ? (s2 - s1 * mu) / (M - 1.0) : 0.0;
+        if (var < 0.0) var = 0.0;
+        const double mv = b.coef[pr.coef + 2 * pr.n + e] + scale * mu;
+        const double se = scale * sqrt(var / M);
+        b.mean[pr.slot + e] = mv;
+        b.sem[pr.slot + e] = se;
+        if (!isfinite(mv) || !isfinite(se)) atomicOr(status, ST_OVERFLOW);
+    } else {
+        const uint32_t eb = b.vexp[k];
+        const double vs = scaled ? ldexp(1.0, eb ? (int)eb - (int)VEXP_BIAS : 0) : 1.0;
+        finish_entry(s1, s2, mx, M, vs, b.mean + pr.slot + e, b.sem + pr.slot + e, status);
+    }
+}
+
+template <bool CV, bool F64, bool WEIGHTED, bool STAGED>
+void *walk_fn() {
+    return (void *)k_cvb_walk<CV, F64, WEIGHTED, STAGED>;
+}
+
+void *pick_walk(bool cv, bool f64, bool weighted, bool staged) {
+    void *(*table[16])() = {
+        walk_fn<false, false, false, false>, walk_fn<false, false, false, true>, walk_fn<false, false, true, false>,
+        walk_fn<false, false, true, true>,   walk_fn<false, true, false, false>,  walk_fn<false, true, false, true>,
+        walk_fn<false, true, true, false>,   walk_fn<false, true, true, true>,    walk_fn<true, false, false, false>,
+        walk_fn<true, false, false, true>,   walk_fn<true, false, true, false>,   walk_fn<true, false, true, true>,
+        walk_fn<true, true, false, false>,   walk_fn<true, true, false, true>,    walk_fn<true, true, true, false>,
+        walk_fn<true, true, true, true>};
+    return table[(cv ? 8 : 0) + (f64 ? 4 : 0) + (weighted ? 2 : 0) + (staged ? 1 : 0)]();
+}
+
+}  // namespace
+}  // namespace mcx
+
+using namespace mcx;
+
+struct mcx_cvbatch {
+    int32_t problems = 0;
+    int32_t n_pair = 0;
+    int control = MCX_CV_NONE;
+    int precision = MCX_FP32;
+    const mcx_mlp *net = nullptr;
+    int64_t N = 0;        // padded states
+    int64_t slots = 0;    // sum over pairs of n_b
+    int64_t max_n = 0;
+    mcx_plan *plan = nullptr;
+    std::vector<CvbPair> pair_host;
+    std::vector<double> cost_per_path;  // per pair
+    std::vector<uint64_t> paths;        // per problem
+    // per-problem CSR (local indices) on the device, concatenated
+    std::vector<int64_t> csr_rp_off, csr_nz_off;
+    int64_t *rp = nullptr;
+    int32_t *col = nullptr;
+    double *val = nullptr;
+    // per-pair arrays
+    double *v = nullptr;      // [slots]
+    float *vf = nullptr;      // [slots]
+    uint32_t *vexp = nullptr;  // [pairs]
+    double *taylor = nullptr;  // [4 slots]
+    float *feat = nullptr;     // [5 slots]
+    float *y = nullptr;        // [slots]
+    double *coef = nullptr;    // per pair, 32-double aligned
+    int64_t coef_len = 0;
+    double *work = nullptr;    // [3 max_n + 64]
+    double *mean = nullptr, *sem = nullptr;  // [slots]
+    CvbPair *pairs = nullptr;
+    int32_t *warp_pairs = nullptr;
+    int32_t n_warp_pairs = 0;
+    int64_t warp_pairs_max_n = 0;
+    Partial *part = nullptr;
+    int64_t part_cap = 0;
+    CvbItem *items = nullptr;
+    uint64_t items_cap = 0;
+    uint32_t n_items = 0;
+    unsigned int *next_item = nullptr;
+    uint32_t chunk = 2048;
+    int blocks_per_sm = CVB_MIN_BLOCKS;
+    bool staged = true;
+    int sms = 0;
+    double tuned_ms = 0.0;
+    WalkParams wp{};
+    CvbArgs ba{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t walk_node = nullptr;
+};
+
+namespace {
+
+mcx_status cvb_status(cudaError_t e) {
+    if (e == cudaSuccess) return MCX_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return MCX_E_OOM;
+    }
+    return MCX_E_CUDA;
+}
+
+void free_cvbatch(mcx_cvbatch *b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    void *bufs[] = {b->rp, b->col, b->val, b->v, b->vf, b->vexp, b->taylor, b->feat, b->y, b->coef, b->work,
+                    b->mean, b->sem, b->pairs, b->warp_pairs, b->part, b->items, b->next_item};
+    for (void *p : bufs) dev_free(p);
+    if (b->plan) mcx_plan_destroy(b->plan);
+    delete b;
+}
+
+bool cv_mode(const mcx_cvbatch *b) { return b->control != MCX_CV_NONE; }
+
+// Per-pair layout for the current paths and chunk length: lane or warp layout,
+// chunks per entry, partial offsets.  Host only.
+void layout_pairs(mcx_cvbatch *b) {
+    int64_t part = 0;
+    for (auto &pr : b->pair_host) {
+        pr.paths = b->paths[pr.problem];
+        if (pr.paths <= LANE_MODE_MAX_PATHS) {
+            pr.cpe = 0;
+            pr.chunk = pr.paths;
+            pr.part0 = 0;
+            continue;
+        }
+        uint64_t cpe = (pr.paths + b->chunk - 1) / b->chunk;
+        const uint64_t cap = std::max<uint64_t>(1, CVB_ITEMS_PER_PAIR / (uint64_t)pr.n);
+        if (cpe > cap) cpe = cap;
+        const uint64_t min_cpe = (pr.paths + (1ull << 30) - 1) >> 30;  // chunks below 2^30 paths
+        if (cpe < min_cpe) cpe = min_cpe;
+        uint64_t chunk = (pr.paths + cpe - 1) / cpe;
+        chunk = (chunk + 31) / 32 * 32;
+        cpe = (pr.paths + chunk - 1) / chunk;
+        pr.cpe = (uint32_t)cpe;
+        pr.chunk = chunk;
+        pr.part0 = part;
+        part += pr.n * (int64_t)cpe;
+    }
+}
+
+int64_t partials_needed(const mcx_cvbatch *b) {
+    int64_t part = 0;
+    for (const auto &pr : b->pair_host)
+        if (pr.cpe) part += pr.n * (int64_t)pr.cpe;
+    return part;
+}
+
+// Items of the current layout in largest-estimated-cost-first order; with
+// stride > 1 only every stride-th (the autotuner's sample).
+std::vector<CvbItem> make_items(const mcx_cvbatch *b, uint32_t stride) {
+    std::vector<int32_t> order(b->n_pair);
+    for (int32_t k = 0; k < b->n_pair; ++k) order[k] = k;
+    auto item_cost = [b](int32_t k) {
+        const CvbPair &p = b->pair_host[k];
+        const double paths = p.cpe ? (double)p.chunk : 32.0 * (double)p.paths;
+        return paths * b->cost_per_path[k];
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return item_cost(x) > item_cost(y); });
+    std::vector<CvbItem> items;
+    uint64_t idx = 0;
+    for (int32_t k : order) {
+        const CvbPair &p = b->pair_host[k];
+        if (p.cpe == 0) {
+            for (int64_t e = 0; e < p.n; e += 32, ++idx)
+                if (idx % stride == 0) items.push_back(CvbItem{(uint32_t)k, (uint32_t)e, 0u, 0u});
+        } else {
+            for (int64_t e = 0; e < p.n; ++e)
+                for (uint32_t c = 0; c < p.cpe; ++c, ++idx)
+                    if (idx % stride == 0) items.push_back(CvbItem{(uint32_t)k, (uint32_t)e, c, 0u});
+        }
+    }
+    return items;
+}
+
+cudaError_t upload_items(mcx_cvbatch *b, const std::vector<CvbItem> &items, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    if (items.size() + 1 > b->items_cap) {
+        dev_free(b->items);
+        b->items = nullptr;
+        b->items_cap = 0;
+        if ((e = dev_malloc(reinterpret_cast<void **>(&b->items), sizeof(CvbItem) * (items.size() + 1))) !=
+            cudaSuccess)
+            return e;
+        b->items_cap = items.size() + 1;
+    }
+    if (!items.empty())
+        e = cudaMemcpyAsync(b->items, items.data(), sizeof(CvbItem) * items.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    b->n_items = (uint32_t)items.size();
+    b->ba.items = b->items;
+    b->ba.n_items = b->n_items;
+    return e;
+}
+
+// Apply a new layout on the device: pairs, partials, warp-pair list, full item list.
+cudaError_t apply_layout(mcx_cvbatch *b, cudaStream_t st) {
+    layout_pairs(b);
+    cudaError_t e;
+    const int64_t need = partials_needed(b);
+    if (need + 1 > b->part_cap) {
+        dev_free(b->part);
+        b->part = nullptr;
+        b->part_cap = 0;
+        if ((e = dev_malloc(reinterpret_cast<void **>(&b->part), sizeof(Partial) * (size_t)(need + 1))) != cudaSuccess)
+            return e;
+        b->part_cap = need + 1;
+    }
+    std::vector<int32_t> wp;
+    int64_t mx = 0;
+    for (int32_t k = 0; k < b->n_pair; ++k)
+        if (b->pair_host[k].cpe) {
+            wp.push_back(k);
+            mx = std::max(mx, b->pair_host[k].n);
+        }
+    b->n_warp_pairs = (int32_t)wp.size();
+    b->warp_pairs_max_n = mx;
+    if ((e = cudaMemcpyAsync(b->pairs, b->pair_host.data(), sizeof(CvbPair) * b->n_pair, cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess)
+        return e;
+    if (!wp.empty() &&
+        (e = cudaMemcpyAsync(b->warp_pairs, wp.data(), sizeof(int32_t) * wp.size(), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+        return e;
+    b->ba.part = b->part;
+    const uint64_t total = [&]() {
+        uint64_t s = 0;
+        for (const auto &p : b->pair_host) s += p.cpe ? (uint64_t)p.n * p.cpe : (uint64_t)((p.n + 31) / 32);
+        return s;
+    }();
+    if (total >= (1ull << 31)) return cudaErrorInvalidValue;
+    return upload_items(b, make_items(b, 1), st);
+}
+
+// The pre-pass of every pair: control-variate Taylor terms, features,
+// prediction, coefficients; or the scaled FP32 copy of v.
+cudaError_t prepass(mcx_cvbatch *b, cudaStream_t st) {
+    for (int32_t k = 0; k < b->n_pair; ++k) {
+        const CvbPair &pr = b->pair_host[k];
+        const int32_t pb = pr.problem;
+        const int64_t n = pr.n;
+        const int64_t *rp = b->rp + b->csr_rp_off[pb];
+        const int32_t *col = b->col + b->csr_nz_off[pb];
+        const double *val = b->val + b->csr_nz_off[pb];
+        const double *v = b->v + pr.slot;
+        if (cv_mode(b)) {
+            double *T = b->taylor + 4 * pr.slot;
+            float *F = b->feat + 5 * pr.slot;
+            mcx_status rc = mcx_cv_prepare(n, rp, col, val, v, pr.t, b->work, T, F, st);
+            if (rc == MCX_OK && b->control == MCX_CV_LEARNED) rc = mcx_mlp_predict(b->net, n, F, b->y + pr.slot, st);
+            if (rc == MCX_OK)
+                rc = mcx_cv_coefficients(n, rp, col, val, T, b->control == MCX_CV_LEARNED ? b->y + pr.slot : nullptr,
+                                         pr.t, b->work, b->coef + pr.coef, st);
+            if (rc != MCX_OK) return rc == MCX_E_OOM ? cudaErrorMemoryAllocation : cudaErrorUnknown;
+        } else if (b->precision == MCX_FP32) {
+            cudaError_t e = cudaMemsetAsync(b->vexp + k, 0, sizeof(uint32_t), st);
+            if (e != cudaSuccess) return e;
+            const unsigned nb = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8);
+            k_cvb_vexp<<<nb, 256, 0, st>>>(n, v, b->vexp + k);
+            k_cvb_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, v, b->vexp + k, b->vf + pr.slot);
+        }
+    }
+    return cudaGetLastError();
+}
+
+void launch_walk(const mcx_cvbatch *b, cudaStream_t st) {
+    const bool weighted = b->plan->weighted_rows > 0;
+    void *fn = pick_walk(cv_mode(b), b->precision == MCX_FP64, weighted, b->staged);
+    void *args[] = {const_cast<WalkParams *>(&b->wp), const_cast<CvbArgs *>(&b->ba)};
+    cudaLaunchKernel(fn, dim3((unsigned)(b->sms * b->blocks_per_sm)), dim3(WALK_THREADS), args, 0, st);
+}
+
+void launch_finish(const mcx_cvbatch *b, cudaStream_t st) {
+    if (b->n_warp_pairs == 0) return;
+    const dim3 grid((unsigned)((b->warp_pairs_max_n + 255) / 256), (unsigned)b->n_warp_pairs);
+    k_cvb_finish<<<grid, 256, 0, st>>>(b->pairs, b->warp_pairs, cv_mode(b),
+                                       !cv_mode(b) && b->precision == MCX_FP32, b->ba, b->plan->status);
+}
+
+cudaError_t capture(mcx_cvbatch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->walk_node = nullptr;
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t ep = prepass(b, cs);
+        cudaMemsetAsync(b->next_item, 0, sizeof(unsigned int), cs);
+        launch_walk(b, cs);
+        launch_finish(b, cs);
+        e = cudaStreamEndCapture(cs, &b->graph);
+        if (e == cudaSuccess && ep != cudaSuccess) e = ep;
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) return e;
+    size_t nn = 0;
+    cudaGraphGetNodes(b->graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(b->graph, nodes.data(), &nn);
+    const void *wf = pick_walk(cv_mode(b), b->precision == MCX_FP64, b->plan->weighted_rows > 0, b->staged);
+    for (auto nd : nodes) {
+        cudaGraphNodeType ty;
+        cudaGraphNodeGetType(nd, &ty);
+        if (ty != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp;
+        if (cudaGraphKernelNodeGetParams(nd, &kp) == cudaSuccess && kp.func == wf) b->walk_node = nd;
+    }
+    return b->walk_node ? cudaSuccess : cudaErrorUnknown;
+}
+
+cudaError_t run_graph(mcx_cvbatch *b, uint64_t seed, cudaStream_t st) {
+    set_round_keys(b->wp, seed);
+    void *args[] = {&b->wp, &b->ba};
+    cudaKernelNodeParams kp;
+    cudaError_t e = cudaGraphKernelNodeGetParams(b->walk_node, &kp);
+    if (e != cudaSuccess) return e;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    if ((e = cudaGraphExecKernelNodeSetParams(b->exec, b->walk_node, &kp)) != cudaSuccess) return e;
+    return cudaGraphLaunch(b->exec, st);
+}
+
+std::string signature(const mcx_cvbatch *b) {
+    char buf[512];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp pr;
+    cudaGetDeviceProperties(&pr, dev);
+    uint64_t paths = 0;
+    int warp_pairs = 0;
+    for (const auto &p : b->pair_host) {
+        paths += p.paths * (uint64_t)p.n;
+        warp_pairs += p.paths > LANE_MODE_MAX_PATHS;
+    }
+    snprintf(buf, sizeof buf, "%s|cvbatch|control=%d|prec=%d|pairs=%d|warp_pairs=%d|states=%lld|paths=%llu|nnz=%lld|w=%d",
+             pr.name, b->control, b->precision, b->n_pair, warp_pairs, (long long)b->N, (unsigned long long)paths,
+             (long long)b->plan->nnz_off, b->plan->weighted_rows > 0 ? 1 : 0);
+    return buf;
+}
+
+// Time the walk alone on every 8th item for each (chunk, blocks per SM, staging)
+// setting and keep the fastest.  Chunk and staging matter only for warp-layout pairs.
+cudaError_t autotune(mcx_cvbatch *b, cudaStream_t st) {
+    bool any_warp = false;
+    for (const auto &p : b->pair_host) any_warp |= b->paths[p.problem] > LANE_MODE_MAX_PATHS;
+    const std::vector<uint32_t> Ls = any_warp ? std::vector<uint32_t>{512, 1024, 2048, 4096}
+                                              : std::vector<uint32_t>{2048};
+    const std::vector<int> bpss = {2, 3, 4, 6};
+    const std::vector<int> stg = any_warp ? std::vector<int>{0, 1} : std::vector<int>{1};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e300;
+    uint32_t bL = b->chunk;
+    int bb = b->blocks_per_sm;
+    bool bs = b->staged;
+    cudaError_t e = cudaSuccess;
+    for (uint32_t L : Ls) {
+        b->chunk = L;
+        layout_pairs(b);
+        if (partials_needed(b) + 1 > b->part_cap) {  // the full run's partials cover every sample
+            if ((e = apply_layout(b, st)) != cudaSuccess) break;
+        }
+        if ((e = cudaMemcpyAsync(b->pairs, b->pair_host.data(), sizeof(CvbPair) * b->n_pair, cudaMemcpyHostToDevice,
+                                 st)) != cudaSuccess)
+            break;
+        if ((e = upload_items(b, make_items(b, 8), st)) != cudaSuccess) break;
+        for (int bc : bpss) {
+            for (int s : stg) {
+                b->blocks_per_sm = bc;
+                b->staged = s != 0;
+                float ms = 0.f;
+                for (int rep = 0; rep < 2; ++rep) {  // warm, then timed
+                    cudaMemsetAsync(b->next_item, 0, sizeof(unsigned int), st);
+                    cudaEventRecord(e0, st);
+                    launch_walk(b, st);
+                    cudaEventRecord(e1, st);
+                    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                }
+                if (e != cudaSuccess) break;
+                if (ms < best) {
+                    best = ms;
+                    bL = L;
+                    bb = bc;
+                    bs = s != 0;
+                }
+            }
+            if (e != cudaSuccess) break;
+        }
+        if (e != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->chunk = bL;
+    b->blocks_per_sm = bb;
+    b->staged = bs;
+    b->tuned_ms = best < 1e300 ? best : 0.0;
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int control, const mcx_mlp *net,
+                              int precision, const char *tune_cache, void *stream, mcx_cvbatch **out) {
+    if (!out) return MCX_E_INVALID;
+    *out = nullptr;
+    if (count < 1 || !pr) return MCX_E_INVALID;
+    if (control != MCX_CV_NONE && control != MCX_CV_TAYLOR && control != MCX_CV_LEARNED) return MCX_E_INVALID;
+    if (control == MCX_CV_LEARNED && !net) return MCX_E_INVALID;
+    if (precision != MCX_FP32 && precision != MCX_FP64) return MCX_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int64_t N = 0, nnz = 0, slots = 0, max_n = 0, coef_len = 0;
+    std::vector<int64_t> off(count);
+    for (int32_t i = 0; i < count; ++i) {
+        const mcx_cv_problem &p = pr[i];
+        if (p.n < 1 || p.nnz < 0 || !p.row_ptr || (p.nnz > 0 && (!p.col || !p.val)) || p.n_rhs < 1 || !p.v ||
+            !p.t || p.paths < 1 || p.paths > (1ull << 40))
+            return MCX_E_INVALID;
+        if (p.row_ptr[0] != 0 || p.row_ptr[p.n] != p.nnz) return MCX_E_INVALID;
+        for (int32_t r = 0; r < p.n_rhs; ++r)
+            if (!(p.t[r] > 0.0) || !isfinite(p.t[r])) return MCX_E_INVALID;
+        for (int64_t q = 0; q < p.nnz; ++q)
+            if (p.col[q] < 0 || p.col[q] >= p.n) return MCX_E_INVALID;
+        off[i] = N;
+        N += (p.n + CVB_BLOCK - 1) / CVB_BLOCK * CVB_BLOCK;
+        nnz += p.nnz;
+        slots += p.n * p.n_rhs;
+        max_n = std::max(max_n, p.n);
+        coef_len += p.n_rhs * ((3 * p.n + 31) / 32 * 32);
+    }
+    if (N >= (int64_t)0x7fffffff) return MCX_E_INVALID;
+    mcx_cvbatch *b = new (std::nothrow) mcx_cvbatch();
+    if (!b) return MCX_E_OOM;
+    b->problems = count;
+    b->control = control;
+    b->precision = precision;
+    b->net = net;
+    b->N = N;
+    b->slots = slots;
+    b->max_n = max_n;
+    b->coef_len = coef_len;
+    // block-diagonal CSR (host), the per-problem local CSRs, the pairs
+    std::vector<int64_t> rp(N + 1, 0);
+    std::vector<int32_t> col((size_t)std::max<int64_t>(nnz, 1));
+    std::vector<double> val((size_t)std::max<int64_t>(nnz, 1));
+    std::vector<int64_t> lrp;
+    std::vector<double> vall((size_t)std::max<int64_t>(slots, 1));
+    int64_t w = 0, slot = 0, coef = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        const mcx_cv_problem &p = pr[i];
+        b->csr_rp_off.push_back((int64_t)lrp.size());
+        b->csr_nz_off.push_back(w);
+        double lam = 0.0;  // mean jump rate (cost model)
+        for (int64_t r = 0; r < p.n; ++r) {
+            rp[off[i] + r] = w;
+            lrp.push_back(p.row_ptr[r]);
+            for (int64_t q = p.row_ptr[r]; q < p.row_ptr[r + 1]; ++q) {
+                col[w] = (int32_t)(p.col[q] + off[i]);
+                val[w] = p.val[q];
+                if (p.col[q] != r && p.val[q] > 0.0) lam += p.val[q];
+                ++w;
+            }
+        }
+        lrp.push_back(p.row_ptr[p.n]);
+        lam /= (double)p.n;
+        const int64_t end = (i + 1 < count) ? off[i + 1] : N;
+        for (int64_t r = off[i] + p.n; r < end; ++r) rp[r] = w;
+        b->paths.push_back(p.paths);
+        for (int32_t r = 0; r < p.n_rhs; ++r) {
+            CvbPair q{};
+            q.off = off[i];
+            q.n = p.n;
+            q.slot = slot;
+            q.coef = coef;
+            q.paths = p.paths;
+            q.path_base = (uint64_t)b->pair_host.size() << 40;
+            q.t = p.t[r];
+            q.t32 = (float)p.t[r];
+            q.problem = i;
+            q.rhs = r;
+            memcpy(vall.data() + slot, p.v + (size_t)r * (size_t)p.n, sizeof(double) * (size_t)p.n);
+            b->pair_host.push_back(q);
+            b->cost_per_path.push_back(1.0 + p.t[r] * lam);
+            slot += p.n;
+            coef += (3 * p.n + 31) / 32 * 32;
+        }
+    }
+    rp[N] = w;
+    b->n_pair = (int32_t)b->pair_host.size();
+    mcx_status rc = mcx_plan_create(N, w, rp.data(), col.data(), val.data(), MCX_PLAN_HOST_INPUT, stream, &b->plan);
+    if (rc != MCX_OK) {
+        b->plan = nullptr;
+        free_cvbatch(b);
+        return rc;
+    }
+    cudaError_t e = cudaSuccess;
+    const bool cv = control != MCX_CV_NONE;
+    const size_t sl = (size_t)std::max<int64_t>(slots, 1);
+    do {
+        // the local CSRs for the pre-pass (Taylor terms, rates, features, coefficients)
+        std::vector<int32_t> lcol((size_t)std::max<int64_t>(nnz, 1));
+        for (int32_t i = 0; i < count; ++i)
+            for (int64_t q = 0; q < pr[i].nnz; ++q) lcol[b->csr_nz_off[i] + q] = pr[i].col[q];
+        if ((e = dev_malloc(reinterpret_cast<void **>(&b->rp), sizeof(int64_t) * lrp.size())) != cudaSuccess) break;
+        if ((e = dev_malloc(reinterpret_cast<void **>(&b->col), sizeof(int32_t) * lcol.size())) != cudaSuccess) break;
+        if ((e = dev_malloc(reinterpret_cast<void **>(&b->val), sizeof(double) * val.size())) != cudaSuccess) break;
+        if ((e = dev_malloc(reinterpret_cast<void **>(&b->v), sizeof(double) * sl)) != cudaSuccess) break;
+        if ((e = dev_malloc(reinterpret_cast<void **>(&b->mean), sizeof(double) * sl)) != cudaSuccess) break;
+        if ((e = dev_malloc(reinterpret_cast<void **>(&b->sem), sizeof(double) * sl)) != cudaSuccess) break;
+        if ((e = dev_malloc(reinterpret_cast<void **>(&b->pairs), sizeof(CvbPair) * b->n_pair)) != cudaSuccess) break;
+        if ((e = dev_malloc(reinterpret_cast<void **>(&b->warp_pairs), sizeof(int32_t) * b->n_pair)) != cudaSuccess)
+            break;
+        if ((e = dev_malloc(reinterpret_cast<void **>(&b->vexp), sizeof(uint32_t) * b->n_pair)) != cudaSuccess) break;
+        if ((e = dev_malloc(reinterpret_cast<void **>(&b->next_item), 16)) != cudaSuccess) break;
+        if (cv) {
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->taylor), 4 * sizeof(double) * sl)) != cudaSuccess) break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->feat), 5 * sizeof(float) * sl)) != cudaSuccess) break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->y), sizeof(float) * sl)) != cudaSuccess) break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->coef), sizeof(double) * (size_t)coef_len)) !=
+                cudaSuccess)
+                break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->work), sizeof(double) * (size_t)(3 * max_n + 64))) !=
+                cudaSuccess)
+                break;
+        } else {
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->vf), sizeof(float) * sl)) != cudaSuccess) break;
+        }
+        cudaMemsetAsync(b->vexp, 0, sizeof(uint32_t) * b->n_pair, st);
+        cudaMemcpyAsync(b->rp, lrp.data(), sizeof(int64_t) * lrp.size(), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(b->col, lcol.data(), sizeof(int32_t) * lcol.size(), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(b->val, val.data(), sizeof(double) * val.size(), cudaMemcpyHostToDevice, st);
+        if ((e = cudaMemcpyAsync(b->v, vall.data(), sizeof(double) * sl, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            break;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+        WalkParams &wp = b->wp;
+        wp.node = b->plan->node;
+        wp.node64 = b->plan->node64;
+        wp.edge_col = b->plan->edge_col;
+        wp.edge16 = b->plan->edge16;
+        wp.nsteps = 1;
+        wp.n = N;
+        wp.max_events = 1u << 30;
+        wp.status = b->plan->status;
+        CvbArgs &ba = b->ba;
+        ba.pairs = b->pairs;
+        ba.next_item = b->next_item;
+        ba.coef = b->coef;
+        ba.v = b->v;
+        ba.vf = b->vf;
+        ba.vexp = b->vexp;
+        ba.mean = b->mean;
+        ba.sem = b->sem;
+        // one pre-pass outside the graph, so the autotuner's walks read real coefficients
+        if ((e = prepass(b, st)) != cudaSuccess) break;
+        // schedule: cached, else autotuned
+        const std::string key = signature(b);
+        long L = 0, k = 0, s = 1;
+        if (tune_cache_get(tune_cache, key, "chunk", &L) && tune_cache_get(tune_cache, key, "blocks_per_sm", &k) &&
+            L > 0 && k > 0) {
+            tune_cache_get(tune_cache, key, "staged", &s);
+            b->chunk = (uint32_t)L;
+            b->blocks_per_sm = (int)k;
+            b->staged = s != 0;
+        } else {
+            set_round_keys(b->wp, 0x5eed);
+            if ((e = autotune(b, st)) != cudaSuccess) break;
+            tune_cache_put(tune_cache, key,
+                           {{"chunk", (long)b->chunk}, {"blocks_per_sm", (long)b->blocks_per_sm},
+                            {"staged", b->staged ? 1L : 0L}},
+                           b->tuned_ms);
+        }
+        if ((e = apply_layout(b, st)) != cudaSuccess) break;
+        if ((e = capture(b)) != cudaSuccess) break;
+        cudaMemsetAsync(b->plan->status, 0, 4 * STATUS_SYNC_WORDS, st);  // the tuning runs' statistics
+        e = cudaStreamSynchronize(st);
+    } while (0);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        free_cvbatch(b);
+        return cvb_status(e);
+    }
+    *out = b;
+    return MCX_OK;
+}
+
+mcx_status mcx_cvbatch_set_paths(mcx_cvbatch *b, const uint64_t *paths, void *stream) {
+    if (!b || !paths) return MCX_E_INVALID;
+    for (int32_t i = 0; i < b->problems; ++i)
+        if (paths[i] < 1 || paths[i] > (1ull << 40)) return MCX_E_INVALID;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);  // no run of the old layout in flight
+    if (e != cudaSuccess) return cvb_status(e);
+    for (int32_t i = 0; i < b->problems; ++i) b->paths[i] = paths[i];
+    if ((e = apply_layout(b, st)) != cudaSuccess) return cvb_status(e);
+    if ((e = capture(b)) != cudaSuccess) return cvb_status(e);
+    return cvb_status(cudaStreamSynchronize(st));
+}
+
+mcx_status mcx_cvbatch_run(mcx_cvbatch *b, uint64_t seed, void *stream) {
+    if (!b) return MCX_E_INVALID;
+    return cvb_status(run_graph(b, seed, static_cast<cudaStream_t>(stream)));
+}
+
+mcx_status mcx_cvbatch_result(const mcx_cvbatch *b, int32_t problem, int32_t rhs, double *x, double *sem,
+                              void *stream) {
+    if (!b || !x) return MCX_E_INVALID;
+    for (const auto &p : b->pair_host) {
+        if (p.problem != problem || p.rhs != rhs) continue;
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        cudaError_t e = cudaMemcpyAsync(x, b->mean + p.slot, sizeof(double) * p.n, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && sem)
+            e = cudaMemcpyAsync(sem, b->sem + p.slot, sizeof(double) * p.n, cudaMemcpyDeviceToDevice, st);
+        return cvb_status(e);
+    }
+    return MCX_E_INVALID;
+}
+
+mcx_status mcx_cvbatch_coefficients(const mcx_cvbatch *b, int32_t problem, int32_t rhs, double *coef,
+                                    void *stream) {
+    if (!b || !coef || !cv_mode(b)) return MCX_E_INVALID;
+    for (const auto &p : b->pair_host) {
+        if (p.problem != problem || p.rhs != rhs) continue;
+        return cvb_status(cudaMemcpyAsync(coef, b->coef + p.coef, sizeof(double) * 3 * (size_t)p.n,
+                                          cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+    }
+    return MCX_E_INVALID;
+}
+
+mcx_status mcx_cvbatch_get_info(const mcx_cvbatch *b, mcx_cvbatch_info *info) {
+    if (!b || !info) return MCX_E_INVALID;
+    info->problems = b->problems;
+    info->pairs = b->n_pair;
+    info->states = b->N;
+    uint64_t total = 0;
+    for (const auto &p : b->pair_host) total += p.paths * (uint64_t)p.n;
+    info->total_paths = total;
+    info->work_items = b->n_items;
+    info->chunk = b->chunk;
+    info->blocks_per_sm = b->blocks_per_sm;
+    info->grid = b->sms * b->blocks_per_sm;
+    info->staged = b->staged ? 1 : 0;
+    info->control = b->control;
+    info->tuned_ms = b->tuned_ms;
+    return MCX_OK;
+}
+
+mcx_status mcx_cvbatch_sync(mcx_cvbatch *b, void *stream, mcx_stats *stats) {
+    if (!b) return MCX_E_INVALID;
+    mcx_status rc = mcx_sync(b->plan, stream, stats);
+    if (rc == MCX_OK && b->control == MCX_CV_LEARNED) rc = mcx_mlp_sync(const_cast<mcx_mlp *>(b->net), stream);
+    return rc;
+}
+
+void mcx_cvbatch_destroy(mcx_cvbatch *b) {
+    if (!b) return;
+    cudaDeviceSynchronize();
+    free_cvbatch(b);
+}
+
+}  // extern "C"

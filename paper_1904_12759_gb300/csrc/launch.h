@@ -60,6 +60,15 @@ cudaError_t launch_estimate_forward(mcx_plan *plan, const double *v, double t, i
 // without device-wide synchronisation).
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t st);
 void pool_free(void *p, cudaStream_t st);
+// Device allocations outside the pool (grow-only scratch, batch and network
+// arrays).  Like pool_alloc they honour the failure-injection test hook
+// (mcx_debug_fail_alloc): the armed allocation returns cudaErrorMemoryAllocation.
+cudaError_t dev_malloc(void **p, size_t bytes);
+template <typename T>
+inline cudaError_t dev_malloc(T **p, size_t bytes) {
+    return dev_malloc(reinterpret_cast<void **>(p), bytes);
+}
+void dev_free(void *p);
 cudaError_t launch_total_communicability(mcx_plan *plan, double t, int mode, int nsteps, uint64_t paths,
                                          uint64_t seed, uint64_t path_offset, int precision, double *tc, double *sem,
                                          cudaStream_t st);

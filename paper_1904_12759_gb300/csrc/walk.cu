@@ -781,10 +781,10 @@ cudaError_t launch_estimate(mcx_plan *plan, const EstimateArgs &a, cudaStream_t 
     if (c.cpe > 1) {
         const size_t need = sizeof(Partial) * (size_t)c.n_chunks;
         if (plan->scratch_bytes < need) {
-            cudaFree(plan->scratch);
+            dev_free(plan->scratch);
             plan->scratch = nullptr;
             plan->scratch_bytes = 0;
-            cudaError_t e = cudaMalloc(&plan->scratch, need);
+            cudaError_t e = dev_malloc(&plan->scratch, need);
             if (e != cudaSuccess) return e;
             plan->scratch_bytes = need;
         }
@@ -814,11 +814,11 @@ cudaError_t fwd_scratch(mcx_plan *plan, FwdScratch *fs) {
     const size_t need = seg(16 * (size_t)n) + seg(8 * (size_t)G) + seg(8 * (size_t)G) + seg(8 * (size_t)n) +
                         seg(8 * (size_t)m) + seg(4 * (size_t)m) + seg(8) + seg(8);
     if (plan->fwd_bytes < need) {
-        cudaFree(plan->fwd);
+        dev_free(plan->fwd);
         plan->fwd = nullptr;
         plan->fwd_bytes = 0;
         plan->fwd_ones = false;
-        cudaError_t e = cudaMalloc(&plan->fwd, need);
+        cudaError_t e = dev_malloc(&plan->fwd, need);
         if (e != cudaSuccess) return e;
         plan->fwd_bytes = need;
     }
@@ -971,10 +971,10 @@ cudaError_t launch_total_communicability(mcx_plan *plan, double t, int mode, int
     const uint64_t n_warps = (paths + chunk - 1) / chunk;
     const size_t need = sizeof(Partial) * (size_t)n_warps;
     if (plan->scratch_bytes < need) {
-        cudaFree(plan->scratch);
+        dev_free(plan->scratch);
         plan->scratch = nullptr;
         plan->scratch_bytes = 0;
-        if ((e = cudaMalloc(&plan->scratch, need)) != cudaSuccess) return e;
+        if ((e = dev_malloc(&plan->scratch, need)) != cudaSuccess) return e;
         plan->scratch_bytes = need;
     }
     p.partials = static_cast<Partial *>(plan->scratch);
