@@ -56,6 +56,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle CPU time for cpu_baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tta", action="store_true",
+                    help="skip the learned control variate's time-to-accuracy study in the default line")
     ap.add_argument("--generators", type=int, default=256, help="ctmc_batch: number of generators")
     ap.add_argument("--tune-cache", default=None, help="ctmc_batch: schedule cache file (JSON lines)")
     ap.add_argument("--workload", default="erdos_renyi",
@@ -452,116 +454,214 @@ def run_heat3d(args):
     plan.close()
 
 
-def run_ba_cv(args):
-    """Learned control variate vs plain MC: time to 1e-2 relative L2 error on the full
-    vector exp(beta A) v, A the adjacency of a Barabasi-Albert graph (n = 4e6, m = 5),
-    beta = 0.5/lambda_max, v ~ U[0,1).  The network is trained first (reported
-    separately) on 8 BA(1e5, 5) graphs labelled by the Taylor-only control-variate
-    estimator with 256 paths per node.  GPU time per method includes every kernel the
-    method needs: features and Taylor terms, network, coefficients, walk, reduction."""
+# ---------------------------------------------------------------------------
+# Time to accuracy of the learned control variate (BA n = 4e6), batched form
+# ---------------------------------------------------------------------------
+BA_N, BA_M = 4 * 10 ** 6, 5
+TRAIN_SEEDS = range(1, 9)
+TRAIN_N = 10 ** 5
+
+
+def _gen_ba_inputs(outdir):
+    """Child process (spawned before any CUDA call): the BA graphs of the
+    time-to-accuracy study written as .npy files."""
+    import numpy as np
+
+    import workloads as W
+
+    for seed in TRAIN_SEEDS:
+        c = W.barabasi_albert(TRAIN_N, BA_M, seed)
+        np.save(os.path.join(outdir, f"train{seed}_rp.npy"), c.row_ptr)
+        np.save(os.path.join(outdir, f"train{seed}_col.npy"), c.col)
+        np.save(os.path.join(outdir, f"train{seed}_v.npy"), W.uniform_vector(TRAIN_N, seed + 100))
+    c = W.barabasi_albert(BA_N, BA_M, SEED)
+    np.save(os.path.join(outdir, "target_v.npy"), W.uniform_vector(BA_N, SEED))
+    np.save(os.path.join(outdir, "target_col.npy"), c.col)
+    np.save(os.path.join(outdir, "target_rp.npy"), c.row_ptr)  # written last: marks completion
+
+
+class BAInputs:
+    """Generates the BA inputs in a spawned process while the GPU is busy elsewhere."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        import tempfile
+
+        self.dir = tempfile.mkdtemp(prefix="mcx_ba_")
+        self.proc = mp.get_context("spawn").Process(target=_gen_ba_inputs, args=(self.dir,))
+        self.proc.start()
+
+    def load(self):
+        import numpy as np
+
+        import workloads as W
+
+        self.proc.join()
+        if self.proc.exitcode != 0:
+            raise RuntimeError(f"BA input generation failed ({self.proc.exitcode})")
+
+        def csr(prefix, n):
+            rp = np.load(os.path.join(self.dir, prefix + "_rp.npy"))
+            col = np.load(os.path.join(self.dir, prefix + "_col.npy"))
+            return W.CSR(n, rp, col, np.ones(col.size))
+
+        train = [(csr(f"train{s}", TRAIN_N), np.load(os.path.join(self.dir, f"train{s}_v.npy"))) for s in TRAIN_SEEDS]
+        target = (csr("target", BA_N), np.load(os.path.join(self.dir, "target_v.npy")))
+        return train, target
+
+    def close(self):
+        import shutil
+
+        if self.proc.is_alive():
+            self.proc.terminate()
+        shutil.rmtree(self.dir, ignore_errors=True)
+
+
+def _time_to_accuracy(inputs, seeds=5, verbose=False):
+    """GPU time to relative L2 error 1e-2 (and 1e-3) of the full vector exp(beta A) v,
+    A the adjacency of BA(n = 4e6, m = 5), beta = 0.5/lambda_max, v ~ U[0,1), for plain
+    MC, the Taylor-only control variate and the learned one, all through the batched
+    form (mcx_cvbatch_run: one graph launch per run, pre-pass + walk + finish inside the
+    timed events).  The network is trained first, on the GPU, in this run: labels from
+    the batched Taylor-only estimator (256 paths per node) on 8 BA(1e5, 5) graphs, then
+    30 epochs of Adam; its time is reported separately.  For each method the paths per
+    entry M double from 1; every M runs `seeds` independent seeds, and M counts as
+    reaching a target when the worst seed's error does; a sweep stops once the worst
+    seed is at or below 1e-3 (or at its largest M).  The FP64 Taylor oracle scores
+    each run outside the timed events."""
     import numpy as np
     import torch
 
     import paper_1904_12759_gb300 as P
-    import workloads as W
     from oracle import dense as OD
 
-    torch.cuda.set_device(0)
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
 
     def dev(c):
         return (torch.as_tensor(c.row_ptr).cuda(), torch.as_tensor(c.col).cuda(), torch.as_tensor(c.val).cuda())
 
-    # ---- training (once) ----
-    t_train0 = time.perf_counter()
-    graphs = [(W.barabasi_albert(10 ** 5, 5, seed), W.uniform_vector(10 ** 5, seed + 100)) for seed in range(1, 9)]
+    import tempfile
+
+    cache = os.path.join(tempfile.gettempdir(), f"mcx_cvbatch_tune_{os.getpid()}.jsonl")
+    train, (csr, v) = inputs
+    # ---- training (once, reported separately) ----
+    t0 = time.perf_counter()
     e0, e1, e2 = ev(), ev(), ev()
     e0.record()
-    feats, tgts = [], []
-    for seed, (csr, vh) in enumerate(graphs, start=1):
-        rp, col, val = dev(csr)
-        vd = torch.as_tensor(vh).cuda()
+    probs, feats, taylor, ts = [], [], [], []
+    for c, vh in train:
+        rp, col, val = dev(c)
         lam, _ = P.power_iteration(rp, col, val, max_iters=20000, tol=1e-9)
         t = 0.5 / lam
-        plan = P.Plan(rp, col, val)
-        T, F = P.cv_prepare(rp, col, val, vd, t)
-        x, _ = plan.estimate_cv(P.cv_coefficients(rp, col, val, T, None, t), t, 256, seed=seed)
+        T, F = P.cv_prepare(rp, col, val, torch.as_tensor(vh).cuda(), t)
         feats.append(F)
-        tgts.append(P.cv_targets(x, T, t))
-        plan.close()
+        taylor.append(T)
+        ts.append(t)
+        probs.append(dict(row_ptr=c.row_ptr, col=c.col, val=c.val, v=vh, t=t, paths=256))
+    labels = P.CVBatch(probs, control="taylor", tune_cache=cache)
+    labels.run(seed=1)
+    tgts = [P.cv_targets(labels.result(k)[0], taylor[k], ts[k]) for k in range(len(train))]
+    labels.close()
     e1.record()
     net = P.MLP(seed=0)
     losses = net.fit(torch.cat(feats), torch.cat(tgts), epochs=30, batch=4096, lr=2e-3, seed=1)
     e2.record()
     torch.cuda.synchronize()
-    train = {"graphs": 8, "n": 10 ** 5, "label_paths": 256, "epochs": 30, "batch": 4096,
-             "labels_ms": e0.elapsed_time(e1), "fit_ms": e1.elapsed_time(e2),
-             "wall_s": time.perf_counter() - t_train0, "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
-    # ---- target graph ----
-    csr = W.barabasi_albert(4 * 10 ** 6, 5, SEED)
-    v = W.uniform_vector(csr.n, SEED)
+    training = {"graphs": len(train), "n": TRAIN_N, "label_paths": 256, "labels": "batched Taylor-only CV",
+                "epochs": 30, "batch": 4096, "labels_ms": round(e0.elapsed_time(e1), 3),
+                "fit_ms": round(e1.elapsed_time(e2), 3), "wall_s": round(time.perf_counter() - t0, 2),
+                "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
+    del feats, taylor
+    # ---- target problem ----
     rp, col, val = dev(csr)
-    vd = torch.as_tensor(v).cuda()
     lam, iters = P.power_iteration(rp, col, val, max_iters=20000, tol=1e-9)
     t = 0.5 / lam
-    x_ref = OD.taylor_expmv(csr.to_scipy(), t, v, norm_bound=lam)  # A, v >= 0: one sub-step, positive terms
+    desc = [dict(row_ptr=csr.row_ptr, col=csr.col, val=csr.val, v=v, t=t, paths=64)]
+    # the FP64 Taylor oracle scores each run outside the timed events (A, v >= 0: positive terms)
+    x_ref = OD.taylor_expmv(csr.to_scipy(), t, v, norm_bound=lam)
     xn = float(np.linalg.norm(x_ref))
-    plan = P.Plan(rp, col, val)
-    out = (torch.empty(csr.n, dtype=torch.float64, device="cuda"), torch.empty(csr.n, dtype=torch.float64, device="cuda"))
-
-    def run(method, M, seed):
-        e = [ev() for _ in range(5)]
-        e[0].record()
-        if method == "plain":
-            m, _ = plan.estimate(vd, t, M, seed=seed, out=out)
-            e[4].record()
-            torch.cuda.synchronize()
-            phases = {"walk": e[0].elapsed_time(e[4])}
-        else:
-            T, F = P.cv_prepare(rp, col, val, vd, t)
-            e[1].record()
-            y = net.predict(F) if method == "learned_cv" else None
-            e[2].record()
-            coef = P.cv_coefficients(rp, col, val, T, y, t)
-            e[3].record()
-            m, _ = plan.estimate_cv(coef, t, M, seed=seed, out=out)
-            e[4].record()
-            torch.cuda.synchronize()
-            phases = {"taylor_features": e[0].elapsed_time(e[1]), "network": e[1].elapsed_time(e[2]),
-                      "coefficients": e[2].elapsed_time(e[3]), "walk": e[3].elapsed_time(e[4])}
-        err = float(np.linalg.norm(m.cpu().numpy() - x_ref)) / xn
-        return e[0].elapsed_time(e[4]), err, {k: round(v, 3) for k, v in phases.items()}
-
-    for mth in ("plain", "taylor_cv", "learned_cv"):  # warm
-        run(mth, 1, 999)
-    results = {}
-    with ClockSampler(0) as clk:
-        for mth, mmax in (("plain", 1 << 15), ("taylor_cv", 1 << 12), ("learned_cv", 1 << 12)):
-            sweep = []
-            M = 1
-            while M <= mmax:
-                ms, err, ph = run(mth, M, SEED + M)
-                sweep.append({"M": M, "ms": round(ms, 3), "rel_l2": err, "phases_ms": ph})
-                if err <= 1e-3:
-                    break
-                M *= 2
-            hit = next((r for r in sweep if r["rel_l2"] <= 1e-2), None)
-            hit3 = next((r for r in sweep if r["rel_l2"] <= 1e-3), None)
-            results[mth] = {"time_to_1e-2_ms": hit["ms"] if hit else None, "M": hit["M"] if hit else None,
-                            "time_to_1e-3_ms": hit3["ms"] if hit3 else None, "sweep": sweep}
-    tp = results["plain"]["time_to_1e-2_ms"]
-    tl = results["learned_cv"]["time_to_1e-2_ms"]
-    line = {"metric": "GPU time to 1e-2 relative L2 error, learned CV", "value": tl, "unit": "ms",
-            "higher_is_better": False, "n_gpus": 1, "dtype": "f32 paths, f64 accumulation", "data": "synthetic",
-            "config": {"workload": "ba_cv", "n": csr.n, "m": 5, "beta": "0.5/lambda_max", "lambda_max": lam,
-                       "power_iters": iters, "v": "U[0,1)", "target": "relative L2 error 1e-2 vs FP64 Taylor oracle"},
-            "speedup_vs_plain": (tp / tl) if (tp and tl) else None,
-            "speedup_vs_plain_lower_bound": (None if tp or not tl else
-                                             results["plain"]["sweep"][-1]["ms"] / tl),
-            "results": results, "training": train, "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
-    plan.close()
+    stream = torch.cuda.current_stream()
+    limits = {"plain": 1 << 15, "taylor_cv": 1 << 12, "learned_cv": 1 << 12}
+    methods = {}
+    for method, control in (("plain", "none"), ("taylor_cv", "taylor"), ("learned_cv", "learned")):
+        b = P.CVBatch(desc, control=control, net=net if control == "learned" else None, tune_cache=cache)
+        info = b.info()
+        rows = []
+        M = 1
+        while M <= limits[method]:
+            b.set_paths([M])
+            b.run(seed=999)  # warm (graph upload)
+            ms, errs = [], []
+            for s in range(seeds):
+                a, c = ev(), ev()
+                a.record(stream)
+                b.run(seed=SEED + 1000 * s + M)
+                c.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(c))
+                errs.append(float(np.linalg.norm(b.result(0)[0].cpu().numpy() - x_ref)) / xn)
+            st = b.sync()
+            assert st["status_bits"] == 0, st
+            rows.append({"M": M, "ms_median": round(float(np.median(ms)), 3), "ms_max": round(max(ms), 3),
+                         "rel_l2_worst": max(errs), "rel_l2_median": float(np.median(errs))})
+            if max(errs) <= 1e-3:
+                break
+            M *= 2
+        b.close()
+        hit2 = next((x for x in rows if x["rel_l2_worst"] <= 1e-2), None)
+        hit3 = next((x for x in rows if x["rel_l2_worst"] <= 1e-3), None)
+        allw = [x["rel_l2_worst"] for x in rows]
+        methods[method] = {
+            "time_to_1e-2_ms": hit2["ms_median"] if hit2 else None, "M_1e-2": hit2["M"] if hit2 else None,
+            "time_to_1e-3_ms": hit3["ms_median"] if hit3 else None, "M_1e-3": hit3["M"] if hit3 else None,
+            "reached_1e-2": hit2 is not None, "max_M_tried": rows[-1]["M"],
+            "worst_error_range": [min(allw), max(allw)],
+            "schedule": {k: info[k] for k in ("chunk", "blocks_per_sm", "staged")},
+            "sweep": rows if verbose else [{k: x[k] for k in ("M", "ms_median", "rel_l2_worst")} for x in rows]}
     net.close()
+    pl, lc = methods["plain"], methods["learned_cv"]
+    if pl["reached_1e-2"] and lc["reached_1e-2"]:
+        verdict = {"learned_vs_plain_1e-2": pl["time_to_1e-2_ms"] / lc["time_to_1e-2_ms"]}
+    else:
+        verdict = {"learned_vs_plain_1e-2": None,
+                   "plain_mc": (f"did not reach 1e-2 up to M = {pl['max_M_tried']} paths per entry "
+                                f"(worst-seed error {pl['worst_error_range'][0]:.3g} .. {pl['worst_error_range'][1]:.3g}); "
+                                f"its last run took {pl['sweep'][-1]['ms_median']:.1f} ms")}
+    tl, tt = lc["time_to_1e-3_ms"], methods["taylor_cv"]["time_to_1e-3_ms"]
+    verdict["learned_vs_taylor_1e-3"] = (tt / tl) if (tl and tt) else None
+    try:
+        os.remove(cache)
+    except OSError:
+        pass
+    return {"workload": f"BA n={BA_N} m={BA_M}, beta=0.5/lambda_max, v~U[0,1) (seed {SEED})",
+            "lambda_max": lam, "power_iters": iters, "target": "relative L2 error vs FP64 Taylor oracle",
+            "seeds_per_M": seeds, "criterion": "worst seed at or below the target",
+            "timed": "one mcx_cvbatch_run graph launch (pre-pass + walk + finish), CUDA events",
+            "methods": methods, "comparison": verdict, "training": training}
+
+
+def run_ba_cv(args):
+    """The time-to-accuracy study of the learned control variate as its own line
+    (the default line carries the same object as `time_to_accuracy`)."""
+    import torch
+
+    inputs = BAInputs()
+    try:
+        torch.cuda.set_device(0)
+        from paper_1904_12759_gb300 import build as B
+
+        B.build()
+        with ClockSampler(0) as clk:
+            tta = _time_to_accuracy(inputs.load(), seeds=5, verbose=True)
+    finally:
+        inputs.close()
+    lc = tta["methods"]["learned_cv"]
+    line = {"metric": "GPU time to 1e-2 relative L2 error, learned CV (batched form)",
+            "value": lc["time_to_1e-2_ms"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+            "dtype": "f32 paths, f64 accumulation", "data": "synthetic",
+            "config": {"workload": "ba_cv", "n": BA_N, "m": BA_M, "beta": "0.5/lambda_max", "v": "U[0,1)"},
+            "time_to_accuracy": tta, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
 
 
 def run_rqmc(args):
@@ -971,6 +1071,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    # the time-to-accuracy study's BA graphs are generated in a spawned process meanwhile
+    ba_inputs = BAInputs() if (world == 1 and not args.no_tta) else None
     if world > 1:
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -1108,6 +1210,13 @@ def main():
             dist.destroy_process_group()
         return
 
+    # join the BA generator first, so that the CPU baseline below has the host cores to itself
+    ba_data = None
+    if ba_inputs is not None:
+        try:
+            ba_data = ba_inputs.load()
+        except Exception as exc:
+            ba_data = exc
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         import scipy  # noqa: F401
@@ -1164,6 +1273,16 @@ def main():
     # torch's, not counted
     batches = -(-iters // 8)
     line["gpu_launches"] = args.steps * (5 + 2 + 8 * batches + 3)
+    # second half of the headline metric: GPU time to 1e-2 relative error, learned CV vs plain MC
+    if ba_inputs is not None:
+        try:
+            if isinstance(ba_data, Exception):
+                raise ba_data
+            line["time_to_accuracy"] = _time_to_accuracy(ba_data, seeds=5)
+        except Exception as exc:  # reported, never silently dropped
+            line["time_to_accuracy"] = {"error": f"{type(exc).__name__}: {exc}"[:300]}
+        finally:
+            ba_inputs.close()
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
