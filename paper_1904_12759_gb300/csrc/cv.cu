@@ -598,10 +598,26 @@ __global__ void k_cv_ab(int64_t n, const double *__restrict__ T, const double *_
 // ---------------------------------------------------------------------------
 // CV walker
 // ---------------------------------------------------------------------------
+// FP32 residual integrals read the coefficients scaled by 2^-k, k the binary
+// exponent of the largest |a_i|, |b_i| (exact), so that the residuals and
+// their squares stay inside the FP32 range whatever the scale of v; the means
+// and standard errors are scaled back by 2^k when finished.  FP64 integrals
+// read them as they are.
 struct CVArgs {
-    const double *h;    // [n] h(t, i) = xhat_i
-    const double2 *ab;  // [n] (a, b)
+    const double *h;        // [n] h(t, i) = xhat_i
+    const double2 *ab;      // [n] (a, b)
+    const uint32_t *cexp;   // biased exponent word of the coefficients (FP32 integrals), or NULL
 };
+
+__device__ __forceinline__ double coef_scale_down(const CVArgs &cv) {
+    return cv.cexp ? 1.0 / exp_scale(*cv.cexp) : 1.0;
+}
+
+__device__ __forceinline__ double coef_scale_up(const CVArgs &cv) { return cv.cexp ? exp_scale(*cv.cexp) : 1.0; }
+
+__global__ void k_coef_exponent(int64_t n2, const double *__restrict__ ab, uint32_t *word) {
+    exponent_max(n2, ab, word);
+}
 
 // Residual accumulators: FP64 plain sums, or FP32 per-path scaled sums.
 template <bool F64I, bool WEIGHTED>
@@ -626,6 +642,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_cv(const __grid_constant_
     const uint32_t len = (uint32_t)(min(a.paths, p_begin + a.chunk_len) - p_begin);
     const uint64_t base = a.path_offset + p_begin;
     const NodeRec start = load_node(a.node, i);
+    const double cs = F64I ? 1.0 : coef_scale_down(cv);
     Walker<false> w;
     w.rec = start; w.j = i; w.r = a.t32; w.acc = 0.0f; w.delta = start.delta; w.k = 0;
     // per-path residual: y = e^{Ls} ys (FP32) or y (FP64)
@@ -644,7 +661,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_cv(const __grid_constant_
             float D;  // the hold just simulated: S (jump) or r0 (end)
             fin = advance<MCX_EXACT, WEIGHTED, false>(w, a, (uint32_t)i, base + p, nullptr, -1, &D);
             const double2 c = __ldg(cv.ab + j);
-            const R J = hold_integral<R>((R)c.x, (R)c.y, (R)dl, (R)r0, (R)D);
+            const R J = hold_integral<R>((R)(c.x * cs), (R)(c.y * cs), (R)dl, (R)r0, (R)D);
             if (F64I) {
                 ys += (R)exp((double)L0) * J;
             } else {
@@ -730,6 +747,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_cv_lanes(const __grid_con
             if (a.sem) a.sem[e] = QNAN;
         } else {
             const NodeRec start = load_node(a.node, i);
+            const double cs = F64I ? 1.0 : coef_scale_down(cv);
             double s1 = 0.0, s2 = 0.0;                           // FP64 residual sums
             float m = -INFINITY, f1 = 0.f, c1 = 0.f, f2 = 0.f;  // FP32 shifted sums
             for (uint64_t p = 0; p < a.paths; ++p) {
@@ -744,7 +762,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_cv_lanes(const __grid_con
                     float D;
                     fin = advance<MCX_EXACT, WEIGHTED, false>(w, a, (uint32_t)i, a.path_offset + p, nullptr, -1, &D);
                     const double2 c = __ldg(cv.ab + j);
-                    const R J = hold_integral<R>((R)c.x, (R)c.y, (R)dl, (R)r0, (R)D);
+                    const R J = hold_integral<R>((R)(c.x * cs), (R)(c.y * cs), (R)dl, (R)r0, (R)D);
                     if (F64I) {
                         ys += (R)exp((double)L0) * J;
                     } else {
@@ -783,8 +801,9 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_cv_lanes(const __grid_con
                 const float mu = __fdiv_rn(S1, M);
                 float var = M > 1.0f ? __fdiv_rn(__fsub_rn(f2, __fmul_rn(S1, mu)), M - 1.0f) : 0.0f;
                 if (var < 0.0f) var = 0.0f;
-                a.mean[e] = cv.h[i] + (double)__fmul_rn(sc, mu);
-                if (a.sem) a.sem[e] = (double)__fmul_rn(sc, sqrtf(__fdiv_rn(var, M)));
+                const double up = coef_scale_up(cv);  // undo the coefficients' power-of-two scaling
+                a.mean[e] = cv.h[i] + (double)__fmul_rn(sc, mu) * up;
+                if (a.sem) a.sem[e] = (double)__fmul_rn(sc, sqrtf(__fdiv_rn(var, M))) * up;
             } else {
                 double S1, S2, scale;
                 if (F64I) {
@@ -794,7 +813,7 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_cv_lanes(const __grid_con
                 } else {
                     S1 = (double)f1 - (double)c1;
                     S2 = (double)f2;
-                    scale = exp((double)m);
+                    scale = exp((double)m) * coef_scale_up(cv);
                 }
                 const double M = (double)a.paths;
                 const double mu = S1 / M;
@@ -820,8 +839,8 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_cv_lanes(const __grid_con
 
 // mean = h_i + (e^m sum y)/M over the entry's chunks; sem from the residual variance
 __global__ void k_cv_finish(const Partial *__restrict__ part, int64_t n_entries, uint32_t cpe, double M,
-                            const int32_t *__restrict__ entries, const double *__restrict__ h, double *mean,
-                            double *sem, uint32_t *status) {
+                            const int32_t *__restrict__ entries, const double *__restrict__ h,
+                            const uint32_t *__restrict__ cexp, double *mean, double *sem, uint32_t *status) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n_entries) return;
     const Partial *pp = part + (uint64_t)e * cpe;
@@ -842,7 +861,7 @@ __global__ void k_cv_finish(const Partial *__restrict__ part, int64_t n_entries,
         if (sem) sem[e] = QNAN;
         return;
     }
-    const double scale = mx == -INFINITY ? 0.0 : exp(mx);
+    const double scale = (mx == -INFINITY ? 0.0 : exp(mx)) * (cexp ? exp_scale(*cexp) : 1.0);
     const double mu = s1 / M;
     double var = M > 1.0 ? (s2 - s1 * mu) / (M - 1.0) : 0.0;
     if (var < 0.0) var = 0.0;
@@ -1169,10 +1188,18 @@ mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_
     set_round_keys(p, seed);
     if (reinterpret_cast<uintptr_t>(coef) % 16 != 0) return MCX_E_INVALID;  // (a, b) pairs are read as double2
     const bool wgt = plan->weighted_rows > 0;
+    const uint32_t *cexp = nullptr;  // FP32 integrals: the coefficients' exponent, for their scaling
+    if (precision == MCX_FP32) {
+        uint32_t *word = plan->status + STATUS_CEXP;
+        cudaError_t e0 = cudaMemsetAsync(word, 0, sizeof(uint32_t), st);
+        if (e0 != cudaSuccess) return stat(e0);
+        k_coef_exponent<<<blocks_for(2 * plan->n, 256), 256, 0, st>>>(2 * plan->n, coef, word);
+        cexp = word;
+    }
     if (paths <= LANE_MODE_MAX_PATHS) {  // few paths per entry: one lane per entry
         p.mean = mean;
         p.sem = sem;
-        CVArgs cvl{coef + 2 * plan->n, reinterpret_cast<const double2 *>(coef)};
+        CVArgs cvl{coef + 2 * plan->n, reinterpret_cast<const double2 *>(coef), cexp};
         const unsigned grid = (unsigned)((n_entries + WALK_THREADS - 1) / WALK_THREADS);
         if (precision == MCX_FP64) {
             if (wgt) k_walk_cv_lanes<true, true><<<grid, WALK_THREADS, 0, st>>>(p, cvl);
@@ -1205,7 +1232,7 @@ mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_
         plan->scratch_bytes = need;
     }
     p.partials = static_cast<Partial *>(plan->scratch);
-    CVArgs cv{coef + 2 * plan->n, reinterpret_cast<const double2 *>(coef)};
+    CVArgs cv{coef + 2 * plan->n, reinterpret_cast<const double2 *>(coef), cexp};
     const unsigned grid = (unsigned)((n_chunks + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
     if (precision == MCX_FP64) {
         if (wgt) k_walk_cv<true, true><<<grid, WALK_THREADS, 0, st>>>(p, cv);
@@ -1216,7 +1243,7 @@ mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_
     }
     k_cv_finish<<<(unsigned)((n_entries + 255) / 256), 256, 0, st>>>(p.partials, n_entries, (uint32_t)cpe,
                                                                        (double)paths, entries, coef + 2 * plan->n,
-                                                                       mean, sem, plan->status);
+                                                                       cexp, mean, sem, plan->status);
     return stat(cudaGetLastError());
 }
 

@@ -80,22 +80,14 @@ struct CvbArgs {
     const double *coef;    // per pair at pairs[k].coef (control variates)
     const double *v;       // [slots] float64 v of each pair (FP64 plain paths)
     const float *vf;       // [slots] v * 2^-vexp (FP32 plain paths)
-    const uint32_t *vexp;  // [pairs] biased exponent (see v_scale)
+    const uint32_t *vexp;  // [pairs] biased exponent: of v (plain FP32) or of the CV coefficients (FP32 integrals)
     Partial *part;
     double *mean, *sem;    // [slots]
 };
 
-// Exponent of the largest finite |v_i| of one pair, biased (the word is cleared first).
-__global__ void k_cvb_vexp(int64_t n, const double *__restrict__ v, uint32_t *vexp) {
-    uint32_t e = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double x = fabs(v[i]);
-        if (x > 0.0 && x <= 1.7976931348623157e308) e = max(e, (uint32_t)(ilogb(x) + (int)VEXP_BIAS));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-    if ((threadIdx.x & 31) == 0 && e) atomicMax(vexp, e);
-}
+// Exponent of the largest finite |x_i| of one pair (its v, or its control-variate
+// coefficients), biased (the word is cleared first).
+__global__ void k_cvb_vexp(int64_t n, const double *__restrict__ x, uint32_t *word) { exponent_max(n, x, word); }
 
 __global__ void k_cvb_pack(int64_t n, const double *__restrict__ v, const uint32_t *vexp, float *__restrict__ vf) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -156,14 +148,14 @@ struct CvLane {
 template <bool F64I, bool WEIGHTED>
 __device__ __forceinline__ bool cv_event(Walker<false> &w, const WalkParams &a, uint32_t stream, uint64_t path,
                                          const StageWarp *sw, int32_t i0, const double2 *__restrict__ ab,
-                                         int64_t off, typename CvLane<F64I>::R &ys, float &Ls) {
+                                         int64_t off, double cs, typename CvLane<F64I>::R &ys, float &Ls) {
     using R = typename CvLane<F64I>::R;
     const int32_t j = w.j;
     const float r0 = w.r, L0 = w.acc, dl = w.delta;
     float D;
     const bool fin = advance<MCX_EXACT, WEIGHTED, false>(w, a, stream, path, sw, i0, &D);
     const double2 c = __ldg(ab + (j - off));
-    const R J = hold_integral<R>((R)c.x, (R)c.y, (R)dl, (R)r0, (R)D);
+    const R J = hold_integral<R>((R)(c.x * cs), (R)(c.y * cs), (R)dl, (R)r0, (R)D);
     if (F64I) {
         ys += (R)exp((double)L0) * J;
     } else {
@@ -199,6 +191,9 @@ __global__ void __launch_bounds__(WALK_THREADS, CV ? CVB_MIN_BLOCKS_CV : CVB_MIN
         const CvbItem it = b.items[item];
         const CvbPair pr = b.pairs[it.pair];
         const double2 *ab = CV ? reinterpret_cast<const double2 *>(b.coef + pr.coef) : nullptr;
+        // FP32 residual integrals: coefficients scaled by 2^-k (k from the pre-pass), results by 2^k
+        const double up = (CV && !F64) ? exp_scale(b.vexp[it.pair]) : 1.0;
+        const double cs = 1.0 / up;
         const T t0 = P64 ? (T)pr.t : (T)pr.t32;
         if (pr.cpe == 0) {
             // ---- lane layout: lane = entry, all paths in path order ----
@@ -216,7 +211,8 @@ __global__ void __launch_bounds__(WALK_THREADS, CV ? CVB_MIN_BLOCKS_CV : CVB_MIN
                         w.rec = start; w.j = i0; w.r = pr.t32; w.acc = 0.0f; w.delta = start.delta; w.k = 0;
                         R ys = (R)0;
                         float Ls = 0.0f;
-                        while (!cv_event<F64, WEIGHTED>(w, a, (uint32_t)e, path, nullptr, i0, ab, pr.off, ys, Ls)) {
+                        while (!cv_event<F64, WEIGHTED>(w, a, (uint32_t)e, path, nullptr, i0, ab, pr.off, cs, ys,
+                                                        Ls)) {
                         }
                         cl.end_path(ys, Ls);
                         jumps_done += w.k;
@@ -236,7 +232,7 @@ __global__ void __launch_bounds__(WALK_THREADS, CV ? CVB_MIN_BLOCKS_CV : CVB_MIN
                 double S1, S2, Mw;
                 if constexpr (CV) {
                     cl.result(S1, S2, Mw);
-                    const double scale = (Mw == -INFINITY) ? 0.0 : exp(Mw);
+                    const double scale = ((Mw == -INFINITY) ? 0.0 : exp(Mw)) * up;
                     const double mu = S1 / M;
                     double var = M > 1.0 ? (S2 - S1 * mu) / (M - 1.0) : 0.0;
                     if (var < 0.0) var = 0.0;
@@ -282,7 +278,7 @@ __global__ void __launch_bounds__(WALK_THREADS, CV ? CVB_MIN_BLOCKS_CV : CVB_MIN
             CvLane<F64> cl;
             while (__any_sync(0xffffffffu, active)) {
                 bool fin = false;
-                if (active && cv_event<F64, WEIGHTED>(w, a, (uint32_t)e, base + p, swp, i0, ab, pr.off, ys, Ls)) {
+                if (active && cv_event<F64, WEIGHTED>(w, a, (uint32_t)e, base + p, swp, i0, ab, pr.off, cs, ys, Ls)) {
                     fin = true;
                     cl.end_path(ys, Ls);
                     jumps += w.k;
@@ -366,7 +362,8 @@ __global__ void k_cvb_finish(const CvbPair *__restrict__ pairs, const int32_t *_
     }
     const double M = (double)pr.paths;
     if (cv) {
-        const double scale = mx == -INFINITY ? 0.0 : exp(mx);
+        // FP32 residual integrals carry the coefficients' power-of-two scale (word 0 otherwise)
+        const double scale = (mx == -INFINITY ? 0.0 : exp(mx)) * exp_scale(b.vexp[k]);
         const double mu = s1 / M;
         double var = M > 1.0 ? (s2 - s1 * mu) / (M - 1.0) : 0.0;
         if (var < 0.0) var = 0.0;
@@ -618,6 +615,12 @@ cudaError_t prepass(mcx_cvbatch *b, cudaStream_t st) {
                 rc = mcx_cv_coefficients(n, rp, col, val, T, b->control == MCX_CV_LEARNED ? b->y + pr.slot : nullptr,
                                          pr.t, b->work, b->coef + pr.coef, st);
             if (rc != MCX_OK) return rc == MCX_E_OOM ? cudaErrorMemoryAllocation : cudaErrorUnknown;
+            cudaError_t e = cudaMemsetAsync(b->vexp + k, 0, sizeof(uint32_t), st);
+            if (e != cudaSuccess) return e;
+            if (b->precision == MCX_FP32) {  // the coefficients' exponent (their FP32 scaling)
+                const unsigned nb = (unsigned)std::min<int64_t>((2 * n + 255) / 256, 152 * 8);
+                k_cvb_vexp<<<nb, 256, 0, st>>>(2 * n, b->coef + pr.coef, b->vexp + k);
+            }
         } else if (b->precision == MCX_FP32) {
             cudaError_t e = cudaMemsetAsync(b->vexp + k, 0, sizeof(uint32_t), st);
             if (e != cudaSuccess) return e;

@@ -76,6 +76,7 @@ constexpr uint32_t ST_BAD_V = 32u;
 constexpr int STATUS_SYNC_WORDS = 8;
 constexpr int STATUS_WORDS = 16;
 constexpr int STATUS_VEXP = 8;
+constexpr int STATUS_CEXP = 9;  // exponent of the control-variate coefficients (see cv.cu)
 constexpr uint32_t VEXP_BIAS = 2048u;
 
 // The FP32 node records hold v scaled by a power of two, v * 2^-k with k the
@@ -87,6 +88,22 @@ constexpr uint32_t VEXP_BIAS = 2048u;
 __device__ __forceinline__ double v_scale(const uint32_t *status) {
     const uint32_t e = status[STATUS_VEXP];
     return e ? ldexp(1.0, (int)e - (int)VEXP_BIAS) : 1.0;
+}
+
+// 2^k for a biased exponent word (0: k = 0).
+__device__ __forceinline__ double exp_scale(uint32_t e) { return e ? ldexp(1.0, (int)e - (int)VEXP_BIAS) : 1.0; }
+
+// Largest biased exponent (ilogb + VEXP_BIAS) of the finite nonzero |x_i|,
+// i < n, merged into *word by atomicMax (the word is cleared before the launch).
+__device__ __forceinline__ void exponent_max(int64_t n, const double *__restrict__ x, uint32_t *word) {
+    uint32_t e = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double y = fabs(x[i]);
+        if (y > 0.0 && y <= 1.7976931348623157e308) e = max(e, (uint32_t)(ilogb(y) + (int)VEXP_BIAS));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    if ((threadIdx.x & 31) == 0 && e) atomicMax(word, e);
 }
 
 }  // namespace mcx

@@ -278,14 +278,7 @@ __global__ void k_trace_t0(int32_t i, uint32_t count, int32_t *end, uint32_t *nj
 // Exponent of the largest finite |v_i| into status word STATUS_VEXP (biased;
 // the word is cleared before the launch).
 __global__ void k_v_exponent(int64_t n, const double *__restrict__ v, uint32_t *status) {
-    uint32_t e = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double x = fabs(v[i]);
-        if (x > 0.0 && x <= 1.7976931348623157e308) e = max(e, (uint32_t)(ilogb(x) + (int)VEXP_BIAS));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-    if ((threadIdx.x & 31) == 0 && e) atomicMax(status + STATUS_VEXP, e);
+    exponent_max(n, v, status + STATUS_VEXP);
 }
 
 // v into the node records: FP64 as given, FP32 scaled by 2^-k (exact; see v_scale).

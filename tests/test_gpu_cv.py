@@ -170,6 +170,37 @@ def test_cv_estimates_match_oracle_same_paths(mcx, prec, M):
     plan.close()
 
 
+@pytest.mark.parametrize("M", [3000, 40])  # warp-per-entry and lane-per-entry layouts
+@pytest.mark.parametrize("vscale", [1e-30, 1e30])
+def test_cv_fp32_integrals_at_any_scale_of_v(mcx, M, vscale):
+    """FP32 residual integrals read the coefficients scaled by a power of two (exact), so
+    v scaled by 1e-30 or 1e30 gives estimates and standard errors that match the oracle
+    as v itself does: no squared residual underflows to a zero standard error, none
+    overflows.  The scale of the comparison adds the estimate of the absolute
+    integrand (|a|, |b|) on the same paths, what the FP32 sums add up."""
+    a = _conditioned(80, 21)
+    csr = W.dense_to_csr(a)
+    v = W.uniform_vector(80, 2, -1.0, 1.0) * vscale
+    t = 0.8
+    rp, col, val = _dev(csr)
+    T, F = mcx.cv_prepare(rp, col, val, torch.as_tensor(v).cuda(), t)
+    yrand = torch.as_tensor(np.random.default_rng(3).normal(0, 0.5, 80).astype(np.float32)).cuda()
+    coef = mcx.cv_coefficients(rp, col, val, T, yrand, t)
+    plan = mcx.Plan.from_csr(csr)
+    gm, gs = plan.estimate_cv(coef, t, M, seed=7, prec="fp32")
+    cg = coef.cpu().numpy()
+    ab = cg[:160].reshape(80, 2)
+    og = OW.Graph(csr)
+    om, os_ = og.estimate_cv(ab[:, 0].copy(), ab[:, 1].copy(), cg[160:].copy(), t, M, seed=7)
+    habs, _ = og.estimate_cv(np.abs(ab[:, 0]), np.abs(ab[:, 1]), np.zeros(80), t, M, seed=7)
+    gm, gs = gm.cpu().numpy(), gs.cpu().numpy()
+    scale = np.abs(cg[160:]) + os_ * math.sqrt(M) + habs
+    assert np.all(np.abs(gm - om) <= 1e-5 * scale), np.max(np.abs(gm - om) / scale)
+    assert np.allclose(gs, os_, rtol=1e-3, atol=1e-6 * scale.max()) and np.all(gs[os_ > 0] > 0)
+    assert plan.sync()["status_bits"] == 0
+    plan.close()
+
+
 def test_cv_exact_h_zero_variance(mcx):
     a = np.zeros((3, 3))
     a[0, 1] = 1.3
