@@ -610,9 +610,18 @@ def _time_to_accuracy(inputs, seeds=5, verbose=False):
         b.close()
         hit2 = next((x for x in rows if x["rel_l2_worst"] <= 1e-2), None)
         hit3 = next((x for x in rows if x["rel_l2_worst"] <= 1e-3), None)
+        # sustained: the smallest M from which every larger M of the sweep also meets 1e-2
+        # (the per-path weights are heavy-tailed at hubs, so a larger M can draw a rarer path)
+        sus = None
+        for x in reversed(rows):
+            if x["rel_l2_worst"] > 1e-2:
+                break
+            sus = x
         allw = [x["rel_l2_worst"] for x in rows]
         methods[method] = {
             "time_to_1e-2_ms": hit2["ms_median"] if hit2 else None, "M_1e-2": hit2["M"] if hit2 else None,
+            "time_to_1e-2_sustained_ms": sus["ms_median"] if sus else None,
+            "M_1e-2_sustained": sus["M"] if sus else None,
             "time_to_1e-3_ms": hit3["ms_median"] if hit3 else None, "M_1e-3": hit3["M"] if hit3 else None,
             "reached_1e-2": hit2 is not None, "max_M_tried": rows[-1]["M"],
             "worst_error_range": [min(allw), max(allw)],
@@ -633,8 +642,12 @@ def _time_to_accuracy(inputs, seeds=5, verbose=False):
         os.remove(cache)
     except OSError:
         pass
+    max_deg = int(np.diff(csr.row_ptr).max())
     return {"workload": f"BA n={BA_N} m={BA_M}, beta=0.5/lambda_max, v~U[0,1) (seed {SEED})",
-            "lambda_max": lam, "power_iters": iters, "target": "relative L2 error vs FP64 Taylor oracle",
+            "lambda_max": lam, "power_iters": iters, "t": t,
+            "hub": {"max_degree": max_deg, "max_degree_t": max_deg * t,
+                    "note": "at a node of degree d the potential equals the jump rate d, so a path holding "
+                            "there carries e^{d S}: its weight's second moment grows like e^{d t}"}, "target": "relative L2 error vs FP64 Taylor oracle",
             "seeds_per_M": seeds, "criterion": "worst seed at or below the target",
             "timed": "one mcx_cvbatch_run graph launch (pre-pass + walk + finish), CUDA events",
             "methods": methods, "comparison": verdict, "training": training}

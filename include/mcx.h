@@ -712,6 +712,14 @@ const char *mcx_status_string(int status);
 int64_t mcx_debug_fail_alloc(int64_t k);
 mcx_status mcx_debug_pool_usage(uint64_t *used, uint64_t *reserved);
 
+/* Test hook: the polls the network's tensor-core inference spends waiting for
+ * its MMAs of a tile before it gives up (default 2^22; 0xFFFFFFFF restores the
+ * default).  With 0 every wait gives up at once: the kernel latches the error
+ * (mcx_mlp_sync returns MCX_E_TIMEOUT), waits with the default limit for the
+ * MMAs it has in flight, frees its tensor memory and returns; nothing traps.
+ * Errors: MCX_E_INVALID. */
+mcx_status mcx_debug_mlp_wait_polls(mcx_mlp *model, uint32_t polls);
+
 /* Library version as 10000*major + 100*minor + patch. */
 int mcx_version(void);
 

@@ -59,6 +59,7 @@ EXPORTS = (
     "mcx_cvbatch_destroy",
     "mcx_debug_fail_alloc",
     "mcx_debug_pool_usage",
+    "mcx_debug_mlp_wait_polls",
 )
 
 MCX_OK = 0
@@ -219,6 +220,8 @@ def load(path: str = LIB_PATH):
     L.mcx_debug_fail_alloc.restype = i64
     L.mcx_debug_pool_usage.argtypes = [C.POINTER(u64), C.POINTER(u64)]
     L.mcx_debug_pool_usage.restype = st
+    L.mcx_debug_mlp_wait_polls.argtypes = [vp, u32]
+    L.mcx_debug_mlp_wait_polls.restype = st
     L.mcx_status_string.argtypes = [C.c_int]
     L.mcx_status_string.restype = C.c_char_p
     L.mcx_version.restype = C.c_int

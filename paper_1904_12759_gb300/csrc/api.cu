@@ -149,6 +149,7 @@ const char *mcx_status_string(int s) {
 
 mcx_status mcx_plan_create(int64_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col, const double *val,
                            uint32_t flags, void *stream, mcx_plan **out) {
+    NvtxRange nvtx("mcx_plan_create");
     if (!out) return MCX_E_INVALID;
     *out = nullptr;
     if (n < 0 || n >= (int64_t)0x7fffffff || nnz < 0 || !row_ptr || (nnz > 0 && (!col || !val)))
@@ -231,6 +232,7 @@ static mcx_status check_common(const mcx_plan *p, double t, int functional, int3
 mcx_status mcx_estimate(mcx_plan *p, const double *v, double t, int functional, int32_t nsteps,
                         uint64_t paths_per_entry, const int32_t *entries, int64_t n_entries, uint64_t seed,
                         uint64_t path_offset, int precision, double *mean, double *sem, void *stream) {
+    NvtxRange nvtx("mcx_estimate");
     mcx_status rc = check_common(p, t, functional, nsteps, precision);
     if (rc != MCX_OK) return rc;
     if (n_entries == 0) return MCX_OK;  // nothing requested (an empty entry list may be NULL)
@@ -259,6 +261,7 @@ mcx_status mcx_estimate_level_difference(mcx_plan *p, const double *v, double t,
                                          uint64_t paths_per_entry, const int32_t *entries, int64_t n_entries,
                                          uint64_t seed, uint64_t path_offset, int precision, double *mean,
                                          double *sem, void *stream) {
+    NvtxRange nvtx("mcx_estimate_level_difference");
     mcx_status rc = check_common(p, t, functional, nsteps, precision);
     if (rc != MCX_OK) return rc;
     if (functional != MCX_STRANG && functional != MCX_LIE) return MCX_E_INVALID;
@@ -294,6 +297,7 @@ mcx_status mcx_estimate_rqmc(mcx_plan *p, const double *v, double t, int functio
                              uint32_t log2_points, uint32_t replicates, uint32_t replicate_offset,
                              const int32_t *entries, int64_t n_entries, uint64_t seed, int precision, double *mean,
                              double *sem, void *stream) {
+    NvtxRange nvtx("mcx_estimate_rqmc");
     mcx_status rc = check_common(p, t, functional, nsteps, precision);
     if (rc != MCX_OK) return rc;
     if (n_entries == 0) return MCX_OK;
@@ -337,6 +341,7 @@ mcx_status mcx_estimate_rqmc(mcx_plan *p, const double *v, double t, int functio
 mcx_status mcx_estimate_noalloc(mcx_plan *p, const double *v, double t, int functional, int32_t nsteps,
                                 uint64_t paths_per_entry, const int32_t *entries, int64_t n_entries, uint64_t seed,
                                 uint64_t path_offset, int precision, double *mean, double *sem, void *stream) {
+    NvtxRange nvtx("mcx_estimate_noalloc");
     mcx_status rc = check_common(p, t, functional, nsteps, precision);
     if (rc != MCX_OK) return rc;
     if (n_entries == 0) return MCX_OK;
@@ -364,6 +369,7 @@ mcx_status mcx_estimate_noalloc(mcx_plan *p, const double *v, double t, int func
 mcx_status mcx_estimate_forward(mcx_plan *p, const double *v, double t, int functional, int32_t nsteps,
                                 uint64_t total_paths, uint64_t seed, uint64_t path_offset, int precision, double *x,
                                 double *sem, void *stream) {
+    NvtxRange nvtx("mcx_estimate_forward");
     mcx_status rc = check_common(p, t, functional, nsteps, precision);
     if (rc != MCX_OK) return rc;
     if (p->n == 0) return MCX_OK;
@@ -381,6 +387,7 @@ mcx_status mcx_estimate_forward(mcx_plan *p, const double *v, double t, int func
 mcx_status mcx_total_communicability(mcx_plan *p, double t, int functional, int32_t nsteps, uint64_t total_paths,
                                      uint64_t seed, uint64_t path_offset, int precision, double *tc, double *sem,
                                      void *stream) {
+    NvtxRange nvtx("mcx_total_communicability");
     mcx_status rc = check_common(p, t, functional, nsteps, precision);
     if (rc != MCX_OK) return rc;
     if (p->n == 0 || !tc || total_paths < 2 || total_paths > (1ull << 53)) return MCX_E_INVALID;
@@ -399,6 +406,7 @@ mcx_status mcx_total_communicability(mcx_plan *p, double t, int functional, int3
 mcx_status mcx_trace_forward(mcx_plan *p, const double *v, double t, int functional, int32_t nsteps, uint64_t seed,
                              uint64_t first_path, uint32_t count, int precision, int32_t *start, int32_t *end,
                              uint32_t *njumps, uint64_t *hash, double *logw, void *stream) {
+    NvtxRange nvtx("mcx_trace_forward");
     mcx_status rc = check_common(p, t, functional, nsteps, precision);
     if (rc != MCX_OK) return rc;
     if (!v || !start || !end || !njumps || !hash || !logw) return MCX_E_INVALID;
@@ -409,6 +417,7 @@ mcx_status mcx_trace_forward(mcx_plan *p, const double *v, double t, int functio
 mcx_status mcx_trace_paths(mcx_plan *p, double t, int functional, int32_t nsteps, int32_t entry, uint64_t seed,
                            uint64_t first_path, uint32_t count, int precision, int32_t *end, uint32_t *njumps,
                            uint64_t *hash, double *logw, void *stream) {
+    NvtxRange nvtx("mcx_trace_paths");
     mcx_status rc = check_common(p, t, functional, nsteps, precision);
     if (rc != MCX_OK) return rc;
     if (entry < 0 || entry >= p->n || !end || !njumps || !hash || !logw) return MCX_E_INVALID;
@@ -419,6 +428,7 @@ mcx_status mcx_trace_paths(mcx_plan *p, double t, int functional, int32_t nsteps
 mcx_status mcx_power_iteration(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
                                int32_t max_iters, double tol, double *work, double *lambda_out, int32_t *iters_out,
                                void *stream) {
+    NvtxRange nvtx("mcx_power_iteration");
     if (n <= 0 || !row_ptr || !col || !val || !work || max_iters < 1 || !(tol >= 0.0)) return MCX_E_INVALID;
     double lam = 0.0;
     int32_t it = 0;
@@ -435,6 +445,7 @@ mcx_status mcx_expm_multiply(int64_t n, int64_t nnz, const int64_t *row_ptr, con
                              uint64_t paths_per_entry, const int32_t *entries, int64_t n_entries, uint64_t seed,
                              uint64_t path_offset, int precision, uint32_t flags, double *mean, double *sem,
                              double *t_used, void *stream) {
+    NvtxRange nvtx("mcx_expm_multiply");
     if (flags & ~MCX_PLAN_HOST_INPUT) return MCX_E_INVALID;
     if (n < 1 || nnz < 0 || !row_ptr || (nnz > 0 && (!col || !val)) || !v || !mean) return MCX_E_INVALID;
     if (!(t <= 0.0) && !(t > 0.0)) return MCX_E_INVALID;  // NaN
@@ -520,6 +531,7 @@ mcx_status mcx_plan_export(const mcx_plan *p, int32_t *deg, int64_t *row_start, 
 }
 
 mcx_status mcx_sync(mcx_plan *p, void *stream, mcx_stats *stats) {
+    NvtxRange nvtx("mcx_sync");
     if (!p) return MCX_E_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     uint32_t hs[STATUS_SYNC_WORDS] = {0, 0, 0, 0, 0, 0, 0, 0};

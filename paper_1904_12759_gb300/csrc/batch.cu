@@ -466,6 +466,7 @@ extern "C" {
 
 mcx_status mcx_batch_create(int32_t count, const mcx_problem *pr, const char *tune_cache, void *stream,
                             mcx_batch **out) {
+    NvtxRange nvtx("mcx_batch_create");
     if (!out) return MCX_E_INVALID;
     *out = nullptr;
     if (count < 1 || !pr) return MCX_E_INVALID;
@@ -706,6 +707,7 @@ mcx_status mcx_batch_create(int32_t count, const mcx_problem *pr, const char *tu
 }
 
 mcx_status mcx_batch_run(mcx_batch *b, uint64_t seed, void *stream) {
+    NvtxRange nvtx("mcx_batch_run");
     if (!b) return MCX_E_INVALID;
     return st_from(run_graph(b, seed, static_cast<cudaStream_t>(stream)));
 }

@@ -333,7 +333,8 @@ __device__ __forceinline__ uint32_t bf16_bits(float x) {
 }
 
 __global__ void __launch_bounds__(TC_ROWS, 7) k_mlp_predict_tc(int64_t n, const float *__restrict__ F, MLPView m,
-                                                               float *__restrict__ y, uint32_t *err) {
+                                                               float *__restrict__ y, uint32_t *err,
+                                                               uint32_t wait_polls) {
     __shared__ __align__(1024) uint8_t sA[TC_ROWS * HID * 2];  // 16 KB
     __shared__ __align__(1024) uint8_t sB[HID * HID * 2];      // 8 KB
     __shared__ float sW1[NF * HID], sb1[HID], sb2[HID], sw3[HID];
@@ -396,8 +397,10 @@ __global__ void __launch_bounds__(TC_ROWS, 7) k_mlp_predict_tc(int64_t n, const 
                              tc::smem_desc(b_addr + kk * 256u, 128u, 1024u), idesc, kk > 0);
             tc::mma_commit(&bar);
         }
-        const bool got = tc::mbar_wait(&bar, phase, TC_WAIT);
-        if (__syncthreads_or(!got)) {  // the MMAs did not complete: flag, wait once more, stop
+        const bool got = tc::mbar_wait(&bar, phase, wait_polls);
+        if (__syncthreads_or(!got)) {
+            // the MMAs did not complete within the limit: flag, wait (bounded) for the MMAs
+            // in flight to land before the tensor memory is freed, stop
             if (tid == 0) atomicOr(err, 1u);
             tc::mbar_wait(&bar, phase, TC_WAIT);
             break;
@@ -892,11 +895,12 @@ struct mcx_mlp {
     int64_t idx_n = 0;
     int64_t step = 0;
     uint32_t *err = nullptr;  // latched device status of inference (bit 0: an MMA wait gave up)
+    uint32_t wait_polls = TC_WAIT;  // polls of the MMA completion wait (test hook: mcx_debug_mlp_wait_polls)
 };
 
 namespace {
 
-mcx_status stat(cudaError_t e) {
+mcx_status cv_status(cudaError_t e) {
     if (e == cudaSuccess) return MCX_OK;
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
@@ -925,6 +929,7 @@ extern "C" {
 
 mcx_status mcx_cv_prepare(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val, const double *v,
                           double t, double *work, double *taylor, float *features, void *stream) {
+    NvtxRange nvtx("mcx_cv_prepare");
     if (n < 1 || !row_ptr || !col || !val || !v || !work || !taylor || !features || !(t > 0.0)) return MCX_E_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const unsigned nb = blocks_for(n, 256);
@@ -933,7 +938,7 @@ mcx_status mcx_cv_prepare(int64_t n, const int64_t *row_ptr, const int32_t *col,
     unsigned int *qn = reinterpret_cast<unsigned int *>(work + 2 * n);
     cudaError_t e = cudaMemcpyAsync(taylor, v, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(qn, 0, 2 * sizeof(unsigned int), st);
-    if (e != cudaSuccess) return stat(e);
+    if (e != cudaSuccess) return cv_status(e);
     k_find_long_rows<<<nb, 256, 0, st>>>(n, row_ptr, queue, qn);
     for (int k = 1; k <= 3; ++k) {
         const double *x = taylor + (k - 1) * n;
@@ -948,13 +953,13 @@ mcx_status mcx_cv_prepare(int64_t n, const int64_t *row_ptr, const int32_t *col,
     k_features<<<nb, 256, 0, st>>>(n, row_ptr, col, val, lam, taylor, t, features);
     k_features_long<<<152 * 8, 256, 0, st>>>(n, queue, qn, row_ptr, col, val, lam, taylor, t, features);
     k_features_huge<<<152 * 2, ROW_BLOCK, 0, st>>>(n, queue, qn, row_ptr, col, val, lam, taylor, t, features);
-    return stat(cudaGetLastError());
+    return cv_status(cudaGetLastError());
 }
 
 mcx_status mcx_cv_targets(int64_t n, const double *x, const double *taylor, double t, float *y, void *stream) {
     if (n < 1 || !x || !taylor || !y || !(t > 0.0)) return MCX_E_INVALID;
     k_cv_targets<<<blocks_for(n, 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(n, x, taylor, t, y);
-    return stat(cudaGetLastError());
+    return cv_status(cudaGetLastError());
 }
 
 mcx_status mcx_mlp_create(uint64_t seed, mcx_mlp **out) {
@@ -1000,7 +1005,7 @@ mcx_status mcx_mlp_create(uint64_t seed, mcx_mlp **out) {
     } while (0);
     if (e != cudaSuccess) {
         mcx_mlp_destroy(m);
-        return stat(e);
+        return cv_status(e);
     }
     *out = m;
     return MCX_OK;
@@ -1012,7 +1017,7 @@ mcx_status mcx_mlp_set(mcx_mlp *m, const float *params, const float *mu, const f
     if (params) e = cudaMemcpy(m->params, params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && mu) e = cudaMemcpy(m->stats, mu, sizeof(float) * NF, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && sd) e = cudaMemcpy(m->stats + NF, sd, sizeof(float) * NF, cudaMemcpyHostToDevice);
-    return stat(e);
+    return cv_status(e);
 }
 
 mcx_status mcx_mlp_get(const mcx_mlp *m, float *params, float *mu, float *sd) {
@@ -1021,17 +1026,25 @@ mcx_status mcx_mlp_get(const mcx_mlp *m, float *params, float *mu, float *sd) {
     if (params) e = cudaMemcpy(params, m->params, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && mu) e = cudaMemcpy(mu, m->stats, sizeof(float) * NF, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && sd) e = cudaMemcpy(sd, m->stats + NF, sizeof(float) * NF, cudaMemcpyDeviceToHost);
-    return stat(e);
+    return cv_status(e);
 }
 
 mcx_status mcx_mlp_predict(const mcx_mlp *m, int64_t n, const float *features, float *y, void *stream) {
+    NvtxRange nvtx("mcx_mlp_predict");
     if (!m || n < 0 || (n > 0 && (!features || !y))) return MCX_E_INVALID;
     if (n == 0) return MCX_OK;
     const int64_t tiles = (n + TC_ROWS - 1) / TC_ROWS;
     // 7 resident CTAs per SM (registers and shared memory allow 7; 7 x 64 of the 512 TMEM columns)
     const unsigned grid = (unsigned)std::min<int64_t>(tiles, 152 * 7);
-    k_mlp_predict_tc<<<grid, TC_ROWS, 0, static_cast<cudaStream_t>(stream)>>>(n, features, view(m), y, m->err);
-    return stat(cudaGetLastError());
+    k_mlp_predict_tc<<<grid, TC_ROWS, 0, static_cast<cudaStream_t>(stream)>>>(n, features, view(m), y, m->err,
+                                                                              m->wait_polls);
+    return cv_status(cudaGetLastError());
+}
+
+mcx_status mcx_debug_mlp_wait_polls(mcx_mlp *m, uint32_t polls) {
+    if (!m) return MCX_E_INVALID;
+    m->wait_polls = polls == 0xFFFFFFFFu ? TC_WAIT : polls;
+    return MCX_OK;
 }
 
 mcx_status mcx_mlp_sync(mcx_mlp *m, void *stream) {
@@ -1041,17 +1054,18 @@ mcx_status mcx_mlp_sync(mcx_mlp *m, void *stream) {
     cudaError_t e = cudaMemcpyAsync(&h, m->err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e == cudaSuccess && h) e = cudaMemsetAsync(m->err, 0, sizeof(uint32_t), st);
-    if (e != cudaSuccess) return stat(e);
+    if (e != cudaSuccess) return cv_status(e);
     return h ? MCX_E_TIMEOUT : MCX_OK;
 }
 
 mcx_status mcx_mlp_gradient(mcx_mlp *m, int64_t n, const float *features, const float *targets, float *grad,
                             float *loss, void *stream) {
+    NvtxRange nvtx("mcx_mlp_gradient");
     if (!m || n < 1 || !features || !targets || !grad) return MCX_E_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t blocks = (n + GRAD_SAMPLES - 1) / GRAD_SAMPLES;
     cudaError_t e = ensure_part(m, blocks);
-    if (e != cudaSuccess) return stat(e);
+    if (e != cudaSuccess) return cv_status(e);
     cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem());
     k_mlp_grad<<<(unsigned)blocks, GRAD_SAMPLES, grad_smem(), st>>>(n, features, targets, nullptr, view(m),
                                                                      1.0f / (float)n, m->part);
@@ -1062,29 +1076,30 @@ mcx_status mcx_mlp_gradient(mcx_mlp *m, int64_t n, const float *features, const 
         e = cudaMemcpyAsync(loss, m->grad + NPARAM, sizeof(float), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
-    return stat(e == cudaSuccess ? cudaGetLastError() : e);
+    return cv_status(e == cudaSuccess ? cudaGetLastError() : e);
 }
 
 mcx_status mcx_mlp_fit(mcx_mlp *m, int64_t n, const float *features, const float *targets, int32_t epochs,
                        int32_t batch, float lr, uint64_t seed, float *epoch_loss, void *stream) {
+    NvtxRange nvtx("mcx_mlp_fit");
     if (!m || n < 1 || !features || !targets || epochs < 0 || batch < 1 || !(lr > 0.0f)) return MCX_E_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // feature standardisation from this training set
     k_feature_stats<<<NF, 256, 0, st>>>(n, features, m->stats, m->stats + NF);
     const int64_t bblocks = (batch + GRAD_SAMPLES - 1) / GRAD_SAMPLES;
     cudaError_t e = ensure_part(m, bblocks);
-    if (e != cudaSuccess) return stat(e);
+    if (e != cudaSuccess) return cv_status(e);
     if (m->idx_n < n) {
         dev_free(m->idx);
         m->idx = nullptr;
-        if ((e = dev_malloc(&m->idx, sizeof(int64_t) * (size_t)n)) != cudaSuccess) return stat(e);
+        if ((e = dev_malloc(&m->idx, sizeof(int64_t) * (size_t)n)) != cudaSuccess) return cv_status(e);
         m->idx_n = n;
     }
     const int64_t steps = (n + batch - 1) / batch;  // minibatches per epoch
     if (epoch_loss && m->losses_n < steps) {
         dev_free(m->losses);
         m->losses = nullptr;
-        if ((e = dev_malloc(&m->losses, sizeof(float) * (size_t)steps)) != cudaSuccess) return stat(e);
+        if ((e = dev_malloc(&m->losses, sizeof(float) * (size_t)steps)) != cudaSuccess) return cv_status(e);
         m->losses_n = steps;
     }
     cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem());
@@ -1122,13 +1137,13 @@ mcx_status mcx_mlp_fit(mcx_mlp *m, int64_t n, const float *features, const float
             if ((e = cudaMemcpyAsync(hl.data(), m->losses, sizeof(float) * (size_t)nb, cudaMemcpyDeviceToHost, st)) !=
                     cudaSuccess ||
                 (e = cudaStreamSynchronize(st)) != cudaSuccess)
-                return stat(e);
+                return cv_status(e);
             for (int64_t k = 0; k < nb; ++k) eloss += hl[k];
             epoch_loss[ep] = (float)(eloss / (double)std::max<int64_t>(nb, 1));
         }
-        if ((e = cudaGetLastError()) != cudaSuccess) return stat(e);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cv_status(e);
     }
-    return stat(cudaStreamSynchronize(st));
+    return cv_status(cudaStreamSynchronize(st));
 }
 
 void mcx_mlp_destroy(mcx_mlp *m) {
@@ -1148,6 +1163,7 @@ void mcx_mlp_destroy(mcx_mlp *m) {
 mcx_status mcx_cv_coefficients(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
                                const double *taylor, const float *y, double t, double *work, double *coef,
                                void *stream) {
+    NvtxRange nvtx("mcx_cv_coefficients");
     if (n < 1 || !row_ptr || !col || !val || !taylor || !work || !coef || !(t > 0.0)) return MCX_E_INVALID;
     if (reinterpret_cast<uintptr_t>(coef) % 16 != 0) return MCX_E_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1157,14 +1173,15 @@ mcx_status mcx_cv_coefficients(int64_t n, const int64_t *row_ptr, const int32_t 
     k_cv_xhat<<<nb, 256, 0, st>>>(n, taylor, y, t, coef + 2 * n, c3);
     cudaError_t e = spmv_hybrid(n, row_ptr, col, val, c3, Ac3, reinterpret_cast<int32_t *>(work + 2 * n),
                                 reinterpret_cast<unsigned int *>(work + 3 * n), st);
-    if (e != cudaSuccess) return stat(e);
+    if (e != cudaSuccess) return cv_status(e);
     k_cv_ab<<<nb, 256, 0, st>>>(n, taylor, c3, Ac3, reinterpret_cast<double2 *>(coef));
-    return stat(cudaGetLastError());
+    return cv_status(cudaGetLastError());
 }
 
 mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_t paths, const int32_t *entries,
                            int64_t n_entries, uint64_t seed, uint64_t path_offset, int precision, double *mean,
                            double *sem, void *stream) {
+    NvtxRange nvtx("mcx_estimate_cv");
     if (!plan || !coef || !(t > 0.0) || !isfinite(t) || paths < 1 || paths > (1ull << 53)) return MCX_E_INVALID;
     if (precision != MCX_FP32 && precision != MCX_FP64) return MCX_E_INVALID;
     if (n_entries == 0) return MCX_OK;
@@ -1192,7 +1209,7 @@ mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_
     if (precision == MCX_FP32) {
         uint32_t *word = plan->status + STATUS_CEXP;
         cudaError_t e0 = cudaMemsetAsync(word, 0, sizeof(uint32_t), st);
-        if (e0 != cudaSuccess) return stat(e0);
+        if (e0 != cudaSuccess) return cv_status(e0);
         k_coef_exponent<<<blocks_for(2 * plan->n, 256), 256, 0, st>>>(2 * plan->n, coef, word);
         cexp = word;
     }
@@ -1208,7 +1225,7 @@ mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_
             if (wgt) k_walk_cv_lanes<false, true><<<grid, WALK_THREADS, 0, st>>>(p, cvl);
             else k_walk_cv_lanes<false, false><<<grid, WALK_THREADS, 0, st>>>(p, cvl);
         }
-        return stat(cudaGetLastError());
+        return cv_status(cudaGetLastError());
     }
     const uint64_t target_warps = 152ull * 64ull * 8ull;
     uint64_t cpe = (target_warps + (uint64_t)n_entries - 1) / (uint64_t)n_entries;
@@ -1228,7 +1245,7 @@ mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_
         plan->scratch = nullptr;
         plan->scratch_bytes = 0;
         cudaError_t e = dev_malloc(&plan->scratch, need);
-        if (e != cudaSuccess) return stat(e);
+        if (e != cudaSuccess) return cv_status(e);
         plan->scratch_bytes = need;
     }
     p.partials = static_cast<Partial *>(plan->scratch);
@@ -1244,7 +1261,7 @@ mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_
     k_cv_finish<<<(unsigned)((n_entries + 255) / 256), 256, 0, st>>>(p.partials, n_entries, (uint32_t)cpe,
                                                                        (double)paths, entries, coef + 2 * plan->n,
                                                                        cexp, mean, sem, plan->status);
-    return stat(cudaGetLastError());
+    return cv_status(cudaGetLastError());
 }
 
 }  // extern "C"

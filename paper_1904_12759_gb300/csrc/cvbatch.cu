@@ -779,6 +779,7 @@ extern "C" {
 
 mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int control, const mcx_mlp *net,
                               int precision, const char *tune_cache, void *stream, mcx_cvbatch **out) {
+    NvtxRange nvtx("mcx_cvbatch_create");
     if (!out) return MCX_E_INVALID;
     *out = nullptr;
     if (count < 1 || !pr) return MCX_E_INVALID;
@@ -963,6 +964,7 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
 }
 
 mcx_status mcx_cvbatch_set_paths(mcx_cvbatch *b, const uint64_t *paths, void *stream) {
+    NvtxRange nvtx("mcx_cvbatch_set_paths");
     if (!b || !paths) return MCX_E_INVALID;
     for (int32_t i = 0; i < b->problems; ++i)
         if (paths[i] < 1 || paths[i] > (1ull << 40)) return MCX_E_INVALID;
@@ -976,6 +978,7 @@ mcx_status mcx_cvbatch_set_paths(mcx_cvbatch *b, const uint64_t *paths, void *st
 }
 
 mcx_status mcx_cvbatch_run(mcx_cvbatch *b, uint64_t seed, void *stream) {
+    NvtxRange nvtx("mcx_cvbatch_run");
     if (!b) return MCX_E_INVALID;
     return cvb_status(run_graph(b, seed, static_cast<cudaStream_t>(stream)));
 }

@@ -22,6 +22,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+import zstats
 from oracle import cv as CV
 from oracle import dense as OD
 from oracle import walker as OW
@@ -202,11 +203,7 @@ def test_cvbatch_unbiased_against_expm(mcx):
     for i, (a, v, t) in enumerate(((a1, v1, 0.7), (a2, v2, 0.4))):
         x, s = b.result(i)
         z.append((x.cpu().numpy() - OD.expmv_dense(a, t, v)) / s.cpu().numpy())
-    z = np.concatenate(z)
-    k = z.size
-    assert (np.abs(z) > 3).mean() <= 0.0027 + 5 * math.sqrt(0.0027 / k)
-    assert abs(z.mean()) <= 5 / math.sqrt(k)
-    assert 0.8 <= z.var() <= 1.25, z.var()
+    zstats.check(np.concatenate(z), samples=20000)
     b.close()
     net.close()
 

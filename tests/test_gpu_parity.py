@@ -18,6 +18,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+import zstats
 from oracle import dense as OD
 from oracle import walker as OW
 
@@ -173,8 +174,7 @@ def test_functionals_estimates_match_oracle(mcx):
             assert np.all(np.abs(gm - om) <= tol * np.abs(om)), (mode, prec)
     # and the Strang estimate is unbiased for the Strang product
     gm, gs, _, _ = _estimate_both(plan, og, v, 2.0, 20000, None, mode="strang", nsteps=2, prec="fp32")
-    z = (gm - OD.split_expmv(a, 2.0, 2, v, "strang")) / gs
-    assert abs(z.mean()) < 5 / math.sqrt(50) and 0.6 < z.var() < 1.5
+    zstats.check((gm - OD.split_expmv(a, 2.0, 2, v, "strang")) / gs, samples=20000)
     plan.close()
 
 
@@ -188,11 +188,7 @@ def test_grid2d_full_vector_vs_kronecker(mcx):
     plan = mcx.Plan.from_csr(csr)
     for prec in ("fp32", "fp64"):
         gm, gs = plan.estimate(_cuda(v, torch.float64), t, 2000, prec=prec)
-        z = (gm.cpu().numpy() - x) / gs.cpu().numpy()
-        k = z.size
-        assert (np.abs(z) > 3).mean() <= 0.0027 + 5 * math.sqrt(0.0027 / k)
-        assert abs(z.mean()) <= 5 / math.sqrt(k)
-        assert 0.8 <= z.var() <= 1.25
+        zstats.check((gm.cpu().numpy() - x) / gs.cpu().numpy(), samples=2000)
     # centre entry (16, 16) -> 528 with 10^6 paths, seed 0: |z| <= 3
     gm, gs = plan.estimate(_cuda(v, torch.float64), t, 10 ** 6, entries=_cuda([528], torch.int32), seed=0)
     z = (gm.item() - x[528]) / gs.item()

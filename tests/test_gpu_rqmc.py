@@ -17,6 +17,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+import zstats
 from oracle import dense as OD
 from oracle import walker as OW
 
@@ -151,8 +152,7 @@ def test_rqmc_reduces_variance_on_gpu(mcx):
     p, ps = plan.estimate(vd, t, 16 << 7, entries=_cuda(ent, torch.int32), seed=2)
     q, qs, p, ps = (a.cpu().numpy() for a in (q, qs, p, ps))
     assert np.mean(qs ** 2) < 0.5 * np.mean(ps ** 2), (np.mean(qs ** 2), np.mean(ps ** 2))
-    zq = (q - x) / qs
-    assert np.mean(np.abs(zq) > 3.5) < 0.02 and abs(zq.mean()) < 0.3
+    zstats.check((q - x) / qs, samples=16, dof=15)  # SE from 16 replicate means
     plan.close()
 
 

@@ -18,6 +18,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+import zstats
 from oracle import dense as OD
 from oracle import walker as OW
 
@@ -66,8 +67,7 @@ def test_level_mean_matches_split_products(mode):
     t, N = 0.9, 4
     exact = OD.split_expmv(a, t, N, v, mode) - OD.split_expmv(a, t, N // 2, v, mode)
     m, s = g.estimate_level_difference(v, t, N, 40000, seed=11, mode=mode, prec="fp64")
-    z = (m - exact) / s
-    assert np.mean(np.abs(z) > 3.5) <= 0.05 and abs(z.mean()) < 5 / math.sqrt(csr.n) + 0.2, z
+    zstats.check((m - exact) / s, samples=40000)
 
 
 def test_level_variance_decay():

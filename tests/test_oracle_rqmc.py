@@ -24,6 +24,7 @@ import pytest
 import scipy.linalg
 
 import workloads as W
+import zstats
 from oracle import dense as OD
 from oracle import walker as OW
 
@@ -123,16 +124,15 @@ def test_rqmc_unbiased_against_expm():
     v = W.uniform_vector(csr.n, 1)
     x = scipy.linalg.expm(t * a) @ v
     g = OW.Graph(csr)
+    # the standard error comes from 16 replicate means: z ~ Student t with 15 dof
     mean, sem, _ = g.estimate_rqmc(v, t, 6, 16, seed=3)
-    z = (mean - x) / sem
-    assert abs(z.mean()) < 5 / math.sqrt(csr.n) + 0.2
-    assert np.mean(np.abs(z) > 3.5) <= 0.05
+    zstats.check((mean - x) / sem, samples=16, dof=15)
     # FP64 paths and a split functional: unbiased for their own targets
     mean64, sem64, _ = g.estimate_rqmc(v, t, 6, 16, seed=4, prec="fp64")
-    assert np.mean(np.abs((mean64 - x) / sem64) > 3.5) <= 0.05
+    zstats.check((mean64 - x) / sem64, samples=16, dof=15)
     xs = OD.split_expmv(a, t, 2, v, "strang")
     ms, ss, _ = g.estimate_rqmc(v, t, 6, 16, seed=6, mode="strang", nsteps=2)
-    assert np.mean(np.abs((ms - xs) / ss) > 3.5) <= 0.05
+    zstats.check((ms - xs) / ss, samples=16, dof=15)
 
 
 def test_rqmc_standard_error_and_variance_reduction():
@@ -178,7 +178,7 @@ def test_one_point_replicates_are_plain_monte_carlo():
     x = scipy.linalg.expm(t * a) @ v
     mean, sem, reps = OW.Graph(csr).estimate_rqmc(v, t, 0, 256, seed=8)
     assert reps.shape == (csr.n, 256)
-    assert np.mean(np.abs((mean - x) / sem) > 3.5) <= 0.05
+    zstats.check((mean - x) / sem, samples=256, dof=255)
 
 
 def test_replicate_ranges_merge_like_one_run():
@@ -215,8 +215,7 @@ def test_rqmc_unbiased_on_weighted_rows():
     v = W.uniform_vector(n, 9)
     x = scipy.linalg.expm(t * a) @ v
     mean, sem, _ = g.estimate_rqmc(v, t, 6, 16, seed=12)
-    z = (mean - x) / sem
-    assert np.mean(np.abs(z) > 3.5) <= 0.06 and abs(z.mean()) < 0.5
+    zstats.check((mean - x) / sem, samples=16, dof=15)
     _, sem_mc, _ = g.estimate(v, t, 16 << 6, seed=12)
     assert np.mean(sem ** 2) < np.mean(sem_mc ** 2)
 
