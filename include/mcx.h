@@ -395,6 +395,22 @@ mcx_status mcx_power_iteration(int64_t n, const int64_t *row_ptr, const int32_t 
                                int32_t *iters_out, void *stream);
 
 /*
+ * Multilevel combination (Giles' telescoping sum over the step count of the
+ * STRANG/LIE functionals, the multilevel reading of the split error of Sec. 5):
+ * per entry, mean = the sum of the level means in level order (level 0 the
+ * plain estimate with N_0 steps, level l the level difference N_l vs N_l/2),
+ * sem = the square root of the sum of the squared level standard errors (the
+ * levels use disjoint path ranges, so they are independent).
+ *   levels       1 .. 64
+ *   means, sems  host arrays of `levels` device pointers, each float64
+ *                [n_entries]; sems may be NULL when sem is NULL
+ *   mean, sem    float64 [n_entries] device outputs (sem may be NULL)
+ * Asynchronous on `stream`.  Errors: MCX_E_INVALID, MCX_E_CUDA.
+ */
+mcx_status mcx_combine_levels(int32_t levels, int64_t n_entries, const double *const *means,
+                              const double *const *sems, double *mean, double *sem, void *stream);
+
+/*
  * Copy the plan's preparation results (Sec. 2 decomposition, Sec. 4 jump
  * tables) into caller-owned device arrays, for parity checks against an
  * independent preparation.  Per row [n]: deg (int32), row_start (int64),

@@ -19,6 +19,7 @@ EXPORTS = (
     "mcx_expm_multiply",
     "mcx_estimate_rqmc",
     "mcx_estimate_level_difference",
+    "mcx_combine_levels",
     "mcx_gather_rate",
     "mcx_estimate_noalloc",
     "mcx_estimate_forward",
@@ -143,6 +144,8 @@ def load(path: str = LIB_PATH):
     L.mcx_estimate_level_difference.argtypes = [vp, vp, dbl, C.c_int, i32, u64, vp, i64, u64, u64, C.c_int, vp,
                                                 vp, vp]
     L.mcx_estimate_level_difference.restype = st
+    L.mcx_combine_levels.argtypes = [i32, i64, vp, vp, vp, vp, vp]
+    L.mcx_combine_levels.restype = st
     L.mcx_gather_rate.argtypes = [u64, C.c_int, u64, C.POINTER(dbl), vp]
     L.mcx_gather_rate.restype = st
     L.mcx_estimate_noalloc.argtypes = [vp, vp, dbl, C.c_int, i32, u64, vp, i64, u64, u64, C.c_int, vp, vp, vp]

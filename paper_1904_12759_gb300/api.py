@@ -130,6 +130,21 @@ class Plan:
                                               C.c_void_p(p_sem), _stream(stream)), "mcx_estimate_level_difference")
         return mean, sem
 
+    def combine_levels(self, means, sems, stream=None):
+        """Multilevel telescoping sum (mcx_combine_levels): per entry the sum of the
+        level means and the root sum of squares of their standard errors."""
+        L = len(means)
+        n = means[0].numel()
+        if len(sems) != L or any(m.numel() != n or s.numel() != n for m, s in zip(means, sems)):
+            raise ValueError("one (mean, sem) pair of equal length per level")
+        pm = (C.c_void_p * L)(*[_dev(m, torch.float64, "mean") for m in means])
+        ps = (C.c_void_p * L)(*[_dev(s, torch.float64, "sem") for s in sems])
+        mean = torch.empty(n, dtype=torch.float64, device=means[0].device)
+        sem = torch.empty(n, dtype=torch.float64, device=means[0].device)
+        check(_lib.load().mcx_combine_levels(L, n, pm, ps, C.c_void_p(mean.data_ptr()), C.c_void_p(sem.data_ptr()),
+                                             _stream(stream)), "mcx_combine_levels")
+        return mean, sem
+
     def estimate_rqmc(self, v: torch.Tensor, t: float, log2_points: int, replicates: int,
                       entries: torch.Tensor | None = None, seed: int = 0, mode: str = "exact", nsteps: int = 1,
                       prec: str = "fp32", replicate_offset: int = 0, out: tuple | None = None, stream=None):

@@ -18,6 +18,8 @@
 // per-lane sums merged per warp, chunk partials merged per entry in chunk order.
 #include <math.h>
 
+#include <algorithm>
+
 #include <type_traits>
 
 #include "accum.cuh"
@@ -228,3 +230,50 @@ cudaError_t launch_level_difference(mcx_plan *plan, const EstimateArgs &a, cudaS
 }
 
 }  // namespace mcx
+
+namespace mcx {
+namespace {
+
+constexpr int MAX_LEVELS = 64;
+
+struct LevelPtrs {
+    const double *mean[MAX_LEVELS];
+    const double *sem[MAX_LEVELS];
+};
+
+// Giles' telescoping sum per entry: the level means added in level order, the
+// standard errors in quadrature (the levels use disjoint paths: independent).
+__global__ void k_combine_levels(int32_t levels, int64_t n, const __grid_constant__ LevelPtrs p, double *mean,
+                                 double *sem) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double m = 0.0, v = 0.0;
+        for (int32_t l = 0; l < levels; ++l) {
+            m += p.mean[l][i];
+            if (sem) {
+                const double s = p.sem[l][i];
+                v = fma(s, s, v);
+            }
+        }
+        mean[i] = m;
+        if (sem) sem[i] = sqrt(v);
+    }
+}
+
+}  // namespace
+}  // namespace mcx
+
+extern "C" mcx_status mcx_combine_levels(int32_t levels, int64_t n_entries, const double *const *means,
+                                         const double *const *sems, double *mean, double *sem, void *stream) {
+    using namespace mcx;
+    if (levels < 1 || levels > MAX_LEVELS || n_entries < 0 || !means || !mean || (sem && !sems)) return MCX_E_INVALID;
+    if (n_entries == 0) return MCX_OK;
+    LevelPtrs p{};
+    for (int32_t l = 0; l < levels; ++l) {
+        if (!means[l] || (sem && !sems[l])) return MCX_E_INVALID;
+        p.mean[l] = means[l];
+        p.sem[l] = sem ? sems[l] : nullptr;
+    }
+    const unsigned grid = (unsigned)std::min<int64_t>((n_entries + 255) / 256, 152 * 8);
+    k_combine_levels<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(levels, n_entries, p, mean, sem);
+    return cudaGetLastError() == cudaSuccess ? MCX_OK : MCX_E_CUDA;
+}

@@ -9,8 +9,9 @@ The target is the split estimate with the finest step count N_L = n0 2^L:
 level 0 the plain estimate with n0 steps, level l the coupled difference of the
 functionals with N_l and N_l / 2 steps on the same paths.  The levels draw from
 disjoint path ranges (path_offset = l 2^40), so they are independent and the
-standard errors add in quadrature.  All sampling runs in the library's kernels;
-this module only chooses sample sizes and adds the level results.
+standard errors add in quadrature.  Sampling and the combination run in the
+library's kernels (mcx_combine_levels adds the levels on the device); this
+module only chooses sample sizes and path ranges.
 """
 from __future__ import annotations
 
@@ -37,8 +38,6 @@ def estimate(plan, v, t: float, n0: int, levels: int, paths, entries=None, seed:
 
     `paths` gives the samples per level (levels + 1 numbers).  Returns
     (mean, sem, per_level) with per_level a list of (mean, sem) tensors."""
-    import torch
-
     if mode not in ("strang", "lie"):
         raise ValueError("multilevel estimates need the STRANG or LIE functional")
     if n0 < 1 or levels < 0 or len(paths) != levels + 1:
@@ -49,8 +48,7 @@ def estimate(plan, v, t: float, n0: int, levels: int, paths, entries=None, seed:
         per_level.append(plan.estimate_level_difference(v, t, n0 << lvl, int(paths[lvl]), entries=entries,
                                                         seed=seed, path_offset=lvl * LEVEL_STRIDE, mode=mode,
                                                         prec=prec))
-    mean = torch.stack([m for m, _ in per_level]).sum(dim=0)
-    sem = torch.stack([s * s for _, s in per_level]).sum(dim=0).sqrt()
+    mean, sem = plan.combine_levels([m for m, _ in per_level], [s for _, s in per_level])
     return mean, sem, per_level
 
 

@@ -135,3 +135,22 @@ def test_multilevel_driver_against_split_product(mcx):
     V = [float((s.cpu().numpy() ** 2).mean()) * M for (_, s), M in zip(levels, [200000, 40000, 20000, 10000, 5000])]
     assert V[1] < V[0] and V[4] < V[1]
     plan.close()
+
+
+def test_combine_levels_on_the_device(mcx):
+    """mcx_combine_levels: the level means added in level order (bit for bit the same
+    sequential FP64 sum) and the standard errors in quadrature."""
+    rng = np.random.default_rng(0)
+    L, n = 5, 777
+    ms = [rng.normal(size=n) for _ in range(L)]
+    ss = [rng.uniform(0, 1, n) for _ in range(L)]
+    plan = mcx.Plan.from_csr(W.erdos_renyi(10, 2, 1))
+    m, s = plan.combine_levels([_cuda(x, torch.float64) for x in ms], [_cuda(x, torch.float64) for x in ss])
+    want = ms[0].copy()
+    for x in ms[1:]:
+        want = want + x
+    assert np.array_equal(m.cpu().numpy(), want)
+    assert np.allclose(s.cpu().numpy(), np.sqrt(sum(x * x for x in ss)), rtol=1e-15, atol=0)
+    with pytest.raises(ValueError):
+        plan.combine_levels([_cuda(ms[0], torch.float64)], [])
+    plan.close()

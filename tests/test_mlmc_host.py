@@ -46,6 +46,13 @@ class _FakePlan:
         self.calls.append(("diff", nsteps, paths, path_offset, mode, seed))
         return torch.tensor([0.1 * nsteps, -0.01 * nsteps]), torch.tensor([0.01, 0.02])
 
+    def combine_levels(self, means, sems):
+        """Stands in for the library's device combination (checked on the GPU)."""
+        import torch
+
+        self.calls.append(("combine", len(means)))
+        return torch.stack(means).sum(dim=0), torch.stack([s * s for s in sems]).sum(dim=0).sqrt()
+
 
 def test_driver_levels_offsets_and_combination():
     torch = pytest.importorskip("torch")
@@ -53,7 +60,7 @@ def test_driver_levels_offsets_and_combination():
     mean, sem, levels = mlmc.estimate(plan, None, 0.5, 4, 3, [1000, 500, 250, 125], seed=7, mode="lie")
     assert plan.calls == [("plain", 4, 1000, 0, "lie", 7), ("diff", 8, 500, mlmc.LEVEL_STRIDE, "lie", 7),
                           ("diff", 16, 250, 2 * mlmc.LEVEL_STRIDE, "lie", 7),
-                          ("diff", 32, 125, 3 * mlmc.LEVEL_STRIDE, "lie", 7)]
+                          ("diff", 32, 125, 3 * mlmc.LEVEL_STRIDE, "lie", 7), ("combine", 4)]
     assert torch.allclose(mean, torch.tensor([10.0 + 0.1 * (8 + 16 + 32), 20.0 - 0.01 * (8 + 16 + 32)]))
     assert torch.allclose(sem, torch.tensor([math.sqrt(0.09 + 3e-4), math.sqrt(0.16 + 3 * 4e-4)]))
     assert len(levels) == 4
@@ -79,6 +86,8 @@ def test_adaptive_pilot_then_allocation():
     # pilot variances: mean SE^2 x 100 -> level 0: (0.09 + 0.16)/2 x 100, levels 1, 2: (1e-4 + 4e-4)/2 x 100
     V = [12.5, 0.025, 0.025]
     assert sizes == mlmc.allocation(V, [1.0, 1.0, 1.0], 0.01)
+    assert run[-1] == ("combine", 3)
+    run = run[:-1]
     assert [c[2] for c in run] == sizes and [c[3] for c in run] == [0, mlmc.LEVEL_STRIDE, 2 * mlmc.LEVEL_STRIDE]
     with pytest.raises(ValueError):
         mlmc.adaptive(plan, None, 0.5, 2, 2, eps=0.01, pilot_paths=1)
