@@ -244,6 +244,40 @@ def _fp64_check(P, plan_args, v, t, M, n, k=256, seed=SEED):
             "diverged_path_fraction": diverged / (k * M), "seed": seed}
 
 
+def _fp64_forward_check(P, csr, v, t, paths, seed, path_offset=0, trace=20000, mode="exact", nsteps=1):
+    """FP32 against FP64 paths of the forward form (Theorem 2) under the same seed
+    (outside the timed region): the relative difference of the full-vector estimates
+    (max, median, and in FP64 standard errors) and of their sums, and the fraction of
+    `trace` traced paths whose start, end, jump count or index hash differ."""
+    import numpy as np
+    import torch
+
+    plan = P.Plan.from_csr(csr)
+    try:
+        vd = torch.as_tensor(np.asarray(v, dtype=np.float64)).cuda()
+        x32, _ = plan.forward(vd, t, paths, seed=seed, path_offset=path_offset, mode=mode, nsteps=nsteps, prec="fp32")
+        x64, s64 = plan.forward(vd, t, paths, seed=seed, path_offset=path_offset, mode=mode, nsteps=nsteps,
+                                prec="fp64")
+        x32, x64, s64 = x32.cpu().numpy(), x64.cpu().numpy(), s64.cpu().numpy()
+        nz = x64 != 0
+        rel = np.abs(x32 - x64)[nz] / np.abs(x64[nz])
+        a = plan.trace_forward(vd, t, seed=seed, first_path=path_offset, count=trace, mode=mode, nsteps=nsteps,
+                               prec="fp32")
+        b = plan.trace_forward(vd, t, seed=seed, first_path=path_offset, count=trace, mode=mode, nsteps=nsteps,
+                               prec="fp64")
+        same = ((a["start"] == b["start"]) & (a["end"] == b["end"]) & (a["njumps"] == b["njumps"])
+                & (a["hash"] == b["hash"]))
+        diverged = int((~same).sum().item())
+        plan.sync()
+    finally:
+        plan.close()
+    return {"paths": paths, "max_rel_diff": float(rel.max()) if rel.size else 0.0,
+            "median_rel_diff": float(np.median(rel)) if rel.size else 0.0,
+            "max_diff_in_fp64_se": float(np.max(np.abs(x32 - x64)[s64 > 0] / s64[s64 > 0])) if (s64 > 0).any() else 0.0,
+            "sum_rel_diff": float(abs(x32.sum() - x64.sum()) / abs(x64.sum())),
+            "traced_paths": trace, "diverged_path_fraction": diverged / trace}
+
+
 def _beta_cpu(csr):
     from oracle import dense as OD
 
@@ -356,6 +390,20 @@ def run_ctmc_batch(args):
         used += 1
         if cpu_s > 10.0:
             break
+    # FP32 vs FP64 paths on the 4 smallest generators at t = 10 (the most jumps), on the pairs' own
+    # paths (pair k of the batch uses path indices k 2^40 + p)
+    fp64 = []
+    for i in order[:4]:
+        p = probs[i]
+        k = 3 * i + 2
+        fp64.append(dict(generator=i, n=p["csr"].n, t=p["times"][2],
+                         **_fp64_forward_check(P, p["csr"], p["v"], p["times"][2], p["paths"], SEED,
+                                               path_offset=k << 40)))
+    # the walk's working set at any moment is one generator's rows (largest-cost-first order runs a
+    # matrix's items together): its random-gather ceiling is that of the largest generator's records
+    big = max(probs, key=lambda p: p["csr"].nnz)
+    ws = 32 * big["csr"].n + 16 * big["csr"].nnz
+    l2 = P.gather_rate(ws, dependent=True, loads=1 << 31) * 32 / 1e9
     line = {"metric": "walker jumps/s", "value": jumps / step_s, "unit": "jumps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -365,9 +413,13 @@ def run_ctmc_batch(args):
                        "l2": "inputs (2 GB of edge records) larger than L2"},
             "walker": {"paths": paths, "jumps": jumps, "paths_per_s": paths / step_s,
                        "max_conservation_error": worst, "batch_create_s": create_s},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "roofline": {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+                         "peak_source": f"measured in this run: random dependent 32-B sector gathers over "
+                                        f"{ws / 2 ** 20:.1f} MB, the largest generator's node and edge records",
+                         "hbm_copy": {"peak": peak, "frac": achieved / peak},
                          "traffic": _traffic("ctmc_batch") if args.generators == 256 else None,
                          "kernel": "k_batch_walk", "bytes_per_jump": BYTES_PER_JUMP},
+            "fp64_check": fp64,
             "cpu_baseline": None if not used else {
                 "value": cpu_paths / cpu_s, "unit": "paths/s", "cores": 1, "kind": "oracle",
                 "sample": f"{used} smallest generators x 3 horizons, forward form, sequential"},
@@ -627,6 +679,22 @@ def _time_to_accuracy(inputs, seeds=5, verbose=False):
             "worst_error_range": [min(allw), max(allw)],
             "schedule": {k: info[k] for k in ("chunk", "blocks_per_sm", "staged")},
             "sweep": rows if verbose else [{k: x[k] for k in ("M", "ms_median", "rel_l2_worst")} for x in rows]}
+    # FP32 vs FP64 residual integrals of the learned control variate at its 1e-2 M, same paths
+    # (both on FP32 paths, so no path diverges): the full-vector difference
+    M2 = methods["learned_cv"]["M_1e-2"] or 1
+    ests = {}
+    for prec in ("fp32", "fp64"):
+        b = P.CVBatch([dict(desc[0], paths=M2)], control="learned", net=net, prec=prec, tune_cache=cache)
+        b.run(seed=SEED)
+        ests[prec] = [x.cpu().numpy() for x in b.result(0)]
+        b.close()
+    d = np.abs(ests["fp32"][0] - ests["fp64"][0])
+    nz = ests["fp64"][0] != 0
+    fp64 = {"method": "learned_cv", "M": M2, "max_rel_diff": float((d[nz] / np.abs(ests["fp64"][0][nz])).max()),
+            "median_rel_diff": float(np.median(d[nz] / np.abs(ests["fp64"][0][nz]))),
+            "rel_l2_diff": float(np.linalg.norm(d) / np.linalg.norm(ests["fp64"][0])),
+            "diverged_path_fraction": 0.0, "note": "both precisions walk the same FP32 paths; FP64 is the "
+                                                   "residual integrals' accumulation"}
     net.close()
     pl, lc = methods["plain"], methods["learned_cv"]
     if pl["reached_1e-2"] and lc["reached_1e-2"]:
@@ -650,7 +718,7 @@ def _time_to_accuracy(inputs, seeds=5, verbose=False):
                             "there carries e^{d S}: its weight's second moment grows like e^{d t}"}, "target": "relative L2 error vs FP64 Taylor oracle",
             "seeds_per_M": seeds, "criterion": "worst seed at or below the target",
             "timed": "one mcx_cvbatch_run graph launch (pre-pass + walk + finish), CUDA events",
-            "methods": methods, "comparison": verdict, "training": training}
+            "methods": methods, "comparison": verdict, "fp64_check": fp64, "training": training}
 
 
 def run_ba_cv(args):
@@ -737,6 +805,16 @@ def run_rqmc(args):
                 res[f"time_to_{eps:g}_ms"] = hit["ms"] if hit else None
                 res[f"M_to_{eps:g}"] = hit["M"] if hit else None
             results[mth] = res
+    # FP32 vs FP64 paths of the quasi-random estimator on 256 sampled entries, 16 replicates of
+    # 2^10 points, same scrambles and shifts
+    ent = torch.as_tensor(W.random_entries(csr.n, 256, 11)).cuda()
+    q32, _ = plan.estimate_rqmc(vd, beta, 10, R, entries=ent, seed=SEED, prec="fp32")
+    q64, s64 = plan.estimate_rqmc(vd, beta, 10, R, entries=ent, seed=SEED, prec="fp64")
+    q32, q64, s64 = q32.cpu().numpy(), q64.cpu().numpy(), s64.cpu().numpy()
+    rel = np.abs(q32 - q64) / np.abs(q64)
+    fp64 = {"entries": 256, "points_per_replicate": 1 << 10, "replicates": R, "max_rel_diff": float(rel.max()),
+            "median_rel_diff": float(np.median(rel)),
+            "max_diff_in_fp64_se": float(np.max(np.abs(q32 - q64) / s64))}
     Ms = [r["M"] for r in results["rqmc"]["sweep"]]
     vr = [(p["rel_l2"] / q["rel_l2"]) ** 2 for p, q in zip(results["plain"]["sweep"], results["rqmc"]["sweep"])]
     tq = results["rqmc"]["time_to_0.001_ms"]
@@ -748,7 +826,7 @@ def run_rqmc(args):
                        "quasi_random_events": 8, "target": "relative L2 error vs FP64 Taylor oracle"},
             "speedup_vs_plain": (tp / tq) if (tp and tq) else None,
             "error_variance_ratio_plain_over_rqmc": {str(M): round(r, 2) for M, r in zip(Ms, vr)},
-            "results": results, "clocks": clk.summary()}
+            "fp64_check": fp64, "results": results, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     plan.close()
 
@@ -821,6 +899,16 @@ def run_tc(args):
                           "jumps_per_path": st["jumps"] / max(st["paths"], 1)}
             plan.close()
             res[name] = r
+            # FP32 vs FP64 paths: TC from the forward paths of v = 1 at the paper's setting
+            plan = P.Plan.from_csr(csr)
+            t32, _ = plan.total_communicability(beta, M, mode="strang", nsteps=N, seed=SEED, prec="fp32")
+            t64, s64 = plan.total_communicability(beta, M, mode="strang", nsteps=N, seed=SEED, prec="fp64")
+            plan.close()
+            fc = _fp64_forward_check(P, csr, np.ones(n), beta, 10 ** 5, SEED, trace=20000, mode="strang", nsteps=N)
+            r["fp64_check"] = {"tc_rel_diff": abs(t32.item() - t64.item()) / abs(t64.item()),
+                               "tc_diff_in_fp64_se": abs(t32.item() - t64.item()) / s64.item(),
+                               "traced_paths": fc["traced_paths"],
+                               "diverged_path_fraction": fc["diverged_path_fraction"]}
     head = res["small_world"]["strang_N32_M1e6"]
     thr = res["small_world"]["exact_M1e9"]  # the throughput launch: the walk dominates
     achieved = BYTES_PER_JUMP * thr["jumps_per_path"] * thr["paths_per_s"] / 1e9
@@ -837,7 +925,7 @@ def run_tc(args):
             "config": {"workload": "tc_small_world_n1e6", "beta": 1.0, "paths": M, "functional": "strang",
                        "nsteps": N, "graph": "ring lattice k=1 + shortcuts p=0.2 (mean degree 2.4)",
                        "l2": "512 MiB buffer written between timed calls"},
-            "results": res, "clocks": clk.summary()}
+            "fp64_check": res["small_world"]["fp64_check"], "results": res, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 

@@ -468,8 +468,8 @@ typedef struct {
  * blocks per SM, lane refill on or off) is read from `tune_cache` (a file of
  * JSON lines keyed by GPU
  * name and problem-set sizes; NULL: no cache) or autotuned by timing sampled
- * runs, then appended to the cache.  The reset + walk + finish sequence is
- * captured into a CUDA graph.  Pair k of the batch uses path indices
+ * runs, then appended to the cache.  The reset + start tables + walk +
+ * finish sequence is captured into a CUDA graph.  Pair k of the batch uses path indices
  * k * 2^40 + p (pairs numbered problem by problem, time by time), so its
  * paths are those of mcx_estimate_forward on that problem alone with
  * path_offset = k * 2^40.  EXACT functional, FP32 paths.  Synchronises
@@ -483,6 +483,14 @@ mcx_status mcx_batch_create(int32_t count, const mcx_problem *problems, const ch
 /* One run of the whole batch (one graph launch) with the given seed; results
  * replace the previous run's.  Asynchronous on `stream`. */
 mcx_status mcx_batch_run(mcx_batch *batch, uint64_t seed, void *stream);
+
+/* Replace the start vector of problem `problem` (device float64 [n], >= 0 with a
+ * positive sum) for the next runs: every run's graph rebuilds the start tables
+ * (Lemma 2) from the batch's current values, so no re-creation is needed.  An
+ * invalid v is found on the device: that run's results are NaN and
+ * mcx_batch_sync returns MCX_E_NEG_V.  Asynchronous on `stream`.
+ * Errors: MCX_E_INVALID, MCX_E_CUDA. */
+mcx_status mcx_batch_set_v(mcx_batch *batch, int32_t problem, const double *v, void *stream);
 
 /* Copy the last run's estimate of problem `problem` at horizon `time_index`
  * into caller-owned device arrays x [n] and sem [n] (sem may be NULL).

@@ -35,6 +35,7 @@ EXPORTS = (
     "mcx_batch_create",
     "mcx_batch_run",
     "mcx_batch_result",
+    "mcx_batch_set_v",
     "mcx_batch_get_info",
     "mcx_batch_sync",
     "mcx_batch_destroy",
@@ -172,6 +173,8 @@ def load(path: str = LIB_PATH):
     L.mcx_batch_run.restype = st
     L.mcx_batch_result.argtypes = [vp, i32, i32, vp, vp, vp]
     L.mcx_batch_result.restype = st
+    L.mcx_batch_set_v.argtypes = [vp, i32, vp, vp]
+    L.mcx_batch_set_v.restype = st
     L.mcx_batch_get_info.argtypes = [vp, C.POINTER(BatchInfo)]
     L.mcx_batch_get_info.restype = st
     L.mcx_batch_sync.argtypes = [vp, vp, C.POINTER(Stats)]

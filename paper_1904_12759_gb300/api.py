@@ -415,6 +415,14 @@ class Batch:
     def run(self, seed: int, stream=None) -> None:
         check(_lib.load().mcx_batch_run(self._h, int(seed), _stream(stream)), "mcx_batch_run")
 
+    def set_v(self, problem: int, v, stream=None) -> None:
+        """New start vector of one problem for the next runs (tables rebuilt in the graph)."""
+        n = self.sizes[problem][0]
+        if v.numel() != n:
+            raise ValueError("v must have the problem's n entries")
+        check(_lib.load().mcx_batch_set_v(self._h, int(problem), C.c_void_p(_dev(v, torch.float64, "v")),
+                                          _stream(stream)), "mcx_batch_set_v")
+
     def result(self, problem: int, time_index: int, stream=None):
         n = self.sizes[problem][0]
         dev = torch.device("cuda", torch.cuda.current_device())

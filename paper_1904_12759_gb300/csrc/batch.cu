@@ -113,21 +113,23 @@ __global__ void k_btop(int32_t problems, const BatchPT *__restrict__ pbase, cons
     vose_build((int32_t)p.G, S + p.g0, s, [](int32_t k) { return k; }, top + p.g0, q + p.g0, stack + p.g0);
 }
 
-// One thread per group: member table over the group's states (true end of the block).
+// One warp per group: member table over the group's states (true end of the block).
 __global__ void k_binner(int64_t ngroups, const int32_t *__restrict__ gprob, const BatchPT *__restrict__ pbase,
                          const double *__restrict__ v, const double *__restrict__ S, AliasEnt *in, double *q,
                          int32_t *stack) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= ngroups) return;
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= ngroups) return;  // uniform across the warp
     const int32_t b = gprob[g];
     if (b < 0) return;
     const BatchPT p = pbase[b];
     const int64_t lo = g * BGROUP;
     const int32_t d = (int32_t)(min(p.off + p.n, lo + BGROUP) - lo);
     if (S[g] > 0.0) {
-        vose_build(d, v + lo, S[g], [lo](int32_t k) { return (int32_t)(lo + k); }, in + lo, q + lo, stack + lo);
+        vose_build_warp(d, v + lo, S[g], [lo](int32_t k) { return (int32_t)(lo + k); }, in + lo, q + lo, stack + lo,
+                        lane);
     } else {
-        for (int32_t k = 0; k < d; ++k) in[lo + k] = AliasEnt{(int32_t)(lo + k), 0xFFFFFFFFu};
+        for (int32_t k = lane; k < d; k += 32) in[lo + k] = AliasEnt{(int32_t)(lo + k), 0xFFFFFFFFu};
     }
 }
 
@@ -377,6 +379,22 @@ void launch_walk(const mcx_batch *b, bool weighted, unsigned grid, cudaStream_t 
     }
 }
 
+// The start tables of every problem from the batch's current v (Lemma 2: j ~ v/V):
+// group sums, per-problem top tables, member tables (one warp per group); an
+// invalid v anywhere latches `bad` (the walk then does nothing and the finish
+// writes NaN).  Enqueued at creation and inside every run's graph, so new
+// values (mcx_batch_set_v) take effect at the next run.
+cudaError_t enqueue_tables(mcx_batch *b, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(b->bad, 0, 16, st);
+    if (e != cudaSuccess) return e;
+    const unsigned gb = (unsigned)((b->ngroups + 127) / 128);
+    k_bgroup_sums<<<gb, 128, 0, st>>>(b->ngroups, b->gprob, b->pbase, b->v, b->S, b->bad);
+    k_btop<<<(b->problems + 63) / 64, 64, 0, st>>>(b->problems, b->pbase, b->S, b->top, b->q, b->stack, b->V, b->bad);
+    k_binner<<<(unsigned)((b->ngroups + 3) / 4), 128, 0, st>>>(b->ngroups, b->gprob, b->pbase, b->v, b->S, b->in, b->q,
+                                                              b->stack);
+    return cudaGetLastError();
+}
+
 cudaError_t capture(mcx_batch *b, cudaStream_t st) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
@@ -393,6 +411,7 @@ cudaError_t capture(mcx_batch *b, cudaStream_t st) {
     if (e == cudaSuccess) {
         cudaMemsetAsync(b->next_item, 0, sizeof(unsigned int), cs);
         cudaMemsetAsync(b->dep, 0, (b->count_mode ? 8 : 16) * (size_t)b->slots, cs);
+        enqueue_tables(b, cs);
         const unsigned grid = (unsigned)(b->sms * b->blocks_per_sm);
         if (b->refill) launch_walk<true>(b, weighted, grid, cs);
         else launch_walk<false>(b, weighted, grid, cs);
@@ -590,12 +609,7 @@ mcx_status mcx_batch_create(int32_t count, const mcx_problem *pr, const char *tu
         cudaMemcpyAsync(b->pbase, pbase.data(), sizeof(BatchPT) * count, cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(b->gprob, gprob.data(), sizeof(int32_t) * b->ngroups, cudaMemcpyHostToDevice, st);
         cudaMemcpyAsync(b->v, v.data(), sizeof(double) * N, cudaMemcpyHostToDevice, st);
-        cudaMemsetAsync(b->bad, 0, 16, st);
-        const unsigned gb = (unsigned)((b->ngroups + 127) / 128);
-        k_bgroup_sums<<<gb, 128, 0, st>>>(b->ngroups, b->gprob, b->pbase, b->v, b->S, b->bad);
-        k_btop<<<(count + 63) / 64, 64, 0, st>>>(count, b->pbase, b->S, b->top, b->q, b->stack, b->V, b->bad);
-        k_binner<<<gb, 128, 0, st>>>(b->ngroups, b->gprob, b->pbase, b->v, b->S, b->in, b->q, b->stack);
-        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        if ((e = enqueue_tables(b, st)) != cudaSuccess) break;
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) break;
         uint32_t hbad = 0;
         cudaMemcpy(&hbad, b->bad, 4, cudaMemcpyDeviceToHost);
@@ -710,6 +724,17 @@ mcx_status mcx_batch_run(mcx_batch *b, uint64_t seed, void *stream) {
     NvtxRange nvtx("mcx_batch_run");
     if (!b) return MCX_E_INVALID;
     return st_from(run_graph(b, seed, static_cast<cudaStream_t>(stream)));
+}
+
+mcx_status mcx_batch_set_v(mcx_batch *b, int32_t problem, const double *v, void *stream) {
+    NvtxRange nvtx("mcx_batch_set_v");
+    if (!b || problem < 0 || problem >= b->problems || !v) return MCX_E_INVALID;
+    for (const auto &t : b->pt_host) {
+        if (t.problem != problem) continue;
+        return st_from(cudaMemcpyAsync(b->v + t.off, v, sizeof(double) * (size_t)t.n, cudaMemcpyDeviceToDevice,
+                                       static_cast<cudaStream_t>(stream)));
+    }
+    return MCX_E_INVALID;
 }
 
 mcx_status mcx_batch_result(const mcx_batch *b, int32_t problem, int32_t time_index, double *x, double *sem,

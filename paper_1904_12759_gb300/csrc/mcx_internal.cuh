@@ -260,4 +260,48 @@ __device__ void vose_build(int32_t d, const double *__restrict__ w, double lam, 
     }
 }
 
+// The same canonical Vose table built by one warp (lane = this thread's lane,
+// all 32 lanes call it): the scaled weights, the initial entries and the two
+// worklists in index order are written lane-parallel (positions from ballots),
+// then lane 0 runs the pairing loop.  Bit-identical to vose_build.
+template <typename IdF>
+__device__ void vose_build_warp(int32_t d, const double *__restrict__ w, double lam, IdF id, AliasEnt *__restrict__ out,
+                                double *__restrict__ q, int32_t *__restrict__ stack, int lane) {
+    int32_t ns = 0, nl = 0;  // warp-uniform counts of the small and large lists so far
+    const unsigned lt = (1u << lane) - 1u;
+    for (int32_t k0 = 0; k0 < d; k0 += 32) {
+        const int32_t k = k0 + lane;
+        const bool valid = k < d;
+        bool small = false;
+        if (valid) {
+            const double s = __ddiv_rn(__dmul_rn(w[k], (double)d), lam);
+            q[k] = s;
+            out[k] = AliasEnt{id(k), 0xFFFFFFFFu};
+            small = s < 1.0;
+        }
+        const unsigned sm = __ballot_sync(0xffffffffu, valid && small);
+        const unsigned lg = __ballot_sync(0xffffffffu, valid && !small);
+        if (valid) {
+            if (small) stack[ns + __popc(sm & lt)] = k;
+            else stack[d - 1 - (nl + __popc(lg & lt))] = k;
+        }
+        ns += __popc(sm);
+        nl += __popc(lg);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        while (ns > 0 && nl > 0) {
+            const int32_t s = stack[--ns];
+            const int32_t l = stack[d - 1 - (--nl)];
+            const double qs = q[s];
+            out[s] = AliasEnt{id(l), (uint32_t)__double2ull_rz(__dmul_rn(qs, 4294967296.0))};
+            const double ql = __dsub_rn(__dadd_rn(q[l], qs), 1.0);
+            q[l] = ql;
+            if (ql < 1.0) stack[ns++] = l;
+            else stack[d - 1 - nl++] = l;
+        }
+    }
+    __syncwarp();
+}
+
 }  // namespace mcx

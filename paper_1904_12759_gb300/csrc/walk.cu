@@ -366,18 +366,20 @@ __global__ void k_top_table(int64_t G, const double *__restrict__ S, AliasEnt *t
     vose_build((int32_t)G, S, s, [](int32_t k) { return k; }, top, q, stack);
 }
 
-// Member tables, one thread per group (all-zero groups are never drawn).
+// Member tables, one warp per group (all-zero groups are never drawn).
 __global__ void k_inner_tables(int64_t n, const double *__restrict__ v, const double *__restrict__ S, AliasEnt *in,
                                double *q, int32_t *stack) {
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     const int64_t G = (n + START_GROUP - 1) / START_GROUP;
-    if (g >= G) return;
+    if (g >= G) return;  // uniform across the warp
     const int64_t lo = g * START_GROUP;
     const int32_t d = (int32_t)(min(n, lo + START_GROUP) - lo);
     if (S[g] > 0.0) {
-        vose_build(d, v + lo, S[g], [lo](int32_t k) { return (int32_t)(lo + k); }, in + lo, q + lo, stack + lo);
+        vose_build_warp(d, v + lo, S[g], [lo](int32_t k) { return (int32_t)(lo + k); }, in + lo, q + lo, stack + lo,
+                        lane);
     } else {
-        for (int32_t k = 0; k < d; ++k) in[lo + k] = AliasEnt{(int32_t)(lo + k), 0xFFFFFFFFu};
+        for (int32_t k = lane; k < d; k += 32) in[lo + k] = AliasEnt{(int32_t)(lo + k), 0xFFFFFFFFu};
     }
 }
 
@@ -854,7 +856,7 @@ cudaError_t build_start_tables(mcx_plan *plan, const double *v, const FwdScratch
     const unsigned gb = (unsigned)((G + 127) / 128);
     k_group_sums<<<gb, 128, 0, st>>>(n, v, fs.S, fs.bad);
     k_top_table<<<1, 1, 0, st>>>(G, fs.S, fs.top, fs.q, fs.stack, fs.V, fs.bad);
-    k_inner_tables<<<gb, 128, 0, st>>>(n, v, fs.S, fs.in, fs.q, fs.stack);
+    k_inner_tables<<<(unsigned)((G + 3) / 4), 128, 0, st>>>(n, v, fs.S, fs.in, fs.q, fs.stack);  // warp per group
     *f = start_view(plan, fs);
     return cudaGetLastError();
 }

@@ -105,3 +105,41 @@ def test_batch_rejects_bad_vectors(mcx):
     with pytest.raises(mcx.MCXError) as e:
         mcx.Batch(probs)
     assert e.value.code == -4
+
+
+def test_batch_new_start_vector_rebuilds_tables_in_the_graph(mcx, tmp_path):
+    """mcx_batch_set_v: the next run's graph rebuilds the start tables from the new v
+    (the pair reproduces the oracle's single-problem forward run with that v, count for
+    count); the other problems are unchanged; an invalid v is caught on the device (NaN
+    results, MCX_E_NEG_V at sync) and a valid one afterwards runs normally."""
+    from paper_1904_12759_gb300 import MCXError
+
+    probs = W.ctmc_batch(3, 11, n_min=300, n_max=1500, paths_per_state=8)
+    b = mcx.Batch(probs, tune_cache=str(tmp_path / "tune.jsonl"))
+    b.run(seed=4)
+    before = [b.result(i, ti)[0].clone() for i in range(3) for ti in range(3)]
+    v1 = W.dirichlet_probability(probs[1]["csr"].n, 99)
+    b.set_v(1, torch.as_tensor(v1).cuda())
+    b.run(seed=4)
+    og = OW.Graph(probs[1]["csr"])
+    for ti, t in enumerate(probs[1]["times"]):
+        x = b.result(1, ti)[0].cpu().numpy()
+        ox, _, _ = og.forward(v1, t, probs[1]["paths"], seed=4, path_offset=(3 + ti) << 40)
+        assert np.allclose(x, ox, rtol=1e-12, atol=1e-15), ti
+    for i in (0, 2):
+        for ti in range(3):
+            assert torch.equal(b.result(i, ti)[0], before[3 * i + ti])
+    assert b.sync()["status_bits"] == 0
+    bad = v1.copy()
+    bad[5] = -0.1
+    b.set_v(1, torch.as_tensor(bad).cuda())
+    b.run(seed=4)
+    with pytest.raises(MCXError) as ei:
+        b.sync()
+    assert ei.value.code == -4  # MCX_E_NEG_V
+    assert torch.isnan(b.result(0, 0)[0]).all()
+    b.set_v(1, torch.as_tensor(v1).cuda())
+    b.run(seed=4)
+    assert b.sync()["status_bits"] == 0
+    assert torch.equal(b.result(0, 0)[0], before[0])
+    b.close()
