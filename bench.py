@@ -913,13 +913,21 @@ def run_tc(args):
     thr = res["small_world"]["exact_M1e9"]  # the throughput launch: the walk dominates
     achieved = BYTES_PER_JUMP * thr["jumps_per_path"] * thr["paths_per_s"] / 1e9
     peak = float(_peaks().get("hbm_gbs", 6800.0))
+    # the small-world graph's node records and columns (42 MB) sit in L2: the walk is judged
+    # against the random-gather ceiling of a buffer that size, measured here
+    sw = graphs["small_world"]
+    ws = 32 * sw.n + 4 * sw.nnz
+    l2 = P.gather_rate(ws, dependent=True, loads=1 << 31) * 32 / 1e9
     line = {"metric": "total communicability paths/s (Algorithm 2, v = 1)", "value": head["paths_per_s"],
             "unit": "paths/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": head["ms_per_call"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": head["paths_per_s"] / PAPER_TC_PATHS_PER_S["small_world"],
             "vs_baseline_note": "paper: one Xeon E5620 core, Fortran, small-world n=1e6, M=1e6, dt=0.03125: 0.95 s",
             "dtype": "f32", "data": "synthetic",
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "roofline": {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+                         "peak_source": f"measured in this run: random dependent 32-B sector gathers over "
+                                        f"{ws / 2 ** 20:.1f} MB (the graph's node records and columns)",
+                         "hbm_copy": {"peak": peak, "frac": achieved / peak},
                          "traffic": _traffic("tc"), "kernel": "k_walk_tc (M = 1e9 call, EXACT)",
                          "bytes_per_jump": BYTES_PER_JUMP},
             "config": {"workload": "tc_small_world_n1e6", "beta": 1.0, "paths": M, "functional": "strang",
