@@ -62,13 +62,14 @@ def _args():
     ap.add_argument("--tune-cache", default=None, help="ctmc_batch: schedule cache file (JSON lines)")
     ap.add_argument("--workload", default="erdos_renyi",
                     choices=["erdos_renyi", "ctmc_batch", "heat3d", "ba_cv", "tc", "splitting", "ranking", "rqmc",
-                             "mlmc"],
+                             "mlmc", "cvbatch"],
                     help="erdos_renyi: the default line; ctmc_batch / heat3d / ba_cv / tc: the batched CTMC "
                          "transients, the 3D heat equation, the learned control variate's time to 1e-2 "
                          "error and the total communicability at the paper's settings; splitting / ranking: "
                          "the splitting-error and sample-size study and the ranking similarities; rqmc: "
                          "randomised quasi-Monte Carlo against plain Monte Carlo; mlmc: multilevel Monte Carlo "
-                         "over the time step (own JSON lines)")
+                         "over the time step; cvbatch: the batched control-variate form's throughput on 32 BA "
+                         "problems with two right-hand sides each (own JSON lines)")
     return ap.parse_args()
 
 
@@ -745,6 +746,64 @@ def run_ba_cv(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cvbatch(args):
+    """Throughput of the batched control-variate form: 32 Barabasi-Albert problems (m = 5,
+    n log-uniform in 1e4..5e4, seeds 1..32), two right-hand sides each (v ~ U[0,1),
+    t = 0.25/lambda_max and 0.5/lambda_max), the learned control (network weights from
+    mcx_mlp_create: the cost does not depend on them), 64 paths per entry.  One timed
+    step = one mcx_cvbatch_run graph launch (per pair Taylor terms, features, network,
+    coefficients; the persistent walk; the finish).  Metric: walker paths/s."""
+    import numpy as np
+    import torch
+
+    import paper_1904_12759_gb300 as P
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(SEED)
+    sizes = np.round(10 ** rng.uniform(4, np.log10(5e4), 32)).astype(int)
+    probs = []
+    for k, n in enumerate(sizes, start=1):
+        c = W.barabasi_albert(int(n), 5, k)
+        rp, col, val = (torch.as_tensor(a).cuda() for a in (c.row_ptr, c.col, c.val))
+        lam, _ = P.power_iteration(rp, col, val, max_iters=20000, tol=1e-9)
+        v = np.stack([W.uniform_vector(int(n), 100 + k), W.uniform_vector(int(n), 200 + k)])
+        probs.append(dict(row_ptr=c.row_ptr, col=c.col, val=c.val, v=v, t=[0.25 / lam, 0.5 / lam], paths=64))
+    net = P.MLP(seed=0)
+    t0 = time.perf_counter()
+    b = P.CVBatch(probs, control="learned", net=net, tune_cache=args.tune_cache)
+    create_s = time.perf_counter() - t0
+    info = b.info()
+    for w in range(args.warmup):
+        b.run(seed=1000 + w)
+    torch.cuda.synchronize()
+    b.sync()
+    ms = []
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            b.run(seed=SEED + k)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    st = b.sync()
+    paths = st["paths"] / args.steps
+    step_s = sum(ms) / 1e3 / args.steps
+    line = {"metric": "walker paths/s (batched learned control variate)", "value": paths / step_s,
+            "unit": "paths/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 paths, f32 integrals",
+            "data": "synthetic",
+            "config": {"workload": "cvbatch", "problems": len(probs), "pairs": info["pairs"],
+                       "states": int(sizes.sum()), "paths_per_entry": 64, "control": "learned",
+                       "schedule": {k: info[k] for k in ("chunk", "blocks_per_sm", "staged", "grid", "work_items")}},
+            "walker": {"paths": paths, "jumps_per_path": st["jumps"] / max(st["paths"], 1), "batch_create_s": create_s},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    b.close()
+    net.close()
+
+
 def run_rqmc(args):
     """Randomised quasi-Monte Carlo against plain Monte Carlo on the default graph
     (Erdos-Renyi n = 1e6, mean degree 10, beta = 1/lambda_max, v = 1, every entry):
@@ -1172,6 +1231,9 @@ def main():
         return
     if args.workload == "mlmc":
         run_mlmc(args)
+        return
+    if args.workload == "cvbatch":
+        run_cvbatch(args)
         return
     import numpy as np
     import torch
