@@ -608,15 +608,27 @@ __global__ void k_cv_ab(int64_t n, const double *__restrict__ T, const double *_
 // read them as they are.
 struct CVArgs {
     const double *h;        // [n] h(t, i) = xhat_i
-    const double2 *ab;      // [n] (a, b)
-    const uint32_t *cexp;   // biased exponent word of the coefficients (FP32 integrals), or NULL
+    const double2 *ab;      // [n] (a, b) (FP64 integrals)
+    const float2 *abf;      // [n] (a, b) 2^-k in FP32 (FP32 integrals, see k_coef_f32)
+    const uint32_t *cexp;   // biased exponent word k of the coefficients (FP32 integrals), or NULL
 };
 
-__device__ __forceinline__ double coef_scale_down(const CVArgs &cv) {
-    return cv.cexp ? 1.0 / exp_scale(*cv.cexp) : 1.0;
-}
-
 __device__ __forceinline__ double coef_scale_up(const CVArgs &cv) { return cv.cexp ? exp_scale(*cv.cexp) : 1.0; }
+
+// the coefficients of state j in the integrals' precision
+template <bool F64I>
+__device__ __forceinline__ void coef_load(const CVArgs &cv, int32_t j, typename std::conditional<F64I, double, float>::type &ca,
+                                          typename std::conditional<F64I, double, float>::type &cb) {
+    if constexpr (F64I) {
+        const double2 c = __ldg(cv.ab + j);
+        ca = c.x;
+        cb = c.y;
+    } else {
+        const float2 c = __ldg(cv.abf + j);
+        ca = c.x;
+        cb = c.y;
+    }
+}
 
 __global__ void k_coef_exponent(int64_t n2, const double *__restrict__ ab, uint32_t *word) {
     exponent_max(n2, ab, word);
@@ -645,7 +657,6 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_cv(const __grid_constant_
     const uint32_t len = (uint32_t)(min(a.paths, p_begin + a.chunk_len) - p_begin);
     const uint64_t base = a.path_offset + p_begin;
     const NodeRec start = load_node(a.node, i);
-    const double cs = F64I ? 1.0 : coef_scale_down(cv);
     Walker<false> w;
     w.rec = start; w.j = i; w.r = a.t32; w.acc = 0.0f; w.delta = start.delta; w.k = 0;
     // per-path residual: y = e^{Ls} ys (FP32) or y (FP64)
@@ -663,8 +674,9 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_cv(const __grid_constant_
             const float r0 = w.r, L0 = w.acc, dl = w.delta;
             float D;  // the hold just simulated: S (jump) or r0 (end)
             fin = advance<MCX_EXACT, WEIGHTED, false>(w, a, (uint32_t)i, base + p, nullptr, -1, &D);
-            const double2 c = __ldg(cv.ab + j);
-            const R J = hold_integral<R>((R)(c.x * cs), (R)(c.y * cs), (R)dl, (R)r0, (R)D);
+            R ca, cb;
+            coef_load<F64I>(cv, j, ca, cb);
+            const R J = hold_integral<R>(ca, cb, (R)dl, (R)r0, (R)D);
             if (F64I) {
                 ys += (R)exp((double)L0) * J;
             } else {
@@ -750,7 +762,6 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_cv_lanes(const __grid_con
             if (a.sem) a.sem[e] = QNAN;
         } else {
             const NodeRec start = load_node(a.node, i);
-            const double cs = F64I ? 1.0 : coef_scale_down(cv);
             double s1 = 0.0, s2 = 0.0;                           // FP64 residual sums
             float m = -INFINITY, f1 = 0.f, c1 = 0.f, f2 = 0.f;  // FP32 shifted sums
             for (uint64_t p = 0; p < a.paths; ++p) {
@@ -764,8 +775,9 @@ __global__ void __launch_bounds__(WALK_THREADS) k_walk_cv_lanes(const __grid_con
                     const float r0 = w.r, L0 = w.acc, dl = w.delta;
                     float D;
                     fin = advance<MCX_EXACT, WEIGHTED, false>(w, a, (uint32_t)i, a.path_offset + p, nullptr, -1, &D);
-                    const double2 c = __ldg(cv.ab + j);
-                    const R J = hold_integral<R>((R)(c.x * cs), (R)(c.y * cs), (R)dl, (R)r0, (R)D);
+                    R ca, cb;
+                    coef_load<F64I>(cv, j, ca, cb);
+                    const R J = hold_integral<R>(ca, cb, (R)dl, (R)r0, (R)D);
                     if (F64I) {
                         ys += (R)exp((double)L0) * J;
                     } else {
@@ -1206,17 +1218,26 @@ mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_
     if (reinterpret_cast<uintptr_t>(coef) % 16 != 0) return MCX_E_INVALID;  // (a, b) pairs are read as double2
     const bool wgt = plan->weighted_rows > 0;
     const uint32_t *cexp = nullptr;  // FP32 integrals: the coefficients' exponent, for their scaling
+    float2 *abf = nullptr;           // FP32 integrals: their scaled FP32 copy (pool, freed after the walk)
     if (precision == MCX_FP32) {
         uint32_t *word = plan->status + STATUS_CEXP;
         cudaError_t e0 = cudaMemsetAsync(word, 0, sizeof(uint32_t), st);
+        if (e0 == cudaSuccess) e0 = pool_alloc(reinterpret_cast<void **>(&abf), sizeof(float2) * (size_t)plan->n, st);
         if (e0 != cudaSuccess) return cv_status(e0);
         k_coef_exponent<<<blocks_for(2 * plan->n, 256), 256, 0, st>>>(2 * plan->n, coef, word);
+        k_coef_f32<<<blocks_for(plan->n, 256), 256, 0, st>>>(plan->n, reinterpret_cast<const double2 *>(coef), word,
+                                                             abf);
         cexp = word;
     }
+    struct PoolRelease {  // the FP32 copy goes back to the pool behind the walk on the stream
+        float2 *p;
+        cudaStream_t s;
+        ~PoolRelease() { pool_free(p, s); }
+    } release{abf, st};
     if (paths <= LANE_MODE_MAX_PATHS) {  // few paths per entry: one lane per entry
         p.mean = mean;
         p.sem = sem;
-        CVArgs cvl{coef + 2 * plan->n, reinterpret_cast<const double2 *>(coef), cexp};
+        CVArgs cvl{coef + 2 * plan->n, reinterpret_cast<const double2 *>(coef), abf, cexp};
         const unsigned grid = (unsigned)((n_entries + WALK_THREADS - 1) / WALK_THREADS);
         if (precision == MCX_FP64) {
             if (wgt) k_walk_cv_lanes<true, true><<<grid, WALK_THREADS, 0, st>>>(p, cvl);
@@ -1249,7 +1270,7 @@ mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_
         plan->scratch_bytes = need;
     }
     p.partials = static_cast<Partial *>(plan->scratch);
-    CVArgs cv{coef + 2 * plan->n, reinterpret_cast<const double2 *>(coef), cexp};
+    CVArgs cv{coef + 2 * plan->n, reinterpret_cast<const double2 *>(coef), abf, cexp};
     const unsigned grid = (unsigned)((n_chunks + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK);
     if (precision == MCX_FP64) {
         if (wgt) k_walk_cv<true, true><<<grid, WALK_THREADS, 0, st>>>(p, cv);

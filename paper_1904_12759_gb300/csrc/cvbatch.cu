@@ -78,6 +78,7 @@ struct CvbArgs {
     uint32_t n_items;
     unsigned int *next_item;
     const double *coef;    // per pair at pairs[k].coef (control variates)
+    const float2 *abf;     // [slots] (a, b) 2^-k in FP32 (control variates with FP32 integrals)
     const double *v;       // [slots] float64 v of each pair (FP64 plain paths)
     const float *vf;       // [slots] v * 2^-vexp (FP32 plain paths)
     const uint32_t *vexp;  // [pairs] biased exponent: of v (plain FP32) or of the CV coefficients (FP32 integrals)
@@ -145,17 +146,29 @@ struct CvLane {
 
 // One event of a control-variate path: advance, then add the hold's residual
 // integral e^{L0} int R to the path's running sum (ys with shift Ls in FP32).
+// FP64 integrals read the coefficient pairs from ab, FP32 ones the scaled FP32
+// copy abf (see k_coef_f32); both indexed by the state's offset in its problem.
 template <bool F64I, bool WEIGHTED>
 __device__ __forceinline__ bool cv_event(Walker<false> &w, const WalkParams &a, uint32_t stream, uint64_t path,
                                          const StageWarp *sw, int32_t i0, const double2 *__restrict__ ab,
-                                         int64_t off, double cs, typename CvLane<F64I>::R &ys, float &Ls) {
+                                         const float2 *__restrict__ abf, int64_t off,
+                                         typename CvLane<F64I>::R &ys, float &Ls) {
     using R = typename CvLane<F64I>::R;
     const int32_t j = w.j;
     const float r0 = w.r, L0 = w.acc, dl = w.delta;
     float D;
     const bool fin = advance<MCX_EXACT, WEIGHTED, false>(w, a, stream, path, sw, i0, &D);
-    const double2 c = __ldg(ab + (j - off));
-    const R J = hold_integral<R>((R)(c.x * cs), (R)(c.y * cs), (R)dl, (R)r0, (R)D);
+    R ca, cb;
+    if constexpr (F64I) {
+        const double2 c = __ldg(ab + (j - off));
+        ca = c.x;
+        cb = c.y;
+    } else {
+        const float2 c = __ldg(abf + (j - off));
+        ca = c.x;
+        cb = c.y;
+    }
+    const R J = hold_integral<R>(ca, cb, (R)dl, (R)r0, (R)D);
     if (F64I) {
         ys += (R)exp((double)L0) * J;
     } else {
@@ -191,9 +204,9 @@ __global__ void __launch_bounds__(WALK_THREADS, CV ? CVB_MIN_BLOCKS_CV : CVB_MIN
         const CvbItem it = b.items[item];
         const CvbPair pr = b.pairs[it.pair];
         const double2 *ab = CV ? reinterpret_cast<const double2 *>(b.coef + pr.coef) : nullptr;
+        const float2 *abf = (CV && !F64) ? b.abf + pr.slot : nullptr;
         // FP32 residual integrals: coefficients scaled by 2^-k (k from the pre-pass), results by 2^k
         const double up = (CV && !F64) ? exp_scale(b.vexp[it.pair]) : 1.0;
-        const double cs = 1.0 / up;
         const T t0 = P64 ? (T)pr.t : (T)pr.t32;
         if (pr.cpe == 0) {
             // ---- lane layout: lane = entry, all paths in path order ----
@@ -211,7 +224,7 @@ __global__ void __launch_bounds__(WALK_THREADS, CV ? CVB_MIN_BLOCKS_CV : CVB_MIN
                         w.rec = start; w.j = i0; w.r = pr.t32; w.acc = 0.0f; w.delta = start.delta; w.k = 0;
                         R ys = (R)0;
                         float Ls = 0.0f;
-                        while (!cv_event<F64, WEIGHTED>(w, a, (uint32_t)e, path, nullptr, i0, ab, pr.off, cs, ys,
+                        while (!cv_event<F64, WEIGHTED>(w, a, (uint32_t)e, path, nullptr, i0, ab, abf, pr.off, ys,
                                                         Ls)) {
                         }
                         cl.end_path(ys, Ls);
@@ -278,7 +291,7 @@ __global__ void __launch_bounds__(WALK_THREADS, CV ? CVB_MIN_BLOCKS_CV : CVB_MIN
             CvLane<F64> cl;
             while (__any_sync(0xffffffffu, active)) {
                 bool fin = false;
-                if (active && cv_event<F64, WEIGHTED>(w, a, (uint32_t)e, base + p, swp, i0, ab, pr.off, cs, ys, Ls)) {
+                if (active && cv_event<F64, WEIGHTED>(w, a, (uint32_t)e, base + p, swp, i0, ab, abf, pr.off, ys, Ls)) {
                     fin = true;
                     cl.end_path(ys, Ls);
                     jumps += w.k;
@@ -426,6 +439,7 @@ struct mcx_cvbatch {
     float *feat = nullptr;     // [5 slots]
     float *y = nullptr;        // [slots]
     double *coef = nullptr;    // per pair, 32-double aligned
+    float2 *abf = nullptr;     // [slots] scaled FP32 coefficient pairs (FP32 integrals)
     int64_t coef_len = 0;
     double *work = nullptr;    // [3 max_n + 64]
     double *mean = nullptr, *sem = nullptr;  // [slots]
@@ -466,7 +480,7 @@ void free_cvbatch(mcx_cvbatch *b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    void *bufs[] = {b->rp, b->col, b->val, b->v, b->vf, b->vexp, b->taylor, b->feat, b->y, b->coef, b->work,
+    void *bufs[] = {b->rp, b->col, b->val, b->v, b->vf, b->vexp, b->taylor, b->feat, b->y, b->coef, b->abf, b->work,
                     b->mean, b->sem, b->pairs, b->warp_pairs, b->part, b->items, b->next_item};
     for (void *p : bufs) dev_free(p);
     if (b->plan) mcx_plan_destroy(b->plan);
@@ -617,9 +631,11 @@ cudaError_t prepass(mcx_cvbatch *b, cudaStream_t st) {
             if (rc != MCX_OK) return rc == MCX_E_OOM ? cudaErrorMemoryAllocation : cudaErrorUnknown;
             cudaError_t e = cudaMemsetAsync(b->vexp + k, 0, sizeof(uint32_t), st);
             if (e != cudaSuccess) return e;
-            if (b->precision == MCX_FP32) {  // the coefficients' exponent (their FP32 scaling)
+            if (b->precision == MCX_FP32) {  // the coefficients' exponent and their scaled FP32 copy
                 const unsigned nb = (unsigned)std::min<int64_t>((2 * n + 255) / 256, 152 * 8);
                 k_cvb_vexp<<<nb, 256, 0, st>>>(2 * n, b->coef + pr.coef, b->vexp + k);
+                k_coef_f32<<<nb, 256, 0, st>>>(n, reinterpret_cast<const double2 *>(b->coef + pr.coef), b->vexp + k,
+                                               b->abf + pr.slot);
             }
         } else if (b->precision == MCX_FP32) {
             cudaError_t e = cudaMemsetAsync(b->vexp + k, 0, sizeof(uint32_t), st);
@@ -900,6 +916,9 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
             if ((e = dev_malloc(reinterpret_cast<void **>(&b->work), sizeof(double) * (size_t)(3 * max_n + 64))) !=
                 cudaSuccess)
                 break;
+            if (precision == MCX_FP32 &&
+                (e = dev_malloc(reinterpret_cast<void **>(&b->abf), sizeof(float2) * sl)) != cudaSuccess)
+                break;
         } else {
             if ((e = dev_malloc(reinterpret_cast<void **>(&b->vf), sizeof(float) * sl)) != cudaSuccess) break;
         }
@@ -925,6 +944,7 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
         ba.pairs = b->pairs;
         ba.next_item = b->next_item;
         ba.coef = b->coef;
+        ba.abf = b->abf;
         ba.v = b->v;
         ba.vf = b->vf;
         ba.vexp = b->vexp;

@@ -9,6 +9,8 @@
 
 #include <math.h>
 
+#include "mcx_internal.cuh"
+
 namespace mcx {
 namespace {
 
@@ -78,6 +80,21 @@ __device__ __forceinline__ R hold_integral(R a, R b, R delta, R r, R D) {
     R ph[4];
     phis<R>(delta * D, ph);
     return c0 * D * ph[0] + c1 * D * D * ph[1] + c2 * D * D * D * ph[2] + c3 * D * D * D * D * ph[3];
+}
+
+// FP32 residual integrals read the coefficient pairs (a_j, b_j) as an FP32 copy
+// scaled by 2^-k, k the binary exponent of the largest |a|, |b| (from the
+// biased word; the scaling is exact, the copy rounds once): one 8-byte load per
+// hold and no FP64 arithmetic in the walk, with the residuals and their squares
+// inside the FP32 range whatever the scale of v.  Results are scaled back by 2^k.
+__global__ void k_coef_f32(int64_t n, const double2 *__restrict__ ab, const uint32_t *__restrict__ word,
+                           float2 *__restrict__ out) {
+    const uint32_t e = *word;
+    const int k = e ? (int)e - (int)VEXP_BIAS : 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 c = ab[i];
+        out[i] = make_float2(__double2float_rn(ldexp(c.x, -k)), __double2float_rn(ldexp(c.y, -k)));
+    }
 }
 
 }  // namespace
