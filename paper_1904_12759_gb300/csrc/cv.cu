@@ -194,7 +194,8 @@ __device__ __forceinline__ void neighbour_stats_fp64(int64_t i, const int64_t *_
 __device__ __forceinline__ void write_features(int64_t n, int64_t i, RowSums r, const int64_t *__restrict__ rp,
                                                const int32_t *__restrict__ col, const double *__restrict__ val,
                                                const double *__restrict__ lam, const double *__restrict__ T,
-                                               double t, float *__restrict__ F) {
+                                               double t_all, const double *__restrict__ t_row, float *__restrict__ F) {
+    const double t = t_row ? t_row[i] : t_all;  // the horizon of this row's problem
     float mean = 0.0f, sd = 0.0f;
     if (r.bad) {
         neighbour_stats_fp64(i, rp, col, val, lam, mean, sd);
@@ -222,7 +223,8 @@ __device__ __forceinline__ void write_features(int64_t n, int64_t i, RowSums r, 
 
 __global__ void k_features(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                            const double *__restrict__ val, const double *__restrict__ lam,
-                           const double *__restrict__ T, double t, float *__restrict__ F) {
+                           const double *__restrict__ T, double t, const double *__restrict__ t_row,
+                           float *__restrict__ F) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         if (rp[i + 1] - rp[i] > LONG_ROW) continue;
         RowSums r{{0.0f, 0.0f}, {0.0f, 0.0f}, 0, false};
@@ -230,14 +232,15 @@ __global__ void k_features(int64_t n, const int64_t *__restrict__ rp, const int3
             const int32_t c = col[p];
             if (c != i && val[p] > 0.0) row_add(r, df_split(lam[c], r.bad));
         }
-        write_features(n, i, r, rp, col, val, lam, T, t, F);
+        write_features(n, i, r, rp, col, val, lam, T, t, t_row, F);
     }
 }
 
 __global__ void k_features_long(int64_t n, const int32_t *__restrict__ queue, const unsigned int *qn,
                                 const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                                 const double *__restrict__ val, const double *__restrict__ lam,
-                                const double *__restrict__ T, double t, float *__restrict__ F) {
+                                const double *__restrict__ T, double t, const double *__restrict__ t_row,
+                                float *__restrict__ F) {
     const int lane = threadIdx.x & 31;
     const unsigned int nq = *qn;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -249,7 +252,7 @@ __global__ void k_features_long(int64_t n, const int32_t *__restrict__ queue, co
             if (c != i && val[p] > 0.0) row_add(r, df_split(lam[c], r.bad));
         }
         r = warp_rowsums(r);
-        if (lane == 0) write_features(n, i, r, rp, col, val, lam, T, t, F);
+        if (lane == 0) write_features(n, i, r, rp, col, val, lam, T, t, t_row, F);
     }
 }
 
@@ -260,6 +263,7 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_features_huge(int64_t n, const in
                                                              const double *__restrict__ val,
                                                              const double *__restrict__ lam,
                                                              const double *__restrict__ T, double t,
+                                                             const double *__restrict__ t_row,
                                                              float *__restrict__ F) {
     __shared__ df shd[ROW_BLOCK / 32];
     __shared__ double sh[ROW_BLOCK / 32];
@@ -275,7 +279,7 @@ __global__ void __launch_bounds__(ROW_BLOCK) k_features_huge(int64_t n, const in
         r.s1 = block_sum_df(r.s1, shd);
         r.s2 = block_sum_df(r.s2, shd);
         r.d = (int)block_sum_row((double)r.d, sh);
-        if (threadIdx.x == 0) write_features(n, i, r, rp, col, val, lam, T, t, F);
+        if (threadIdx.x == 0) write_features(n, i, r, rp, col, val, lam, T, t, t_row, F);
     }
 }
 
@@ -573,9 +577,10 @@ __global__ void k_feature_stats(int64_t n, const float *__restrict__ F, float *m
 }
 
 // xhat = T2 e^y; c3 = (xhat - T2)/t^3 -> coef: h [n], then (a, b) pairs [n]; c3 staged in b's slot
-__global__ void k_cv_xhat(int64_t n, const double *__restrict__ T, const float *__restrict__ y, double t,
-                          double *__restrict__ h, double *__restrict__ c3) {
+__global__ void k_cv_xhat(int64_t n, const double *__restrict__ T, const float *__restrict__ y, double t_all,
+                          const double *__restrict__ t_row, double *__restrict__ h, double *__restrict__ c3) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double t = t_row ? t_row[i] : t_all;
         const double T2 = T[i] + t * T[n + i] + t * t * T[2 * n + i] / 2.0;
         const double xh = T2 * exp((double)(y ? y[i] : 0.0f));
         h[i] = xh;
@@ -890,6 +895,51 @@ unsigned blocks_for(int64_t n, int threads) {
 }
 
 }  // namespace
+
+// Taylor terms and features of rows 0..n-1 (see mcx_cv_prepare); t_row, when
+// given, holds each row's own horizon (rows of several problems at once).
+cudaError_t cv_prepare_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                            const double *v, double t, const double *t_row, double *work, double *taylor,
+                            float *features, cudaStream_t st) {
+    const unsigned nb = blocks_for(n, 256);
+    double *lam = work;
+    int32_t *queue = reinterpret_cast<int32_t *>(work + n);  // n int32
+    unsigned int *qn = reinterpret_cast<unsigned int *>(work + 2 * n);
+    cudaError_t e = cudaMemcpyAsync(taylor, v, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(qn, 0, 2 * sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    k_find_long_rows<<<nb, 256, 0, st>>>(n, row_ptr, queue, qn);
+    for (int k = 1; k <= 3; ++k) {
+        const double *x = taylor + (k - 1) * n;
+        double *y = taylor + k * n;
+        k_spmv_short<<<nb, 256, 0, st>>>(n, row_ptr, col, val, x, nullptr, y, nullptr);
+        k_spmv_long<<<152 * 8, 256, 0, st>>>(queue, qn, row_ptr, col, val, x, nullptr, y, nullptr);
+        k_spmv_huge<<<152 * 2, ROW_BLOCK, 0, st>>>(n, queue, qn, row_ptr, col, val, x, nullptr, y, nullptr);
+    }
+    k_rates<<<nb, 256, 0, st>>>(n, row_ptr, col, val, lam);
+    k_rates_long<<<152 * 8, 256, 0, st>>>(queue, qn, row_ptr, col, val, lam);
+    k_rates_huge<<<152 * 2, ROW_BLOCK, 0, st>>>(n, queue, qn, row_ptr, col, val, lam);
+    k_features<<<nb, 256, 0, st>>>(n, row_ptr, col, val, lam, taylor, t, t_row, features);
+    k_features_long<<<152 * 8, 256, 0, st>>>(n, queue, qn, row_ptr, col, val, lam, taylor, t, t_row, features);
+    k_features_huge<<<152 * 2, ROW_BLOCK, 0, st>>>(n, queue, qn, row_ptr, col, val, lam, taylor, t, t_row, features);
+    return cudaGetLastError();
+}
+
+// Control-variate coefficients of rows 0..n-1 (see mcx_cv_coefficients) into
+// ab [n] and h [n]; t_row as in cv_prepare_rows.  work: float64 [3n + 64].
+cudaError_t cv_coefficients_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                                 const double *taylor, const float *y, double t, const double *t_row, double *work,
+                                 double2 *ab, double *h, cudaStream_t st) {
+    const unsigned nb = blocks_for(n, 256);
+    double *c3 = work, *Ac3 = work + n;
+    k_cv_xhat<<<nb, 256, 0, st>>>(n, taylor, y, t, t_row, h, c3);
+    cudaError_t e = spmv_hybrid(n, row_ptr, col, val, c3, Ac3, reinterpret_cast<int32_t *>(work + 2 * n),
+                                reinterpret_cast<unsigned int *>(work + 3 * n), st);
+    if (e != cudaSuccess) return e;
+    k_cv_ab<<<nb, 256, 0, st>>>(n, taylor, c3, Ac3, ab);
+    return cudaGetLastError();
+}
+
 }  // namespace mcx
 
 using namespace mcx;
@@ -943,29 +993,8 @@ mcx_status mcx_cv_prepare(int64_t n, const int64_t *row_ptr, const int32_t *col,
                           double t, double *work, double *taylor, float *features, void *stream) {
     NvtxRange nvtx("mcx_cv_prepare");
     if (n < 1 || !row_ptr || !col || !val || !v || !work || !taylor || !features || !(t > 0.0)) return MCX_E_INVALID;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const unsigned nb = blocks_for(n, 256);
-    double *lam = work;
-    int32_t *queue = reinterpret_cast<int32_t *>(work + n);  // n int32
-    unsigned int *qn = reinterpret_cast<unsigned int *>(work + 2 * n);
-    cudaError_t e = cudaMemcpyAsync(taylor, v, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(qn, 0, 2 * sizeof(unsigned int), st);
-    if (e != cudaSuccess) return cv_status(e);
-    k_find_long_rows<<<nb, 256, 0, st>>>(n, row_ptr, queue, qn);
-    for (int k = 1; k <= 3; ++k) {
-        const double *x = taylor + (k - 1) * n;
-        double *y = taylor + k * n;
-        k_spmv_short<<<nb, 256, 0, st>>>(n, row_ptr, col, val, x, nullptr, y, nullptr);
-        k_spmv_long<<<152 * 8, 256, 0, st>>>(queue, qn, row_ptr, col, val, x, nullptr, y, nullptr);
-        k_spmv_huge<<<152 * 2, ROW_BLOCK, 0, st>>>(n, queue, qn, row_ptr, col, val, x, nullptr, y, nullptr);
-    }
-    k_rates<<<nb, 256, 0, st>>>(n, row_ptr, col, val, lam);
-    k_rates_long<<<152 * 8, 256, 0, st>>>(queue, qn, row_ptr, col, val, lam);
-    k_rates_huge<<<152 * 2, ROW_BLOCK, 0, st>>>(n, queue, qn, row_ptr, col, val, lam);
-    k_features<<<nb, 256, 0, st>>>(n, row_ptr, col, val, lam, taylor, t, features);
-    k_features_long<<<152 * 8, 256, 0, st>>>(n, queue, qn, row_ptr, col, val, lam, taylor, t, features);
-    k_features_huge<<<152 * 2, ROW_BLOCK, 0, st>>>(n, queue, qn, row_ptr, col, val, lam, taylor, t, features);
-    return cv_status(cudaGetLastError());
+    return cv_status(cv_prepare_rows(n, row_ptr, col, val, v, t, nullptr, work, taylor, features,
+                                     static_cast<cudaStream_t>(stream)));
 }
 
 mcx_status mcx_cv_targets(int64_t n, const double *x, const double *taylor, double t, float *y, void *stream) {
@@ -1178,16 +1207,10 @@ mcx_status mcx_cv_coefficients(int64_t n, const int64_t *row_ptr, const int32_t 
     NvtxRange nvtx("mcx_cv_coefficients");
     if (n < 1 || !row_ptr || !col || !val || !taylor || !work || !coef || !(t > 0.0)) return MCX_E_INVALID;
     if (reinterpret_cast<uintptr_t>(coef) % 16 != 0) return MCX_E_INVALID;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const unsigned nb = blocks_for(n, 256);
     // layout: (a, b) pairs at offset 0 (16-byte aligned with the buffer), then h
-    double *c3 = work, *Ac3 = work + n;
-    k_cv_xhat<<<nb, 256, 0, st>>>(n, taylor, y, t, coef + 2 * n, c3);
-    cudaError_t e = spmv_hybrid(n, row_ptr, col, val, c3, Ac3, reinterpret_cast<int32_t *>(work + 2 * n),
-                                reinterpret_cast<unsigned int *>(work + 3 * n), st);
-    if (e != cudaSuccess) return cv_status(e);
-    k_cv_ab<<<nb, 256, 0, st>>>(n, taylor, c3, Ac3, reinterpret_cast<double2 *>(coef));
-    return cv_status(cudaGetLastError());
+    return cv_status(cv_coefficients_rows(n, row_ptr, col, val, taylor, y, t, nullptr, work,
+                                          reinterpret_cast<double2 *>(coef), coef + 2 * n,
+                                          static_cast<cudaStream_t>(stream)));
 }
 
 mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_t paths, const int32_t *entries,

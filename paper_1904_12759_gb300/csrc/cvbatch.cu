@@ -46,14 +46,13 @@ namespace {
 
 constexpr int64_t CVB_BLOCK = 1024;        // plan blocks padded to multiples of this
 constexpr int CVB_MIN_BLOCKS = 4;          // resident blocks per SM the plain walk is compiled for
-constexpr int CVB_MIN_BLOCKS_CV = 2;       // and the control-variate walk (hold integrals need registers)
+constexpr int CVB_MIN_BLOCKS_CV = 3;       // and the control-variate walk (hold integrals need registers)
 constexpr uint64_t CVB_ITEMS_PER_PAIR = 1ull << 20;  // chunk items per pair before chunks grow
 
 struct CvbPair {
     int64_t off;         // first global state of the problem
     int64_t n;           // states (entries) of the problem
-    int64_t slot;        // first per-state slot of this pair (v, vf, mean, sem)
-    int64_t coef;        // first double of this pair's coefficients [(a, b) pairs | h] (32-double aligned)
+    int64_t slot;        // first per-state slot of this pair (every per-state array is slot-indexed)
     int64_t part0;       // first chunk partial (warp layout)
     uint64_t paths;      // paths per entry
     uint64_t path_base;  // pair index << 40
@@ -77,7 +76,8 @@ struct CvbArgs {
     const CvbItem *items;
     uint32_t n_items;
     unsigned int *next_item;
-    const double *coef;    // per pair at pairs[k].coef (control variates)
+    const double2 *ab;     // [slots] control-variate coefficients (a, b) of each pair's states
+    const double *h;       // [slots] h(t) = the prediction of each pair's entries
     const float2 *abf;     // [slots] (a, b) 2^-k in FP32 (control variates with FP32 integrals)
     const double *v;       // [slots] float64 v of each pair (FP64 plain paths)
     const float *vf;       // [slots] v * 2^-vexp (FP32 plain paths)
@@ -86,15 +86,53 @@ struct CvbArgs {
     double *mean, *sem;    // [slots]
 };
 
-// Exponent of the largest finite |x_i| of one pair (its v, or its control-variate
-// coefficients), biased (the word is cleared first).
-__global__ void k_cvb_vexp(int64_t n, const double *__restrict__ x, uint32_t *word) { exponent_max(n, x, word); }
+// Per-pair biased exponent of the largest finite |x| over the pair's slots, `per`
+// doubles per slot (1 for v, 2 for the coefficient pairs); the words are cleared
+// first.  A warp takes 32 consecutive slots, mostly of one pair: one atomic per
+// warp then, one per lane where a pair boundary falls inside.
+__global__ void k_pair_exponent(int64_t slots, int per, const double *__restrict__ x,
+                                const int32_t *__restrict__ slot_pair, uint32_t *vexp) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < slots; w0 += warps * 32) {
+        const int64_t s = w0 + lane;
+        uint32_t e = 0;
+        int32_t k = -1;
+        if (s < slots) {
+            k = slot_pair[s];
+            for (int q = 0; q < per; ++q) {
+                const double y = fabs(x[s * per + q]);
+                if (y > 0.0 && y <= 1.7976931348623157e308) e = max(e, (uint32_t)(ilogb(y) + (int)VEXP_BIAS));
+            }
+        }
+        const int32_t k0 = __shfl_sync(0xffffffffu, k, 0);
+        if (__all_sync(0xffffffffu, k == k0 || k < 0)) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+            if (lane == 0 && e) atomicMax(vexp + k0, e);
+        } else if (k >= 0 && e) {
+            atomicMax(vexp + k, e);
+        }
+    }
+}
 
-__global__ void k_cvb_pack(int64_t n, const double *__restrict__ v, const uint32_t *vexp, float *__restrict__ vf) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t eb = *vexp;
-    vf[i] = __double2float_rn(ldexp(v[i], eb ? -((int)eb - (int)VEXP_BIAS) : 0));
+// FP32 copies scaled by the pair's power of two: v (plain) and the coefficient pairs.
+__global__ void k_pair_pack(int64_t slots, const double *__restrict__ v, const int32_t *__restrict__ slot_pair,
+                            const uint32_t *__restrict__ vexp, float *__restrict__ vf) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < slots; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t eb = vexp[slot_pair[s]];
+        vf[s] = __double2float_rn(ldexp(v[s], eb ? -((int)eb - (int)VEXP_BIAS) : 0));
+    }
+}
+
+__global__ void k_pair_coef_f32(int64_t slots, const double2 *__restrict__ ab, const int32_t *__restrict__ slot_pair,
+                                const uint32_t *__restrict__ vexp, float2 *__restrict__ out) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < slots; s += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t eb = vexp[slot_pair[s]];
+        const int k = eb ? (int)eb - (int)VEXP_BIAS : 0;
+        const double2 c = ab[s];
+        out[s] = make_float2(__double2float_rn(ldexp(c.x, -k)), __double2float_rn(ldexp(c.y, -k)));
+    }
 }
 
 // The lane sums of a control-variate walker: FP64 plain sums of the per-path
@@ -203,7 +241,7 @@ __global__ void __launch_bounds__(WALK_THREADS, CV ? CVB_MIN_BLOCKS_CV : CVB_MIN
         if (item >= b.n_items) break;
         const CvbItem it = b.items[item];
         const CvbPair pr = b.pairs[it.pair];
-        const double2 *ab = CV ? reinterpret_cast<const double2 *>(b.coef + pr.coef) : nullptr;
+        const double2 *ab = CV ? b.ab + pr.slot : nullptr;
         const float2 *abf = (CV && !F64) ? b.abf + pr.slot : nullptr;
         // FP32 residual integrals: coefficients scaled by 2^-k (k from the pre-pass), results by 2^k
         const double up = (CV && !F64) ? exp_scale(b.vexp[it.pair]) : 1.0;
@@ -249,7 +287,7 @@ __global__ void __launch_bounds__(WALK_THREADS, CV ? CVB_MIN_BLOCKS_CV : CVB_MIN
                     const double mu = S1 / M;
                     double var = M > 1.0 ? (S2 - S1 * mu) / (M - 1.0) : 0.0;
                     if (var < 0.0) var = 0.0;
-                    const double mv = b.coef[pr.coef + 2 * pr.n + e] + scale * mu;
+                    const double mv = b.h[pr.slot + e] + scale * mu;
                     const double se = scale * sqrt(var / M);
                     b.mean[pr.slot + e] = mv;
                     b.sem[pr.slot + e] = se;
@@ -380,7 +418,7 @@ __global__ void k_cvb_finish(const CvbPair *__restrict__ pairs, const int32_t *_
         const double mu = s1 / M;
         double var = M > 1.0 ? (s2 - s1 * mu) / (M - 1.0) : 0.0;
         if (var < 0.0) var = 0.0;
-        const double mv = b.coef[pr.coef + 2 * pr.n + e] + scale * mu;
+        const double mv = b.h[pr.slot + e] + scale * mu;
         const double se = scale * sqrt(var / M);
         b.mean[pr.slot + e] = mv;
         b.sem[pr.slot + e] = se;
@@ -421,27 +459,29 @@ struct mcx_cvbatch {
     const mcx_mlp *net = nullptr;
     int64_t N = 0;        // padded states
     int64_t slots = 0;    // sum over pairs of n_b
-    int64_t max_n = 0;
     mcx_plan *plan = nullptr;
     std::vector<CvbPair> pair_host;
     std::vector<double> cost_per_path;  // per pair
     std::vector<uint64_t> paths;        // per problem
-    // per-problem CSR (local indices) on the device, concatenated
-    std::vector<int64_t> csr_rp_off, csr_nz_off;
-    int64_t *rp = nullptr;
-    int32_t *col = nullptr;
-    double *val = nullptr;
-    // per-pair arrays
+    // the pre-pass's CSR over slots (control variates): each pair's copy of its
+    // problem's rows, columns shifted to the pair's slots, so that one pass
+    // prepares every pair
+    int64_t *srp = nullptr;     // [slots + 1]
+    int32_t *scol = nullptr;
+    double *sval = nullptr;
+    double *t_row = nullptr;    // [slots] horizon of each slot's pair
+    int32_t *slot_pair = nullptr;  // [slots] pair of each slot
+    // per-slot arrays
     double *v = nullptr;      // [slots]
     float *vf = nullptr;      // [slots]
     uint32_t *vexp = nullptr;  // [pairs]
     double *taylor = nullptr;  // [4 slots]
     float *feat = nullptr;     // [5 slots]
     float *y = nullptr;        // [slots]
-    double *coef = nullptr;    // per pair, 32-double aligned
+    double2 *ab = nullptr;     // [slots] coefficient pairs
+    double *h = nullptr;       // [slots] predictions h(t)
     float2 *abf = nullptr;     // [slots] scaled FP32 coefficient pairs (FP32 integrals)
-    int64_t coef_len = 0;
-    double *work = nullptr;    // [3 max_n + 64]
+    double *work = nullptr;    // [3 slots + 64]
     double *mean = nullptr, *sem = nullptr;  // [slots]
     CvbPair *pairs = nullptr;
     int32_t *warp_pairs = nullptr;
@@ -480,7 +520,8 @@ void free_cvbatch(mcx_cvbatch *b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    void *bufs[] = {b->rp, b->col, b->val, b->v, b->vf, b->vexp, b->taylor, b->feat, b->y, b->coef, b->abf, b->work,
+    void *bufs[] = {b->srp, b->scol, b->sval, b->t_row, b->slot_pair, b->v, b->vf, b->vexp, b->taylor, b->feat, b->y,
+                    b->ab, b->h, b->abf, b->work,
                     b->mean, b->sem, b->pairs, b->warp_pairs, b->part, b->items, b->next_item};
     for (void *p : bufs) dev_free(p);
     if (b->plan) mcx_plan_destroy(b->plan);
@@ -609,41 +650,34 @@ cudaError_t apply_layout(mcx_cvbatch *b, cudaStream_t st) {
     return upload_items(b, make_items(b, 1), st);
 }
 
-// The pre-pass of every pair: control-variate Taylor terms, features,
-// prediction, coefficients; or the scaled FP32 copy of v.
+// The pre-pass of every pair in one pass over all slots: control-variate
+// Taylor terms, features, prediction, coefficients (and their exponent and
+// scaled FP32 copy for FP32 integrals); or the scaled FP32 copy of v.
 cudaError_t prepass(mcx_cvbatch *b, cudaStream_t st) {
-    for (int32_t k = 0; k < b->n_pair; ++k) {
-        const CvbPair &pr = b->pair_host[k];
-        const int32_t pb = pr.problem;
-        const int64_t n = pr.n;
-        const int64_t *rp = b->rp + b->csr_rp_off[pb];
-        const int32_t *col = b->col + b->csr_nz_off[pb];
-        const double *val = b->val + b->csr_nz_off[pb];
-        const double *v = b->v + pr.slot;
-        if (cv_mode(b)) {
-            double *T = b->taylor + 4 * pr.slot;
-            float *F = b->feat + 5 * pr.slot;
-            mcx_status rc = mcx_cv_prepare(n, rp, col, val, v, pr.t, b->work, T, F, st);
-            if (rc == MCX_OK && b->control == MCX_CV_LEARNED) rc = mcx_mlp_predict(b->net, n, F, b->y + pr.slot, st);
-            if (rc == MCX_OK)
-                rc = mcx_cv_coefficients(n, rp, col, val, T, b->control == MCX_CV_LEARNED ? b->y + pr.slot : nullptr,
-                                         pr.t, b->work, b->coef + pr.coef, st);
+    const int64_t S = b->slots;
+    const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((S + 255) / 256, 152 * 8));
+    if (cv_mode(b)) {
+        cudaError_t e = cv_prepare_rows(S, b->srp, b->scol, b->sval, b->v, 0.0, b->t_row, b->work, b->taylor, b->feat,
+                                        st);
+        if (e != cudaSuccess) return e;
+        if (b->control == MCX_CV_LEARNED) {
+            const mcx_status rc = mcx_mlp_predict(b->net, S, b->feat, b->y, st);
             if (rc != MCX_OK) return rc == MCX_E_OOM ? cudaErrorMemoryAllocation : cudaErrorUnknown;
-            cudaError_t e = cudaMemsetAsync(b->vexp + k, 0, sizeof(uint32_t), st);
-            if (e != cudaSuccess) return e;
-            if (b->precision == MCX_FP32) {  // the coefficients' exponent and their scaled FP32 copy
-                const unsigned nb = (unsigned)std::min<int64_t>((2 * n + 255) / 256, 152 * 8);
-                k_cvb_vexp<<<nb, 256, 0, st>>>(2 * n, b->coef + pr.coef, b->vexp + k);
-                k_coef_f32<<<nb, 256, 0, st>>>(n, reinterpret_cast<const double2 *>(b->coef + pr.coef), b->vexp + k,
-                                               b->abf + pr.slot);
-            }
-        } else if (b->precision == MCX_FP32) {
-            cudaError_t e = cudaMemsetAsync(b->vexp + k, 0, sizeof(uint32_t), st);
-            if (e != cudaSuccess) return e;
-            const unsigned nb = (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 8);
-            k_cvb_vexp<<<nb, 256, 0, st>>>(n, v, b->vexp + k);
-            k_cvb_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, v, b->vexp + k, b->vf + pr.slot);
         }
+        if ((e = cv_coefficients_rows(S, b->srp, b->scol, b->sval, b->taylor,
+                                      b->control == MCX_CV_LEARNED ? b->y : nullptr, 0.0, b->t_row, b->work, b->ab,
+                                      b->h, st)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemsetAsync(b->vexp, 0, sizeof(uint32_t) * b->n_pair, st)) != cudaSuccess) return e;
+        if (b->precision == MCX_FP32) {  // the coefficients' exponent per pair and their scaled FP32 copy
+            k_pair_exponent<<<nb, 256, 0, st>>>(S, 2, reinterpret_cast<const double *>(b->ab), b->slot_pair, b->vexp);
+            k_pair_coef_f32<<<nb, 256, 0, st>>>(S, b->ab, b->slot_pair, b->vexp, b->abf);
+        }
+    } else if (b->precision == MCX_FP32) {
+        cudaError_t e = cudaMemsetAsync(b->vexp, 0, sizeof(uint32_t) * b->n_pair, st);
+        if (e != cudaSuccess) return e;
+        k_pair_exponent<<<nb, 256, 0, st>>>(S, 1, b->v, b->slot_pair, b->vexp);
+        k_pair_pack<<<nb, 256, 0, st>>>(S, b->v, b->slot_pair, b->vexp, b->vf);
     }
     return cudaGetLastError();
 }
@@ -803,7 +837,7 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
     if (control == MCX_CV_LEARNED && !net) return MCX_E_INVALID;
     if (precision != MCX_FP32 && precision != MCX_FP64) return MCX_E_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int64_t N = 0, nnz = 0, slots = 0, max_n = 0, coef_len = 0;
+    int64_t N = 0, nnz = 0, slots = 0, snnz = 0;
     std::vector<int64_t> off(count);
     for (int32_t i = 0; i < count; ++i) {
         const mcx_cv_problem &p = pr[i];
@@ -819,8 +853,7 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
         N += (p.n + CVB_BLOCK - 1) / CVB_BLOCK * CVB_BLOCK;
         nnz += p.nnz;
         slots += p.n * p.n_rhs;
-        max_n = std::max(max_n, p.n);
-        coef_len += p.n_rhs * ((3 * p.n + 31) / 32 * 32);
+        snnz += p.nnz * p.n_rhs;
     }
     if (N >= (int64_t)0x7fffffff) return MCX_E_INVALID;
     mcx_cvbatch *b = new (std::nothrow) mcx_cvbatch();
@@ -831,23 +864,28 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
     b->net = net;
     b->N = N;
     b->slots = slots;
-    b->max_n = max_n;
-    b->coef_len = coef_len;
-    // block-diagonal CSR (host), the per-problem local CSRs, the pairs
+    const bool cv = control != MCX_CV_NONE;
+    // block-diagonal CSR (host), the pairs, the slot CSR of the pre-pass
     std::vector<int64_t> rp(N + 1, 0);
     std::vector<int32_t> col((size_t)std::max<int64_t>(nnz, 1));
     std::vector<double> val((size_t)std::max<int64_t>(nnz, 1));
-    std::vector<int64_t> lrp;
     std::vector<double> vall((size_t)std::max<int64_t>(slots, 1));
-    int64_t w = 0, slot = 0, coef = 0;
+    std::vector<int32_t> spair((size_t)std::max<int64_t>(slots, 1));
+    std::vector<double> trow((size_t)std::max<int64_t>(slots, 1));
+    std::vector<int64_t> srp;
+    std::vector<int32_t> scol;
+    std::vector<double> sval;
+    if (cv) {
+        srp.assign((size_t)slots + 1, 0);
+        scol.resize((size_t)std::max<int64_t>(snnz, 1));
+        sval.resize((size_t)std::max<int64_t>(snnz, 1));
+    }
+    int64_t w = 0, slot = 0, sw = 0;
     for (int32_t i = 0; i < count; ++i) {
         const mcx_cv_problem &p = pr[i];
-        b->csr_rp_off.push_back((int64_t)lrp.size());
-        b->csr_nz_off.push_back(w);
         double lam = 0.0;  // mean jump rate (cost model)
         for (int64_t r = 0; r < p.n; ++r) {
             rp[off[i] + r] = w;
-            lrp.push_back(p.row_ptr[r]);
             for (int64_t q = p.row_ptr[r]; q < p.row_ptr[r + 1]; ++q) {
                 col[w] = (int32_t)(p.col[q] + off[i]);
                 val[w] = p.val[q];
@@ -855,7 +893,6 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
                 ++w;
             }
         }
-        lrp.push_back(p.row_ptr[p.n]);
         lam /= (double)p.n;
         const int64_t end = (i + 1 < count) ? off[i + 1] : N;
         for (int64_t r = off[i] + p.n; r < end; ++r) rp[r] = w;
@@ -865,7 +902,6 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
             q.off = off[i];
             q.n = p.n;
             q.slot = slot;
-            q.coef = coef;
             q.paths = p.paths;
             q.path_base = (uint64_t)b->pair_host.size() << 40;
             q.t = p.t[r];
@@ -873,13 +909,26 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
             q.problem = i;
             q.rhs = r;
             memcpy(vall.data() + slot, p.v + (size_t)r * (size_t)p.n, sizeof(double) * (size_t)p.n);
+            for (int64_t j = 0; j < p.n; ++j) {
+                spair[slot + j] = (int32_t)b->pair_host.size();
+                trow[slot + j] = p.t[r];
+            }
+            if (cv)
+                for (int64_t j = 0; j < p.n; ++j) {  // this pair's copy of the rows, columns in its slots
+                    srp[slot + j] = sw;
+                    for (int64_t q2 = p.row_ptr[j]; q2 < p.row_ptr[j + 1]; ++q2) {
+                        scol[sw] = (int32_t)(slot + p.col[q2]);
+                        sval[sw] = p.val[q2];
+                        ++sw;
+                    }
+                }
             b->pair_host.push_back(q);
             b->cost_per_path.push_back(1.0 + p.t[r] * lam);
             slot += p.n;
-            coef += (3 * p.n + 31) / 32 * 32;
         }
     }
     rp[N] = w;
+    if (cv) srp[slots] = sw;
     b->n_pair = (int32_t)b->pair_host.size();
     mcx_status rc = mcx_plan_create(N, w, rp.data(), col.data(), val.data(), MCX_PLAN_HOST_INPUT, stream, &b->plan);
     if (rc != MCX_OK) {
@@ -888,17 +937,10 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
         return rc;
     }
     cudaError_t e = cudaSuccess;
-    const bool cv = control != MCX_CV_NONE;
     const size_t sl = (size_t)std::max<int64_t>(slots, 1);
     do {
-        // the local CSRs for the pre-pass (Taylor terms, rates, features, coefficients)
-        std::vector<int32_t> lcol((size_t)std::max<int64_t>(nnz, 1));
-        for (int32_t i = 0; i < count; ++i)
-            for (int64_t q = 0; q < pr[i].nnz; ++q) lcol[b->csr_nz_off[i] + q] = pr[i].col[q];
-        if ((e = dev_malloc(reinterpret_cast<void **>(&b->rp), sizeof(int64_t) * lrp.size())) != cudaSuccess) break;
-        if ((e = dev_malloc(reinterpret_cast<void **>(&b->col), sizeof(int32_t) * lcol.size())) != cudaSuccess) break;
-        if ((e = dev_malloc(reinterpret_cast<void **>(&b->val), sizeof(double) * val.size())) != cudaSuccess) break;
         if ((e = dev_malloc(reinterpret_cast<void **>(&b->v), sizeof(double) * sl)) != cudaSuccess) break;
+        if ((e = dev_malloc(reinterpret_cast<void **>(&b->slot_pair), sizeof(int32_t) * sl)) != cudaSuccess) break;
         if ((e = dev_malloc(reinterpret_cast<void **>(&b->mean), sizeof(double) * sl)) != cudaSuccess) break;
         if ((e = dev_malloc(reinterpret_cast<void **>(&b->sem), sizeof(double) * sl)) != cudaSuccess) break;
         if ((e = dev_malloc(reinterpret_cast<void **>(&b->pairs), sizeof(CvbPair) * b->n_pair)) != cudaSuccess) break;
@@ -907,14 +949,18 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
         if ((e = dev_malloc(reinterpret_cast<void **>(&b->vexp), sizeof(uint32_t) * b->n_pair)) != cudaSuccess) break;
         if ((e = dev_malloc(reinterpret_cast<void **>(&b->next_item), 16)) != cudaSuccess) break;
         if (cv) {
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->srp), sizeof(int64_t) * srp.size())) != cudaSuccess) break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->scol), sizeof(int32_t) * scol.size())) != cudaSuccess)
+                break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->sval), sizeof(double) * sval.size())) != cudaSuccess)
+                break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->t_row), sizeof(double) * sl)) != cudaSuccess) break;
             if ((e = dev_malloc(reinterpret_cast<void **>(&b->taylor), 4 * sizeof(double) * sl)) != cudaSuccess) break;
             if ((e = dev_malloc(reinterpret_cast<void **>(&b->feat), 5 * sizeof(float) * sl)) != cudaSuccess) break;
             if ((e = dev_malloc(reinterpret_cast<void **>(&b->y), sizeof(float) * sl)) != cudaSuccess) break;
-            if ((e = dev_malloc(reinterpret_cast<void **>(&b->coef), sizeof(double) * (size_t)coef_len)) !=
-                cudaSuccess)
-                break;
-            if ((e = dev_malloc(reinterpret_cast<void **>(&b->work), sizeof(double) * (size_t)(3 * max_n + 64))) !=
-                cudaSuccess)
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->ab), sizeof(double2) * sl)) != cudaSuccess) break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->h), sizeof(double) * sl)) != cudaSuccess) break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->work), sizeof(double) * (3 * sl + 64))) != cudaSuccess)
                 break;
             if (precision == MCX_FP32 &&
                 (e = dev_malloc(reinterpret_cast<void **>(&b->abf), sizeof(float2) * sl)) != cudaSuccess)
@@ -923,9 +969,13 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
             if ((e = dev_malloc(reinterpret_cast<void **>(&b->vf), sizeof(float) * sl)) != cudaSuccess) break;
         }
         cudaMemsetAsync(b->vexp, 0, sizeof(uint32_t) * b->n_pair, st);
-        cudaMemcpyAsync(b->rp, lrp.data(), sizeof(int64_t) * lrp.size(), cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(b->col, lcol.data(), sizeof(int32_t) * lcol.size(), cudaMemcpyHostToDevice, st);
-        cudaMemcpyAsync(b->val, val.data(), sizeof(double) * val.size(), cudaMemcpyHostToDevice, st);
+        if (cv) {
+            cudaMemcpyAsync(b->srp, srp.data(), sizeof(int64_t) * srp.size(), cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(b->scol, scol.data(), sizeof(int32_t) * scol.size(), cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(b->sval, sval.data(), sizeof(double) * sval.size(), cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(b->t_row, trow.data(), sizeof(double) * sl, cudaMemcpyHostToDevice, st);
+        }
+        cudaMemcpyAsync(b->slot_pair, spair.data(), sizeof(int32_t) * sl, cudaMemcpyHostToDevice, st);
         if ((e = cudaMemcpyAsync(b->v, vall.data(), sizeof(double) * sl, cudaMemcpyHostToDevice, st)) != cudaSuccess)
             break;
         int dev = 0;
@@ -943,7 +993,8 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
         CvbArgs &ba = b->ba;
         ba.pairs = b->pairs;
         ba.next_item = b->next_item;
-        ba.coef = b->coef;
+        ba.ab = b->ab;
+        ba.h = b->h;
         ba.abf = b->abf;
         ba.v = b->v;
         ba.vf = b->vf;
@@ -1022,8 +1073,12 @@ mcx_status mcx_cvbatch_coefficients(const mcx_cvbatch *b, int32_t problem, int32
     if (!b || !coef || !cv_mode(b)) return MCX_E_INVALID;
     for (const auto &p : b->pair_host) {
         if (p.problem != problem || p.rhs != rhs) continue;
-        return cvb_status(cudaMemcpyAsync(coef, b->coef + p.coef, sizeof(double) * 3 * (size_t)p.n,
-                                          cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream)));
+        const cudaStream_t st = static_cast<cudaStream_t>(stream);
+        const cudaError_t e = cudaMemcpyAsync(coef, b->ab + p.slot, sizeof(double2) * (size_t)p.n,
+                                              cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cvb_status(e);
+        return cvb_status(cudaMemcpyAsync(coef + 2 * p.n, b->h + p.slot, sizeof(double) * (size_t)p.n,
+                                          cudaMemcpyDeviceToDevice, st));
     }
     return MCX_E_INVALID;
 }

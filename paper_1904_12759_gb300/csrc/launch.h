@@ -88,6 +88,16 @@ cudaError_t launch_trace_forward(mcx_plan *plan, const double *v, double t, int 
 cudaError_t launch_trace(mcx_plan *plan, double t, int mode, int nsteps, int32_t entry, uint64_t seed,
                          uint64_t first_path, uint32_t count, int precision, int32_t *end, uint32_t *njumps,
                          uint64_t *hash, double *logw, cudaStream_t st);
+// The control variate's pre-pass over rows 0..n-1 of one CSR (cv.cu): Taylor
+// terms and features (as mcx_cv_prepare), coefficients into ab [n] and h [n]
+// (as mcx_cv_coefficients); t_row, when not NULL, gives each row its own
+// horizon, so that the rows of many problems are prepared in one pass.
+cudaError_t cv_prepare_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                            const double *v, double t, const double *t_row, double *work, double *taylor,
+                            float *features, cudaStream_t st);
+cudaError_t cv_coefficients_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                                 const double *taylor, const float *y, double t, const double *t_row, double *work,
+                                 double2 *ab, double *h, cudaStream_t st);
 cudaError_t run_power_iteration(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
                                 int32_t max_iters, double tol, double *work, double *lambda, int32_t *iters,
                                 cudaStream_t st);
