@@ -527,9 +527,11 @@ typedef struct mcx_mlp mcx_mlp;
  *   features float32 [5n] out, node-major: log1p(lambda_i), log1p(mean of the
  *            neighbours' lambda), log1p(their standard deviation),
  *            t(Av)_i/T2_i, t^2(A^2v)_i/(2 T2_i), T2 = v + tAv + t^2A^2v/2
- *   work     float64 [2n + 64] scratch
- * Rows longer than 32 entries (hubs) are handled one warp per row.
- * Errors: MCX_E_INVALID, MCX_E_CUDA.
+ *   work     float64 [3n + 64] scratch, 16-byte aligned
+ * Two passes over the rows form Av with the rates lambda, then A^2 v with the
+ * features; a third forms A^3 v.  Rows longer than 32 entries (hubs) are
+ * handled one warp per row, rows longer than 1024 one block per row.
+ * Errors: MCX_E_INVALID (also a misaligned work), MCX_E_CUDA.
  */
 mcx_status mcx_cv_prepare(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
                           const double *v, double t, double *work, double *taylor, float *features, void *stream);

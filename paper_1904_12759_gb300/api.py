@@ -456,7 +456,7 @@ def cv_prepare(row_ptr, col, val, v, t: float, stream=None):
     """Taylor terms [4, n] (v, Av, A^2v, A^3v) and node features [n, 5] of (A, v, t)."""
     n = row_ptr.numel() - 1
     dev = row_ptr.device
-    work = torch.empty(2 * n + 64, dtype=torch.float64, device=dev)
+    work = torch.empty(3 * n + 64, dtype=torch.float64, device=dev)
     taylor = torch.empty(4 * n, dtype=torch.float64, device=dev)
     feat = torch.empty(5 * n, dtype=torch.float32, device=dev)
     check(_lib.load().mcx_cv_prepare(n, C.c_void_p(_dev(row_ptr, torch.int64, "row_ptr")),

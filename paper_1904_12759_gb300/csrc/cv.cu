@@ -51,237 +51,425 @@ constexpr int GRAD_SAMPLES = 64;  // samples per gradient block (one per thread)
 constexpr int HS = HID + 1;
 
 // ---------------------------------------------------------------------------
-// Taylor terms and features
+// Row passes: Taylor terms, rates, features, cubic coefficients
 // ---------------------------------------------------------------------------
-// Sums over the kept (positive off-diagonal) entries of row i of the double-float
-// values f(p, c): one thread per row for rows of at most LONG_ROW entries, one
-// warp per queued long row.  `bad` flags values outside the double-float range.
-struct RowSums {
-    df s1, s2;
-    int d;
-    bool bad;
-};
+// The pre-pass visits each row of A three times: (1) (Av)_i and the rate
+// lambda_i; (2) (A^2 v)_i and the features (neighbour statistics of lambda,
+// gathered with Av from one 16-byte record per neighbour); (3) (A^3 v)_i (and,
+// in the batched form, (A c3)_i from one 16-byte record (A^2 v, c3) per
+// neighbour).
+//
+// Traversal.  Every pass visits the rows in the same way, decided by a row's
+// length alone: rows of at most LONG_ROW entries one thread per row, entries
+// in order; rows of at most HUGE_ROW entries one warp per row (lanes stride
+// the row, xor tree over the lanes); longer rows one block per row (threads
+// stride the row; warp trees, then a tree over the warps' results).  A row's
+// sums therefore depend only on the row, so two passes (or two layouts) that
+// form the same sum get the same bits.  A row schedule lists the rows longer
+// than HUGE_ROW, then those longer than LONG_ROW, then the short rows; one
+// launch per pass, a static split: blocks take the huge rows, then warps the
+// long rows, then groups of 32 short rows.
+//
+// The short rows are the bulk of a power-law graph and their loads decide the
+// time: the matrix entries of 32 rows read one per lane, plus one random
+// gather per entry.  Two layouts of the short rows:
+//  * CSR (mcx_cv_prepare, mcx_cv_coefficients): short rows in their natural
+//    order, so a warp's 32 rows are adjacent in memory;
+//  * sliced ELL (the batched form, built once at creation): short rows sorted
+//    by length within windows of CV_ROW_WINDOW rows and stored in chunks of 32
+//    rows, entry k of the chunk's rows contiguous, so that a warp's loads of
+//    the matrix are coalesced and its lanes run rows of nearly equal length.
+// GB300 runs FP64 at a small fraction of its FP32 rate: the sums' multiply-adds
+// stay FP64, but sign tests, the rates and the features run on the integer and
+// FP32 pipes (double-float).  A row operation Op supplies
+//   Acc zero(); add(acc, i, c, a) per entry (column c, value a);
+//   combine(x, y) and shfl(x, o) for the trees; finish(i, acc), one thread.
+constexpr int WINDOW = CV_ROW_WINDOW;  // rows per window of the schedule builder (one block per window)
+constexpr int PASS_THREADS = 256;
+constexpr int PASS_MIN_BLOCKS = 6;
 
-__device__ __forceinline__ void row_add(RowSums &r, df x) {
-    r.s1 = df_add(r.s1, x);
-    r.s2 = df_add(r.s2, df_mul(x, x));
-    r.d += 1;
-}
+// Row schedule (CvRowSchedule): order [n] = huge rows, long rows, short rows in
+// natural order; cnt = {huge, long, short, huge cursor, long cursor}; hist:
+// [windows + 1] the windows' starts among the short rows.
+using RowSchedule = CvRowSchedule;
+static_assert(CV_ROW_CNT >= 5, "row schedule counters");
 
-__device__ __forceinline__ RowSums warp_rowsums(RowSums r) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        r.s1 = df_add(r.s1, df_shfl_xor(r.s1, o));
-        r.s2 = df_add(r.s2, df_shfl_xor(r.s2, o));
-        r.d += __shfl_xor_sync(0xffffffffu, r.d, o);
+__device__ __forceinline__ bool is_short(int64_t len) { return len <= LONG_ROW; }
+
+// per window: its number of short rows; global numbers of huge and long rows
+__global__ void __launch_bounds__(WINDOW) k_sched_count(int64_t n, const int64_t *__restrict__ rp,
+                                                        uint32_t *__restrict__ win, uint32_t *cnt) {
+    const int64_t i = (int64_t)blockIdx.x * WINDOW + threadIdx.x;
+    int s = 0, l = 0, h = 0;
+    if (i < n) {
+        const int64_t len = rp[i + 1] - rp[i];
+        s = is_short(len);
+        h = len > HUGE_ROW;
+        l = !s && !h;
     }
-    r.bad = __any_sync(0xffffffffu, r.bad);
-    return r;
+    s = __syncthreads_count(s);
+    l = __syncthreads_count(l);
+    h = __syncthreads_count(h);
+    if (threadIdx.x == 0) {
+        win[blockIdx.x] = (uint32_t)s;
+        if (l) atomicAdd(cnt + 1, (uint32_t)l);
+        if (h) atomicAdd(cnt + 0, (uint32_t)h);
+    }
 }
 
-// rate lambda_i = sum of the positive off-diagonal entries (FP64 if a value is
-// outside the double-float range)
-__device__ __forceinline__ double rate_fp64(int64_t i, int64_t p0, int64_t p1, int64_t step,
+// exclusive scan of the windows' short counts (one block); cnt[2] = total
+__global__ void __launch_bounds__(1024) k_sched_scan(int64_t windows, uint32_t *win, uint32_t *cnt) {
+    __shared__ uint32_t part[1024];
+    const int64_t per = (windows + 1023) / 1024;
+    const int64_t a = (int64_t)threadIdx.x * per, b = a + per < windows ? a + per : windows;
+    uint32_t s = 0;
+    for (int64_t w = a; w < b; ++w) s += win[w];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the partial sums
+        const uint32_t add = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += add;
+        __syncthreads();
+    }
+    uint32_t run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+    for (int64_t w = a; w < b; ++w) {
+        const uint32_t c = win[w];
+        win[w] = run;
+        run += c;
+    }
+    if (threadIdx.x == 1023) cnt[2] = part[1023];
+}
+
+// place every row: huge and long rows at their lists' cursors (any order),
+// short rows in natural order
+__global__ void __launch_bounds__(WINDOW) k_sched_fill(int64_t n, const int64_t *__restrict__ rp,
+                                                       const uint32_t *__restrict__ win, uint32_t *cnt,
+                                                       int32_t *__restrict__ order) {
+    __shared__ uint32_t wc[WINDOW / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * WINDOW + threadIdx.x;
+    const int64_t len = i < n ? rp[i + 1] - rp[i] : -1;
+    const bool sh = i < n && is_short(len);
+    const unsigned m = __ballot_sync(0xffffffffu, sh);
+    if (lane == 0) wc[warp] = (uint32_t)__popc(m);
+    __syncthreads();
+    uint32_t before = (uint32_t)__popc(m & ((1u << lane) - 1u));
+    for (int w = 0; w < warp; ++w) before += wc[w];
+    if (i < n) {
+        const uint32_t n_huge = cnt[0], n_long = cnt[1];
+        if (sh) order[n_huge + n_long + win[blockIdx.x] + before] = (int32_t)i;
+        else if (len > HUGE_ROW) order[atomicAdd(cnt + 3, 1u)] = (int32_t)i;
+        else order[n_huge + atomicAdd(cnt + 4, 1u)] = (int32_t)i;
+    }
+}
+
+template <class Op, bool ELL>
+__global__ void __launch_bounds__(PASS_THREADS, PASS_MIN_BLOCKS)
+    k_pass(const int64_t *__restrict__ rp, const int32_t *__restrict__ col, const double *__restrict__ val,
+           const int32_t *__restrict__ order, const uint32_t *__restrict__ cnt, CvSell ell, Op op) {
+    __shared__ typename Op::Acc sh[PASS_THREADS / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t n_huge = cnt[0], n_long = cnt[1], n_short = cnt[2];
+    for (uint32_t r = blockIdx.x; r < n_huge; r += gridDim.x) {
+        const int32_t i = order[r];
+        typename Op::Acc a = Op::zero();
+#pragma unroll 4
+        for (int64_t p = rp[i] + threadIdx.x; p < rp[i + 1]; p += PASS_THREADS) op.add(a, i, col[p], val[p]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a = Op::combine(a, Op::shfl(a, o));
+        if (lane == 0) sh[warp] = a;
+        __syncthreads();
+        if (warp == 0) {
+            typename Op::Acc s = lane < PASS_THREADS / 32 ? sh[lane] : Op::zero();
+#pragma unroll
+            for (int o = PASS_THREADS / 64; o > 0; o >>= 1) s = Op::combine(s, Op::shfl(s, o));
+            if (lane == 0) op.finish(i, s);
+        }
+        __syncthreads();  // sh reusable
+    }
+    const uint32_t warps = gridDim.x * (PASS_THREADS / 32);
+    const uint32_t gw = blockIdx.x * (PASS_THREADS / 32) + (uint32_t)warp;
+    for (uint32_t k = gw; k < n_long; k += warps) {
+        const int32_t i = order[n_huge + k];
+        typename Op::Acc a = Op::zero();
+#pragma unroll 4
+        for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) op.add(a, i, col[p], val[p]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a = Op::combine(a, Op::shfl(a, o));
+        if (lane == 0) op.finish(i, a);
+    }
+    const uint32_t items = (n_short + 31) / 32;
+    for (uint32_t k = gw; k < items; k += warps) {
+        const uint32_t j = k * 32u + (uint32_t)lane;
+        if (j >= n_short) continue;
+        const int32_t i = order[n_huge + n_long + j];
+        typename Op::Acc a = Op::zero();
+        if constexpr (ELL) {
+            const int d = ell.len[j];
+            const int32_t *c = ell.col + ell.chunk[k] + lane;
+            const double *w = ell.val + ell.chunk[k] + lane;
+#pragma unroll 4
+            for (int e = 0; e < d; ++e) op.add(a, i, c[32 * e], w[32 * e]);
+        } else {
+            const int64_t p0 = rp[i], p1 = rp[i + 1];
+#pragma unroll 4
+            for (int64_t p = p0; p < p1; ++p) op.add(a, i, col[p], val[p]);
+        }
+        op.finish(i, a);
+    }
+}
+
+unsigned pass_grid() { return 152u * PASS_MIN_BLOCKS; }
+
+// Build the row schedule of rows 0..n-1 (short rows in natural order).
+cudaError_t build_schedule(int64_t n, const int64_t *rp, const RowSchedule &s, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(s.cnt, 0, sizeof(uint32_t) * CV_ROW_CNT, st);
+    if (e != cudaSuccess) return e;
+    const int64_t windows = (n + WINDOW - 1) / WINDOW;
+    k_sched_count<<<(unsigned)windows, WINDOW, 0, st>>>(n, rp, s.hist, s.cnt);
+    k_sched_scan<<<1, 1024, 0, st>>>(windows, s.hist, s.cnt);
+    k_sched_fill<<<(unsigned)windows, WINDOW, 0, st>>>(n, rp, s.hist, s.cnt, s.order);
+    return cudaGetLastError();
+}
+
+// One pass of `op` over the scheduled rows; ell: the short rows' sliced ELL
+// copy, or NULL (CSR).
+template <class Op>
+void run_pass(const int64_t *rp, const int32_t *col, const double *val, const RowSchedule &s, const CvSell *ell,
+              const Op &op, cudaStream_t st) {
+    if (ell)
+        k_pass<Op, true><<<pass_grid(), PASS_THREADS, 0, st>>>(rp, col, val, s.order, s.cnt, *ell, op);
+    else
+        k_pass<Op, false><<<pass_grid(), PASS_THREADS, 0, st>>>(rp, col, val, s.order, s.cnt, CvSell{}, op);
+}
+
+// a > 0 for a double by its bits (integer pipe): sign clear, not zero, not NaN
+__device__ __forceinline__ bool positive(double a) {
+    const long long b = __double_as_longlong(a);
+    return b > 0 && b <= 0x7ff0000000000000ll;
+}
+
+__device__ __forceinline__ df df_shfl(df a, int o) { return df_shfl_xor(a, o); }
+
+// A double-float value in the second half of a 16-byte record (h in the low word).
+__device__ __forceinline__ double df_pack(df a) { return __hiloint2double(__float_as_int(a.l), __float_as_int(a.h)); }
+__device__ __forceinline__ df df_unpack(double d) {
+    return df{__int_as_float(__double2loint(d)), __int_as_float(__double2hiint(d))};
+}
+
+// rate lambda_i = sum of the positive off-diagonal entries in FP64, entry order
+// (rows with a value outside the double-float range)
+__device__ __forceinline__ double rate_fp64(int64_t i, const int64_t *__restrict__ rp,
                                             const int32_t *__restrict__ col, const double *__restrict__ val) {
     double s = 0.0;
-    for (int64_t p = p0; p < p1; p += step)
-        if (col[p] != i && val[p] > 0.0) s = __dadd_rn(s, val[p]);
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p)
+        if (col[p] != i && positive(val[p])) s = __dadd_rn(s, val[p]);
     return s;
 }
 
-__global__ void k_rates(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                        const double *__restrict__ val, double *__restrict__ lam) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p0 = rp[i], p1 = rp[i + 1];
-        if (p1 - p0 > LONG_ROW) continue;
-        df s{0.0f, 0.0f};
-        bool bad = false;
-        for (int64_t p = p0; p < p1; ++p)
-            if (col[p] != i && val[p] > 0.0) s = df_add(s, df_split(val[p], bad));
-        lam[i] = bad ? rate_fp64(i, p0, p1, 1, col, val) : df_to_double(df_norm(s));
+// Pass 1 on row i: (Av)_i (FP64) and lambda_i (double-float sum of the kept
+// entries, FP64 where a value is outside the double-float range).  Writes Av,
+// lambda (FP64) and the record g_i = (Av_i, lambda_i as double-float) for pass
+// 2, whose high part is a NaN where lambda_i is outside 2^-60 .. 2^60 (pass 2
+// squares it), so that pass 2 takes that row's neighbours in FP64.
+struct PassRates {
+    const int64_t *rp;
+    const int32_t *col;
+    const double *val;
+    const double *x;  // v
+    double *t1;       // Av
+    double *lam;      // lambda (FP64)
+    double2 *g;       // (Av_i, lambda_i)
+    struct Acc {
+        double t;
+        df s;
+        int bad;
+    };
+    static __device__ __forceinline__ Acc zero() { return Acc{0.0, {0.0f, 0.0f}, 0}; }
+    __device__ __forceinline__ void add(Acc &a, int64_t i, int32_t c, double w) const {
+        a.t = __fma_rn(w, __ldg(x + c), a.t);
+        if (c != i && positive(w)) {
+            bool b = false;
+            a.s = df_add(a.s, df_split(w, b));
+            a.bad |= (int)b;
+        }
     }
-}
-
-__global__ void k_rates_long(const int32_t *__restrict__ queue, const unsigned int *qn,
-                             const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                             const double *__restrict__ val, double *__restrict__ lam) {
-    const int lane = threadIdx.x & 31;
-    const unsigned int nq = *qn;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
-        const int32_t i = queue[q];
-        df s{0.0f, 0.0f};
-        bool bad = false;
-        for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32)
-            if (col[p] != i && val[p] > 0.0) s = df_add(s, df_split(val[p], bad));
-        if (__any_sync(0xffffffffu, bad)) {
-            double r = rate_fp64(i, rp[i] + lane, rp[i + 1], 32, col, val);
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-            if (lane == 0) lam[i] = r;
+    static __device__ __forceinline__ Acc shfl(Acc a, int o) {
+        return Acc{__shfl_xor_sync(0xffffffffu, a.t, o), df_shfl(a.s, o), __shfl_xor_sync(0xffffffffu, a.bad, o)};
+    }
+    static __device__ __forceinline__ Acc combine(Acc a, Acc b) { return Acc{a.t + b.t, df_add(a.s, b.s), a.bad | b.bad}; }
+    __device__ __forceinline__ void finish(int64_t i, Acc a) const {
+        df d;
+        double l;
+        bool b = false;
+        if (a.bad) {
+            l = rate_fp64(i, rp, col, val);
+            d = df_split(l, b);
         } else {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s = df_add(s, df_shfl_xor(s, o));
-            if (lane == 0) lam[i] = df_to_double(df_norm(s));
+            d = df_norm(a.s);
+            l = df_to_double(d);
         }
+        const float m = fabsf(d.h);
+        if (b || !(m == 0.0f || (m >= 8.673617379884035e-19f && m <= 1.152921504606847e18f)))
+            d.h = __int_as_float(0x7fc00000);
+        t1[i] = a.t;
+        lam[i] = l;
+        g[i] = make_double2(a.t, df_pack(d));
     }
+};
+
+// Features of node i, mapped to FP32: log1p(lambda), log1p(mean and standard
+// deviation of the neighbours' lambda), t Av / T2, t^2 A^2 v / (2 T2) with
+// T2 = v + t Av + t^2 A^2 v/2.  T2 and the two numerators in double-float on
+// the FP32 pipe where every input and intermediate stays well inside its
+// range (2^-90 .. 2^100), else in FP64.
+__device__ __forceinline__ bool df_safe(df a) {
+    const float m = fabsf(a.h);
+    return m == 0.0f || (m >= 8.077935669463161e-28f && m <= 1.2676506002282294e30f);
 }
 
-// Fixed-shape double-float sum over a block of ROW_BLOCK threads; valid in thread 0.
-__device__ __forceinline__ df block_sum_df(df v, df *sh) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = df_add(v, df_shfl_xor(v, o));
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    df r{0.0f, 0.0f};
-    if (warp == 0) {
-        if (lane < ROW_BLOCK / 32) r = sh[lane];
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) r = df_add(r, df_shfl_xor(r, o));
+__device__ __forceinline__ void feature_row(int64_t i, float mean, float sd, float lam_i, double v_i, double t1,
+                                            double t2, double t, float *__restrict__ F) {
+    bool bad = false;
+    const df dv = df_split(v_i, bad), d1 = df_split(t1, bad), d2 = df_split(t2, bad), dt = df_split(t, bad);
+    const df a1 = df_mul(dt, d1);              // t Av
+    const df a2 = df_mul(df_mul(dt, dt), d2);  // t^2 A^2 v
+    const df T2 = df_norm(df_add(df_add(dv, a1), df{__fmul_rn(0.5f, a2.h), __fmul_rn(0.5f, a2.l)}));
+    float n3, n4, T2s;
+    if (!bad && df_safe(dv) && df_safe(a1) && df_safe(a2) && df_safe(T2)) {
+        n3 = __fadd_rn(a1.h, a1.l);
+        n4 = __fadd_rn(a2.h, a2.l);
+        T2s = T2.h != 0.0f ? T2.h : 1.0f;
+    } else {
+        const double T2d = v_i + t * t1 + t * t * t2 / 2.0;
+        n3 = (float)(t * t1);
+        n4 = (float)(t * t * t2);
+        T2s = T2d != 0.0 ? (float)T2d : 1.0f;
     }
-    __syncthreads();
-    return r;
-}
-
-// rates of the queued rows above HUGE_ROW entries, one block per row
-__global__ void __launch_bounds__(ROW_BLOCK) k_rates_huge(int64_t n, const int32_t *__restrict__ queue,
-                                                          const unsigned int *qn, const int64_t *__restrict__ rp,
-                                                          const int32_t *__restrict__ col,
-                                                          const double *__restrict__ val, double *__restrict__ lam) {
-    __shared__ df shd[ROW_BLOCK / 32];
-    __shared__ double sh[ROW_BLOCK / 32];
-    const unsigned int nq = qn[1];
-    for (unsigned int b = blockIdx.x; b < nq; b += gridDim.x) {
-        const int32_t i = queue[n - 1 - (int64_t)b];
-        df s{0.0f, 0.0f};
-        bool bad = false;
-        for (int64_t p = rp[i] + threadIdx.x; p < rp[i + 1]; p += ROW_BLOCK)
-            if (col[p] != i && val[p] > 0.0) s = df_add(s, df_split(val[p], bad));
-        if (__syncthreads_or(bad)) {
-            const double r = block_sum_row(rate_fp64(i, rp[i] + threadIdx.x, rp[i + 1], ROW_BLOCK, col, val), sh);
-            if (threadIdx.x == 0) lam[i] = r;
-        } else {
-            s = block_sum_df(s, shd);
-            if (threadIdx.x == 0) lam[i] = df_to_double(df_norm(s));
-        }
-    }
-}
-
-// Features of node i from the neighbour sums (double-float) and the Taylor
-// terms (FP64), mapped to FP32: log1p(lambda), log1p(mean and standard
-// deviation of the neighbours' lambda), t Av / T2, t^2 A^2 v / (2 T2).
-// Neighbour mean and standard deviation of lambda in FP64 (rows where a
-// neighbour's lambda is outside the double-float range).
-__device__ __forceinline__ void neighbour_stats_fp64(int64_t i, const int64_t *__restrict__ rp,
-                                                     const int32_t *__restrict__ col, const double *__restrict__ val,
-                                                     const double *__restrict__ lam, float &mean, float &sd) {
-    double s1 = 0.0, s2 = 0.0, d = 0.0;
-    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-        const int32_t c = col[p];
-        if (c != i && val[p] > 0.0) {
-            s1 += lam[c];
-            s2 += lam[c] * lam[c];
-            d += 1.0;
-        }
-    }
-    const double m = d > 0.0 ? s1 / d : 0.0;
-    const double var = d > 0.0 ? s2 / d - m * m : 0.0;
-    mean = (float)m;
-    sd = var > 0.0 ? (float)sqrt(var) : 0.0f;
-}
-
-__device__ __forceinline__ void write_features(int64_t n, int64_t i, RowSums r, const int64_t *__restrict__ rp,
-                                               const int32_t *__restrict__ col, const double *__restrict__ val,
-                                               const double *__restrict__ lam, const double *__restrict__ T,
-                                               double t_all, const double *__restrict__ t_row, float *__restrict__ F) {
-    const double t = t_row ? t_row[i] : t_all;  // the horizon of this row's problem
-    float mean = 0.0f, sd = 0.0f;
-    if (r.bad) {
-        neighbour_stats_fp64(i, rp, col, val, lam, mean, sd);
-    } else if (r.d > 0) {
-        const float d = (float)r.d;  // exact: rows have fewer than 2^24 entries
-        // mean = s1/d and var = s2/d - mean^2 in double-float (one correction step per quotient)
-        const float m1 = __fdiv_rn(r.s1.h, d);
-        const df mu = df{m1, __fdiv_rn(__fadd_rn(__fmaf_rn(-m1, d, r.s1.h), r.s1.l), d)};
-        const float m2 = __fdiv_rn(r.s2.h, d);
-        const df q2 = df{m2, __fdiv_rn(__fadd_rn(__fmaf_rn(-m2, d, r.s2.h), r.s2.l), d)};
-        const df mm = df_mul(mu, mu);
-        const df var = df_norm(df_add(q2, df{-mm.h, -mm.l}));
-        mean = __fadd_rn(mu.h, mu.l);
-        sd = var.h > 0.0f ? sqrtf(var.h) : 0.0f;
-    }
-    const double T2 = T[i] + t * T[n + i] + t * t * T[2 * n + i] / 2.0;
-    const float T2s = T2 != 0.0 ? (float)T2 : 1.0f;
     float *f = F + i * NF;
-    f[0] = log1pf((float)lam[i]);
+    f[0] = log1pf(lam_i);
     f[1] = log1pf(mean);
     f[2] = log1pf(sd);
-    f[3] = __fdiv_rn((float)(t * T[n + i]), T2s);
-    f[4] = __fdiv_rn((float)(t * t * T[2 * n + i]), __fmul_rn(2.0f, T2s));
+    f[3] = __fdiv_rn(n3, T2s);
+    f[4] = __fdiv_rn(n4, __fmul_rn(2.0f, T2s));
 }
 
-__global__ void k_features(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                           const double *__restrict__ val, const double *__restrict__ lam,
-                           const double *__restrict__ T, double t, const double *__restrict__ t_row,
-                           float *__restrict__ F) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        if (rp[i + 1] - rp[i] > LONG_ROW) continue;
-        RowSums r{{0.0f, 0.0f}, {0.0f, 0.0f}, 0, false};
-        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
-            const int32_t c = col[p];
-            if (c != i && val[p] > 0.0) row_add(r, df_split(lam[c], r.bad));
+// Pass 2 on row i: (A^2 v)_i (FP64) and the features.  The neighbours' lambda
+// sums s1 = sum lambda_c, s2 = sum lambda_c^2 over the kept entries in
+// double-float; where either is not finite (a neighbour's lambda outside the
+// double-float range, or an overflow) the row's statistics are redone in FP64.
+struct PassFeatures {
+    const int64_t *rp;
+    const int32_t *col;
+    const double *val;
+    const double2 *g;   // pass 1's records
+    const double *v;
+    const double *lam;  // FP64 lambda
+    double *t2;         // A^2 v
+    float *F;
+    double t_all;
+    const double *t_row;  // per-row horizon, or NULL (t_all)
+    struct Acc {
+        double t;
+        df s1, s2;
+        int d;
+    };
+    static __device__ __forceinline__ Acc zero() { return Acc{0.0, {0.0f, 0.0f}, {0.0f, 0.0f}, 0}; }
+    __device__ __forceinline__ void add(Acc &a, int64_t i, int32_t c, double w) const {
+        const double2 q = __ldg(g + c);
+        a.t = __fma_rn(w, q.x, a.t);
+        if (c != i && positive(w)) {
+            const df x = df_unpack(q.y);
+            a.s1 = df_add(a.s1, x);
+            a.s2 = df_add(a.s2, df_mul(x, x));
+            a.d += 1;
         }
-        write_features(n, i, r, rp, col, val, lam, T, t, t_row, F);
     }
-}
+    static __device__ __forceinline__ Acc shfl(Acc a, int o) {
+        return Acc{__shfl_xor_sync(0xffffffffu, a.t, o), df_shfl(a.s1, o), df_shfl(a.s2, o),
+                   __shfl_xor_sync(0xffffffffu, a.d, o)};
+    }
+    static __device__ __forceinline__ Acc combine(Acc a, Acc b) {
+        return Acc{a.t + b.t, df_add(a.s1, b.s1), df_add(a.s2, b.s2), a.d + b.d};
+    }
+    __device__ __forceinline__ void finish(int64_t i, Acc a) const {
+        float mean = 0.0f, sd = 0.0f;
+        const bool bad = !(fabsf(a.s1.h) <= 3.4028234663852886e38f) || !(fabsf(a.s2.h) <= 3.4028234663852886e38f);
+        if (bad) {
+            double s1 = 0.0, s2 = 0.0, d = 0.0;
+            for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+                const int32_t c = col[p];
+                if (c != i && positive(val[p])) {
+                    s1 += lam[c];
+                    s2 += lam[c] * lam[c];
+                    d += 1.0;
+                }
+            }
+            const double m = d > 0.0 ? s1 / d : 0.0;
+            const double var = d > 0.0 ? s2 / d - m * m : 0.0;
+            mean = (float)m;
+            sd = var > 0.0 ? (float)sqrt(var) : 0.0f;
+        } else if (a.d > 0) {
+            const float d = (float)a.d;  // exact: rows have fewer than 2^24 entries
+            // mean = s1/d and var = s2/d - mean^2 in double-float (one correction step per quotient)
+            const float m1 = __fdiv_rn(a.s1.h, d);
+            const df mu = df{m1, __fdiv_rn(__fadd_rn(__fmaf_rn(-m1, d, a.s1.h), a.s1.l), d)};
+            const float m2 = __fdiv_rn(a.s2.h, d);
+            const df q2 = df{m2, __fdiv_rn(__fadd_rn(__fmaf_rn(-m2, d, a.s2.h), a.s2.l), d)};
+            const df mm = df_mul(mu, mu);
+            const df var = df_norm(df_add(q2, df{-mm.h, -mm.l}));
+            mean = __fadd_rn(mu.h, mu.l);
+            sd = var.h > 0.0f ? sqrtf(var.h) : 0.0f;
+        }
+        t2[i] = a.t;
+        const double2 gi = g[i];
+        const df li = df_unpack(gi.y);
+        const float lf = li.h == li.h ? __fadd_rn(li.h, li.l) : (float)lam[i];
+        feature_row(i, mean, sd, lf, v[i], gi.x, a.t, t_row ? t_row[i] : t_all, F);
+    }
+};
 
-__global__ void k_features_long(int64_t n, const int32_t *__restrict__ queue, const unsigned int *qn,
-                                const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                                const double *__restrict__ val, const double *__restrict__ lam,
-                                const double *__restrict__ T, double t, const double *__restrict__ t_row,
-                                float *__restrict__ F) {
-    const int lane = threadIdx.x & 31;
-    const unsigned int nq = *qn;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += warps) {
-        const int32_t i = queue[q];
-        RowSums r{{0.0f, 0.0f}, {0.0f, 0.0f}, 0, false};
-        for (int64_t p = rp[i] + lane; p < rp[i + 1]; p += 32) {
-            const int32_t c = col[p];
-            if (c != i && val[p] > 0.0) row_add(r, df_split(lam[c], r.bad));
-        }
-        r = warp_rowsums(r);
-        if (lane == 0) write_features(n, i, r, rp, col, val, lam, T, t, t_row, F);
+// y = A x as a row pass.
+struct PassSpmv {
+    const double *x;
+    double *y;
+    struct Acc {
+        double t;
+    };
+    static __device__ __forceinline__ Acc zero() { return Acc{0.0}; }
+    __device__ __forceinline__ void add(Acc &a, int64_t, int32_t c, double w) const {
+        a.t = __fma_rn(w, __ldg(x + c), a.t);
     }
-}
+    static __device__ __forceinline__ Acc shfl(Acc a, int o) { return Acc{__shfl_xor_sync(0xffffffffu, a.t, o)}; }
+    static __device__ __forceinline__ Acc combine(Acc a, Acc b) { return Acc{a.t + b.t}; }
+    __device__ __forceinline__ void finish(int64_t i, Acc a) const { y[i] = a.t; }
+};
 
-// features of the queued rows above HUGE_ROW entries, one block per row
-__global__ void __launch_bounds__(ROW_BLOCK) k_features_huge(int64_t n, const int32_t *__restrict__ queue,
-                                                             const unsigned int *qn, const int64_t *__restrict__ rp,
-                                                             const int32_t *__restrict__ col,
-                                                             const double *__restrict__ val,
-                                                             const double *__restrict__ lam,
-                                                             const double *__restrict__ T, double t,
-                                                             const double *__restrict__ t_row,
-                                                             float *__restrict__ F) {
-    __shared__ df shd[ROW_BLOCK / 32];
-    __shared__ double sh[ROW_BLOCK / 32];
-    const unsigned int nq = qn[1];
-    for (unsigned int b = blockIdx.x; b < nq; b += gridDim.x) {
-        const int32_t i = queue[n - 1 - (int64_t)b];
-        RowSums r{{0.0f, 0.0f}, {0.0f, 0.0f}, 0, false};
-        for (int64_t p = rp[i] + threadIdx.x; p < rp[i + 1]; p += ROW_BLOCK) {
-            const int32_t c = col[p];
-            if (c != i && val[p] > 0.0) row_add(r, df_split(lam[c], r.bad));
-        }
-        r.bad = __syncthreads_or(r.bad);
-        r.s1 = block_sum_df(r.s1, shd);
-        r.s2 = block_sum_df(r.s2, shd);
-        r.d = (int)block_sum_row((double)r.d, sh);
-        if (threadIdx.x == 0) write_features(n, i, r, rp, col, val, lam, T, t, t_row, F);
+// Pass 3 of the batched form on row i: (A^3 v)_i and (A c3)_i from the records
+// q_c = (A^2 v_c, c3_c), each sum formed as PassSpmv forms it, then the
+// coefficient pair (a_i, b_i) = (A^3 v_i / 2 - 3 c3_i, (A c3)_i), as k_cv_ab
+// forms it from those sums.
+struct PassCubic {
+    const double2 *q;
+    double2 *ab;
+    struct Acc {
+        double t, b;
+    };
+    static __device__ __forceinline__ Acc zero() { return Acc{0.0, 0.0}; }
+    __device__ __forceinline__ void add(Acc &a, int64_t, int32_t c, double w) const {
+        const double2 r = __ldg(q + c);
+        a.t = __fma_rn(w, r.x, a.t);
+        a.b = __fma_rn(w, r.y, a.b);
     }
-}
+    static __device__ __forceinline__ Acc shfl(Acc a, int o) {
+        return Acc{__shfl_xor_sync(0xffffffffu, a.t, o), __shfl_xor_sync(0xffffffffu, a.b, o)};
+    }
+    static __device__ __forceinline__ Acc combine(Acc a, Acc b) { return Acc{a.t + b.t, a.b + b.b}; }
+    __device__ __forceinline__ void finish(int64_t i, Acc a) const {
+        ab[i] = make_double2(a.t / 2.0 - 3.0 * q[i].y, a.b);
+    }
+};
 
 // ---------------------------------------------------------------------------
 // MLP
@@ -577,14 +765,19 @@ __global__ void k_feature_stats(int64_t n, const float *__restrict__ F, float *m
 }
 
 // xhat = T2 e^y; c3 = (xhat - T2)/t^3 -> coef: h [n], then (a, b) pairs [n]; c3 staged in b's slot
+// h = xhat = T2 e^y and c3 = (xhat - T2)/t^3; c3 into c3[i], or with A^2 v into
+// the record q[i] = (A^2 v_i, c3_i) of the fused third pass.
 __global__ void k_cv_xhat(int64_t n, const double *__restrict__ T, const float *__restrict__ y, double t_all,
-                          const double *__restrict__ t_row, double *__restrict__ h, double *__restrict__ c3) {
+                          const double *__restrict__ t_row, double *__restrict__ h, double *__restrict__ c3,
+                          double2 *__restrict__ q) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double t = t_row ? t_row[i] : t_all;
         const double T2 = T[i] + t * T[n + i] + t * t * T[2 * n + i] / 2.0;
         const double xh = T2 * exp((double)(y ? y[i] : 0.0f));
+        const double c = (xh - T2) / (t * t * t);
         h[i] = xh;
-        c3[i] = (xh - T2) / (t * t * t);
+        if (q) q[i] = make_double2(T[2 * n + i], c);
+        else c3[i] = c;
     }
 }
 
@@ -896,47 +1089,71 @@ unsigned blocks_for(int64_t n, int threads) {
 
 }  // namespace
 
-// Taylor terms and features of rows 0..n-1 (see mcx_cv_prepare); t_row, when
-// given, holds each row's own horizon (rows of several problems at once).
-cudaError_t cv_prepare_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
-                            const double *v, double t, const double *t_row, double *work, double *taylor,
-                            float *features, cudaStream_t st) {
-    const unsigned nb = blocks_for(n, 256);
-    double *lam = work;
-    int32_t *queue = reinterpret_cast<int32_t *>(work + n);  // n int32
-    unsigned int *qn = reinterpret_cast<unsigned int *>(work + 2 * n);
-    cudaError_t e = cudaMemcpyAsync(taylor, v, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(qn, 0, 2 * sizeof(unsigned int), st);
+// A row schedule carved from float64 scratch at `w`: order [n] int32, then the
+// counters and the window starts.
+void carve_schedule(int64_t n, double *w, CvRowSchedule &s) {
+    s.order = reinterpret_cast<int32_t *>(w);
+    s.cnt = reinterpret_cast<uint32_t *>(w) + n;
+    s.hist = s.cnt + CV_ROW_CNT;
+}
+
+// Taylor terms v, Av, A^2 v (and A^3 v when `third`) and the features of rows
+// 0..n-1 (see mcx_cv_prepare) in two row passes (three with `third`); t_row,
+// when given, holds each row's own horizon (rows of several problems at once).
+// s: the rows' schedule; ell: its short rows' sliced ELL copy or NULL; g: [n]
+// records, 16-byte aligned; lam: float64 [n] scratch (may be taylor + 3n when
+// `third`: the third pass overwrites it).
+cudaError_t cv_taylor_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                           const double *v, double t, const double *t_row, const CvRowSchedule &s, const CvSell *ell,
+                           double2 *g, double *lam, double *taylor, float *features, bool third, cudaStream_t st) {
+    const cudaError_t e = cudaMemcpyAsync(taylor, v, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return e;
-    k_find_long_rows<<<nb, 256, 0, st>>>(n, row_ptr, queue, qn);
-    for (int k = 1; k <= 3; ++k) {
-        const double *x = taylor + (k - 1) * n;
-        double *y = taylor + k * n;
-        k_spmv_short<<<nb, 256, 0, st>>>(n, row_ptr, col, val, x, nullptr, y, nullptr);
-        k_spmv_long<<<152 * 8, 256, 0, st>>>(queue, qn, row_ptr, col, val, x, nullptr, y, nullptr);
-        k_spmv_huge<<<152 * 2, ROW_BLOCK, 0, st>>>(n, queue, qn, row_ptr, col, val, x, nullptr, y, nullptr);
-    }
-    k_rates<<<nb, 256, 0, st>>>(n, row_ptr, col, val, lam);
-    k_rates_long<<<152 * 8, 256, 0, st>>>(queue, qn, row_ptr, col, val, lam);
-    k_rates_huge<<<152 * 2, ROW_BLOCK, 0, st>>>(n, queue, qn, row_ptr, col, val, lam);
-    k_features<<<nb, 256, 0, st>>>(n, row_ptr, col, val, lam, taylor, t, t_row, features);
-    k_features_long<<<152 * 8, 256, 0, st>>>(n, queue, qn, row_ptr, col, val, lam, taylor, t, t_row, features);
-    k_features_huge<<<152 * 2, ROW_BLOCK, 0, st>>>(n, queue, qn, row_ptr, col, val, lam, taylor, t, t_row, features);
+    run_pass(row_ptr, col, val, s, ell, PassRates{row_ptr, col, val, v, taylor + n, lam, g}, st);
+    run_pass(row_ptr, col, val, s, ell,
+             PassFeatures{row_ptr, col, val, g, v, lam, taylor + 2 * n, features, t, t_row}, st);
+    if (third) run_pass(row_ptr, col, val, s, ell, PassSpmv{taylor + 2 * n, taylor + 3 * n}, st);
     return cudaGetLastError();
 }
 
+// mcx_cv_prepare on rows 0..n-1; work: float64 [3n + 64], 16-byte aligned.
+cudaError_t cv_prepare_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                            const double *v, double t, const double *t_row, double *work, double *taylor,
+                            float *features, cudaStream_t st) {
+    double2 *g = reinterpret_cast<double2 *>(work);  // 2n doubles
+    CvRowSchedule s;
+    carve_schedule(n, work + 2 * n, s);
+    const cudaError_t e = build_schedule(n, row_ptr, s, st);
+    if (e != cudaSuccess) return e;
+    return cv_taylor_rows(n, row_ptr, col, val, v, t, t_row, s, nullptr, g, taylor + 3 * n, taylor, features, true,
+                          st);
+}
+
 // Control-variate coefficients of rows 0..n-1 (see mcx_cv_coefficients) into
-// ab [n] and h [n]; t_row as in cv_prepare_rows.  work: float64 [3n + 64].
+// ab [n] and h [n]; t_row as in cv_taylor_rows.  work: float64 [3n + 64].
 cudaError_t cv_coefficients_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
                                  const double *taylor, const float *y, double t, const double *t_row, double *work,
                                  double2 *ab, double *h, cudaStream_t st) {
     const unsigned nb = blocks_for(n, 256);
     double *c3 = work, *Ac3 = work + n;
-    k_cv_xhat<<<nb, 256, 0, st>>>(n, taylor, y, t, t_row, h, c3);
-    cudaError_t e = spmv_hybrid(n, row_ptr, col, val, c3, Ac3, reinterpret_cast<int32_t *>(work + 2 * n),
-                                reinterpret_cast<unsigned int *>(work + 3 * n), st);
+    CvRowSchedule s;
+    carve_schedule(n, work + 2 * n, s);
+    const cudaError_t e = build_schedule(n, row_ptr, s, st);
     if (e != cudaSuccess) return e;
+    k_cv_xhat<<<nb, 256, 0, st>>>(n, taylor, y, t, t_row, h, c3, nullptr);
+    run_pass(row_ptr, col, val, s, nullptr, PassSpmv{c3, Ac3}, st);
     k_cv_ab<<<nb, 256, 0, st>>>(n, taylor, c3, Ac3, ab);
+    return cudaGetLastError();
+}
+
+// The same coefficients from the Taylor terms v, Av, A^2 v alone: A^3 v and A c3
+// in one row pass over the records (A^2 v_c, c3_c) (q: [n], 16-byte aligned);
+// bit-identical to cv_prepare_rows' A^3 v followed by cv_coefficients_rows.
+cudaError_t cv_cubic_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                          const double *taylor, const float *y, double t, const double *t_row,
+                          const CvRowSchedule &s, const CvSell *ell, double2 *q, double2 *ab, double *h,
+                          cudaStream_t st) {
+    k_cv_xhat<<<blocks_for(n, 256), 256, 0, st>>>(n, taylor, y, t, t_row, h, nullptr, q);
+    run_pass(row_ptr, col, val, s, ell, PassCubic{q, ab}, st);
     return cudaGetLastError();
 }
 
@@ -993,6 +1210,7 @@ mcx_status mcx_cv_prepare(int64_t n, const int64_t *row_ptr, const int32_t *col,
                           double t, double *work, double *taylor, float *features, void *stream) {
     NvtxRange nvtx("mcx_cv_prepare");
     if (n < 1 || !row_ptr || !col || !val || !v || !work || !taylor || !features || !(t > 0.0)) return MCX_E_INVALID;
+    if (reinterpret_cast<uintptr_t>(work) & 15u) return MCX_E_INVALID;  // 16-byte records
     return cv_status(cv_prepare_rows(n, row_ptr, col, val, v, t, nullptr, work, taylor, features,
                                      static_cast<cudaStream_t>(stream)));
 }

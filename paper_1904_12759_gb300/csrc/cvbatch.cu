@@ -14,9 +14,13 @@
 // block-diagonal plan, whose rows are the problems' rows shifted by a
 // constant, so every slot choice and every visited state is the same.
 //
-// Run (one graph launch).  Pre-pass per pair: the Taylor terms, features,
-// network prediction (tensor cores) and coefficients of the control variate,
-// or the exponent and scaled FP32 copy of v for plain estimates.  Then one
+// Run (one graph launch).  Pre-pass over all pairs at once, on a CSR of the
+// pairs' slots (each pair's copy of its problem's rows, columns shifted into
+// its slots, each row with its pair's horizon) and a sliced ELL copy of its
+// short rows: with a control variate three row passes (Av with the rates; A^2 v
+// with the features; after the network's prediction on the tensor cores, A^3 v
+// with A c3 and the coefficients), or the exponent and scaled FP32 copy of v
+// for plain estimates.  Then one
 // persistent walk over a work list in largest-estimated-cost-first order
 // (cost ~ paths x (1 + t x mean jump rate)): pairs with at most 64 paths per
 // entry take items of 32 entries with one lane per entry (all paths of the
@@ -38,6 +42,7 @@
 #include "accum.cuh"
 #include "cvmath.cuh"
 #include "launch.h"
+#include "rows.cuh"
 #include "tune_cache.h"
 #include "walker.cuh"
 
@@ -88,12 +93,15 @@ struct CvbArgs {
 
 // Per-pair biased exponent of the largest finite |x| over the pair's slots, `per`
 // doubles per slot (1 for v, 2 for the coefficient pairs); the words are cleared
-// first.  A warp takes 32 consecutive slots, mostly of one pair: one atomic per
-// warp then, one per lane where a pair boundary falls inside.
+// first.  A warp takes 32 consecutive slots, mostly of one pair, and keeps a
+// running maximum while its pair stays the same: one atomic per warp and pair
+// then, one per lane where a pair boundary falls inside the 32 slots.
 __global__ void k_pair_exponent(int64_t slots, int per, const double *__restrict__ x,
                                 const int32_t *__restrict__ slot_pair, uint32_t *vexp) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    uint32_t acc = 0;  // the warp's running maximum for pair acc_k (warp-uniform)
+    int32_t acc_k = -1;
     for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; w0 < slots; w0 += warps * 32) {
         const int64_t s = w0 + lane;
         uint32_t e = 0;
@@ -109,11 +117,18 @@ __global__ void k_pair_exponent(int64_t slots, int per, const double *__restrict
         if (__all_sync(0xffffffffu, k == k0 || k < 0)) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
-            if (lane == 0 && e) atomicMax(vexp + k0, e);
+            if (k0 == acc_k) {
+                acc = max(acc, e);
+            } else {
+                if (lane == 0 && acc) atomicMax(vexp + acc_k, acc);
+                acc_k = k0;
+                acc = e;
+            }
         } else if (k >= 0 && e) {
             atomicMax(vexp + k, e);
         }
     }
+    if (lane == 0 && acc) atomicMax(vexp + acc_k, acc);
 }
 
 // FP32 copies scaled by the pair's power of two: v (plain) and the coefficient pairs.
@@ -469,6 +484,12 @@ struct mcx_cvbatch {
     int64_t *srp = nullptr;     // [slots + 1]
     int32_t *scol = nullptr;
     double *sval = nullptr;
+    int32_t *sorder = nullptr;   // [slots] its row schedule (built once, on the host)
+    uint32_t *scnt = nullptr;    // [CV_ROW_CNT] the schedule's counts
+    int32_t *ell_col = nullptr;  // sliced ELL copy of its short rows (see CvSell)
+    double *ell_val = nullptr;
+    int64_t *ell_chunk = nullptr;
+    uint8_t *ell_len = nullptr;
     double *t_row = nullptr;    // [slots] horizon of each slot's pair
     int32_t *slot_pair = nullptr;  // [slots] pair of each slot
     // per-slot arrays
@@ -481,7 +502,7 @@ struct mcx_cvbatch {
     double2 *ab = nullptr;     // [slots] coefficient pairs
     double *h = nullptr;       // [slots] predictions h(t)
     float2 *abf = nullptr;     // [slots] scaled FP32 coefficient pairs (FP32 integrals)
-    double *work = nullptr;    // [3 slots + 64]
+    double *work = nullptr;    // [2 slots] 16-byte records of the row passes
     double *mean = nullptr, *sem = nullptr;  // [slots]
     CvbPair *pairs = nullptr;
     int32_t *warp_pairs = nullptr;
@@ -520,7 +541,8 @@ void free_cvbatch(mcx_cvbatch *b) {
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
-    void *bufs[] = {b->srp, b->scol, b->sval, b->t_row, b->slot_pair, b->v, b->vf, b->vexp, b->taylor, b->feat, b->y,
+    void *bufs[] = {b->srp, b->scol, b->sval, b->sorder, b->scnt, b->ell_col, b->ell_val, b->ell_chunk, b->ell_len,
+                    b->t_row, b->slot_pair, b->v, b->vf, b->vexp, b->taylor, b->feat, b->y,
                     b->ab, b->h, b->abf, b->work,
                     b->mean, b->sem, b->pairs, b->warp_pairs, b->part, b->items, b->next_item};
     for (void *p : bufs) dev_free(p);
@@ -650,23 +672,88 @@ cudaError_t apply_layout(mcx_cvbatch *b, cudaStream_t st) {
     return upload_items(b, make_items(b, 1), st);
 }
 
-// The pre-pass of every pair in one pass over all slots: control-variate
-// Taylor terms, features, prediction, coefficients (and their exponent and
-// scaled FP32 copy for FP32 integrals); or the scaled FP32 copy of v.
+// The row schedule of the pre-pass's CSR and the sliced ELL copy of its short
+// rows (see CvSell), built on the host: huge rows, long rows, then the short
+// rows window by window (CV_ROW_WINDOW rows), each window's sorted by
+// decreasing length (stable), so that a chunk's 32 rows have nearly equal
+// lengths.  Padding slots of a chunk are zero and never read.
+struct HostEll {
+    std::vector<int32_t> order, col;
+    std::vector<double> val;
+    std::vector<int64_t> chunk;
+    std::vector<uint8_t> len;
+    uint32_t cnt[CV_ROW_CNT] = {};
+};
+
+void build_ell(int64_t n, const std::vector<int64_t> &rp, const std::vector<int32_t> &col,
+               const std::vector<double> &val, HostEll &E) {
+    std::vector<int32_t> huge, lng, shrt;
+    std::vector<int32_t> bucket[LONG_ROW + 1];
+    for (int64_t w0 = 0; w0 < n; w0 += CV_ROW_WINDOW) {
+        const int64_t w1 = std::min<int64_t>(w0 + CV_ROW_WINDOW, n);
+        for (int64_t i = w0; i < w1; ++i) {
+            const int64_t len = rp[i + 1] - rp[i];
+            if (len > HUGE_ROW) huge.push_back((int32_t)i);
+            else if (len > LONG_ROW) lng.push_back((int32_t)i);
+            else bucket[len].push_back((int32_t)i);
+        }
+        for (int64_t d = LONG_ROW; d >= 0; --d) {
+            shrt.insert(shrt.end(), bucket[d].begin(), bucket[d].end());
+            bucket[d].clear();
+        }
+    }
+    E.cnt[0] = (uint32_t)huge.size();
+    E.cnt[1] = (uint32_t)lng.size();
+    E.cnt[2] = (uint32_t)shrt.size();
+    E.order.reserve((size_t)std::max<int64_t>(n, 1));
+    E.order.insert(E.order.end(), huge.begin(), huge.end());
+    E.order.insert(E.order.end(), lng.begin(), lng.end());
+    E.order.insert(E.order.end(), shrt.begin(), shrt.end());
+    const size_t ns = shrt.size(), chunks = (ns + 31) / 32;
+    E.chunk.assign(std::max<size_t>(chunks, 1), 0);
+    E.len.assign(std::max<size_t>(ns, 1), 0);
+    int64_t off = 0;
+    for (size_t k = 0; k < chunks; ++k) {
+        int64_t L = 0;
+        for (size_t j = 32 * k; j < std::min(ns, 32 * k + 32); ++j) {
+            const int64_t d = rp[shrt[j] + 1] - rp[shrt[j]];
+            E.len[j] = (uint8_t)d;
+            L = std::max(L, d);
+        }
+        E.chunk[k] = off;
+        off += 32 * L;
+    }
+    E.col.assign((size_t)std::max<int64_t>(off, 1), 0);
+    E.val.assign((size_t)std::max<int64_t>(off, 1), 0.0);
+    for (size_t j = 0; j < ns; ++j) {
+        const int64_t p0 = rp[shrt[j]], base = E.chunk[j / 32] + (int64_t)(j % 32);
+        for (int64_t e = 0; e < E.len[j]; ++e) {
+            E.col[(size_t)(base + 32 * e)] = col[(size_t)(p0 + e)];
+            E.val[(size_t)(base + 32 * e)] = val[(size_t)(p0 + e)];
+        }
+    }
+}
+
+// The pre-pass of every pair over all slots at once: control-variate Taylor
+// terms and features (two row passes), prediction, coefficients (one row pass;
+// with their exponent and scaled FP32 copy for FP32 integrals); or the scaled
+// FP32 copy of v.
 cudaError_t prepass(mcx_cvbatch *b, cudaStream_t st) {
     const int64_t S = b->slots;
     const unsigned nb = (unsigned)std::max<int64_t>(1, std::min<int64_t>((S + 255) / 256, 152 * 8));
     if (cv_mode(b)) {
-        cudaError_t e = cv_prepare_rows(S, b->srp, b->scol, b->sval, b->v, 0.0, b->t_row, b->work, b->taylor, b->feat,
-                                        st);
+        const CvRowSchedule sch{b->sorder, b->scnt, nullptr};
+        const CvSell ell{b->ell_col, b->ell_val, b->ell_chunk, b->ell_len};
+        double2 *rec = reinterpret_cast<double2 *>(b->work);
+        cudaError_t e = cv_taylor_rows(S, b->srp, b->scol, b->sval, b->v, 0.0, b->t_row, sch, &ell, rec,
+                                       b->taylor + 3 * S, b->taylor, b->feat, false, st);
         if (e != cudaSuccess) return e;
         if (b->control == MCX_CV_LEARNED) {
             const mcx_status rc = mcx_mlp_predict(b->net, S, b->feat, b->y, st);
             if (rc != MCX_OK) return rc == MCX_E_OOM ? cudaErrorMemoryAllocation : cudaErrorUnknown;
         }
-        if ((e = cv_coefficients_rows(S, b->srp, b->scol, b->sval, b->taylor,
-                                      b->control == MCX_CV_LEARNED ? b->y : nullptr, 0.0, b->t_row, b->work, b->ab,
-                                      b->h, st)) != cudaSuccess)
+        if ((e = cv_cubic_rows(S, b->srp, b->scol, b->sval, b->taylor, b->control == MCX_CV_LEARNED ? b->y : nullptr,
+                               0.0, b->t_row, sch, &ell, rec, b->ab, b->h, st)) != cudaSuccess)
             return e;
         if ((e = cudaMemsetAsync(b->vexp, 0, sizeof(uint32_t) * b->n_pair, st)) != cudaSuccess) return e;
         if (b->precision == MCX_FP32) {  // the coefficients' exponent per pair and their scaled FP32 copy
@@ -929,6 +1016,8 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
     }
     rp[N] = w;
     if (cv) srp[slots] = sw;
+    HostEll ell;
+    if (cv) build_ell(slots, srp, scol, sval, ell);
     b->n_pair = (int32_t)b->pair_host.size();
     mcx_status rc = mcx_plan_create(N, w, rp.data(), col.data(), val.data(), MCX_PLAN_HOST_INPUT, stream, &b->plan);
     if (rc != MCX_OK) {
@@ -960,8 +1049,20 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
             if ((e = dev_malloc(reinterpret_cast<void **>(&b->y), sizeof(float) * sl)) != cudaSuccess) break;
             if ((e = dev_malloc(reinterpret_cast<void **>(&b->ab), sizeof(double2) * sl)) != cudaSuccess) break;
             if ((e = dev_malloc(reinterpret_cast<void **>(&b->h), sizeof(double) * sl)) != cudaSuccess) break;
-            if ((e = dev_malloc(reinterpret_cast<void **>(&b->work), sizeof(double) * (3 * sl + 64))) != cudaSuccess)
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->work), sizeof(double2) * sl)) != cudaSuccess) break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->sorder), sizeof(int32_t) * sl)) != cudaSuccess) break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->scnt), sizeof(uint32_t) * CV_ROW_CNT)) != cudaSuccess)
                 break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->ell_col), sizeof(int32_t) * ell.col.size())) !=
+                cudaSuccess)
+                break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->ell_val), sizeof(double) * ell.val.size())) !=
+                cudaSuccess)
+                break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->ell_chunk), sizeof(int64_t) * ell.chunk.size())) !=
+                cudaSuccess)
+                break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->ell_len), ell.len.size())) != cudaSuccess) break;
             if (precision == MCX_FP32 &&
                 (e = dev_malloc(reinterpret_cast<void **>(&b->abf), sizeof(float2) * sl)) != cudaSuccess)
                 break;
@@ -974,6 +1075,13 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
             cudaMemcpyAsync(b->scol, scol.data(), sizeof(int32_t) * scol.size(), cudaMemcpyHostToDevice, st);
             cudaMemcpyAsync(b->sval, sval.data(), sizeof(double) * sval.size(), cudaMemcpyHostToDevice, st);
             cudaMemcpyAsync(b->t_row, trow.data(), sizeof(double) * sl, cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(b->sorder, ell.order.data(), sizeof(int32_t) * ell.order.size(), cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(b->scnt, ell.cnt, sizeof(ell.cnt), cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(b->ell_col, ell.col.data(), sizeof(int32_t) * ell.col.size(), cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(b->ell_val, ell.val.data(), sizeof(double) * ell.val.size(), cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(b->ell_chunk, ell.chunk.data(), sizeof(int64_t) * ell.chunk.size(),
+                            cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(b->ell_len, ell.len.data(), ell.len.size(), cudaMemcpyHostToDevice, st);
         }
         cudaMemcpyAsync(b->slot_pair, spair.data(), sizeof(int32_t) * sl, cudaMemcpyHostToDevice, st);
         if ((e = cudaMemcpyAsync(b->v, vall.data(), sizeof(double) * sl, cudaMemcpyHostToDevice, st)) != cudaSuccess)

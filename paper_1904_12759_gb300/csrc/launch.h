@@ -91,13 +91,41 @@ cudaError_t launch_trace(mcx_plan *plan, double t, int mode, int nsteps, int32_t
 // The control variate's pre-pass over rows 0..n-1 of one CSR (cv.cu): Taylor
 // terms and features (as mcx_cv_prepare), coefficients into ab [n] and h [n]
 // (as mcx_cv_coefficients); t_row, when not NULL, gives each row its own
-// horizon, so that the rows of many problems are prepared in one pass.
+// horizon, so that the rows of many problems are prepared in one pass.  The
+// batched form builds its row schedule and sliced ELL copy once, then per run
+// calls cv_taylor_rows without the third Taylor term and cv_cubic_rows, which
+// forms A^3 v and A c3 in one pass (bit-identical to the single-problem calls).
 cudaError_t cv_prepare_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
                             const double *v, double t, const double *t_row, double *work, double *taylor,
                             float *features, cudaStream_t st);
 cudaError_t cv_coefficients_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
                                  const double *taylor, const float *y, double t, const double *t_row, double *work,
                                  double2 *ab, double *h, cudaStream_t st);
+// Row schedule of the control variate's row passes (cv.cu): order [n] int32,
+// cnt [CV_ROW_CNT] and hist [ceil(n / CV_ROW_WINDOW) + 1] uint32, device memory.
+constexpr int CV_ROW_CNT = 8;
+constexpr int CV_ROW_WINDOW = 256;
+struct CvRowSchedule {
+    int32_t *order;
+    uint32_t *cnt;
+    uint32_t *hist;
+};
+// Sliced ELL copy of a schedule's short rows: chunk k holds the short rows
+// 32k .. 32k + 31 of the schedule, entry e of the chunk's row l at
+// chunk[k] + 32 e + l of col / val; len [short rows] their lengths.
+struct CvSell {
+    const int32_t *col;
+    const double *val;
+    const int64_t *chunk;
+    const uint8_t *len;
+};
+cudaError_t cv_taylor_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                           const double *v, double t, const double *t_row, const CvRowSchedule &s, const CvSell *ell,
+                           double2 *g, double *lam, double *taylor, float *features, bool third, cudaStream_t st);
+cudaError_t cv_cubic_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
+                          const double *taylor, const float *y, double t, const double *t_row,
+                          const CvRowSchedule &s, const CvSell *ell, double2 *q, double2 *ab, double *h,
+                          cudaStream_t st);
 cudaError_t run_power_iteration(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
                                 int32_t max_iters, double tol, double *work, double *lambda, int32_t *iters,
                                 cudaStream_t st);
