@@ -28,6 +28,7 @@
 
 #include "cvmath.cuh"
 #include "dfloat.cuh"
+#include "expd.cuh"
 #include "launch.h"
 #include "rows.cuh"
 #include "tc.cuh"
@@ -765,16 +766,18 @@ __global__ void k_feature_stats(int64_t n, const float *__restrict__ F, float *m
 }
 
 // xhat = T2 e^y; c3 = (xhat - T2)/t^3 -> coef: h [n], then (a, b) pairs [n]; c3 staged in b's slot
-// h = xhat = T2 e^y and c3 = (xhat - T2)/t^3; c3 into c3[i], or with A^2 v into
-// the record q[i] = (A^2 v_i, c3_i) of the fused third pass.
+// h = xhat = T2 e^y and c3 = (xhat - T2) / t^3, formed as (xhat - T2) times the
+// FP64 1/(t*t*t) (t3inv); c3 into c3[i], or with A^2 v into the record
+// q[i] = (A^2 v_i, c3_i) of the fused third pass.  t_row / t3inv_row: per-row
+// horizons (both, or neither: t_all / t3inv_all).
 __global__ void k_cv_xhat(int64_t n, const double *__restrict__ T, const float *__restrict__ y, double t_all,
-                          const double *__restrict__ t_row, double *__restrict__ h, double *__restrict__ c3,
-                          double2 *__restrict__ q) {
+                          double t3inv_all, const double *__restrict__ t_row, const double *__restrict__ t3inv_row,
+                          double *__restrict__ h, double *__restrict__ c3, double2 *__restrict__ q) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double t = t_row ? t_row[i] : t_all;
         const double T2 = T[i] + t * T[n + i] + t * t * T[2 * n + i] / 2.0;
-        const double xh = T2 * exp((double)(y ? y[i] : 0.0f));
-        const double c = (xh - T2) / (t * t * t);
+        const double xh = T2 * exp_of_f32(y ? y[i] : 0.0f);
+        const double c = (xh - T2) * (t3inv_row ? t3inv_row[i] : t3inv_all);
         h[i] = xh;
         if (q) q[i] = make_double2(T[2 * n + i], c);
         else c3[i] = c;
@@ -1115,31 +1118,30 @@ cudaError_t cv_taylor_rows(int64_t n, const int64_t *row_ptr, const int32_t *col
     return cudaGetLastError();
 }
 
-// mcx_cv_prepare on rows 0..n-1; work: float64 [3n + 64], 16-byte aligned.
+// mcx_cv_prepare; work: float64 [3n + 64], 16-byte aligned.
 cudaError_t cv_prepare_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
-                            const double *v, double t, const double *t_row, double *work, double *taylor,
-                            float *features, cudaStream_t st) {
+                            const double *v, double t, double *work, double *taylor, float *features,
+                            cudaStream_t st) {
     double2 *g = reinterpret_cast<double2 *>(work);  // 2n doubles
     CvRowSchedule s;
     carve_schedule(n, work + 2 * n, s);
     const cudaError_t e = build_schedule(n, row_ptr, s, st);
     if (e != cudaSuccess) return e;
-    return cv_taylor_rows(n, row_ptr, col, val, v, t, t_row, s, nullptr, g, taylor + 3 * n, taylor, features, true,
-                          st);
+    return cv_taylor_rows(n, row_ptr, col, val, v, t, nullptr, s, nullptr, g, taylor + 3 * n, taylor, features,
+                          true, st);
 }
 
-// Control-variate coefficients of rows 0..n-1 (see mcx_cv_coefficients) into
-// ab [n] and h [n]; t_row as in cv_taylor_rows.  work: float64 [3n + 64].
+// mcx_cv_coefficients into ab [n] and h [n]; work: float64 [3n + 64].
 cudaError_t cv_coefficients_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
-                                 const double *taylor, const float *y, double t, const double *t_row, double *work,
-                                 double2 *ab, double *h, cudaStream_t st) {
+                                 const double *taylor, const float *y, double t, double *work, double2 *ab,
+                                 double *h, cudaStream_t st) {
     const unsigned nb = blocks_for(n, 256);
     double *c3 = work, *Ac3 = work + n;
     CvRowSchedule s;
     carve_schedule(n, work + 2 * n, s);
     const cudaError_t e = build_schedule(n, row_ptr, s, st);
     if (e != cudaSuccess) return e;
-    k_cv_xhat<<<nb, 256, 0, st>>>(n, taylor, y, t, t_row, h, c3, nullptr);
+    k_cv_xhat<<<nb, 256, 0, st>>>(n, taylor, y, t, 1.0 / (t * t * t), nullptr, nullptr, h, c3, nullptr);
     run_pass(row_ptr, col, val, s, nullptr, PassSpmv{c3, Ac3}, st);
     k_cv_ab<<<nb, 256, 0, st>>>(n, taylor, c3, Ac3, ab);
     return cudaGetLastError();
@@ -1149,10 +1151,10 @@ cudaError_t cv_coefficients_rows(int64_t n, const int64_t *row_ptr, const int32_
 // in one row pass over the records (A^2 v_c, c3_c) (q: [n], 16-byte aligned);
 // bit-identical to cv_prepare_rows' A^3 v followed by cv_coefficients_rows.
 cudaError_t cv_cubic_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
-                          const double *taylor, const float *y, double t, const double *t_row,
+                          const double *taylor, const float *y, const double *t_row, const double *t3inv_row,
                           const CvRowSchedule &s, const CvSell *ell, double2 *q, double2 *ab, double *h,
                           cudaStream_t st) {
-    k_cv_xhat<<<blocks_for(n, 256), 256, 0, st>>>(n, taylor, y, t, t_row, h, nullptr, q);
+    k_cv_xhat<<<blocks_for(n, 256), 256, 0, st>>>(n, taylor, y, 0.0, 0.0, t_row, t3inv_row, h, nullptr, q);
     run_pass(row_ptr, col, val, s, ell, PassCubic{q, ab}, st);
     return cudaGetLastError();
 }
@@ -1211,7 +1213,7 @@ mcx_status mcx_cv_prepare(int64_t n, const int64_t *row_ptr, const int32_t *col,
     NvtxRange nvtx("mcx_cv_prepare");
     if (n < 1 || !row_ptr || !col || !val || !v || !work || !taylor || !features || !(t > 0.0)) return MCX_E_INVALID;
     if (reinterpret_cast<uintptr_t>(work) & 15u) return MCX_E_INVALID;  // 16-byte records
-    return cv_status(cv_prepare_rows(n, row_ptr, col, val, v, t, nullptr, work, taylor, features,
+    return cv_status(cv_prepare_rows(n, row_ptr, col, val, v, t, work, taylor, features,
                                      static_cast<cudaStream_t>(stream)));
 }
 
@@ -1426,7 +1428,7 @@ mcx_status mcx_cv_coefficients(int64_t n, const int64_t *row_ptr, const int32_t 
     if (n < 1 || !row_ptr || !col || !val || !taylor || !work || !coef || !(t > 0.0)) return MCX_E_INVALID;
     if (reinterpret_cast<uintptr_t>(coef) % 16 != 0) return MCX_E_INVALID;
     // layout: (a, b) pairs at offset 0 (16-byte aligned with the buffer), then h
-    return cv_status(cv_coefficients_rows(n, row_ptr, col, val, taylor, y, t, nullptr, work,
+    return cv_status(cv_coefficients_rows(n, row_ptr, col, val, taylor, y, t, work,
                                           reinterpret_cast<double2 *>(coef), coef + 2 * n,
                                           static_cast<cudaStream_t>(stream)));
 }

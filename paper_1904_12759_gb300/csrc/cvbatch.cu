@@ -490,7 +490,7 @@ struct mcx_cvbatch {
     double *ell_val = nullptr;
     int64_t *ell_chunk = nullptr;
     uint8_t *ell_len = nullptr;
-    double *t_row = nullptr;    // [slots] horizon of each slot's pair
+    double *t_row = nullptr;    // [2 slots] horizon t of each slot's pair, then 1/(t*t*t)
     int32_t *slot_pair = nullptr;  // [slots] pair of each slot
     // per-slot arrays
     double *v = nullptr;      // [slots]
@@ -753,7 +753,7 @@ cudaError_t prepass(mcx_cvbatch *b, cudaStream_t st) {
             if (rc != MCX_OK) return rc == MCX_E_OOM ? cudaErrorMemoryAllocation : cudaErrorUnknown;
         }
         if ((e = cv_cubic_rows(S, b->srp, b->scol, b->sval, b->taylor, b->control == MCX_CV_LEARNED ? b->y : nullptr,
-                               0.0, b->t_row, sch, &ell, rec, b->ab, b->h, st)) != cudaSuccess)
+                               b->t_row, b->t_row + S, sch, &ell, rec, b->ab, b->h, st)) != cudaSuccess)
             return e;
         if ((e = cudaMemsetAsync(b->vexp, 0, sizeof(uint32_t) * b->n_pair, st)) != cudaSuccess) return e;
         if (b->precision == MCX_FP32) {  // the coefficients' exponent per pair and their scaled FP32 copy
@@ -958,7 +958,7 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
     std::vector<double> val((size_t)std::max<int64_t>(nnz, 1));
     std::vector<double> vall((size_t)std::max<int64_t>(slots, 1));
     std::vector<int32_t> spair((size_t)std::max<int64_t>(slots, 1));
-    std::vector<double> trow((size_t)std::max<int64_t>(slots, 1));
+    std::vector<double> trow((size_t)std::max<int64_t>(2 * slots, 1));
     std::vector<int64_t> srp;
     std::vector<int32_t> scol;
     std::vector<double> sval;
@@ -999,6 +999,7 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
             for (int64_t j = 0; j < p.n; ++j) {
                 spair[slot + j] = (int32_t)b->pair_host.size();
                 trow[slot + j] = p.t[r];
+                trow[slots + slot + j] = 1.0 / (p.t[r] * p.t[r] * p.t[r]);
             }
             if (cv)
                 for (int64_t j = 0; j < p.n; ++j) {  // this pair's copy of the rows, columns in its slots
@@ -1043,7 +1044,8 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
                 break;
             if ((e = dev_malloc(reinterpret_cast<void **>(&b->sval), sizeof(double) * sval.size())) != cudaSuccess)
                 break;
-            if ((e = dev_malloc(reinterpret_cast<void **>(&b->t_row), sizeof(double) * sl)) != cudaSuccess) break;
+            if ((e = dev_malloc(reinterpret_cast<void **>(&b->t_row), sizeof(double) * trow.size())) != cudaSuccess)
+                break;
             if ((e = dev_malloc(reinterpret_cast<void **>(&b->taylor), 4 * sizeof(double) * sl)) != cudaSuccess) break;
             if ((e = dev_malloc(reinterpret_cast<void **>(&b->feat), 5 * sizeof(float) * sl)) != cudaSuccess) break;
             if ((e = dev_malloc(reinterpret_cast<void **>(&b->y), sizeof(float) * sl)) != cudaSuccess) break;
@@ -1074,7 +1076,7 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
             cudaMemcpyAsync(b->srp, srp.data(), sizeof(int64_t) * srp.size(), cudaMemcpyHostToDevice, st);
             cudaMemcpyAsync(b->scol, scol.data(), sizeof(int32_t) * scol.size(), cudaMemcpyHostToDevice, st);
             cudaMemcpyAsync(b->sval, sval.data(), sizeof(double) * sval.size(), cudaMemcpyHostToDevice, st);
-            cudaMemcpyAsync(b->t_row, trow.data(), sizeof(double) * sl, cudaMemcpyHostToDevice, st);
+            cudaMemcpyAsync(b->t_row, trow.data(), sizeof(double) * trow.size(), cudaMemcpyHostToDevice, st);
             cudaMemcpyAsync(b->sorder, ell.order.data(), sizeof(int32_t) * ell.order.size(), cudaMemcpyHostToDevice, st);
             cudaMemcpyAsync(b->scnt, ell.cnt, sizeof(ell.cnt), cudaMemcpyHostToDevice, st);
             cudaMemcpyAsync(b->ell_col, ell.col.data(), sizeof(int32_t) * ell.col.size(), cudaMemcpyHostToDevice, st);

@@ -88,19 +88,13 @@ cudaError_t launch_trace_forward(mcx_plan *plan, const double *v, double t, int 
 cudaError_t launch_trace(mcx_plan *plan, double t, int mode, int nsteps, int32_t entry, uint64_t seed,
                          uint64_t first_path, uint32_t count, int precision, int32_t *end, uint32_t *njumps,
                          uint64_t *hash, double *logw, cudaStream_t st);
-// The control variate's pre-pass over rows 0..n-1 of one CSR (cv.cu): Taylor
-// terms and features (as mcx_cv_prepare), coefficients into ab [n] and h [n]
-// (as mcx_cv_coefficients); t_row, when not NULL, gives each row its own
-// horizon, so that the rows of many problems are prepared in one pass.  The
-// batched form builds its row schedule and sliced ELL copy once, then per run
-// calls cv_taylor_rows without the third Taylor term and cv_cubic_rows, which
-// forms A^3 v and A c3 in one pass (bit-identical to the single-problem calls).
-cudaError_t cv_prepare_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
-                            const double *v, double t, const double *t_row, double *work, double *taylor,
-                            float *features, cudaStream_t st);
-cudaError_t cv_coefficients_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
-                                 const double *taylor, const float *y, double t, const double *t_row, double *work,
-                                 double2 *ab, double *h, cudaStream_t st);
+// The batched control variate's pre-pass over the rows of its slot CSR (cv.cu):
+// t_row gives each row its own horizon and t3inv_row the FP64 1/(t*t*t) of it,
+// so that the rows of many problems are prepared at once.  The batched form
+// builds its row schedule and sliced ELL copy once, then per run calls
+// cv_taylor_rows without the third Taylor term and cv_cubic_rows, which forms
+// A^3 v and A c3 in one pass; both give the bits of mcx_cv_prepare and
+// mcx_cv_coefficients on each problem alone.
 // Row schedule of the control variate's row passes (cv.cu): order [n] int32,
 // cnt [CV_ROW_CNT] and hist [ceil(n / CV_ROW_WINDOW) + 1] uint32, device memory.
 constexpr int CV_ROW_CNT = 8;
@@ -123,7 +117,7 @@ cudaError_t cv_taylor_rows(int64_t n, const int64_t *row_ptr, const int32_t *col
                            const double *v, double t, const double *t_row, const CvRowSchedule &s, const CvSell *ell,
                            double2 *g, double *lam, double *taylor, float *features, bool third, cudaStream_t st);
 cudaError_t cv_cubic_rows(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,
-                          const double *taylor, const float *y, double t, const double *t_row,
+                          const double *taylor, const float *y, const double *t_row, const double *t3inv_row,
                           const CvRowSchedule &s, const CvSell *ell, double2 *q, double2 *ab, double *h,
                           cudaStream_t st);
 cudaError_t run_power_iteration(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *val,

@@ -92,6 +92,34 @@ def test_prepare_matches_oracle(mcx, scale):
     assert np.allclose(F.cpu().numpy(), oF.astype(np.float32), rtol=2e-6, atol=1e-6 * scale)
 
 
+def test_coefficient_exponential_within_two_ulp(mcx):
+    """xhat = T2 e^y with T2 = 1 (v = 1, Av = A^2 v = 0): the coefficients' FP64
+    exponential of the network's FP32 output against numpy's, within 2 units in
+    the last place, over [-30, 30], the reduction's edges (multiples of ln(2)/64
+    and halfway between), and the range ends (|y| >= 700 takes the library's
+    exponential; overflow to inf, underflow to 0)."""
+    rng = np.random.default_rng(4)
+    k = np.arange(-40, 41)
+    edges = np.concatenate([k * math.log(2) / 64, (k + 0.5) * math.log(2) / 64])
+    special = [0.0, 1e-30, -1e-30, 2.0 ** -20, -(2.0 ** -20), 88.0, -88.0, 699.9, -699.9, 700.0, -700.0, 705.0,
+               -705.0, 709.7, 710.0, -708.0, -760.0, 1000.0]
+    y = np.concatenate([rng.uniform(-30, 30, 200000), edges, special]).astype(np.float32)
+    n = y.size
+    taylor = torch.zeros(4 * n, dtype=torch.float64, device="cuda")
+    taylor[:n] = 1.0
+    rp = torch.arange(n + 1, dtype=torch.int64, device="cuda")
+    col = torch.arange(n, dtype=torch.int32, device="cuda")
+    val = torch.ones(n, dtype=torch.float64, device="cuda")
+    coef = mcx.cv_coefficients(rp, col, val, taylor, torch.as_tensor(y).cuda(), 0.5)
+    h = coef[2 * n:].cpu().numpy()
+    with np.errstate(over="ignore"):
+        e = np.exp(y.astype(np.float64))
+    fin = np.isfinite(e) & (e > 0)
+    assert np.all(np.abs(h[fin] - e[fin]) <= 2 * np.spacing(e[fin])), \
+        np.max(np.abs(h[fin] - e[fin]) / np.spacing(e[fin]))
+    assert np.all(h[~fin] == e[~fin])
+
+
 def test_network_forward_and_gradient_match_oracle(mcx):
     rng = np.random.default_rng(2)
     X = rng.normal(size=(777, 5)).astype(np.float32)  # ragged: not a multiple of 64
