@@ -41,6 +41,7 @@
 
 #include "accum.cuh"
 #include "cvmath.cuh"
+#include "expd.cuh"
 #include "launch.h"
 #include "rows.cuh"
 #include "tune_cache.h"
@@ -66,7 +67,7 @@ struct CvbPair {
     float t32;
     uint32_t cpe;        // chunks per entry; 0: lane layout (paths <= LANE_MODE_MAX_PATHS)
     int32_t problem, rhs;
-    int32_t pad[2];
+    double inv_m, inv_m1;  // 1/paths, 1/(paths - 1) (0 for one path)
 };
 
 struct CvbItem {
@@ -108,9 +109,14 @@ __global__ void k_pair_exponent(int64_t slots, int per, const double *__restrict
         int32_t k = -1;
         if (s < slots) {
             k = slot_pair[s];
-            for (int q = 0; q < per; ++q) {
-                const double y = fabs(x[s * per + q]);
-                if (y > 0.0 && y <= 1.7976931348623157e308) e = max(e, (uint32_t)(ilogb(y) + (int)VEXP_BIAS));
+            for (int q = 0; q < per; ++q) {  // ilogb of finite nonzero values, from the bits
+                const unsigned long long y =
+                    (unsigned long long)__double_as_longlong(x[s * per + q]) & 0x7fffffffffffffffull;
+                if (y != 0ull && y < 0x7ff0000000000000ull) {
+                    const int E = (int)(y >> 52);
+                    const int lg = E ? E - 1023 : (63 - __clzll((long long)y)) - 1074;
+                    e = max(e, (uint32_t)(lg + (int)VEXP_BIAS));
+                }
             }
         }
         const int32_t k0 = __shfl_sync(0xffffffffu, k, 0);
@@ -146,7 +152,12 @@ __global__ void k_pair_coef_f32(int64_t slots, const double2 *__restrict__ ab, c
         const uint32_t eb = vexp[slot_pair[s]];
         const int k = eb ? (int)eb - (int)VEXP_BIAS : 0;
         const double2 c = ab[s];
-        out[s] = make_float2(__double2float_rn(ldexp(c.x, -k)), __double2float_rn(ldexp(c.y, -k)));
+        if (k >= -1022 && k <= 1022) {  // 2^-k a normal number: one exact product each
+            const double p2 = __longlong_as_double((long long)(1023 - k) << 52);
+            out[s] = make_float2(__double2float_rn(__dmul_rn(c.x, p2)), __double2float_rn(__dmul_rn(c.y, p2)));
+        } else {
+            out[s] = make_float2(__double2float_rn(ldexp(c.x, -k)), __double2float_rn(ldexp(c.y, -k)));
+        }
     }
 }
 
@@ -234,6 +245,11 @@ __device__ __forceinline__ bool cv_event(Walker<false> &w, const WalkParams &a, 
     return fin;
 }
 
+// x finite, by its exponent bits (integer pipe)
+__device__ __forceinline__ bool finite_bits(double x) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
 // The persistent walk.  CV: control variate (FP32 paths; F64: residual
 // integrals in FP64); plain: F64 selects the FP64 path version.
 template <bool CV, bool F64, bool WEIGHTED, bool STAGED>
@@ -296,7 +312,26 @@ __global__ void __launch_bounds__(WALK_THREADS, CV ? CVB_MIN_BLOCKS_CV : CVB_MIN
                 paths_done += pr.paths;
                 const double M = (double)pr.paths;
                 double S1, S2, Mw;
-                if constexpr (CV) {
+                if constexpr (CV && !F64) {
+                    // FP32 integrals, one entry per lane: the few FP64 operations of the
+                    // finish (GB300 runs FP64 slowly) -- e^Mw of the FP32 maximum by the
+                    // table-driven exponential, the divisions by M as products with the
+                    // pair's reciprocals, the standard error's root in FP32 where its
+                    // argument is well inside the FP32 range (relative error 2^-23)
+                    cl.result(S1, S2, Mw);
+                    const float mf = (float)Mw;
+                    const double scale = (mf == -INFINITY ? 0.0 : exp_of_f32(mf)) * up;
+                    const double mu = S1 * pr.inv_m;
+                    double var = (S2 - S1 * mu) * pr.inv_m1;
+                    if (!(var > 0.0)) var = 0.0;
+                    const double q = var * pr.inv_m;
+                    const double mv = b.h[pr.slot + e] + scale * mu;
+                    const double se = scale * ((q > 1e-30 && q < 1e30) ? (double)__fsqrt_rn((float)q)
+                                                                       : (q > 0.0 ? sqrt(q) : 0.0));
+                    b.mean[pr.slot + e] = mv;
+                    b.sem[pr.slot + e] = se;
+                    if (!finite_bits(mv) || !finite_bits(se)) atomicOr(a.status, ST_OVERFLOW);
+                } else if constexpr (CV) {
                     cl.result(S1, S2, Mw);
                     const double scale = ((Mw == -INFINITY) ? 0.0 : exp(Mw)) * up;
                     const double mu = S1 / M;
@@ -558,6 +593,8 @@ void layout_pairs(mcx_cvbatch *b) {
     int64_t part = 0;
     for (auto &pr : b->pair_host) {
         pr.paths = b->paths[pr.problem];
+        pr.inv_m = 1.0 / (double)pr.paths;
+        pr.inv_m1 = pr.paths > 1 ? 1.0 / (double)(pr.paths - 1) : 0.0;
         if (pr.paths <= LANE_MODE_MAX_PATHS) {
             pr.cpe = 0;
             pr.chunk = pr.paths;
