@@ -19,6 +19,7 @@
 // full-batch gradients and Adam training (block partial gradients reduced in a
 // fixed order: deterministic); the coefficient builder; and the CV walker (the
 // FP32 path of the backward walker, with the residual integral in FP32 or FP64).
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include <algorithm>
@@ -76,10 +77,11 @@ constexpr int HS = HID + 1;
 // gather per entry.  Two layouts of the short rows:
 //  * CSR (mcx_cv_prepare, mcx_cv_coefficients): short rows in their natural
 //    order, so a warp's 32 rows are adjacent in memory;
-//  * sliced ELL (the batched form, built once at creation): short rows sorted
-//    by length within windows of CV_ROW_WINDOW rows and stored in chunks of 32
-//    rows, entry k of the chunk's rows contiguous, so that a warp's loads of
-//    the matrix are coalesced and its lanes run rows of nearly equal length.
+//  * sliced ELL (the batched form, built once at creation): the same order,
+//    stored in chunks of 32 rows with entry k of the chunk's rows contiguous,
+//    so that a warp's loads of the matrix are coalesced too.  (Sorting rows by
+//    length within windows, so that a warp's lanes run rows of nearly equal
+//    length, scatters the per-row reads and writes; measured slower.)
 // GB300 runs FP64 at a small fraction of its FP32 rate: the sums' multiply-adds
 // stay FP64, but sign tests, the rates and the features run on the integer and
 // FP32 pipes (double-float).  A row operation Op supplies
@@ -495,9 +497,11 @@ __device__ void load_params(const float *__restrict__ p, float *s) {
     }
 }
 
-__device__ __forceinline__ void standardise(const float *__restrict__ f, const MLPView &m, float x[NF]) {
+// x = (f - mu) * (1/sd), isd = 1/sd rounded to FP32 (the same in training and inference)
+__device__ __forceinline__ void standardise(const float *__restrict__ f, const float *mu, const float *isd,
+                                           float x[NF]) {
 #pragma unroll
-    for (int q = 0; q < NF; ++q) x[q] = (f[q] - m.mu[q]) / m.sd[q];
+    for (int q = 0; q < NF; ++q) x[q] = __fmul_rn(__fsub_rn(f[q], mu[q]), isd[q]);
 }
 
 // ---------------------------------------------------------------------------
@@ -530,8 +534,11 @@ __global__ void __launch_bounds__(TC_ROWS, 7) k_mlp_predict_tc(int64_t n, const 
                                                                uint32_t wait_polls) {
     __shared__ __align__(1024) uint8_t sA[TC_ROWS * HID * 2];  // 16 KB
     __shared__ __align__(1024) uint8_t sB[HID * HID * 2];      // 8 KB
-    __shared__ float sW1[NF * HID], sb1[HID], sb2[HID], sw3[HID];
-    __shared__ float sb3;
+    __shared__ __align__(16) float sW1[NF * HID];
+    __shared__ __align__(16) float sb1[HID];
+    __shared__ __align__(16) float sb2[HID];
+    __shared__ __align__(16) float sw3[HID];
+    __shared__ float sb3, smu[NF], sisd[NF];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -544,6 +551,10 @@ __global__ void __launch_bounds__(TC_ROWS, 7) k_mlp_predict_tc(int64_t n, const 
         sb1[tid] = m.params[P_B1 + tid];
         sb2[tid] = m.params[P_B2 + tid];
         sw3[tid] = bf16_round(m.params[P_W3 + tid]);
+    }
+    if (tid < NF) {
+        smu[tid] = m.mu[tid];
+        sisd[tid] = __fdiv_rn(1.0f, m.sd[tid]);
     }
     if (tid == 0) {
         sb3 = m.params[P_B3];
@@ -562,20 +573,32 @@ __global__ void __launch_bounds__(TC_ROWS, 7) k_mlp_predict_tc(int64_t n, const 
     for (int64_t tile = blockIdx.x; tile * TC_ROWS < n; tile += gridDim.x) {
         const int64_t i = tile * TC_ROWS + tid;
         float x[NF] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        if (i < n) standardise(F + i * NF, m, x);
-        // first hidden layer, BF16, 16 bytes (8 K elements) per store
+        if (i < n) standardise(F + i * NF, smu, sisd, x);
+        // first hidden layer, BF16 (round to nearest even), 16 bytes (8 K elements) per
+        // store; the weights and biases read as 16-byte vectors
 #pragma unroll
         for (int kc = 0; kc < HID; kc += 8) {
+            float a[8];
+            *reinterpret_cast<float4 *>(a) = *reinterpret_cast<const float4 *>(sb1 + kc);
+            *reinterpret_cast<float4 *>(a + 4) = *reinterpret_cast<const float4 *>(sb1 + kc + 4);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const float4 w0 = *reinterpret_cast<const float4 *>(sW1 + f * HID + kc);
+                const float4 w1 = *reinterpret_cast<const float4 *>(sW1 + f * HID + kc + 4);
+                a[0] = fmaf(x[f], w0.x, a[0]);
+                a[1] = fmaf(x[f], w0.y, a[1]);
+                a[2] = fmaf(x[f], w0.z, a[2]);
+                a[3] = fmaf(x[f], w0.w, a[3]);
+                a[4] = fmaf(x[f], w1.x, a[4]);
+                a[5] = fmaf(x[f], w1.y, a[5]);
+                a[6] = fmaf(x[f], w1.z, a[6]);
+                a[7] = fmaf(x[f], w1.w, a[7]);
+            }
             uint32_t pk[4];
 #pragma unroll
             for (int q = 0; q < 8; q += 2) {
-                float a0 = sb1[kc + q], a1 = sb1[kc + q + 1];
-#pragma unroll
-                for (int f = 0; f < NF; ++f) {
-                    a0 = fmaf(x[f], sW1[f * HID + kc + q], a0);
-                    a1 = fmaf(x[f], sW1[f * HID + kc + q + 1], a1);
-                }
-                pk[q >> 1] = bf16_bits(fmaxf(a0, 0.0f)) | (bf16_bits(fmaxf(a1, 0.0f)) << 16);
+                const __nv_bfloat162 h2 = __floats2bfloat162_rn(fmaxf(a[q], 0.0f), fmaxf(a[q + 1], 0.0f));
+                pk[q >> 1] = *reinterpret_cast<const uint32_t *>(&h2);
             }
             *reinterpret_cast<uint4 *>(sA + tc_off((uint32_t)tid, (uint32_t)kc)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
@@ -606,8 +629,14 @@ __global__ void __launch_bounds__(TC_ROWS, 7) k_mlp_predict_tc(int64_t n, const 
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + c, v);
             tc::tmem_ld_wait();
+            float b2[16], w3[16];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) yv = fmaf(fmaxf(v[k] + sb2[c + k], 0.0f), sw3[c + k], yv);
+            for (int k = 0; k < 16; k += 4) {
+                *reinterpret_cast<float4 *>(b2 + k) = *reinterpret_cast<const float4 *>(sb2 + c + k);
+                *reinterpret_cast<float4 *>(w3 + k) = *reinterpret_cast<const float4 *>(sw3 + c + k);
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k) yv = fmaf(fmaxf(v[k] + b2[k], 0.0f), w3[k], yv);
         }
         if (i < n) y[i] = yv;
         tc::fence_before_sync();
@@ -642,7 +671,13 @@ __global__ void __launch_bounds__(GRAD_SAMPLES) k_mlp_grad(int64_t n, const floa
     float target = 0.0f;
     if (valid) {
         const int64_t row = idx ? idx[smp] : smp;
-        standardise(F + row * NF, m, x);
+        float mu[NF], isd[NF];
+#pragma unroll
+        for (int q = 0; q < NF; ++q) {
+            mu[q] = m.mu[q];
+            isd[q] = __fdiv_rn(1.0f, m.sd[q]);
+        }
+        standardise(F + row * NF, mu, isd, x);
         target = tgt[row];
     }
 #pragma unroll

@@ -711,9 +711,10 @@ cudaError_t apply_layout(mcx_cvbatch *b, cudaStream_t st) {
 
 // The row schedule of the pre-pass's CSR and the sliced ELL copy of its short
 // rows (see CvSell), built on the host: huge rows, long rows, then the short
-// rows window by window (CV_ROW_WINDOW rows), each window's sorted by
-// decreasing length (stable), so that a chunk's 32 rows have nearly equal
-// lengths.  Padding slots of a chunk are zero and never read.
+// rows in natural order, so that a chunk's 32 rows are neighbours and their
+// per-row reads and writes fall in few sectors (sorting rows by length within
+// windows of 64..256 rows, to keep every lane busy, measured slower on GB300).
+// Padding slots of a chunk are zero and never read.
 struct HostEll {
     std::vector<int32_t> order, col;
     std::vector<double> val;
@@ -725,19 +726,11 @@ struct HostEll {
 void build_ell(int64_t n, const std::vector<int64_t> &rp, const std::vector<int32_t> &col,
                const std::vector<double> &val, HostEll &E) {
     std::vector<int32_t> huge, lng, shrt;
-    std::vector<int32_t> bucket[LONG_ROW + 1];
-    for (int64_t w0 = 0; w0 < n; w0 += CV_ROW_WINDOW) {
-        const int64_t w1 = std::min<int64_t>(w0 + CV_ROW_WINDOW, n);
-        for (int64_t i = w0; i < w1; ++i) {
-            const int64_t len = rp[i + 1] - rp[i];
-            if (len > HUGE_ROW) huge.push_back((int32_t)i);
-            else if (len > LONG_ROW) lng.push_back((int32_t)i);
-            else bucket[len].push_back((int32_t)i);
-        }
-        for (int64_t d = LONG_ROW; d >= 0; --d) {
-            shrt.insert(shrt.end(), bucket[d].begin(), bucket[d].end());
-            bucket[d].clear();
-        }
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t len = rp[i + 1] - rp[i];
+        if (len > HUGE_ROW) huge.push_back((int32_t)i);
+        else if (len > LONG_ROW) lng.push_back((int32_t)i);
+        else shrt.push_back((int32_t)i);
     }
     E.cnt[0] = (uint32_t)huge.size();
     E.cnt[1] = (uint32_t)lng.size();
