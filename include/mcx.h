@@ -560,21 +560,29 @@ mcx_status mcx_mlp_get(const mcx_mlp *model, float *params, float *mu, float *sd
  * returned by mcx_mlp_sync. */
 mcx_status mcx_mlp_predict(const mcx_mlp *model, int64_t n, const float *features, float *y, void *stream);
 
-/* Synchronise `stream`; return and clear the model's latched inference status:
- * MCX_OK, or MCX_E_TIMEOUT if an MMA completion wait gave up (that call's
- * outputs are unspecified).  Errors: MCX_E_INVALID, MCX_E_CUDA. */
+/* Synchronise `stream`; return and clear the model's latched device status
+ * (inference and training): MCX_OK, or MCX_E_TIMEOUT if an MMA completion wait
+ * gave up (that call's outputs, or the training step's gradient, are
+ * unspecified).  Errors: MCX_E_INVALID, MCX_E_CUDA. */
 mcx_status mcx_mlp_sync(mcx_mlp *model, void *stream);
 
 /* Gradient of the mean squared error (1/n) sum (net(f_i) - y_i)^2 with respect
  * to the parameters as used (BF16-rounded weights): grad float32 [4609]
- * (device) and the loss (host, may be NULL; the call then synchronises).
- * Deterministic: block partial sums are added in a fixed order. */
+ * (device) and the loss (host, may be NULL; the call then synchronises).  On
+ * the tensor cores, tiles of 128 samples: the forward pass as in
+ * mcx_mlp_predict (h1 rounded to BF16); the hidden layer's backward signal
+ * dh2 = dy W3 [z2 > 0] rounded to BF16 (round to nearest even); dh1 = dh2 W2^T
+ * and dW2 = h1^T dh2, db2 = sum dh2 as BF16 MMAs with FP32 accumulation in
+ * tensor memory; dW1, db1, dW3, db3 and the loss in FP32 on CUDA cores.
+ * Deterministic: tile partial sums are added in a fixed order.  A device-side
+ * failure of an MMA completion wait is latched for mcx_mlp_sync. */
 mcx_status mcx_mlp_gradient(mcx_mlp *model, int64_t n, const float *features, const float *targets,
                             float *grad, float *loss, void *stream);
 
 /* Adam (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on minibatches of
- * `batch` rows, `epochs` passes over a permutation drawn from `seed`; first
- * sets the feature standardisation from these features.  epoch_loss (host,
+ * `batch` rows (gradients as mcx_mlp_gradient computes them), `epochs` passes
+ * over a permutation drawn from `seed`; first sets the feature standardisation
+ * from these features.  epoch_loss (host,
  * [epochs], may be NULL) receives the mean minibatch loss of each epoch.
  * Synchronises `stream`. */
 mcx_status mcx_mlp_fit(mcx_mlp *model, int64_t n, const float *features, const float *targets, int32_t epochs,
@@ -738,8 +746,8 @@ const char *mcx_status_string(int status);
 int64_t mcx_debug_fail_alloc(int64_t k);
 mcx_status mcx_debug_pool_usage(uint64_t *used, uint64_t *reserved);
 
-/* Test hook: the polls the network's tensor-core inference spends waiting for
- * its MMAs of a tile before it gives up (default 2^22; 0xFFFFFFFF restores the
+/* Test hook: the polls the network's tensor-core kernels (inference and
+ * gradient) spend waiting for the MMAs of a tile before they give up (default 2^22; 0xFFFFFFFF restores the
  * default).  With 0 every wait gives up at once: the kernel latches the error
  * (mcx_mlp_sync returns MCX_E_TIMEOUT), waits with the default limit for the
  * MMAs it has in flight, frees its tensor memory and returns; nothing traps.

@@ -17,11 +17,14 @@ may land from this FP64 forward pass when it rounds each first-layer
 activation to BF16 once and accumulates in FP32 (a bound from the arithmetic,
 not a restatement of any implementation's operation order), and
 `forward_rounding_sigma` the typical size of that difference when the
-roundings are to nearest (independent errors, uniform over half an ulp).
+roundings are to nearest (independent errors, uniform over half an ulp);
+`gradient_error_bound` does the same for the gradient of the squared error when
+the backward signal of the hidden layer is rounded to BF16 once too.
 """
 from __future__ import annotations
 
 import numpy as np
+from scipy.special import erfc
 
 N_FEATURES = 5
 HIDDEN = 64
@@ -153,6 +156,116 @@ def loss_and_grad(p, X, target, round_weights=True):
     g["W1"] = X.T @ d1
     g["b1"] = d1.sum(axis=0)
     return loss, g
+
+
+def gradient_error_bound(p, X, target, tile=128):
+    """Elementwise bounds on |g' - g| and |loss' - loss| between the FP64 gradient g of
+    `loss_and_grad` (BF16 weights) and any evaluation g' that
+      - runs the forward pass as `forward_error_bound` allows (FP32 first layer, each
+        ReLU(z1) rounded to BF16 once, FP32 sums), so |z2' - z2| <= dz2 and |y' - y| <= dyv;
+      - forms dy = 2 (y - target) / B in FP32 and the hidden backward signal
+        d2 = dy W3^T [z2 > 0], rounded to BF16 once (relative <= 2^-8);
+      - forms d1 = d2 W2^T (64 terms) and dW2 = h1^T d2, db2 = sum d2 over tiles of
+        `tile` samples with FP32 accumulation in any order (taken as 4x the IEEE
+        bound: 2^-16 of the sum of magnitudes for 64 terms, 2^-15 for 128), the tiles
+        then summed in FP32 (one more 2^-24 per tile);
+      - forms dW1 = X^T d1 [z1 > 0], db1, dW3 = h2^T dy, db3 and the loss in FP32 over
+        the tiles ((tile + tiles) 2^-24 of the sums of magnitudes).
+    A ReLU mask may differ where |z| is within its forward error of zero: such units
+    contribute their whole magnitude.  Errors propagate through |W2| and |W3| (ReLU is
+    1-Lipschitz); standard forward-error analysis (Higham, Sec. 3.1)."""
+    y, (X, z1, h1, z2, h2, W) = forward(p, X, round_weights=True)
+    B = X.shape[0]
+    nb = -(-B // tile)
+    u = U_BF16
+    A2, A3 = np.abs(W["W2"]), np.abs(W["W3"])
+    w3 = W["W3"][:, 0]
+    e1 = 2.0 ** -21 * (np.abs(W["b1"]) + np.abs(X) @ np.abs(W["W1"]))
+    Dh1 = (1.0 + u) * e1 + u * np.abs(h1)
+    dz2 = Dh1 @ A2 + 2.0 ** -16 * ((np.abs(h1) + Dh1) @ A2 + np.abs(W["b2"]))
+    dyv = forward_error_bound(p, X)
+    r = y - np.asarray(target, dtype=np.float64)
+    dy = (2.0 / B) * r
+    ddy = (2.0 / B) * dyv + 2.0 ** -22 * np.abs(dy)
+    Ady = np.abs(dy) + ddy
+    # hidden backward signal d2 (rounded to BF16); masks uncertain where |z2| <= dz2
+    d2 = dy[:, None] * w3[None, :] * (z2 > 0)
+    flip2 = np.abs(z2) <= dz2
+    Dd2 = np.where(flip2, (1.0 + u) * Ady[:, None] * np.abs(w3)[None, :],
+                   (1.0 + u) * ddy[:, None] * np.abs(w3)[None, :] + u * np.abs(d2))
+    Ad2 = np.abs(d2) + Dd2
+    acc_t = 2.0 ** -15 + nb * 2.0 ** -24           # a tile's tensor-core sum, then the tile sum
+    acc_c = (tile + nb) * 2.0 ** -24                # FP32 sums over a tile, then the tile sum
+    Ah1 = np.abs(h1) + Dh1
+    b = {}
+    b["W2"] = Dh1.T @ Ad2 + np.abs(h1).T @ Dd2 + acc_t * (Ah1.T @ Ad2)
+    b["b2"] = Dd2.sum(axis=0) + acc_t * Ad2.sum(axis=0)
+    Ah2 = np.abs(h2) + dz2
+    b["W3"] = (dz2.T @ Ady + np.abs(h2).T @ ddy + acc_c * (Ah2.T @ Ady))[:, None]
+    b["b3"] = np.array([ddy.sum() + acc_c * Ady.sum()])
+    # first-layer backward signal d1 = (d2 W2^T) [z1 > 0]
+    d1pre = d2 @ W["W2"].T
+    Dd1pre = Dd2 @ A2.T + 2.0 ** -16 * (Ad2 @ A2.T)
+    flip1 = np.abs(z1) <= e1
+    d1 = d1pre * (z1 > 0)
+    Dd1 = np.where(flip1, np.abs(d1pre) + Dd1pre, Dd1pre)
+    Ad1 = np.abs(d1) + Dd1
+    b["W1"] = np.abs(X).T @ Dd1 + acc_c * (np.abs(X).T @ Ad1)
+    b["b1"] = Dd1.sum(axis=0) + acc_c * Ad1.sum(axis=0)
+    bl = float(np.mean(2.0 * np.abs(r) * dyv + dyv * dyv) + acc_c * np.mean((np.abs(r) + dyv) ** 2))
+    return {k: v + 1e-30 for k, v in b.items()}, bl + 1e-30
+
+
+def _bf16_ulp(a):
+    """Spacing of BF16 numbers at |a| (2^(floor(log2 |a|) - 7)); 0 where a == 0."""
+    a = np.abs(a)
+    nz = a > 0
+    return np.where(nz, np.exp2(np.floor(np.log2(np.where(nz, a, 1.0))) - 7), 0.0)
+
+
+def gradient_rounding_sigma(p, X, target):
+    """Standard deviation of each gradient entry's change when every first-layer
+    activation h1 and every hidden backward signal d2 = dy W3^T [z2 > 0] is rounded to
+    the nearest BF16 value, the errors taken as independent and uniform over half an
+    ulp (variance ulp^2 / 12), to first order; a hidden ReLU mask near zero flips with
+    the probability that the summed h1 roundings (normal approximation) cross it.  The
+    h1 errors reach the gradient directly and through y (so through dy = 2 (y - t) / B,
+    with dy/dh1_j = g_j = sum_k W2_jk [z2_k > 0] W3_k) and through z2 (so through h2)."""
+    y, (X, z1, h1, z2, h2, W) = forward(p, X, round_weights=True)
+    B = X.shape[0]
+    w3 = W["W3"][:, 0]
+    W2 = W["W2"]
+    m2 = (z2 > 0).astype(np.float64)
+    m1 = (z1 > 0).astype(np.float64)
+    dy = (2.0 / B) * (y - np.asarray(target, dtype=np.float64))
+    d2 = dy[:, None] * w3[None, :] * m2
+    vh = _bf16_ulp(h1) ** 2 / 12.0                      # var of the h1 roundings [B, 64]
+    # a z2 mask flips with probability Phi(-|z2| / sd(z2 change)) (normal approximation of
+    # the summed h1 roundings), moving d2 by its whole value dy W3: variance p (dy W3)^2
+    sz2 = np.sqrt(vh @ (W2 * W2))
+    pf = 0.5 * erfc(np.abs(z2) / np.maximum(sz2, 1e-300) / np.sqrt(2.0))
+    vd = _bf16_ulp(d2) ** 2 / 12.0 + pf * (dy[:, None] * w3[None, :]) ** 2   # d2 roundings and flips
+    g = (W2[None, :, :] * (m2 * w3[None, :])[:, None, :]).sum(-1)   # dy/dh1 [B, 64]
+    vdy = (2.0 / B) ** 2 * (vh * g * g).sum(1)           # var of the dy change [B]
+    c = (2.0 / B) * m2 * w3[None, :]                     # d(d2_k)/d(y)  [B, 64]
+    s2 = {}
+    # dW2_jk = sum_s h1_sj d2_sk: the h1_sj rounding directly and via y; the d2 rounding
+    Gd = np.einsum("sj,sk->jk", vh, d2 * d2)
+    Gx = 2.0 * np.einsum("sj,sk->jk", vh * g * h1, d2 * c)
+    Gy = np.einsum("sj,sk->jk", h1 * h1, (c * c) * (vh * g * g).sum(1)[:, None])
+    Gr = np.einsum("sj,sk->jk", h1 * h1, vd)
+    s2["W2"] = Gd + Gx + Gy + Gr
+    s2["b2"] = ((c * c) * (vh * g * g).sum(1)[:, None] + vd).sum(0)
+    # dW3_k = sum_s h2_sk dy_s: h2 moves through z2 (sum_j dh1_j W2_jk), dy through y
+    a = dy[:, None, None] * m2[:, None, :] * W2[None, :, :] + h2[:, None, :] * (2.0 / B) * g[:, :, None]
+    s2["W3"] = np.einsum("sj,sjk->k", vh, a * a)[:, None]
+    s2["b3"] = np.array([vdy.sum()])
+    # d1_sj = [z1_sj > 0] sum_k W2_jk d2_sk: the d2 changes through dy and their roundings
+    q = (W2[None, :, :] * (m2 * w3[None, :])[:, None, :]).sum(-1)   # sum_k W2_jk m_k w3_k [B, 64]
+    vd1 = m1 * ((2.0 / B) ** 2 * q * q * (vh * g * g).sum(1)[:, None] + vd @ (W2 * W2).T)
+    s2["W1"] = (X * X).T @ vd1
+    s2["b1"] = vd1.sum(0)
+    return {k: np.sqrt(v) + 1e-30 for k, v in s2.items()}
 
 
 def cv_coefficients(csr, T, t, xhat):

@@ -47,10 +47,6 @@ constexpr int P_B2 = P_W2 + HID * HID;
 constexpr int P_W3 = P_B2 + HID;
 constexpr int P_B3 = P_W3 + HID;
 constexpr int NPARAM = P_B3 + 1;  // 4609
-constexpr int GRAD_SAMPLES = 64;  // samples per gradient block (one per thread)
-// Row stride of the per-sample activation arrays in shared memory: one float of
-// padding puts the rows of a warp's samples in distinct banks.
-constexpr int HS = HID + 1;
 
 // ---------------------------------------------------------------------------
 // Row passes: Taylor terms, rates, features, cubic coefficients
@@ -489,14 +485,6 @@ struct MLPView {
     const float *sd;      // [NF] feature standard deviations
 };
 
-// weights to shared memory: W rounded to BF16, biases as they are
-__device__ void load_params(const float *__restrict__ p, float *s) {
-    for (int k = threadIdx.x; k < NPARAM; k += blockDim.x) {
-        const bool is_w = (k < P_B1) || (k >= P_W2 && k < P_B2) || (k >= P_W3 && k < P_B3);
-        s[k] = is_w ? bf16_round(p[k]) : p[k];
-    }
-}
-
 // x = (f - mu) * (1/sd), isd = 1/sd rounded to FP32 (the same in training and inference)
 __device__ __forceinline__ void standardise(const float *__restrict__ f, const float *mu, const float *isd,
                                            float x[NF]) {
@@ -646,113 +634,283 @@ __global__ void __launch_bounds__(TC_ROWS, 7) k_mlp_predict_tc(int64_t n, const 
     if (warp == 0) tc::tmem_dealloc(tmem, TC_COLS);
 }
 
-// Gradient of the mean squared error over samples [0, n) with respect to the
-// weights as used (BF16-rounded).  Block b takes samples [b*64, b*64+64), one
-// per thread, and writes its partial gradient (and loss) to part[b]; the
-// per-sample activations and deltas go through shared memory for the
-// reductions over the block's samples.
-__global__ void __launch_bounds__(GRAD_SAMPLES) k_mlp_grad(int64_t n, const float *__restrict__ F,
-                                                          const float *__restrict__ tgt, const int64_t *__restrict__ idx,
-                                                          MLPView m, float inv_batch, float *__restrict__ part) {
-    extern __shared__ float sm[];
-    float *s = sm;                          // NPARAM weights (+3 pad)
-    float *X = s + NPARAM + 3;              // [64][NF] standardised inputs
-    float *H1 = X + GRAD_SAMPLES * NF;      // [64][HS]
-    float *H2 = H1 + GRAD_SAMPLES * HS;     // [64][HS]
-    float *D2 = H2 + GRAD_SAMPLES * HS;     // [64][HS]
-    float *D1 = D2 + GRAD_SAMPLES * HS;     // [64][HS]
-    float *DY = D1 + GRAD_SAMPLES * HS;     // [64]
-    float *LS = DY + GRAD_SAMPLES;          // [64] squared residuals
-    load_params(m.params, s);
-    const int tid = threadIdx.x;
-    const int64_t smp = (int64_t)blockIdx.x * GRAD_SAMPLES + tid;
+// ---------------------------------------------------------------------------
+// Gradient on the tensor cores.  A CTA of 4 warps takes a tile of 128 samples,
+// one per thread, and writes its partial gradient (and loss) to part[tile]:
+//  * forward as in inference: the first layer on CUDA cores (FP32, BF16
+//    weights), h1 rounded to BF16 into A1 = [samples x 64] and into the
+//    transposed operand H1T = [units x samples]; MMA z2 = h1 W2 (128 x 64 x 64,
+//    TMEM columns 0..63); bias, ReLU and the output layer on CUDA cores;
+//  * backward: dy = 2 (y - target) / batch, dh2 = dy w3 [z2 > 0] rounded to
+//    BF16 into D2 = [samples x 64] and D2T = [units x samples]; two MMAs:
+//    dh1 = dh2 W2^T (128 x 64 x 64, columns 64..127) and
+//    [dW2 ; db2] = [h1^T ; 1] dh2 (128 x 64 x 128 over the tile's samples: rows
+//    0..63 of H1T are h1^T, row 64 ones, the rest zero; columns 128..191);
+//  * dW1, db1 (from dh1 masked by z1 > 0), dW3, db3 and the loss on CUDA cores
+//    in FP32 over the tile (shared memory, fixed order).
+// All operands K-major without swizzle; K = 64 operands have their 8-row groups
+// 1024 bytes apart, K = 128 operands (samples as K) 2048 bytes apart.
+// ---------------------------------------------------------------------------
+constexpr int TG_ROWS = 128;  // samples per tile (MMA M)
+constexpr uint32_t TG_COLS = 256;  // TMEM columns allocated (three 64-column accumulators)
+constexpr int TG_FS = HID + 1;     // row stride of the FP32 per-sample arrays
+
+// byte offset of element (r, k) in a K-major no-swizzle operand with 128 K
+// elements per row: 8-row groups 2048 B apart, K-adjacent core matrices 128 B apart
+__device__ __forceinline__ uint32_t tc_off128(uint32_t r, uint32_t k) {
+    return (r >> 3) * 2048u + (k >> 3) * 128u + (r & 7u) * 16u + (k & 7u) * 2u;
+}
+
+// dynamic shared memory of k_mlp_grad_tc (byte offsets; operands 1024-aligned)
+constexpr uint32_t TG_W2T = 0;                            // [64 x 64] bf16, (k, j) = W2[j][k]
+constexpr uint32_t TG_W2 = TG_W2T + 64 * 64 * 2;          // [64 x 64] bf16, (j, k) = W2[j][k]
+constexpr uint32_t TG_A1 = TG_W2 + 64 * 64 * 2;           // [128 x 64] bf16, (s, j) = h1[s][j]
+constexpr uint32_t TG_D2 = TG_A1 + 128 * 64 * 2;          // [128 x 64] bf16, (s, k) = dh2[s][k]
+constexpr uint32_t TG_H1T = TG_D2 + 128 * 64 * 2;         // [128 x 128] bf16, (j, s) = h1[s][j]; row 64 ones
+constexpr uint32_t TG_D2T = TG_H1T + 128 * 128 * 2;       // [64 x 128] bf16, (k, s) = dh2[s][k]
+constexpr uint32_t TG_F = TG_D2T + 64 * 128 * 2;          // [128][65] f32: h2, then dh1
+constexpr uint32_t TG_X = TG_F + TG_ROWS * TG_FS * 4;     // [128][5] f32 standardised inputs
+constexpr uint32_t TG_DY = TG_X + TG_ROWS * NF * 4;       // [128] f32 dy
+constexpr uint32_t TG_LS = TG_DY + TG_ROWS * 4;           // [128] f32 squared residuals
+constexpr uint32_t TG_W1 = TG_LS + TG_ROWS * 4;           // [5 x 64] f32 (BF16-rounded)
+constexpr uint32_t TG_B1 = TG_W1 + NF * HID * 4;          // [64] f32
+constexpr uint32_t TG_B2 = TG_B1 + HID * 4;               // [64] f32
+constexpr uint32_t TG_W3 = TG_B2 + HID * 4;               // [64] f32 (BF16-rounded)
+constexpr uint32_t TG_SMEM = TG_W3 + HID * 4;
+
+__global__ void __launch_bounds__(TG_ROWS, 1) k_mlp_grad_tc(int64_t n, const float *__restrict__ F,
+                                                          const float *__restrict__ tgt,
+                                                          const int64_t *__restrict__ idx, MLPView m,
+                                                          float inv_batch, float *__restrict__ part, uint32_t *err,
+                                                          uint32_t wait_polls) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    __shared__ float sb3, smu[NF], sisd[NF];
+    float *sF = reinterpret_cast<float *>(sm + TG_F);
+    float *sX = reinterpret_cast<float *>(sm + TG_X);
+    float *sDY = reinterpret_cast<float *>(sm + TG_DY);
+    float *sLS = reinterpret_cast<float *>(sm + TG_LS);
+    float *sW1 = reinterpret_cast<float *>(sm + TG_W1);
+    float *sb1 = reinterpret_cast<float *>(sm + TG_B1);
+    float *sb2 = reinterpret_cast<float *>(sm + TG_B2);
+    float *sw3 = reinterpret_cast<float *>(sm + TG_W3);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // ---- weights (BF16 as used), the constant rows of H1T, TMEM, mbarrier ----
+    for (int k = tid; k < HID * HID; k += TG_ROWS) {
+        const int j = k / HID, kk = k % HID;
+        const uint16_t w = (uint16_t)bf16_bits(m.params[P_W2 + k]);  // W2[j][kk]
+        *reinterpret_cast<uint16_t *>(sm + TG_W2T + tc_off((uint32_t)kk, (uint32_t)j)) = w;
+        *reinterpret_cast<uint16_t *>(sm + TG_W2 + tc_off((uint32_t)j, (uint32_t)kk)) = w;
+    }
+    for (int k = tid; k < NF * HID; k += TG_ROWS) sW1[k] = bf16_round(m.params[P_W1 + k]);
+    if (tid < HID) {
+        sb1[tid] = m.params[P_B1 + tid];
+        sb2[tid] = m.params[P_B2 + tid];
+        sw3[tid] = bf16_round(m.params[P_W3 + tid]);
+    }
+    for (int r = HID; r < TG_ROWS; ++r)  // row 64 of H1T: ones (db2); rows 65..127: zero
+        *reinterpret_cast<uint16_t *>(sm + TG_H1T + tc_off128((uint32_t)r, (uint32_t)tid)) =
+            r == HID ? (uint16_t)0x3F80u : (uint16_t)0u;
+    if (tid < NF) {
+        smu[tid] = m.mu[tid];
+        sisd[tid] = __fdiv_rn(1.0f, m.sd[tid]);
+    }
+    if (tid == 0) {
+        sb3 = m.params[P_B3];
+        tc::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, TG_COLS);
+    __syncthreads();
+    // ---- forward: first layer (FP32, BF16 weights), h1 to both operands ----
+    const int64_t smp = (int64_t)blockIdx.x * TG_ROWS + tid;
     const bool valid = smp < n;
     float x[NF] = {0.f, 0.f, 0.f, 0.f, 0.f};
     float target = 0.0f;
     if (valid) {
         const int64_t row = idx ? idx[smp] : smp;
-        float mu[NF], isd[NF];
-#pragma unroll
-        for (int q = 0; q < NF; ++q) {
-            mu[q] = m.mu[q];
-            isd[q] = __fdiv_rn(1.0f, m.sd[q]);
-        }
-        standardise(F + row * NF, mu, isd, x);
+        standardise(F + row * NF, smu, sisd, x);
         target = tgt[row];
     }
 #pragma unroll
-    for (int q = 0; q < NF; ++q) X[tid * NF + q] = x[q];
+    for (int f = 0; f < NF; ++f) sX[tid * NF + f] = x[f];
+    uint32_t mask1[2] = {0u, 0u};  // z1 > 0, bit per hidden unit
+#pragma unroll
+    for (int kc = 0; kc < HID; kc += 8) {
+        float a[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) a[q] = sb1[kc + q];
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) a[q] = fmaf(x[f], sW1[f * HID + kc + q], a[q]);
+        uint32_t pk[4];
+#pragma unroll
+        for (int q = 0; q < 8; q += 2) {
+            const __nv_bfloat162 h2v = __floats2bfloat162_rn(fmaxf(a[q], 0.0f), fmaxf(a[q + 1], 0.0f));
+            pk[q >> 1] = *reinterpret_cast<const uint32_t *>(&h2v);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (a[q] > 0.0f) mask1[(kc + q) >> 5] |= 1u << ((kc + q) & 31);
+            const uint16_t hb = (uint16_t)(pk[q >> 1] >> ((q & 1) * 16));
+            *reinterpret_cast<uint16_t *>(sm + TG_H1T + tc_off128((uint32_t)(kc + q), (uint32_t)tid)) = hb;
+        }
+        *reinterpret_cast<uint4 *>(sm + TG_A1 + tc_off((uint32_t)tid, (uint32_t)kc)) =
+            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    tc::fence_proxy_async_smem();
+    tc::fence_before_sync();
     __syncthreads();
-    // forward (one sample per thread)
-    for (int j = 0; j < HID; ++j) {
-        float a = s[P_B1 + j];
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(TG_ROWS, 64);
+    const uint32_t base = tc::smem_addr(sm);
+    if (tid == 0) {  // z2 = h1 W2
 #pragma unroll
-        for (int q = 0; q < NF; ++q) a = fmaf(x[q], s[P_W1 + q * HID + j], a);
-        H1[tid * HS + j] = fmaxf(a, 0.0f);
+        for (uint32_t kk = 0; kk < HID / 16; ++kk)
+            tc::mma_bf16(tmem, tc::smem_desc(base + TG_A1 + kk * 256u, 128u, 1024u),
+                         tc::smem_desc(base + TG_W2T + kk * 256u, 128u, 1024u), idesc, kk > 0);
+        tc::mma_commit(&bar);
     }
-    float y = s[P_B3];
-    for (int kc = 0; kc < HID; kc += 16) {
-        float acc[16];
+    bool ok = tc::mbar_wait(&bar, 0u, wait_polls);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicOr(err, 2u);
+        tc::mbar_wait(&bar, 0u, TC_WAIT);
+    } else {
+        tc::fence_after_sync();
+        // ---- output layer and the backward signal dh2 ----
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        float z[HID];
 #pragma unroll
-        for (int k = 0; k < 16; ++k) acc[k] = s[P_B2 + kc + k];
-        for (int j = 0; j < HID; ++j) {
-            const float hj = H1[tid * HS + j];
+        for (uint32_t c = 0; c < HID; c += 16) tc::tmem_ld16(tmem + lane_base + c, z + c);
+        tc::tmem_ld_wait();
+        float y = sb3;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) acc[k] = fmaf(hj, s[P_W2 + j * HID + kc + k], acc[k]);
+        for (int k = 0; k < HID; ++k) {
+            z[k] = z[k] + sb2[k];
+            const float h = fmaxf(z[k], 0.0f);
+            sF[tid * TG_FS + k] = h;
+            y = fmaf(h, sw3[k], y);
         }
+        const float r = valid ? y - target : 0.0f;
+        const float dy = 2.0f * r * inv_batch;
+        sDY[tid] = dy;
+        sLS[tid] = r * r;
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            H2[tid * HS + kc + k] = fmaxf(acc[k], 0.0f);
-            D2[tid * HS + kc + k] = acc[k] > 0.0f ? 1.0f : 0.0f;  // mask, scaled below
-            y = fmaf(fmaxf(acc[k], 0.0f), s[P_W3 + kc + k], y);
+        for (int kc = 0; kc < HID; kc += 8) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int q = 0; q < 8; q += 2) {
+                const float d0 = z[kc + q] > 0.0f ? dy * sw3[kc + q] : 0.0f;
+                const float d1 = z[kc + q + 1] > 0.0f ? dy * sw3[kc + q + 1] : 0.0f;
+                const __nv_bfloat162 dv = __floats2bfloat162_rn(d0, d1);
+                pk[q >> 1] = *reinterpret_cast<const uint32_t *>(&dv);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                *reinterpret_cast<uint16_t *>(sm + TG_D2T + tc_off128((uint32_t)(kc + q), (uint32_t)tid)) =
+                    (uint16_t)(pk[q >> 1] >> ((q & 1) * 16));
+            *reinterpret_cast<uint4 *>(sm + TG_D2 + tc_off((uint32_t)tid, (uint32_t)kc)) =
+                make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+        tc::fence_proxy_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {  // dh1 = dh2 W2^T;  [dW2 ; db2] = [h1^T ; 1] dh2 over the tile's samples
+#pragma unroll
+            for (uint32_t kk = 0; kk < HID / 16; ++kk)
+                tc::mma_bf16(tmem + 64u, tc::smem_desc(base + TG_D2 + kk * 256u, 128u, 1024u),
+                             tc::smem_desc(base + TG_W2 + kk * 256u, 128u, 1024u), idesc, kk > 0);
+#pragma unroll
+            for (uint32_t kk = 0; kk < TG_ROWS / 16; ++kk)
+                tc::mma_bf16(tmem + 128u, tc::smem_desc(base + TG_H1T + kk * 256u, 128u, 2048u),
+                             tc::smem_desc(base + TG_D2T + kk * 256u, 128u, 2048u), idesc, kk > 0);
+            tc::mma_commit(&bar);
+        }
+        // meanwhile: dW3, db3 and the loss over the tile (FP32, sample order)
+        float *out = part + (int64_t)blockIdx.x * (NPARAM + 1);
+        if (tid < HID) {
+            float g = 0.0f;
+            for (int s = 0; s < TG_ROWS; ++s) g = fmaf(sF[s * TG_FS + tid], sDY[s], g);
+            out[P_W3 + tid] = g;
+        } else if (tid == HID) {
+            float gb3 = 0.0f, loss = 0.0f;
+            for (int s = 0; s < TG_ROWS; ++s) {
+                gb3 += sDY[s];
+                loss += sLS[s];
+            }
+            out[P_B3] = gb3;
+            out[NPARAM] = loss * inv_batch;
+        }
+        ok = tc::mbar_wait(&bar, 1u, wait_polls);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(err, 2u);
+            tc::mbar_wait(&bar, 1u, TC_WAIT);
+        } else {
+            tc::fence_after_sync();
+            // dh1 (masked by z1 > 0) to shared memory for dW1 and db1
+#pragma unroll
+            for (uint32_t c = 0; c < HID; c += 16) {
+                float v[16];
+                tc::tmem_ld16(tmem + lane_base + 64u + c, v);
+                tc::tmem_ld_wait();
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int j = (int)c + k;
+                    sF[tid * TG_FS + j] = ((mask1[j >> 5] >> (j & 31)) & 1u) ? v[k] : 0.0f;
+                }
+            }
+            // dW2 (TMEM rows 0..63) and db2 (row 64), one row per thread of warps 0..2
+#pragma unroll
+            for (uint32_t c = 0; c < HID; c += 16) {
+                float v[16];
+                tc::tmem_ld16(tmem + lane_base + 128u + c, v);
+                tc::tmem_ld_wait();
+                const int row = warp * 32 + lane;
+                if (row < HID) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) out[P_W2 + row * HID + (int)c + k] = v[k];
+                } else if (row == HID) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) out[P_B2 + (int)c + k] = v[k];
+                }
+            }
+            __syncthreads();
+            {  // dW1 and db1: thread t sums column j = t mod 64 over the tile, half the outputs each
+                const int j = tid & (HID - 1);
+                if (tid < HID) {
+                    float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
+                    for (int s = 0; s < TG_ROWS; ++s) {
+                        const float d = sF[s * TG_FS + j];
+                        g0 = fmaf(sX[s * NF + 0], d, g0);
+                        g1 = fmaf(sX[s * NF + 1], d, g1);
+                        g2 = fmaf(sX[s * NF + 2], d, g2);
+                    }
+                    out[P_W1 + 0 * HID + j] = g0;
+                    out[P_W1 + 1 * HID + j] = g1;
+                    out[P_W1 + 2 * HID + j] = g2;
+                } else {
+                    float g3 = 0.0f, g4 = 0.0f, gb = 0.0f;
+                    for (int s = 0; s < TG_ROWS; ++s) {
+                        const float d = sF[s * TG_FS + j];
+                        g3 = fmaf(sX[s * NF + 3], d, g3);
+                        g4 = fmaf(sX[s * NF + 4], d, g4);
+                        gb += d;
+                    }
+                    out[P_W1 + 3 * HID + j] = g3;
+                    out[P_W1 + 4 * HID + j] = g4;
+                    out[P_B1 + j] = gb;
+                }
+            }
         }
     }
-    const float r = valid ? y - target : 0.0f;
-    const float dy = 2.0f * r * inv_batch;
-    DY[tid] = dy;
-    LS[tid] = r * r;
-    for (int k = 0; k < HID; ++k) D2[tid * HS + k] *= dy * s[P_W3 + k];
-    // d1 = (W2 d2) masked by h1 > 0
-    for (int j = 0; j < HID; ++j) {
-        float a = 0.0f;
-#pragma unroll 8
-        for (int k = 0; k < HID; ++k) a = fmaf(s[P_W2 + j * HID + k], D2[tid * HS + k], a);
-        D1[tid * HS + j] = H1[tid * HS + j] > 0.0f ? a : 0.0f;
-    }
+    tc::fence_before_sync();
     __syncthreads();
-    float *out = part + (int64_t)blockIdx.x * (NPARAM + 1);
-    for (int e = tid; e < HID * HID; e += GRAD_SAMPLES) {  // W2[j][k] = sum_s h1[s][j] d2[s][k]
-        const int j = e / HID, k = e % HID;
-        float a = 0.0f;
-        for (int q = 0; q < GRAD_SAMPLES; ++q) a = fmaf(H1[q * HS + j], D2[q * HS + k], a);
-        out[P_W2 + e] = a;
-    }
-    {
-        const int k = tid;  // one hidden unit per thread
-        float gb2 = 0.0f, gb1 = 0.0f, gw3 = 0.0f;
-        for (int q = 0; q < GRAD_SAMPLES; ++q) {
-            gb2 += D2[q * HS + k];
-            gb1 += D1[q * HS + k];
-            gw3 = fmaf(H2[q * HS + k], DY[q], gw3);
-        }
-        out[P_B2 + k] = gb2;
-        out[P_B1 + k] = gb1;
-        out[P_W3 + k] = gw3;
-        for (int f = 0; f < NF; ++f) {
-            float a = 0.0f;
-            for (int q = 0; q < GRAD_SAMPLES; ++q) a = fmaf(X[q * NF + f], D1[q * HS + k], a);
-            out[P_W1 + f * HID + k] = a;
-        }
-    }
-    if (tid == 0) {
-        float gb3 = 0.0f, loss = 0.0f;
-        for (int q = 0; q < GRAD_SAMPLES; ++q) {
-            gb3 += DY[q];
-            loss += LS[q];
-        }
-        out[P_B3] = gb3;
-        out[NPARAM] = loss * inv_batch;
-    }
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(tmem, TG_COLS);
 }
 
 // Sum the block partials in block order (deterministic); optionally apply Adam.
@@ -1237,7 +1395,6 @@ cudaError_t ensure_part(mcx_mlp *m, int64_t blocks) {
     return e;
 }
 
-size_t grad_smem() { return sizeof(float) * (NPARAM + 3 + GRAD_SAMPLES * NF + 4 * GRAD_SAMPLES * HS + 2 * GRAD_SAMPLES); }
 
 }  // namespace
 
@@ -1359,12 +1516,12 @@ mcx_status mcx_mlp_gradient(mcx_mlp *m, int64_t n, const float *features, const 
     NvtxRange nvtx("mcx_mlp_gradient");
     if (!m || n < 1 || !features || !targets || !grad) return MCX_E_INVALID;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t blocks = (n + GRAD_SAMPLES - 1) / GRAD_SAMPLES;
+    const int64_t blocks = (n + TG_ROWS - 1) / TG_ROWS;
     cudaError_t e = ensure_part(m, blocks);
     if (e != cudaSuccess) return cv_status(e);
-    cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem());
-    k_mlp_grad<<<(unsigned)blocks, GRAD_SAMPLES, grad_smem(), st>>>(n, features, targets, nullptr, view(m),
-                                                                     1.0f / (float)n, m->part);
+    cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TG_SMEM);
+    k_mlp_grad_tc<<<(unsigned)blocks, TG_ROWS, TG_SMEM, st>>>(n, features, targets, nullptr, view(m),
+                                                               1.0f / (float)n, m->part, m->err, m->wait_polls);
     k_grad_reduce<<<(NPARAM + 256) / 256, 256, 0, st>>>((int)blocks, m->part, m->grad, nullptr, nullptr, nullptr,
                                                          0.f, 1.f, 1.f, 0);
     e = cudaMemcpyAsync(grad, m->grad, sizeof(float) * NPARAM, cudaMemcpyDeviceToDevice, st);
@@ -1382,7 +1539,7 @@ mcx_status mcx_mlp_fit(mcx_mlp *m, int64_t n, const float *features, const float
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // feature standardisation from this training set
     k_feature_stats<<<NF, 256, 0, st>>>(n, features, m->stats, m->stats + NF);
-    const int64_t bblocks = (batch + GRAD_SAMPLES - 1) / GRAD_SAMPLES;
+    const int64_t bblocks = (batch + TG_ROWS - 1) / TG_ROWS;
     cudaError_t e = ensure_part(m, bblocks);
     if (e != cudaSuccess) return cv_status(e);
     if (m->idx_n < n) {
@@ -1398,7 +1555,7 @@ mcx_status mcx_mlp_fit(mcx_mlp *m, int64_t n, const float *features, const float
         if ((e = dev_malloc(&m->losses, sizeof(float) * (size_t)steps)) != cudaSuccess) return cv_status(e);
         m->losses_n = steps;
     }
-    cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_smem());
+    cudaFuncSetAttribute(k_mlp_grad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TG_SMEM);
     std::vector<int64_t> perm(n);
     std::vector<float> hl(epoch_loss ? (size_t)steps : 0);
     uint64_t s = seed * 0xD1B54A32D192ED03ull + 1;
@@ -1417,12 +1574,13 @@ mcx_status mcx_mlp_fit(mcx_mlp *m, int64_t n, const float *features, const float
         int64_t nb = 0;
         for (int64_t b0 = 0; b0 < n; b0 += batch) {
             const int64_t bn = std::min<int64_t>(batch, n - b0);
-            const int64_t blocks = (bn + GRAD_SAMPLES - 1) / GRAD_SAMPLES;
+            const int64_t blocks = (bn + TG_ROWS - 1) / TG_ROWS;
             ++m->step;
             const float b1c = 1.0f - powf(0.9f, (float)m->step);
             const float b2c = 1.0f - powf(0.999f, (float)m->step);
-            k_mlp_grad<<<(unsigned)blocks, GRAD_SAMPLES, grad_smem(), st>>>(bn, features, targets, m->idx + b0,
-                                                                             view(m), 1.0f / (float)bn, m->part);
+            k_mlp_grad_tc<<<(unsigned)blocks, TG_ROWS, TG_SMEM, st>>>(bn, features, targets, m->idx + b0, view(m),
+                                                                       1.0f / (float)bn, m->part, m->err,
+                                                                       m->wait_polls);
             k_grad_reduce<<<(NPARAM + 256) / 256, 256, 0, st>>>((int)blocks, m->part, m->grad, m->params, m->m1,
                                                                  m->m2, lr, b1c, b2c, 1);
             if (epoch_loss)  // kept on the device; read once per epoch

@@ -6,10 +6,10 @@
   k = 1, 2, ... fails each of its allocations in turn: the call returns
   MCX_E_OOM, the library's pool usage is back where it was and no cudaMalloc'd
   memory is left behind; once k passes the call's allocations it succeeds.
-* Bounded wait: the tensor-core inference's MMA wait given a limit of zero polls
-  gives up at once; the kernel latches the error, drains its MMAs with the normal
-  limit, frees its tensor memory and returns: mcx_mlp_sync reports
-  MCX_E_TIMEOUT and the context stays usable (a later inference is correct).
+* Bounded wait: the tensor-core inference's and gradient's MMA waits given a
+  limit of zero polls give up at once; the kernel latches the error, drains its
+  MMAs with the normal limit, frees its tensor memory and returns: mcx_mlp_sync
+  reports MCX_E_TIMEOUT and the context stays usable (a later call is correct).
 """
 import numpy as np
 import pytest
@@ -139,4 +139,20 @@ def test_tensor_core_wait_gives_up_and_context_survives(mcx):
     X64 = X.astype(np.float64)
     oy, _ = CV.forward(prm, X64)
     assert np.all(np.abs(y - oy) <= CV.forward_error_bound(prm, X64))
+    # the tensor-core gradient's waits: the same limit, the same latch
+    t = np.random.default_rng(1).normal(size=1000).astype(np.float32)
+    Xd, td = torch.as_tensor(X).cuda(), torch.as_tensor(t).cuda()
+    assert L.mcx_debug_mlp_wait_polls(net._h, 0) == 0
+    net.gradient(Xd, td)
+    with pytest.raises(MCXError) as ei:
+        net.sync()
+    assert ei.value.code == -7
+    assert L.mcx_debug_mlp_wait_polls(net._h, 0xFFFFFFFF) == 0
+    g, _ = net.gradient(Xd, td)
+    net.sync()
+    _, og = CV.loss_and_grad(prm, X64, t.astype(np.float64))
+    gb, _ = CV.gradient_error_bound(prm, X64, t.astype(np.float64))
+    order = ("W1", "b1", "W2", "b2", "W3", "b3")
+    assert np.all(np.abs(g.cpu().numpy() - np.concatenate([og[k].ravel() for k in order]))
+                  <= np.concatenate([gb[k].ravel() for k in order]))
     net.close()

@@ -171,6 +171,64 @@ def test_forward_error_bound_covers_bf16_hidden_and_fp32_sums():
         assert np.any(np.abs(no_relu[:, 0] - y) > bound)
 
 
+def _bf16_gradient_eval(p, X, target, rnd=CV.bf16, bug=None):
+    """A test-local gradient evaluation inside the model the bound and the sigma cover:
+    the forward pass of _fp32_bf16_forward, dy in FP32, the hidden backward signal
+    d2 = dy W3^T [z2 > 0] rounded once by `rnd`, the sums in FP64 (below FP32's
+    error).  `bug` plants a mistake: "d1_no_transpose" (d1 = d2 W2 instead of d2 W2^T),
+    "no_mask2" (d2 without the z2 mask), "half_dy" (dy = (y - t) / B)."""
+    Wb = {k: (CV.bf16(v) if k[0] == "W" else np.asarray(v, np.float32)) for k, v in p.items()}
+    Xf = np.asarray(X, np.float32)
+    z1 = Xf @ Wb["W1"] + Wb["b1"]
+    h1 = rnd(np.maximum(z1, 0).astype(np.float32))
+    z2 = (h1 @ Wb["W2"] + Wb["b2"]).astype(np.float32)
+    h2 = np.maximum(z2, 0)
+    y = (h2 @ Wb["W3"] + Wb["b3"])[:, 0]
+    B = X.shape[0]
+    dy = np.float32(1.0 if bug == "half_dy" else 2.0) * (y - np.asarray(target, np.float32)) * np.float32(1.0 / B)
+    mask2 = np.ones_like(z2) if bug == "no_mask2" else (z2 > 0)
+    d2 = rnd(np.where(mask2, dy[:, None] * Wb["W3"][:, 0][None, :], 0).astype(np.float32)).astype(np.float64)
+    W2 = Wb["W2"].astype(np.float64)
+    d1 = np.where(z1 > 0, d2 @ (W2 if bug == "d1_no_transpose" else W2.T), 0.0)
+    h1, h2, dy = h1.astype(np.float64), h2.astype(np.float64), dy.astype(np.float64)
+    return {"W1": np.asarray(X, np.float64).T @ d1, "b1": d1.sum(0), "W2": h1.T @ d2, "b2": d2.sum(0),
+            "W3": (h2.T @ dy)[:, None], "b3": np.array([dy.sum()])}
+
+
+def _truncate_bf16(a):
+    return (np.asarray(a, np.float32).view(np.uint32) & 0xFFFF0000).view(np.float32)
+
+
+def test_gradient_bound_and_sigma_cover_bf16_backward():
+    """With h1 and the hidden backward signal rounded to BF16 (to nearest): every
+    gradient entry within gradient_error_bound; the mean square of the differences in
+    units of gradient_rounding_sigma near 1 (0.71 .. 1.56 over 20 networks of 777
+    samples; here 8 networks must fall in [0.4, 3]), while truncation instead of
+    rounding gives more than 10; a planted mistake (transposed W2 in the backward
+    signal, a dropped ReLU mask, half the residual's factor) breaks the bound or the
+    mean square."""
+    rng = np.random.default_rng(9)
+    for seed in range(8):
+        p = CV.init_params(seed)
+        X = rng.normal(size=(777, CV.N_FEATURES)).astype(np.float32).astype(np.float64)
+        t = rng.normal(size=777)
+        _, g = CV.loss_and_grad(p, X, t)
+        bound, _ = CV.gradient_error_bound(p, X, t)
+        sig = CV.gradient_rounding_sigma(p, X, t)
+
+        def stats(h):
+            inb = all(np.all(np.abs(h[k] - g[k]) <= bound[k]) for k in g)
+            z = np.concatenate([((h[k] - g[k]) / sig[k]).ravel() for k in g])
+            return inb, float(np.mean(z * z))
+
+        inb, ms = stats(_bf16_gradient_eval(p, X, t))
+        assert inb and 0.4 < ms < 3.0, (seed, ms)
+        assert stats(_bf16_gradient_eval(p, X, t, rnd=_truncate_bf16))[1] > 10.0
+        for bug in ("d1_no_transpose", "no_mask2", "half_dy"):
+            inb, ms = stats(_bf16_gradient_eval(p, X, t, bug=bug))
+            assert not inb or ms > 10.0, (seed, bug, ms)
+
+
 def test_features_and_taylor_terms_brute_force():
     """Every feature column, the rates and the Taylor terms against per-node loops over
     explicit neighbour lists and dense matrix powers on a small weighted graph with a
