@@ -74,6 +74,58 @@ def _with_hub(csr):
     return W.CSR(n + 1, m.indptr.astype(np.int64), m.indices.astype(np.int32), m.data.astype(np.float64))
 
 
+def _mixed_rows(n=2037, seed=6, signed=True):
+    """A CSR with every row class of the row passes and a ragged last window: empty
+    rows, short rows, rows of 33..1024 entries and one above 1024 (a hub); values of
+    both signs (negative off-diagonal entries do not count in the rates), or with
+    signed=False nonnegative off the diagonal (a matrix the walkers accept)."""
+    import scipy.sparse as sp
+
+    rng = np.random.default_rng(seed)
+    a = sp.random(n, n, density=4.0 / n, random_state=seed, format="lil")
+    a[5, rng.choice(n, min(1500, n - 1), replace=False)] = 1.0
+    for i in (17, 400, n - 40):
+        a[i, rng.choice(n, 40 + i % 300, replace=False)] = 0.5
+    a = sp.csr_matrix(a)
+    a.data = rng.normal(size=a.data.size)
+    if not signed:
+        r, c = a.nonzero()
+        a.data = np.where(r == c, a.data, np.abs(a.data))
+    a = a.tolil()
+    for i in range(0, n, 9):  # every 9th row empty
+        a.rows[i] = []
+        a.data[i] = []
+    m = sp.csr_matrix(a)
+    m.sort_indices()
+    return W.CSR(n, m.indptr.astype(np.int64), m.indices.astype(np.int32), m.data.astype(np.float64))
+
+
+def test_prepare_and_coefficients_on_every_row_class(mcx):
+    """Taylor terms, features and coefficients on a matrix with empty, short, long and
+    hub rows and a ragged last window of the row schedule, against the oracle."""
+    csr = _mixed_rows()
+    deg = np.diff(csr.row_ptr)
+    assert deg.min() == 0 and deg.max() > 1024 and np.any((deg > 32) & (deg <= 1024)) and csr.n % 256
+    v = W.uniform_vector(csr.n, 3, -1.0, 1.0)
+    t = 0.05
+    rp, col, val = _dev(csr)
+    T, F = mcx.cv_prepare(rp, col, val, torch.as_tensor(v).cuda(), t)
+    oF, _, oT = CV.features(csr, v, t)
+    assert np.all(np.abs(T.cpu().numpy() - oT) <= _fp64_bound(csr, v))
+    assert np.allclose(F.cpu().numpy(), oF.astype(np.float32), rtol=2e-6, atol=1e-6)
+    y = torch.as_tensor(np.random.default_rng(2).normal(0, 0.3, csr.n).astype(np.float32)).cuda()
+    coef = mcx.cv_coefficients(rp, col, val, T, y, t).cpu().numpy()
+    T2 = oT[0] + t * oT[1] + t * t * oT[2] / 2
+    xhat = T2 * np.exp(y.cpu().numpy().astype(np.float64))
+    _, ca, cb = CV.cv_coefficients(csr, oT, t, xhat)
+    B = _fp64_bound(csr, v)
+    assert np.all(np.abs(coef[2 * csr.n:] - xhat) <= 1e-15 * np.abs(xhat) + np.exp(y.cpu().numpy()) *
+                  (t * B[1] + t * t * B[2] / 2) + 1e-300)
+    ab = coef[:2 * csr.n].reshape(csr.n, 2)
+    assert np.allclose(ab[:, 0], ca, rtol=1e-11, atol=1e-12 * np.abs(ca).max())
+    assert np.allclose(ab[:, 1], cb, rtol=1e-10, atol=1e-11 * np.abs(cb).max())
+
+
 @pytest.mark.parametrize("scale", [1.0, 3e-26])  # 3e-26: rates below 2^-74, the FP64 feature sums
 def test_prepare_matches_oracle(mcx, scale):
     import dataclasses

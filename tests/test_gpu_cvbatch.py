@@ -208,6 +208,30 @@ def test_cvbatch_unbiased_against_expm(mcx):
     net.close()
 
 
+def test_cvbatch_coefficients_bit_identical_on_every_row_class(mcx):
+    """The batch's pre-pass (slot CSR, sliced ELL short rows, fused A^3 v / A c3 pass)
+    gives the bits of the single-problem calls on matrices with empty, short, long and
+    hub rows, for two problems with two right-hand sides each."""
+    from test_gpu_cv import _mixed_rows
+
+    csrs = [_mixed_rows(2037, 6, signed=False), _mixed_rows(1100, 7, signed=False)]
+    probs = [dict(row_ptr=c.row_ptr, col=c.col, val=c.val,
+                  v=np.stack([W.uniform_vector(c.n, 20 + i, -1.0, 1.0), W.uniform_vector(c.n, 30 + i)]),
+                  t=np.array([0.05, 0.02]), paths=8) for i, c in enumerate(csrs)]
+    net = _net(mcx)
+    b = mcx.CVBatch(probs, control="learned", net=net)
+    b.run(seed=1)
+    for pb, c in enumerate(csrs):
+        rp, col, val = _dev(c)
+        for r in range(2):
+            v, t = probs[pb]["v"][r], float(probs[pb]["t"][r])
+            T, F = mcx.cv_prepare(rp, col, val, torch.as_tensor(v).cuda(), t)
+            assert torch.equal(b.coefficients(pb, r), mcx.cv_coefficients(rp, col, val, T, net.predict(F), t))
+    assert b.sync()["status_bits"] == 0
+    b.close()
+    net.close()
+
+
 def test_cvbatch_rejects_invalid_descriptions(mcx):
     probs = _problems()
     d = _desc(probs)
