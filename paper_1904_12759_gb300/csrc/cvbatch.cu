@@ -68,6 +68,7 @@ struct CvbPair {
     uint32_t cpe;        // chunks per entry; 0: lane layout (paths <= LANE_MODE_MAX_PATHS)
     int32_t problem, rhs;
     double inv_m, inv_m1;  // 1/paths, 1/(paths - 1) (0 for one path)
+    float inv_mf, inv_m1f;  // the same rounded to FP32
 };
 
 struct CvbItem {
@@ -312,12 +313,27 @@ __global__ void __launch_bounds__(WALK_THREADS, CV ? CVB_MIN_BLOCKS_CV : CVB_MIN
                 paths_done += pr.paths;
                 const double M = (double)pr.paths;
                 double S1, S2, Mw;
-                if constexpr (CV && !F64) {
-                    // FP32 integrals, one entry per lane: the few FP64 operations of the
-                    // finish (GB300 runs FP64 slowly) -- e^Mw of the FP32 maximum by the
-                    // table-driven exponential, the divisions by M as products with the
-                    // pair's reciprocals, the standard error's root in FP32 where its
-                    // argument is well inside the FP32 range (relative error 2^-23)
+                const int ku = b.vexp[it.pair] ? (int)b.vexp[it.pair] - (int)VEXP_BIAS : 0;
+                if (CV && !F64 && cl.m >= -40.0f && cl.m <= 40.0f && ku >= -60 && ku <= 60) {
+                    // FP32 integrals, one entry per lane, scale e^m 2^k inside the FP32
+                    // range: the residual mean and standard error in FP32 (the sums are
+                    // FP32 already; GB300 runs FP64 slowly), added to h in FP64
+                    const float sc = __fmul_rn(expf(cl.m), __uint_as_float((uint32_t)(ku + 127) << 23));
+                    const float s1 = __fsub_rn(cl.f1, cl.c1);
+                    const float muf = __fmul_rn(s1, pr.inv_mf);
+                    float varf = __fmul_rn(__fsub_rn(cl.f2, __fmul_rn(s1, muf)), pr.inv_m1f);
+                    if (!(varf > 0.0f)) varf = 0.0f;
+                    const double mv = b.h[pr.slot + e] + (double)__fmul_rn(sc, muf);
+                    const double se = (double)__fmul_rn(sc, __fsqrt_rn(__fmul_rn(varf, pr.inv_mf)));
+                    b.mean[pr.slot + e] = mv;
+                    b.sem[pr.slot + e] = se;
+                    if (!finite_bits(mv) || !finite_bits(se)) atomicOr(a.status, ST_OVERFLOW);
+                } else if constexpr (CV && !F64) {
+                    // FP32 integrals with a scale outside that range: the few FP64 operations
+                    // of the finish -- e^Mw of the FP32 maximum by the table-driven
+                    // exponential, the divisions by M as products with the pair's
+                    // reciprocals, the standard error's root in FP32 where its argument is
+                    // well inside the FP32 range (relative error 2^-23)
                     cl.result(S1, S2, Mw);
                     const float mf = (float)Mw;
                     const double scale = (mf == -INFINITY ? 0.0 : exp_of_f32(mf)) * up;
@@ -595,6 +611,8 @@ void layout_pairs(mcx_cvbatch *b) {
         pr.paths = b->paths[pr.problem];
         pr.inv_m = 1.0 / (double)pr.paths;
         pr.inv_m1 = pr.paths > 1 ? 1.0 / (double)(pr.paths - 1) : 0.0;
+        pr.inv_mf = (float)pr.inv_m;
+        pr.inv_m1f = (float)pr.inv_m1;
         if (pr.paths <= LANE_MODE_MAX_PATHS) {
             pr.cpe = 0;
             pr.chunk = pr.paths;
