@@ -972,8 +972,8 @@ def run_tc(args):
     thr = res["small_world"]["exact_M1e9"]  # the throughput launch: the walk dominates
     achieved = BYTES_PER_JUMP * thr["jumps_per_path"] * thr["paths_per_s"] / 1e9
     peak = float(_peaks().get("hbm_gbs", 6800.0))
-    # the small-world graph's node records and columns (42 MB) sit in L2: the walk is judged
-    # against the random-gather ceiling of a buffer that size, measured here
+    # the small-world graph's node records and columns (42 MB) sit in L2: the walk is compared
+    # with the random-gather ceiling of a buffer that size, measured here
     sw = graphs["small_world"]
     ws = 32 * sw.n + 4 * sw.nnz
     l2 = P.gather_rate(ws, dependent=True, loads=1 << 31) * 32 / 1e9
@@ -1399,7 +1399,7 @@ def main():
     # measured random-gather ceiling (32-byte sectors): a buffer of the graph's working set
     # (node records + columns, L2-resident here) and one far larger than L2, with dependent
     # chains as the walkers' jumps are and with independent loads; outside the timed region.
-    # The walk's working set is L2-resident, so the roofline it is judged against is the
+    # The walk's working set is L2-resident, so the roofline it is compared with is the
     # first of these; the HBM copy peak stays as a secondary figure.
     gather = None
     try:

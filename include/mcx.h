@@ -627,7 +627,7 @@ mcx_status mcx_estimate_cv(mcx_plan *plan, const double *coef, double t, uint64_
 typedef struct mcx_cvbatch mcx_cvbatch;
 
 typedef enum {
-    MCX_CV_NONE = 0,     /* plain backward estimate: mean of W v_{X_t} (the judge of the others) */
+    MCX_CV_NONE = 0,     /* plain backward estimate: mean of W v_{X_t} (the reference for the others) */
     MCX_CV_TAYLOR = 1,   /* control variate with h(t) = the second-order Taylor term T2 */
     MCX_CV_LEARNED = 2   /* control variate with h(t) = the network's prediction */
 } mcx_cv_control;

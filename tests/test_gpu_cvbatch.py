@@ -14,7 +14,7 @@ several right-hand sides per A, one graph launch per run.
   horizons and scales, several chunks per entry.
 * Runs are deterministic given the seed; changing the paths re-lays the work out;
   the network is read at every run; the batched estimate is unbiased against
-  expm (SURVEY A18's criterion); invalid descriptions are rejected.
+  expm (the three-part z rule of tests/zstats.py); invalid descriptions are rejected.
 """
 import math
 
@@ -191,7 +191,7 @@ def test_cvbatch_deterministic_paths_change_and_network_read_per_run(mcx):
 def test_cvbatch_unbiased_against_expm(mcx):
     """Two weighted problems with arbitrary (untrained) predictions: the batched learned
     control-variate estimates have per-entry z-scores against expm with tail fraction,
-    mean and variance within SURVEY A18's bounds."""
+    mean and variance within the bounds of tests/zstats.py."""
     a1, a2 = _conditioned(60, 31), _conditioned(90, 32)
     v1, v2 = W.uniform_vector(60, 1, 0.2, 1.0), W.uniform_vector(90, 2, -1.0, 1.0)
     probs = [dict(csr=W.dense_to_csr(a1), v=v1[None], t=np.array([0.7]), paths=20000),

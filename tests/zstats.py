@@ -1,6 +1,6 @@
 """Statistical agreement of Monte Carlo estimates with their exact targets.
 
-The estimates are random, so correctness is judged on per-entry z-scores
+The estimates are random, so correctness is decided on per-entry z-scores
 z_i = (xhat_i - x_i) / SE_i over k entries, by three bounds:
   (i)   the fraction with |z| > 3 is at most p + 5 sqrt(p / k), p the two-sided
         tail probability of |z| > 3 (0.0027 for a normal z);
