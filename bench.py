@@ -788,6 +788,21 @@ def run_cvbatch(args):
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
     st = b.sync()
+    # FP32 against FP64 residual integrals on the same FP32 paths (outside the timed region):
+    # the last timed seed again through an FP64-integral batch of the same problems
+    b64 = P.CVBatch(probs, control="learned", net=net, prec="fp64", tune_cache=args.tune_cache)
+    b64.run(seed=SEED + args.steps - 1)
+    rels = []
+    for i in range(len(probs)):
+        for r in range(2):
+            x32 = b.result(i, r)[0].cpu().numpy()
+            x64 = b64.result(i, r)[0].cpu().numpy()
+            rels.append(np.abs(x32 - x64) / np.maximum(np.abs(x64), 1e-300))
+    b64.sync()
+    b64.close()
+    rels = np.concatenate(rels)
+    fp64 = {"max_rel_diff": float(rels.max()), "median_rel_diff": float(np.median(rels)), "entries": int(rels.size),
+            "note": "both precisions walk the same FP32 paths; FP64 is the residual integrals' accumulation"}
     paths = st["paths"] / args.steps
     step_s = sum(ms) / 1e3 / args.steps
     line = {"metric": "walker paths/s (batched learned control variate)", "value": paths / step_s,
@@ -798,7 +813,7 @@ def run_cvbatch(args):
                        "states": int(sizes.sum()), "paths_per_entry": 64, "control": "learned",
                        "schedule": {k: info[k] for k in ("chunk", "blocks_per_sm", "staged", "grid", "work_items")}},
             "walker": {"paths": paths, "jumps_per_path": st["jumps"] / max(st["paths"], 1), "batch_create_s": create_s},
-            "clocks": clk.summary()}
+            "fp64_check": fp64, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     b.close()
     net.close()
@@ -1126,6 +1141,24 @@ def run_mlmc(args):
         (ms_out, ms_single) = timed(lambda: plan.estimate(v, t, M_single, seed=SEED + 3, mode="strang",
                                                           nsteps=n0 << L))
         (me_out, ms_exact) = timed(lambda: plan.estimate(v, t, M_single, seed=SEED + 4))
+    # FP32 against FP64 paths (outside the timed region): the multilevel estimate with the
+    # same allocation and seed in both precisions, and the traced index sequences of the
+    # finest level's paths for 16 entries (the split functional does not move the paths)
+    m64, s64, _ = mlmc.estimate(plan, v, t, n0, L, Ms, seed=SEED + 1, prec="fp64")
+    m64, s64 = m64.cpu().numpy(), s64.cpu().numpy()
+    diverged = 0
+    for i in range(0, n, n // 16):
+        a32 = plan.trace(t, i, seed=SEED + 1, first_path=L * mlmc.LEVEL_STRIDE, count=4096, mode="strang",
+                         nsteps=n0 << L, prec="fp32")
+        a64 = plan.trace(t, i, seed=SEED + 1, first_path=L * mlmc.LEVEL_STRIDE, count=4096, mode="strang",
+                         nsteps=n0 << L, prec="fp64")
+        same = (a32["end"] == a64["end"]) & (a32["njumps"] == a64["njumps"]) & (a32["hash"] == a64["hash"])
+        diverged += int((~same).sum().item())
+    plan.sync()
+    fp64 = {"max_rel_diff": float(np.max(np.abs(mean - m64) / np.abs(m64))),
+            "median_rel_diff": float(np.median(np.abs(mean - m64) / np.abs(m64))),
+            "max_diff_in_fp64_se": float(np.max(np.abs(mean - m64) / np.maximum(s64, 1e-300))),
+            "diverged_path_fraction": diverged / (16 * 4096), "traced_paths": 16 * 4096}
     plan.close()
     rel = lambda x, y: float(np.linalg.norm(x - y) / np.linalg.norm(y))  # noqa: E731
     line = {"metric": "multilevel (STRANG, N = 2..64) GPU time at sampling error 1e-4", "value": ms_ml, "unit": "ms",
@@ -1143,7 +1176,7 @@ def run_mlmc(args):
                                  "rel_l2_vs_expm": rel(me_out[0].cpu().numpy(), exact)},
             "strang64_bias_rel_l2": rel(target, exact),
             "cost_ratio_mlmc_over_single": ms_ml / ms_single,
-            "clocks": clk.summary()}
+            "fp64_check": fp64, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
