@@ -209,6 +209,21 @@ def test_power_iteration_vs_oracle(mcx):
 
 
 @pytest.mark.parametrize("scale", [1.0, 1e-30, 1e60])
+def test_power_iteration_fused_rows_at_scale(mcx, scale):
+    """A matrix without long rows (the fused one-kernel iteration) with its values
+    scaled by 1, 1e-30 and 1e60: the quotient agrees with the oracle's to 1e-10."""
+    import dataclasses
+
+    csr = W.erdos_renyi(50000, 10, 4)
+    assert np.diff(csr.row_ptr).max() <= 32
+    csr = dataclasses.replace(csr, val=csr.val * scale)
+    lam, it = mcx.power_iteration(_cuda(csr.row_ptr, torch.int64), _cuda(csr.col, torch.int32),
+                                  _cuda(csr.val, torch.float64), max_iters=2000, tol=1e-13)
+    want = OD.power_iteration(csr.to_scipy(), iters=20000, tol=1e-15)
+    assert abs(lam - want) / want < 1e-10, (lam, want, it)
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e-30, 1e60])
 def test_power_iteration_hub_rows_and_fp64_fallback(mcx, scale):
     """Barabasi-Albert hubs take the warp-per-row kernels; values below 2^-74 or
     above 2^127 are outside the double-float range and take the FP64 kernels."""
