@@ -82,3 +82,31 @@ def test_walker_log_table_matches_the_oracle_table():
     oinv, oL = OW.ln_table()
     assert np.array_equal(inv.view(np.uint32), oinv.view(np.uint32))
     assert np.array_equal(L.view(np.uint32), oL.view(np.uint32))
+
+
+def test_exponential_table_matches_its_definition():
+    """The FP64 exponential's table (exp_table.cuh, written by its generator script):
+    each entry is 2^(j/64) correctly rounded to FP64 (checked against 40-digit decimal
+    arithmetic, independently of the script), L1 keeps at most 36 significant bits (so
+    N L1 is exact for |N| < 2^17), and L1 + L2 is ln(2)/64 to within an FP64 rounding
+    of L2."""
+    import re
+    import struct
+    from decimal import Decimal, getcontext
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    text = open(os.path.join(here, "..", "paper_1904_12759_gb300", "csrc", "exp_table.cuh")).read()
+    words = [int(w, 16) for w in re.findall(r"0x([0-9a-f]{16})ull", text)]
+    assert len(words) == 64
+    getcontext().prec = 40
+    ln2 = Decimal(2).ln()
+    for j, w in enumerate(words):
+        x = struct.unpack("<d", struct.pack("<Q", w))[0]
+        exact = (Decimal(j) / 64 * ln2).exp()
+        ulp = Decimal(x) - Decimal(struct.unpack("<d", struct.pack("<Q", w - 1))[0])
+        assert abs(Decimal(x) - exact) <= ulp / 2, j
+    l1 = float(re.search(r"EXP_L1 = ([0-9.e+-]+);", text).group(1))
+    l2 = float(re.search(r"EXP_L2 = ([0-9.e+-]+);", text).group(1))
+    mant = struct.unpack("<Q", struct.pack("<d", l1))[0] & ((1 << 52) - 1)
+    assert mant & ((1 << 17) - 1) == 0  # 52 - 17 = 35 stored bits + the implicit one
+    assert abs(Decimal(l1) + Decimal(l2) - ln2 / 64) <= Decimal(2) ** -96
