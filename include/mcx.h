@@ -682,8 +682,10 @@ typedef struct {
  * entry, i.e. exactly the paths of mcx_estimate (MCX_CV_NONE) or
  * mcx_estimate_cv on that problem alone with path_offset = k * 2^40 and the
  * run's seed (EXACT functional).  Synchronises `stream`.
- * Errors: MCX_E_INVALID (bad description or CSR, missing net), MCX_E_NEG_OFFDIAG,
- * MCX_E_NONFINITE, MCX_E_OOM, MCX_E_CUDA.
+ * Limits: the problems' states (each padded to a multiple of 1024) and the
+ * slots (sum over pairs of n) must each stay below 2^31 - 1.
+ * Errors: MCX_E_INVALID (bad description or CSR, missing net, a limit
+ * exceeded), MCX_E_NEG_OFFDIAG, MCX_E_NONFINITE, MCX_E_OOM, MCX_E_CUDA.
  */
 mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *problems, int control, const mcx_mlp *net,
                               int precision, const char *tune_cache, void *stream, mcx_cvbatch **out);

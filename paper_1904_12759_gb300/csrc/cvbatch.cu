@@ -990,7 +990,8 @@ mcx_status mcx_cvbatch_create(int32_t count, const mcx_cv_problem *pr, int contr
         slots += p.n * p.n_rhs;
         snnz += p.nnz * p.n_rhs;
     }
-    if (N >= (int64_t)0x7fffffff) return MCX_E_INVALID;
+    // states of the block-diagonal plan and slots of the pre-pass are indexed in 32 bits
+    if (N >= (int64_t)0x7fffffff || slots >= (int64_t)0x7fffffff) return MCX_E_INVALID;
     mcx_cvbatch *b = new (std::nothrow) mcx_cvbatch();
     if (!b) return MCX_E_OOM;
     b->problems = count;

@@ -110,3 +110,26 @@ def test_exponential_table_matches_its_definition():
     mant = struct.unpack("<Q", struct.pack("<d", l1))[0] & ((1 << 52) - 1)
     assert mant & ((1 << 17) - 1) == 0  # 52 - 17 = 35 stored bits + the implicit one
     assert abs(Decimal(l1) + Decimal(l2) - ln2 / 64) <= Decimal(2) ** -96
+
+
+def test_cvbatch_rejects_slots_beyond_32_bit_indices(lib):
+    """A batch whose pairs' slots (sum of n over pairs) reach 2^31 is rejected with
+    MCX_E_INVALID while the description is checked, before any device work (so this
+    runs without a GPU): 2100 right-hand sides of a 2^20-state problem."""
+    import ctypes as C
+
+    import numpy as np
+
+    from paper_1904_12759_gb300 import _lib
+
+    n, nrhs = 1 << 20, 2100
+    rp = np.zeros(n + 1, np.int64)  # no entries
+    col = np.zeros(1, np.int32)
+    val = np.zeros(1)
+    v = np.zeros(8)  # not read: the limit comes first
+    t = np.full(nrhs, 0.1)
+    pr = _lib.CvProblem(n=n, nnz=0, row_ptr=rp.ctypes.data, col=col.ctypes.data, val=val.ctypes.data,
+                        n_rhs=nrhs, v=v.ctypes.data, t=t.ctypes.data, paths=8)
+    out = C.c_void_p()
+    assert lib.mcx_cvbatch_create(1, C.byref(pr), 0, None, 0, None, None, C.byref(out)) == -1
+    assert not out.value
