@@ -1057,6 +1057,22 @@ def run_splitting(args):
                              "node0_mc_err": abs(m0.item() - x_exact[0]) / x_exact[0],
                              "node0_mc_rel_se": s0.item() / m0.item()}
             rows.append(row)
+        # FP32 against FP64 paths at the finest step (same seeds, outside the sweeps above):
+        # TC and node 0 by STRANG with 64 steps, and the traced index sequences of node 0
+        tc32, _ = plan.total_communicability(1.0, 10 ** 7, mode="strang", nsteps=64, seed=SEED + 5, prec="fp32")
+        tc64, tcs64 = plan.total_communicability(1.0, 10 ** 7, mode="strang", nsteps=64, seed=SEED + 5,
+                                                 prec="fp64")
+        n32, _ = plan.estimate(one, 1.0, 10 ** 6, entries=ent, mode="strang", nsteps=64, seed=SEED + 6, prec="fp32")
+        n64, ns64 = plan.estimate(one, 1.0, 10 ** 6, entries=ent, mode="strang", nsteps=64, seed=SEED + 6,
+                                  prec="fp64")
+        a32 = plan.trace(1.0, 0, seed=SEED + 6, first_path=0, count=65536, mode="strang", nsteps=64, prec="fp32")
+        a64 = plan.trace(1.0, 0, seed=SEED + 6, first_path=0, count=65536, mode="strang", nsteps=64, prec="fp64")
+        same = (a32["end"] == a64["end"]) & (a32["njumps"] == a64["njumps"]) & (a32["hash"] == a64["hash"])
+        fp64 = {"tc_rel_diff": abs(tc32.item() - tc64.item()) / abs(tc64.item()),
+                "tc_diff_in_fp64_se": abs(tc32.item() - tc64.item()) / max(tcs64.item(), 1e-300),
+                "node0_rel_diff": abs(n32.item() - n64.item()) / abs(n64.item()),
+                "node0_diff_in_fp64_se": abs(n32.item() - n64.item()) / max(ns64.item(), 1e-300),
+                "diverged_path_fraction": float((~same).sum().item()) / 65536, "traced_paths": 65536}
         mrows = []
         for M in (10 ** 3, 10 ** 4, 10 ** 5, 10 ** 6, 10 ** 7, 10 ** 8):
             errs = []
@@ -1074,7 +1090,7 @@ def run_splitting(args):
             "config": {"workload": "splitting_small_world_n1000", "beta": 1.0, "tc_exact": tc_exact,
                        "paths_tc": 4e8, "paths_node0": 1e8},
             "slopes": slopes, "dt_sweep": rows, "m_sweep": mrows, "wall_s": time.perf_counter() - t0,
-            "clocks": clk.summary()}
+            "fp64_check": fp64, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
@@ -1197,6 +1213,7 @@ def run_ranking(args):
 
     torch.cuda.set_device(0)
     t1, t3 = [], []
+    fp64 = None
     with ClockSampler(0) as clk:
         for n in (1000, 10000):
             csr = W.small_world(n, 1, 0.2, SEED)
@@ -1209,6 +1226,15 @@ def run_ranking(args):
                 xe = x.cpu().numpy()
                 t1.append({"n": n, "M": M, "isim_100": metrics.isim(xe, exact),
                            "isim_10": metrics.isim(xe, exact, n // 10)})
+                if n == 10000 and M == 10 ** 7:  # FP32 against FP64 paths, same seed (outside the table)
+                    x64, s64 = plan.forward(one, 1.0, M, mode="strang", nsteps=32, seed=SEED + M % 101,
+                                            prec="fp64")
+                    x64, s64 = x64.cpu().numpy(), s64.cpu().numpy()
+                    d = np.abs(xe - x64)
+                    fp64 = {"max_rel_diff": float(np.max(d / np.abs(x64))),
+                            "median_rel_diff": float(np.median(d / np.abs(x64))),
+                            "max_diff_in_fp64_se": float(np.max(d / np.maximum(s64, 1e-300))),
+                            "isim_100_fp64": metrics.isim(x64, exact), "isim_100_fp32": metrics.isim(xe, exact)}
             plan.close()
         for n in (1000, 10000):
             csr = W.barabasi_albert(n, 2, SEED)
@@ -1232,7 +1258,7 @@ def run_ranking(args):
             "unit": "isim over all nodes, small-world n=1e4, M=1e7", "higher_is_better": False, "n_gpus": 1,
             "data": "synthetic", "config": {"workload": "ranking_small_world_scale_free", "dt": 1 / 32,
                                             "functional": "strang"},
-            "table1": t1, "table3": t3, "clocks": clk.summary()}
+            "table1": t1, "table3": t3, "fp64_check": fp64, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
